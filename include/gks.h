@@ -1,0 +1,227 @@
+/*
+ * gks.h -- C ABI of the GB300 (sm_103a) implementation of one explicit step of
+ * the third-order gas-kinetic scheme with compact least-squares (CLS)
+ * reconstruction on unstructured triangular grids
+ * (J. Li, C. Zhong, C. Zhuo, "A third order gas-kinetic scheme for
+ * unstructured grid", arXiv:1802.00704).
+ *
+ * One step (Eq. (6), a single stage):
+ *   1. time step from a CFL condition (not stated in the paper; see gks_cfl_dt);
+ *   2. CLS reconstruction (Sec. III.A, Eqs. (16)-(29)): per cell a quadratic
+ *      zero-mean polynomial (k = 2, linear k = 1 at boundary cells, Eq. (28))
+ *      whose coefficients solve the sparse block system of the per-cell
+ *      least-squares normal equations (Eqs. (32)-(33)); solved by GMRES with an
+ *      ILU(0) preconditioner on a Reverse-Cuthill-McKee order (Sec. III.B);
+ *   3. third-order BGK flux (Sec. II.B, Eqs. (8)-(15)) at two Gauss points per
+ *      face (Eq. (7)), integrated analytically over [0, dt];
+ *   4. conservative update of the cell averages (Eq. (6)).
+ *
+ * Conventions
+ *  - Every array argument documented as "device" is a pointer to device
+ *    memory owned by the caller; "host" arrays are read during the call only.
+ *    The library keeps no pointer to caller memory after a call returns.
+ *  - Cell and face numbering in every argument is the caller's (the order of
+ *    the arrays given to gks_mesh_create).  The library stores its data in RCM
+ *    order and permutes on the way in and out.
+ *  - Cell-average arrays w are float64 SoA [4][n_tri]: rho, rho*u, rho*v, E.
+ *  - Reconstruction coefficients are float64 [4][5][n_tri]: variable, basis
+ *    index l = 1..5 of Eq. (19) stored at 0..4, cell.  At cells with k = 1
+ *    basis indices 3..5 are zero.
+ *  - Face fluxes are float64 [4][n_face]: int_0^dt of the Gauss-summed flux
+ *    (Eq. (7)) times the face length, signed along the normal from cell_l to
+ *    cell_r, in the global frame.
+ *  - `stream` is a cudaStream_t (NULL: the legacy default stream).  Calls are
+ *    stream-ordered; where a call returns host-visible results (info structs,
+ *    dt_out) it synchronises `stream` before returning.
+ *  - A mesh handle must not be used from two host threads or two streams at
+ *    once.  No C++ exception crosses this ABI.
+ *  - Errors: every call returns a gks_status; gks_last_error() gives a
+ *    thread-local message for the last failing call.  Argument errors are
+ *    detected before any device work is queued.  Numerical failures
+ *    (non-physical state, GMRES not converged) are detected on the device and
+ *    reported by the calls that read back an info struct.
+ */
+#ifndef GKS_H
+#define GKS_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GKS_EXPORT __attribute__((visibility("default")))
+#else
+#define GKS_EXPORT
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gks_status {
+    GKS_OK = 0,
+    GKS_EINVAL = 1,        /* bad argument (sizes, indices, pointers, config)        */
+    GKS_ENOMEM = 2,        /* device or host allocation failed                        */
+    GKS_ECUDA = 3,         /* a CUDA runtime call failed                              */
+    GKS_ENOCONV = 4,       /* GMRES reached gmres_maxit before gmres_rtol             */
+    GKS_ENONPHYS = 5,      /* rho <= 0 or p <= 0 at a Gauss point or a cell           */
+    GKS_ETIMEOUT = 6,      /* a bounded device wait gave up                           */
+    GKS_EUNSUPPORTED = 7   /* option not implemented                                  */
+} gks_status;
+
+/* Boundary tags of a face (column 4 of the faces array). */
+enum {
+    GKS_BC_INTERIOR = 0,   /* two cells                                               */
+    GKS_BC_PERIODIC = 1,   /* two cells; face_shift moves cell_r next to cell_l        */
+    GKS_BC_DIRICHLET = 2,  /* ghost = bc_state (conservative), zero derivatives       */
+    GKS_BC_OUTFLOW = 3,    /* ghost = interior state and derivatives                  */
+    GKS_BC_SLIP = 4,       /* ghost = mirror image (normal momentum reversed)         */
+    GKS_BC_NOSLIP = 5      /* ghost: velocity reflected about the wall velocity,
+                              temperature about the wall temperature; bc_state =
+                              (u_wall, v_wall, T_wall, 0), T = p / rho               */
+};
+
+/* Preconditioner of the CLS GMRES. */
+enum {
+    GKS_PC_ILU_EXACT = 0,  /* block ILU(0) on the RCM order, level-scheduled exact
+                              triangular solves (Sec. III.B as written)              */
+    GKS_PC_ILU_SWEEP = 1,  /* the same ILU(0) factors, each triangular solve applied
+                              by ilu_sweeps block-Jacobi sweeps (fully parallel)     */
+    GKS_PC_BJACOBI = 2     /* block-diagonal (cell) inverse only                      */
+};
+
+enum { GKS_FP64 = 0, GKS_MIXED = 1 };
+
+typedef struct gks_config {
+    double gamma;          /* ratio of specific heats; K = 2/(gamma-1) - 2 (Eq. (3)) */
+    double cfl;            /* CFL number                                              */
+    double mu;             /* dynamic viscosity; 0: inviscid collision time Eq. (39),
+                              > 0: viscous collision time Eq. (40)                    */
+    double cls_w;          /* derivative weight w of Eq. (29) (paper: 0.3)             */
+    int32_t gmres_m;       /* GMRES restart length (<= 64)                             */
+    int32_t gmres_maxit;   /* iteration cap per variable and reconstruction            */
+    double gmres_rtol;     /* ||b - A x||_2 <= gmres_rtol ||b||_2                       */
+    int32_t precision;     /* GKS_FP64 (only value implemented by this version)       */
+    int32_t precond;       /* GKS_PC_*                                                 */
+    int32_t ilu_sweeps;    /* sweeps per triangular solve for GKS_PC_ILU_SWEEP         */
+    int32_t tau2_exact;    /* 0: c4, c5, c6 exactly as printed in Eq. (13);
+                              1: with the 2 tau^2 (1 - e^{-t/tau}) term that the exact
+                              time integral of Eq. (8) carries                          */
+    int32_t reserved[8];   /* must be zero                                             */
+} gks_config;
+
+typedef struct gks_mesh gks_mesh;
+
+typedef struct gks_solve_info {
+    int32_t iters[4];      /* GMRES iterations per conserved variable                  */
+    double relres[4];      /* final ||b - A x|| / ||b|| (0 when b = 0)                  */
+    int32_t converged;     /* 1 if all four met gmres_rtol                              */
+} gks_solve_info;
+
+typedef struct gks_step_info {
+    double dt;             /* step taken                                               */
+    int32_t iters[4];
+    double relres[4];
+    int32_t status;        /* GKS_OK, GKS_ENONPHYS or GKS_ENOCONV                      */
+} gks_step_info;
+
+typedef struct gks_run_info {
+    int64_t steps;         /* steps taken                                              */
+    double t;              /* time reached                                             */
+    double last_dt;
+    int64_t gmres_iters;   /* sum over steps and variables                             */
+    double steady_res;     /* max over variables of the area-weighted L2 norm of
+                              (w^{n+1} - w^n)/dt, relative to its first-step value       */
+    int32_t status;
+} gks_run_info;
+
+typedef struct gks_mesh_stats {
+    int64_t n_tri, n_face, n_boundary_face;
+    int64_t n_k1;          /* cells reconstructed at k = 1                              */
+    int64_t nnzb;          /* 5x5 blocks of the CLS operator                            */
+    int32_t levels_lower;  /* level-schedule depth of the forward ILU solve             */
+    int32_t levels_upper;  /* ... and of the backward solve                             */
+    int64_t rcm_bandwidth; /* max |i - j| over neighbouring cells in RCM order          */
+    int64_t device_bytes;  /* device memory held by the handle                          */
+} gks_mesh_stats;
+
+/* Fill *cfg with defaults: gamma 1.4, cfl 0.3, mu 0, cls_w 0.3, gmres_m 30,
+ * gmres_maxit 1000, gmres_rtol 1e-12, FP64, GKS_PC_ILU_SWEEP with 2 sweeps,
+ * tau2_exact 0. */
+GKS_EXPORT void gks_config_default(gks_config *cfg);
+
+/* Build the mesh handle on the current CUDA device (host set-up: geometry,
+ * k_i of Eq. (28), RCM order, CLS blocks of Eq. (29), block ILU(0) factors and
+ * level sets; then one upload).  All inputs are host arrays, copied:
+ *   nodes      [n_nodes][2] float64 coordinates;
+ *   tris       [n_tri][3] int32 node indices (any orientation);
+ *   faces      [n_face][5] int32: n0, n1 (node indices in cell_l's frame),
+ *              cell_l, cell_r (-1 on a non-periodic boundary), bc tag
+ *              (GKS_BC_*); every cell has at most three faces;
+ *   face_shift [n_face][2] float64: translation added to cell_r's coordinates
+ *              to place it next to cell_l across a periodic face, else 0;
+ *   bc_state   [n_face][4] float64: per-face boundary data (see GKS_BC_*);
+ *   cfg        may be NULL for the defaults.
+ * Errors: GKS_EINVAL (sizes <= 0, an index out of range, degenerate triangle,
+ * a cell with more than three faces, tag/cell_r mismatch, bad config),
+ * GKS_ENOMEM, GKS_ECUDA.  On error *out is NULL. */
+GKS_EXPORT gks_status gks_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t n_tri,
+                           const int32_t *faces, const double *face_shift, int64_t n_face,
+                           const double *bc_state, const gks_config *cfg, gks_mesh **out);
+
+/* Free every device and host resource of the handle (NULL is accepted). */
+GKS_EXPORT gks_status gks_mesh_destroy(gks_mesh *mesh);
+
+/* Sizes and solver structure of a handle (host output). */
+GKS_EXPORT gks_status gks_mesh_get_stats(const gks_mesh *mesh, gks_mesh_stats *stats);
+
+/* Time step dt = cfl * min_i r_i / (|U_i| + c_i + 2 mu / (rho_i r_i)), r_i the
+ * inradius of cell i (the paper does not state its CFL rule).
+ * w: device [4][n_tri].  *dt_out: host.  Synchronises the stream. */
+GKS_EXPORT gks_status gks_cfl_dt(gks_mesh *mesh, const double *w, double *dt_out, void *stream);
+
+/* CLS reconstruction (Sec. III): solves the per-cell least-squares system
+ * for the four variables of w (device [4][n_tri]) and writes the coefficients
+ * to coef (device [4][5][n_tri]).  GMRES starts from the handle's previous
+ * solution (zero after creation or gks_reset_warm_start).  info (host, may be
+ * NULL) receives iterations and residuals; GKS_ENOCONV when a variable did not
+ * converge within gmres_maxit. */
+GKS_EXPORT gks_status gks_cls_reconstruct(gks_mesh *mesh, const double *w, double *coef, gks_solve_info *info,
+                               void *stream);
+
+/* Forget the warm start of the reconstruction. */
+GKS_EXPORT gks_status gks_reset_warm_start(gks_mesh *mesh);
+
+/* Third-order BGK face fluxes (Sec. II.B) for given cell averages w (device
+ * [4][n_tri]) and coefficients coef (device [4][5][n_tri]) over the step dt > 0;
+ * writes face_flux (device [4][n_face]).  Returns GKS_ENONPHYS if a Gauss-point
+ * state had rho <= 0 or p <= 0 (synchronises the stream to find out). */
+GKS_EXPORT gks_status gks_flux(gks_mesh *mesh, const double *w, const double *coef, double dt, double *face_flux,
+                    void *stream);
+
+/* One explicit step (Eq. (6)) in place on w (device [4][n_tri]).
+ * *dt_inout (host): > 0 fixes the step; <= 0 takes the CFL step and returns it.
+ * info (host, may be NULL).  The call synchronises the stream. */
+GKS_EXPORT gks_status gks_step(gks_mesh *mesh, double *w, double *dt_inout, gks_step_info *info, void *stream);
+
+/* Steps w (device [4][n_tri]) in place until t_final (the last step is cut to
+ * land on it; t_final <= 0: no time limit), max_steps steps, or, if
+ * steady_tol > 0, until the steady residual (gks_run_info) drops below it.
+ * info (host, may be NULL). */
+GKS_EXPORT gks_status gks_run(gks_mesh *mesh, double *w, double t_final, int64_t max_steps, double steady_tol,
+                   gks_run_info *info, void *stream);
+
+/* Gauss-point flux kernel on its own (Sec. II.B), for n independent points in
+ * their face frames: wl, wr device [n][6][4] (rows: value, d/dn, d/dt,
+ * d2/dn2, d2/dndt, d2/dt2 of rho, rho*U, rho*V, E; U normal from left to
+ * right); out device [n][4] = int_0^dt of the flux through a unit-length face.
+ * cfg supplies gamma, mu and tau2_exact (NULL: defaults).  Stream-ordered, no
+ * synchronisation. */
+GKS_EXPORT gks_status gks_point_flux(int64_t n, const double *wl, const double *wr, double dt, const gks_config *cfg,
+                          double *out, void *stream);
+
+/* Thread-local message of the last error, or "" if none. */
+GKS_EXPORT const char *gks_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GKS_H */

@@ -265,6 +265,37 @@ static void ghost_state(const or_mesh *m, int64_t f, const double *wl, double *w
     }
 }
 
+/* Time-integrated flux of face f (global frame, 4 values).  Returns the
+ * number of its Gauss points with a non-physical state. */
+static int face_flux_one(const or_mesh *m, const double *w, const double *coef, double dt, int64_t f, double *out)
+{
+    const int *fc = &m->face[5 * f];
+    const double nx = m->fnx[f], ny = m->fny[f];
+    double acc[4] = {0, 0, 0, 0};
+    int bad = 0;
+    for (int g = 0; g < 2; ++g) {
+        double x = m->gx[2 * f + g], y = m->gy[2 * f + g];
+        double gl[24], gr[24], wl[24], wr[24], F4[4];
+        eval_cell(m, w, coef, fc[2], x, y, gl);
+        to_face_frame(gl, nx, ny, wl);
+        if (fc[3] >= 0) {
+            eval_cell(m, w, coef, fc[3], x - m->shift[2 * f], y - m->shift[2 * f + 1], gr);
+            to_face_frame(gr, nx, ny, wr);
+        } else {
+            ghost_state(m, f, wl, wr);
+        }
+        if (or_gp_flux(wl, wr, dt, &m->prm, F4, NULL) != 0) ++bad;
+        for (int v = 0; v < 4; ++v) acc[v] += 0.5 * F4[v];       /* Gauss weight 1/2 */
+    }
+    /* back to the global frame, times the face length (Eq. (7)) */
+    double S = m->flen[f];
+    out[0] = S * acc[0];
+    out[1] = S * (nx * acc[1] - ny * acc[2]);
+    out[2] = S * (ny * acc[1] + nx * acc[2]);
+    out[3] = S * acc[3];
+    return bad;
+}
+
 /* Time-integrated face fluxes [4][F] (global frame) for the states w, the CLS
  * coefficients and the step dt.  Returns the number of Gauss points with a
  * non-physical state. */
@@ -272,32 +303,26 @@ int or_face_flux(const or_mesh *m, const double *w, const double *coef, double d
 {
     const int64_t F = m->n_face;
     int bad = 0;
-    /* faces are independent: optional OpenMP over faces (no reduction order issue) */
+    /* faces are independent: optional OpenMP over faces */
     #pragma omp parallel for schedule(dynamic, 64) reduction(+ : bad)
     for (int64_t f = 0; f < F; ++f) {
-        const int *fc = &m->face[5 * f];
-        const double nx = m->fnx[f], ny = m->fny[f];
-        double acc[4] = {0, 0, 0, 0};
-        for (int g = 0; g < 2; ++g) {
-            double x = m->gx[2 * f + g], y = m->gy[2 * f + g];
-            double gl[24], gr[24], wl[24], wr[24], F4[4];
-            eval_cell(m, w, coef, fc[2], x, y, gl);
-            to_face_frame(gl, nx, ny, wl);
-            if (fc[3] >= 0) {
-                eval_cell(m, w, coef, fc[3], x - m->shift[2 * f], y - m->shift[2 * f + 1], gr);
-                to_face_frame(gr, nx, ny, wr);
-            } else {
-                ghost_state(m, f, wl, wr);
-            }
-            if (or_gp_flux(wl, wr, dt, &m->prm, F4, NULL) != 0) ++bad;
-            for (int v = 0; v < 4; ++v) acc[v] += 0.5 * F4[v];       /* Gauss weight 1/2 */
-        }
-        /* back to the global frame, times the face length (Eq. (7)) */
-        double S = m->flen[f];
-        flux[0 * F + f] = S * acc[0];
-        flux[1 * F + f] = S * (nx * acc[1] - ny * acc[2]);
-        flux[2 * F + f] = S * (ny * acc[1] + nx * acc[2]);
-        flux[3 * F + f] = S * acc[3];
+        double o[4];
+        bad += face_flux_one(m, w, coef, dt, f, o);
+        for (int v = 0; v < 4; ++v) flux[v * F + f] = o[v];
+    }
+    return bad;
+}
+
+/* Fluxes of the listed faces only: out[4][n] (sampled checks on large meshes). */
+int or_face_flux_subset(const or_mesh *m, const double *w, const double *coef, double dt, const int64_t *ids,
+                        int64_t n, double *out)
+{
+    int bad = 0;
+    #pragma omp parallel for schedule(dynamic, 16) reduction(+ : bad)
+    for (int64_t q = 0; q < n; ++q) {
+        double o[4];
+        bad += face_flux_one(m, w, coef, dt, ids[q], o);
+        for (int v = 0; v < 4; ++v) out[v * n + q] = o[v];
     }
     return bad;
 }

@@ -70,6 +70,8 @@ def _load():
         lib.or_eval_cell.argtypes = [P, P, P, I, D, D, P]
         lib.or_face_flux.restype = I
         lib.or_face_flux.argtypes = [P, P, P, D, P]
+        lib.or_face_flux_subset.restype = I
+        lib.or_face_flux_subset.argtypes = [P, P, P, D, P, I64, P]
         lib.or_update.argtypes = [P, P, P]
         lib.or_cfl_dt.restype = D
         lib.or_cfl_dt.argtypes = [P, P]
@@ -203,6 +205,17 @@ class OracleMesh:
         coef = np.ascontiguousarray(coef, dtype=np.float64)
         out = np.zeros((4, self.F))
         bad = self._lib.or_face_flux(self._h, _ptr(w), _ptr(coef), float(dt), _ptr(out))
+        if bad:
+            raise FloatingPointError(f"{bad} Gauss points with a non-physical state")
+        return out
+
+    def face_flux_subset(self, w, coef, dt: float, ids) -> np.ndarray:
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        coef = np.ascontiguousarray(coef, dtype=np.float64)
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        out = np.zeros((4, ids.shape[0]))
+        bad = self._lib.or_face_flux_subset(self._h, _ptr(w), _ptr(coef), float(dt), _ptr(ids), ids.shape[0],
+                                            _ptr(out))
         if bad:
             raise FloatingPointError(f"{bad} Gauss points with a non-physical state")
         return out

@@ -1,0 +1,339 @@
+// C ABI entry points (include/gks.h).
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "gks_internal.h"
+
+namespace gks {
+const char *last_error();
+}
+
+using namespace gks;
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+gks_status check_config(const gks_config &c)
+{
+    bool ok = c.gamma > 1.0 && c.cfl > 0.0 && c.mu >= 0.0 && c.cls_w > 0.0 && c.gmres_m >= 1 &&
+              c.gmres_m <= kMaxRestart && c.gmres_maxit >= 1 && c.gmres_rtol > 0.0 &&
+              (c.tau2_exact == 0 || c.tau2_exact == 1) && c.ilu_sweeps >= 0 && c.ilu_sweeps <= 16;
+    for (int q = 0; q < 8; ++q) ok = ok && c.reserved[q] == 0;
+    if (!ok) {
+        set_error("invalid gks_config");
+        return GKS_EINVAL;
+    }
+    if (c.precision != GKS_FP64) {
+        set_error("gks_config.precision: only GKS_FP64 is implemented");
+        return GKS_EUNSUPPORTED;
+    }
+    if (c.precond != GKS_PC_ILU_EXACT && c.precond != GKS_PC_ILU_SWEEP) {
+        set_error("gks_config.precond: only GKS_PC_ILU_EXACT and GKS_PC_ILU_SWEEP are implemented");
+        return GKS_EUNSUPPORTED;
+    }
+    return GKS_OK;
+}
+
+gks_status read_status(gks_mesh *m, cudaStream_t s, int32_t *out)
+{
+    GKS_CUDA(cudaMemcpyAsync(m->wk.h_ctl + 16, m->wk.status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    GKS_CUDA(cudaStreamSynchronize(s));
+    *out = m->wk.h_ctl[16];
+    return GKS_OK;
+}
+
+// one step on the internal state m->wk.w; dt_fixed > 0 fixes the step
+gks_status step_internal(gks_mesh *m, double dt_fixed, cudaStream_t s, gks_step_info *info, double *dt_taken)
+{
+    gks_status st;
+    Work &k = m->wk;
+    if (dt_fixed > 0.0) {
+        k.h_scal[7] = dt_fixed;
+        GKS_CUDA(cudaMemcpyAsync(k.dt, &k.h_scal[7], sizeof(double), cudaMemcpyHostToDevice, s));
+    } else if ((st = launch_cfl_dt(m, k.w, k.dt, s)) != GKS_OK) {
+        return st;
+    }
+    gks_solve_info si;
+    if ((st = cls_solve(m, s, &si)) != GKS_OK) return st;
+    if ((st = launch_flux(m, k.w, k.x, 0.0, k.dt, k.flux, s)) != GKS_OK) return st;
+    if ((st = launch_update(m, k.w, k.flux, s)) != GKS_OK) return st;
+    GKS_CUDA(cudaMemcpyAsync(&k.h_scal[6], k.dt, sizeof(double), cudaMemcpyDeviceToHost, s));
+    int32_t stat = 0;
+    if ((st = read_status(m, s, &stat)) != GKS_OK) return st;
+    if (dt_taken) *dt_taken = k.h_scal[6];
+    gks_status res = GKS_OK;
+    if (!si.converged) res = GKS_ENOCONV;
+    if (stat & kStatusNonPhys) res = GKS_ENONPHYS;
+    if (info) {
+        info->dt = k.h_scal[6];
+        for (int v = 0; v < 4; ++v) {
+            info->iters[v] = si.iters[v];
+            info->relres[v] = si.relres[v];
+        }
+        info->status = res;
+    }
+    if (res == GKS_ENOCONV) set_error("GMRES did not reach gmres_rtol within gmres_maxit");
+    if (res == GKS_ENONPHYS) set_error("non-physical state (rho <= 0 or p <= 0)");
+    return res;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gks_config_default(gks_config *c)
+{
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->gamma = 1.4;
+    c->cfl = 0.3;
+    c->mu = 0.0;
+    c->cls_w = 0.3;
+    c->gmres_m = 30;
+    c->gmres_maxit = 1000;
+    c->gmres_rtol = 1e-12;
+    c->precision = GKS_FP64;
+    c->precond = GKS_PC_ILU_SWEEP;
+    c->ilu_sweeps = 2;
+    c->tau2_exact = 0;
+}
+
+const char *gks_last_error(void) { return gks::last_error(); }
+
+gks_status gks_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t n_tri,
+                           const int32_t *faces, const double *face_shift, int64_t n_face, const double *bc_state,
+                           const gks_config *cfg, gks_mesh **out)
+{
+    set_error("");
+    if (!out) {
+        set_error("gks_mesh_create: out is NULL");
+        return GKS_EINVAL;
+    }
+    *out = nullptr;
+    gks_mesh *m = new (std::nothrow) gks_mesh();
+    if (!m) {
+        set_error("gks_mesh_create: host allocation failed");
+        return GKS_ENOMEM;
+    }
+    if (cfg) m->cfg = *cfg;
+    else gks_config_default(&m->cfg);
+    gks_status st = check_config(m->cfg);
+    if (st == GKS_OK && cudaGetDevice(&m->device) != cudaSuccess) {
+        set_error("gks_mesh_create: no CUDA device");
+        st = GKS_ECUDA;
+    }
+    if (st == GKS_OK) st = build_mesh(m, nodes, n_nodes, tris, n_tri, faces, face_shift, n_face, bc_state);
+    if (st != GKS_OK) {
+        free_mesh(m);
+        delete m;
+        return st;
+    }
+    *out = m;
+    return GKS_OK;
+}
+
+gks_status gks_mesh_destroy(gks_mesh *m)
+{
+    if (!m) return GKS_OK;
+    DeviceGuard g(m->device);
+    free_mesh(m);
+    delete m;
+    return GKS_OK;
+}
+
+gks_status gks_mesh_get_stats(const gks_mesh *m, gks_mesh_stats *s)
+{
+    if (!m || !s) {
+        set_error("gks_mesh_get_stats: NULL argument");
+        return GKS_EINVAL;
+    }
+    s->n_tri = m->n_tri;
+    s->n_face = m->n_face;
+    s->n_boundary_face = m->n_bface;
+    s->n_k1 = m->n_k1;
+    s->nnzb = m->nnzb;
+    s->levels_lower = (int32_t)m->lvl_lo_ptr.size() - 1;
+    s->levels_upper = (int32_t)m->lvl_up_ptr.size() - 1;
+    s->rcm_bandwidth = m->bandwidth;
+    s->device_bytes = m->device_bytes;
+    return GKS_OK;
+}
+
+gks_status gks_cfl_dt(gks_mesh *m, const double *w, double *dt_out, void *stream)
+{
+    if (!m || !w || !dt_out) {
+        set_error("gks_cfl_dt: NULL argument");
+        return GKS_EINVAL;
+    }
+    DeviceGuard g(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    gks_status st;
+    if ((st = launch_permute(w, m->wk.w, m->d.perm, m->d.T, 4, true, s)) != GKS_OK) return st;
+    if ((st = launch_cfl_dt(m, m->wk.w, m->wk.dt, s)) != GKS_OK) return st;
+    GKS_CUDA(cudaMemcpyAsync(&m->wk.h_scal[6], m->wk.dt, sizeof(double), cudaMemcpyDeviceToHost, s));
+    GKS_CUDA(cudaStreamSynchronize(s));
+    *dt_out = m->wk.h_scal[6];
+    return GKS_OK;
+}
+
+gks_status gks_cls_reconstruct(gks_mesh *m, const double *w, double *coef, gks_solve_info *info, void *stream)
+{
+    if (!m || !w || !coef) {
+        set_error("gks_cls_reconstruct: NULL argument");
+        return GKS_EINVAL;
+    }
+    DeviceGuard g(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    gks_status st;
+    if ((st = launch_permute(w, m->wk.w, m->d.perm, m->d.T, 4, true, s)) != GKS_OK) return st;
+    gks_solve_info si;
+    if ((st = cls_solve(m, s, &si)) != GKS_OK) return st;
+    if ((st = launch_permute(m->wk.x, coef, m->d.perm, m->d.T, 20, false, s)) != GKS_OK) return st;
+    if (info) *info = si;
+    if (!si.converged) {
+        set_error("GMRES did not reach gmres_rtol within gmres_maxit");
+        return GKS_ENOCONV;
+    }
+    return GKS_OK;
+}
+
+gks_status gks_reset_warm_start(gks_mesh *m)
+{
+    if (!m) {
+        set_error("gks_reset_warm_start: NULL mesh");
+        return GKS_EINVAL;
+    }
+    DeviceGuard g(m->device);
+    GKS_CUDA(cudaMemset(m->wk.x, 0, sizeof(double) * 20 * m->d.T));
+    return GKS_OK;
+}
+
+gks_status gks_flux(gks_mesh *m, const double *w, const double *coef, double dt, double *face_flux, void *stream)
+{
+    if (!m || !w || !coef || !face_flux || !(dt > 0.0)) {
+        set_error("gks_flux: NULL argument or dt <= 0");
+        return GKS_EINVAL;
+    }
+    DeviceGuard g(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    gks_status st;
+    Work &k = m->wk;
+    GKS_CUDA(cudaMemsetAsync(k.status, 0, sizeof(int32_t), s));
+    if ((st = launch_permute(w, k.w, m->d.perm, m->d.T, 4, true, s)) != GKS_OK) return st;
+    if ((st = launch_permute(coef, k.r, m->d.perm, m->d.T, 20, true, s)) != GKS_OK) return st;
+    if ((st = launch_flux(m, k.w, k.r, dt, nullptr, k.flux, s)) != GKS_OK) return st;
+    if ((st = launch_permute(k.flux, face_flux, m->d.fperm, m->d.F, 4, false, s)) != GKS_OK) return st;
+    int32_t stat = 0;
+    if ((st = read_status(m, s, &stat)) != GKS_OK) return st;
+    if (stat & kStatusNonPhys) {
+        set_error("non-physical state at a Gauss point");
+        return GKS_ENONPHYS;
+    }
+    return GKS_OK;
+}
+
+gks_status gks_step(gks_mesh *m, double *w, double *dt_inout, gks_step_info *info, void *stream)
+{
+    if (!m || !w) {
+        set_error("gks_step: NULL argument");
+        return GKS_EINVAL;
+    }
+    DeviceGuard g(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    gks_status st;
+    GKS_CUDA(cudaMemsetAsync(m->wk.status, 0, sizeof(int32_t), s));
+    if ((st = launch_permute(w, m->wk.w, m->d.perm, m->d.T, 4, true, s)) != GKS_OK) return st;
+    double dt = 0.0;
+    gks_status res = step_internal(m, dt_inout ? *dt_inout : 0.0, s, info, &dt);
+    if (res != GKS_OK && res != GKS_ENOCONV && res != GKS_ENONPHYS) return res;
+    if ((st = launch_permute(m->wk.w, w, m->d.perm, m->d.T, 4, false, s)) != GKS_OK) return st;
+    GKS_CUDA(cudaStreamSynchronize(s));
+    if (dt_inout) *dt_inout = dt;
+    return res;
+}
+
+gks_status gks_run(gks_mesh *m, double *w, double t_final, int64_t max_steps, double steady_tol, gks_run_info *info,
+                   void *stream)
+{
+    if (!m || !w || max_steps < 0) {
+        set_error("gks_run: NULL argument or max_steps < 0");
+        return GKS_EINVAL;
+    }
+    DeviceGuard g(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    gks_status st, res = GKS_OK;
+    Work &k = m->wk;
+    GKS_CUDA(cudaMemsetAsync(k.status, 0, sizeof(int32_t), s));
+    if ((st = launch_permute(w, k.w, m->d.perm, m->d.T, 4, true, s)) != GKS_OK) return st;
+    double t = 0.0, last_dt = 0.0, res0 = -1.0, sres = 0.0;
+    int64_t steps = 0, iters = 0;
+    while (steps < max_steps) {
+        double dt_fixed = 0.0;
+        if (t_final > 0.0) {
+            if (t >= t_final * (1.0 - 1e-14)) break;
+            if ((st = launch_cfl_dt(m, k.w, k.dt, s)) != GKS_OK) return st;
+            GKS_CUDA(cudaMemcpyAsync(&k.h_scal[6], k.dt, sizeof(double), cudaMemcpyDeviceToHost, s));
+            GKS_CUDA(cudaStreamSynchronize(s));
+            dt_fixed = std::fmin(k.h_scal[6], t_final - t);
+        }
+        if (steady_tol > 0.0)
+            GKS_CUDA(cudaMemcpyAsync(k.w_old, k.w, sizeof(double) * 4 * m->d.T, cudaMemcpyDeviceToDevice, s));
+        gks_step_info si;
+        double dt = 0.0;
+        res = step_internal(m, dt_fixed, s, &si, &dt);
+        if (res != GKS_OK) break;
+        ++steps;
+        t += dt;
+        last_dt = dt;
+        for (int v = 0; v < 4; ++v) iters += si.iters[v];
+        if (steady_tol > 0.0) {
+            if ((st = launch_steady_partial(m, s)) != GKS_OK) return st;
+            GKS_CUDA(cudaMemcpyAsync(k.h_scal, k.scal, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+            GKS_CUDA(cudaStreamSynchronize(s));
+            double r = 0.0;
+            for (int v = 0; v < 4; ++v) r = std::fmax(r, std::sqrt(k.h_scal[v]) / dt);
+            if (res0 < 0.0) res0 = r > 0.0 ? r : 1.0;
+            sres = r / res0;
+            if (sres < steady_tol) break;
+        }
+    }
+    if ((st = launch_permute(k.w, w, m->d.perm, m->d.T, 4, false, s)) != GKS_OK) return st;
+    GKS_CUDA(cudaStreamSynchronize(s));
+    if (info) {
+        info->steps = steps;
+        info->t = t;
+        info->last_dt = last_dt;
+        info->gmres_iters = iters;
+        info->steady_res = sres;
+        info->status = res;
+    }
+    return res;
+}
+
+gks_status gks_point_flux(int64_t n, const double *wl, const double *wr, double dt, const gks_config *cfg, double *out,
+                          void *stream)
+{
+    if (n < 0 || (n > 0 && (!wl || !wr || !out)) || !(dt > 0.0)) {
+        set_error("gks_point_flux: bad argument");
+        return GKS_EINVAL;
+    }
+    gks_config c;
+    if (cfg) c = *cfg;
+    else gks_config_default(&c);
+    return launch_point_flux(n, wl, wr, dt, c, out, nullptr, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,599 @@
+// CLS reconstruction on the device (Sec. III): right-hand side, operator
+// application, block ILU(0) preconditioner and restarted GMRES.
+//
+// Four independent systems (rho, rho u, rho v, E) share one operator; every
+// kernel handles one cell and all four variables, so each block of the
+// operator is read once per application.  Vectors are SoA [var][dof][cell] in
+// RCM order.  GMRES (Saad & Schultz 1986) is right-preconditioned, uses
+// classical Gram-Schmidt applied twice (CGS2), and keeps per-variable state on
+// the device (running/converged masks); reductions go through per-block
+// partial sums and a fixed-order second pass, so results are deterministic.
+#include <algorithm>
+#include <cmath>
+
+#include "gks_internal.h"
+
+namespace gks {
+namespace {
+
+constexpr int NV = 4, ND = 5, NX = 20;
+
+// ctl layout: [0..3] active, [4..7] running, [8..11] vectors in cycle, [12..15] iterations
+__device__ __forceinline__ int &ctl_active(int32_t *c, int v) { return c[v]; }
+__device__ __forceinline__ int &ctl_running(int32_t *c, int v) { return c[4 + v]; }
+__device__ __forceinline__ int &ctl_jv(int32_t *c, int v) { return c[8 + v]; }
+__device__ __forceinline__ int &ctl_iters(int32_t *c, int v) { return c[12 + v]; }
+
+// y = O x_j for the gradient entries (g1, g2) of neighbour j
+__device__ __forceinline__ void oapply(double a, double ex, double ey, double g1, double g2, double *o)
+{
+    o[0] = a * g1;
+    o[1] = a * g2;
+    o[2] = a * ex * g1;
+    o[3] = a * (ey * g1 + ex * g2);
+    o[4] = a * ey * g2;
+}
+
+// Block reduction of NV values; thread 0 of the block gets the totals.
+__device__ __forceinline__ void block_sum4(double *v, double *sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sh[warp * NV + q] = v[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        for (int q = 0; q < NV; ++q) {
+            double s = 0.0;
+            for (int k = 0; k < nw; ++k) s += sh[k * NV + q];
+            v[q] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// r_i = sum_j a0_ij (ubar_j - ubar_i), Eq. (25) with b_ij = (ubar_j - ubar_i, 0, 0)
+__global__ void k_rhs(DeviceMesh d, const double *__restrict__ w, double *__restrict__ b)
+{
+    const int64_t T = d.T;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= T) return;
+    double acc[NX];
+#pragma unroll
+    for (int q = 0; q < NX; ++q) acc[q] = 0.0;
+    double wi[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) wi[v] = w[v * T + i];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        const int j = d.nb[s * T + i];
+        if (j < 0) continue;
+        double a[ND];
+#pragma unroll
+        for (int l = 0; l < ND; ++l) a[l] = d.a0[(s * ND + l) * T + i];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const double du = w[v * T + j] - wi[v];
+#pragma unroll
+            for (int l = 0; l < ND; ++l) acc[v * ND + l] += a[l] * du;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NX; ++q) b[q * T + i] = acc[q];
+}
+
+// y = K x (mode 0) or y = b - K x with partial sums of |y|^2 and |b|^2 (mode 1).
+// K_ii = D_i (symmetric, 15 stored values), K_ij = -O_ij.
+__global__ void k_spmv(DeviceMesh d, const double *__restrict__ x, double *__restrict__ y, int mode,
+                       const double *__restrict__ b, double *__restrict__ part, int pstride)
+{
+    __shared__ double sh[32 * NV];
+    const int64_t T = d.T;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double nr[NV] = {0, 0, 0, 0}, nb[NV] = {0, 0, 0, 0};
+    if (i < T) {
+        double Dm[15];
+#pragma unroll
+        for (int q = 0; q < 15; ++q) Dm[q] = d.D[q * T + i];
+        double acc[NX];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            double xv[ND];
+#pragma unroll
+            for (int l = 0; l < ND; ++l) xv[l] = x[(v * ND + l) * T + i];
+            // symmetric 5x5 times vector
+            acc[v * ND + 0] = Dm[0] * xv[0] + Dm[1] * xv[1] + Dm[2] * xv[2] + Dm[3] * xv[3] + Dm[4] * xv[4];
+            acc[v * ND + 1] = Dm[1] * xv[0] + Dm[5] * xv[1] + Dm[6] * xv[2] + Dm[7] * xv[3] + Dm[8] * xv[4];
+            acc[v * ND + 2] = Dm[2] * xv[0] + Dm[6] * xv[1] + Dm[9] * xv[2] + Dm[10] * xv[3] + Dm[11] * xv[4];
+            acc[v * ND + 3] = Dm[3] * xv[0] + Dm[7] * xv[1] + Dm[10] * xv[2] + Dm[12] * xv[3] + Dm[13] * xv[4];
+            acc[v * ND + 4] = Dm[4] * xv[0] + Dm[8] * xv[1] + Dm[11] * xv[2] + Dm[13] * xv[3] + Dm[14] * xv[4];
+        }
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            const int j = d.nb[s * T + i];
+            if (j < 0) continue;
+            const double a = d.alpha[s * T + i], ex = d.ex[s * T + i], ey = d.ey[s * T + i];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                double o[ND];
+                oapply(a, ex, ey, x[(v * ND + 0) * T + j], x[(v * ND + 1) * T + j], o);
+#pragma unroll
+                for (int l = 0; l < ND; ++l) acc[v * ND + l] -= o[l];
+            }
+        }
+        if (mode == 0) {
+#pragma unroll
+            for (int q = 0; q < NX; ++q) y[q * T + i] = acc[q];
+        } else {
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int l = 0; l < ND; ++l) {
+                    const double bv = b[(v * ND + l) * T + i];
+                    const double rv = bv - acc[v * ND + l];
+                    y[(v * ND + l) * T + i] = rv;
+                    nr[v] += rv * rv;
+                    nb[v] += bv * bv;
+                }
+        }
+    }
+    if (mode == 1) {
+        block_sum4(nr, sh);
+        block_sum4(nb, sh);
+        if (threadIdx.x == 0)
+            for (int v = 0; v < NV; ++v) {
+                part[(blockIdx.x * NV + v) * pstride + 0] = nr[v];
+                part[(blockIdx.x * NV + v) * pstride + 1] = nb[v];
+            }
+    }
+}
+
+// Forward block-ILU relation for the listed rows (or all rows when rows == nullptr):
+//   z_i = P_i (r_i + sum_{k<i} O_ik zin_k)      (use_nb = 0: z_i = P_i r_i)
+__global__ void k_ilu_fwd(DeviceMesh d, const int32_t *__restrict__ rows, int64_t nrows, const double *r,
+                          const double *zin, double *zout, int use_nb)
+{
+    const int64_t T = d.T;
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= nrows) return;
+    const int64_t i = rows ? rows[q] : q;
+    double y[NX];
+#pragma unroll
+    for (int k = 0; k < NX; ++k) y[k] = r[k * T + i];
+    if (use_nb) {
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            const int j = d.nb[s * T + i];
+            if (j < 0 || j >= i) continue;
+            const double a = d.alpha[s * T + i], ex = d.ex[s * T + i], ey = d.ey[s * T + i];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                double o[ND];
+                oapply(a, ex, ey, zin[(v * ND + 0) * T + j], zin[(v * ND + 1) * T + j], o);
+#pragma unroll
+                for (int l = 0; l < ND; ++l) y[v * ND + l] += o[l];
+            }
+        }
+    }
+    double Pm[25];
+#pragma unroll
+    for (int k = 0; k < 25; ++k) Pm[k] = d.P[k * T + i];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int a = 0; a < ND; ++a) {
+            double s = 0.0;
+#pragma unroll
+            for (int c = 0; c < ND; ++c) s += Pm[a * ND + c] * y[v * ND + c];
+            zout[(v * ND + a) * T + i] = s;
+        }
+}
+
+// Backward block-ILU relation: x_i = z_i + P_i sum_{j>i} O_ij xin_j
+__global__ void k_ilu_bwd(DeviceMesh d, const int32_t *__restrict__ rows, int64_t nrows, const double *z,
+                          const double *xin, double *xout)
+{
+    const int64_t T = d.T;
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= nrows) return;
+    const int64_t i = rows ? rows[q] : q;
+    double y[NX];
+#pragma unroll
+    for (int k = 0; k < NX; ++k) y[k] = 0.0;
+    bool any = false;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        const int j = d.nb[s * T + i];
+        if (j <= i) continue;
+        any = true;
+        const double a = d.alpha[s * T + i], ex = d.ex[s * T + i], ey = d.ey[s * T + i];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            double o[ND];
+            oapply(a, ex, ey, xin[(v * ND + 0) * T + j], xin[(v * ND + 1) * T + j], o);
+#pragma unroll
+            for (int l = 0; l < ND; ++l) y[v * ND + l] += o[l];
+        }
+    }
+    if (!any) {
+        if (xout != z)
+#pragma unroll
+            for (int k = 0; k < NX; ++k) xout[k * T + i] = z[k * T + i];
+        return;
+    }
+    double Pm[25];
+#pragma unroll
+    for (int k = 0; k < 25; ++k) Pm[k] = d.P[k * T + i];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int a = 0; a < ND; ++a) {
+            double s = z[(v * ND + a) * T + i];
+#pragma unroll
+            for (int c = 0; c < ND; ++c) s += Pm[a * ND + c] * y[v * ND + c];
+            xout[(v * ND + a) * T + i] = s;
+        }
+}
+
+// Partial dot products <V_k, w> for k = 0..j, per variable.
+__global__ void k_dots(int64_t T, const double *__restrict__ V, const double *__restrict__ w, int j,
+                       double *__restrict__ part, int pstride)
+{
+    __shared__ double sh[32 * NV];
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t vs = (int64_t)NX * T;
+    double wv[NX];
+#pragma unroll
+    for (int q = 0; q < NX; ++q) wv[q] = i < T ? w[q * T + i] : 0.0;
+    for (int k = 0; k <= j; ++k) {
+        double s[NV] = {0, 0, 0, 0};
+        if (i < T) {
+            const double *vk = V + k * vs;
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int l = 0; l < ND; ++l) s[v] += vk[(v * ND + l) * T + i] * wv[v * ND + l];
+        }
+        block_sum4(s, sh);
+        if (threadIdx.x == 0)
+            for (int v = 0; v < NV; ++v) part[(blockIdx.x * NV + v) * pstride + k] = s[v];
+    }
+}
+
+// w -= sum_{k<=j} h[v][k] V_k for running variables; optional partial |w|^2.
+__global__ void k_orth_update(int64_t T, const double *__restrict__ V, double *__restrict__ w, int j,
+                              const double *__restrict__ hc, int hstride, const int32_t *__restrict__ ctl,
+                              double *__restrict__ part, int pstride, int want_norm)
+{
+    __shared__ double sh[32 * NV];
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t vs = (int64_t)NX * T;
+    double nrm[NV] = {0, 0, 0, 0};
+    if (i < T) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            if (!ctl[4 + v]) continue;
+            double wv[ND];
+#pragma unroll
+            for (int l = 0; l < ND; ++l) wv[l] = w[(v * ND + l) * T + i];
+            for (int k = 0; k <= j; ++k) {
+                const double hk = hc[v * hstride + k];
+                const double *vk = V + k * vs;
+#pragma unroll
+                for (int l = 0; l < ND; ++l) wv[l] -= hk * vk[(v * ND + l) * T + i];
+            }
+#pragma unroll
+            for (int l = 0; l < ND; ++l) {
+                w[(v * ND + l) * T + i] = wv[l];
+                nrm[v] += wv[l] * wv[l];
+            }
+        }
+    }
+    if (want_norm) {
+        block_sum4(nrm, sh);
+        if (threadIdx.x == 0)
+            for (int v = 0; v < NV; ++v) part[(blockIdx.x * NV + v) * pstride + 0] = nrm[v];
+    }
+}
+
+// out[v][q] (op) sum over blocks of part[blk][v][q], q < nq, fixed order.
+// op 0: store, 1: add, 2: store sqrt.  Grid (nq, 4).
+__global__ void k_reduce(const double *__restrict__ part, int nblk, int pstride, double *out, int ostride, int op)
+{
+    __shared__ double sh[kBlock];
+    const int q = blockIdx.x, v = blockIdx.y;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[(b * NV + v) * pstride + q];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double r = sh[0];
+        if (op == 0) out[v * ostride + q] = r;
+        else if (op == 1) out[v * ostride + q] += r;
+        else out[v * ostride + q] = sqrt(r);
+    }
+}
+
+// h[v][q] += h2[v][q], q <= j (second Gram-Schmidt pass)
+__global__ void k_hadd(double *hc, int hstride, const double *__restrict__ h2, int h2stride, int j)
+{
+    for (int t = threadIdx.x; t < NV * (j + 1); t += blockDim.x) {
+        const int v = t / (j + 1), q = t % (j + 1);
+        hc[v * hstride + q] += h2[v * h2stride + q];
+    }
+}
+
+// V_{j+1} = w / |w| for running variables (w stored in the V_{j+1} slot).
+__global__ void k_scale(int64_t T, double *__restrict__ vj1, const double *__restrict__ hc, int hstride, int j,
+                        const int32_t *__restrict__ ctl)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= T) return;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const double h = hc[v * hstride + j + 1];
+        if (!ctl[4 + v] || !(h > 0.0)) continue;
+        const double inv = 1.0 / h;
+#pragma unroll
+        for (int l = 0; l < ND; ++l) vj1[(v * ND + l) * T + i] *= inv;
+    }
+}
+
+// Givens step of column j for each running variable (one thread per variable).
+__global__ void k_givens(int j, int m, const double *__restrict__ hc, int hstride, double *H, double *cs,
+                         double *sn, double *g, int32_t *ctl, const double *__restrict__ bnorm, double rtol, int maxit)
+{
+    const int v = threadIdx.x;
+    if (v >= NV || !ctl[4 + v]) return;
+    double h[kMaxRestart + 1];
+    for (int k = 0; k <= j + 1; ++k) h[k] = hc[v * hstride + k];
+    const double hnext = h[j + 1];
+    for (int k = 0; k < j; ++k) {
+        const double c = cs[v * m + k], s = sn[v * m + k];
+        const double t0 = h[k], t1 = h[k + 1];
+        h[k] = c * t0 + s * t1;
+        h[k + 1] = -s * t0 + c * t1;
+    }
+    const double dd = hypot(h[j], h[j + 1]);
+    const double c = dd > 0.0 ? h[j] / dd : 1.0, s = dd > 0.0 ? h[j + 1] / dd : 0.0;
+    cs[v * m + j] = c;
+    sn[v * m + j] = s;
+    h[j] = dd;
+    for (int k = 0; k <= j; ++k) H[(v * (m + 1) + k) * m + j] = h[k];
+    const double gj = g[v * (m + 1) + j];
+    g[v * (m + 1) + j + 1] = -s * gj;
+    g[v * (m + 1) + j] = c * gj;
+    ctl[8 + v] = j + 1;
+    ctl[12 + v] += 1;
+    if (fabs(g[v * (m + 1) + j + 1]) <= rtol * bnorm[v] || !(hnext > 0.0) || ctl[12 + v] >= maxit || j + 1 == m)
+        ctl[4 + v] = 0;
+}
+
+// y = H^{-1} g on the first jv columns (upper triangular after the rotations).
+__global__ void k_backsolve(int m, const double *__restrict__ H, const double *__restrict__ g, double *y,
+                            const int32_t *__restrict__ ctl)
+{
+    const int v = threadIdx.x;
+    if (v >= NV) return;
+    const int jv = ctl[8 + v];
+    for (int k = jv - 1; k >= 0; --k) {
+        double s = g[v * (m + 1) + k];
+        for (int q = k + 1; q < jv; ++q) s -= H[(v * (m + 1) + k) * m + q] * y[v * m + q];
+        y[v * m + k] = s / H[(v * (m + 1) + k) * m + k];
+    }
+}
+
+// u = sum_{k<jv} y_k V_k per variable (zero where jv = 0)
+__global__ void k_combine(int64_t T, const double *__restrict__ V, const double *__restrict__ y, int m,
+                          const int32_t *__restrict__ ctl, double *__restrict__ u)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= T) return;
+    const int64_t vs = (int64_t)NX * T;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const int jv = ctl[8 + v];
+        double acc[ND] = {0, 0, 0, 0, 0};
+        for (int k = 0; k < jv; ++k) {
+            const double yk = y[v * m + k];
+#pragma unroll
+            for (int l = 0; l < ND; ++l) acc[l] += yk * V[k * vs + (v * ND + l) * T + i];
+        }
+#pragma unroll
+        for (int l = 0; l < ND; ++l) u[(v * ND + l) * T + i] = acc[l];
+    }
+}
+
+// x += t for variables that took a cycle (jv > 0)
+__global__ void k_addx(int64_t T, double *__restrict__ x, const double *__restrict__ t, const int32_t *__restrict__ ctl)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= T) return;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        if (ctl[8 + v] <= 0) continue;
+#pragma unroll
+        for (int l = 0; l < ND; ++l) x[(v * ND + l) * T + i] += t[(v * ND + l) * T + i];
+    }
+}
+
+// Start of the solve: sums[v][0] = |r|^2, sums[v][1] = |b|^2 (already reduced).
+__global__ void k_start(const double *__restrict__ sums, int sstride, double *bnorm, double *beta, int32_t *ctl,
+                        double rtol, int maxit, int first)
+{
+    const int v = threadIdx.x;
+    if (v >= NV) return;
+    const double bn = sqrt(sums[v * sstride + 1]), be = sqrt(sums[v * sstride + 0]);
+    if (first) {
+        bnorm[v] = bn;
+        ctl[12 + v] = 0;
+        ctl[v] = 1;
+    }
+    beta[v] = be;
+    const int act = ctl[v] && bn > 0.0 && be > rtol * bn && ctl[12 + v] < maxit;
+    ctl[v] = act;
+    ctl[4 + v] = act;
+    ctl[8 + v] = 0;
+}
+
+// V_0 = r / beta for active variables, zero otherwise; g = beta e_1.
+__global__ void k_init_v0(int64_t T, const double *__restrict__ r, double *__restrict__ v0,
+                          const double *__restrict__ beta, const int32_t *__restrict__ ctl, double *g, int m)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < NV * (m + 1)) g[i] = (i % (m + 1) == 0 && ctl[i / (m + 1)]) ? beta[i / (m + 1)] : 0.0;
+    if (i >= T) return;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const double s = ctl[v] ? 1.0 / beta[v] : 0.0;
+#pragma unroll
+        for (int l = 0; l < ND; ++l) v0[(v * ND + l) * T + i] = ctl[v] ? r[(v * ND + l) * T + i] * s : 0.0;
+    }
+}
+
+// x[v] = 0 for variables with b = 0 (free stream: zero coefficients exactly)
+__global__ void k_zero_trivial(int64_t T, double *__restrict__ x, const double *__restrict__ bnorm)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= T) return;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        if (bnorm[v] > 0.0) continue;
+#pragma unroll
+        for (int l = 0; l < ND; ++l) x[(v * ND + l) * T + i] = 0.0;
+    }
+}
+
+inline unsigned nblocks(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+// dst = M^{-1} src (block ILU(0) on the RCM order)
+gks_status precond(gks_mesh *m, const double *src, double *dst, cudaStream_t s)
+{
+    DeviceMesh &d = m->d;
+    Work &k = m->wk;
+    const int64_t T = d.T;
+    if (m->cfg.precond == GKS_PC_ILU_EXACT) {
+        const auto &lp = m->lvl_lo_ptr;
+        for (size_t l = 0; l + 1 < lp.size(); ++l) {
+            const int64_t n = lp[l + 1] - lp[l];
+            k_ilu_fwd<<<nblocks(n), kBlock, 0, s>>>(d, d.lvl_lo + lp[l], n, src, dst, dst, 1);
+        }
+        const auto &up = m->lvl_up_ptr;
+        for (size_t l = 0; l + 1 < up.size(); ++l) {
+            const int64_t n = up[l + 1] - up[l];
+            k_ilu_bwd<<<nblocks(n), kBlock, 0, s>>>(d, d.lvl_up + up[l], n, dst, dst, dst);
+        }
+    } else {
+        // sweeps: forward z^0 = P r, z^{q+1} = F(z^q); backward x^0 = z, x^{q+1} = B(x^q)
+        const int ns = m->cfg.ilu_sweeps;
+        double *za = (ns % 2 == 0) ? k.t2 : dst;   // buffers chosen so z ends in t2
+        double *zb = (ns % 2 == 0) ? dst : k.t2;
+        k_ilu_fwd<<<nblocks(T), kBlock, 0, s>>>(d, nullptr, T, src, nullptr, za, 0);
+        for (int q = 0; q < ns; ++q) {
+            k_ilu_fwd<<<nblocks(T), kBlock, 0, s>>>(d, nullptr, T, src, za, zb, 1);
+            std::swap(za, zb);
+        }
+        // now za == t2 holds z
+        if (ns == 0) {
+            GKS_CUDA(cudaMemcpyAsync(dst, za, sizeof(double) * NX * T, cudaMemcpyDeviceToDevice, s));
+        } else {
+            double *xa = za;                                    // x^0 = z
+            double *xb = (ns % 2 == 1) ? dst : k.t3;
+            for (int q = 0; q < ns; ++q) {
+                k_ilu_bwd<<<nblocks(T), kBlock, 0, s>>>(d, nullptr, T, za, xa, xb);
+                xa = xb;
+                xb = (xb == dst) ? k.t3 : dst;
+            }
+        }
+    }
+    GKS_CUDA(cudaGetLastError());
+    return GKS_OK;
+}
+
+gks_status read_ctl(gks_mesh *m, cudaStream_t s)
+{
+    GKS_CUDA(cudaMemcpyAsync(m->wk.h_ctl, m->wk.ctl, sizeof(int32_t) * 16, cudaMemcpyDeviceToHost, s));
+    GKS_CUDA(cudaStreamSynchronize(s));
+    return GKS_OK;
+}
+
+}  // namespace
+
+// Solve the CLS system for the right-hand side built from m->wk.w; the solution
+// (and warm start) is m->wk.x.
+gks_status cls_solve(gks_mesh *m, cudaStream_t s, gks_solve_info *info)
+{
+    DeviceMesh &d = m->d;
+    Work &k = m->wk;
+    const int64_t T = d.T;
+    const int mm = k.m;
+    const int ps = mm + 2;
+    const unsigned nb = nblocks(T);
+    const double rtol = m->cfg.gmres_rtol;
+    const int maxit = m->cfg.gmres_maxit;
+    const int64_t vs = (int64_t)NX * T;
+    gks_status st;
+
+    k_rhs<<<nb, kBlock, 0, s>>>(d, k.w, k.b);
+    k_spmv<<<nb, kBlock, 0, s>>>(d, k.x, k.r, 1, k.b, k.part, ps);
+    k_reduce<<<dim3(2, NV), kBlock, 0, s>>>(k.part, k.nblk, ps, k.hcol, ps, 0);
+    k_start<<<1, 32, 0, s>>>(k.hcol, ps, k.bnorm, k.beta, k.ctl, rtol, maxit, 1);
+    k_zero_trivial<<<nb, kBlock, 0, s>>>(T, k.x, k.bnorm);
+    GKS_CUDA(cudaGetLastError());
+    if ((st = read_ctl(m, s)) != GKS_OK) return st;
+
+    while (k.h_ctl[0] | k.h_ctl[1] | k.h_ctl[2] | k.h_ctl[3]) {
+        k_init_v0<<<std::max(nb, nblocks(NV * (mm + 1))), kBlock, 0, s>>>(T, k.r, k.V, k.beta, k.ctl, k.g, mm);
+        for (int j = 0; j < mm; ++j) {
+            double *vj = k.V + j * vs, *vj1 = k.V + (j + 1) * vs;
+            if ((st = precond(m, vj, k.t, s)) != GKS_OK) return st;
+            k_spmv<<<nb, kBlock, 0, s>>>(d, k.t, vj1, 0, nullptr, nullptr, 0);
+            // classical Gram-Schmidt, twice
+            k_dots<<<nb, kBlock, 0, s>>>(T, k.V, vj1, j, k.part, ps);
+            k_reduce<<<dim3(j + 1, NV), kBlock, 0, s>>>(k.part, k.nblk, ps, k.hcol, ps, 0);
+            k_orth_update<<<nb, kBlock, 0, s>>>(T, k.V, vj1, j, k.hcol, ps, k.ctl, k.part, ps, 0);
+            k_dots<<<nb, kBlock, 0, s>>>(T, k.V, vj1, j, k.part, ps);
+            k_reduce<<<dim3(j + 1, NV), kBlock, 0, s>>>(k.part, k.nblk, ps, k.y, mm, 0);   // second-pass coefficients
+            k_orth_update<<<nb, kBlock, 0, s>>>(T, k.V, vj1, j, k.y, mm, k.ctl, k.part, ps, 1);
+            k_reduce<<<dim3(1, NV), kBlock, 0, s>>>(k.part, k.nblk, ps, k.hcol + j + 1, ps, 2);
+            k_hadd<<<1, 128, 0, s>>>(k.hcol, ps, k.y, mm, j);
+            k_scale<<<nb, kBlock, 0, s>>>(T, vj1, k.hcol, ps, j, k.ctl);
+            k_givens<<<1, 32, 0, s>>>(j, mm, k.hcol, ps, k.H, k.cs, k.sn, k.g, k.ctl, k.bnorm, rtol, maxit);
+            GKS_CUDA(cudaGetLastError());
+            if ((st = read_ctl(m, s)) != GKS_OK) return st;
+            if (!(k.h_ctl[4] | k.h_ctl[5] | k.h_ctl[6] | k.h_ctl[7])) break;
+        }
+        k_backsolve<<<1, 32, 0, s>>>(mm, k.H, k.g, k.y, k.ctl);
+        k_combine<<<nb, kBlock, 0, s>>>(T, k.V, k.y, mm, k.ctl, k.r);
+        if ((st = precond(m, k.r, k.t, s)) != GKS_OK) return st;
+        k_addx<<<nb, kBlock, 0, s>>>(T, k.x, k.t, k.ctl);
+        k_spmv<<<nb, kBlock, 0, s>>>(d, k.x, k.r, 1, k.b, k.part, ps);
+        k_reduce<<<dim3(2, NV), kBlock, 0, s>>>(k.part, k.nblk, ps, k.hcol, ps, 0);
+        k_start<<<1, 32, 0, s>>>(k.hcol, ps, k.bnorm, k.beta, k.ctl, rtol, maxit, 0);
+        GKS_CUDA(cudaGetLastError());
+        if ((st = read_ctl(m, s)) != GKS_OK) return st;
+        if (!(k.h_ctl[0] | k.h_ctl[1] | k.h_ctl[2] | k.h_ctl[3])) break;
+    }
+    if (info) {
+        GKS_CUDA(cudaMemcpyAsync(k.h_scal, k.beta, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+        GKS_CUDA(cudaMemcpyAsync(k.h_scal + 4, k.bnorm, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+        GKS_CUDA(cudaStreamSynchronize(s));
+        info->converged = 1;
+        for (int v = 0; v < NV; ++v) {
+            info->iters[v] = k.h_ctl[12 + v];
+            info->relres[v] = k.h_scal[4 + v] > 0.0 ? k.h_scal[v] / k.h_scal[4 + v] : 0.0;
+            if (info->relres[v] > rtol) info->converged = 0;
+        }
+    }
+    return GKS_OK;
+}
+
+}  // namespace gks

@@ -1,0 +1,341 @@
+// Face fluxes, conservative update, CFL time step and permutations.
+//
+// Flux (Eqs. (7), (11), (15)): one thread per face Gauss point; the two points
+// of a face sit in neighbouring lanes and are summed with one shuffle, so each
+// face flux is written once, without atomics.  The update (Eq. (6)) gathers
+// the (at most three) face fluxes of each cell: no atomics, a fixed summation
+// order, one write per cell.
+#include <cfloat>
+
+#include "gks_internal.h"
+#include "gks_kinetic.cuh"
+
+namespace gks {
+namespace {
+
+constexpr int kFluxBlock = 128;
+
+// Value and derivatives (global frame) of cell c's reconstruction (Eq. (19))
+// at the point whose scaled offsets from the centroid are (dx, dy).
+// o[6][4]: W, W_x, W_y, W_xx, W_xy, W_yy.
+__device__ __forceinline__ void recon(const DeviceMesh &d, const double *__restrict__ w,
+                                      const double *__restrict__ x, int c, double dx, double dy, double *o)
+{
+    const int64_t T = d.T;
+    const double ih = 1.0 / d.h[c];
+    const double qx = dx * dx - d.mxx[c], qxy = dx * dy - d.mxy[c], qy = dy * dy - d.myy[c];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const double u1 = x[(v * 5 + 0) * T + c], u2 = x[(v * 5 + 1) * T + c], u3 = x[(v * 5 + 2) * T + c];
+        const double u4 = x[(v * 5 + 3) * T + c], u5 = x[(v * 5 + 4) * T + c];
+        o[v] = w[v * T + c] + u1 * dx + u2 * dy + 0.5 * u3 * qx + u4 * qxy + 0.5 * u5 * qy;
+        o[4 + v] = (u1 + u3 * dx + u4 * dy) * ih;
+        o[8 + v] = (u2 + u4 * dx + u5 * dy) * ih;
+        o[12 + v] = u3 * ih * ih;
+        o[16 + v] = u4 * ih * ih;
+        o[20 + v] = u5 * ih * ih;
+    }
+}
+
+// Global rows -> face frame (n = (nx, ny), t = (-ny, nx)): directions of the
+// derivatives and the momentum components of every row.
+__device__ __forceinline__ void to_face(const double *g, double nx, double ny, double *f)
+{
+    const double tx = -ny, ty = nx;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const double gx = g[4 + v], gy = g[8 + v], gxx = g[12 + v], gxy = g[16 + v], gyy = g[20 + v];
+        f[v] = g[v];
+        f[4 + v] = nx * gx + ny * gy;
+        f[8 + v] = tx * gx + ty * gy;
+        f[12 + v] = nx * nx * gxx + 2.0 * nx * ny * gxy + ny * ny * gyy;
+        f[16 + v] = nx * tx * gxx + (nx * ty + ny * tx) * gxy + ny * ty * gyy;
+        f[20 + v] = tx * tx * gxx + 2.0 * tx * ty * gxy + ty * ty * gyy;
+    }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+        const double mx = f[4 * r + 1], my = f[4 * r + 2];
+        f[4 * r + 1] = nx * mx + ny * my;
+        f[4 * r + 2] = tx * mx + ty * my;
+    }
+}
+
+// Ghost right state of a boundary face (face frame).
+__device__ __forceinline__ void ghost(int tag, const double *bc, double nx, double ny, double gamma,
+                                      const double *wl, double *wr)
+{
+    if (tag == GKS_BC_DIRICHLET) {
+#pragma unroll
+        for (int q = 0; q < 24; ++q) wr[q] = 0.0;
+        wr[0] = bc[0];
+        wr[1] = nx * bc[1] + ny * bc[2];
+        wr[2] = -ny * bc[1] + nx * bc[2];
+        wr[3] = bc[3];
+        return;
+    }
+    if (tag == GKS_BC_OUTFLOW) {
+#pragma unroll
+        for (int q = 0; q < 24; ++q) wr[q] = wl[q];
+        return;
+    }
+    // mirror image: q_R(n, t) = s_q q_L(-n, t); a derivative of order p in n gets (-1)^p
+    const bool noslip = tag == GKS_BC_NOSLIP;
+    const int npar[6] = {0, 1, 0, 0, 1, 0};   // parity of the n-order of each row
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            double s = (v == 1 || (noslip && v == 2)) ? -1.0 : 1.0;
+            if (npar[r]) s = -s;
+            wr[4 * r + v] = s * wl[4 * r + v];
+        }
+    if (noslip) {
+        const double rho = wl[0], un = wl[1] / rho, ut = wl[2] / rho;
+        const double p = (gamma - 1.0) * (wl[3] - 0.5 * rho * (un * un + ut * ut));
+        const double uwn = nx * bc[0] + ny * bc[1], uwt = -ny * bc[0] + nx * bc[1];
+        const double tg = 2.0 * bc[2] - p / rho;
+        const double gn = 2.0 * uwn - un, gt = 2.0 * uwt - ut;
+        wr[0] = rho;
+        wr[1] = rho * gn;
+        wr[2] = rho * gt;
+        wr[3] = rho * tg / (gamma - 1.0) + 0.5 * rho * (gn * gn + gt * gt);
+    }
+}
+
+__global__ void __launch_bounds__(kFluxBlock) k_face_flux(DeviceMesh d, const double *__restrict__ w,
+                                                          const double *__restrict__ x, double dt_const,
+                                                          const double *__restrict__ dt_dev, double gamma, double mu,
+                                                          int tau2, double *__restrict__ flux, int32_t *status)
+{
+    const int64_t F = d.F;
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t f = g >> 1;
+    const int k = (int)(g & 1);
+    const bool valid = f < F;
+    double out[4] = {0.0, 0.0, 0.0, 0.0};
+    if (valid) {
+        const double dt = dt_dev ? *dt_dev : dt_const;
+        const double nx = d.fnx[f], ny = d.fny[f];
+        const int l = d.fl[f], r = d.fr[f];
+        double gl[24], wl[24], wr[24];
+        recon(d, w, x, l, d.gl[(2 * k) * F + f], d.gl[(2 * k + 1) * F + f], gl);
+        to_face(gl, nx, ny, wl);
+        if (r >= 0) {
+            recon(d, w, x, r, d.gr[(2 * k) * F + f], d.gr[(2 * k + 1) * F + f], gl);
+            to_face(gl, nx, ny, wr);
+        } else {
+            const double bc[4] = {d.bc[f], d.bc[F + f], d.bc[2 * F + f], d.bc[3 * F + f]};
+            ghost(d.ftag[f], bc, nx, ny, gamma, wl, wr);
+        }
+        double fk[4];
+        if (!kin::gp_flux<double>(wl, wr, dt, gamma, mu, tau2, fk)) atomicOr(status, kStatusNonPhys);
+        const double s = 0.5 * d.flen[f];      // Gauss weight 1/2 times the face length
+        out[0] = s * fk[0];
+        out[1] = s * (nx * fk[1] - ny * fk[2]);
+        out[2] = s * (ny * fk[1] + nx * fk[2]);
+        out[3] = s * fk[3];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[q] += __shfl_xor_sync(0xffffffffu, out[q], 1);
+    if (valid && k == 0)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) flux[q * F + f] = out[q];
+}
+
+// w_i -= (1/|Omega_i|) sum_f sigma_if F_f; flags non-physical results.
+__global__ void k_update(DeviceMesh d, double *__restrict__ w, const double *__restrict__ flux, double gamma,
+                         int32_t *status)
+{
+    const int64_t T = d.T, F = d.F;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= T) return;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        const int cf = d.cf[s * T + i];
+        if (cf < 0) continue;
+        const int64_t f = cf >> 1;
+        const double sg = (cf & 1) ? 1.0 : -1.0;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[v] += sg * flux[v * F + f];
+    }
+    const double ia = d.inv_area[i];
+    double wn[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        wn[v] = w[v * T + i] + acc[v] * ia;
+        w[v * T + i] = wn[v];
+    }
+    const double p = (gamma - 1.0) * (wn[3] - 0.5 * (wn[1] * wn[1] + wn[2] * wn[2]) / wn[0]);
+    if (!(wn[0] > 0.0) || !(p > 0.0)) atomicOr(status, kStatusNonPhys);
+}
+
+// Per-cell CFL bound, block minimum.
+__global__ void k_cfl_partial(DeviceMesh d, const double *__restrict__ w, double gamma, double mu,
+                              double *__restrict__ part)
+{
+    __shared__ double sh[kBlock];
+    const int64_t T = d.T;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double dti = DBL_MAX;
+    if (i < T) {
+        const double rho = w[i], u = w[T + i] / rho, v = w[2 * T + i] / rho;
+        const double p = (gamma - 1.0) * (w[3 * T + i] - 0.5 * rho * (u * u + v * v));
+        const double c = sqrt(gamma * p / rho);
+        const double r = d.inrad[i];
+        dti = r / (sqrt(u * u + v * v) + c + 2.0 * mu / (rho * r));
+        if (!(dti > 0.0)) dti = 0.0;          // non-physical cell: forces dt = 0
+    }
+    sh[threadIdx.x] = dti;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_min_final(const double *__restrict__ part, int n, double scale, double *out)
+{
+    __shared__ double sh[kBlock];
+    double m = DBL_MAX;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) m = fmin(m, part[b]);
+    sh[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = scale * sh[0];
+}
+
+__global__ void __launch_bounds__(kFluxBlock) k_point_flux(int64_t n, const double *__restrict__ wl,
+                                                           const double *__restrict__ wr, double dt, double gamma,
+                                                           double mu, int tau2, double *__restrict__ out,
+                                                           int32_t *status)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    double a[24], b[24], f[4];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) {
+        a[k] = wl[24 * q + k];
+        b[k] = wr[24 * q + k];
+    }
+    if (!kin::gp_flux<double>(a, b, dt, gamma, mu, tau2, f) && status) atomicOr(status, kStatusNonPhys);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[4 * q + k] = f[k];
+}
+
+__global__ void k_permute(const double *__restrict__ src, double *__restrict__ dst, const int32_t *__restrict__ perm,
+                          int64_t n, int nvar, int gather)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t p = perm[i];
+    for (int v = 0; v < nvar; ++v) {
+        if (gather) dst[v * n + i] = src[v * n + p];
+        else dst[v * n + p] = src[v * n + i];
+    }
+}
+
+// partial sums over cells of area * (w - w_old)^2 per variable
+__global__ void k_steady_partial(DeviceMesh d, const double *__restrict__ w, const double *__restrict__ w_old,
+                                 double *__restrict__ part)
+{
+    __shared__ double sh[kBlock];
+    const int64_t T = d.T;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (int v = 0; v < 4; ++v) {
+        double s = 0.0;
+        if (i < T) {
+            const double dw = w[v * T + i] - w_old[v * T + i];
+            s = d.area[i] * dw * dw;
+        }
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[blockIdx.x * 4 + v] = sh[0];
+        __syncthreads();
+    }
+}
+
+__global__ void k_sum4_final(const double *__restrict__ part, int n, double *out)
+{
+    __shared__ double sh[kBlock];
+    for (int v = 0; v < 4; ++v) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < n; b += blockDim.x) s += part[b * 4 + v];
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[v] = sh[0];
+        __syncthreads();
+    }
+}
+
+inline unsigned blocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+gks_status launch_flux(gks_mesh *m, const double *w, const double *x, double dt_const, const double *dt_dev,
+                       double *flux, cudaStream_t s)
+{
+    const int64_t npts = 2 * m->d.F;
+    k_face_flux<<<blocks(npts, kFluxBlock), kFluxBlock, 0, s>>>(m->d, w, x, dt_const, dt_dev, m->cfg.gamma, m->cfg.mu,
+                                                                m->cfg.tau2_exact, flux, m->wk.status);
+    GKS_CUDA(cudaGetLastError());
+    return GKS_OK;
+}
+
+gks_status launch_update(gks_mesh *m, double *w, const double *flux, cudaStream_t s)
+{
+    k_update<<<blocks(m->d.T, kBlock), kBlock, 0, s>>>(m->d, w, flux, m->cfg.gamma, m->wk.status);
+    GKS_CUDA(cudaGetLastError());
+    return GKS_OK;
+}
+
+gks_status launch_cfl_dt(gks_mesh *m, const double *w, double *dt_dev, cudaStream_t s)
+{
+    const unsigned nb = blocks(m->d.T, kBlock);
+    k_cfl_partial<<<nb, kBlock, 0, s>>>(m->d, w, m->cfg.gamma, m->cfg.mu, m->wk.dpart);
+    k_min_final<<<1, kBlock, 0, s>>>(m->wk.dpart, (int)nb, m->cfg.cfl, dt_dev);
+    GKS_CUDA(cudaGetLastError());
+    return GKS_OK;
+}
+
+gks_status launch_point_flux(int64_t n, const double *wl, const double *wr, double dt, const gks_config &cfg,
+                             double *out, int32_t *status, cudaStream_t s)
+{
+    if (n <= 0) return GKS_OK;
+    k_point_flux<<<blocks(n, kFluxBlock), kFluxBlock, 0, s>>>(n, wl, wr, dt, cfg.gamma, cfg.mu, cfg.tau2_exact, out,
+                                                              status);
+    GKS_CUDA(cudaGetLastError());
+    return GKS_OK;
+}
+
+gks_status launch_permute(const double *src, double *dst, const int32_t *perm, int64_t n, int nvar, bool gather,
+                          cudaStream_t s)
+{
+    k_permute<<<blocks(n, kBlock), kBlock, 0, s>>>(src, dst, perm, n, nvar, gather ? 1 : 0);
+    GKS_CUDA(cudaGetLastError());
+    return GKS_OK;
+}
+
+// m->wk.scal[0..3] = sum over cells of area (w - w_old)^2 per variable
+gks_status launch_steady_partial(gks_mesh *m, cudaStream_t s)
+{
+    const unsigned nb = blocks(m->d.T, kBlock);
+    k_steady_partial<<<nb, kBlock, 0, s>>>(m->d, m->wk.w, m->wk.w_old, m->wk.dpart);
+    k_sum4_final<<<1, kBlock, 0, s>>>(m->wk.dpart, (int)nb, m->wk.scal);
+    GKS_CUDA(cudaGetLastError());
+    return GKS_OK;
+}
+
+}  // namespace gks

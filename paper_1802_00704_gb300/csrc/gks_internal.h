@@ -1,0 +1,118 @@
+// Internal declarations of the GB300 gas-kinetic library (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/gks.h"
+
+namespace gks {
+
+constexpr int kBlock = 256;          // threads per block of the cell/face kernels
+constexpr int kMaxRestart = 64;      // upper bound on gmres_m
+
+void set_error(const char *fmt, ...);
+
+#define GKS_CUDA(call)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            ::gks::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),       \
+                             __FILE__, __LINE__);                                         \
+            return GKS_ECUDA;                                                             \
+        }                                                                                 \
+    } while (0)
+
+// Device status bits (a word the kernels OR into).
+enum : int { kStatusNonPhys = 1 };
+
+// Device data of one mesh, all in RCM ("internal") cell order.
+struct DeviceMesh {
+    int64_t T = 0, F = 0;
+    // cells
+    double *area = nullptr, *inv_area = nullptr, *h = nullptr, *mxx = nullptr, *mxy = nullptr, *myy = nullptr;
+    double *inrad = nullptr;
+    int32_t *nb = nullptr;           // [3][T] neighbour (internal index) or -1
+    double *alpha = nullptr;         // [3][T] w^2 h_i / h_j
+    double *ex = nullptr, *ey = nullptr;  // [3][T] centroid offsets of j in i's frame (0 when k_i = 1)
+    double *a0 = nullptr;            // [3][5][T] weighted row 0 of A_ij (right-hand side)
+    double *D = nullptr;             // [15][T] symmetric diagonal block, upper triangle row-major
+    double *P = nullptr;             // [25][T] inverse of the ILU(0) diagonal block, row-major
+    int32_t *cf = nullptr;           // [3][T] (face << 1) | side, -1 unused
+    int32_t *perm = nullptr;         // [T] internal -> caller cell
+    int32_t *lvl_lo = nullptr;       // [T] rows sorted by forward level
+    int32_t *lvl_up = nullptr;       // [T] rows sorted by backward level
+    // faces (internal order)
+    int32_t *fl = nullptr, *fr = nullptr, *ftag = nullptr;
+    int32_t *fperm = nullptr;        // [F] internal -> caller face
+    double *fnx = nullptr, *fny = nullptr, *flen = nullptr;
+    double *gl = nullptr;            // [4][F] Gauss points in l's scaled frame: dx0 dy0 dx1 dy1
+    double *gr = nullptr;            // [4][F] Gauss points in r's scaled frame
+    double *bc = nullptr;            // [4][F]
+};
+
+struct Work {
+    int m = 0;                       // restart length
+    int nblk = 0;                    // blocks of the cell kernels
+    double *w = nullptr;             // [4][T] state (internal order)
+    double *w_old = nullptr;         // [4][T]
+    double *x = nullptr;             // [20][T] CLS coefficients (warm start)
+    double *b = nullptr, *r = nullptr, *t = nullptr, *t2 = nullptr, *t3 = nullptr;  // [20][T]
+    double *V = nullptr;             // [(m+1)][20][T]
+    double *flux = nullptr;          // [4][F]
+    double *part = nullptr;          // [nblk][4][m+2] partial sums
+    double *dpart = nullptr;         // [nblk] partial minima / sums
+    // small GMRES state (device)
+    double *H = nullptr;             // [4][m+1][m]  (Givens-rotated Hessenberg)
+    double *cs = nullptr, *sn = nullptr;  // [4][m]
+    double *g = nullptr;             // [4][m+1]
+    double *y = nullptr;             // [4][m]
+    double *hcol = nullptr;          // [4][m+2]
+    double *bnorm = nullptr, *beta = nullptr;  // [4]
+    int32_t *ctl = nullptr;          // [4][4]: active, running, jv, iters
+    double *dt = nullptr;            // [1]
+    double *scal = nullptr;          // [8] misc device scalars
+    int32_t *status = nullptr;       // [1]
+    // pinned host mirror
+    int32_t *h_ctl = nullptr;        // [16 + 4]
+    double *h_scal = nullptr;        // [8]
+};
+
+}  // namespace gks
+
+struct gks_mesh {
+    gks_config cfg{};
+    int device = 0;
+    int64_t n_tri = 0, n_face = 0, n_bface = 0, n_k1 = 0, nnzb = 0, bandwidth = 0;
+    std::vector<int32_t> lvl_lo_ptr, lvl_up_ptr;   // level offsets (host)
+    gks::DeviceMesh d;
+    gks::Work wk;
+    int64_t device_bytes = 0;
+    std::vector<void *> allocations;
+};
+
+namespace gks {
+
+// set-up (gks_setup.cu)
+gks_status build_mesh(gks_mesh *m, const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t n_tri,
+                      const int32_t *faces, const double *face_shift, int64_t n_face, const double *bc_state);
+void free_mesh(gks_mesh *m);
+
+// CLS reconstruction (gks_cls.cu): rhs from m->wk.w, solution in m->wk.x
+gks_status cls_solve(gks_mesh *m, cudaStream_t s, gks_solve_info *info);
+
+// flux and update (gks_flux.cu)
+gks_status launch_flux(gks_mesh *m, const double *w, const double *x, double dt_const, const double *dt_dev,
+                       double *flux, cudaStream_t s);
+gks_status launch_update(gks_mesh *m, double *w, const double *flux, cudaStream_t s);
+gks_status launch_cfl_dt(gks_mesh *m, const double *w, double *dt_dev, cudaStream_t s);
+gks_status launch_point_flux(int64_t n, const double *wl, const double *wr, double dt, const gks_config &cfg,
+                             double *out, int32_t *status, cudaStream_t s);
+gks_status launch_permute(const double *src, double *dst, const int32_t *perm, int64_t n, int nvar, bool gather,
+                          cudaStream_t s);
+gks_status launch_steady_partial(gks_mesh *m, cudaStream_t s);
+
+}  // namespace gks

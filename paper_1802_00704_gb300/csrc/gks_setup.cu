@@ -1,0 +1,518 @@
+// Host set-up of a mesh handle: geometry, boundary order reduction, RCM order,
+// CLS blocks, block ILU(0) factors, level sets, and the upload to HBM.
+//
+// Geometry-only data (Sec. III.A): the CLS operator depends on the mesh only,
+// so it is assembled once here.  For a cell i and a face neighbour j (Eq. (29),
+// M = 1 derivative order, weights w_{i,0} = 1 and w_{i,1} = w h_i) the rows of
+// A_ij are
+//   row 0: mean over cell j of phi_{l,i}                       (= a0 below)
+//   row 1: w (1, 0, dx, dy, 0)      row 2: w (0, 1, 0, dx, dy)
+// with (dx, dy) the centroid of j in i's scaled frame, and B_ij has only
+// w (h_i/h_j) on the gradient entries of rows 1 and 2 (zero-mean basis).  The
+// per-cell least-squares normal equations (Eqs. (32)-(33)) give
+//   D_i u_i - sum_j O_ij u_j = sum_j A_ij^T b_ij,   D_i = sum_j A_ij^T A_ij,
+//   O_ij = A_ij^T B_ij = w^2 (h_i/h_j) [e1 + dx e3 + dy e4 | e2 + dx e4 + dy e5],
+// so an off-diagonal block is stored as three numbers (alpha, dx, dy).
+// Means of quadratics over a triangle use its centroidal second moments
+// (1/12) sum_k (p_k - c)(p_k - c)^T.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+
+#include "gks_internal.h"
+
+namespace gks {
+
+static thread_local char g_err[512];
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+const char *last_error() { return g_err; }
+
+namespace {
+
+struct HostCell {
+    double area, cx, cy, crad, inrad, h, sxx, sxy, syy;   // s**: centroidal second moments (unscaled)
+    int k;
+    int nf;
+    int face[3];
+};
+
+template <typename T>
+gks_status dalloc(gks_mesh *m, T **p, size_t n)
+{
+    void *q = nullptr;
+    size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? GKS_ENOMEM : GKS_ECUDA;
+    }
+    m->allocations.push_back(q);
+    m->device_bytes += (int64_t)bytes;
+    *p = static_cast<T *>(q);
+    return GKS_OK;
+}
+
+template <typename T>
+gks_status upload(gks_mesh *m, T **p, const std::vector<T> &h)
+{
+    gks_status st = dalloc(m, p, h.size());
+    if (st != GKS_OK) return st;
+    GKS_CUDA(cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return GKS_OK;
+}
+
+// 5x5 inverse by Gauss-Jordan with partial pivoting (row-major).  Returns false if singular.
+bool inv5(const double *a, double *out)
+{
+    double m[5][10];
+    for (int r = 0; r < 5; ++r)
+        for (int c = 0; c < 10; ++c) m[r][c] = c < 5 ? a[5 * r + c] : (c - 5 == r ? 1.0 : 0.0);
+    for (int c = 0; c < 5; ++c) {
+        int p = c;
+        for (int r = c + 1; r < 5; ++r)
+            if (std::fabs(m[r][c]) > std::fabs(m[p][c])) p = r;
+        if (m[p][c] == 0.0) return false;
+        if (p != c)
+            for (int q = 0; q < 10; ++q) std::swap(m[p][q], m[c][q]);
+        double d = 1.0 / m[c][c];
+        for (int q = 0; q < 10; ++q) m[c][q] *= d;
+        for (int r = 0; r < 5; ++r) {
+            if (r == c || m[r][c] == 0.0) continue;
+            double f = m[r][c];
+            for (int q = 0; q < 10; ++q) m[r][q] -= f * m[c][q];
+        }
+    }
+    for (int r = 0; r < 5; ++r)
+        for (int c = 0; c < 5; ++c) out[5 * r + c] = m[r][5 + c];
+    return true;
+}
+
+// Off-diagonal block O (5x5, row-major) from its three parameters.
+void oblock(double alpha, double ex, double ey, double *O)
+{
+    std::fill(O, O + 25, 0.0);
+    O[0 * 5 + 0] = alpha;
+    O[1 * 5 + 1] = alpha;
+    O[2 * 5 + 0] = alpha * ex;
+    O[3 * 5 + 0] = alpha * ey;
+    O[3 * 5 + 1] = alpha * ex;
+    O[4 * 5 + 1] = alpha * ey;
+}
+
+// Reverse Cuthill-McKee order (new -> old) of the cell graph given by adjacency lists.
+// Start vertex of each component: a pseudo-peripheral vertex found by repeated
+// breadth-first searches (George & Liu); neighbours are queued by increasing degree.
+std::vector<int32_t> rcm_order(const std::vector<std::array<int32_t, 3>> &adj, const std::vector<int> &deg)
+{
+    const int64_t T = (int64_t)adj.size();
+    std::vector<int32_t> order;
+    order.reserve(T);
+    std::vector<char> done(T, 0);
+    std::vector<int32_t> level(T, -1), queue(T);
+    auto bfs = [&](int32_t s, int32_t &far) {
+        // returns eccentricity; far = min-degree vertex of the last level
+        int64_t head = 0, tail = 0;
+        queue[tail++] = s;
+        level[s] = 0;
+        int ecc = 0;
+        while (head < tail) {
+            int32_t c = queue[head++];
+            for (int q = 0; q < deg[c]; ++q) {
+                int32_t j = adj[c][q];
+                if (level[j] < 0) {
+                    level[j] = level[c] + 1;
+                    ecc = std::max(ecc, level[j]);
+                    queue[tail++] = j;
+                }
+            }
+        }
+        far = -1;
+        for (int64_t q = 0; q < tail; ++q) {
+            int32_t c = queue[q];
+            if (level[c] == ecc && (far < 0 || deg[c] < deg[far] || (deg[c] == deg[far] && c < far))) far = c;
+        }
+        for (int64_t q = 0; q < tail; ++q) level[queue[q]] = -1;
+        return ecc;
+    };
+    for (int64_t seed = 0; seed < T; ++seed) {
+        if (done[seed]) continue;
+        // first unvisited vertex, then walk to a pseudo-peripheral one
+        int32_t s = (int32_t)seed;
+        int32_t far;
+        int ecc = bfs(s, far);
+        for (int it = 0; it < 32; ++it) {
+            int32_t far2;
+            int ecc2 = bfs(far, far2);
+            if (ecc2 <= ecc) break;
+            s = far;
+            ecc = ecc2;
+            far = far2;
+        }
+        int64_t head = (int64_t)order.size();
+        order.push_back(s);
+        done[s] = 1;
+        while (head < (int64_t)order.size()) {
+            int32_t c = order[head++];
+            int32_t cand[3];
+            int nc = 0;
+            for (int q = 0; q < deg[c]; ++q) {
+                int32_t j = adj[c][q];
+                if (!done[j]) {
+                    done[j] = 1;
+                    cand[nc++] = j;
+                }
+            }
+            std::sort(cand, cand + nc, [&](int32_t a, int32_t b) { return deg[a] != deg[b] ? deg[a] < deg[b] : a < b; });
+            for (int q = 0; q < nc; ++q) order.push_back(cand[q]);
+        }
+    }
+    std::reverse(order.begin(), order.end());
+    return order;
+}
+
+}  // namespace
+
+gks_status build_mesh(gks_mesh *m, const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t n_tri,
+                      const int32_t *faces, const double *face_shift, int64_t n_face, const double *bc_state)
+{
+    const int64_t T = n_tri, F = n_face;
+    if (!nodes || !tris || !faces || !face_shift || !bc_state || n_nodes <= 0 || T <= 0 || F <= 0 ||
+        T > (int64_t)INT32_MAX / 4 || F > (int64_t)INT32_MAX / 4) {
+        set_error("gks_mesh_create: null array or size out of range");
+        return GKS_EINVAL;
+    }
+    const gks_config &cfg = m->cfg;
+    const double w = cfg.cls_w;
+
+    // ---- cells: orientation, area, centroid, radii, length scale (Eq. (17))
+    std::vector<HostCell> cell(T);
+    for (int64_t i = 0; i < T; ++i) {
+        const int32_t *t = tris + 3 * i;
+        for (int q = 0; q < 3; ++q)
+            if (t[q] < 0 || t[q] >= n_nodes) {
+                set_error("gks_mesh_create: triangle %lld has node index %d out of range", (long long)i, t[q]);
+                return GKS_EINVAL;
+            }
+        double px[3], py[3];
+        for (int q = 0; q < 3; ++q) { px[q] = nodes[2 * t[q]]; py[q] = nodes[2 * t[q] + 1]; }
+        double a2 = (px[1] - px[0]) * (py[2] - py[0]) - (px[2] - px[0]) * (py[1] - py[0]);
+        if (!(std::fabs(a2) > 0.0) || !std::isfinite(a2)) {
+            set_error("gks_mesh_create: triangle %lld is degenerate", (long long)i);
+            return GKS_EINVAL;
+        }
+        HostCell &c = cell[i];
+        c.area = 0.5 * std::fabs(a2);
+        c.cx = (px[0] + px[1] + px[2]) / 3.0;
+        c.cy = (py[0] + py[1] + py[2]) / 3.0;
+        double e0 = std::hypot(px[1] - px[0], py[1] - py[0]);
+        double e1 = std::hypot(px[2] - px[1], py[2] - py[1]);
+        double e2 = std::hypot(px[0] - px[2], py[0] - py[2]);
+        c.crad = e0 * e1 * e2 / (4.0 * c.area);
+        c.inrad = 2.0 * c.area / (e0 + e1 + e2);
+        c.h = std::max(c.crad, std::sqrt(c.area));
+        c.sxx = c.sxy = c.syy = 0.0;
+        for (int q = 0; q < 3; ++q) {
+            double dx = px[q] - c.cx, dy = py[q] - c.cy;
+            c.sxx += dx * dx / 12.0;
+            c.sxy += dx * dy / 12.0;
+            c.syy += dy * dy / 12.0;
+        }
+        c.k = 2;
+        c.nf = 0;
+        c.face[0] = c.face[1] = c.face[2] = -1;
+    }
+
+    // ---- faces: validation, incidence, boundary order reduction (Eq. (28))
+    int64_t nbf = 0;
+    for (int64_t f = 0; f < F; ++f) {
+        const int32_t *fc = faces + 5 * f;
+        bool bad = fc[0] < 0 || fc[0] >= n_nodes || fc[1] < 0 || fc[1] >= n_nodes || fc[2] < 0 || fc[2] >= T ||
+                   fc[3] < -1 || fc[3] >= T || fc[4] < GKS_BC_INTERIOR || fc[4] > GKS_BC_NOSLIP || fc[2] == fc[3];
+        bad = bad || ((fc[3] < 0) != (fc[4] >= GKS_BC_DIRICHLET));
+        if (bad) {
+            set_error("gks_mesh_create: face %lld is invalid (indices or tag)", (long long)f);
+            return GKS_EINVAL;
+        }
+        for (int side = 0; side < 2; ++side) {
+            int32_t c = fc[2 + side];
+            if (c < 0) continue;
+            if (cell[c].nf == 3) {
+                set_error("gks_mesh_create: cell %d has more than three faces", c);
+                return GKS_EINVAL;
+            }
+            cell[c].face[cell[c].nf++] = (int32_t)(2 * f + side);
+        }
+        if (fc[3] < 0) {
+            cell[fc[2]].k = 1;
+            ++nbf;
+        }
+    }
+
+    // ---- cell graph and RCM order (Sec. III.B)
+    std::vector<std::array<int32_t, 3>> adj(T);
+    std::vector<int> deg(T, 0);
+    for (int64_t i = 0; i < T; ++i)
+        for (int q = 0; q < cell[i].nf; ++q) {
+            int64_t f = cell[i].face[q] >> 1;
+            int side = cell[i].face[q] & 1;
+            int32_t j = faces[5 * f + 3 - side];   // the other cell
+            if (j < 0) continue;
+            bool dup = false;
+            for (int p = 0; p < deg[i]; ++p) dup = dup || adj[i][p] == j;
+            if (!dup) adj[i][deg[i]++] = j;
+        }
+    std::vector<int32_t> perm = rcm_order(adj, deg);   // internal -> caller
+    std::vector<int32_t> inv(T);
+    for (int64_t i = 0; i < T; ++i) inv[perm[i]] = (int32_t)i;
+
+    // ---- CLS blocks in internal order
+    std::vector<int32_t> h_nb(3 * T, -1), h_cf(3 * T, -1);
+    std::vector<double> h_alpha(3 * T, 0.0), h_ex(3 * T, 0.0), h_ey(3 * T, 0.0), h_a0(15 * T, 0.0);
+    std::vector<double> h_D(15 * T, 0.0), h_Dfull(25 * T, 0.0);
+    std::vector<double> h_area(T), h_iarea(T), h_h(T), h_mxx(T), h_mxy(T), h_myy(T), h_inrad(T);
+    int64_t nk1 = 0, nnzb = 0, bw = 0;
+    for (int64_t i = 0; i < T; ++i) {
+        const HostCell &c = cell[perm[i]];
+        h_area[i] = c.area;
+        h_iarea[i] = 1.0 / c.area;
+        h_h[i] = c.h;
+        h_mxx[i] = c.sxx / (c.h * c.h);
+        h_mxy[i] = c.sxy / (c.h * c.h);
+        h_myy[i] = c.syy / (c.h * c.h);
+        h_inrad[i] = c.inrad;
+        nk1 += c.k == 1;
+    }
+    for (int64_t i = 0; i < T; ++i) {
+        const int32_t ci = perm[i];
+        const HostCell &c = cell[ci];
+        const int ni = c.k == 2 ? 5 : 2;
+        double D[25] = {0};
+        int slot = 0;
+        for (int q = 0; q < c.nf; ++q) {
+            int64_t f = c.face[q] >> 1;
+            int side = c.face[q] & 1;
+            int32_t cj = faces[5 * f + 3 - side];
+            if (cj < 0) continue;
+            // translation of j's coordinates next to i
+            double ox = side == 0 ? face_shift[2 * f] : -face_shift[2 * f];
+            double oy = side == 0 ? face_shift[2 * f + 1] : -face_shift[2 * f + 1];
+            const HostCell &d = cell[cj];
+            double dx = (d.cx + ox - c.cx) / c.h, dy = (d.cy + oy - c.cy) / c.h;
+            double s2 = 1.0 / (c.h * c.h);
+            double a0[5] = {dx, dy, 0.5 * (dx * dx + d.sxx * s2 - h_mxx[i]), dx * dy + d.sxy * s2 - h_mxy[i],
+                            0.5 * (dy * dy + d.syy * s2 - h_myy[i])};
+            double r1[5] = {w, 0.0, w * dx, w * dy, 0.0};
+            double r2[5] = {0.0, w, 0.0, w * dx, w * dy};
+            for (int a = 0; a < ni; ++a)
+                for (int b = 0; b < ni; ++b) D[5 * a + b] += a0[a] * a0[b] + r1[a] * r1[b] + r2[a] * r2[b];
+            int32_t j = inv[cj];
+            h_nb[slot * T + i] = j;
+            h_alpha[slot * T + i] = w * w * c.h / d.h;
+            h_ex[slot * T + i] = c.k == 2 ? dx : 0.0;
+            h_ey[slot * T + i] = c.k == 2 ? dy : 0.0;
+            for (int l = 0; l < 5; ++l) h_a0[(slot * 5 + l) * T + i] = l < ni ? a0[l] : 0.0;
+            bw = std::max<int64_t>(bw, std::llabs((long long)(j - i)));
+            ++slot;
+            ++nnzb;
+        }
+        for (int a = ni; a < 5; ++a) D[5 * a + a] = 1.0;    // padding of k = 1 cells
+        int u = 0;
+        for (int a = 0; a < 5; ++a)
+            for (int b = a; b < 5; ++b) h_D[(u++) * T + i] = D[5 * a + b];
+        std::copy(D, D + 25, &h_Dfull[25 * i]);
+        ++nnzb;
+    }
+
+    // ---- block ILU(0) in internal (RCM) order: only diagonal blocks change,
+    // Dt_i = D_i - sum_{k<i} O_ik Dt_k^{-1} O_ki, because no two face
+    // neighbours of a triangle are face neighbours of each other.
+    std::vector<double> h_P(25 * T, 0.0), Pinv(25 * T, 0.0);
+    for (int64_t i = 0; i < T; ++i) {
+        double Dt[25];
+        std::copy(&h_Dfull[25 * i], &h_Dfull[25 * i] + 25, Dt);
+        for (int s = 0; s < 3; ++s) {
+            int32_t k = h_nb[s * T + i];
+            if (k < 0 || k >= i) continue;
+            double Oik[25];
+            oblock(h_alpha[s * T + i], h_ex[s * T + i], h_ey[s * T + i], Oik);
+            for (int s2 = 0; s2 < 3; ++s2) {
+                if (h_nb[s2 * T + k] != (int32_t)i) continue;
+                double Oki[25], tmp[25];
+                oblock(h_alpha[s2 * T + k], h_ex[s2 * T + k], h_ey[s2 * T + k], Oki);
+                const double *Pk = &Pinv[25 * k];
+                for (int a = 0; a < 5; ++a)
+                    for (int b = 0; b < 5; ++b) {
+                        double sacc = 0.0;
+                        for (int q = 0; q < 5; ++q) sacc += Pk[5 * a + q] * Oki[5 * q + b];
+                        tmp[5 * a + b] = sacc;
+                    }
+                for (int a = 0; a < 5; ++a)
+                    for (int b = 0; b < 5; ++b) {
+                        double sacc = 0.0;
+                        for (int q = 0; q < 5; ++q) sacc += Oik[5 * a + q] * tmp[5 * q + b];
+                        Dt[5 * a + b] -= sacc;
+                    }
+            }
+        }
+        if (!inv5(Dt, &Pinv[25 * i])) {
+            set_error("gks_mesh_create: singular ILU(0) pivot block at cell %d", perm[i]);
+            return GKS_EINVAL;
+        }
+    }
+    for (int64_t i = 0; i < T; ++i)
+        for (int q = 0; q < 25; ++q) h_P[q * T + i] = Pinv[25 * i + q];
+
+    // ---- level sets of the two triangular solves
+    std::vector<int32_t> lev(T, 0);
+    int32_t nlo = 0, nup = 0;
+    for (int64_t i = 0; i < T; ++i) {
+        int32_t l = 0;
+        for (int s = 0; s < 3; ++s) {
+            int32_t k = h_nb[s * T + i];
+            if (k >= 0 && k < i) l = std::max(l, lev[k] + 1);
+        }
+        lev[i] = l;
+        nlo = std::max(nlo, l + 1);
+    }
+    auto bucket = [&](int32_t nlev, std::vector<int32_t> &rows, std::vector<int32_t> &ptr) {
+        ptr.assign(nlev + 1, 0);
+        for (int64_t i = 0; i < T; ++i) ++ptr[lev[i] + 1];
+        for (int32_t l = 0; l < nlev; ++l) ptr[l + 1] += ptr[l];
+        std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+        rows.assign(T, 0);
+        for (int64_t i = 0; i < T; ++i) rows[fill[lev[i]]++] = (int32_t)i;
+    };
+    std::vector<int32_t> rows_lo, rows_up;
+    bucket(nlo, rows_lo, m->lvl_lo_ptr);
+    for (int64_t i = T - 1; i >= 0; --i) {
+        int32_t l = 0;
+        for (int s = 0; s < 3; ++s) {
+            int32_t k = h_nb[s * T + i];
+            if (k > i) l = std::max(l, lev[k] + 1);
+        }
+        lev[i] = l;
+        nup = std::max(nup, l + 1);
+    }
+    // lev[] now holds the backward levels (rows with higher indices first)
+    bucket(nup, rows_up, m->lvl_up_ptr);
+
+    // ---- faces in internal order (sorted by the lower internal cell index)
+    std::vector<int64_t> forder(F);
+    std::iota(forder.begin(), forder.end(), 0);
+    auto fkey = [&](int64_t f) {
+        int32_t l = inv[faces[5 * f + 2]];
+        int32_t r = faces[5 * f + 3] >= 0 ? inv[faces[5 * f + 3]] : l;
+        return std::min(l, r);
+    };
+    std::stable_sort(forder.begin(), forder.end(), [&](int64_t a, int64_t b) { return fkey(a) < fkey(b); });
+    std::vector<int32_t> h_fl(F), h_fr(F), h_ftag(F), h_fperm(F);
+    std::vector<double> h_fnx(F), h_fny(F), h_flen(F), h_gl(4 * F), h_gr(4 * F, 0.0), h_bc(4 * F);
+    std::vector<int32_t> finv(F);
+    const double s0 = 0.5 - 0.5 / std::sqrt(3.0), s1 = 0.5 + 0.5 / std::sqrt(3.0);
+    for (int64_t q = 0; q < F; ++q) {
+        int64_t f = forder[q];
+        finv[f] = (int32_t)q;
+        const int32_t *fc = faces + 5 * f;
+        h_fperm[q] = (int32_t)f;
+        h_fl[q] = inv[fc[2]];
+        h_fr[q] = fc[3] >= 0 ? inv[fc[3]] : -1;
+        h_ftag[q] = fc[4];
+        double ax = nodes[2 * fc[0]], ay = nodes[2 * fc[0] + 1], bx = nodes[2 * fc[1]], by = nodes[2 * fc[1] + 1];
+        double len = std::hypot(bx - ax, by - ay);
+        if (!(len > 0.0)) {
+            set_error("gks_mesh_create: face %lld has zero length", (long long)f);
+            return GKS_EINVAL;
+        }
+        double nx = (by - ay) / len, ny = -(bx - ax) / len;
+        const HostCell &cl = cell[fc[2]];
+        if (nx * (0.5 * (ax + bx) - cl.cx) + ny * (0.5 * (ay + by) - cl.cy) < 0.0) {
+            nx = -nx;
+            ny = -ny;
+        }
+        h_fnx[q] = nx;
+        h_fny[q] = ny;
+        h_flen[q] = len;
+        double gx[2] = {ax + s0 * (bx - ax), ax + s1 * (bx - ax)};
+        double gy[2] = {ay + s0 * (by - ay), ay + s1 * (by - ay)};
+        for (int g = 0; g < 2; ++g) {
+            h_gl[(2 * g) * F + q] = (gx[g] - cl.cx) / cl.h;
+            h_gl[(2 * g + 1) * F + q] = (gy[g] - cl.cy) / cl.h;
+            if (fc[3] >= 0) {
+                const HostCell &cr = cell[fc[3]];
+                h_gr[(2 * g) * F + q] = (gx[g] - face_shift[2 * f] - cr.cx) / cr.h;
+                h_gr[(2 * g + 1) * F + q] = (gy[g] - face_shift[2 * f + 1] - cr.cy) / cr.h;
+            }
+        }
+        for (int v = 0; v < 4; ++v) h_bc[v * F + q] = bc_state[4 * f + v];
+    }
+    for (int64_t i = 0; i < T; ++i) {
+        const HostCell &c = cell[perm[i]];
+        for (int q = 0; q < c.nf; ++q) {
+            int64_t f = c.face[q] >> 1;
+            h_cf[q * T + i] = (finv[f] << 1) | (c.face[q] & 1);
+        }
+    }
+
+    // ---- upload
+    m->n_tri = T;
+    m->n_face = F;
+    m->n_bface = nbf;
+    m->n_k1 = nk1;
+    m->nnzb = nnzb;
+    m->bandwidth = bw;
+    DeviceMesh &d = m->d;
+    d.T = T;
+    d.F = F;
+    gks_status st;
+#define UP(ptr, vec) \
+    if ((st = upload(m, &d.ptr, vec)) != GKS_OK) return st
+    UP(area, h_area); UP(inv_area, h_iarea); UP(h, h_h); UP(mxx, h_mxx); UP(mxy, h_mxy); UP(myy, h_myy);
+    UP(inrad, h_inrad); UP(nb, h_nb); UP(alpha, h_alpha); UP(ex, h_ex); UP(ey, h_ey); UP(a0, h_a0);
+    UP(D, h_D); UP(P, h_P); UP(cf, h_cf); UP(perm, perm); UP(lvl_lo, rows_lo); UP(lvl_up, rows_up);
+    UP(fl, h_fl); UP(fr, h_fr); UP(ftag, h_ftag); UP(fperm, h_fperm); UP(fnx, h_fnx); UP(fny, h_fny);
+    UP(flen, h_flen); UP(gl, h_gl); UP(gr, h_gr); UP(bc, h_bc);
+#undef UP
+
+    // ---- work buffers
+    Work &k = m->wk;
+    k.m = cfg.gmres_m;
+    k.nblk = (int)((T + kBlock - 1) / kBlock);
+    const int mm = k.m;
+#define AL(ptr, n) \
+    if ((st = dalloc(m, &k.ptr, (size_t)(n))) != GKS_OK) return st
+    AL(w, 4 * T); AL(w_old, 4 * T); AL(x, 20 * T); AL(b, 20 * T); AL(r, 20 * T); AL(t, 20 * T); AL(t2, 20 * T); AL(t3, 20 * T);
+    AL(V, (size_t)(mm + 1) * 20 * T); AL(flux, 4 * F);
+    AL(part, (size_t)k.nblk * 4 * (mm + 2)); AL(dpart, (size_t)std::max<int64_t>(k.nblk, (F + kBlock - 1) / kBlock) * 4);
+    AL(H, 4 * (mm + 1) * mm); AL(cs, 4 * mm); AL(sn, 4 * mm); AL(g, 4 * (mm + 1)); AL(y, 4 * mm);
+    AL(hcol, 4 * (mm + 2)); AL(bnorm, 4); AL(beta, 4); AL(ctl, 16); AL(dt, 1); AL(scal, 8); AL(status, 1);
+#undef AL
+    GKS_CUDA(cudaMemset(k.x, 0, sizeof(double) * 20 * T));
+    GKS_CUDA(cudaMemset(k.status, 0, sizeof(int32_t)));
+    GKS_CUDA(cudaMallocHost(&k.h_ctl, sizeof(int32_t) * 20));
+    GKS_CUDA(cudaMallocHost(&k.h_scal, sizeof(double) * 8));
+    return GKS_OK;
+}
+
+void free_mesh(gks_mesh *m)
+{
+    for (void *p : m->allocations) cudaFree(p);
+    m->allocations.clear();
+    if (m->wk.h_ctl) cudaFreeHost(m->wk.h_ctl);
+    if (m->wk.h_scal) cudaFreeHost(m->wk.h_scal);
+    m->wk.h_ctl = nullptr;
+    m->wk.h_scal = nullptr;
+}
+
+}  // namespace gks

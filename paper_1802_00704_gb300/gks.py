@@ -1,0 +1,235 @@
+"""ctypes binding of libgks.so (C ABI in include/gks.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of the library.  Device arrays are torch tensors (float64, CUDA,
+contiguous); the current torch stream is passed to the library.  If the
+library has not been built, loading fails with an error: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgks.so")
+
+GKS_OK, GKS_EINVAL, GKS_ENOMEM, GKS_ECUDA, GKS_ENOCONV, GKS_ENONPHYS, GKS_ETIMEOUT, GKS_EUNSUPPORTED = range(8)
+STATUS_NAMES = ["GKS_OK", "GKS_EINVAL", "GKS_ENOMEM", "GKS_ECUDA", "GKS_ENOCONV", "GKS_ENONPHYS", "GKS_ETIMEOUT",
+                "GKS_EUNSUPPORTED"]
+PC_ILU_EXACT, PC_ILU_SWEEP, PC_BJACOBI = 0, 1, 2
+FP64, MIXED = 0, 1
+
+EXPORTED = ["gks_config_default", "gks_mesh_create", "gks_mesh_destroy", "gks_mesh_get_stats", "gks_cfl_dt",
+            "gks_cls_reconstruct", "gks_reset_warm_start", "gks_flux", "gks_step", "gks_run", "gks_point_flux",
+            "gks_last_error"]
+
+
+class GksError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+
+
+class Config(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("mu", C.c_double), ("cls_w", C.c_double),
+                ("gmres_m", C.c_int32), ("gmres_maxit", C.c_int32), ("gmres_rtol", C.c_double),
+                ("precision", C.c_int32), ("precond", C.c_int32), ("ilu_sweeps", C.c_int32),
+                ("tau2_exact", C.c_int32), ("reserved", C.c_int32 * 8)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int32 * 4), ("relres", C.c_double * 4), ("converged", C.c_int32)]
+
+
+class StepInfo(C.Structure):
+    _fields_ = [("dt", C.c_double), ("iters", C.c_int32 * 4), ("relres", C.c_double * 4), ("status", C.c_int32)]
+
+
+class RunInfo(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("t", C.c_double), ("last_dt", C.c_double), ("gmres_iters", C.c_int64),
+                ("steady_res", C.c_double), ("status", C.c_int32)]
+
+
+class MeshStats(C.Structure):
+    _fields_ = [("n_tri", C.c_int64), ("n_face", C.c_int64), ("n_boundary_face", C.c_int64), ("n_k1", C.c_int64),
+                ("nnzb", C.c_int64), ("levels_lower", C.c_int32), ("levels_upper", C.c_int32),
+                ("rcm_bandwidth", C.c_int64), ("device_bytes", C.c_int64)]
+
+
+_lib = None
+
+
+def load():
+    """Load libgks.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1802_00704_gb300.build.build() "
+                          "(there is no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    P, D, I64, I32 = C.c_void_p, C.c_double, C.c_int64, C.c_int32
+    st = C.c_int
+    lib.gks_config_default.argtypes = [C.POINTER(Config)]
+    lib.gks_config_default.restype = None
+    lib.gks_mesh_create.argtypes = [P, I64, P, I64, P, P, I64, P, C.POINTER(Config), C.POINTER(P)]
+    lib.gks_mesh_create.restype = st
+    lib.gks_mesh_destroy.argtypes = [P]
+    lib.gks_mesh_destroy.restype = st
+    lib.gks_mesh_get_stats.argtypes = [P, C.POINTER(MeshStats)]
+    lib.gks_mesh_get_stats.restype = st
+    lib.gks_cfl_dt.argtypes = [P, P, C.POINTER(D), P]
+    lib.gks_cfl_dt.restype = st
+    lib.gks_cls_reconstruct.argtypes = [P, P, P, C.POINTER(SolveInfo), P]
+    lib.gks_cls_reconstruct.restype = st
+    lib.gks_reset_warm_start.argtypes = [P]
+    lib.gks_reset_warm_start.restype = st
+    lib.gks_flux.argtypes = [P, P, P, D, P, P]
+    lib.gks_flux.restype = st
+    lib.gks_step.argtypes = [P, P, C.POINTER(D), C.POINTER(StepInfo), P]
+    lib.gks_step.restype = st
+    lib.gks_run.argtypes = [P, P, D, I64, D, C.POINTER(RunInfo), P]
+    lib.gks_run.restype = st
+    lib.gks_point_flux.argtypes = [I64, P, P, D, C.POINTER(Config), P, P]
+    lib.gks_point_flux.restype = st
+    lib.gks_last_error.argtypes = []
+    lib.gks_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().gks_last_error().decode()
+
+
+def _check(status: int, where: str, ok=(GKS_OK,)):
+    if status not in ok:
+        raise GksError(status, where, last_error())
+    return status
+
+
+def config(**kw) -> Config:
+    c = Config()
+    load().gks_config_default(C.byref(c))
+    for k, v in kw.items():
+        if not hasattr(c, k):
+            raise AttributeError(f"gks_config has no field {k}")
+        setattr(c, k, v)
+    return c
+
+
+def _dev(t, shape=None):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {shape}, got {tuple(t.shape)}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class GksMesh:
+    """A mesh handle: geometry, CLS operator, ILU(0) factors and work buffers in HBM."""
+
+    def __init__(self, mesh, **cfg):
+        self._lib = load()
+        self.cfg = config(**cfg)
+        nodes = np.ascontiguousarray(mesh.nodes, dtype=np.float64)
+        tris = np.ascontiguousarray(mesh.tris, dtype=np.int32)
+        faces = np.ascontiguousarray(mesh.faces, dtype=np.int32)
+        shift = np.ascontiguousarray(mesh.face_shift, dtype=np.float64)
+        bc = np.ascontiguousarray(mesh.bc_state, dtype=np.float64)
+        self.T, self.F = int(tris.shape[0]), int(faces.shape[0])
+        h = C.c_void_p()
+        p = lambda a: a.ctypes.data_as(C.c_void_p)
+        _check(self._lib.gks_mesh_create(p(nodes), nodes.shape[0], p(tris), self.T, p(faces), p(shift), self.F,
+                                         p(bc), C.byref(self.cfg), C.byref(h)), "gks_mesh_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gks_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stats(self) -> dict:
+        s = MeshStats()
+        _check(self._lib.gks_mesh_get_stats(self._h, C.byref(s)), "gks_mesh_get_stats")
+        return {k: getattr(s, k) for k, _ in MeshStats._fields_}
+
+    def cfl_dt(self, w, stream=None) -> float:
+        dt = C.c_double(0.0)
+        _check(self._lib.gks_cfl_dt(self._h, _dev(w, (4, self.T)), C.byref(dt), _stream(stream)), "gks_cfl_dt")
+        return dt.value
+
+    def cls_reconstruct(self, w, coef=None, stream=None, check=True):
+        import torch
+        if coef is None:
+            coef = torch.empty((4, 5, self.T), dtype=torch.float64, device=w.device)
+        info = SolveInfo()
+        st = self._lib.gks_cls_reconstruct(self._h, _dev(w, (4, self.T)), _dev(coef, (4, 5, self.T)),
+                                           C.byref(info), _stream(stream))
+        if check:
+            _check(st, "gks_cls_reconstruct")
+        return coef, {"iters": list(info.iters), "relres": list(info.relres), "converged": info.converged,
+                      "status": st}
+
+    def reset_warm_start(self):
+        _check(self._lib.gks_reset_warm_start(self._h), "gks_reset_warm_start")
+
+    def flux(self, w, coef, dt: float, out=None, stream=None, check=True):
+        import torch
+        if out is None:
+            out = torch.empty((4, self.F), dtype=torch.float64, device=w.device)
+        st = self._lib.gks_flux(self._h, _dev(w, (4, self.T)), _dev(coef, (4, 5, self.T)), float(dt),
+                                _dev(out, (4, self.F)), _stream(stream))
+        if check:
+            _check(st, "gks_flux")
+        return out, st
+
+    def step(self, w, dt: float = 0.0, stream=None, check=True) -> dict:
+        info = StepInfo()
+        d = C.c_double(dt)
+        st = self._lib.gks_step(self._h, _dev(w, (4, self.T)), C.byref(d), C.byref(info), _stream(stream))
+        if check:
+            _check(st, "gks_step")
+        return {"dt": d.value, "iters": list(info.iters), "relres": list(info.relres), "status": st}
+
+    def step_async(self, w, dt_ptr, info_ptr, stream_ptr) -> int:
+        """Raw call for timing loops: pointers already marshalled."""
+        return self._lib.gks_step(self._h, w, dt_ptr, info_ptr, stream_ptr)
+
+    def run(self, w, t_final: float = 0.0, max_steps: int = 1, steady_tol: float = 0.0, stream=None,
+            check=True) -> dict:
+        info = RunInfo()
+        st = self._lib.gks_run(self._h, _dev(w, (4, self.T)), float(t_final), int(max_steps), float(steady_tol),
+                               C.byref(info), _stream(stream))
+        if check:
+            _check(st, "gks_run")
+        return {k: getattr(info, k) for k, _ in RunInfo._fields_}
+
+
+def point_flux(wl, wr, dt: float, out=None, stream=None, **cfg):
+    """Gauss-point fluxes for n face-frame state pairs wl, wr (n, 6, 4) -> (n, 4)."""
+    import torch
+    n = int(wl.shape[0])
+    if out is None:
+        out = torch.empty((n, 4), dtype=torch.float64, device=wl.device)
+    c = config(**cfg)
+    _check(load().gks_point_flux(n, _dev(wl, (n, 6, 4)), _dev(wr, (n, 6, 4)), float(dt), C.byref(c),
+                                 _dev(out, (n, 4)), _stream(stream)), "gks_point_flux")
+    return out

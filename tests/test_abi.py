@@ -1,0 +1,49 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/gks.h declares (no compute call: this runs without a GPU)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1802_00704_gb300 import build, gks
+    build.build()
+    return gks.load()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "gks.h")).read()
+    return re.findall(r"GKS_EXPORT\s+[\w\s\*]+?\b(gks_\w+)\s*\(", txt)
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    assert set(names) >= {"gks_mesh_create", "gks_cls_reconstruct", "gks_flux", "gks_step", "gks_run"}
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_1802_00704_gb300 import gks
+    for name in _declared():
+        assert hasattr(lib, name), name
+    assert set(_declared()) == set(gks.EXPORTED)
+
+
+def test_config_defaults(lib):
+    from paper_1802_00704_gb300 import gks
+    c = gks.config()
+    assert c.gamma == 1.4 and c.cfl == 0.3 and c.cls_w == 0.3 and c.gmres_m == 30
+    assert c.gmres_rtol == 1e-12 and c.precision == gks.FP64 and list(c.reserved) == [0] * 8
+    # the ctypes mirror has the size of the C struct: 4 doubles, 2 ints, 1 double, 4 ints, 8 ints
+    assert C.sizeof(gks.Config) == 4 * 8 + 2 * 4 + 8 + 4 * 4 + 8 * 4
+
+
+def test_binding_refuses_cpu_tensors(lib):
+    import torch
+    from paper_1802_00704_gb300 import gks
+    with pytest.raises(TypeError):
+        gks._dev(torch.zeros(4, 3, dtype=torch.float64))
