@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark of one explicit step of the third-order gas-kinetic scheme with
+CLS reconstruction (GMRES + ILU(0) on RCM order, BGK flux at face Gauss
+points, conservative update) on the 1,000,000-triangle shock-vortex workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gks|reference]
+
+Prints one JSON line (rank 0).  `value` is triangle-steps/s with the state
+resident in HBM; `e2e` is the same metric through the C ABI with the state
+copied host->device and device->host every step.  With N > 1 (launched by
+torch.distributed.run) every rank advances its own independent replica of the
+workload (weak scaling, no data-path collective).  `--impl reference` times the
+CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "triangle-steps/s"
+HBM_FALLBACK_GBS = 6800.0
+# FP64 (non-tensor) peak: 4 flop/clk/SM (2 DFMA) x 152 SMs x 2.07 GHz; the nominal
+# 1.25 TFLOP/s of the part corresponds to 3.97 flop/clk/SM at that clock.
+FP64_PEAK_TFLOPS = 4 * 152 * 2.07e9 / 1e12
+# FP64 flops executed per face Gauss point by the FP64 flux kernel
+# (dadd + dmul + 2 dfma, ncu instruction counters on the 399,424-triangle case;
+# profiles/flux_fp64_shock_vortex_400k.md).
+FLUX_FP64_FLOP_PER_GP = 8389.3
+
+WORKLOADS = {
+    "shock_vortex_1m": dict(kind="shock_vortex", nx=1000, ny=500),
+    "shock_vortex_small": dict(kind="shock_vortex", nx=200, ny=100),
+    "shock_vortex_400k": dict(kind="shock_vortex", nx=632, ny=316),
+    "advection_20": dict(kind="advection", n=20),
+}
+
+
+def make_case(name: str, replica: int = 0):
+    from paper_1802_00704_gb300 import inputs as I
+    w = WORKLOADS[name]
+    if w["kind"] == "shock_vortex":
+        return I.shock_vortex_case(w["nx"], w["ny"], seed=1802 + replica)
+    return I.advection_case(w["n"], seed=1802 + replica)
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1802_00704_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh)
+    return {}
+
+
+def traffic_record(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (profiles/traffic.txt: kernel source_hash bytes
+    units_per_launch)."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    cur = source_hash()
+    for line in open(p):
+        parts = line.split()
+        if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[1] == cur:
+            return float(parts[2]), float(parts[3])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.tmp.read().splitlines():
+            parts = [q.strip() for q in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.tmp.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_median": statistics.median(power) if power else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(steps: int, warmup: int = 0):
+    """The CPU oracle on a bounded sample of the workload: the same shock-vortex
+    problem on a 200 x 100 split-quad mesh (40,000 triangles)."""
+    from oracle import oracle
+    oracle.build()
+    c = make_case("shock_vortex_small")
+    om = oracle.OracleMesh(c.mesh)
+    w = c.w0.copy()
+    for _ in range(warmup):
+        om.step(w)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        info = om.step(w)
+        if info.status != 0:
+            raise RuntimeError(f"oracle step status {info.status}")
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": c.mesh.n_tri * steps / el, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} oracle steps of the 200x100 (40,000-triangle) shock-vortex mesh, "
+                      f"FP64, OpenMP over faces, sequential GMRES+ILU(0)",
+            "seconds": el}
+
+
+def bytes_per_cell(cls: str, sweeps: int, exact: bool) -> float:
+    """Algorithmic DRAM bytes per cell (FP64) of one launch group of a class."""
+    if cls == "spmv":   # D (15) + 3 x (alpha, ex, ey) + x (20) read, y (20) written, 3 int32 neighbours
+        return 8 * (15 + 9 + 20 + 20) + 12
+    if cls == "ilu":
+        if exact:       # forward and backward: P (25), coefficients, r/z in, z/x out
+            return 2 * (8 * (25 + 9 + 20 + 20) + 12) + 8
+        first = 8 * (25 + 20 + 20)
+        sweep = 8 * (25 + 9 + 20 + 20 + 20) + 12
+        return first + 2 * sweeps * sweep
+    if cls == "update":  # 3 faces x 4 fluxes, w in/out, 1/area, 3 int32
+        return 8 * (12 + 4 + 4 + 1) + 12
+    raise KeyError(cls)
+
+
+def run_gks(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1802_00704_gb300 import gks
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    case = make_case(args.workload, replica=rank)
+    T, F = case.mesh.n_tri, case.mesh.n_face
+    exact = args.precond == "exact"
+    m = gks.GksMesh(case.mesh, precond=gks.PC_ILU_EXACT if exact else gks.PC_ILU_SWEEP, ilu_sweeps=args.sweeps)
+    st = m.stats()
+    w0 = torch.from_numpy(case.w0.copy()).to(dev)
+    w = w0.clone()
+    stream = torch.cuda.current_stream()
+
+    # warm-up
+    for _ in range(args.warmup):
+        m.run(w, max_steps=1)
+    torch.cuda.synchronize()
+
+    # timed region: K steps, state resident in HBM
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = str(local)
+    if getattr(props, "uuid", None) is not None:
+        gpu_id = str(props.uuid)
+        gpu_id = gpu_id if gpu_id.startswith("GPU-") else "GPU-" + gpu_id
+    sampler = ClockSampler(gpu_id)
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = gks.launch_count()
+    m.profile_begin([gks.PROF_FLUX, gks.PROF_SPMV, gks.PROF_ILU, gks.PROF_ORTH, gks.PROF_UPDATE])
+    ev0.record(stream)
+    info = m.run(w, max_steps=args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    prof = m.profile_end()
+    launches = gks.launch_count() - l0
+    barrier(world)
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    ms_max = allmax(world, ms)
+    value = world * T * args.steps / (ms_max / 1e3)
+
+    # end to end through the C ABI with host buffers
+    w_host = torch.from_numpy(case.w0.copy()).pin_memory()
+    w_dev = torch.empty_like(w0)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        w_dev.copy_(w_host, non_blocking=True)
+        m.step(w_dev)
+        w_host.copy_(w_dev, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = allmax(world, time.perf_counter() - t0)
+    e2e_value = world * T * args.steps / e2e_s
+    bytes_state = 4 * T * 8
+
+    # roofline of the dominant kernel class
+    names = ["flux", "spmv", "ilu", "orth", "update"]
+    share = {nm: prof["ms"][q] for q, nm in enumerate(names)}
+    dominant = max(share, key=share.get)
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    hbm_src = "measured" if hbm_peak else "fallback"
+    hbm_peak = hbm_peak or HBM_FALLBACK_GBS
+    q = names.index(dominant)
+    per_launch_ms = prof["ms"][q] / max(prof["n"][q], 1)
+    roof = {"kernel": dominant, "launches": prof["n"][q], "avg_ms": per_launch_ms}
+    if dominant == "flux":
+        gp = 2 * F
+        ach = FLUX_FP64_FLOP_PER_GP * gp / (per_launch_ms / 1e3) / 1e12
+        roof.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": ach / FP64_PEAK_TFLOPS, "flop_per_gauss_point": FLUX_FP64_FLOP_PER_GP,
+                     "peak_source": "FP64 pipe rate from unit count and 2070 MHz clock"})
+    elif dominant == "orth":
+        # CGS2 at Arnoldi index j moves 2 x (160 (j+2) + 160 (j+3)) bytes per cell; the library
+        # reports the launch groups, the mean j comes from the iteration counts.
+        its = max(1, int(round(info["gmres_iters"] / 4 / max(info["steps"], 1))))
+        jbar = (its - 1) / 2.0
+        per_cell = 2 * 8 * 20 * ((jbar + 2) + (jbar + 3))
+        ach = per_cell * T / (per_launch_ms / 1e3) / 1e9
+        roof.update({"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                     "peak_source": hbm_src, "bytes_per_cell": per_cell})
+    else:
+        per_cell = bytes_per_cell(dominant, args.sweeps, exact)
+        ach = per_cell * T / (per_launch_ms / 1e3) / 1e9
+        roof.update({"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                     "peak_source": hbm_src, "bytes_per_cell": per_cell})
+    tr = traffic_record(dominant)
+    roof["traffic"] = tr[0] if tr else None
+    roof["class_ms"] = {nm: round(share[nm], 3) for nm in names}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"shock-vortex {case.mesh.nx}x{case.mesh.ny} split quads, {T} triangles, "
+                               f"{F} faces, FP64, GMRES(30) rtol 1e-12",
+                   "n_tri": T, "n_face": F, "precond": ("ilu0_rcm_exact" if exact else f"ilu0_rcm_sweep{args.sweeps}"),
+                   "l2": f"inputs larger than L2: {st['device_bytes'] / 2**30:.1f} GiB resident per replica",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "gmres_iters_per_step": info["gmres_iters"] / max(info["steps"], 1),
+                   "levels_lower": st["levels_lower"], "levels_upper": st["levels_upper"]},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": bytes_state,
+                "d2h_bytes_per_step": bytes_state},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = oracle_sample(args.cpu_steps)
+        cb.pop("seconds", None)
+        out["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    cb = oracle_sample(args.steps, warmup=args.warmup)
+    secs = cb.pop("seconds")
+    out = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": METRIC, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "shock-vortex, CPU oracle on a 200x100 (40,000-triangle) sample of the "
+                                  "1000x500 workload", "n_tri": 40000},
+           "cpu_baseline": cb,
+           "e2e": {"value": cb["value"], "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gks", choices=["gks", "reference"])
+    ap.add_argument("--workload", default="shock_vortex_1m", choices=sorted(WORKLOADS))
+    ap.add_argument("--precond", default="sweep", choices=["sweep", "exact"])
+    ap.add_argument("--sweeps", type=int, default=2)
+    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gks":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_gks(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

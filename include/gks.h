@@ -218,6 +218,22 @@ GKS_EXPORT gks_status gks_run(gks_mesh *mesh, double *w, double t_final, int64_t
 GKS_EXPORT gks_status gks_point_flux(int64_t n, const double *wl, const double *wr, double dt, const gks_config *cfg,
                           double *out, void *stream);
 
+/* Optional CUDA-event timing of kernel classes, for benchmarks.  Bit c of
+ * class_mask enables class c: 0 face flux, 1 CLS operator application in
+ * GMRES, 2 ILU(0) preconditioner application, 3 Gram-Schmidt orthogonalisation
+ * (dot products, updates, reductions), 4 conservative update.  Events are
+ * recorded on the stream of each call between begin and end. */
+typedef struct gks_profile {
+    int64_t n[5];          /* timed launches (or launch groups) per class              */
+    double ms[5];          /* summed device time per class                             */
+} gks_profile;
+
+GKS_EXPORT gks_status gks_profile_begin(gks_mesh *mesh, int32_t class_mask);
+/* Synchronises on the recorded events, fills *out, disables timing. */
+GKS_EXPORT gks_status gks_profile_end(gks_mesh *mesh, gks_profile *out);
+/* Number of kernel launches issued by the library in this process. */
+GKS_EXPORT int64_t gks_launch_count(void);
+
 /* Thread-local message of the last error, or "" if none. */
 GKS_EXPORT const char *gks_last_error(void);
 

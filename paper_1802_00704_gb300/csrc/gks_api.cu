@@ -7,7 +7,29 @@
 
 namespace gks {
 const char *last_error();
+std::atomic<int64_t> g_launches{0};
+
+int prof_start(gks_mesh *m, int cls, cudaStream_t s)
+{
+    gks_profiler &p = m->prof;
+    if (!(p.mask & (1 << cls))) return -1;
+    while (p.events.size() < p.used + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        p.events.push_back(e);
+    }
+    const int slot = (int)p.used;
+    p.used += 2;
+    p.cls.push_back(cls);
+    cudaEventRecord(p.events[slot], s);
+    return slot;
 }
+
+void prof_stop(gks_mesh *m, int slot, cudaStream_t s)
+{
+    if (slot >= 0) cudaEventRecord(m->prof.events[slot + 1], s);
+}
+}  // namespace gks
 
 using namespace gks;
 
@@ -149,6 +171,7 @@ gks_status gks_mesh_destroy(gks_mesh *m)
 {
     if (!m) return GKS_OK;
     DeviceGuard g(m->device);
+    for (cudaEvent_t e : m->prof.events) cudaEventDestroy(e);
     free_mesh(m);
     delete m;
     return GKS_OK;
@@ -322,6 +345,42 @@ gks_status gks_run(gks_mesh *m, double *w, double t_final, int64_t max_steps, do
     }
     return res;
 }
+
+gks_status gks_profile_begin(gks_mesh *m, int32_t class_mask)
+{
+    if (!m || class_mask < 0 || class_mask >= (1 << kProfClasses)) {
+        set_error("gks_profile_begin: bad argument");
+        return GKS_EINVAL;
+    }
+    m->prof.mask = class_mask;
+    m->prof.used = 0;
+    m->prof.cls.clear();
+    return GKS_OK;
+}
+
+gks_status gks_profile_end(gks_mesh *m, gks_profile *out)
+{
+    if (!m || !out) {
+        set_error("gks_profile_end: NULL argument");
+        return GKS_EINVAL;
+    }
+    DeviceGuard g(m->device);
+    std::memset(out, 0, sizeof(*out));
+    gks_profiler &p = m->prof;
+    for (size_t q = 0; q < p.cls.size(); ++q) {
+        GKS_CUDA(cudaEventSynchronize(p.events[2 * q + 1]));
+        float ms = 0.0f;
+        GKS_CUDA(cudaEventElapsedTime(&ms, p.events[2 * q], p.events[2 * q + 1]));
+        out->ms[p.cls[q]] += ms;
+        out->n[p.cls[q]] += 1;
+    }
+    p.mask = 0;
+    p.used = 0;
+    p.cls.clear();
+    return GKS_OK;
+}
+
+int64_t gks_launch_count(void) { return g_launches.load(); }
 
 gks_status gks_point_flux(int64_t n, const double *wl, const double *wr, double dt, const gks_config *cfg, double *out,
                           void *stream)

@@ -484,21 +484,21 @@ gks_status precond(gks_mesh *m, const double *src, double *dst, cudaStream_t s)
         const auto &lp = m->lvl_lo_ptr;
         for (size_t l = 0; l + 1 < lp.size(); ++l) {
             const int64_t n = lp[l + 1] - lp[l];
-            k_ilu_fwd<<<nblocks(n), kBlock, 0, s>>>(d, d.lvl_lo + lp[l], n, src, dst, dst, 1);
+            k_ilu_fwd<<<nblocks(n), kBlock, 0, s>>>(d, d.lvl_lo + lp[l], n, src, dst, dst, 1); note_launch();
         }
         const auto &up = m->lvl_up_ptr;
         for (size_t l = 0; l + 1 < up.size(); ++l) {
             const int64_t n = up[l + 1] - up[l];
-            k_ilu_bwd<<<nblocks(n), kBlock, 0, s>>>(d, d.lvl_up + up[l], n, dst, dst, dst);
+            k_ilu_bwd<<<nblocks(n), kBlock, 0, s>>>(d, d.lvl_up + up[l], n, dst, dst, dst); note_launch();
         }
     } else {
         // sweeps: forward z^0 = P r, z^{q+1} = F(z^q); backward x^0 = z, x^{q+1} = B(x^q)
         const int ns = m->cfg.ilu_sweeps;
         double *za = (ns % 2 == 0) ? k.t2 : dst;   // buffers chosen so z ends in t2
         double *zb = (ns % 2 == 0) ? dst : k.t2;
-        k_ilu_fwd<<<nblocks(T), kBlock, 0, s>>>(d, nullptr, T, src, nullptr, za, 0);
+        k_ilu_fwd<<<nblocks(T), kBlock, 0, s>>>(d, nullptr, T, src, nullptr, za, 0); note_launch();
         for (int q = 0; q < ns; ++q) {
-            k_ilu_fwd<<<nblocks(T), kBlock, 0, s>>>(d, nullptr, T, src, za, zb, 1);
+            k_ilu_fwd<<<nblocks(T), kBlock, 0, s>>>(d, nullptr, T, src, za, zb, 1); note_launch();
             std::swap(za, zb);
         }
         // now za == t2 holds z
@@ -508,7 +508,7 @@ gks_status precond(gks_mesh *m, const double *src, double *dst, cudaStream_t s)
             double *xa = za;                                    // x^0 = z
             double *xb = (ns % 2 == 1) ? dst : k.t3;
             for (int q = 0; q < ns; ++q) {
-                k_ilu_bwd<<<nblocks(T), kBlock, 0, s>>>(d, nullptr, T, za, xa, xb);
+                k_ilu_bwd<<<nblocks(T), kBlock, 0, s>>>(d, nullptr, T, za, xa, xb); note_launch();
                 xa = xb;
                 xb = (xb == dst) ? k.t3 : dst;
             }
@@ -542,42 +542,48 @@ gks_status cls_solve(gks_mesh *m, cudaStream_t s, gks_solve_info *info)
     const int64_t vs = (int64_t)NX * T;
     gks_status st;
 
-    k_rhs<<<nb, kBlock, 0, s>>>(d, k.w, k.b);
-    k_spmv<<<nb, kBlock, 0, s>>>(d, k.x, k.r, 1, k.b, k.part, ps);
-    k_reduce<<<dim3(2, NV), kBlock, 0, s>>>(k.part, k.nblk, ps, k.hcol, ps, 0);
-    k_start<<<1, 32, 0, s>>>(k.hcol, ps, k.bnorm, k.beta, k.ctl, rtol, maxit, 1);
-    k_zero_trivial<<<nb, kBlock, 0, s>>>(T, k.x, k.bnorm);
+    k_rhs<<<nb, kBlock, 0, s>>>(d, k.w, k.b); note_launch();
+    k_spmv<<<nb, kBlock, 0, s>>>(d, k.x, k.r, 1, k.b, k.part, ps); note_launch();
+    k_reduce<<<dim3(2, NV), kBlock, 0, s>>>(k.part, k.nblk, ps, k.hcol, ps, 0); note_launch();
+    k_start<<<1, 32, 0, s>>>(k.hcol, ps, k.bnorm, k.beta, k.ctl, rtol, maxit, 1); note_launch();
+    k_zero_trivial<<<nb, kBlock, 0, s>>>(T, k.x, k.bnorm); note_launch();
     GKS_CUDA(cudaGetLastError());
     if ((st = read_ctl(m, s)) != GKS_OK) return st;
 
     while (k.h_ctl[0] | k.h_ctl[1] | k.h_ctl[2] | k.h_ctl[3]) {
-        k_init_v0<<<std::max(nb, nblocks(NV * (mm + 1))), kBlock, 0, s>>>(T, k.r, k.V, k.beta, k.ctl, k.g, mm);
+        k_init_v0<<<std::max(nb, nblocks(NV * (mm + 1))), kBlock, 0, s>>>(T, k.r, k.V, k.beta, k.ctl, k.g, mm); note_launch();
         for (int j = 0; j < mm; ++j) {
             double *vj = k.V + j * vs, *vj1 = k.V + (j + 1) * vs;
+            int slot = prof_start(m, kProfIlu, s);
             if ((st = precond(m, vj, k.t, s)) != GKS_OK) return st;
-            k_spmv<<<nb, kBlock, 0, s>>>(d, k.t, vj1, 0, nullptr, nullptr, 0);
+            prof_stop(m, slot, s);
+            slot = prof_start(m, kProfSpmv, s);
+            k_spmv<<<nb, kBlock, 0, s>>>(d, k.t, vj1, 0, nullptr, nullptr, 0); note_launch();
+            prof_stop(m, slot, s);
+            slot = prof_start(m, kProfOrth, s);
             // classical Gram-Schmidt, twice
-            k_dots<<<nb, kBlock, 0, s>>>(T, k.V, vj1, j, k.part, ps);
-            k_reduce<<<dim3(j + 1, NV), kBlock, 0, s>>>(k.part, k.nblk, ps, k.hcol, ps, 0);
-            k_orth_update<<<nb, kBlock, 0, s>>>(T, k.V, vj1, j, k.hcol, ps, k.ctl, k.part, ps, 0);
-            k_dots<<<nb, kBlock, 0, s>>>(T, k.V, vj1, j, k.part, ps);
-            k_reduce<<<dim3(j + 1, NV), kBlock, 0, s>>>(k.part, k.nblk, ps, k.y, mm, 0);   // second-pass coefficients
-            k_orth_update<<<nb, kBlock, 0, s>>>(T, k.V, vj1, j, k.y, mm, k.ctl, k.part, ps, 1);
-            k_reduce<<<dim3(1, NV), kBlock, 0, s>>>(k.part, k.nblk, ps, k.hcol + j + 1, ps, 2);
-            k_hadd<<<1, 128, 0, s>>>(k.hcol, ps, k.y, mm, j);
-            k_scale<<<nb, kBlock, 0, s>>>(T, vj1, k.hcol, ps, j, k.ctl);
-            k_givens<<<1, 32, 0, s>>>(j, mm, k.hcol, ps, k.H, k.cs, k.sn, k.g, k.ctl, k.bnorm, rtol, maxit);
+            k_dots<<<nb, kBlock, 0, s>>>(T, k.V, vj1, j, k.part, ps); note_launch();
+            k_reduce<<<dim3(j + 1, NV), kBlock, 0, s>>>(k.part, k.nblk, ps, k.hcol, ps, 0); note_launch();
+            k_orth_update<<<nb, kBlock, 0, s>>>(T, k.V, vj1, j, k.hcol, ps, k.ctl, k.part, ps, 0); note_launch();
+            k_dots<<<nb, kBlock, 0, s>>>(T, k.V, vj1, j, k.part, ps); note_launch();
+            k_reduce<<<dim3(j + 1, NV), kBlock, 0, s>>>(k.part, k.nblk, ps, k.y, mm, 0); note_launch();   // second-pass coefficients
+            k_orth_update<<<nb, kBlock, 0, s>>>(T, k.V, vj1, j, k.y, mm, k.ctl, k.part, ps, 1); note_launch();
+            k_reduce<<<dim3(1, NV), kBlock, 0, s>>>(k.part, k.nblk, ps, k.hcol + j + 1, ps, 2); note_launch();
+            k_hadd<<<1, 128, 0, s>>>(k.hcol, ps, k.y, mm, j); note_launch();
+            prof_stop(m, slot, s);
+            k_scale<<<nb, kBlock, 0, s>>>(T, vj1, k.hcol, ps, j, k.ctl); note_launch();
+            k_givens<<<1, 32, 0, s>>>(j, mm, k.hcol, ps, k.H, k.cs, k.sn, k.g, k.ctl, k.bnorm, rtol, maxit); note_launch();
             GKS_CUDA(cudaGetLastError());
             if ((st = read_ctl(m, s)) != GKS_OK) return st;
             if (!(k.h_ctl[4] | k.h_ctl[5] | k.h_ctl[6] | k.h_ctl[7])) break;
         }
-        k_backsolve<<<1, 32, 0, s>>>(mm, k.H, k.g, k.y, k.ctl);
-        k_combine<<<nb, kBlock, 0, s>>>(T, k.V, k.y, mm, k.ctl, k.r);
+        k_backsolve<<<1, 32, 0, s>>>(mm, k.H, k.g, k.y, k.ctl); note_launch();
+        k_combine<<<nb, kBlock, 0, s>>>(T, k.V, k.y, mm, k.ctl, k.r); note_launch();
         if ((st = precond(m, k.r, k.t, s)) != GKS_OK) return st;
-        k_addx<<<nb, kBlock, 0, s>>>(T, k.x, k.t, k.ctl);
-        k_spmv<<<nb, kBlock, 0, s>>>(d, k.x, k.r, 1, k.b, k.part, ps);
-        k_reduce<<<dim3(2, NV), kBlock, 0, s>>>(k.part, k.nblk, ps, k.hcol, ps, 0);
-        k_start<<<1, 32, 0, s>>>(k.hcol, ps, k.bnorm, k.beta, k.ctl, rtol, maxit, 0);
+        k_addx<<<nb, kBlock, 0, s>>>(T, k.x, k.t, k.ctl); note_launch();
+        k_spmv<<<nb, kBlock, 0, s>>>(d, k.x, k.r, 1, k.b, k.part, ps); note_launch();
+        k_reduce<<<dim3(2, NV), kBlock, 0, s>>>(k.part, k.nblk, ps, k.hcol, ps, 0); note_launch();
+        k_start<<<1, 32, 0, s>>>(k.hcol, ps, k.bnorm, k.beta, k.ctl, rtol, maxit, 0); note_launch();
         GKS_CUDA(cudaGetLastError());
         if ((st = read_ctl(m, s)) != GKS_OK) return st;
         if (!(k.h_ctl[0] | k.h_ctl[1] | k.h_ctl[2] | k.h_ctl[3])) break;

@@ -288,15 +288,19 @@ gks_status launch_flux(gks_mesh *m, const double *w, const double *x, double dt_
                        double *flux, cudaStream_t s)
 {
     const int64_t npts = 2 * m->d.F;
+    const int slot = prof_start(m, kProfFlux, s);
     k_face_flux<<<blocks(npts, kFluxBlock), kFluxBlock, 0, s>>>(m->d, w, x, dt_const, dt_dev, m->cfg.gamma, m->cfg.mu,
-                                                                m->cfg.tau2_exact, flux, m->wk.status);
+                                                                m->cfg.tau2_exact, flux, m->wk.status); note_launch();
+    prof_stop(m, slot, s);
     GKS_CUDA(cudaGetLastError());
     return GKS_OK;
 }
 
 gks_status launch_update(gks_mesh *m, double *w, const double *flux, cudaStream_t s)
 {
-    k_update<<<blocks(m->d.T, kBlock), kBlock, 0, s>>>(m->d, w, flux, m->cfg.gamma, m->wk.status);
+    const int slot = prof_start(m, kProfUpdate, s);
+    k_update<<<blocks(m->d.T, kBlock), kBlock, 0, s>>>(m->d, w, flux, m->cfg.gamma, m->wk.status); note_launch();
+    prof_stop(m, slot, s);
     GKS_CUDA(cudaGetLastError());
     return GKS_OK;
 }
@@ -304,8 +308,8 @@ gks_status launch_update(gks_mesh *m, double *w, const double *flux, cudaStream_
 gks_status launch_cfl_dt(gks_mesh *m, const double *w, double *dt_dev, cudaStream_t s)
 {
     const unsigned nb = blocks(m->d.T, kBlock);
-    k_cfl_partial<<<nb, kBlock, 0, s>>>(m->d, w, m->cfg.gamma, m->cfg.mu, m->wk.dpart);
-    k_min_final<<<1, kBlock, 0, s>>>(m->wk.dpart, (int)nb, m->cfg.cfl, dt_dev);
+    k_cfl_partial<<<nb, kBlock, 0, s>>>(m->d, w, m->cfg.gamma, m->cfg.mu, m->wk.dpart); note_launch();
+    k_min_final<<<1, kBlock, 0, s>>>(m->wk.dpart, (int)nb, m->cfg.cfl, dt_dev); note_launch();
     GKS_CUDA(cudaGetLastError());
     return GKS_OK;
 }
@@ -315,7 +319,7 @@ gks_status launch_point_flux(int64_t n, const double *wl, const double *wr, doub
 {
     if (n <= 0) return GKS_OK;
     k_point_flux<<<blocks(n, kFluxBlock), kFluxBlock, 0, s>>>(n, wl, wr, dt, cfg.gamma, cfg.mu, cfg.tau2_exact, out,
-                                                              status);
+                                                              status); note_launch();
     GKS_CUDA(cudaGetLastError());
     return GKS_OK;
 }
@@ -323,7 +327,7 @@ gks_status launch_point_flux(int64_t n, const double *wl, const double *wr, doub
 gks_status launch_permute(const double *src, double *dst, const int32_t *perm, int64_t n, int nvar, bool gather,
                           cudaStream_t s)
 {
-    k_permute<<<blocks(n, kBlock), kBlock, 0, s>>>(src, dst, perm, n, nvar, gather ? 1 : 0);
+    k_permute<<<blocks(n, kBlock), kBlock, 0, s>>>(src, dst, perm, n, nvar, gather ? 1 : 0); note_launch();
     GKS_CUDA(cudaGetLastError());
     return GKS_OK;
 }
@@ -332,8 +336,8 @@ gks_status launch_permute(const double *src, double *dst, const int32_t *perm, i
 gks_status launch_steady_partial(gks_mesh *m, cudaStream_t s)
 {
     const unsigned nb = blocks(m->d.T, kBlock);
-    k_steady_partial<<<nb, kBlock, 0, s>>>(m->d, m->wk.w, m->wk.w_old, m->wk.dpart);
-    k_sum4_final<<<1, kBlock, 0, s>>>(m->wk.dpart, (int)nb, m->wk.scal);
+    k_steady_partial<<<nb, kBlock, 0, s>>>(m->d, m->wk.w, m->wk.w_old, m->wk.dpart); note_launch();
+    k_sum4_final<<<1, kBlock, 0, s>>>(m->wk.dpart, (int)nb, m->wk.scal); note_launch();
     GKS_CUDA(cudaGetLastError());
     return GKS_OK;
 }

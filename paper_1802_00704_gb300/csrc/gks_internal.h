@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -25,6 +26,13 @@ void set_error(const char *fmt, ...);
             return GKS_ECUDA;                                                             \
         }                                                                                 \
     } while (0)
+
+// Process-wide count of kernel launches issued by the library.
+extern std::atomic<int64_t> g_launches;
+inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// Kernel classes timed by the optional CUDA-event profiler.
+enum : int { kProfFlux = 0, kProfSpmv = 1, kProfIlu = 2, kProfOrth = 3, kProfUpdate = 4, kProfClasses = 5 };
 
 // Device status bits (a word the kernels OR into).
 enum : int { kStatusNonPhys = 1 };
@@ -83,8 +91,17 @@ struct Work {
 
 }  // namespace gks
 
+struct gks_profiler {
+    int mask = 0;                                   // bit c: time class c
+    std::vector<cudaEvent_t> events;                // pool
+    size_t used = 0;
+    std::vector<int> cls;                           // class of each start/stop pair
+    int64_t count[gks::kProfClasses] = {0};
+};
+
 struct gks_mesh {
     gks_config cfg{};
+    gks_profiler prof;
     int device = 0;
     int64_t n_tri = 0, n_face = 0, n_bface = 0, n_k1 = 0, nnzb = 0, bandwidth = 0;
     std::vector<int32_t> lvl_lo_ptr, lvl_up_ptr;   // level offsets (host)
@@ -114,5 +131,9 @@ gks_status launch_point_flux(int64_t n, const double *wl, const double *wr, doub
 gks_status launch_permute(const double *src, double *dst, const int32_t *perm, int64_t n, int nvar, bool gather,
                           cudaStream_t s);
 gks_status launch_steady_partial(gks_mesh *m, cudaStream_t s);
+
+// optional CUDA-event timing of one kernel class (no-op unless enabled)
+int prof_start(gks_mesh *m, int cls, cudaStream_t s);
+void prof_stop(gks_mesh *m, int slot, cudaStream_t s);
 
 }  // namespace gks

@@ -25,7 +25,8 @@ FP64, MIXED = 0, 1
 
 EXPORTED = ["gks_config_default", "gks_mesh_create", "gks_mesh_destroy", "gks_mesh_get_stats", "gks_cfl_dt",
             "gks_cls_reconstruct", "gks_reset_warm_start", "gks_flux", "gks_step", "gks_run", "gks_point_flux",
-            "gks_last_error"]
+            "gks_profile_begin", "gks_profile_end", "gks_launch_count", "gks_last_error"]
+PROF_FLUX, PROF_SPMV, PROF_ILU, PROF_ORTH, PROF_UPDATE = range(5)
 
 
 class GksError(RuntimeError):
@@ -52,6 +53,10 @@ class StepInfo(C.Structure):
 class RunInfo(C.Structure):
     _fields_ = [("steps", C.c_int64), ("t", C.c_double), ("last_dt", C.c_double), ("gmres_iters", C.c_int64),
                 ("steady_res", C.c_double), ("status", C.c_int32)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("n", C.c_int64 * 5), ("ms", C.c_double * 5)]
 
 
 class MeshStats(C.Structure):
@@ -96,6 +101,12 @@ def load():
     lib.gks_run.restype = st
     lib.gks_point_flux.argtypes = [I64, P, P, D, C.POINTER(Config), P, P]
     lib.gks_point_flux.restype = st
+    lib.gks_profile_begin.argtypes = [P, I32]
+    lib.gks_profile_begin.restype = st
+    lib.gks_profile_end.argtypes = [P, C.POINTER(Profile)]
+    lib.gks_profile_end.restype = st
+    lib.gks_launch_count.argtypes = []
+    lib.gks_launch_count.restype = I64
     lib.gks_last_error.argtypes = []
     lib.gks_last_error.restype = C.c_char_p
     _lib = lib
@@ -213,6 +224,17 @@ class GksMesh:
         """Raw call for timing loops: pointers already marshalled."""
         return self._lib.gks_step(self._h, w, dt_ptr, info_ptr, stream_ptr)
 
+    def profile_begin(self, classes) -> None:
+        mask = 0
+        for c in classes:
+            mask |= 1 << c
+        _check(self._lib.gks_profile_begin(self._h, mask), "gks_profile_begin")
+
+    def profile_end(self) -> dict:
+        p = Profile()
+        _check(self._lib.gks_profile_end(self._h, C.byref(p)), "gks_profile_end")
+        return {"n": list(p.n), "ms": list(p.ms)}
+
     def run(self, w, t_final: float = 0.0, max_steps: int = 1, steady_tol: float = 0.0, stream=None,
             check=True) -> dict:
         info = RunInfo()
@@ -221,6 +243,11 @@ class GksMesh:
         if check:
             _check(st, "gks_run")
         return {k: getattr(info, k) for k, _ in RunInfo._fields_}
+
+
+def launch_count() -> int:
+    """Kernel launches issued by the library in this process."""
+    return int(load().gks_launch_count())
 
 
 def point_flux(wl, wr, dt: float, out=None, stream=None, **cfg):
