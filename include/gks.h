@@ -178,6 +178,24 @@ GKS_EXPORT gks_status gks_mesh_get_stats(const gks_mesh *mesh, gks_mesh_stats *s
  * w: device [4][n_tri].  *dt_out: host.  Synchronises the stream. */
 GKS_EXPORT gks_status gks_cfl_dt(gks_mesh *mesh, const double *w, double *dt_out, void *stream);
 
+/* Same time step as gks_cfl_dt, for callers that cannot allocate device
+ * memory when they need it: code running while a stream is captured into a
+ * CUDA graph (an allocation may synchronise the device and break the
+ * capture), time loops that reserve all memory at start-up, or hosts whose
+ * device memory belongs to another allocator.  The paper has no counterpart;
+ * this entry point only changes where the scratch lives.
+ *   w      device [4][n_tri], caller's cell order (read only);
+ *   dt_dev device pointer to one double that receives the step; nothing is
+ *          copied to the host and the stream is not synchronised.
+ * The call allocates nothing: the block minima of its reduction live in a
+ * 128 KiB static device array of the library, held by every GPU that loads
+ * it until exit, which limits meshes to 4,194,304 cells (GKS_EINVAL above).
+ * The first call on each device looks up that array's device address; make
+ * it before any stream capture.  All calls share the array, so calls that
+ * overlap on the GPU (two streams, or two handles on one device) race; each
+ * call writes every entry it reads, so nothing has to start at zero. */
+GKS_EXPORT gks_status gks_cfl_dt_noalloc(const gks_mesh *mesh, const double *w, double *dt_dev, void *stream);
+
 /* CLS reconstruction (Sec. III): solves the per-cell least-squares system
  * for the four variables of w (device [4][n_tri]) and writes the coefficients
  * to coef (device [4][5][n_tri]).  GMRES starts from the handle's previous

@@ -25,7 +25,7 @@ FP64, MIXED = 0, 1
 
 EXPORTED = ["gks_config_default", "gks_mesh_create", "gks_mesh_destroy", "gks_mesh_get_stats", "gks_cfl_dt",
             "gks_cls_reconstruct", "gks_reset_warm_start", "gks_flux", "gks_step", "gks_run", "gks_point_flux",
-            "gks_profile_begin", "gks_profile_end", "gks_launch_count", "gks_last_error"]
+            "gks_profile_begin", "gks_profile_end", "gks_launch_count", "gks_cfl_dt_noalloc", "gks_last_error"]
 PROF_FLUX, PROF_SPMV, PROF_ILU, PROF_ORTH, PROF_UPDATE = range(5)
 
 
@@ -89,6 +89,8 @@ def load():
     lib.gks_mesh_get_stats.restype = st
     lib.gks_cfl_dt.argtypes = [P, P, C.POINTER(D), P]
     lib.gks_cfl_dt.restype = st
+    lib.gks_cfl_dt_noalloc.argtypes = [P, P, P, P]
+    lib.gks_cfl_dt_noalloc.restype = st
     lib.gks_cls_reconstruct.argtypes = [P, P, P, C.POINTER(SolveInfo), P]
     lib.gks_cls_reconstruct.restype = st
     lib.gks_reset_warm_start.argtypes = [P]
@@ -186,6 +188,13 @@ class GksMesh:
         dt = C.c_double(0.0)
         _check(self._lib.gks_cfl_dt(self._h, _dev(w, (4, self.T)), C.byref(dt), _stream(stream)), "gks_cfl_dt")
         return dt.value
+
+    def cfl_dt_noalloc(self, w, dt_dev, stream=None):
+        """CFL step into the device scalar dt_dev (1-element float64 CUDA tensor);
+        allocates nothing, does not synchronise."""
+        _check(self._lib.gks_cfl_dt_noalloc(self._h, _dev(w, (4, self.T)), _dev(dt_dev, (1,)), _stream(stream)),
+               "gks_cfl_dt_noalloc")
+        return dt_dev
 
     def cls_reconstruct(self, w, coef=None, stream=None, check=True):
         import torch
