@@ -38,6 +38,8 @@ FP64_PEAK_TFLOPS = 4 * 152 * 2.07e9 / 1e12
 # (dadd + dmul + 2 dfma, ncu instruction counters on the 399,424-triangle case;
 # profiles/flux_fp64_shock_vortex_400k.md).
 FLUX_FP64_FLOP_PER_GP = 8389.3
+# FP64 flops per Gauss point left in the mixed flux kernel (to be measured).
+FLUX_MIXED_FP64_FLOP_PER_GP = None
 
 WORKLOADS = {
     "shock_vortex_1m": dict(kind="shock_vortex", nx=1000, ny=500),
@@ -183,51 +185,50 @@ def oracle_sample(steps: int, warmup: int = 0):
             "seconds": el}
 
 
-def bytes_per_cell(cls: str, sweeps: int, exact: bool) -> float:
-    """Algorithmic DRAM bytes per cell (FP64) of one launch group of a class."""
-    if cls == "spmv":   # D (15) + 3 x (alpha, ex, ey) + x (20) read, y (20) written, 3 int32 neighbours
-        return 8 * (15 + 9 + 20 + 20) + 12
+def bytes_per_cell(cls: str, sweeps: int, exact: bool, mixed: bool) -> float:
+    """Algorithmic DRAM bytes per cell of one launch group of a kernel class.
+    Operator data per cell: diagonal block 15 values, ILU pivot inverse 25,
+    off-diagonal blocks 3 x (alpha, dx, dy) + 3 int32 neighbours; vectors 20
+    values.  FP64 path: 8-byte everything.  Mixed: 4-byte operator, factors and
+    preconditioner vectors; the Krylov vectors stay FP64."""
+    sm = 4 if mixed else 8          # operator / factor values
+    sz = 4 if mixed else 8          # preconditioner work vectors
+    if cls == "spmv":               # D, offdiag, x (precond output), y (Krylov, FP64)
+        return sm * (15 + 9) + 12 + sz * 20 + 8 * 20
     if cls == "ilu":
-        if exact:       # forward and backward: P (25), coefficients, r/z in, z/x out
-            return 2 * (8 * (25 + 9 + 20 + 20) + 12) + 8
-        first = 8 * (25 + 20 + 20)
-        sweep = 8 * (25 + 9 + 20 + 20 + 20) + 12
-        return first + 2 * sweeps * sweep
-    if cls == "update":  # 3 faces x 4 fluxes, w in/out, 1/area, 3 int32
+        if exact:                   # one forward and one backward pass over all rows
+            return 2 * (sm * (25 + 9) + 12) + 8 * 20 + 3 * sz * 20 + 8
+        first = sm * 25 + 8 * 20 + sz * 20
+        fwd = sm * (25 + 9) + 12 + 8 * 20 + 2 * sz * 20
+        bwd = sm * (25 + 9) + 12 + 3 * sz * 20
+        return first + sweeps * (fwd + bwd)
+    if cls == "update":             # 3 faces x 4 fluxes, w in/out, 1/area, 3 int32
         return 8 * (12 + 4 + 4 + 1) + 12
     raise KeyError(cls)
 
 
-def run_gks(args, world, rank, local):
-    import numpy as np
+def timed_leg(args, case, precision: str, world: int, dev, sample_clocks: bool):
+    """W warm-up steps, then K timed steps of the step on the resident state."""
     import torch
 
     from paper_1802_00704_gb300 import gks
-
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    case = make_case(args.workload, replica=rank)
-    T, F = case.mesh.n_tri, case.mesh.n_face
     exact = args.precond == "exact"
-    m = gks.GksMesh(case.mesh, precond=gks.PC_ILU_EXACT if exact else gks.PC_ILU_SWEEP, ilu_sweeps=args.sweeps)
-    st = m.stats()
-    w0 = torch.from_numpy(case.w0.copy()).to(dev)
-    w = w0.clone()
+    m = gks.GksMesh(case.mesh, precond=gks.PC_ILU_EXACT if exact else gks.PC_ILU_SWEEP, ilu_sweeps=args.sweeps,
+                    precision=gks.MIXED if precision == "mixed" else gks.FP64)
+    w = torch.from_numpy(case.w0.copy()).to(dev)
     stream = torch.cuda.current_stream()
-
-    # warm-up
     for _ in range(args.warmup):
         m.run(w, max_steps=1)
     torch.cuda.synchronize()
-
-    # timed region: K steps, state resident in HBM
-    props = torch.cuda.get_device_properties(dev)
-    gpu_id = str(local)
-    if getattr(props, "uuid", None) is not None:
-        gpu_id = str(props.uuid)
-        gpu_id = gpu_id if gpu_id.startswith("GPU-") else "GPU-" + gpu_id
-    sampler = ClockSampler(gpu_id)
-    time.sleep(0.3)
+    sampler = None
+    if sample_clocks:
+        props = torch.cuda.get_device_properties(dev)
+        gpu_id = str(dev.index)
+        if getattr(props, "uuid", None) is not None:
+            gpu_id = str(props.uuid)
+            gpu_id = gpu_id if gpu_id.startswith("GPU-") else "GPU-" + gpu_id
+        sampler = ClockSampler(gpu_id)
+        time.sleep(0.3)
     barrier(world)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -240,14 +241,30 @@ def run_gks(args, world, rank, local):
     prof = m.profile_end()
     launches = gks.launch_count() - l0
     barrier(world)
-    clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    ms_max = allmax(world, ms)
-    value = world * T * args.steps / (ms_max / 1e3)
+    clocks = sampler.stop() if sampler else None
+    ms = allmax(world, ev0.elapsed_time(ev1))
+    return {"mesh": m, "w": w, "info": info, "prof": prof, "launches": launches, "clocks": clocks, "ms": ms,
+            "stats": m.stats()}
 
-    # end to end through the C ABI with host buffers
+
+def run_gks(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    case = make_case(args.workload, replica=rank)
+    T, F = case.mesh.n_tri, case.mesh.n_face
+    exact = args.precond == "exact"
+    mixed = args.precision == "mixed"
+
+    main = timed_leg(args, case, args.precision, world, dev, sample_clocks=True)
+    value = world * T * args.steps / (main["ms"] / 1e3)
+
+    # end to end through the C ABI with host buffers (pinned), every step
+    m = main["mesh"]
     w_host = torch.from_numpy(case.w0.copy()).pin_memory()
-    w_dev = torch.empty_like(w0)
+    w_dev = torch.empty((4, T), dtype=torch.float64, device=dev)
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -261,6 +278,7 @@ def run_gks(args, world, rank, local):
     bytes_state = 4 * T * 8
 
     # roofline of the dominant kernel class
+    prof, info = main["prof"], main["info"]
     names = ["flux", "spmv", "ilu", "orth", "update"]
     share = {nm: prof["ms"][q] for q, nm in enumerate(names)}
     dominant = max(share, key=share.get)
@@ -271,15 +289,21 @@ def run_gks(args, world, rank, local):
     q = names.index(dominant)
     per_launch_ms = prof["ms"][q] / max(prof["n"][q], 1)
     roof = {"kernel": dominant, "launches": prof["n"][q], "avg_ms": per_launch_ms}
-    if dominant == "flux":
+    if dominant == "flux" and not mixed:
         gp = 2 * F
         ach = FLUX_FP64_FLOP_PER_GP * gp / (per_launch_ms / 1e3) / 1e12
         roof.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": ach / FP64_PEAK_TFLOPS, "flop_per_gauss_point": FLUX_FP64_FLOP_PER_GP,
                      "peak_source": "FP64 pipe rate from unit count and 2070 MHz clock"})
+    elif dominant == "flux":
+        gp = 2 * F
+        ach = FLUX_MIXED_FP64_FLOP_PER_GP * gp / (per_launch_ms / 1e3) / 1e12 if FLUX_MIXED_FP64_FLOP_PER_GP else None
+        roof.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": ach / FP64_PEAK_TFLOPS if ach else None,
+                     "flop_per_gauss_point": FLUX_MIXED_FP64_FLOP_PER_GP,
+                     "peak_source": "FP64 pipe rate from unit count and 2070 MHz clock"})
     elif dominant == "orth":
-        # CGS2 at Arnoldi index j moves 2 x (160 (j+2) + 160 (j+3)) bytes per cell; the library
-        # reports the launch groups, the mean j comes from the iteration counts.
+        # CGS2 at Arnoldi index j moves 2 x 160 (2 j + 5) bytes per cell (FP64 basis)
         its = max(1, int(round(info["gmres_iters"] / 4 / max(info["steps"], 1))))
         jbar = (its - 1) / 2.0
         per_cell = 2 * 8 * 20 * ((jbar + 2) + (jbar + 3))
@@ -287,21 +311,23 @@ def run_gks(args, world, rank, local):
         roof.update({"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
                      "peak_source": hbm_src, "bytes_per_cell": per_cell})
     else:
-        per_cell = bytes_per_cell(dominant, args.sweeps, exact)
+        per_cell = bytes_per_cell(dominant, args.sweeps, exact, mixed)
         ach = per_cell * T / (per_launch_ms / 1e3) / 1e9
         roof.update({"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
                      "peak_source": hbm_src, "bytes_per_cell": per_cell})
-    tr = traffic_record(dominant)
+    tr = traffic_record(("mixed_" if mixed else "") + dominant)
     roof["traffic"] = tr[0] if tr else None
     roof["class_ms"] = {nm: round(share[nm], 3) for nm in names}
+    st = main["stats"]
 
     out = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "warmup": args.warmup, "ms_per_step": main["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64 (mixed)" if mixed else "f64", "data": "synthetic",
         "config": {"workload": f"shock-vortex {case.mesh.nx}x{case.mesh.ny} split quads, {T} triangles, "
-                               f"{F} faces, FP64, GMRES(30) rtol 1e-12",
-                   "n_tri": T, "n_face": F, "precond": ("ilu0_rcm_exact" if exact else f"ilu0_rcm_sweep{args.sweeps}"),
+                               f"{F} faces, GMRES(30) rtol 1e-12",
+                   "n_tri": T, "n_face": F, "precision": args.precision,
+                   "precond": ("ilu0_rcm_exact" if exact else f"ilu0_rcm_sweep{args.sweeps}"),
                    "l2": f"inputs larger than L2: {st['device_bytes'] / 2**30:.1f} GiB resident per replica",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "gmres_iters_per_step": info["gmres_iters"] / max(info["steps"], 1),
@@ -309,9 +335,22 @@ def run_gks(args, world, rank, local):
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": bytes_state,
                 "d2h_bytes_per_step": bytes_state},
-        "gpu_launches": launches,
-        "clocks": clocks,
+        "gpu_launches": main["launches"],
+        "clocks": main["clocks"],
     }
+    if mixed and not args.no_compare:
+        # the plain FP64 path on the same GPU, same steps, and the distance between the two states
+        ref = timed_leg(args, case, "fp64", world, dev, sample_clocks=False)
+        wm, wf = main["w"].cpu().numpy(), ref["w"].cpu().numpy()
+        p = case.mesh.nodes[case.mesh.tris]
+        area = 0.5 * np.abs((p[:, 1, 0] - p[:, 0, 0]) * (p[:, 2, 1] - p[:, 0, 1]) -
+                            (p[:, 2, 0] - p[:, 0, 0]) * (p[:, 1, 1] - p[:, 0, 1]))
+        l1 = np.sum(area * np.abs(wm - wf), axis=1) / np.sum(area * np.abs(wf), axis=1)
+        out["fp64"] = {"value": world * T * args.steps / (ref["ms"] / 1e3), "ms_per_step": ref["ms"] / args.steps,
+                       "gmres_iters_per_step": ref["info"]["gmres_iters"] / max(ref["info"]["steps"], 1),
+                       "class_ms": {nm: round(ref["prof"]["ms"][q], 3) for q, nm in enumerate(names)}}
+        out["mixed_vs_fp64_rel_l1"] = [float(x) for x in l1]
+        out["speedup_vs_fp64"] = value / out["fp64"]["value"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_sample(args.cpu_steps)
         cb.pop("seconds", None)
@@ -343,6 +382,8 @@ def main():
     ap.add_argument("--impl", default="gks", choices=["gks", "reference"])
     ap.add_argument("--workload", default="shock_vortex_1m", choices=sorted(WORKLOADS))
     ap.add_argument("--precond", default="sweep", choices=["sweep", "exact"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison leg")
     ap.add_argument("--sweeps", type=int, default=2)
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")

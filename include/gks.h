@@ -99,7 +99,12 @@ typedef struct gks_config {
     int32_t gmres_m;       /* GMRES restart length (<= 64)                             */
     int32_t gmres_maxit;   /* iteration cap per variable and reconstruction            */
     double gmres_rtol;     /* ||b - A x||_2 <= gmres_rtol ||b||_2                       */
-    int32_t precision;     /* GKS_FP64 (only value implemented by this version)       */
+    int32_t precision;     /* GKS_FP64: everything in FP64.  GKS_MIXED: the GMRES
+                              operator and ILU(0) applications in FP32 inside FP64
+                              iterative refinement (FP64 residual, Arnoldi and
+                              Givens); the flux's interface state, collision time,
+                              time integrals and zeroth-order terms in FP64 and its
+                              slope-carrying terms in FP32; FP64 update            */
     int32_t precond;       /* GKS_PC_*                                                 */
     int32_t ilu_sweeps;    /* sweeps per triangular solve for GKS_PC_ILU_SWEEP         */
     int32_t tau2_exact;    /* 0: c4, c5, c6 exactly as printed in Eq. (13);

@@ -58,9 +58,9 @@ gks_status check_config(const gks_config &c)
         set_error("invalid gks_config");
         return GKS_EINVAL;
     }
-    if (c.precision != GKS_FP64) {
-        set_error("gks_config.precision: only GKS_FP64 is implemented");
-        return GKS_EUNSUPPORTED;
+    if (c.precision != GKS_FP64 && c.precision != GKS_MIXED) {
+        set_error("gks_config.precision: GKS_FP64 or GKS_MIXED");
+        return GKS_EINVAL;
     }
     if (c.precond != GKS_PC_ILU_EXACT && c.precond != GKS_PC_ILU_SWEEP) {
         set_error("gks_config.precond: only GKS_PC_ILU_EXACT and GKS_PC_ILU_SWEEP are implemented");

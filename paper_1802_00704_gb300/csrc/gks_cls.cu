@@ -17,6 +17,10 @@ namespace gks {
 namespace {
 
 constexpr int NV = 4, ND = 5, NX = 20;
+// Mixed precision: an inner GMRES cycle (FP32 operator and ILU) stops once its
+// residual estimate has dropped by this factor; the FP64 residual of the next
+// refinement sweep then measures the true error.
+constexpr double kInnerRtol = 1e-6;
 
 // ctl layout: [0..3] active, [4..7] running, [8..11] vectors in cycle, [12..15] iterations
 __device__ __forceinline__ int &ctl_active(int32_t *c, int v) { return c[v]; }
@@ -25,7 +29,8 @@ __device__ __forceinline__ int &ctl_jv(int32_t *c, int v) { return c[8 + v]; }
 __device__ __forceinline__ int &ctl_iters(int32_t *c, int v) { return c[12 + v]; }
 
 // y = O x_j for the gradient entries (g1, g2) of neighbour j
-__device__ __forceinline__ void oapply(double a, double ex, double ey, double g1, double g2, double *o)
+template <typename R>
+__device__ __forceinline__ void oapply(R a, R ex, R ey, R g1, R g2, R *o)
 {
     o[0] = a * g1;
     o[1] = a * g2;
@@ -87,24 +92,28 @@ __global__ void k_rhs(DeviceMesh d, const double *__restrict__ w, double *__rest
 }
 
 // y = K x (mode 0) or y = b - K x with partial sums of |y|^2 and |b|^2 (mode 1).
-// K_ii = D_i (symmetric, 15 stored values), K_ij = -O_ij.
-__global__ void k_spmv(DeviceMesh d, const double *__restrict__ x, double *__restrict__ y, int mode,
-                       const double *__restrict__ b, double *__restrict__ part, int pstride)
+// K_ii = D_i (symmetric, 15 stored values), K_ij = -O_ij.  TX: type of x,
+// TM: type of the operator data and of the arithmetic (mode 1 is FP64 only).
+template <typename TX, typename TM>
+__global__ void k_spmv(DeviceMesh d, const TM *__restrict__ Dg, const TM *__restrict__ alg,
+                       const TM *__restrict__ exg, const TM *__restrict__ eyg, const TX *__restrict__ x,
+                       double *__restrict__ y, int mode, const double *__restrict__ b, double *__restrict__ part,
+                       int pstride)
 {
     __shared__ double sh[32 * NV];
     const int64_t T = d.T;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double nr[NV] = {0, 0, 0, 0}, nb[NV] = {0, 0, 0, 0};
     if (i < T) {
-        double Dm[15];
+        TM Dm[15];
 #pragma unroll
-        for (int q = 0; q < 15; ++q) Dm[q] = d.D[q * T + i];
-        double acc[NX];
+        for (int q = 0; q < 15; ++q) Dm[q] = Dg[q * T + i];
+        TM acc[NX];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            double xv[ND];
+            TM xv[ND];
 #pragma unroll
-            for (int l = 0; l < ND; ++l) xv[l] = x[(v * ND + l) * T + i];
+            for (int l = 0; l < ND; ++l) xv[l] = TM(x[(v * ND + l) * T + i]);
             // symmetric 5x5 times vector
             acc[v * ND + 0] = Dm[0] * xv[0] + Dm[1] * xv[1] + Dm[2] * xv[2] + Dm[3] * xv[3] + Dm[4] * xv[4];
             acc[v * ND + 1] = Dm[1] * xv[0] + Dm[5] * xv[1] + Dm[6] * xv[2] + Dm[7] * xv[3] + Dm[8] * xv[4];
@@ -116,25 +125,25 @@ __global__ void k_spmv(DeviceMesh d, const double *__restrict__ x, double *__res
         for (int s = 0; s < 3; ++s) {
             const int j = d.nb[s * T + i];
             if (j < 0) continue;
-            const double a = d.alpha[s * T + i], ex = d.ex[s * T + i], ey = d.ey[s * T + i];
+            const TM a = alg[s * T + i], ex = exg[s * T + i], ey = eyg[s * T + i];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                double o[ND];
-                oapply(a, ex, ey, x[(v * ND + 0) * T + j], x[(v * ND + 1) * T + j], o);
+                TM o[ND];
+                oapply(a, ex, ey, TM(x[(v * ND + 0) * T + j]), TM(x[(v * ND + 1) * T + j]), o);
 #pragma unroll
                 for (int l = 0; l < ND; ++l) acc[v * ND + l] -= o[l];
             }
         }
         if (mode == 0) {
 #pragma unroll
-            for (int q = 0; q < NX; ++q) y[q * T + i] = acc[q];
+            for (int q = 0; q < NX; ++q) y[q * T + i] = double(acc[q]);
         } else {
 #pragma unroll
             for (int v = 0; v < NV; ++v)
 #pragma unroll
                 for (int l = 0; l < ND; ++l) {
                     const double bv = b[(v * ND + l) * T + i];
-                    const double rv = bv - acc[v * ND + l];
+                    const double rv = bv - double(acc[v * ND + l]);
                     y[(v * ND + l) * T + i] = rv;
                     nr[v] += rv * rv;
                     nb[v] += bv * bv;
@@ -154,67 +163,72 @@ __global__ void k_spmv(DeviceMesh d, const double *__restrict__ x, double *__res
 
 // Forward block-ILU relation for the listed rows (or all rows when rows == nullptr):
 //   z_i = P_i (r_i + sum_{k<i} O_ik zin_k)      (use_nb = 0: z_i = P_i r_i)
-__global__ void k_ilu_fwd(DeviceMesh d, const int32_t *__restrict__ rows, int64_t nrows, const double *r,
-                          const double *zin, double *zout, int use_nb)
+// TR: type of r, TZ: type of z, TM: type of the factors and of the arithmetic.
+template <typename TR, typename TZ, typename TM>
+__global__ void k_ilu_fwd(DeviceMesh d, const TM *__restrict__ Pg, const TM *__restrict__ alg,
+                          const TM *__restrict__ exg, const TM *__restrict__ eyg, const int32_t *__restrict__ rows,
+                          int64_t nrows, const TR *r, const TZ *zin, TZ *zout, int use_nb)
 {
     const int64_t T = d.T;
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= nrows) return;
     const int64_t i = rows ? rows[q] : q;
-    double y[NX];
+    TM y[NX];
 #pragma unroll
-    for (int k = 0; k < NX; ++k) y[k] = r[k * T + i];
+    for (int k = 0; k < NX; ++k) y[k] = TM(r[k * T + i]);
     if (use_nb) {
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
             const int j = d.nb[s * T + i];
             if (j < 0 || j >= i) continue;
-            const double a = d.alpha[s * T + i], ex = d.ex[s * T + i], ey = d.ey[s * T + i];
+            const TM a = alg[s * T + i], ex = exg[s * T + i], ey = eyg[s * T + i];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                double o[ND];
-                oapply(a, ex, ey, zin[(v * ND + 0) * T + j], zin[(v * ND + 1) * T + j], o);
+                TM o[ND];
+                oapply(a, ex, ey, TM(zin[(v * ND + 0) * T + j]), TM(zin[(v * ND + 1) * T + j]), o);
 #pragma unroll
                 for (int l = 0; l < ND; ++l) y[v * ND + l] += o[l];
             }
         }
     }
-    double Pm[25];
+    TM Pm[25];
 #pragma unroll
-    for (int k = 0; k < 25; ++k) Pm[k] = d.P[k * T + i];
+    for (int k = 0; k < 25; ++k) Pm[k] = Pg[k * T + i];
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
         for (int a = 0; a < ND; ++a) {
-            double s = 0.0;
+            TM s = TM(0);
 #pragma unroll
             for (int c = 0; c < ND; ++c) s += Pm[a * ND + c] * y[v * ND + c];
-            zout[(v * ND + a) * T + i] = s;
+            zout[(v * ND + a) * T + i] = TZ(s);
         }
 }
 
 // Backward block-ILU relation: x_i = z_i + P_i sum_{j>i} O_ij xin_j
-__global__ void k_ilu_bwd(DeviceMesh d, const int32_t *__restrict__ rows, int64_t nrows, const double *z,
-                          const double *xin, double *xout)
+template <typename TZ, typename TM>
+__global__ void k_ilu_bwd(DeviceMesh d, const TM *__restrict__ Pg, const TM *__restrict__ alg,
+                          const TM *__restrict__ exg, const TM *__restrict__ eyg, const int32_t *__restrict__ rows,
+                          int64_t nrows, const TZ *z, const TZ *xin, TZ *xout)
 {
     const int64_t T = d.T;
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= nrows) return;
     const int64_t i = rows ? rows[q] : q;
-    double y[NX];
+    TM y[NX];
 #pragma unroll
-    for (int k = 0; k < NX; ++k) y[k] = 0.0;
+    for (int k = 0; k < NX; ++k) y[k] = TM(0);
     bool any = false;
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
         const int j = d.nb[s * T + i];
         if (j <= i) continue;
         any = true;
-        const double a = d.alpha[s * T + i], ex = d.ex[s * T + i], ey = d.ey[s * T + i];
+        const TM a = alg[s * T + i], ex = exg[s * T + i], ey = eyg[s * T + i];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            double o[ND];
-            oapply(a, ex, ey, xin[(v * ND + 0) * T + j], xin[(v * ND + 1) * T + j], o);
+            TM o[ND];
+            oapply(a, ex, ey, TM(xin[(v * ND + 0) * T + j]), TM(xin[(v * ND + 1) * T + j]), o);
 #pragma unroll
             for (int l = 0; l < ND; ++l) y[v * ND + l] += o[l];
         }
@@ -225,17 +239,17 @@ __global__ void k_ilu_bwd(DeviceMesh d, const int32_t *__restrict__ rows, int64_
             for (int k = 0; k < NX; ++k) xout[k * T + i] = z[k * T + i];
         return;
     }
-    double Pm[25];
+    TM Pm[25];
 #pragma unroll
-    for (int k = 0; k < 25; ++k) Pm[k] = d.P[k * T + i];
+    for (int k = 0; k < 25; ++k) Pm[k] = Pg[k * T + i];
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
         for (int a = 0; a < ND; ++a) {
-            double s = z[(v * ND + a) * T + i];
+            TM s = TM(z[(v * ND + a) * T + i]);
 #pragma unroll
             for (int c = 0; c < ND; ++c) s += Pm[a * ND + c] * y[v * ND + c];
-            xout[(v * ND + a) * T + i] = s;
+            xout[(v * ND + a) * T + i] = TZ(s);
         }
 }
 
@@ -349,7 +363,8 @@ __global__ void k_scale(int64_t T, double *__restrict__ vj1, const double *__res
 
 // Givens step of column j for each running variable (one thread per variable).
 __global__ void k_givens(int j, int m, const double *__restrict__ hc, int hstride, double *H, double *cs,
-                         double *sn, double *g, int32_t *ctl, const double *__restrict__ bnorm, double rtol, int maxit)
+                         double *sn, double *g, int32_t *ctl, const double *__restrict__ bnorm,
+                         const double *__restrict__ beta, double rtol, double eta, int maxit)
 {
     const int v = threadIdx.x;
     if (v >= NV || !ctl[4 + v]) return;
@@ -373,7 +388,10 @@ __global__ void k_givens(int j, int m, const double *__restrict__ hc, int hstrid
     g[v * (m + 1) + j] = c * gj;
     ctl[8 + v] = j + 1;
     ctl[12 + v] += 1;
-    if (fabs(g[v * (m + 1) + j + 1]) <= rtol * bnorm[v] || !(hnext > 0.0) || ctl[12 + v] >= maxit || j + 1 == m)
+    // stop the cycle at the target, or (mixed precision, eta > 0) once the inner
+    // residual has dropped by eta: the FP64 refinement residual then restarts it
+    const double gn = fabs(g[v * (m + 1) + j + 1]);
+    if (gn <= rtol * bnorm[v] || gn <= eta * beta[v] || !(hnext > 0.0) || ctl[12 + v] >= maxit || j + 1 == m)
         ctl[4 + v] = 0;
 }
 
@@ -413,7 +431,8 @@ __global__ void k_combine(int64_t T, const double *__restrict__ V, const double 
 }
 
 // x += t for variables that took a cycle (jv > 0)
-__global__ void k_addx(int64_t T, double *__restrict__ x, const double *__restrict__ t, const int32_t *__restrict__ ctl)
+template <typename TT>
+__global__ void k_addx(int64_t T, double *__restrict__ x, const TT *__restrict__ t, const int32_t *__restrict__ ctl)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= T) return;
@@ -421,7 +440,7 @@ __global__ void k_addx(int64_t T, double *__restrict__ x, const double *__restri
     for (int v = 0; v < NV; ++v) {
         if (ctl[8 + v] <= 0) continue;
 #pragma unroll
-        for (int l = 0; l < ND; ++l) x[(v * ND + l) * T + i] += t[(v * ND + l) * T + i];
+        for (int l = 0; l < ND; ++l) x[(v * ND + l) * T + i] += double(t[(v * ND + l) * T + i]);
     }
 }
 
@@ -474,48 +493,67 @@ __global__ void k_zero_trivial(int64_t T, double *__restrict__ x, const double *
 
 inline unsigned nblocks(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
-// dst = M^{-1} src (block ILU(0) on the RCM order)
-gks_status precond(gks_mesh *m, const double *src, double *dst, cudaStream_t s)
+// dst = M^{-1} src (block ILU(0) on the RCM order).  TZ, TM: storage and
+// arithmetic precision of the application; tA, tB: work buffers of type TZ.
+template <typename TZ, typename TM>
+gks_status precond_t(gks_mesh *m, const TM *Pg, const TM *alg, const TM *exg, const TM *eyg, const double *src,
+                     TZ *dst, TZ *tA, TZ *tB, cudaStream_t s)
 {
     DeviceMesh &d = m->d;
-    Work &k = m->wk;
     const int64_t T = d.T;
     if (m->cfg.precond == GKS_PC_ILU_EXACT) {
         const auto &lp = m->lvl_lo_ptr;
         for (size_t l = 0; l + 1 < lp.size(); ++l) {
             const int64_t n = lp[l + 1] - lp[l];
-            k_ilu_fwd<<<nblocks(n), kBlock, 0, s>>>(d, d.lvl_lo + lp[l], n, src, dst, dst, 1); note_launch();
+            k_ilu_fwd<double, TZ, TM><<<nblocks(n), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, d.lvl_lo + lp[l], n, src,
+                                                                     dst, dst, 1);
+            note_launch();
         }
         const auto &up = m->lvl_up_ptr;
         for (size_t l = 0; l + 1 < up.size(); ++l) {
             const int64_t n = up[l + 1] - up[l];
-            k_ilu_bwd<<<nblocks(n), kBlock, 0, s>>>(d, d.lvl_up + up[l], n, dst, dst, dst); note_launch();
+            k_ilu_bwd<TZ, TM><<<nblocks(n), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, d.lvl_up + up[l], n, dst, dst, dst);
+            note_launch();
         }
     } else {
         // sweeps: forward z^0 = P r, z^{q+1} = F(z^q); backward x^0 = z, x^{q+1} = B(x^q)
         const int ns = m->cfg.ilu_sweeps;
-        double *za = (ns % 2 == 0) ? k.t2 : dst;   // buffers chosen so z ends in t2
-        double *zb = (ns % 2 == 0) ? dst : k.t2;
-        k_ilu_fwd<<<nblocks(T), kBlock, 0, s>>>(d, nullptr, T, src, nullptr, za, 0); note_launch();
+        TZ *za = (ns % 2 == 0) ? tA : dst;   // buffers chosen so that z ends in tA
+        TZ *zb = (ns % 2 == 0) ? dst : tA;
+        k_ilu_fwd<double, TZ, TM><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, src, nullptr, za, 0);
+        note_launch();
         for (int q = 0; q < ns; ++q) {
-            k_ilu_fwd<<<nblocks(T), kBlock, 0, s>>>(d, nullptr, T, src, za, zb, 1); note_launch();
+            k_ilu_fwd<double, TZ, TM><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, src, za, zb, 1);
+            note_launch();
             std::swap(za, zb);
         }
-        // now za == t2 holds z
         if (ns == 0) {
-            GKS_CUDA(cudaMemcpyAsync(dst, za, sizeof(double) * NX * T, cudaMemcpyDeviceToDevice, s));
+            GKS_CUDA(cudaMemcpyAsync(dst, za, sizeof(TZ) * NX * T, cudaMemcpyDeviceToDevice, s));
         } else {
-            double *xa = za;                                    // x^0 = z
-            double *xb = (ns % 2 == 1) ? dst : k.t3;
+            TZ *xa = za;                                    // x^0 = z (in tA)
+            TZ *xb = (ns % 2 == 1) ? dst : tB;
             for (int q = 0; q < ns; ++q) {
-                k_ilu_bwd<<<nblocks(T), kBlock, 0, s>>>(d, nullptr, T, za, xa, xb); note_launch();
+                k_ilu_bwd<TZ, TM><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, za, xa, xb);
+                note_launch();
                 xa = xb;
-                xb = (xb == dst) ? k.t3 : dst;
+                xb = (xb == dst) ? tB : dst;
             }
         }
     }
     GKS_CUDA(cudaGetLastError());
     return GKS_OK;
+}
+
+gks_status precond(gks_mesh *m, const double *src, double *dst, cudaStream_t s)
+{
+    DeviceMesh &d = m->d;
+    return precond_t<double, double>(m, d.P, d.alpha, d.ex, d.ey, src, dst, m->wk.t2, m->wk.t3, s);
+}
+
+gks_status precond32(gks_mesh *m, const double *src, float *dst, cudaStream_t s)
+{
+    DeviceMesh &d = m->d;
+    return precond_t<float, float>(m, d.P32, d.alpha32, d.ex32, d.ey32, src, dst, m->wk.t2_32, m->wk.t3_32, s);
 }
 
 gks_status read_ctl(gks_mesh *m, cudaStream_t s)
@@ -542,8 +580,10 @@ gks_status cls_solve(gks_mesh *m, cudaStream_t s, gks_solve_info *info)
     const int64_t vs = (int64_t)NX * T;
     gks_status st;
 
+    const bool mixed = m->cfg.precision == GKS_MIXED;
+    const double eta = mixed ? kInnerRtol : 0.0;
     k_rhs<<<nb, kBlock, 0, s>>>(d, k.w, k.b); note_launch();
-    k_spmv<<<nb, kBlock, 0, s>>>(d, k.x, k.r, 1, k.b, k.part, ps); note_launch();
+    k_spmv<double, double><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, k.r, 1, k.b, k.part, ps); note_launch();
     k_reduce<<<dim3(2, NV), kBlock, 0, s>>>(k.part, k.nblk, ps, k.hcol, ps, 0); note_launch();
     k_start<<<1, 32, 0, s>>>(k.hcol, ps, k.bnorm, k.beta, k.ctl, rtol, maxit, 1); note_launch();
     k_zero_trivial<<<nb, kBlock, 0, s>>>(T, k.x, k.bnorm); note_launch();
@@ -555,10 +595,16 @@ gks_status cls_solve(gks_mesh *m, cudaStream_t s, gks_solve_info *info)
         for (int j = 0; j < mm; ++j) {
             double *vj = k.V + j * vs, *vj1 = k.V + (j + 1) * vs;
             int slot = prof_start(m, kProfIlu, s);
-            if ((st = precond(m, vj, k.t, s)) != GKS_OK) return st;
+            if ((st = mixed ? precond32(m, vj, k.t32, s) : precond(m, vj, k.t, s)) != GKS_OK) return st;
             prof_stop(m, slot, s);
             slot = prof_start(m, kProfSpmv, s);
-            k_spmv<<<nb, kBlock, 0, s>>>(d, k.t, vj1, 0, nullptr, nullptr, 0); note_launch();
+            if (mixed)
+                k_spmv<float, float><<<nb, kBlock, 0, s>>>(d, d.D32, d.alpha32, d.ex32, d.ey32, k.t32, vj1, 0, nullptr,
+                                                           nullptr, 0);
+            else
+                k_spmv<double, double><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.t, vj1, 0, nullptr, nullptr,
+                                                             0);
+            note_launch();
             prof_stop(m, slot, s);
             slot = prof_start(m, kProfOrth, s);
             // classical Gram-Schmidt, twice
@@ -572,16 +618,24 @@ gks_status cls_solve(gks_mesh *m, cudaStream_t s, gks_solve_info *info)
             k_hadd<<<1, 128, 0, s>>>(k.hcol, ps, k.y, mm, j); note_launch();
             prof_stop(m, slot, s);
             k_scale<<<nb, kBlock, 0, s>>>(T, vj1, k.hcol, ps, j, k.ctl); note_launch();
-            k_givens<<<1, 32, 0, s>>>(j, mm, k.hcol, ps, k.H, k.cs, k.sn, k.g, k.ctl, k.bnorm, rtol, maxit); note_launch();
+            k_givens<<<1, 32, 0, s>>>(j, mm, k.hcol, ps, k.H, k.cs, k.sn, k.g, k.ctl, k.bnorm, k.beta, rtol, eta, maxit);
+            note_launch();
             GKS_CUDA(cudaGetLastError());
             if ((st = read_ctl(m, s)) != GKS_OK) return st;
             if (!(k.h_ctl[4] | k.h_ctl[5] | k.h_ctl[6] | k.h_ctl[7])) break;
         }
         k_backsolve<<<1, 32, 0, s>>>(mm, k.H, k.g, k.y, k.ctl); note_launch();
         k_combine<<<nb, kBlock, 0, s>>>(T, k.V, k.y, mm, k.ctl, k.r); note_launch();
-        if ((st = precond(m, k.r, k.t, s)) != GKS_OK) return st;
-        k_addx<<<nb, kBlock, 0, s>>>(T, k.x, k.t, k.ctl); note_launch();
-        k_spmv<<<nb, kBlock, 0, s>>>(d, k.x, k.r, 1, k.b, k.part, ps); note_launch();
+        if (mixed) {
+            if ((st = precond32(m, k.r, k.t32, s)) != GKS_OK) return st;
+            k_addx<float><<<nb, kBlock, 0, s>>>(T, k.x, k.t32, k.ctl);
+        } else {
+            if ((st = precond(m, k.r, k.t, s)) != GKS_OK) return st;
+            k_addx<double><<<nb, kBlock, 0, s>>>(T, k.x, k.t, k.ctl);
+        }
+        note_launch();
+        k_spmv<double, double><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, k.r, 1, k.b, k.part, ps);
+        note_launch();
         k_reduce<<<dim3(2, NV), kBlock, 0, s>>>(k.part, k.nblk, ps, k.hcol, ps, 0); note_launch();
         k_start<<<1, 32, 0, s>>>(k.hcol, ps, k.bnorm, k.beta, k.ctl, rtol, maxit, 0); note_launch();
         GKS_CUDA(cudaGetLastError());

@@ -102,6 +102,8 @@ __device__ __forceinline__ void ghost(int tag, const double *bc, double nx, doub
     }
 }
 
+// MIXED: interface state and leading terms in FP64, slope-carrying terms in FP32.
+template <bool MIXED>
 __global__ void __launch_bounds__(kFluxBlock) k_face_flux(DeviceMesh d, const double *__restrict__ w,
                                                           const double *__restrict__ x, double dt_const,
                                                           const double *__restrict__ dt_dev, double gamma, double mu,
@@ -128,7 +130,9 @@ __global__ void __launch_bounds__(kFluxBlock) k_face_flux(DeviceMesh d, const do
             ghost(d.ftag[f], bc, nx, ny, gamma, wl, wr);
         }
         double fk[4];
-        if (!kin::gp_flux<double>(wl, wr, dt, gamma, mu, tau2, fk)) atomicOr(status, kStatusNonPhys);
+        const bool ok = MIXED ? kin::gp_flux_mixed(wl, wr, dt, gamma, mu, tau2, fk)
+                              : kin::gp_flux<double>(wl, wr, dt, gamma, mu, tau2, fk);
+        if (!ok) atomicOr(status, kStatusNonPhys);
         const double s = 0.5 * d.flen[f];      // Gauss weight 1/2 times the face length
         out[0] = s * fk[0];
         out[1] = s * (nx * fk[1] - ny * fk[2]);
@@ -209,6 +213,7 @@ __global__ void k_min_final(const double *__restrict__ part, int n, double scale
     if (threadIdx.x == 0) *out = scale * sh[0];
 }
 
+template <bool MIXED>
 __global__ void __launch_bounds__(kFluxBlock) k_point_flux(int64_t n, const double *__restrict__ wl,
                                                            const double *__restrict__ wr, double dt, double gamma,
                                                            double mu, int tau2, double *__restrict__ out,
@@ -222,7 +227,8 @@ __global__ void __launch_bounds__(kFluxBlock) k_point_flux(int64_t n, const doub
         a[k] = wl[24 * q + k];
         b[k] = wr[24 * q + k];
     }
-    if (!kin::gp_flux<double>(a, b, dt, gamma, mu, tau2, f) && status) atomicOr(status, kStatusNonPhys);
+    const bool ok = MIXED ? kin::gp_flux_mixed(a, b, dt, gamma, mu, tau2, f) : kin::gp_flux<double>(a, b, dt, gamma, mu, tau2, f);
+    if (!ok && status) atomicOr(status, kStatusNonPhys);
 #pragma unroll
     for (int k = 0; k < 4; ++k) out[4 * q + k] = f[k];
 }
@@ -289,8 +295,16 @@ gks_status launch_flux(gks_mesh *m, const double *w, const double *x, double dt_
 {
     const int64_t npts = 2 * m->d.F;
     const int slot = prof_start(m, kProfFlux, s);
-    k_face_flux<<<blocks(npts, kFluxBlock), kFluxBlock, 0, s>>>(m->d, w, x, dt_const, dt_dev, m->cfg.gamma, m->cfg.mu,
-                                                                m->cfg.tau2_exact, flux, m->wk.status); note_launch();
+    if (m->cfg.precision == GKS_MIXED) {
+        k_face_flux<true><<<blocks(npts, kFluxBlock), kFluxBlock, 0, s>>>(m->d, w, x, dt_const, dt_dev, m->cfg.gamma,
+                                                                          m->cfg.mu, m->cfg.tau2_exact, flux,
+                                                                          m->wk.status);
+    } else {
+        k_face_flux<false><<<blocks(npts, kFluxBlock), kFluxBlock, 0, s>>>(m->d, w, x, dt_const, dt_dev, m->cfg.gamma,
+                                                                           m->cfg.mu, m->cfg.tau2_exact, flux,
+                                                                           m->wk.status);
+    }
+    note_launch();
     prof_stop(m, slot, s);
     GKS_CUDA(cudaGetLastError());
     return GKS_OK;
@@ -318,8 +332,13 @@ gks_status launch_point_flux(int64_t n, const double *wl, const double *wr, doub
                              double *out, int32_t *status, cudaStream_t s)
 {
     if (n <= 0) return GKS_OK;
-    k_point_flux<<<blocks(n, kFluxBlock), kFluxBlock, 0, s>>>(n, wl, wr, dt, cfg.gamma, cfg.mu, cfg.tau2_exact, out,
-                                                              status); note_launch();
+    if (cfg.precision == GKS_MIXED)
+        k_point_flux<true><<<blocks(n, kFluxBlock), kFluxBlock, 0, s>>>(n, wl, wr, dt, cfg.gamma, cfg.mu, cfg.tau2_exact,
+                                                                         out, status);
+    else
+        k_point_flux<false><<<blocks(n, kFluxBlock), kFluxBlock, 0, s>>>(n, wl, wr, dt, cfg.gamma, cfg.mu,
+                                                                          cfg.tau2_exact, out, status);
+    note_launch();
     GKS_CUDA(cudaGetLastError());
     return GKS_OK;
 }

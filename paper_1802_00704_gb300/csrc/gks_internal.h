@@ -49,6 +49,8 @@ struct DeviceMesh {
     double *a0 = nullptr;            // [3][5][T] weighted row 0 of A_ij (right-hand side)
     double *D = nullptr;             // [15][T] symmetric diagonal block, upper triangle row-major
     double *P = nullptr;             // [25][T] inverse of the ILU(0) diagonal block, row-major
+    // FP32 copies of the operator and factors (mixed precision)
+    float *D32 = nullptr, *P32 = nullptr, *alpha32 = nullptr, *ex32 = nullptr, *ey32 = nullptr;
     int32_t *cf = nullptr;           // [3][T] (face << 1) | side, -1 unused
     int32_t *perm = nullptr;         // [T] internal -> caller cell
     int32_t *lvl_lo = nullptr;       // [T] rows sorted by forward level
@@ -69,6 +71,7 @@ struct Work {
     double *w_old = nullptr;         // [4][T]
     double *x = nullptr;             // [20][T] CLS coefficients (warm start)
     double *b = nullptr, *r = nullptr, *t = nullptr, *t2 = nullptr, *t3 = nullptr;  // [20][T]
+    float *t32 = nullptr, *t2_32 = nullptr, *t3_32 = nullptr;  // [20][T] FP32 preconditioner work
     double *V = nullptr;             // [(m+1)][20][T]
     double *flux = nullptr;          // [4][F]
     double *part = nullptr;          // [nblk][4][m+2] partial sums

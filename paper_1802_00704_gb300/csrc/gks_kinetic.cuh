@@ -365,74 +365,185 @@ __device__ __forceinline__ void time_integrals(R dt, R tau, int tau2_exact, R *C
     }
 }
 
-// Time-integrated flux through a unit-length face at one Gauss point.
-// wl, wr: [6][4] face-frame rows (value, d/dn, d/dt, d2/dn2, d2/dndt, d2/dt2).
-// Returns false if a state is not physical (f is then zero).
+// Interface data of one Gauss point: primitive left/right states, the
+// interface equilibrium W0 = rho_l <psi>_{u>0} + rho_r <psi>_{u<0} with the
+// mean of the left/right derivatives, its primitive state, the collision time
+// (Eqs. (39)-(40), pressure-jump term scaled by dt) and the time integrals.
 template <typename R>
-__device__ __forceinline__ bool gp_flux(const R *wl, const R *wr, R dt, R gamma, R mu, int tau2_exact, R *f)
+struct Iface {
+    KState<R> L, Rs, Z;
+    R w0[24];
+    R tau;
+    R C[9];
+};
+
+template <typename R>
+__device__ __forceinline__ bool interface_state(const R *wl, const R *wr, R dt, R gamma, R mu, int tau2_exact,
+                                                Iface<R> &I)
 {
     const R K = R(2) / (gamma - R(1)) - R(2);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) f[q] = R(0);
-    KState<R> L, Rs, Z;
-    bool ok = prim(wl, gamma, K, L) & prim(wr, gamma, K, Rs);
+    bool ok = prim(wl, gamma, K, I.L) & prim(wr, gamma, K, I.Rs);
     if (!ok) return false;
-    // interface equilibrium W0 = rho_l <psi>_{u>0} + rho_r <psi>_{u<0}
-    R w0[24];
     {
         R ml[10], mr[10], mvl[10], mvr[10], zl[4], zr[4];
-        mom_half(L.U, L.lam, R(1), ml);
-        mom_half(Rs.U, Rs.lam, R(-1), mr);
-        mom_full(L.V, L.lam, mvl);
-        mom_full(Rs.V, Rs.lam, mvr);
-        mom_xi(L.lam, K, zl);
-        mom_xi(Rs.lam, K, zr);
-        w0[0] = L.rho * ml[0] + Rs.rho * mr[0];
-        w0[1] = L.rho * ml[1] + Rs.rho * mr[1];
-        w0[2] = L.rho * ml[0] * mvl[1] + Rs.rho * mr[0] * mvr[1];
-        w0[3] = L.rho * R(0.5) * (ml[2] + ml[0] * mvl[2] + ml[0] * zl[1]) +
-                Rs.rho * R(0.5) * (mr[2] + mr[0] * mvr[2] + mr[0] * zr[1]);
+        mom_half(I.L.U, I.L.lam, R(1), ml);
+        mom_half(I.Rs.U, I.Rs.lam, R(-1), mr);
+        mom_full(I.L.V, I.L.lam, mvl);
+        mom_full(I.Rs.V, I.Rs.lam, mvr);
+        mom_xi(I.L.lam, K, zl);
+        mom_xi(I.Rs.lam, K, zr);
+        I.w0[0] = I.L.rho * ml[0] + I.Rs.rho * mr[0];
+        I.w0[1] = I.L.rho * ml[1] + I.Rs.rho * mr[1];
+        I.w0[2] = I.L.rho * ml[0] * mvl[1] + I.Rs.rho * mr[0] * mvr[1];
+        I.w0[3] = I.L.rho * R(0.5) * (ml[2] + ml[0] * mvl[2] + ml[0] * zl[1]) +
+                  I.Rs.rho * R(0.5) * (mr[2] + mr[0] * mvr[2] + mr[0] * zr[1]);
 #pragma unroll
-        for (int q = 4; q < 24; ++q) w0[q] = R(0.5) * (wl[q] + wr[q]);
+        for (int q = 4; q < 24; ++q) I.w0[q] = R(0.5) * (wl[q] + wr[q]);
     }
-    if (!prim(w0, gamma, K, Z)) return false;
-    // collision time, Eqs. (39)-(40), pressure-jump term scaled by dt
-    const R jump = fabs(L.p - Rs.p) / fabs(L.p + Rs.p);
-    const R tau = mu > R(0) ? mu / Z.p + dt * jump : R(0.01) * dt + dt * jump;
-    R C[9];
-    time_integrals(dt, tau, tau2_exact, C);
+    if (!prim(I.w0, gamma, K, I.Z)) return false;
+    const R jump = fabs(I.L.p - I.Rs.p) / fabs(I.L.p + I.Rs.p);
+    I.tau = mu > R(0) ? mu / I.Z.p + dt * jump : R(0.01) * dt + dt * jump;
+    time_integrals(dt, I.tau, tau2_exact, I.C);
+    return true;
+}
+
+// Flux terms of Eqs. (11) and (15) at y = 0, from the slopes of the three
+// states.  with_const = false leaves out the zeroth-order terms C1 g0 and
+// C7 g_k (see lead_flux).
+template <typename R>
+__device__ __forceinline__ void body_flux(const R *wl, const R *wr, Iface<R> &I, R gamma, bool with_const, R *f)
+{
+    const R K = R(2) / (gamma - R(1)) - R(2);
+    const R tau = I.tau;
+    const R *C = I.C;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) f[q] = R(0);
     R out[4];
     Poly<R> Q;
     Mom<R> m;
-    // equilibrium part, Eq. (15) at y = 0
-    mom_full(Z.U, Z.lam, m.u);
-    mom_full(Z.V, Z.lam, m.v);
-    mom_xi(Z.lam, K, m.z);
-    slopes(Z, w0, K, m, true);
-    build_q(Q, Z, C[0], C[2], C[1], R(0.5) * C[3], C[5], R(0.5) * C[4]);
+    // equilibrium part, Eq. (15)
+    mom_full(I.Z.U, I.Z.lam, m.u);
+    mom_full(I.Z.V, I.Z.lam, m.v);
+    mom_xi(I.Z.lam, K, m.z);
+    slopes(I.Z, I.w0, K, m, true);
+    build_q(Q, I.Z, with_const ? C[0] : R(0), C[2], C[1], R(0.5) * C[3], C[5], R(0.5) * C[4]);
     upsi_contract(Q, m, out);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) f[q] += Z.rho * out[q];
-    // non-equilibrium part, Eq. (11) at y = 0, left (u > 0) and right (u < 0)
+    for (int q = 0; q < 4; ++q) f[q] += I.Z.rho * out[q];
+    // non-equilibrium part, Eq. (11), left (u > 0) and right (u < 0)
     const R kA = -tau * C[6], kL = C[7] - tau * C[6], kS = R(0.5) * C[8] - tau * C[7], kAL = -tau * C[7];
-    mom_full(L.U, L.lam, m.u);
-    mom_full(L.V, L.lam, m.v);
-    mom_xi(L.lam, K, m.z);
-    slopes(L, wl, K, m, false);
-    build_q(Q, L, C[6], kA, kL, kS, kAL, R(0));
-    mom_half(L.U, L.lam, R(1), m.u);
+    const R k7 = with_const ? C[6] : R(0);
+    mom_full(I.L.U, I.L.lam, m.u);
+    mom_full(I.L.V, I.L.lam, m.v);
+    mom_xi(I.L.lam, K, m.z);
+    slopes(I.L, wl, K, m, false);
+    build_q(Q, I.L, k7, kA, kL, kS, kAL, R(0));
+    mom_half(I.L.U, I.L.lam, R(1), m.u);
     upsi_contract(Q, m, out);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) f[q] += L.rho * out[q];
-    mom_full(Rs.U, Rs.lam, m.u);
-    mom_full(Rs.V, Rs.lam, m.v);
-    mom_xi(Rs.lam, K, m.z);
-    slopes(Rs, wr, K, m, false);
-    build_q(Q, Rs, C[6], kA, kL, kS, kAL, R(0));
-    mom_half(Rs.U, Rs.lam, R(-1), m.u);
+    for (int q = 0; q < 4; ++q) f[q] += I.L.rho * out[q];
+    mom_full(I.Rs.U, I.Rs.lam, m.u);
+    mom_full(I.Rs.V, I.Rs.lam, m.v);
+    mom_xi(I.Rs.lam, K, m.z);
+    slopes(I.Rs, wr, K, m, false);
+    build_q(Q, I.Rs, k7, kA, kL, kS, kAL, R(0));
+    mom_half(I.Rs.U, I.Rs.lam, R(-1), m.u);
     upsi_contract(Q, m, out);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) f[q] += Rs.rho * out[q];
+    for (int q = 0; q < 4; ++q) f[q] += I.Rs.rho * out[q];
+}
+
+// Zeroth-order (leading) terms: C1 rho0 <u psi>_0 + C7 (rho_l <u psi>_{u>0,l} +
+// rho_r <u psi>_{u<0,r}); all other terms carry a slope and are smaller by a
+// factor of order dt |grad W| / |W|.
+template <typename R>
+__device__ __forceinline__ void lead_flux(const Iface<R> &I, R gamma, R *f)
+{
+    const R K = R(2) / (gamma - R(1)) - R(2);
+    R mu[4], mv[3], mz[2];
+    // equilibrium: <u psi> of the full Maxwellian of W0
+    {
+        const R h = R(0.5) / I.Z.lam;
+        mu[0] = R(1); mu[1] = I.Z.U; mu[2] = I.Z.U * mu[1] + h; mu[3] = I.Z.U * mu[2] + R(2) * h * mu[1];
+        mv[0] = R(1); mv[1] = I.Z.V; mv[2] = I.Z.V * I.Z.V + h;
+        mz[1] = R(0.5) * K / I.Z.lam;
+        const R s = I.C[0] * I.Z.rho;
+        f[0] = s * mu[1];
+        f[1] = s * mu[2];
+        f[2] = s * mu[1] * mv[1];
+        f[3] = s * R(0.5) * (mu[3] + mu[1] * mv[2] + mu[1] * mz[1]);
+    }
+    const KState<R> *S[2] = {&I.L, &I.Rs};
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const KState<R> &k = *S[side];
+        R m[10];
+        mom_half(k.U, k.lam, side == 0 ? R(1) : R(-1), m);
+        const R h = R(0.5) / k.lam;
+        const R v2 = k.V * k.V + h, z1 = R(0.5) * K / k.lam;
+        const R s = I.C[6] * k.rho;
+        f[0] += s * m[1];
+        f[1] += s * m[2];
+        f[2] += s * m[1] * k.V;
+        f[3] += s * R(0.5) * (m[3] + m[1] * v2 + m[1] * z1);
+    }
+}
+
+// Time-integrated flux through a unit-length face at one Gauss point, all in
+// precision R.  wl, wr: [6][4] face-frame rows (value, d/dn, d/dt, d2/dn2,
+// d2/dndt, d2/dt2).  Returns false if a state is not physical (f is zero).
+template <typename R>
+__device__ __forceinline__ bool gp_flux(const R *wl, const R *wr, R dt, R gamma, R mu, int tau2_exact, R *f)
+{
+    Iface<R> I;
+    if (!interface_state(wl, wr, dt, gamma, mu, tau2_exact, I)) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) f[q] = R(0);
+        return false;
+    }
+    body_flux(wl, wr, I, gamma, true, f);
+    return true;
+}
+
+template <typename A, typename B>
+__device__ __forceinline__ void kstate_cast(const KState<A> &a, KState<B> &b)
+{
+    b.rho = B(a.rho);
+    b.U = B(a.U);
+    b.V = B(a.V);
+    b.lam = B(a.lam);
+    b.p = B(a.p);
+}
+
+// Mixed precision: interface state, collision time, time integrals and the
+// leading terms in FP64; every slope-carrying term in FP32.
+__device__ __forceinline__ bool gp_flux_mixed(const double *wl, const double *wr, double dt, double gamma, double mu,
+                                              int tau2_exact, double *f)
+{
+    Iface<double> I;
+    if (!interface_state(wl, wr, dt, gamma, mu, tau2_exact, I)) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) f[q] = 0.0;
+        return false;
+    }
+    lead_flux(I, gamma, f);
+    Iface<float> J;
+    kstate_cast(I.L, J.L);
+    kstate_cast(I.Rs, J.Rs);
+    kstate_cast(I.Z, J.Z);
+    J.tau = float(I.tau);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) J.C[q] = float(I.C[q]);
+    float fl[24], fr[24], g[4];
+#pragma unroll
+    for (int q = 0; q < 24; ++q) {
+        J.w0[q] = float(I.w0[q]);
+        fl[q] = float(wl[q]);
+        fr[q] = float(wr[q]);
+    }
+    body_flux(fl, fr, J, float(gamma), false, g);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) f[q] += double(g[q]);
     return true;
 }
 

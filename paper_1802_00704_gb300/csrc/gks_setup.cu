@@ -483,6 +483,10 @@ gks_status build_mesh(gks_mesh *m, const double *nodes, int64_t n_nodes, const i
     UP(D, h_D); UP(P, h_P); UP(cf, h_cf); UP(perm, perm); UP(lvl_lo, rows_lo); UP(lvl_up, rows_up);
     UP(fl, h_fl); UP(fr, h_fr); UP(ftag, h_ftag); UP(fperm, h_fperm); UP(fnx, h_fnx); UP(fny, h_fny);
     UP(flen, h_flen); UP(gl, h_gl); UP(gr, h_gr); UP(bc, h_bc);
+    if (cfg.precision == GKS_MIXED) {
+        auto f32 = [](const std::vector<double> &v) { return std::vector<float>(v.begin(), v.end()); };
+        UP(D32, f32(h_D)); UP(P32, f32(h_P)); UP(alpha32, f32(h_alpha)); UP(ex32, f32(h_ex)); UP(ey32, f32(h_ey));
+    }
 #undef UP
 
     // ---- work buffers
@@ -494,6 +498,9 @@ gks_status build_mesh(gks_mesh *m, const double *nodes, int64_t n_nodes, const i
     if ((st = dalloc(m, &k.ptr, (size_t)(n))) != GKS_OK) return st
     AL(w, 4 * T); AL(w_old, 4 * T); AL(x, 20 * T); AL(b, 20 * T); AL(r, 20 * T); AL(t, 20 * T); AL(t2, 20 * T); AL(t3, 20 * T);
     AL(V, (size_t)(mm + 1) * 20 * T); AL(flux, 4 * F);
+    if (cfg.precision == GKS_MIXED) {
+        AL(t32, 20 * T); AL(t2_32, 20 * T); AL(t3_32, 20 * T);
+    }
     AL(part, (size_t)k.nblk * 4 * (mm + 2)); AL(dpart, (size_t)std::max<int64_t>(k.nblk, (F + kBlock - 1) / kBlock) * 4);
     AL(H, 4 * (mm + 1) * mm); AL(cs, 4 * mm); AL(sn, 4 * mm); AL(g, 4 * (mm + 1)); AL(y, 4 * mm);
     AL(hcol, 4 * (mm + 2)); AL(bnorm, 4); AL(beta, 4); AL(ctl, 16); AL(dt, 1); AL(scal, 8); AL(status, 1);

@@ -94,7 +94,10 @@ def test_invalid_inputs_are_rejected(G):
     with pytest.raises(G.GksError):
         G.GksMesh(I.Mesh(c.mesh.nodes, c.mesh.tris, bad, c.mesh.face_shift, c.mesh.bc_state))
     with pytest.raises(G.GksError) as e:
-        G.GksMesh(c.mesh, precision=G.MIXED)
+        G.GksMesh(c.mesh, precision=7)
+    assert e.value.status == G.GKS_EINVAL
+    with pytest.raises(G.GksError) as e:
+        G.GksMesh(c.mesh, precond=G.PC_BJACOBI)
     assert e.value.status == G.GKS_EUNSUPPORTED
     with pytest.raises(G.GksError) as e:
         G.GksMesh(c.mesh, gmres_m=0)
