@@ -146,7 +146,27 @@ typedef struct gks_mesh_stats {
     int32_t levels_upper;  /* ... and of the backward solve                             */
     int64_t rcm_bandwidth; /* max |i - j| over neighbouring cells in RCM order          */
     int64_t device_bytes;  /* device memory held by the handle                          */
+    int32_t n_case;        /* independent cases held by the handle (1 for a mesh)        */
 } gks_mesh_stats;
+
+/* One independent case of a batch: the same arrays as gks_mesh_create. */
+typedef struct gks_case_desc {
+    const double *nodes;
+    int64_t n_nodes;
+    const int32_t *tris;
+    int64_t n_tri;
+    const int32_t *faces;
+    const double *face_shift;
+    int64_t n_face;
+    const double *bc_state;
+} gks_case_desc;
+
+typedef struct gks_batch_info {
+    int64_t steps;         /* steps taken (the step loop of the whole batch)           */
+    int64_t gmres_iters;   /* GMRES iterations summed over cases and variables         */
+    int32_t n_failed;      /* cases stopped by GKS_ENONPHYS or GKS_ENOCONV             */
+    int32_t n_finished;    /* cases that reached their t_final                          */
+} gks_batch_info;
 
 /* Fill *cfg with defaults: gamma 1.4, cfl 0.3, mu 0, cls_w 0.3, gmres_m 30,
  * gmres_maxit 1000, gmres_rtol 1e-12, FP64, GKS_PC_ILU_SWEEP with 2 sweeps,
@@ -172,6 +192,26 @@ GKS_EXPORT gks_status gks_mesh_create(const double *nodes, int64_t n_nodes, cons
                            const int32_t *faces, const double *face_shift, int64_t n_face,
                            const double *bc_state, const gks_config *cfg, gks_mesh **out);
 
+/* Build one handle holding n_cases independent meshes (each described as in
+ * gks_mesh_create) that advance together: every kernel launch covers all
+ * cases, and each case keeps its own time step, GMRES convergence masks and
+ * status.  State arrays of a batch are float64 [4][sum of n_tri] (and
+ * coefficients [4][5][sum of n_tri], face fluxes [4][sum of n_face]) with the
+ * cases' cells (faces) concatenated in case order.  Errors as gks_mesh_create;
+ * the message names the failing case. */
+GKS_EXPORT gks_status gks_batch_create(const gks_case_desc *cases, int32_t n_cases, const gks_config *cfg,
+                                       gks_mesh **out);
+
+/* Advance every case of a batch handle (or a single mesh) with its own CFL
+ * step until its t_final (host [n_cases]; NULL or <= 0: no limit; the last step
+ * is cut to land on it) or max_steps steps of the batch.  A case whose state
+ * goes non-physical or whose GMRES hits gmres_maxit stops; the others go on.
+ * w: device [4][sum n_tri].  t_reached, case_status (GKS_OK, GKS_ENONPHYS,
+ * GKS_ENOCONV): host [n_cases], may be NULL.  Returns GKS_OK unless an argument
+ * or CUDA error occurs.  Synchronises the stream once per step. */
+GKS_EXPORT gks_status gks_batch_run(gks_mesh *batch, double *w, const double *t_final, int64_t max_steps,
+                                    double *t_reached, int32_t *case_status, gks_batch_info *info, void *stream);
+
 /* Free every device and host resource of the handle (NULL is accepted). */
 GKS_EXPORT gks_status gks_mesh_destroy(gks_mesh *mesh);
 
@@ -182,6 +222,7 @@ GKS_EXPORT gks_status gks_mesh_get_stats(const gks_mesh *mesh, gks_mesh_stats *s
  * inradius of cell i (the paper does not state its CFL rule).
  * w: device [4][n_tri].  *dt_out: host.  Synchronises the stream. */
 GKS_EXPORT gks_status gks_cfl_dt(gks_mesh *mesh, const double *w, double *dt_out, void *stream);
+/* (gks_cfl_dt, gks_step and gks_run take single-mesh handles; GKS_EINVAL for a batch.) */
 
 /* Same time step as gks_cfl_dt, for callers that cannot allocate device
  * memory when they need it: code running while a stream is captured into a
@@ -194,7 +235,8 @@ GKS_EXPORT gks_status gks_cfl_dt(gks_mesh *mesh, const double *w, double *dt_out
  *          copied to the host and the stream is not synchronised.
  * The call allocates nothing: the block minima of its reduction live in a
  * 128 KiB static device array of the library, held by every GPU that loads
- * it until exit, which limits meshes to 4,194,304 cells (GKS_EINVAL above).
+ * it until exit, which limits meshes to 4,194,304 cells (GKS_EINVAL above, and
+ * for batch handles).
  * The first call on each device looks up that array's device address; make
  * it before any stream capture.  All calls share the array, so calls that
  * overlap on the GPU (two streams, or two handles on one device) race; each

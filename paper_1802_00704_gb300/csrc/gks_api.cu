@@ -1,5 +1,7 @@
 // C ABI entry points (include/gks.h).
+#include <algorithm>
 #include <cmath>
+#include <vector>
 #include <cstring>
 #include <new>
 
@@ -71,13 +73,22 @@ gks_status check_config(const gks_config &c)
 
 gks_status read_status(gks_mesh *m, cudaStream_t s, int32_t *out)
 {
-    GKS_CUDA(cudaMemcpyAsync(m->wk.h_ctl + 16, m->wk.status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    GKS_CUDA(cudaMemcpyAsync(m->wk.h_flags + 2, m->wk.status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     GKS_CUDA(cudaStreamSynchronize(s));
-    *out = m->wk.h_ctl[16];
+    *out = m->wk.h_flags[2];
     return GKS_OK;
 }
 
-// one step on the internal state m->wk.w; dt_fixed > 0 fixes the step
+gks_status require_single(const gks_mesh *m, const char *who)
+{
+    if (m->n_case != 1) {
+        set_error("%s: the handle holds %d cases; use gks_batch_run", who, m->n_case);
+        return GKS_EINVAL;
+    }
+    return GKS_OK;
+}
+
+// one step of a single-case handle on the internal state m->wk.w; dt_fixed > 0 fixes the step
 gks_status step_internal(gks_mesh *m, double dt_fixed, cudaStream_t s, gks_step_info *info, double *dt_taken)
 {
     gks_status st;
@@ -88,8 +99,9 @@ gks_status step_internal(gks_mesh *m, double dt_fixed, cudaStream_t s, gks_step_
     } else if ((st = launch_cfl_dt(m, k.w, k.dt, s)) != GKS_OK) {
         return st;
     }
-    gks_solve_info si;
-    if ((st = cls_solve(m, s, &si)) != GKS_OK) return st;
+    int32_t iters[4], conv = 1;
+    double relres[4];
+    if ((st = cls_solve(m, s, iters, relres, &conv)) != GKS_OK) return st;
     if ((st = launch_flux(m, k.w, k.x, 0.0, k.dt, k.flux, s)) != GKS_OK) return st;
     if ((st = launch_update(m, k.w, k.flux, s)) != GKS_OK) return st;
     GKS_CUDA(cudaMemcpyAsync(&k.h_scal[6], k.dt, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -97,19 +109,49 @@ gks_status step_internal(gks_mesh *m, double dt_fixed, cudaStream_t s, gks_step_
     if ((st = read_status(m, s, &stat)) != GKS_OK) return st;
     if (dt_taken) *dt_taken = k.h_scal[6];
     gks_status res = GKS_OK;
-    if (!si.converged) res = GKS_ENOCONV;
+    if (!conv) res = GKS_ENOCONV;
     if (stat & kStatusNonPhys) res = GKS_ENONPHYS;
     if (info) {
         info->dt = k.h_scal[6];
         for (int v = 0; v < 4; ++v) {
-            info->iters[v] = si.iters[v];
-            info->relres[v] = si.relres[v];
+            info->iters[v] = iters[v];
+            info->relres[v] = relres[v];
         }
         info->status = res;
     }
     if (res == GKS_ENOCONV) set_error("GMRES did not reach gmres_rtol within gmres_maxit");
     if (res == GKS_ENONPHYS) set_error("non-physical state (rho <= 0 or p <= 0)");
     return res;
+}
+
+gks_status create(const CaseIn *cases, int32_t n, const gks_config *cfg, gks_mesh **out)
+{
+    set_error("");
+    if (!out) {
+        set_error("gks_mesh_create: out is NULL");
+        return GKS_EINVAL;
+    }
+    *out = nullptr;
+    gks_mesh *m = new (std::nothrow) gks_mesh();
+    if (!m) {
+        set_error("gks_mesh_create: host allocation failed");
+        return GKS_ENOMEM;
+    }
+    if (cfg) m->cfg = *cfg;
+    else gks_config_default(&m->cfg);
+    gks_status st = check_config(m->cfg);
+    if (st == GKS_OK && cudaGetDevice(&m->device) != cudaSuccess) {
+        set_error("gks_mesh_create: no CUDA device");
+        st = GKS_ECUDA;
+    }
+    if (st == GKS_OK) st = build_batch(m, cases, n);
+    if (st != GKS_OK) {
+        free_mesh(m);
+        delete m;
+        return st;
+    }
+    *out = m;
+    return GKS_OK;
 }
 
 }  // namespace
@@ -139,32 +181,22 @@ gks_status gks_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *
                            const int32_t *faces, const double *face_shift, int64_t n_face, const double *bc_state,
                            const gks_config *cfg, gks_mesh **out)
 {
-    set_error("");
-    if (!out) {
-        set_error("gks_mesh_create: out is NULL");
+    const CaseIn c{nodes, n_nodes, tris, n_tri, faces, face_shift, n_face, bc_state};
+    return create(&c, 1, cfg, out);
+}
+
+gks_status gks_batch_create(const gks_case_desc *cases, int32_t n_cases, const gks_config *cfg, gks_mesh **out)
+{
+    if (!cases || n_cases <= 0) {
+        set_error("gks_batch_create: no case");
+        if (out) *out = nullptr;
         return GKS_EINVAL;
     }
-    *out = nullptr;
-    gks_mesh *m = new (std::nothrow) gks_mesh();
-    if (!m) {
-        set_error("gks_mesh_create: host allocation failed");
-        return GKS_ENOMEM;
-    }
-    if (cfg) m->cfg = *cfg;
-    else gks_config_default(&m->cfg);
-    gks_status st = check_config(m->cfg);
-    if (st == GKS_OK && cudaGetDevice(&m->device) != cudaSuccess) {
-        set_error("gks_mesh_create: no CUDA device");
-        st = GKS_ECUDA;
-    }
-    if (st == GKS_OK) st = build_mesh(m, nodes, n_nodes, tris, n_tri, faces, face_shift, n_face, bc_state);
-    if (st != GKS_OK) {
-        free_mesh(m);
-        delete m;
-        return st;
-    }
-    *out = m;
-    return GKS_OK;
+    std::vector<CaseIn> in(n_cases);
+    for (int32_t c = 0; c < n_cases; ++c)
+        in[c] = CaseIn{cases[c].nodes, cases[c].n_nodes, cases[c].tris, cases[c].n_tri, cases[c].faces,
+                       cases[c].face_shift, cases[c].n_face, cases[c].bc_state};
+    return create(in.data(), n_cases, cfg, out);
 }
 
 gks_status gks_mesh_destroy(gks_mesh *m)
@@ -192,6 +224,7 @@ gks_status gks_mesh_get_stats(const gks_mesh *m, gks_mesh_stats *s)
     s->levels_upper = (int32_t)m->lvl_up_ptr.size() - 1;
     s->rcm_bandwidth = m->bandwidth;
     s->device_bytes = m->device_bytes;
+    s->n_case = m->n_case;
     return GKS_OK;
 }
 
@@ -201,10 +234,11 @@ gks_status gks_cfl_dt(gks_mesh *m, const double *w, double *dt_out, void *stream
         set_error("gks_cfl_dt: NULL argument");
         return GKS_EINVAL;
     }
+    if (require_single(m, "gks_cfl_dt") != GKS_OK) return GKS_EINVAL;
     DeviceGuard g(m->device);
     cudaStream_t s = (cudaStream_t)stream;
     gks_status st;
-    if ((st = launch_permute(w, m->wk.w, m->d.perm, m->d.T, 4, true, s)) != GKS_OK) return st;
+    if ((st = launch_permute(w, m->wk.w, m->d.perm, m->d.T, m->n_tri, 4, true, s)) != GKS_OK) return st;
     if ((st = launch_cfl_dt(m, m->wk.w, m->wk.dt, s)) != GKS_OK) return st;
     GKS_CUDA(cudaMemcpyAsync(&m->wk.h_scal[6], m->wk.dt, sizeof(double), cudaMemcpyDeviceToHost, s));
     GKS_CUDA(cudaStreamSynchronize(s));
@@ -221,10 +255,17 @@ gks_status gks_cls_reconstruct(gks_mesh *m, const double *w, double *coef, gks_s
     DeviceGuard g(m->device);
     cudaStream_t s = (cudaStream_t)stream;
     gks_status st;
-    if ((st = launch_permute(w, m->wk.w, m->d.perm, m->d.T, 4, true, s)) != GKS_OK) return st;
-    gks_solve_info si;
-    if ((st = cls_solve(m, s, &si)) != GKS_OK) return st;
-    if ((st = launch_permute(m->wk.x, coef, m->d.perm, m->d.T, 20, false, s)) != GKS_OK) return st;
+    if ((st = launch_permute(w, m->wk.w, m->d.perm, m->d.T, m->n_tri, 4, true, s)) != GKS_OK) return st;
+    GKS_CUDA(cudaMemsetAsync(m->wk.done, 0, sizeof(int32_t) * m->n_case, s));
+    std::vector<int32_t> it(m->wk.ns);
+    std::vector<double> rr(m->wk.ns);
+    gks_solve_info si{};
+    if ((st = cls_solve(m, s, it.data(), rr.data(), &si.converged)) != GKS_OK) return st;
+    if ((st = launch_permute(m->wk.x, coef, m->d.perm, m->d.T, m->n_tri, 20, false, s)) != GKS_OK) return st;
+    for (int q = 0; q < m->wk.ns; ++q) {         // per variable: the largest over the cases
+        si.iters[q & 3] = std::max(si.iters[q & 3], it[q]);
+        si.relres[q & 3] = std::max(si.relres[q & 3], rr[q]);
+    }
     if (info) *info = si;
     if (!si.converged) {
         set_error("GMRES did not reach gmres_rtol within gmres_maxit");
@@ -254,17 +295,19 @@ gks_status gks_flux(gks_mesh *m, const double *w, const double *coef, double dt,
     cudaStream_t s = (cudaStream_t)stream;
     gks_status st;
     Work &k = m->wk;
-    GKS_CUDA(cudaMemsetAsync(k.status, 0, sizeof(int32_t), s));
-    if ((st = launch_permute(w, k.w, m->d.perm, m->d.T, 4, true, s)) != GKS_OK) return st;
-    if ((st = launch_permute(coef, k.r, m->d.perm, m->d.T, 20, true, s)) != GKS_OK) return st;
+    GKS_CUDA(cudaMemsetAsync(k.status, 0, sizeof(int32_t) * m->n_case, s));
+    if ((st = launch_permute(w, k.w, m->d.perm, m->d.T, m->n_tri, 4, true, s)) != GKS_OK) return st;
+    if ((st = launch_permute(coef, k.r, m->d.perm, m->d.T, m->n_tri, 20, true, s)) != GKS_OK) return st;
     if ((st = launch_flux(m, k.w, k.r, dt, nullptr, k.flux, s)) != GKS_OK) return st;
-    if ((st = launch_permute(k.flux, face_flux, m->d.fperm, m->d.F, 4, false, s)) != GKS_OK) return st;
-    int32_t stat = 0;
-    if ((st = read_status(m, s, &stat)) != GKS_OK) return st;
-    if (stat & kStatusNonPhys) {
-        set_error("non-physical state at a Gauss point");
-        return GKS_ENONPHYS;
-    }
+    if ((st = launch_permute(k.flux, face_flux, m->d.fperm, m->d.F, m->n_face, 4, false, s)) != GKS_OK) return st;
+    std::vector<int32_t> stat(m->n_case);
+    GKS_CUDA(cudaMemcpyAsync(stat.data(), k.status, sizeof(int32_t) * m->n_case, cudaMemcpyDeviceToHost, s));
+    GKS_CUDA(cudaStreamSynchronize(s));
+    for (int32_t v : stat)
+        if (v & kStatusNonPhys) {
+            set_error("non-physical state at a Gauss point");
+            return GKS_ENONPHYS;
+        }
     return GKS_OK;
 }
 
@@ -274,15 +317,16 @@ gks_status gks_step(gks_mesh *m, double *w, double *dt_inout, gks_step_info *inf
         set_error("gks_step: NULL argument");
         return GKS_EINVAL;
     }
+    if (require_single(m, "gks_step") != GKS_OK) return GKS_EINVAL;
     DeviceGuard g(m->device);
     cudaStream_t s = (cudaStream_t)stream;
     gks_status st;
-    GKS_CUDA(cudaMemsetAsync(m->wk.status, 0, sizeof(int32_t), s));
-    if ((st = launch_permute(w, m->wk.w, m->d.perm, m->d.T, 4, true, s)) != GKS_OK) return st;
+    GKS_CUDA(cudaMemsetAsync(m->wk.status, 0, sizeof(int32_t) * m->n_case, s));
+    if ((st = launch_permute(w, m->wk.w, m->d.perm, m->d.T, m->n_tri, 4, true, s)) != GKS_OK) return st;
     double dt = 0.0;
     gks_status res = step_internal(m, dt_inout ? *dt_inout : 0.0, s, info, &dt);
     if (res != GKS_OK && res != GKS_ENOCONV && res != GKS_ENONPHYS) return res;
-    if ((st = launch_permute(m->wk.w, w, m->d.perm, m->d.T, 4, false, s)) != GKS_OK) return st;
+    if ((st = launch_permute(m->wk.w, w, m->d.perm, m->d.T, m->n_tri, 4, false, s)) != GKS_OK) return st;
     GKS_CUDA(cudaStreamSynchronize(s));
     if (dt_inout) *dt_inout = dt;
     return res;
@@ -295,12 +339,13 @@ gks_status gks_run(gks_mesh *m, double *w, double t_final, int64_t max_steps, do
         set_error("gks_run: NULL argument or max_steps < 0");
         return GKS_EINVAL;
     }
+    if (require_single(m, "gks_run") != GKS_OK) return GKS_EINVAL;
     DeviceGuard g(m->device);
     cudaStream_t s = (cudaStream_t)stream;
     gks_status st, res = GKS_OK;
     Work &k = m->wk;
-    GKS_CUDA(cudaMemsetAsync(k.status, 0, sizeof(int32_t), s));
-    if ((st = launch_permute(w, k.w, m->d.perm, m->d.T, 4, true, s)) != GKS_OK) return st;
+    GKS_CUDA(cudaMemsetAsync(k.status, 0, sizeof(int32_t) * m->n_case, s));
+    if ((st = launch_permute(w, k.w, m->d.perm, m->d.T, m->n_tri, 4, true, s)) != GKS_OK) return st;
     double t = 0.0, last_dt = 0.0, res0 = -1.0, sres = 0.0;
     int64_t steps = 0, iters = 0;
     while (steps < max_steps) {
@@ -333,7 +378,7 @@ gks_status gks_run(gks_mesh *m, double *w, double t_final, int64_t max_steps, do
             if (sres < steady_tol) break;
         }
     }
-    if ((st = launch_permute(k.w, w, m->d.perm, m->d.T, 4, false, s)) != GKS_OK) return st;
+    if ((st = launch_permute(k.w, w, m->d.perm, m->d.T, m->n_tri, 4, false, s)) != GKS_OK) return st;
     GKS_CUDA(cudaStreamSynchronize(s));
     if (info) {
         info->steps = steps;
@@ -344,6 +389,74 @@ gks_status gks_run(gks_mesh *m, double *w, double t_final, int64_t max_steps, do
         info->status = res;
     }
     return res;
+}
+
+gks_status gks_batch_run(gks_mesh *m, double *w, const double *t_final, int64_t max_steps, double *t_reached,
+                         int32_t *case_status, gks_batch_info *info, void *stream)
+{
+    if (!m || !w || max_steps < 0) {
+        set_error("gks_batch_run: NULL argument or max_steps < 0");
+        return GKS_EINVAL;
+    }
+    DeviceGuard g(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Work &k = m->wk;
+    const int32_t n = m->n_case;
+    gks_status st;
+    std::vector<double> tf(n, 0.0);
+    if (t_final)
+        for (int32_t c = 0; c < n; ++c) tf[c] = t_final[c];
+    GKS_CUDA(cudaMemcpyAsync(k.tfinal, tf.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    GKS_CUDA(cudaMemsetAsync(k.tcase, 0, sizeof(double) * n, s));
+    GKS_CUDA(cudaMemsetAsync(k.done, 0, sizeof(int32_t) * n, s));
+    GKS_CUDA(cudaMemsetAsync(k.status, 0, sizeof(int32_t) * n, s));
+    if ((st = launch_permute(w, k.w, m->d.perm, m->d.T, m->n_tri, 4, true, s)) != GKS_OK) return st;
+    std::vector<int32_t> done(n), stat(n), it(k.ns);
+    int64_t steps = 0, iters = 0;
+    while (steps < max_steps) {
+        if ((st = launch_cfl_dt(m, k.w, k.dt, s)) != GKS_OK) return st;
+        if ((st = launch_clip_dt(m, s)) != GKS_OK) return st;
+        GKS_CUDA(cudaMemcpyAsync(done.data(), k.done, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+        GKS_CUDA(cudaStreamSynchronize(s));
+        bool all = true;
+        for (int32_t c = 0; c < n; ++c) all = all && done[c];
+        if (all) break;
+        if ((st = cls_solve(m, s, it.data(), nullptr, nullptr)) != GKS_OK) return st;
+        if ((st = launch_flux(m, k.w, k.x, 0.0, k.dt, k.flux, s)) != GKS_OK) return st;
+        if ((st = launch_update(m, k.w, k.flux, s)) != GKS_OK) return st;
+        // a case that failed stops advancing; the others go on
+        GKS_CUDA(cudaMemcpyAsync(stat.data(), k.status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+        GKS_CUDA(cudaStreamSynchronize(s));
+        bool newfail = false;
+        for (int32_t c = 0; c < n; ++c)
+            if (stat[c] && !done[c]) {
+                done[c] = 1;
+                newfail = true;
+            }
+        if (newfail) GKS_CUDA(cudaMemcpyAsync(k.done, done.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+        for (int32_t q = 0; q < k.ns; ++q) iters += it[q];
+        ++steps;
+    }
+    if ((st = launch_permute(k.w, w, m->d.perm, m->d.T, m->n_tri, 4, false, s)) != GKS_OK) return st;
+    std::vector<double> tr(n);
+    GKS_CUDA(cudaMemcpyAsync(tr.data(), k.tcase, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    GKS_CUDA(cudaMemcpyAsync(stat.data(), k.status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    GKS_CUDA(cudaStreamSynchronize(s));
+    int32_t nfail = 0, ndone = 0;
+    for (int32_t c = 0; c < n; ++c) {
+        const int32_t cs = (stat[c] & kStatusNonPhys) ? GKS_ENONPHYS : (stat[c] & kStatusNoConv) ? GKS_ENOCONV : GKS_OK;
+        if (t_reached) t_reached[c] = tr[c];
+        if (case_status) case_status[c] = cs;
+        nfail += cs != GKS_OK;
+        ndone += cs == GKS_OK && tf[c] > 0.0 && tr[c] >= tf[c] * (1.0 - 1e-14);
+    }
+    if (info) {
+        info->steps = steps;
+        info->gmres_iters = iters;
+        info->n_failed = nfail;
+        info->n_finished = ndone;
+    }
+    return GKS_OK;
 }
 
 gks_status gks_profile_begin(gks_mesh *m, int32_t class_mask)

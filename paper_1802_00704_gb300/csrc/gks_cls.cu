@@ -21,12 +21,11 @@ constexpr int NV = 4, ND = 5, NX = 20;
 // residual estimate has dropped by this factor; the FP64 residual of the next
 // refinement sweep then measures the true error.
 constexpr double kInnerRtol = 1e-6;
+constexpr int kDotBlock = 128;         // threads per block of the dot-product kernel
 
-// ctl layout: [0..3] active, [4..7] running, [8..11] vectors in cycle, [12..15] iterations
-__device__ __forceinline__ int &ctl_active(int32_t *c, int v) { return c[v]; }
-__device__ __forceinline__ int &ctl_running(int32_t *c, int v) { return c[4 + v]; }
-__device__ __forceinline__ int &ctl_jv(int32_t *c, int v) { return c[8 + v]; }
-__device__ __forceinline__ int &ctl_iters(int32_t *c, int v) { return c[12 + v]; }
+// Per-variable control words ctl[16]: [0..3] active (needs more work), [4..7]
+// running (iterating in the current cycle), [8..11] Krylov vectors in the
+// cycle, [12..15] iterations so far.
 
 // y = O x_j for the gradient entries (g1, g2) of neighbour j
 template <typename R>
@@ -253,49 +252,80 @@ __global__ void k_ilu_bwd(DeviceMesh d, const TM *__restrict__ Pg, const TM *__r
         }
 }
 
-// Partial dot products <V_k, w> for k = 0..j, per variable.
-__global__ void k_dots(int64_t T, const double *__restrict__ V, const double *__restrict__ w, int j,
-                       double *__restrict__ part, int pstride)
+// Partial dot products <V_k, w> for k = 0..j (j < JMAX) and the four variables
+// over one block of kBlock cells (kDotBlock threads, two cells each): each
+// thread accumulates every k, then one block reduction writes part[blk][v][k].
+// Blocks never straddle two cases.
+template <int JMAX>
+__global__ void __launch_bounds__(kDotBlock) k_dots(int64_t T, const double *__restrict__ V,
+                                                    const double *__restrict__ w, int j, double *__restrict__ part,
+                                                    int pstride)
 {
-    __shared__ double sh[32 * NV];
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    __shared__ double sh[(kDotBlock / 32) * NV * JMAX];
     const int64_t vs = (int64_t)NX * T;
-    double wv[NX];
+    double acc[NV * JMAX];
 #pragma unroll
-    for (int q = 0; q < NX; ++q) wv[q] = i < T ? w[q * T + i] : 0.0;
-    for (int k = 0; k <= j; ++k) {
-        double s[NV] = {0, 0, 0, 0};
-        if (i < T) {
+    for (int q = 0; q < NV * JMAX; ++q) acc[q] = 0.0;
+#pragma unroll
+    for (int half = 0; half < kBlock / kDotBlock; ++half) {
+        const int64_t i = blockIdx.x * (int64_t)kBlock + half * kDotBlock + threadIdx.x;
+        if (i >= T) break;
+        double wv[NX];
+#pragma unroll
+        for (int q = 0; q < NX; ++q) wv[q] = w[q * T + i];
+#pragma unroll
+        for (int k = 0; k < JMAX; ++k) {
+            if (k > j) break;
             const double *vk = V + k * vs;
 #pragma unroll
-            for (int v = 0; v < NV; ++v)
+            for (int v = 0; v < NV; ++v) {
+                double sum = 0.0;
 #pragma unroll
-                for (int l = 0; l < ND; ++l) s[v] += vk[(v * ND + l) * T + i] * wv[v * ND + l];
+                for (int l = 0; l < ND; ++l) sum += vk[(v * ND + l) * T + i] * wv[v * ND + l];
+                acc[v * JMAX + k] += sum;
+            }
         }
-        block_sum4(s, sh);
-        if (threadIdx.x == 0)
-            for (int v = 0; v < NV; ++v) part[(blockIdx.x * NV + v) * pstride + k] = s[v];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV * JMAX; ++q) {
+        if (q % JMAX > j) continue;
+        double x = acc[q];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[warp * NV * JMAX + q] = x;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < NV * JMAX; q += blockDim.x) {
+        const int v = q / JMAX, k = q % JMAX;
+        if (k > j) continue;
+        double x = 0.0;
+        for (int u = 0; u < nw; ++u) x += sh[u * NV * JMAX + q];
+        part[(blockIdx.x * NV + v) * pstride + k] = x;
     }
 }
 
-// w -= sum_{k<=j} h[v][k] V_k for running variables; optional partial |w|^2.
-__global__ void k_orth_update(int64_t T, const double *__restrict__ V, double *__restrict__ w, int j,
-                              const double *__restrict__ hc, int hstride, const int32_t *__restrict__ ctl,
+// w -= sum_{k<=j} h[s][k] V_k for running systems s = case * 4 + v; optional
+// partial |w|^2 per block.
+__global__ void k_orth_update(DeviceMesh d, const double *__restrict__ V, double *__restrict__ w, int j,
+                              const double *__restrict__ hc, int hstride, const int32_t *__restrict__ ctl, int ns,
                               double *__restrict__ part, int pstride, int want_norm)
 {
     __shared__ double sh[32 * NV];
+    const int64_t T = d.T;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t vs = (int64_t)NX * T;
+    const int c = d.blk_case[blockIdx.x];
     double nrm[NV] = {0, 0, 0, 0};
     if (i < T) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            if (!ctl[4 + v]) continue;
+            const int sy = 4 * c + v;
+            if (!ctl[kCtlRunning * ns + sy]) continue;
             double wv[ND];
 #pragma unroll
             for (int l = 0; l < ND; ++l) wv[l] = w[(v * ND + l) * T + i];
             for (int k = 0; k <= j; ++k) {
-                const double hk = hc[v * hstride + k];
+                const double hk = hc[sy * hstride + k];
                 const double *vk = V + k * vs;
 #pragma unroll
                 for (int l = 0; l < ND; ++l) wv[l] -= hk * vk[(v * ND + l) * T + i];
@@ -314,181 +344,213 @@ __global__ void k_orth_update(int64_t T, const double *__restrict__ V, double *_
     }
 }
 
-// out[v][q] (op) sum over blocks of part[blk][v][q], q < nq, fixed order.
-// op 0: store, 1: add, 2: store sqrt.  Grid (nq, 4).
-__global__ void k_reduce(const double *__restrict__ part, int nblk, int pstride, double *out, int ostride, int op)
+// Segmented sums over the cell blocks of each case, fixed order:
+// out[s][q] (op) sum_{b in case(s)} part[b][v(s)][q], q < nq; op 0 store, 1 add,
+// 2 store sqrt.  One warp per (q, s): grid (nq, ns), 32 threads.
+__global__ void k_reduce(const double *__restrict__ part, const int32_t *__restrict__ case_blk, int pstride,
+                         double *out, int ostride, int op)
 {
-    __shared__ double sh[kBlock];
-    const int q = blockIdx.x, v = blockIdx.y;
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[(b * NV + v) * pstride + q];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-        __syncthreads();
-    }
+    const int q = blockIdx.x, sy = blockIdx.y, c = sy >> 2, v = sy & 3;
+    const int b0 = case_blk[c], b1 = case_blk[c + 1];
+    double acc = 0.0;
+    for (int b = b0 + threadIdx.x; b < b1; b += 32) acc += part[(b * NV + v) * pstride + q];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if (threadIdx.x == 0) {
-        double r = sh[0];
-        if (op == 0) out[v * ostride + q] = r;
-        else if (op == 1) out[v * ostride + q] += r;
-        else out[v * ostride + q] = sqrt(r);
+        if (op == 0) out[sy * ostride + q] = acc;
+        else if (op == 1) out[sy * ostride + q] += acc;
+        else out[sy * ostride + q] = sqrt(acc);
     }
 }
 
-// h[v][q] += h2[v][q], q <= j (second Gram-Schmidt pass)
-__global__ void k_hadd(double *hc, int hstride, const double *__restrict__ h2, int h2stride, int j)
+// h[s][q] += h2[s][q], q <= j (second Gram-Schmidt pass)
+__global__ void k_hadd(double *hc, int hstride, const double *__restrict__ h2, int h2stride, int j, int ns)
 {
-    for (int t = threadIdx.x; t < NV * (j + 1); t += blockDim.x) {
-        const int v = t / (j + 1), q = t % (j + 1);
-        hc[v * hstride + q] += h2[v * h2stride + q];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ns * (j + 1); t += gridDim.x * blockDim.x) {
+        const int sy = t / (j + 1), q = t % (j + 1);
+        hc[sy * hstride + q] += h2[sy * h2stride + q];
     }
 }
 
-// V_{j+1} = w / |w| for running variables (w stored in the V_{j+1} slot).
-__global__ void k_scale(int64_t T, double *__restrict__ vj1, const double *__restrict__ hc, int hstride, int j,
-                        const int32_t *__restrict__ ctl)
+// V_{j+1} = w / |w| for running systems (w stored in the V_{j+1} slot).
+__global__ void k_scale(DeviceMesh d, double *__restrict__ vj1, const double *__restrict__ hc, int hstride, int j,
+                        const int32_t *__restrict__ ctl, int ns)
 {
+    const int64_t T = d.T;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= T) return;
+    const int c = d.blk_case[blockIdx.x];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        const double h = hc[v * hstride + j + 1];
-        if (!ctl[4 + v] || !(h > 0.0)) continue;
+        const int sy = 4 * c + v;
+        const double h = hc[sy * hstride + j + 1];
+        if (!ctl[kCtlRunning * ns + sy] || !(h > 0.0)) continue;
         const double inv = 1.0 / h;
 #pragma unroll
         for (int l = 0; l < ND; ++l) vj1[(v * ND + l) * T + i] *= inv;
     }
 }
 
-// Givens step of column j for each running variable (one thread per variable).
+// Givens step of column j for each running system (one thread per system).
 __global__ void k_givens(int j, int m, const double *__restrict__ hc, int hstride, double *H, double *cs,
-                         double *sn, double *g, int32_t *ctl, const double *__restrict__ bnorm,
+                         double *sn, double *g, int32_t *ctl, int ns, const double *__restrict__ bnorm,
                          const double *__restrict__ beta, double rtol, double eta, int maxit)
 {
-    const int v = threadIdx.x;
-    if (v >= NV || !ctl[4 + v]) return;
+    const int sy = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sy >= ns || !ctl[kCtlRunning * ns + sy]) return;
     double h[kMaxRestart + 1];
-    for (int k = 0; k <= j + 1; ++k) h[k] = hc[v * hstride + k];
+    for (int k = 0; k <= j + 1; ++k) h[k] = hc[sy * hstride + k];
     const double hnext = h[j + 1];
     for (int k = 0; k < j; ++k) {
-        const double c = cs[v * m + k], s = sn[v * m + k];
+        const double c = cs[sy * m + k], s = sn[sy * m + k];
         const double t0 = h[k], t1 = h[k + 1];
         h[k] = c * t0 + s * t1;
         h[k + 1] = -s * t0 + c * t1;
     }
     const double dd = hypot(h[j], h[j + 1]);
     const double c = dd > 0.0 ? h[j] / dd : 1.0, s = dd > 0.0 ? h[j + 1] / dd : 0.0;
-    cs[v * m + j] = c;
-    sn[v * m + j] = s;
+    cs[sy * m + j] = c;
+    sn[sy * m + j] = s;
     h[j] = dd;
-    for (int k = 0; k <= j; ++k) H[(v * (m + 1) + k) * m + j] = h[k];
-    const double gj = g[v * (m + 1) + j];
-    g[v * (m + 1) + j + 1] = -s * gj;
-    g[v * (m + 1) + j] = c * gj;
-    ctl[8 + v] = j + 1;
-    ctl[12 + v] += 1;
+    for (int k = 0; k <= j; ++k) H[((int64_t)sy * (m + 1) + k) * m + j] = h[k];
+    const double gj = g[sy * (m + 1) + j];
+    g[sy * (m + 1) + j + 1] = -s * gj;
+    g[sy * (m + 1) + j] = c * gj;
+    ctl[kCtlJv * ns + sy] = j + 1;
+    ctl[kCtlIters * ns + sy] += 1;
     // stop the cycle at the target, or (mixed precision, eta > 0) once the inner
     // residual has dropped by eta: the FP64 refinement residual then restarts it
-    const double gn = fabs(g[v * (m + 1) + j + 1]);
-    if (gn <= rtol * bnorm[v] || gn <= eta * beta[v] || !(hnext > 0.0) || ctl[12 + v] >= maxit || j + 1 == m)
-        ctl[4 + v] = 0;
+    const double gn = fabs(g[sy * (m + 1) + j + 1]);
+    if (gn <= rtol * bnorm[sy] || gn <= eta * beta[sy] || !(hnext > 0.0) || ctl[kCtlIters * ns + sy] >= maxit ||
+        j + 1 == m)
+        ctl[kCtlRunning * ns + sy] = 0;
 }
 
 // y = H^{-1} g on the first jv columns (upper triangular after the rotations).
 __global__ void k_backsolve(int m, const double *__restrict__ H, const double *__restrict__ g, double *y,
-                            const int32_t *__restrict__ ctl)
+                            const int32_t *__restrict__ ctl, int ns)
 {
-    const int v = threadIdx.x;
-    if (v >= NV) return;
-    const int jv = ctl[8 + v];
+    const int sy = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sy >= ns) return;
+    const int jv = ctl[kCtlJv * ns + sy];
     for (int k = jv - 1; k >= 0; --k) {
-        double s = g[v * (m + 1) + k];
-        for (int q = k + 1; q < jv; ++q) s -= H[(v * (m + 1) + k) * m + q] * y[v * m + q];
-        y[v * m + k] = s / H[(v * (m + 1) + k) * m + k];
+        double s = g[sy * (m + 1) + k];
+        for (int q = k + 1; q < jv; ++q) s -= H[((int64_t)sy * (m + 1) + k) * m + q] * y[sy * m + q];
+        y[sy * m + k] = s / H[((int64_t)sy * (m + 1) + k) * m + k];
     }
 }
 
-// u = sum_{k<jv} y_k V_k per variable (zero where jv = 0)
-__global__ void k_combine(int64_t T, const double *__restrict__ V, const double *__restrict__ y, int m,
-                          const int32_t *__restrict__ ctl, double *__restrict__ u)
+// x += sum_{k<jv} y_k Z_k with Z_k = M^{-1} V_k kept from the iterations
+template <typename TZ>
+__global__ void k_combine_z(DeviceMesh d, const TZ *__restrict__ Z, const double *__restrict__ y, int m,
+                            const int32_t *__restrict__ ctl, int ns, double *__restrict__ x)
 {
+    const int64_t T = d.T;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= T) return;
+    const int c = d.blk_case[blockIdx.x];
     const int64_t vs = (int64_t)NX * T;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        const int jv = ctl[8 + v];
+        const int sy = 4 * c + v;
+        const int jv = ctl[kCtlJv * ns + sy];
+        if (jv <= 0) continue;
         double acc[ND] = {0, 0, 0, 0, 0};
         for (int k = 0; k < jv; ++k) {
-            const double yk = y[v * m + k];
+            const double yk = y[sy * m + k];
 #pragma unroll
-            for (int l = 0; l < ND; ++l) acc[l] += yk * V[k * vs + (v * ND + l) * T + i];
+            for (int l = 0; l < ND; ++l) acc[l] += yk * double(Z[k * vs + (v * ND + l) * T + i]);
         }
 #pragma unroll
-        for (int l = 0; l < ND; ++l) u[(v * ND + l) * T + i] = acc[l];
+        for (int l = 0; l < ND; ++l) x[(v * ND + l) * T + i] += acc[l];
     }
 }
 
-// x += t for variables that took a cycle (jv > 0)
-template <typename TT>
-__global__ void k_addx(int64_t T, double *__restrict__ x, const TT *__restrict__ t, const int32_t *__restrict__ ctl)
-{
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= T) return;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        if (ctl[8 + v] <= 0) continue;
-#pragma unroll
-        for (int l = 0; l < ND; ++l) x[(v * ND + l) * T + i] += double(t[(v * ND + l) * T + i]);
-    }
-}
-
-// Start of the solve: sums[v][0] = |r|^2, sums[v][1] = |b|^2 (already reduced).
+// Start (first = 1) or restart of every system: sums[s][0] = |r|^2,
+// sums[s][1] = |b|^2.  Systems of finished cases stay inactive.
 __global__ void k_start(const double *__restrict__ sums, int sstride, double *bnorm, double *beta, int32_t *ctl,
-                        double rtol, int maxit, int first)
+                        int ns, const int32_t *__restrict__ done, double rtol, int maxit, int first)
 {
-    const int v = threadIdx.x;
-    if (v >= NV) return;
-    const double bn = sqrt(sums[v * sstride + 1]), be = sqrt(sums[v * sstride + 0]);
+    const int sy = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sy >= ns) return;
+    const double bn = sqrt(sums[sy * sstride + 1]), be = sqrt(sums[sy * sstride + 0]);
     if (first) {
-        bnorm[v] = bn;
-        ctl[12 + v] = 0;
-        ctl[v] = 1;
+        bnorm[sy] = bn;
+        ctl[kCtlIters * ns + sy] = 0;
+        ctl[kCtlActive * ns + sy] = !done[sy >> 2];
     }
-    beta[v] = be;
-    const int act = ctl[v] && bn > 0.0 && be > rtol * bn && ctl[12 + v] < maxit;
-    ctl[v] = act;
-    ctl[4 + v] = act;
-    ctl[8 + v] = 0;
+    beta[sy] = be;
+    const int act = ctl[kCtlActive * ns + sy] && bn > 0.0 && be > rtol * bn && ctl[kCtlIters * ns + sy] < maxit;
+    ctl[kCtlActive * ns + sy] = act;
+    ctl[kCtlRunning * ns + sy] = act;
+    ctl[kCtlJv * ns + sy] = 0;
 }
 
-// V_0 = r / beta for active variables, zero otherwise; g = beta e_1.
-__global__ void k_init_v0(int64_t T, const double *__restrict__ r, double *__restrict__ v0,
-                          const double *__restrict__ beta, const int32_t *__restrict__ ctl, double *g, int m)
+// flags[0] = any active system, flags[1] = any running system (one block).
+__global__ void k_any(const int32_t *__restrict__ ctl, int ns, int32_t *flags)
 {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < NV * (m + 1)) g[i] = (i % (m + 1) == 0 && ctl[i / (m + 1)]) ? beta[i / (m + 1)] : 0.0;
-    if (i >= T) return;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        const double s = ctl[v] ? 1.0 / beta[v] : 0.0;
-#pragma unroll
-        for (int l = 0; l < ND; ++l) v0[(v * ND + l) * T + i] = ctl[v] ? r[(v * ND + l) * T + i] * s : 0.0;
+    __shared__ int sh[2];
+    if (threadIdx.x < 2) sh[threadIdx.x] = 0;
+    __syncthreads();
+    int a = 0, r = 0;
+    for (int sy = threadIdx.x; sy < ns; sy += blockDim.x) {
+        a |= ctl[kCtlActive * ns + sy];
+        r |= ctl[kCtlRunning * ns + sy];
+    }
+    if (a) atomicOr(&sh[0], 1);
+    if (r) atomicOr(&sh[1], 1);
+    __syncthreads();
+    if (threadIdx.x < 2) flags[threadIdx.x] = sh[threadIdx.x];
+}
+
+// g = beta e_1 for active systems.
+__global__ void k_init_g(double *g, int m, const double *__restrict__ beta, const int32_t *__restrict__ ctl, int ns)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ns * (m + 1); t += gridDim.x * blockDim.x) {
+        const int sy = t / (m + 1);
+        g[t] = (t % (m + 1) == 0 && ctl[kCtlActive * ns + sy]) ? beta[sy] : 0.0;
     }
 }
 
-// x[v] = 0 for variables with b = 0 (free stream: zero coefficients exactly)
-__global__ void k_zero_trivial(int64_t T, double *__restrict__ x, const double *__restrict__ bnorm)
+// V_0 = r / beta for active systems, zero otherwise.
+__global__ void k_init_v0(DeviceMesh d, const double *__restrict__ r, double *__restrict__ v0,
+                          const double *__restrict__ beta, const int32_t *__restrict__ ctl, int ns)
 {
+    const int64_t T = d.T;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= T) return;
+    const int c = d.blk_case[blockIdx.x];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        if (bnorm[v] > 0.0) continue;
+        const int sy = 4 * c + v;
+        const bool act = ctl[kCtlActive * ns + sy];
+        const double s = act ? 1.0 / beta[sy] : 0.0;
+#pragma unroll
+        for (int l = 0; l < ND; ++l) v0[(v * ND + l) * T + i] = act ? r[(v * ND + l) * T + i] * s : 0.0;
+    }
+}
+
+// x = 0 for systems with b = 0 (free stream: zero coefficients exactly)
+__global__ void k_zero_trivial(DeviceMesh d, double *__restrict__ x, const double *__restrict__ bnorm)
+{
+    const int64_t T = d.T;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= T) return;
+    const int c = d.blk_case[blockIdx.x];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        if (bnorm[4 * c + v] > 0.0) continue;
 #pragma unroll
         for (int l = 0; l < ND; ++l) x[(v * ND + l) * T + i] = 0.0;
     }
+}
+
+// status[c] |= noconv for cases with a system that stopped above the tolerance
+__global__ void k_mark_noconv(const double *__restrict__ bnorm, const double *__restrict__ beta,
+                              const int32_t *__restrict__ done, int ns, double rtol, int32_t *status)
+{
+    const int sy = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sy >= ns || done[sy >> 2]) return;
+    if (bnorm[sy] > 0.0 && beta[sy] > rtol * bnorm[sy]) atomicOr(&status[sy >> 2], kStatusNoConv);
 }
 
 inline unsigned nblocks(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
@@ -556,102 +618,135 @@ gks_status precond32(gks_mesh *m, const double *src, float *dst, cudaStream_t s)
     return precond_t<float, float>(m, d.P32, d.alpha32, d.ex32, d.ey32, src, dst, m->wk.t2_32, m->wk.t3_32, s);
 }
 
-gks_status read_ctl(gks_mesh *m, cudaStream_t s)
+gks_status read_flags(gks_mesh *m, cudaStream_t s)
 {
-    GKS_CUDA(cudaMemcpyAsync(m->wk.h_ctl, m->wk.ctl, sizeof(int32_t) * 16, cudaMemcpyDeviceToHost, s));
+    k_any<<<1, kBlock, 0, s>>>(m->wk.ctl, m->wk.ns, m->wk.flags);
+    note_launch();
+    GKS_CUDA(cudaMemcpyAsync(m->wk.h_flags, m->wk.flags, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, s));
     GKS_CUDA(cudaStreamSynchronize(s));
     return GKS_OK;
 }
 
+// part[blk][v][k] = partial <V_k, w>, k <= j, per cell block
+gks_status dots(gks_mesh *m, const double *w, int j, double *part, int ps, cudaStream_t s)
+{
+    Work &k = m->wk;
+    const int64_t T = m->d.T;
+    const unsigned g = (unsigned)k.nblk;
+    if (j < 4) k_dots<4><<<g, kDotBlock, 0, s>>>(T, k.V, w, j, part, ps);
+    else if (j < 8) k_dots<8><<<g, kDotBlock, 0, s>>>(T, k.V, w, j, part, ps);
+    else if (j < 16) k_dots<16><<<g, kDotBlock, 0, s>>>(T, k.V, w, j, part, ps);
+    else k_dots<kMaxRestart><<<g, kDotBlock, 0, s>>>(T, k.V, w, j, part, ps);
+    note_launch();
+    GKS_CUDA(cudaGetLastError());
+    return GKS_OK;
+}
+
+inline unsigned sblocks(int n) { return (unsigned)((n + 127) / 128); }
+
 }  // namespace
 
-// Solve the CLS system for the right-hand side built from m->wk.w; the solution
-// (and warm start) is m->wk.x.
-gks_status cls_solve(gks_mesh *m, cudaStream_t s, gks_solve_info *info)
+// Solve the CLS systems of every case for the right-hand sides built from
+// m->wk.w; the solutions (and warm starts) are m->wk.x.  GMRES cycles of all
+// systems run in lockstep: every launch covers all cases, and per-system masks
+// stop the systems that have converged.
+gks_status cls_solve(gks_mesh *m, cudaStream_t s, int32_t *iters, double *relres, int32_t *converged)
 {
     DeviceMesh &d = m->d;
     Work &k = m->wk;
     const int64_t T = d.T;
     const int mm = k.m;
     const int ps = mm + 2;
-    const unsigned nb = nblocks(T);
+    const int ns = k.ns;
+    const unsigned nb = (unsigned)k.nblk;
     const double rtol = m->cfg.gmres_rtol;
     const int maxit = m->cfg.gmres_maxit;
     const int64_t vs = (int64_t)NX * T;
-    gks_status st;
-
     const bool mixed = m->cfg.precision == GKS_MIXED;
     const double eta = mixed ? kInnerRtol : 0.0;
-    k_rhs<<<nb, kBlock, 0, s>>>(d, k.w, k.b); note_launch();
-    k_spmv<double, double><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, k.r, 1, k.b, k.part, ps); note_launch();
-    k_reduce<<<dim3(2, NV), kBlock, 0, s>>>(k.part, k.nblk, ps, k.hcol, ps, 0); note_launch();
-    k_start<<<1, 32, 0, s>>>(k.hcol, ps, k.bnorm, k.beta, k.ctl, rtol, maxit, 1); note_launch();
-    k_zero_trivial<<<nb, kBlock, 0, s>>>(T, k.x, k.bnorm); note_launch();
-    GKS_CUDA(cudaGetLastError());
-    if ((st = read_ctl(m, s)) != GKS_OK) return st;
+    gks_status st;
 
-    while (k.h_ctl[0] | k.h_ctl[1] | k.h_ctl[2] | k.h_ctl[3]) {
-        k_init_v0<<<std::max(nb, nblocks(NV * (mm + 1))), kBlock, 0, s>>>(T, k.r, k.V, k.beta, k.ctl, k.g, mm); note_launch();
+    k_rhs<<<nb, kBlock, 0, s>>>(d, k.w, k.b); note_launch();
+    k_spmv<double, double><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, k.r, 1, k.b, k.part, ps);
+    note_launch();
+    k_reduce<<<dim3(2, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.hcol, ps, 0); note_launch();
+    k_start<<<sblocks(ns), 128, 0, s>>>(k.hcol, ps, k.bnorm, k.beta, k.ctl, ns, k.done, rtol, maxit, 1); note_launch();
+    k_zero_trivial<<<nb, kBlock, 0, s>>>(d, k.x, k.bnorm); note_launch();
+    GKS_CUDA(cudaGetLastError());
+    if ((st = read_flags(m, s)) != GKS_OK) return st;
+
+    while (k.h_flags[0]) {
+        k_init_v0<<<nb, kBlock, 0, s>>>(d, k.r, k.V, k.beta, k.ctl, ns); note_launch();
+        k_init_g<<<sblocks(ns * (mm + 1)), 128, 0, s>>>(k.g, mm, k.beta, k.ctl, ns); note_launch();
         for (int j = 0; j < mm; ++j) {
             double *vj = k.V + j * vs, *vj1 = k.V + (j + 1) * vs;
             int slot = prof_start(m, kProfIlu, s);
-            if ((st = mixed ? precond32(m, vj, k.t32, s) : precond(m, vj, k.t, s)) != GKS_OK) return st;
+            // Z_j = M^{-1} V_j, kept for the update of x at the end of the cycle
+            if ((st = mixed ? precond32(m, vj, k.Z32 + j * vs, s) : precond(m, vj, k.Z + j * vs, s)) != GKS_OK)
+                return st;
             prof_stop(m, slot, s);
             slot = prof_start(m, kProfSpmv, s);
             if (mixed)
-                k_spmv<float, float><<<nb, kBlock, 0, s>>>(d, d.D32, d.alpha32, d.ex32, d.ey32, k.t32, vj1, 0, nullptr,
-                                                           nullptr, 0);
+                k_spmv<float, float><<<nb, kBlock, 0, s>>>(d, d.D32, d.alpha32, d.ex32, d.ey32, k.Z32 + j * vs, vj1, 0,
+                                                           nullptr, nullptr, 0);
             else
-                k_spmv<double, double><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.t, vj1, 0, nullptr, nullptr,
-                                                             0);
+                k_spmv<double, double><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.Z + j * vs, vj1, 0, nullptr,
+                                                             nullptr, 0);
             note_launch();
             prof_stop(m, slot, s);
             slot = prof_start(m, kProfOrth, s);
-            // classical Gram-Schmidt, twice
-            k_dots<<<nb, kBlock, 0, s>>>(T, k.V, vj1, j, k.part, ps); note_launch();
-            k_reduce<<<dim3(j + 1, NV), kBlock, 0, s>>>(k.part, k.nblk, ps, k.hcol, ps, 0); note_launch();
-            k_orth_update<<<nb, kBlock, 0, s>>>(T, k.V, vj1, j, k.hcol, ps, k.ctl, k.part, ps, 0); note_launch();
-            k_dots<<<nb, kBlock, 0, s>>>(T, k.V, vj1, j, k.part, ps); note_launch();
-            k_reduce<<<dim3(j + 1, NV), kBlock, 0, s>>>(k.part, k.nblk, ps, k.y, mm, 0); note_launch();   // second-pass coefficients
-            k_orth_update<<<nb, kBlock, 0, s>>>(T, k.V, vj1, j, k.y, mm, k.ctl, k.part, ps, 1); note_launch();
-            k_reduce<<<dim3(1, NV), kBlock, 0, s>>>(k.part, k.nblk, ps, k.hcol + j + 1, ps, 2); note_launch();
-            k_hadd<<<1, 128, 0, s>>>(k.hcol, ps, k.y, mm, j); note_launch();
+            // classical Gram-Schmidt: twice in FP64 mode; once in the mixed mode, whose
+            // cycles only reduce the residual by kInnerRtol before an FP64 restart
+            if ((st = dots(m, vj1, j, k.part, ps, s)) != GKS_OK) return st;
+            k_reduce<<<dim3(j + 1, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.hcol, ps, 0); note_launch();
+            k_orth_update<<<nb, kBlock, 0, s>>>(d, k.V, vj1, j, k.hcol, ps, k.ctl, ns, k.part, ps, mixed ? 1 : 0);
+            note_launch();
+            if (!mixed) {
+                if ((st = dots(m, vj1, j, k.part, ps, s)) != GKS_OK) return st;
+                k_reduce<<<dim3(j + 1, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.y, mm, 0); note_launch();
+                k_orth_update<<<nb, kBlock, 0, s>>>(d, k.V, vj1, j, k.y, mm, k.ctl, ns, k.part, ps, 1); note_launch();
+                k_hadd<<<sblocks(ns * (j + 1)), 128, 0, s>>>(k.hcol, ps, k.y, mm, j, ns); note_launch();
+            }
+            k_reduce<<<dim3(1, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.hcol + j + 1, ps, 2); note_launch();
             prof_stop(m, slot, s);
-            k_scale<<<nb, kBlock, 0, s>>>(T, vj1, k.hcol, ps, j, k.ctl); note_launch();
-            k_givens<<<1, 32, 0, s>>>(j, mm, k.hcol, ps, k.H, k.cs, k.sn, k.g, k.ctl, k.bnorm, k.beta, rtol, eta, maxit);
+            k_scale<<<nb, kBlock, 0, s>>>(d, vj1, k.hcol, ps, j, k.ctl, ns); note_launch();
+            k_givens<<<sblocks(ns), 128, 0, s>>>(j, mm, k.hcol, ps, k.H, k.cs, k.sn, k.g, k.ctl, ns, k.bnorm, k.beta,
+                                                  rtol, eta, maxit);
             note_launch();
             GKS_CUDA(cudaGetLastError());
-            if ((st = read_ctl(m, s)) != GKS_OK) return st;
-            if (!(k.h_ctl[4] | k.h_ctl[5] | k.h_ctl[6] | k.h_ctl[7])) break;
+            if ((st = read_flags(m, s)) != GKS_OK) return st;
+            if (!k.h_flags[1]) break;
         }
-        k_backsolve<<<1, 32, 0, s>>>(mm, k.H, k.g, k.y, k.ctl); note_launch();
-        k_combine<<<nb, kBlock, 0, s>>>(T, k.V, k.y, mm, k.ctl, k.r); note_launch();
-        if (mixed) {
-            if ((st = precond32(m, k.r, k.t32, s)) != GKS_OK) return st;
-            k_addx<float><<<nb, kBlock, 0, s>>>(T, k.x, k.t32, k.ctl);
-        } else {
-            if ((st = precond(m, k.r, k.t, s)) != GKS_OK) return st;
-            k_addx<double><<<nb, kBlock, 0, s>>>(T, k.x, k.t, k.ctl);
-        }
+        k_backsolve<<<sblocks(ns), 128, 0, s>>>(mm, k.H, k.g, k.y, k.ctl, ns); note_launch();
+        if (mixed)
+            k_combine_z<float><<<nb, kBlock, 0, s>>>(d, k.Z32, k.y, mm, k.ctl, ns, k.x);
+        else
+            k_combine_z<double><<<nb, kBlock, 0, s>>>(d, k.Z, k.y, mm, k.ctl, ns, k.x);
         note_launch();
         k_spmv<double, double><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, k.r, 1, k.b, k.part, ps);
         note_launch();
-        k_reduce<<<dim3(2, NV), kBlock, 0, s>>>(k.part, k.nblk, ps, k.hcol, ps, 0); note_launch();
-        k_start<<<1, 32, 0, s>>>(k.hcol, ps, k.bnorm, k.beta, k.ctl, rtol, maxit, 0); note_launch();
+        k_reduce<<<dim3(2, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.hcol, ps, 0); note_launch();
+        k_start<<<sblocks(ns), 128, 0, s>>>(k.hcol, ps, k.bnorm, k.beta, k.ctl, ns, k.done, rtol, maxit, 0);
+        note_launch();
         GKS_CUDA(cudaGetLastError());
-        if ((st = read_ctl(m, s)) != GKS_OK) return st;
-        if (!(k.h_ctl[0] | k.h_ctl[1] | k.h_ctl[2] | k.h_ctl[3])) break;
+        if ((st = read_flags(m, s)) != GKS_OK) return st;
     }
-    if (info) {
-        GKS_CUDA(cudaMemcpyAsync(k.h_scal, k.beta, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
-        GKS_CUDA(cudaMemcpyAsync(k.h_scal + 4, k.bnorm, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+    k_mark_noconv<<<sblocks(ns), 128, 0, s>>>(k.bnorm, k.beta, k.done, ns, rtol, k.status); note_launch();
+    if (iters || relres || converged) {
+        std::vector<int32_t> it(ns);
+        std::vector<double> be(ns), bn(ns);
+        GKS_CUDA(cudaMemcpyAsync(it.data(), k.ctl + kCtlIters * ns, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost, s));
+        GKS_CUDA(cudaMemcpyAsync(be.data(), k.beta, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));
+        GKS_CUDA(cudaMemcpyAsync(bn.data(), k.bnorm, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));
         GKS_CUDA(cudaStreamSynchronize(s));
-        info->converged = 1;
-        for (int v = 0; v < NV; ++v) {
-            info->iters[v] = k.h_ctl[12 + v];
-            info->relres[v] = k.h_scal[4 + v] > 0.0 ? k.h_scal[v] / k.h_scal[4 + v] : 0.0;
-            if (info->relres[v] > rtol) info->converged = 0;
+        int32_t conv = 1;
+        for (int q = 0; q < ns; ++q) {
+            const double rr = bn[q] > 0.0 ? be[q] / bn[q] : 0.0;
+            if (iters) iters[q] = it[q];
+            if (relres) relres[q] = rr;
+            if (rr > rtol) conv = 0;
         }
+        if (converged) *converged = conv;
     }
     return GKS_OK;
 }

@@ -60,6 +60,104 @@ __device__ __forceinline__ void to_face(const double *g, double nx, double ny, d
     }
 }
 
+// Mixed precision reconstruction: FP64 values, FP32 derivative rows (global frame).
+__device__ __forceinline__ void recon_mixed(const DeviceMesh &d, const double *__restrict__ w,
+                                            const double *__restrict__ x, int c, double dx, double dy, double *val,
+                                            float *der)
+{
+    const int64_t T = d.T;
+    const double qx = dx * dx - d.mxx[c], qxy = dx * dy - d.mxy[c], qy = dy * dy - d.myy[c];
+    const float ih = float(1.0 / d.h[c]);
+    const float fx = float(dx), fy = float(dy);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const double u1 = x[(v * 5 + 0) * T + c], u2 = x[(v * 5 + 1) * T + c], u3 = x[(v * 5 + 2) * T + c];
+        const double u4 = x[(v * 5 + 3) * T + c], u5 = x[(v * 5 + 4) * T + c];
+        val[v] = w[v * T + c] + u1 * dx + u2 * dy + 0.5 * u3 * qx + u4 * qxy + 0.5 * u5 * qy;
+        const float f1 = float(u1), f2 = float(u2), f3 = float(u3), f4 = float(u4), f5 = float(u5);
+        der[v] = (f1 + f3 * fx + f4 * fy) * ih;
+        der[4 + v] = (f2 + f4 * fx + f5 * fy) * ih;
+        der[8 + v] = f3 * ih * ih;
+        der[12 + v] = f4 * ih * ih;
+        der[16 + v] = f5 * ih * ih;
+    }
+}
+
+// Face frame of FP64 values (momentum) and FP32 derivative rows (directions and momentum).
+__device__ __forceinline__ void to_face_mixed(double *val, float *der, double nx, double ny)
+{
+    const double mx = val[1], my = val[2];
+    val[1] = nx * mx + ny * my;
+    val[2] = -ny * mx + nx * my;
+    const float fnx = float(nx), fny = float(ny), tx = -fny, ty = fnx;
+    float o[20];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const float gx = der[v], gy = der[4 + v], gxx = der[8 + v], gxy = der[12 + v], gyy = der[16 + v];
+        o[v] = fnx * gx + fny * gy;
+        o[4 + v] = tx * gx + ty * gy;
+        o[8 + v] = fnx * fnx * gxx + 2.0f * fnx * fny * gxy + fny * fny * gyy;
+        o[12 + v] = fnx * tx * gxx + (fnx * ty + fny * tx) * gxy + fny * ty * gyy;
+        o[16 + v] = tx * tx * gxx + 2.0f * tx * ty * gxy + ty * ty * gyy;
+    }
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+        const float a = o[4 * r + 1], b = o[4 * r + 2];
+        der[4 * r + 0] = o[4 * r + 0];
+        der[4 * r + 1] = fnx * a + fny * b;
+        der[4 * r + 2] = tx * a + ty * b;
+        der[4 * r + 3] = o[4 * r + 3];
+    }
+}
+
+// Ghost state of a boundary face for the split (FP64 values, FP32 derivatives) layout.
+__device__ __forceinline__ void ghost_mixed(int tag, const double *bc, double nx, double ny, double gamma,
+                                            const double *vl, const float *dl, double *vr, float *dr)
+{
+    if (tag == GKS_BC_DIRICHLET) {
+        vr[0] = bc[0];
+        vr[1] = nx * bc[1] + ny * bc[2];
+        vr[2] = -ny * bc[1] + nx * bc[2];
+        vr[3] = bc[3];
+#pragma unroll
+        for (int q = 0; q < 20; ++q) dr[q] = 0.0f;
+        return;
+    }
+    if (tag == GKS_BC_OUTFLOW) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) vr[q] = vl[q];
+#pragma unroll
+        for (int q = 0; q < 20; ++q) dr[q] = dl[q];
+        return;
+    }
+    const bool noslip = tag == GKS_BC_NOSLIP;
+    const int npar[5] = {1, 0, 0, 1, 0};   // parity of the n-order of rows d/dn .. d2/dt2
+#pragma unroll
+    for (int r = 0; r < 5; ++r)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            float sg = (v == 1 || (noslip && v == 2)) ? -1.0f : 1.0f;
+            if (npar[r]) sg = -sg;
+            dr[4 * r + v] = sg * dl[4 * r + v];
+        }
+    if (noslip) {
+        const double rho = vl[0], un = vl[1] / rho, ut = vl[2] / rho;
+        const double p = (gamma - 1.0) * (vl[3] - 0.5 * rho * (un * un + ut * ut));
+        const double uwn = nx * bc[0] + ny * bc[1], uwt = -ny * bc[0] + nx * bc[1];
+        const double tg = 2.0 * bc[2] - p / rho;
+        const double gn = 2.0 * uwn - un, gt = 2.0 * uwt - ut;
+        vr[0] = rho;
+        vr[1] = rho * gn;
+        vr[2] = rho * gt;
+        vr[3] = rho * tg / (gamma - 1.0) + 0.5 * rho * (gn * gn + gt * gt);
+    } else {
+        vr[0] = vl[0];
+        vr[1] = -vl[1];
+        vr[2] = vl[2];
+        vr[3] = vl[3];
+    }
+}
+
 // Ghost right state of a boundary face (face frame).
 __device__ __forceinline__ void ghost(int tag, const double *bc, double nx, double ny, double gamma,
                                       const double *wl, double *wr)
@@ -113,26 +211,42 @@ __global__ void __launch_bounds__(kFluxBlock) k_face_flux(DeviceMesh d, const do
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t f = g >> 1;
     const int k = (int)(g & 1);
-    const bool valid = f < F;
+    const int cs = f < F ? d.face_case[f] : 0;
+    const double dt = f < F ? (dt_dev ? dt_dev[cs] : dt_const) : 0.0;
+    const bool valid = f < F && dt > 0.0;       // cases with dt = 0 are not advanced
     double out[4] = {0.0, 0.0, 0.0, 0.0};
     if (valid) {
-        const double dt = dt_dev ? *dt_dev : dt_const;
         const double nx = d.fnx[f], ny = d.fny[f];
         const int l = d.fl[f], r = d.fr[f];
-        double gl[24], wl[24], wr[24];
-        recon(d, w, x, l, d.gl[(2 * k) * F + f], d.gl[(2 * k + 1) * F + f], gl);
-        to_face(gl, nx, ny, wl);
-        if (r >= 0) {
-            recon(d, w, x, r, d.gr[(2 * k) * F + f], d.gr[(2 * k + 1) * F + f], gl);
-            to_face(gl, nx, ny, wr);
-        } else {
-            const double bc[4] = {d.bc[f], d.bc[F + f], d.bc[2 * F + f], d.bc[3 * F + f]};
-            ghost(d.ftag[f], bc, nx, ny, gamma, wl, wr);
-        }
         double fk[4];
-        const bool ok = MIXED ? kin::gp_flux_mixed(wl, wr, dt, gamma, mu, tau2, fk)
-                              : kin::gp_flux<double>(wl, wr, dt, gamma, mu, tau2, fk);
-        if (!ok) atomicOr(status, kStatusNonPhys);
+        bool ok;
+        if (MIXED) {
+            double vl[4], vr[4];
+            float dl[20], dr[20];
+            recon_mixed(d, w, x, l, d.gl[(2 * k) * F + f], d.gl[(2 * k + 1) * F + f], vl, dl);
+            to_face_mixed(vl, dl, nx, ny);
+            if (r >= 0) {
+                recon_mixed(d, w, x, r, d.gr[(2 * k) * F + f], d.gr[(2 * k + 1) * F + f], vr, dr);
+                to_face_mixed(vr, dr, nx, ny);
+            } else {
+                const double bc[4] = {d.bc[f], d.bc[F + f], d.bc[2 * F + f], d.bc[3 * F + f]};
+                ghost_mixed(d.ftag[f], bc, nx, ny, gamma, vl, dl, vr, dr);
+            }
+            ok = kin::gp_flux_mixed_split(vl, vr, dl, dr, dt, gamma, mu, tau2, fk);
+        } else {
+            double gl[24], wl[24], wr[24];
+            recon(d, w, x, l, d.gl[(2 * k) * F + f], d.gl[(2 * k + 1) * F + f], gl);
+            to_face(gl, nx, ny, wl);
+            if (r >= 0) {
+                recon(d, w, x, r, d.gr[(2 * k) * F + f], d.gr[(2 * k + 1) * F + f], gl);
+                to_face(gl, nx, ny, wr);
+            } else {
+                const double bc[4] = {d.bc[f], d.bc[F + f], d.bc[2 * F + f], d.bc[3 * F + f]};
+                ghost(d.ftag[f], bc, nx, ny, gamma, wl, wr);
+            }
+            ok = kin::gp_flux<double>(wl, wr, dt, gamma, mu, tau2, fk);
+        }
+        if (!ok) atomicOr(&status[cs], kStatusNonPhys);
         const double s = 0.5 * d.flen[f];      // Gauss weight 1/2 times the face length
         out[0] = s * fk[0];
         out[1] = s * (nx * fk[1] - ny * fk[2]);
@@ -141,7 +255,7 @@ __global__ void __launch_bounds__(kFluxBlock) k_face_flux(DeviceMesh d, const do
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) out[q] += __shfl_xor_sync(0xffffffffu, out[q], 1);
-    if (valid && k == 0)
+    if (f < F && k == 0)
 #pragma unroll
         for (int q = 0; q < 4; ++q) flux[q * F + f] = out[q];
 }
@@ -171,7 +285,7 @@ __global__ void k_update(DeviceMesh d, double *__restrict__ w, const double *__r
         w[v * T + i] = wn[v];
     }
     const double p = (gamma - 1.0) * (wn[3] - 0.5 * (wn[1] * wn[1] + wn[2] * wn[2]) / wn[0]);
-    if (!(wn[0] > 0.0) || !(p > 0.0)) atomicOr(status, kStatusNonPhys);
+    if (!(wn[0] > 0.0) || !(p > 0.0)) atomicOr(&status[d.blk_case[blockIdx.x]], kStatusNonPhys);
 }
 
 // Per-cell CFL bound, block minimum.
@@ -199,18 +313,35 @@ __global__ void k_cfl_partial(DeviceMesh d, const double *__restrict__ w, double
     if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-__global__ void k_min_final(const double *__restrict__ part, int n, double scale, double *out)
+// out[c] = scale * min of the block minima of case c (one block per case)
+__global__ void k_min_final(const double *__restrict__ part, const int32_t *__restrict__ case_blk, double scale,
+                            double *out)
 {
     __shared__ double sh[kBlock];
+    const int c = blockIdx.x;
     double m = DBL_MAX;
-    for (int b = threadIdx.x; b < n; b += blockDim.x) m = fmin(m, part[b]);
+    for (int b = case_blk[c] + threadIdx.x; b < case_blk[c + 1]; b += blockDim.x) m = fmin(m, part[b]);
     sh[threadIdx.x] = m;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + o]);
         __syncthreads();
     }
-    if (threadIdx.x == 0) *out = scale * sh[0];
+    if (threadIdx.x == 0) out[c] = scale * sh[0];
+}
+
+// Per-case step control: dt = min(cfl step, t_final - t), 0 once done; t += dt.
+__global__ void k_clip_dt(double *dt, double *t, const double *__restrict__ tf, int32_t *done, int n)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    if (done[c] || (tf[c] > 0.0 && t[c] >= tf[c] * (1.0 - 1e-14))) {
+        done[c] = 1;
+        dt[c] = 0.0;
+        return;
+    }
+    if (tf[c] > 0.0) dt[c] = fmin(dt[c], tf[c] - t[c]);
+    t[c] += dt[c];
 }
 
 template <bool MIXED>
@@ -233,15 +364,17 @@ __global__ void __launch_bounds__(kFluxBlock) k_point_flux(int64_t n, const doub
     for (int k = 0; k < 4; ++k) out[4 * q + k] = f[k];
 }
 
+// Internal rows [nvar][n] <-> caller rows [nvar][nc]; padding (perm < 0) untouched.
 __global__ void k_permute(const double *__restrict__ src, double *__restrict__ dst, const int32_t *__restrict__ perm,
-                          int64_t n, int nvar, int gather)
+                          int64_t n, int64_t nc, int nvar, int gather)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t p = perm[i];
+    if (p < 0) return;
     for (int v = 0; v < nvar; ++v) {
-        if (gather) dst[v * n + i] = src[v * n + p];
-        else dst[v * n + p] = src[v * n + i];
+        if (gather) dst[v * n + i] = src[v * nc + p];
+        else dst[v * nc + p] = src[v * n + i];
     }
 }
 
@@ -323,7 +456,7 @@ gks_status launch_cfl_dt(gks_mesh *m, const double *w, double *dt_dev, cudaStrea
 {
     const unsigned nb = blocks(m->d.T, kBlock);
     k_cfl_partial<<<nb, kBlock, 0, s>>>(m->d, w, m->cfg.gamma, m->cfg.mu, m->wk.dpart); note_launch();
-    k_min_final<<<1, kBlock, 0, s>>>(m->wk.dpart, (int)nb, m->cfg.cfl, dt_dev); note_launch();
+    k_min_final<<<m->d.ncase, kBlock, 0, s>>>(m->wk.dpart, m->d.case_blk, m->cfg.cfl, dt_dev); note_launch();
     GKS_CUDA(cudaGetLastError());
     return GKS_OK;
 }
@@ -343,10 +476,18 @@ gks_status launch_point_flux(int64_t n, const double *wl, const double *wr, doub
     return GKS_OK;
 }
 
-gks_status launch_permute(const double *src, double *dst, const int32_t *perm, int64_t n, int nvar, bool gather,
-                          cudaStream_t s)
+gks_status launch_permute(const double *src, double *dst, const int32_t *perm, int64_t n, int64_t ncaller, int nvar,
+                          bool gather, cudaStream_t s)
 {
-    k_permute<<<blocks(n, kBlock), kBlock, 0, s>>>(src, dst, perm, n, nvar, gather ? 1 : 0); note_launch();
+    k_permute<<<blocks(n, kBlock), kBlock, 0, s>>>(src, dst, perm, n, ncaller, nvar, gather ? 1 : 0); note_launch();
+    GKS_CUDA(cudaGetLastError());
+    return GKS_OK;
+}
+
+gks_status launch_clip_dt(gks_mesh *m, cudaStream_t s)
+{
+    const int n = m->d.ncase;
+    k_clip_dt<<<(n + 127) / 128, 128, 0, s>>>(m->wk.dt, m->wk.tcase, m->wk.tfinal, m->wk.done, n); note_launch();
     GKS_CUDA(cudaGetLastError());
     return GKS_OK;
 }

@@ -1,4 +1,10 @@
 // Internal declarations of the GB300 gas-kinetic library (not installed).
+//
+// A handle holds one or more independent cases (meshes).  Their cells are
+// stored one case after the other, each case in its own RCM order and padded
+// to a whole number of kBlock-cell blocks, so that every block of a cell kernel
+// belongs to exactly one case and every reduction is a segmented one.  A
+// single mesh is the one-case instance (no padding).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -12,7 +18,7 @@
 
 namespace gks {
 
-constexpr int kBlock = 256;          // threads per block of the cell/face kernels
+constexpr int kBlock = 256;          // cells per block of the cell kernels (and padding unit)
 constexpr int kMaxRestart = 64;      // upper bound on gmres_m
 
 void set_error(const char *fmt, ...);
@@ -34,15 +40,22 @@ inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); 
 // Kernel classes timed by the optional CUDA-event profiler.
 enum : int { kProfFlux = 0, kProfSpmv = 1, kProfIlu = 2, kProfOrth = 3, kProfUpdate = 4, kProfClasses = 5 };
 
-// Device status bits (a word the kernels OR into).
-enum : int { kStatusNonPhys = 1 };
+// Device status bits (per case words the kernels OR into).
+enum : int { kStatusNonPhys = 1, kStatusNoConv = 2 };
 
-// Device data of one mesh, all in RCM ("internal") cell order.
+// GMRES control words, ctl[field * ns + system] with system = case * 4 + variable.
+enum : int { kCtlActive = 0, kCtlRunning = 1, kCtlJv = 2, kCtlIters = 3, kCtlFields = 4 };
+
+// Device data, all in internal (per-case RCM, padded) cell order.
 struct DeviceMesh {
-    int64_t T = 0, F = 0;
+    int64_t T = 0, F = 0;            // internal cells (with padding) and faces
+    int32_t ncase = 1;
+    int32_t *blk_case = nullptr;     // [T / kBlock rounded up] case of each cell block
+    int32_t *case_blk = nullptr;     // [ncase + 1] first cell block of each case
+    int32_t *face_case = nullptr;    // [F] case of each face
     // cells
     double *area = nullptr, *inv_area = nullptr, *h = nullptr, *mxx = nullptr, *mxy = nullptr, *myy = nullptr;
-    double *inrad = nullptr;
+    double *inrad = nullptr;         // padding cells: +inf (never limit the step)
     int32_t *nb = nullptr;           // [3][T] neighbour (internal index) or -1
     double *alpha = nullptr;         // [3][T] w^2 h_i / h_j
     double *ex = nullptr, *ey = nullptr;  // [3][T] centroid offsets of j in i's frame (0 when k_i = 1)
@@ -52,9 +65,9 @@ struct DeviceMesh {
     // FP32 copies of the operator and factors (mixed precision)
     float *D32 = nullptr, *P32 = nullptr, *alpha32 = nullptr, *ex32 = nullptr, *ey32 = nullptr;
     int32_t *cf = nullptr;           // [3][T] (face << 1) | side, -1 unused
-    int32_t *perm = nullptr;         // [T] internal -> caller cell
-    int32_t *lvl_lo = nullptr;       // [T] rows sorted by forward level
-    int32_t *lvl_up = nullptr;       // [T] rows sorted by backward level
+    int32_t *perm = nullptr;         // [T] internal -> caller cell (-1 for padding)
+    int32_t *lvl_lo = nullptr;       // rows sorted by forward level
+    int32_t *lvl_up = nullptr;       // rows sorted by backward level
     // faces (internal order)
     int32_t *fl = nullptr, *fr = nullptr, *ftag = nullptr;
     int32_t *fperm = nullptr;        // [F] internal -> caller face
@@ -66,29 +79,36 @@ struct DeviceMesh {
 
 struct Work {
     int m = 0;                       // restart length
-    int nblk = 0;                    // blocks of the cell kernels
+    int nblk = 0;                    // cell blocks (kBlock cells each)
+    int ns = 4;                      // GMRES systems: 4 per case
     double *w = nullptr;             // [4][T] state (internal order)
     double *w_old = nullptr;         // [4][T]
     double *x = nullptr;             // [20][T] CLS coefficients (warm start)
-    double *b = nullptr, *r = nullptr, *t = nullptr, *t2 = nullptr, *t3 = nullptr;  // [20][T]
-    float *t32 = nullptr, *t2_32 = nullptr, *t3_32 = nullptr;  // [20][T] FP32 preconditioner work
+    double *b = nullptr, *r = nullptr, *t2 = nullptr, *t3 = nullptr;  // [20][T]
+    float *t2_32 = nullptr, *t3_32 = nullptr;  // [20][T] FP32 preconditioner work
     double *V = nullptr;             // [(m+1)][20][T]
+    double *Z = nullptr;             // [m][20][T] preconditioned basis M^{-1} V_k (FP64 path)
+    float *Z32 = nullptr;            // [m][20][T] preconditioned basis (mixed path)
     double *flux = nullptr;          // [4][F]
-    double *part = nullptr;          // [nblk][4][m+2] partial sums
-    double *dpart = nullptr;         // [nblk] partial minima / sums
-    // small GMRES state (device)
-    double *H = nullptr;             // [4][m+1][m]  (Givens-rotated Hessenberg)
-    double *cs = nullptr, *sn = nullptr;  // [4][m]
-    double *g = nullptr;             // [4][m+1]
-    double *y = nullptr;             // [4][m]
-    double *hcol = nullptr;          // [4][m+2]
-    double *bnorm = nullptr, *beta = nullptr;  // [4]
-    int32_t *ctl = nullptr;          // [4][4]: active, running, jv, iters
-    double *dt = nullptr;            // [1]
+    double *part = nullptr;          // [nblk][4][m+2] partial sums per cell block
+    double *dpart = nullptr;         // [nblk][4] partial minima / sums
+    // small GMRES state (device), one row per system
+    double *H = nullptr;             // [ns][m+1][m]  (Givens-rotated Hessenberg)
+    double *cs = nullptr, *sn = nullptr;  // [ns][m]
+    double *g = nullptr;             // [ns][m+1]
+    double *y = nullptr;             // [ns][m]
+    double *hcol = nullptr;          // [ns][m+2]
+    double *bnorm = nullptr, *beta = nullptr;  // [ns]
+    int32_t *ctl = nullptr;          // [kCtlFields][ns]
+    int32_t *flags = nullptr;        // [4]: any active, any running, all cases done
+    double *dt = nullptr;            // [ncase] step of each case (0: case inactive)
+    double *tcase = nullptr;         // [ncase] time reached
+    double *tfinal = nullptr;        // [ncase] end time (<= 0: none)
+    int32_t *done = nullptr;         // [ncase] case finished or stopped
     double *scal = nullptr;          // [8] misc device scalars
-    int32_t *status = nullptr;       // [1]
-    // pinned host mirror
-    int32_t *h_ctl = nullptr;        // [16 + 4]
+    int32_t *status = nullptr;       // [ncase] status bits
+    // pinned host mirrors
+    int32_t *h_flags = nullptr;      // [4]
     double *h_scal = nullptr;        // [8]
 };
 
@@ -99,14 +119,15 @@ struct gks_profiler {
     std::vector<cudaEvent_t> events;                // pool
     size_t used = 0;
     std::vector<int> cls;                           // class of each start/stop pair
-    int64_t count[gks::kProfClasses] = {0};
 };
 
 struct gks_mesh {
     gks_config cfg{};
     gks_profiler prof;
     int device = 0;
-    int64_t n_tri = 0, n_face = 0, n_bface = 0, n_k1 = 0, nnzb = 0, bandwidth = 0;
+    int32_t n_case = 1;
+    int64_t n_tri = 0, n_face = 0, n_bface = 0, n_k1 = 0, nnzb = 0, bandwidth = 0;  // caller totals
+    std::vector<int64_t> case_tri, case_face;      // caller sizes per case
     std::vector<int32_t> lvl_lo_ptr, lvl_up_ptr;   // level offsets (host)
     gks::DeviceMesh d;
     gks::Work wk;
@@ -116,13 +137,26 @@ struct gks_mesh {
 
 namespace gks {
 
+// One case as given to the ABI (host arrays).
+struct CaseIn {
+    const double *nodes;
+    int64_t n_nodes;
+    const int32_t *tris;
+    int64_t n_tri;
+    const int32_t *faces;
+    const double *face_shift;
+    int64_t n_face;
+    const double *bc_state;
+};
+
 // set-up (gks_setup.cu)
-gks_status build_mesh(gks_mesh *m, const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t n_tri,
-                      const int32_t *faces, const double *face_shift, int64_t n_face, const double *bc_state);
+gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases);
 void free_mesh(gks_mesh *m);
 
-// CLS reconstruction (gks_cls.cu): rhs from m->wk.w, solution in m->wk.x
-gks_status cls_solve(gks_mesh *m, cudaStream_t s, gks_solve_info *info);
+// CLS reconstruction (gks_cls.cu): rhs from m->wk.w, solution in m->wk.x.
+// Per system (case * 4 + variable, may be NULL): iterations, relative residuals;
+// *converged = 1 if every active system met the tolerance.
+gks_status cls_solve(gks_mesh *m, cudaStream_t s, int32_t *iters, double *relres, int32_t *converged);
 
 // flux and update (gks_flux.cu)
 gks_status launch_flux(gks_mesh *m, const double *w, const double *x, double dt_const, const double *dt_dev,
@@ -131,9 +165,12 @@ gks_status launch_update(gks_mesh *m, double *w, const double *flux, cudaStream_
 gks_status launch_cfl_dt(gks_mesh *m, const double *w, double *dt_dev, cudaStream_t s);
 gks_status launch_point_flux(int64_t n, const double *wl, const double *wr, double dt, const gks_config &cfg,
                              double *out, int32_t *status, cudaStream_t s);
-gks_status launch_permute(const double *src, double *dst, const int32_t *perm, int64_t n, int nvar, bool gather,
-                          cudaStream_t s);
+// gather (internal[v][i] = caller[v][perm[i]], padding untouched) or scatter
+gks_status launch_permute(const double *src, double *dst, const int32_t *perm, int64_t n, int64_t ncaller, int nvar,
+                          bool gather, cudaStream_t s);
 gks_status launch_steady_partial(gks_mesh *m, cudaStream_t s);
+// per-case step control for runs: dt = min(cfl dt, t_final - t) or 0 when done; t += dt
+gks_status launch_clip_dt(gks_mesh *m, cudaStream_t s);
 
 // optional CUDA-event timing of one kernel class (no-op unless enabled)
 int prof_start(gks_mesh *m, int cls, cudaStream_t s);

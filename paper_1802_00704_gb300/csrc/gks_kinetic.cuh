@@ -515,36 +515,114 @@ __device__ __forceinline__ void kstate_cast(const KState<A> &a, KState<B> &b)
     b.p = B(a.p);
 }
 
-// Mixed precision: interface state, collision time, time integrals and the
-// leading terms in FP64; every slope-carrying term in FP32.
-__device__ __forceinline__ bool gp_flux_mixed(const double *wl, const double *wr, double dt, double gamma, double mu,
-                                              int tau2_exact, double *f)
+// Primitive state from the FP64 values with one reciprocal.
+__device__ __forceinline__ bool prim64(const double *w, double gamma, double K, KState<double> &s)
 {
-    Iface<double> I;
-    if (!interface_state(wl, wr, dt, gamma, mu, tau2_exact, I)) {
+    s.rho = w[0];
+    const double ir = 1.0 / w[0];
+    s.U = w[1] * ir;
+    s.V = w[2] * ir;
+    const double eint = w[3] - 0.5 * s.rho * (s.U * s.U + s.V * s.V);
+    s.p = (gamma - 1.0) * eint;
+    s.lam = 0.25 * (K + 2.0) * s.rho / eint;
+    return s.rho > 0.0 && s.p > 0.0;
+}
+
+// Half-space moments <u^k>, k = 0..3, in FP64 (sign = +1: u > 0, -1: u < 0).
+__device__ __forceinline__ void mom_half4(double U, double lam, double sign, double *m)
+{
+    const double h = 0.5 / lam;
+    const double sl = sqrt(lam);
+    m[0] = 0.5 * erfc(-sign * sl * U);
+    m[1] = U * m[0] + sign * 0.5 * exp(-lam * U * U) / (sl * 1.7724538509055160273);
+    m[2] = U * m[1] + h * m[0];
+    m[3] = U * m[2] + 2.0 * h * m[1];
+}
+
+// Mixed precision Gauss-point flux.  vl, vr: FP64 face-frame values
+// (rho, rho U, rho V, E); dl, dr: FP32 face-frame derivative rows [5][4]
+// (d/dn, d/dt, d2/dn2, d2/dndt, d2/dt2).  The interface state W0, the
+// collision time, the time integrals and the zeroth-order terms
+// C1 rho0 <u psi>_0 + C7 (rho_l <u psi>_{u>0} + rho_r <u psi>_{u<0}) are FP64;
+// every slope-carrying term is FP32.
+__device__ __forceinline__ bool gp_flux_mixed_split(const double *vl, const double *vr, const float *dl, const float *dr,
+                                                    double dt, double gamma, double mu, int tau2_exact, double *f)
+{
+    const double K = 2.0 / (gamma - 1.0) - 2.0;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) f[q] = 0.0;
-        return false;
+    for (int q = 0; q < 4; ++q) f[q] = 0.0;
+    KState<double> L, Rs, Z;
+    if (!(prim64(vl, gamma, K, L) & prim64(vr, gamma, K, Rs))) return false;
+    double ml[4], mr[4];
+    mom_half4(L.U, L.lam, 1.0, ml);
+    mom_half4(Rs.U, Rs.lam, -1.0, mr);
+    const double hl = 0.5 / L.lam, hr = 0.5 / Rs.lam;
+    const double v2l = L.V * L.V + hl, v2r = Rs.V * Rs.V + hr;
+    const double zl = 0.5 * K / L.lam, zr = 0.5 * K / Rs.lam;
+    double w0[4];
+    w0[0] = L.rho * ml[0] + Rs.rho * mr[0];
+    w0[1] = L.rho * ml[1] + Rs.rho * mr[1];
+    w0[2] = L.rho * ml[0] * L.V + Rs.rho * mr[0] * Rs.V;
+    w0[3] = L.rho * 0.5 * (ml[2] + ml[0] * (v2l + zl)) + Rs.rho * 0.5 * (mr[2] + mr[0] * (v2r + zr));
+    if (!prim64(w0, gamma, K, Z)) return false;
+    const double jump = fabs(L.p - Rs.p) / fabs(L.p + Rs.p);
+    const double tau = mu > 0.0 ? mu / Z.p + dt * jump : 0.01 * dt + dt * jump;
+    double C[9];
+    time_integrals(dt, tau, tau2_exact, C);
+    // leading terms (FP64)
+    {
+        const double h = 0.5 / Z.lam;
+        const double m2 = Z.U * Z.U + h, m3 = Z.U * m2 + 2.0 * h * Z.U;
+        const double v2 = Z.V * Z.V + h, z1 = 0.5 * K / Z.lam;
+        const double s0 = C[0] * Z.rho;
+        f[0] = s0 * Z.U;
+        f[1] = s0 * m2;
+        f[2] = s0 * Z.U * Z.V;
+        f[3] = s0 * 0.5 * (m3 + Z.U * (v2 + z1));
+        const double sl = C[6] * L.rho, sr = C[6] * Rs.rho;
+        f[0] += sl * ml[1] + sr * mr[1];
+        f[1] += sl * ml[2] + sr * mr[2];
+        f[2] += sl * ml[1] * L.V + sr * mr[1] * Rs.V;
+        f[3] += sl * 0.5 * (ml[3] + ml[1] * (v2l + zl)) + sr * 0.5 * (mr[3] + mr[1] * (v2r + zr));
     }
-    lead_flux(I, gamma, f);
+    // slope-carrying terms (FP32)
     Iface<float> J;
-    kstate_cast(I.L, J.L);
-    kstate_cast(I.Rs, J.Rs);
-    kstate_cast(I.Z, J.Z);
-    J.tau = float(I.tau);
+    kstate_cast(L, J.L);
+    kstate_cast(Rs, J.Rs);
+    kstate_cast(Z, J.Z);
+    J.tau = float(tau);
 #pragma unroll
-    for (int q = 0; q < 9; ++q) J.C[q] = float(I.C[q]);
+    for (int q = 0; q < 9; ++q) J.C[q] = float(C[q]);
     float fl[24], fr[24], g[4];
 #pragma unroll
-    for (int q = 0; q < 24; ++q) {
-        J.w0[q] = float(I.w0[q]);
-        fl[q] = float(wl[q]);
-        fr[q] = float(wr[q]);
+    for (int q = 0; q < 4; ++q) {
+        J.w0[q] = float(w0[q]);
+        fl[q] = float(vl[q]);
+        fr[q] = float(vr[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 20; ++q) {
+        fl[4 + q] = dl[q];
+        fr[4 + q] = dr[q];
+        J.w0[4 + q] = 0.5f * (dl[q] + dr[q]);
     }
     body_flux(fl, fr, J, float(gamma), false, g);
 #pragma unroll
     for (int q = 0; q < 4; ++q) f[q] += double(g[q]);
     return true;
+}
+
+// Mixed precision flux from FP64 rows [6][4] (used by the point-flux entry point).
+__device__ __forceinline__ bool gp_flux_mixed(const double *wl, const double *wr, double dt, double gamma, double mu,
+                                              int tau2_exact, double *f)
+{
+    float dl[20], dr[20];
+#pragma unroll
+    for (int q = 0; q < 20; ++q) {
+        dl[q] = float(wl[4 + q]);
+        dr[q] = float(wr[4 + q]);
+    }
+    return gp_flux_mixed_split(wl, wr, dl, dr, dt, gamma, mu, tau2_exact, f);
 }
 
 }  // namespace kin

@@ -98,6 +98,10 @@ extern "C" gks_status gks_cfl_dt_noalloc(const gks_mesh *m, const double *w, dou
         set_error("gks_cfl_dt_noalloc: NULL argument");
         return GKS_EINVAL;
     }
+    if (m->n_case != 1) {
+        set_error("gks_cfl_dt_noalloc: the handle holds %d cases; it takes a single mesh", m->n_case);
+        return GKS_EINVAL;
+    }
     const int64_t T = m->d.T;
     const int64_t nblk = (T + kBlock - 1) / kBlock;
     if (nblk > kNoallocMaxBlocks) {

@@ -21,7 +21,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <numeric>
+#include <thread>
 
 #include "gks_internal.h"
 
@@ -184,18 +186,29 @@ std::vector<int32_t> rcm_order(const std::vector<std::array<int32_t, 3>> &adj, c
 
 }  // namespace
 
-gks_status build_mesh(gks_mesh *m, const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t n_tri,
-                      const int32_t *faces, const double *face_shift, int64_t n_face, const double *bc_state)
+namespace {
+
+// Host data of one case in its own RCM order (local indices).
+struct HostCase {
+    int64_t T = 0, F = 0, nbf = 0, nk1 = 0, nnzb = 0, bw = 0;
+    int32_t nlo = 0, nup = 0;
+    std::vector<int32_t> perm, nb, cf, fl, fr, ftag, fperm, lev_lo, lev_up;
+    std::vector<double> area, iarea, h, mxx, mxy, myy, inrad, alpha, ex, ey, a0, D, P;
+    std::vector<double> fnx, fny, flen, gl, gr, bc;
+};
+
+// Geometry, boundary order reduction (Eq. (28)), RCM order, CLS blocks
+// (Eq. (29)), block ILU(0) factors and levels of one case.
+gks_status build_case(const CaseIn &in, double w, HostCase &hc)
 {
-    const int64_t T = n_tri, F = n_face;
+    const double *nodes = in.nodes, *face_shift = in.face_shift, *bc_state = in.bc_state;
+    const int32_t *tris = in.tris, *faces = in.faces;
+    const int64_t n_nodes = in.n_nodes, T = in.n_tri, F = in.n_face;
     if (!nodes || !tris || !faces || !face_shift || !bc_state || n_nodes <= 0 || T <= 0 || F <= 0 ||
-        T > (int64_t)INT32_MAX / 4 || F > (int64_t)INT32_MAX / 4) {
+        T > (int64_t)INT32_MAX / 8 || F > (int64_t)INT32_MAX / 8) {
         set_error("gks_mesh_create: null array or size out of range");
         return GKS_EINVAL;
     }
-    const gks_config &cfg = m->cfg;
-    const double w = cfg.cls_w;
-
     // ---- cells: orientation, area, centroid, radii, length scale (Eq. (17))
     std::vector<HostCell> cell(T);
     for (int64_t i = 0; i < T; ++i) {
@@ -386,16 +399,8 @@ gks_status build_mesh(gks_mesh *m, const double *nodes, int64_t n_nodes, const i
         lev[i] = l;
         nlo = std::max(nlo, l + 1);
     }
-    auto bucket = [&](int32_t nlev, std::vector<int32_t> &rows, std::vector<int32_t> &ptr) {
-        ptr.assign(nlev + 1, 0);
-        for (int64_t i = 0; i < T; ++i) ++ptr[lev[i] + 1];
-        for (int32_t l = 0; l < nlev; ++l) ptr[l + 1] += ptr[l];
-        std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
-        rows.assign(T, 0);
-        for (int64_t i = 0; i < T; ++i) rows[fill[lev[i]]++] = (int32_t)i;
-    };
-    std::vector<int32_t> rows_lo, rows_up;
-    bucket(nlo, rows_lo, m->lvl_lo_ptr);
+    hc.lev_lo = lev;
+    hc.nlo = nlo;
     for (int64_t i = T - 1; i >= 0; --i) {
         int32_t l = 0;
         for (int s = 0; s < 3; ++s) {
@@ -406,7 +411,8 @@ gks_status build_mesh(gks_mesh *m, const double *nodes, int64_t n_nodes, const i
         nup = std::max(nup, l + 1);
     }
     // lev[] now holds the backward levels (rows with higher indices first)
-    bucket(nup, rows_up, m->lvl_up_ptr);
+    hc.lev_up = lev;
+    hc.nup = nup;
 
     // ---- faces in internal order (sorted by the lower internal cell index)
     std::vector<int64_t> forder(F);
@@ -465,24 +471,189 @@ gks_status build_mesh(gks_mesh *m, const double *nodes, int64_t n_nodes, const i
         }
     }
 
+    hc.T = T;
+    hc.F = F;
+    hc.nbf = nbf;
+    hc.nk1 = nk1;
+    hc.nnzb = nnzb;
+    hc.bw = bw;
+    hc.perm = std::move(perm);
+    hc.nb = std::move(h_nb);
+    hc.cf = std::move(h_cf);
+    hc.area = std::move(h_area);
+    hc.iarea = std::move(h_iarea);
+    hc.h = std::move(h_h);
+    hc.mxx = std::move(h_mxx);
+    hc.mxy = std::move(h_mxy);
+    hc.myy = std::move(h_myy);
+    hc.inrad = std::move(h_inrad);
+    hc.alpha = std::move(h_alpha);
+    hc.ex = std::move(h_ex);
+    hc.ey = std::move(h_ey);
+    hc.a0 = std::move(h_a0);
+    hc.D = std::move(h_D);
+    hc.P = std::move(h_P);
+    hc.fl = std::move(h_fl);
+    hc.fr = std::move(h_fr);
+    hc.ftag = std::move(h_ftag);
+    hc.fperm = std::move(h_fperm);
+    hc.fnx = std::move(h_fnx);
+    hc.fny = std::move(h_fny);
+    hc.flen = std::move(h_flen);
+    hc.gl = std::move(h_gl);
+    hc.gr = std::move(h_gr);
+    hc.bc = std::move(h_bc);
+    return GKS_OK;
+}
+
+// Copy rows [k][n] of a case array into rows [k][N] of the global array at column off.
+template <typename V>
+void place(const std::vector<V> &src, int64_t n, int k, std::vector<V> &dst, int64_t N, int64_t off)
+{
+    for (int q = 0; q < k; ++q) std::copy(src.begin() + q * n, src.begin() + (q + 1) * n, dst.begin() + q * N + off);
+}
+
+}  // namespace
+
+gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
+{
+    if (!cases || n_cases <= 0) {
+        set_error("gks_mesh_create: no case");
+        return GKS_EINVAL;
+    }
+    const gks_config &cfg = m->cfg;
+    std::vector<HostCase> hcs(n_cases);
+    {
+        // cases are independent: build them on all host threads
+        std::atomic<int32_t> next{0};
+        std::atomic<int> failed{-1};
+        std::vector<gks_status> st(n_cases, GKS_OK);
+        std::vector<std::string> msg(n_cases);
+        unsigned nt = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), (unsigned)n_cases));
+        auto work = [&]() {
+            for (int32_t c; (c = next.fetch_add(1)) < n_cases;) {
+                st[c] = build_case(cases[c], cfg.cls_w, hcs[c]);
+                if (st[c] != GKS_OK) {
+                    msg[c] = last_error();
+                    int expect = -1;
+                    failed.compare_exchange_strong(expect, c);
+                }
+            }
+        };
+        std::vector<std::thread> pool;
+        for (unsigned q = 1; q < nt; ++q) pool.emplace_back(work);
+        work();
+        for (auto &t : pool) t.join();
+        if (failed.load() >= 0) {
+            const int c = failed.load();
+            set_error("case %d: %s", c, msg[c].c_str());
+            return st[c];
+        }
+    }
+    // ---- layout: cases one after the other, each padded to whole blocks when batched
+    const bool pad = n_cases > 1;
+    std::vector<int64_t> coff(n_cases + 1, 0), foff(n_cases + 1, 0), ccell(n_cases + 1, 0), cface(n_cases + 1, 0);
+    for (int32_t c = 0; c < n_cases; ++c) {
+        const int64_t Tc = hcs[c].T;
+        coff[c + 1] = coff[c] + (pad ? (Tc + kBlock - 1) / kBlock * kBlock : Tc);
+        foff[c + 1] = foff[c] + hcs[c].F;
+        ccell[c + 1] = ccell[c] + Tc;
+        cface[c + 1] = cface[c] + hcs[c].F;
+    }
+    const int64_t T = coff[n_cases], F = foff[n_cases];
+    if (T > (int64_t)INT32_MAX / 2 || F > (int64_t)INT32_MAX / 2) {
+        set_error("gks_mesh_create: too many cells or faces");
+        return GKS_EINVAL;
+    }
+    const int64_t nblk = (T + kBlock - 1) / kBlock;
+    std::vector<int32_t> h_perm(T, -1), h_nb(3 * T, -1), h_cf(3 * T, -1), h_blk_case(nblk, 0), h_case_blk(n_cases + 1);
+    std::vector<double> h_area(T, 1.0), h_iarea(T, 1.0), h_h(T, 1.0), h_mxx(T, 0.0), h_mxy(T, 0.0), h_myy(T, 0.0);
+    std::vector<double> h_inrad(T, std::numeric_limits<double>::infinity());
+    std::vector<double> h_alpha(3 * T, 0.0), h_ex(3 * T, 0.0), h_ey(3 * T, 0.0), h_a0(15 * T, 0.0);
+    std::vector<double> h_D(15 * T, 0.0), h_P(25 * T, 0.0);
+    std::vector<int32_t> h_fl(F), h_fr(F), h_ftag(F), h_fperm(F), h_face_case(F);
+    std::vector<double> h_fnx(F), h_fny(F), h_flen(F), h_gl(4 * F), h_gr(4 * F), h_bc(4 * F);
+    // padding cells: identity diagonal and pivot blocks, no neighbours, no faces
+    for (int64_t i = 0; i < T; ++i) {
+        h_D[0 * T + i] = h_D[5 * T + i] = h_D[9 * T + i] = h_D[12 * T + i] = h_D[14 * T + i] = 1.0;
+        for (int a = 0; a < 5; ++a) h_P[(6 * a) * T + i] = 1.0;
+    }
+    int32_t nlo = 0, nup = 0;
+    m->n_tri = m->n_face = m->n_bface = m->n_k1 = m->nnzb = m->bandwidth = 0;
+    m->case_tri.assign(n_cases, 0);
+    m->case_face.assign(n_cases, 0);
+    for (int32_t c = 0; c < n_cases; ++c) {
+        HostCase &hc = hcs[c];
+        const int64_t Tc = hc.T, Fc = hc.F, o = coff[c], fo = foff[c];
+        h_case_blk[c] = (int32_t)(o / kBlock);
+        for (int64_t b = o / kBlock; b < (coff[c + 1] + kBlock - 1) / kBlock; ++b) h_blk_case[b] = c;
+        for (int64_t i = 0; i < Tc; ++i) {
+            h_perm[o + i] = (int32_t)(ccell[c] + hc.perm[i]);
+            for (int s = 0; s < 3; ++s) {
+                const int32_t j = hc.nb[s * Tc + i];
+                h_nb[s * T + o + i] = j >= 0 ? (int32_t)(o + j) : -1;
+                const int32_t f = hc.cf[s * Tc + i];
+                h_cf[s * T + o + i] = f >= 0 ? (int32_t)(((fo + (f >> 1)) << 1) | (f & 1)) : -1;
+            }
+        }
+        place(hc.area, Tc, 1, h_area, T, o); place(hc.iarea, Tc, 1, h_iarea, T, o); place(hc.h, Tc, 1, h_h, T, o);
+        place(hc.mxx, Tc, 1, h_mxx, T, o); place(hc.mxy, Tc, 1, h_mxy, T, o); place(hc.myy, Tc, 1, h_myy, T, o);
+        place(hc.inrad, Tc, 1, h_inrad, T, o);
+        place(hc.alpha, Tc, 3, h_alpha, T, o); place(hc.ex, Tc, 3, h_ex, T, o); place(hc.ey, Tc, 3, h_ey, T, o);
+        place(hc.a0, Tc, 15, h_a0, T, o); place(hc.D, Tc, 15, h_D, T, o); place(hc.P, Tc, 25, h_P, T, o);
+        for (int64_t f = 0; f < Fc; ++f) {
+            h_fl[fo + f] = (int32_t)(o + hc.fl[f]);
+            h_fr[fo + f] = hc.fr[f] >= 0 ? (int32_t)(o + hc.fr[f]) : -1;
+            h_ftag[fo + f] = hc.ftag[f];
+            h_fperm[fo + f] = (int32_t)(cface[c] + hc.fperm[f]);
+            h_face_case[fo + f] = c;
+        }
+        place(hc.fnx, Fc, 1, h_fnx, F, fo); place(hc.fny, Fc, 1, h_fny, F, fo); place(hc.flen, Fc, 1, h_flen, F, fo);
+        place(hc.gl, Fc, 4, h_gl, F, fo); place(hc.gr, Fc, 4, h_gr, F, fo); place(hc.bc, Fc, 4, h_bc, F, fo);
+        nlo = std::max(nlo, hc.nlo);
+        nup = std::max(nup, hc.nup);
+        m->n_tri += Tc;
+        m->n_face += Fc;
+        m->n_bface += hc.nbf;
+        m->n_k1 += hc.nk1;
+        m->nnzb += hc.nnzb;
+        m->bandwidth = std::max(m->bandwidth, hc.bw);
+        m->case_tri[c] = Tc;
+        m->case_face[c] = Fc;
+    }
+    h_case_blk[n_cases] = (int32_t)nblk;
+    // level sets: the rows of every case at level l are solved together
+    auto bucket = [&](int32_t nlev, bool lower, std::vector<int32_t> &rows, std::vector<int32_t> &ptr) {
+        ptr.assign(nlev + 1, 0);
+        for (int32_t c = 0; c < n_cases; ++c)
+            for (int64_t i = 0; i < hcs[c].T; ++i) ++ptr[(lower ? hcs[c].lev_lo[i] : hcs[c].lev_up[i]) + 1];
+        for (int32_t l = 0; l < nlev; ++l) ptr[l + 1] += ptr[l];
+        std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+        rows.assign(ptr[nlev], 0);
+        for (int32_t c = 0; c < n_cases; ++c)
+            for (int64_t i = 0; i < hcs[c].T; ++i)
+                rows[fill[lower ? hcs[c].lev_lo[i] : hcs[c].lev_up[i]]++] = (int32_t)(coff[c] + i);
+    };
+    std::vector<int32_t> rows_lo, rows_up;
+    bucket(nlo, true, rows_lo, m->lvl_lo_ptr);
+    bucket(nup, false, rows_up, m->lvl_up_ptr);
+    hcs.clear();
+
     // ---- upload
-    m->n_tri = T;
-    m->n_face = F;
-    m->n_bface = nbf;
-    m->n_k1 = nk1;
-    m->nnzb = nnzb;
-    m->bandwidth = bw;
+    m->n_case = n_cases;
     DeviceMesh &d = m->d;
     d.T = T;
     d.F = F;
+    d.ncase = n_cases;
     gks_status st;
 #define UP(ptr, vec) \
     if ((st = upload(m, &d.ptr, vec)) != GKS_OK) return st
     UP(area, h_area); UP(inv_area, h_iarea); UP(h, h_h); UP(mxx, h_mxx); UP(mxy, h_mxy); UP(myy, h_myy);
     UP(inrad, h_inrad); UP(nb, h_nb); UP(alpha, h_alpha); UP(ex, h_ex); UP(ey, h_ey); UP(a0, h_a0);
-    UP(D, h_D); UP(P, h_P); UP(cf, h_cf); UP(perm, perm); UP(lvl_lo, rows_lo); UP(lvl_up, rows_up);
+    UP(D, h_D); UP(P, h_P); UP(cf, h_cf); UP(perm, h_perm); UP(lvl_lo, rows_lo); UP(lvl_up, rows_up);
     UP(fl, h_fl); UP(fr, h_fr); UP(ftag, h_ftag); UP(fperm, h_fperm); UP(fnx, h_fnx); UP(fny, h_fny);
     UP(flen, h_flen); UP(gl, h_gl); UP(gr, h_gr); UP(bc, h_bc);
+    UP(blk_case, h_blk_case); UP(case_blk, h_case_blk); UP(face_case, h_face_case);
     if (cfg.precision == GKS_MIXED) {
         auto f32 = [](const std::vector<double> &v) { return std::vector<float>(v.begin(), v.end()); };
         UP(D32, f32(h_D)); UP(P32, f32(h_P)); UP(alpha32, f32(h_alpha)); UP(ex32, f32(h_ex)); UP(ey32, f32(h_ey));
@@ -492,22 +663,38 @@ gks_status build_mesh(gks_mesh *m, const double *nodes, int64_t n_nodes, const i
     // ---- work buffers
     Work &k = m->wk;
     k.m = cfg.gmres_m;
-    k.nblk = (int)((T + kBlock - 1) / kBlock);
+    k.nblk = (int)nblk;
+    k.ns = 4 * n_cases;
     const int mm = k.m;
+    const int64_t ns = k.ns;
 #define AL(ptr, n) \
     if ((st = dalloc(m, &k.ptr, (size_t)(n))) != GKS_OK) return st
-    AL(w, 4 * T); AL(w_old, 4 * T); AL(x, 20 * T); AL(b, 20 * T); AL(r, 20 * T); AL(t, 20 * T); AL(t2, 20 * T); AL(t3, 20 * T);
+    AL(w, 4 * T); AL(w_old, 4 * T); AL(x, 20 * T); AL(b, 20 * T); AL(r, 20 * T); AL(t2, 20 * T); AL(t3, 20 * T);
     AL(V, (size_t)(mm + 1) * 20 * T); AL(flux, 4 * F);
     if (cfg.precision == GKS_MIXED) {
-        AL(t32, 20 * T); AL(t2_32, 20 * T); AL(t3_32, 20 * T);
+        AL(t2_32, 20 * T); AL(t3_32, 20 * T); AL(Z32, (size_t)mm * 20 * T);
+    } else {
+        AL(Z, (size_t)mm * 20 * T);
     }
-    AL(part, (size_t)k.nblk * 4 * (mm + 2)); AL(dpart, (size_t)std::max<int64_t>(k.nblk, (F + kBlock - 1) / kBlock) * 4);
-    AL(H, 4 * (mm + 1) * mm); AL(cs, 4 * mm); AL(sn, 4 * mm); AL(g, 4 * (mm + 1)); AL(y, 4 * mm);
-    AL(hcol, 4 * (mm + 2)); AL(bnorm, 4); AL(beta, 4); AL(ctl, 16); AL(dt, 1); AL(scal, 8); AL(status, 1);
+    AL(part, (size_t)nblk * 4 * (mm + 2)); AL(dpart, (size_t)nblk * 4);
+    AL(H, ns * (mm + 1) * mm); AL(cs, ns * mm); AL(sn, ns * mm); AL(g, ns * (mm + 1)); AL(y, ns * mm);
+    AL(hcol, ns * (mm + 2)); AL(bnorm, ns); AL(beta, ns); AL(ctl, kCtlFields * ns); AL(flags, 4);
+    AL(dt, n_cases); AL(tcase, n_cases); AL(tfinal, n_cases); AL(done, n_cases); AL(scal, 8); AL(status, n_cases);
 #undef AL
     GKS_CUDA(cudaMemset(k.x, 0, sizeof(double) * 20 * T));
-    GKS_CUDA(cudaMemset(k.status, 0, sizeof(int32_t)));
-    GKS_CUDA(cudaMallocHost(&k.h_ctl, sizeof(int32_t) * 20));
+    GKS_CUDA(cudaMemset(k.ctl, 0, sizeof(int32_t) * kCtlFields * ns));
+    GKS_CUDA(cudaMemset(k.status, 0, sizeof(int32_t) * n_cases));
+    GKS_CUDA(cudaMemset(k.done, 0, sizeof(int32_t) * n_cases));
+    {
+        // padding cells hold a harmless uniform state
+        std::vector<double> w0(4 * T, 0.0);
+        for (int64_t i = 0; i < T; ++i) {
+            w0[i] = 1.0;
+            w0[3 * T + i] = 2.5;
+        }
+        GKS_CUDA(cudaMemcpy(k.w, w0.data(), sizeof(double) * 4 * T, cudaMemcpyHostToDevice));
+    }
+    GKS_CUDA(cudaMallocHost(&k.h_flags, sizeof(int32_t) * 4));
     GKS_CUDA(cudaMallocHost(&k.h_scal, sizeof(double) * 8));
     return GKS_OK;
 }
@@ -516,9 +703,9 @@ void free_mesh(gks_mesh *m)
 {
     for (void *p : m->allocations) cudaFree(p);
     m->allocations.clear();
-    if (m->wk.h_ctl) cudaFreeHost(m->wk.h_ctl);
+    if (m->wk.h_flags) cudaFreeHost(m->wk.h_flags);
     if (m->wk.h_scal) cudaFreeHost(m->wk.h_scal);
-    m->wk.h_ctl = nullptr;
+    m->wk.h_flags = nullptr;
     m->wk.h_scal = nullptr;
 }
 

@@ -25,7 +25,8 @@ FP64, MIXED = 0, 1
 
 EXPORTED = ["gks_config_default", "gks_mesh_create", "gks_mesh_destroy", "gks_mesh_get_stats", "gks_cfl_dt",
             "gks_cls_reconstruct", "gks_reset_warm_start", "gks_flux", "gks_step", "gks_run", "gks_point_flux",
-            "gks_profile_begin", "gks_profile_end", "gks_launch_count", "gks_cfl_dt_noalloc", "gks_last_error"]
+            "gks_profile_begin", "gks_profile_end", "gks_launch_count", "gks_cfl_dt_noalloc", "gks_batch_create",
+            "gks_batch_run", "gks_last_error"]
 PROF_FLUX, PROF_SPMV, PROF_ILU, PROF_ORTH, PROF_UPDATE = range(5)
 
 
@@ -62,7 +63,16 @@ class Profile(C.Structure):
 class MeshStats(C.Structure):
     _fields_ = [("n_tri", C.c_int64), ("n_face", C.c_int64), ("n_boundary_face", C.c_int64), ("n_k1", C.c_int64),
                 ("nnzb", C.c_int64), ("levels_lower", C.c_int32), ("levels_upper", C.c_int32),
-                ("rcm_bandwidth", C.c_int64), ("device_bytes", C.c_int64)]
+                ("rcm_bandwidth", C.c_int64), ("device_bytes", C.c_int64), ("n_case", C.c_int32)]
+
+
+class CaseDesc(C.Structure):
+    _fields_ = [("nodes", C.c_void_p), ("n_nodes", C.c_int64), ("tris", C.c_void_p), ("n_tri", C.c_int64),
+                ("faces", C.c_void_p), ("face_shift", C.c_void_p), ("n_face", C.c_int64), ("bc_state", C.c_void_p)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("gmres_iters", C.c_int64), ("n_failed", C.c_int32), ("n_finished", C.c_int32)]
 
 
 _lib = None
@@ -83,6 +93,10 @@ def load():
     lib.gks_config_default.restype = None
     lib.gks_mesh_create.argtypes = [P, I64, P, I64, P, P, I64, P, C.POINTER(Config), C.POINTER(P)]
     lib.gks_mesh_create.restype = st
+    lib.gks_batch_create.argtypes = [P, I32, C.POINTER(Config), C.POINTER(P)]
+    lib.gks_batch_create.restype = st
+    lib.gks_batch_run.argtypes = [P, P, P, I64, P, P, C.POINTER(BatchInfo), P]
+    lib.gks_batch_run.restype = st
     lib.gks_mesh_destroy.argtypes = [P]
     lib.gks_mesh_destroy.restype = st
     lib.gks_mesh_get_stats.argtypes = [P, C.POINTER(MeshStats)]
@@ -150,23 +164,60 @@ def _stream(stream=None):
     return C.c_void_p(s.cuda_stream)
 
 
+def _mesh_arrays(mesh):
+    return (np.ascontiguousarray(mesh.nodes, dtype=np.float64), np.ascontiguousarray(mesh.tris, dtype=np.int32),
+            np.ascontiguousarray(mesh.faces, dtype=np.int32), np.ascontiguousarray(mesh.face_shift, dtype=np.float64),
+            np.ascontiguousarray(mesh.bc_state, dtype=np.float64))
+
+
 class GksMesh:
-    """A mesh handle: geometry, CLS operator, ILU(0) factors and work buffers in HBM."""
+    """A handle: geometry, CLS operator, ILU(0) factors and work buffers in HBM.
+    GksMesh(mesh) holds one mesh; GksMesh.batch([mesh, ...]) holds independent
+    cases that advance together (state arrays concatenate the cases' cells)."""
 
     def __init__(self, mesh, **cfg):
         self._lib = load()
         self.cfg = config(**cfg)
-        nodes = np.ascontiguousarray(mesh.nodes, dtype=np.float64)
-        tris = np.ascontiguousarray(mesh.tris, dtype=np.int32)
-        faces = np.ascontiguousarray(mesh.faces, dtype=np.int32)
-        shift = np.ascontiguousarray(mesh.face_shift, dtype=np.float64)
-        bc = np.ascontiguousarray(mesh.bc_state, dtype=np.float64)
+        nodes, tris, faces, shift, bc = _mesh_arrays(mesh)
         self.T, self.F = int(tris.shape[0]), int(faces.shape[0])
+        self.case_tri = [self.T]
         h = C.c_void_p()
         p = lambda a: a.ctypes.data_as(C.c_void_p)
         _check(self._lib.gks_mesh_create(p(nodes), nodes.shape[0], p(tris), self.T, p(faces), p(shift), self.F,
                                          p(bc), C.byref(self.cfg), C.byref(h)), "gks_mesh_create")
         self._h = h
+
+    @classmethod
+    def batch(cls, meshes, **cfg):
+        self = cls.__new__(cls)
+        self._lib = load()
+        self.cfg = config(**cfg)
+        keep = [_mesh_arrays(m) for m in meshes]
+        descs = (CaseDesc * len(keep))()
+        p = lambda a: a.ctypes.data_as(C.c_void_p)
+        for q, (nodes, tris, faces, shift, bc) in enumerate(keep):
+            descs[q] = CaseDesc(p(nodes), nodes.shape[0], p(tris), tris.shape[0], p(faces), p(shift), faces.shape[0],
+                                p(bc))
+        self.case_tri = [int(k[1].shape[0]) for k in keep]
+        self.T = sum(self.case_tri)
+        self.F = sum(int(k[2].shape[0]) for k in keep)
+        h = C.c_void_p()
+        _check(self._lib.gks_batch_create(descs, len(keep), C.byref(self.cfg), C.byref(h)), "gks_batch_create")
+        self._h = h
+        return self
+
+    def batch_run(self, w, t_final=None, max_steps: int = 1, stream=None) -> dict:
+        n = len(self.case_tri)
+        tf = None if t_final is None else np.ascontiguousarray(t_final, dtype=np.float64)
+        tr = np.zeros(n)
+        cs = np.zeros(n, dtype=np.int32)
+        info = BatchInfo()
+        p = lambda a: a.ctypes.data_as(C.c_void_p)
+        _check(self._lib.gks_batch_run(self._h, _dev(w, (4, self.T)), p(tf) if tf is not None else None,
+                                       int(max_steps), p(tr), p(cs), C.byref(info), _stream(stream)),
+               "gks_batch_run")
+        return {"t": tr, "status": cs, "steps": info.steps, "gmres_iters": info.gmres_iters,
+                "n_failed": info.n_failed, "n_finished": info.n_finished}
 
     def close(self):
         if getattr(self, "_h", None):
