@@ -25,6 +25,7 @@ typedef struct or_params {
     double gmres_rtol;  /* relative residual target                              */
     int    tau2_exact;  /* 1: c4..c6 with the 2 tau^2 (1 - e^{-t/tau}) term       */
     int    slope0_mode; /* 0: interface-equilibrium derivatives = mean of L/R     */
+    int    limiter;     /* 1: shock detector + DWBAP limiter (Sec. III.C)          */
 } or_params;
 
 /* Boundary tags (same numbering as the input generator). */
@@ -87,5 +88,8 @@ void or_gauss_legendre(int n, double *x, double *w);
 void or_time_integrals(double dt, double tau, int tau2_exact, double *c);
 int  or_gp_flux(const double *wl, const double *wr, double dt, const or_params *prm,
                 double *f, double *aux);
+
+/* limiter (or_limiter.c) */
+int  or_limit(const or_mesh *m, const double *w, const double *coef, double *coef_out, int32_t *flag);
 
 #endif

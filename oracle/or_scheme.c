@@ -26,7 +26,7 @@ void or_params_default(or_params *p)
 {
     p->gamma = 1.4; p->cfl = 0.3; p->mu = 0.0; p->cls_w = 0.3;
     p->gmres_m = 30; p->gmres_maxit = 5000; p->gmres_rtol = 1e-14;
-    p->tau2_exact = 0; p->slope0_mode = 0;
+    p->tau2_exact = 0; p->slope0_mode = 0; p->limiter = 0;
 }
 
 void or_mesh_free(or_mesh *m)
@@ -369,6 +369,13 @@ int or_step(or_mesh *m, double *w, double dt_in, double *dt_out, int32_t *iters,
     double *coef = malloc(sizeof(double) * 20 * (size_t)T), *flux = malloc(sizeof(double) * 4 * (size_t)F);
     int st = 0;
     if (or_cls_solve(m, w, coef, 1, iters, relres) != 0) st = 2;
+    if (m->prm.limiter) {
+        double *lim = malloc(sizeof(double) * 20 * (size_t)T);
+        int32_t *flag = malloc(sizeof(int32_t) * (size_t)T);
+        or_limit(m, w, coef, lim, flag);
+        memcpy(coef, lim, sizeof(double) * 20 * (size_t)T);
+        free(lim); free(flag);
+    }
     if (or_face_flux(m, w, coef, dt, flux) != 0) st = 1;
     or_update(m, w, flux);
     if (dt_out) *dt_out = dt;

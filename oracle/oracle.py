@@ -17,7 +17,7 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["or_geom_cls.c", "or_linsolve.c", "or_kinetic.c", "or_scheme.c"]
+_SOURCES = ["or_geom_cls.c", "or_linsolve.c", "or_kinetic.c", "or_scheme.c", "or_limiter.c"]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -42,7 +42,7 @@ def build(force: bool = False) -> str:
 class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("mu", C.c_double), ("cls_w", C.c_double),
                 ("gmres_m", C.c_int), ("gmres_maxit", C.c_int), ("gmres_rtol", C.c_double),
-                ("tau2_exact", C.c_int), ("slope0_mode", C.c_int)]
+                ("tau2_exact", C.c_int), ("slope0_mode", C.c_int), ("limiter", C.c_int)]
 
 
 def _load():
@@ -86,6 +86,8 @@ def _load():
         lib.or_time_integrals.argtypes = [D, D, I, P]
         lib.or_gauss_legendre.argtypes = [I, P, P]
         lib.or_params_default.argtypes = [C.POINTER(Params)]
+        lib.or_limit.restype = I
+        lib.or_limit.argtypes = [P, P, P, P, P]
         _lib = lib
         return lib
 
@@ -196,6 +198,15 @@ class OracleMesh:
         return out
 
     # scheme ------------------------------------------------------------
+    def limit(self, w, coef):
+        """Detector + DWBAP limiter: (limited coefficients, flags)."""
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        coef = np.ascontiguousarray(coef, dtype=np.float64)
+        out = np.zeros_like(coef)
+        flag = np.zeros(self.T, dtype=np.int32)
+        self._lib.or_limit(self._h, _ptr(w), _ptr(coef), _ptr(out), _ptr(flag))
+        return out, flag
+
     def cfl_dt(self, w) -> float:
         w = np.ascontiguousarray(w, dtype=np.float64)
         return float(self._lib.or_cfl_dt(self._h, _ptr(w)))
