@@ -110,7 +110,9 @@ typedef struct gks_config {
     int32_t tau2_exact;    /* 0: c4, c5, c6 exactly as printed in Eq. (13);
                               1: with the 2 tau^2 (1 - e^{-t/tau}) term that the exact
                               time integral of Eq. (8) carries                          */
-    int32_t reserved[8];   /* must be zero                                             */
+    int32_t limiter;       /* 1: shock detector (Eq. (37)) and DWBAP limiter (Eqs.
+                              (34)-(36)) on the reconstruction before the flux        */
+    int32_t reserved[7];   /* must be zero                                             */
 } gks_config;
 
 typedef struct gks_mesh gks_mesh;
@@ -261,6 +263,22 @@ GKS_EXPORT gks_status gks_reset_warm_start(gks_mesh *mesh);
  * state had rho <= 0 or p <= 0 (synchronises the stream to find out). */
 GKS_EXPORT gks_status gks_flux(gks_mesh *mesh, const double *w, const double *coef, double dt, double *face_flux,
                     void *stream);
+
+/* Shock detector (Eq. (37)) and DWBAP limiter (Eqs. (34)-(36)) on a
+ * reconstruction: w (device [4][n_tri]) and coef (device [4][5][n_tri], as
+ * returned by gks_cls_reconstruct) in, limited coefficients coef_out (device
+ * [4][5][n_tri], may not alias coef) out; flags (device [n_tri], may be NULL)
+ * receives 0 for an untouched cell, 1 for a limited one and 2 for a limited
+ * cell reset to its average because its limited polynomial still had rho <= 0
+ * or p <= 0 at a face Gauss point.  Derivatives are replaced by
+ * u_0 tan(sum_j omega_j arctan(u_j / u_0)) over the cell's own and its face
+ * neighbours' polynomials at the centroid, omega_j from the distances to the
+ * face midpoints and the spread of the neighbour pressures (Eqs. (35)-(36)).
+ * Requires a mesh created with gks_config.limiter = 1 (GKS_EINVAL otherwise);
+ * with it, gks_step, gks_run and gks_batch_run limit every reconstruction
+ * before the flux.  Stream-ordered, no synchronisation. */
+GKS_EXPORT gks_status gks_limit(gks_mesh *mesh, const double *w, const double *coef, double *coef_out,
+                                int32_t *flags, void *stream);
 
 /* One explicit step (Eq. (6)) in place on w (device [4][n_tri]).
  * *dt_inout (host): > 0 fixes the step; <= 0 takes the CFL step and returns it.

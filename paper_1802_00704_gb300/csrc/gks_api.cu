@@ -55,7 +55,8 @@ gks_status check_config(const gks_config &c)
     bool ok = c.gamma > 1.0 && c.cfl > 0.0 && c.mu >= 0.0 && c.cls_w > 0.0 && c.gmres_m >= 1 &&
               c.gmres_m <= kMaxRestart && c.gmres_maxit >= 1 && c.gmres_rtol > 0.0 &&
               (c.tau2_exact == 0 || c.tau2_exact == 1) && c.ilu_sweeps >= 0 && c.ilu_sweeps <= 16;
-    for (int q = 0; q < 8; ++q) ok = ok && c.reserved[q] == 0;
+    ok = ok && (c.limiter == 0 || c.limiter == 1);
+    for (int q = 0; q < 7; ++q) ok = ok && c.reserved[q] == 0;
     if (!ok) {
         set_error("invalid gks_config");
         return GKS_EINVAL;
@@ -102,7 +103,8 @@ gks_status step_internal(gks_mesh *m, double dt_fixed, cudaStream_t s, gks_step_
     int32_t iters[4], conv = 1;
     double relres[4];
     if ((st = cls_solve(m, s, iters, relres, &conv)) != GKS_OK) return st;
-    if ((st = launch_flux(m, k.w, k.x, 0.0, k.dt, k.flux, s)) != GKS_OK) return st;
+    if (m->cfg.limiter && (st = launch_limiter(m, k.w, k.x, s)) != GKS_OK) return st;
+    if ((st = launch_flux(m, k.w, m->cfg.limiter ? k.xl : k.x, 0.0, k.dt, k.flux, s)) != GKS_OK) return st;
     if ((st = launch_update(m, k.w, k.flux, s)) != GKS_OK) return st;
     GKS_CUDA(cudaMemcpyAsync(&k.h_scal[6], k.dt, sizeof(double), cudaMemcpyDeviceToHost, s));
     int32_t stat = 0;
@@ -285,6 +287,29 @@ gks_status gks_reset_warm_start(gks_mesh *m)
     return GKS_OK;
 }
 
+gks_status gks_limit(gks_mesh *m, const double *w, const double *coef, double *coef_out, int32_t *flags,
+                     void *stream)
+{
+    if (!m || !w || !coef || !coef_out) {
+        set_error("gks_limit: NULL argument");
+        return GKS_EINVAL;
+    }
+    if (!m->cfg.limiter) {
+        set_error("gks_limit: the mesh was created with gks_config.limiter = 0");
+        return GKS_EINVAL;
+    }
+    DeviceGuard g(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    gks_status st;
+    Work &k = m->wk;
+    if ((st = launch_permute(w, k.w, m->d.perm, m->d.T, m->n_tri, 4, true, s)) != GKS_OK) return st;
+    if ((st = launch_permute(coef, k.r, m->d.perm, m->d.T, m->n_tri, 20, true, s)) != GKS_OK) return st;
+    if ((st = launch_limiter(m, k.w, k.r, s)) != GKS_OK) return st;
+    if ((st = launch_permute(k.xl, coef_out, m->d.perm, m->d.T, m->n_tri, 20, false, s)) != GKS_OK) return st;
+    if (flags && (st = launch_scatter_flags(m, flags, s)) != GKS_OK) return st;
+    return GKS_OK;
+}
+
 gks_status gks_flux(gks_mesh *m, const double *w, const double *coef, double dt, double *face_flux, void *stream)
 {
     if (!m || !w || !coef || !face_flux || !(dt > 0.0)) {
@@ -422,7 +447,8 @@ gks_status gks_batch_run(gks_mesh *m, double *w, const double *t_final, int64_t 
         for (int32_t c = 0; c < n; ++c) all = all && done[c];
         if (all) break;
         if ((st = cls_solve(m, s, it.data(), nullptr, nullptr)) != GKS_OK) return st;
-        if ((st = launch_flux(m, k.w, k.x, 0.0, k.dt, k.flux, s)) != GKS_OK) return st;
+        if (m->cfg.limiter && (st = launch_limiter(m, k.w, k.x, s)) != GKS_OK) return st;
+        if ((st = launch_flux(m, k.w, m->cfg.limiter ? k.xl : k.x, 0.0, k.dt, k.flux, s)) != GKS_OK) return st;
         if ((st = launch_update(m, k.w, k.flux, s)) != GKS_OK) return st;
         // a case that failed stops advancing; the others go on
         GKS_CUDA(cudaMemcpyAsync(stat.data(), k.status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));

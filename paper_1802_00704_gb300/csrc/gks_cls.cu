@@ -5,9 +5,13 @@
 // kernel handles one cell and all four variables, so each block of the
 // operator is read once per application.  Vectors are SoA [var][dof][cell] in
 // RCM order.  GMRES (Saad & Schultz 1986) is right-preconditioned, uses
-// classical Gram-Schmidt applied twice (CGS2), and keeps per-variable state on
-// the device (running/converged masks); reductions go through per-block
-// partial sums and a fixed-order second pass, so results are deterministic.
+// classical Gram-Schmidt (twice, CGS2, in FP64 mode), and keeps per-variable
+// state on the device (running/converged masks); reductions go through
+// per-block partial sums and a fixed-order second pass, so results are
+// deterministic.  The Krylov basis is stored unnormalised, V_k = vn_k v_k,
+// with the norms vn_k on the device: the normalisation is folded into the
+// Gram-Schmidt coefficients, the Hessenberg entries and the final combination,
+// which saves one read and one write of the new vector per iteration.
 #include <algorithm>
 #include <cmath>
 
@@ -21,7 +25,8 @@ constexpr int NV = 4, ND = 5, NX = 20;
 // residual estimate has dropped by this factor; the FP64 residual of the next
 // refinement sweep then measures the true error.
 constexpr double kInnerRtol = 1e-6;
-constexpr int kDotBlock = 128;         // threads per block of the dot-product kernel
+constexpr int kDotThreads = 256;       // threads per block of the dot-product kernel
+constexpr int kDotMaxTiles = 65535;    // grid.y limit of the dot-product kernel
 
 // Per-variable control words ctl[16]: [0..3] active (needs more work), [4..7]
 // running (iterating in the current cycle), [8..11] Krylov vectors in the
@@ -252,60 +257,44 @@ __global__ void k_ilu_bwd(DeviceMesh d, const TM *__restrict__ Pg, const TM *__r
         }
 }
 
-// Partial dot products <V_k, w> for k = 0..j (j < JMAX) and the four variables
-// over one block of kBlock cells (kDotBlock threads, two cells each): each
-// thread accumulates every k, then one block reduction writes part[blk][v][k].
-// Blocks never straddle two cases.
-template <int JMAX>
-__global__ void __launch_bounds__(kDotBlock) k_dots(int64_t T, const double *__restrict__ V,
-                                                    const double *__restrict__ w, int j, double *__restrict__ part,
-                                                    int pstride)
+// Partial dot products <V_k, w> of the four variables over one block of
+// kBlock cells: grid (k, block), blockIdx.x = k so that the j + 1 blocks of a
+// cell block run together and read w once from HBM.  64 threads per variable,
+// four cells each (64 apart), all 40 loads issued before the sums (read-only
+// kernels need many bytes in flight); the warp sums then the two warps of a
+// variable give part[blk][v][k].  Fixed order: the sums are deterministic.
+__global__ void __launch_bounds__(kDotThreads, 3) k_dots(int64_t T, int64_t nblk, const double *__restrict__ V,
+                                                         const double *__restrict__ w, double *__restrict__ part,
+                                                         int pstride)
 {
-    __shared__ double sh[(kDotBlock / 32) * NV * JMAX];
-    const int64_t vs = (int64_t)NX * T;
-    double acc[NV * JMAX];
+    constexpr int kPerVar = kDotThreads / NV;          // 64 threads (two warps) per variable
+    constexpr int kCells = kBlock / kPerVar;           // 4 cells per thread
+    __shared__ double sh[kDotThreads / 32];
+    const int k = blockIdx.x;
+    const int v = threadIdx.x / kPerVar, t = threadIdx.x % kPerVar;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double *vk = V + (int64_t)k * NX * T + (int64_t)v * ND * T;
+    const double *wv = w + (int64_t)v * ND * T;
+    for (int64_t b = blockIdx.y; b < nblk; b += gridDim.y) {
+        const int64_t c0 = b * kBlock + t;
+        double s = 0.0;
 #pragma unroll
-    for (int q = 0; q < NV * JMAX; ++q) acc[q] = 0.0;
+        for (int q = 0; q < kCells; ++q) {
+            const int64_t i = c0 + q * kPerVar;
 #pragma unroll
-    for (int half = 0; half < kBlock / kDotBlock; ++half) {
-        const int64_t i = blockIdx.x * (int64_t)kBlock + half * kDotBlock + threadIdx.x;
-        if (i >= T) break;
-        double wv[NX];
-#pragma unroll
-        for (int q = 0; q < NX; ++q) wv[q] = w[q * T + i];
-#pragma unroll
-        for (int k = 0; k < JMAX; ++k) {
-            if (k > j) break;
-            const double *vk = V + k * vs;
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                double sum = 0.0;
-#pragma unroll
-                for (int l = 0; l < ND; ++l) sum += vk[(v * ND + l) * T + i] * wv[v * ND + l];
-                acc[v * JMAX + k] += sum;
-            }
+            for (int l = 0; l < ND; ++l) s += i < T ? vk[l * T + i] * wv[l * T + i] : 0.0;
         }
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int q = 0; q < NV * JMAX; ++q) {
-        if (q % JMAX > j) continue;
-        double x = acc[q];
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) sh[warp * NV * JMAX + q] = x;
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < NV * JMAX; q += blockDim.x) {
-        const int v = q / JMAX, k = q % JMAX;
-        if (k > j) continue;
-        double x = 0.0;
-        for (int u = 0; u < nw; ++u) x += sh[u * NV * JMAX + q];
-        part[(blockIdx.x * NV + v) * pstride + k] = x;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) sh[warp] = s;
+        __syncthreads();
+        if (threadIdx.x < NV) part[(b * NV + threadIdx.x) * pstride + k] = sh[2 * threadIdx.x] + sh[2 * threadIdx.x + 1];
+        __syncthreads();
     }
 }
 
-// w -= sum_{k<=j} h[s][k] V_k for running systems s = case * 4 + v; optional
-// partial |w|^2 per block.
+// w -= sum_{k<=j} c[s][k] V_k for running systems s = case * 4 + v (c: the
+// Gram-Schmidt coefficients of the unnormalised basis), w = 0 for the others;
+// optional partial |w|^2 per block.
 __global__ void k_orth_update(DeviceMesh d, const double *__restrict__ V, double *__restrict__ w, int j,
                               const double *__restrict__ hc, int hstride, const int32_t *__restrict__ ctl, int ns,
                               double *__restrict__ part, int pstride, int want_norm)
@@ -320,7 +309,11 @@ __global__ void k_orth_update(DeviceMesh d, const double *__restrict__ V, double
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             const int sy = 4 * c + v;
-            if (!ctl[kCtlRunning * ns + sy]) continue;
+            if (!ctl[kCtlRunning * ns + sy]) {
+#pragma unroll
+                for (int l = 0; l < ND; ++l) w[(v * ND + l) * T + i] = 0.0;
+                continue;
+            }
             double wv[ND];
 #pragma unroll
             for (int l = 0; l < ND; ++l) wv[l] = w[(v * ND + l) * T + i];
@@ -344,14 +337,18 @@ __global__ void k_orth_update(DeviceMesh d, const double *__restrict__ V, double
     }
 }
 
-// Segmented sums over the cell blocks of each case, fixed order:
+// Segmented sums over the partial-sum rows of each case (cell blocks or
+// super-blocks, seg[c]..seg[c+1]), fixed order:
 // out[s][q] (op) sum_{b in case(s)} part[b][v(s)][q], q < nq; op 0 store, 1 add,
-// 2 store sqrt.  One warp per (q, s): grid (nq, ns), 32 threads.
-__global__ void k_reduce(const double *__restrict__ part, const int32_t *__restrict__ case_blk, int pstride,
-                         double *out, int ostride, int op)
+// 2 store sqrt.  With vn given, also co[s][q] = sum / vn[s][q]^2 (the
+// Gram-Schmidt coefficient of the unnormalised basis vector q).  One warp per
+// (q, s): grid (nq, ns), 32 threads.
+__global__ void k_reduce(const double *__restrict__ part, const int32_t *__restrict__ seg, int pstride,
+                         double *out, int ostride, int op, const double *__restrict__ vn = nullptr,
+                         int vstride = 0, double *co = nullptr, int cstride = 0)
 {
     const int q = blockIdx.x, sy = blockIdx.y, c = sy >> 2, v = sy & 3;
-    const int b0 = case_blk[c], b1 = case_blk[c + 1];
+    const int b0 = seg[c], b1 = seg[c + 1];
     double acc = 0.0;
     for (int b = b0 + threadIdx.x; b < b1; b += 32) acc += part[(b * NV + v) * pstride + q];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -359,6 +356,10 @@ __global__ void k_reduce(const double *__restrict__ part, const int32_t *__restr
         if (op == 0) out[sy * ostride + q] = acc;
         else if (op == 1) out[sy * ostride + q] += acc;
         else out[sy * ostride + q] = sqrt(acc);
+        if (co) {
+            const double n = vn[sy * vstride + q];
+            co[sy * cstride + q] = n > 0.0 ? acc / (n * n) : 0.0;
+        }
     }
 }
 
@@ -371,35 +372,20 @@ __global__ void k_hadd(double *hc, int hstride, const double *__restrict__ h2, i
     }
 }
 
-// V_{j+1} = w / |w| for running systems (w stored in the V_{j+1} slot).
-__global__ void k_scale(DeviceMesh d, double *__restrict__ vj1, const double *__restrict__ hc, int hstride, int j,
-                        const int32_t *__restrict__ ctl, int ns)
-{
-    const int64_t T = d.T;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= T) return;
-    const int c = d.blk_case[blockIdx.x];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        const int sy = 4 * c + v;
-        const double h = hc[sy * hstride + j + 1];
-        if (!ctl[kCtlRunning * ns + sy] || !(h > 0.0)) continue;
-        const double inv = 1.0 / h;
-#pragma unroll
-        for (int l = 0; l < ND; ++l) vj1[(v * ND + l) * T + i] *= inv;
-    }
-}
-
-// Givens step of column j for each running system (one thread per system).
-__global__ void k_givens(int j, int m, const double *__restrict__ hc, int hstride, double *H, double *cs,
-                         double *sn, double *g, int32_t *ctl, int ns, const double *__restrict__ bnorm,
+__global__ void k_givens(int j, int m, const double *__restrict__ hc, int hstride, double *vn, double *H,
+                         double *cs, double *sn, double *g, int32_t *ctl, int ns, const double *__restrict__ bnorm,
                          const double *__restrict__ beta, double rtol, double eta, int maxit)
 {
     const int sy = blockIdx.x * blockDim.x + threadIdx.x;
     if (sy >= ns || !ctl[kCtlRunning * ns + sy]) return;
+    // Hessenberg column of the normalised basis: h_kj = <V_k, u_j> / (vn_k vn_j),
+    // h_{j+1,j} = |V_{j+1}| / vn_j; the new vector's norm becomes vn_{j+1}
     double h[kMaxRestart + 1];
-    for (int k = 0; k <= j + 1; ++k) h[k] = hc[sy * hstride + k];
-    const double hnext = h[j + 1];
+    const double nj = vn[sy * (m + 1) + j];
+    for (int k = 0; k <= j; ++k) h[k] = hc[sy * hstride + k] / (vn[sy * (m + 1) + k] * nj);
+    const double hnext = hc[sy * hstride + j + 1];
+    h[j + 1] = hnext / nj;
+    vn[sy * (m + 1) + j + 1] = hnext;
     for (int k = 0; k < j; ++k) {
         const double c = cs[sy * m + k], s = sn[sy * m + k];
         const double t0 = h[k], t1 = h[k + 1];
@@ -439,6 +425,15 @@ __global__ void k_backsolve(int m, const double *__restrict__ H, const double *_
     }
 }
 
+// y_k /= vn_k: coefficients of the unnormalised preconditioned vectors
+__global__ void k_scale_y(int m, double *y, const double *__restrict__ vn, const int32_t *__restrict__ ctl, int ns)
+{
+    const int sy = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sy >= ns) return;
+    const int jv = ctl[kCtlJv * ns + sy];
+    for (int k = 0; k < jv; ++k) y[sy * m + k] /= vn[sy * (m + 1) + k];
+}
+
 // x += sum_{k<jv} y_k Z_k with Z_k = M^{-1} V_k kept from the iterations
 template <typename TZ>
 __global__ void k_combine_z(DeviceMesh d, const TZ *__restrict__ Z, const double *__restrict__ y, int m,
@@ -447,28 +442,25 @@ __global__ void k_combine_z(DeviceMesh d, const TZ *__restrict__ Z, const double
     const int64_t T = d.T;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= T) return;
-    const int c = d.blk_case[blockIdx.x];
+    const int v = blockIdx.y;                          // one variable per grid row
+    const int sy = 4 * d.blk_case[blockIdx.x] + v;
+    const int jv = ctl[kCtlJv * ns + sy];
+    if (jv <= 0) return;
     const int64_t vs = (int64_t)NX * T;
+    double acc[ND] = {0, 0, 0, 0, 0};
+    for (int k = 0; k < jv; ++k) {
+        const double yk = y[sy * m + k];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        const int sy = 4 * c + v;
-        const int jv = ctl[kCtlJv * ns + sy];
-        if (jv <= 0) continue;
-        double acc[ND] = {0, 0, 0, 0, 0};
-        for (int k = 0; k < jv; ++k) {
-            const double yk = y[sy * m + k];
-#pragma unroll
-            for (int l = 0; l < ND; ++l) acc[l] += yk * double(Z[k * vs + (v * ND + l) * T + i]);
-        }
-#pragma unroll
-        for (int l = 0; l < ND; ++l) x[(v * ND + l) * T + i] += acc[l];
+        for (int l = 0; l < ND; ++l) acc[l] += yk * double(Z[k * vs + (v * ND + l) * T + i]);
     }
+#pragma unroll
+    for (int l = 0; l < ND; ++l) x[(v * ND + l) * T + i] += acc[l];
 }
 
 // Start (first = 1) or restart of every system: sums[s][0] = |r|^2,
 // sums[s][1] = |b|^2.  Systems of finished cases stay inactive.
-__global__ void k_start(const double *__restrict__ sums, int sstride, double *bnorm, double *beta, int32_t *ctl,
-                        int ns, const int32_t *__restrict__ done, double rtol, int maxit, int first)
+__global__ void k_start(const double *__restrict__ sums, int sstride, double *bnorm, double *beta, double *vn, int m,
+                        int32_t *ctl, int ns, const int32_t *__restrict__ done, double rtol, int maxit, int first)
 {
     const int sy = blockIdx.x * blockDim.x + threadIdx.x;
     if (sy >= ns) return;
@@ -479,6 +471,7 @@ __global__ void k_start(const double *__restrict__ sums, int sstride, double *bn
         ctl[kCtlActive * ns + sy] = !done[sy >> 2];
     }
     beta[sy] = be;
+    vn[sy * (m + 1)] = be;                             // V_0 = r, v_0 = r / beta
     const int act = ctl[kCtlActive * ns + sy] && bn > 0.0 && be > rtol * bn && ctl[kCtlIters * ns + sy] < maxit;
     ctl[kCtlActive * ns + sy] = act;
     ctl[kCtlRunning * ns + sy] = act;
@@ -511,25 +504,6 @@ __global__ void k_init_g(double *g, int m, const double *__restrict__ beta, cons
     }
 }
 
-// V_0 = r / beta for active systems, zero otherwise.
-__global__ void k_init_v0(DeviceMesh d, const double *__restrict__ r, double *__restrict__ v0,
-                          const double *__restrict__ beta, const int32_t *__restrict__ ctl, int ns)
-{
-    const int64_t T = d.T;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= T) return;
-    const int c = d.blk_case[blockIdx.x];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        const int sy = 4 * c + v;
-        const bool act = ctl[kCtlActive * ns + sy];
-        const double s = act ? 1.0 / beta[sy] : 0.0;
-#pragma unroll
-        for (int l = 0; l < ND; ++l) v0[(v * ND + l) * T + i] = act ? r[(v * ND + l) * T + i] * s : 0.0;
-    }
-}
-
-// x = 0 for systems with b = 0 (free stream: zero coefficients exactly)
 __global__ void k_zero_trivial(DeviceMesh d, double *__restrict__ x, const double *__restrict__ bnorm)
 {
     const int64_t T = d.T;
@@ -630,13 +604,9 @@ gks_status read_flags(gks_mesh *m, cudaStream_t s)
 // part[blk][v][k] = partial <V_k, w>, k <= j, per cell block
 gks_status dots(gks_mesh *m, const double *w, int j, double *part, int ps, cudaStream_t s)
 {
-    Work &k = m->wk;
-    const int64_t T = m->d.T;
-    const unsigned g = (unsigned)k.nblk;
-    if (j < 4) k_dots<4><<<g, kDotBlock, 0, s>>>(T, k.V, w, j, part, ps);
-    else if (j < 8) k_dots<8><<<g, kDotBlock, 0, s>>>(T, k.V, w, j, part, ps);
-    else if (j < 16) k_dots<16><<<g, kDotBlock, 0, s>>>(T, k.V, w, j, part, ps);
-    else k_dots<kMaxRestart><<<g, kDotBlock, 0, s>>>(T, k.V, w, j, part, ps);
+    const int64_t nblk = m->wk.nblk;
+    const dim3 g((unsigned)(j + 1), (unsigned)std::min<int64_t>(nblk, kDotMaxTiles));
+    k_dots<<<g, kDotThreads, 0, s>>>(m->d.T, nblk, m->wk.V, w, part, ps);
     note_launch();
     GKS_CUDA(cudaGetLastError());
     return GKS_OK;
@@ -667,16 +637,17 @@ gks_status cls_solve(gks_mesh *m, cudaStream_t s, int32_t *iters, double *relres
     gks_status st;
 
     k_rhs<<<nb, kBlock, 0, s>>>(d, k.w, k.b); note_launch();
-    k_spmv<double, double><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, k.r, 1, k.b, k.part, ps);
+    // residual r = b - K x, written straight into the basis slot V_0 (v_0 = V_0 / beta)
+    k_spmv<double, double><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, k.V, 1, k.b, k.part, ps);
     note_launch();
     k_reduce<<<dim3(2, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.hcol, ps, 0); note_launch();
-    k_start<<<sblocks(ns), 128, 0, s>>>(k.hcol, ps, k.bnorm, k.beta, k.ctl, ns, k.done, rtol, maxit, 1); note_launch();
+    k_start<<<sblocks(ns), 128, 0, s>>>(k.hcol, ps, k.bnorm, k.beta, k.vn, mm, k.ctl, ns, k.done, rtol, maxit, 1);
+    note_launch();
     k_zero_trivial<<<nb, kBlock, 0, s>>>(d, k.x, k.bnorm); note_launch();
     GKS_CUDA(cudaGetLastError());
     if ((st = read_flags(m, s)) != GKS_OK) return st;
 
     while (k.h_flags[0]) {
-        k_init_v0<<<nb, kBlock, 0, s>>>(d, k.r, k.V, k.beta, k.ctl, ns); note_launch();
         k_init_g<<<sblocks(ns * (mm + 1)), 128, 0, s>>>(k.g, mm, k.beta, k.ctl, ns); note_launch();
         for (int j = 0; j < mm; ++j) {
             double *vj = k.V + j * vs, *vj1 = k.V + (j + 1) * vs;
@@ -698,35 +669,37 @@ gks_status cls_solve(gks_mesh *m, cudaStream_t s, int32_t *iters, double *relres
             // classical Gram-Schmidt: twice in FP64 mode; once in the mixed mode, whose
             // cycles only reduce the residual by kInnerRtol before an FP64 restart
             if ((st = dots(m, vj1, j, k.part, ps, s)) != GKS_OK) return st;
-            k_reduce<<<dim3(j + 1, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.hcol, ps, 0); note_launch();
-            k_orth_update<<<nb, kBlock, 0, s>>>(d, k.V, vj1, j, k.hcol, ps, k.ctl, ns, k.part, ps, mixed ? 1 : 0);
+            k_reduce<<<dim3(j + 1, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.hcol, ps, 0, k.vn, mm + 1, k.hco, ps);
+            note_launch();
+            k_orth_update<<<nb, kBlock, 0, s>>>(d, k.V, vj1, j, k.hco, ps, k.ctl, ns, k.part, ps, mixed ? 1 : 0);
             note_launch();
             if (!mixed) {
                 if ((st = dots(m, vj1, j, k.part, ps, s)) != GKS_OK) return st;
-                k_reduce<<<dim3(j + 1, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.y, mm, 0); note_launch();
-                k_orth_update<<<nb, kBlock, 0, s>>>(d, k.V, vj1, j, k.y, mm, k.ctl, ns, k.part, ps, 1); note_launch();
+                k_reduce<<<dim3(j + 1, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.y, mm, 0, k.vn, mm + 1, k.hco, ps);
+                note_launch();
+                k_orth_update<<<nb, kBlock, 0, s>>>(d, k.V, vj1, j, k.hco, ps, k.ctl, ns, k.part, ps, 1); note_launch();
                 k_hadd<<<sblocks(ns * (j + 1)), 128, 0, s>>>(k.hcol, ps, k.y, mm, j, ns); note_launch();
             }
             k_reduce<<<dim3(1, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.hcol + j + 1, ps, 2); note_launch();
             prof_stop(m, slot, s);
-            k_scale<<<nb, kBlock, 0, s>>>(d, vj1, k.hcol, ps, j, k.ctl, ns); note_launch();
-            k_givens<<<sblocks(ns), 128, 0, s>>>(j, mm, k.hcol, ps, k.H, k.cs, k.sn, k.g, k.ctl, ns, k.bnorm, k.beta,
-                                                  rtol, eta, maxit);
+            k_givens<<<sblocks(ns), 128, 0, s>>>(j, mm, k.hcol, ps, k.vn, k.H, k.cs, k.sn, k.g, k.ctl, ns, k.bnorm,
+                                                  k.beta, rtol, eta, maxit);
             note_launch();
             GKS_CUDA(cudaGetLastError());
             if ((st = read_flags(m, s)) != GKS_OK) return st;
             if (!k.h_flags[1]) break;
         }
         k_backsolve<<<sblocks(ns), 128, 0, s>>>(mm, k.H, k.g, k.y, k.ctl, ns); note_launch();
+        k_scale_y<<<sblocks(ns), 128, 0, s>>>(mm, k.y, k.vn, k.ctl, ns); note_launch();
         if (mixed)
-            k_combine_z<float><<<nb, kBlock, 0, s>>>(d, k.Z32, k.y, mm, k.ctl, ns, k.x);
+            k_combine_z<float><<<dim3(nb, NV), kBlock, 0, s>>>(d, k.Z32, k.y, mm, k.ctl, ns, k.x);
         else
-            k_combine_z<double><<<nb, kBlock, 0, s>>>(d, k.Z, k.y, mm, k.ctl, ns, k.x);
+            k_combine_z<double><<<dim3(nb, NV), kBlock, 0, s>>>(d, k.Z, k.y, mm, k.ctl, ns, k.x);
         note_launch();
-        k_spmv<double, double><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, k.r, 1, k.b, k.part, ps);
+        k_spmv<double, double><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, k.V, 1, k.b, k.part, ps);
         note_launch();
         k_reduce<<<dim3(2, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.hcol, ps, 0); note_launch();
-        k_start<<<sblocks(ns), 128, 0, s>>>(k.hcol, ps, k.bnorm, k.beta, k.ctl, ns, k.done, rtol, maxit, 0);
+        k_start<<<sblocks(ns), 128, 0, s>>>(k.hcol, ps, k.bnorm, k.beta, k.vn, mm, k.ctl, ns, k.done, rtol, maxit, 0);
         note_launch();
         GKS_CUDA(cudaGetLastError());
         if ((st = read_flags(m, s)) != GKS_OK) return st;

@@ -64,6 +64,8 @@ struct DeviceMesh {
     double *P = nullptr;             // [25][T] inverse of the ILU(0) diagonal block, row-major
     // FP32 copies of the operator and factors (mixed precision)
     float *D32 = nullptr, *P32 = nullptr, *alpha32 = nullptr, *ex32 = nullptr, *ey32 = nullptr;
+    double *ox = nullptr, *oy = nullptr;  // [3][T] neighbour centroid in i's scaled frame (limiter)
+    int32_t *kord = nullptr;         // [T] reconstruction order k_i of Eq. (28) (limiter)
     int32_t *cf = nullptr;           // [3][T] (face << 1) | side, -1 unused
     int32_t *perm = nullptr;         // [T] internal -> caller cell (-1 for padding)
     int32_t *lvl_lo = nullptr;       // rows sorted by forward level
@@ -84,11 +86,13 @@ struct Work {
     double *w = nullptr;             // [4][T] state (internal order)
     double *w_old = nullptr;         // [4][T]
     double *x = nullptr;             // [20][T] CLS coefficients (warm start)
+    double *xl = nullptr;            // [20][T] limited coefficients (limiter on)
+    int32_t *lflag = nullptr;        // [T] 0 untouched, 1 limited, 2 reset to the average
     double *b = nullptr, *r = nullptr, *t2 = nullptr, *t3 = nullptr;  // [20][T]
     float *t2_32 = nullptr, *t3_32 = nullptr;  // [20][T] FP32 preconditioner work
-    double *V = nullptr;             // [(m+1)][20][T]
-    double *Z = nullptr;             // [m][20][T] preconditioned basis M^{-1} V_k (FP64 path)
-    float *Z32 = nullptr;            // [m][20][T] preconditioned basis (mixed path)
+    double *V = nullptr;             // [(m+1)][20][T] Krylov basis, unnormalised: v_k = V_k / vn_k
+    double *Z = nullptr;             // [m][20][T] M^{-1} V_k (FP64 path)
+    float *Z32 = nullptr;            // [m][20][T] M^{-1} V_k (mixed path)
     double *flux = nullptr;          // [4][F]
     double *part = nullptr;          // [nblk][4][m+2] partial sums per cell block
     double *dpart = nullptr;         // [nblk][4] partial minima / sums
@@ -97,7 +101,9 @@ struct Work {
     double *cs = nullptr, *sn = nullptr;  // [ns][m]
     double *g = nullptr;             // [ns][m+1]
     double *y = nullptr;             // [ns][m]
-    double *hcol = nullptr;          // [ns][m+2]
+    double *hcol = nullptr;          // [ns][m+2] raw sums <V_k, u> of the current column, then |V_{j+1}|
+    double *hco = nullptr;           // [ns][m+2] Gram-Schmidt coefficients <V_k, u> / vn_k^2
+    double *vn = nullptr;            // [ns][m+1] norms vn_k of the stored basis vectors
     double *bnorm = nullptr, *beta = nullptr;  // [ns]
     int32_t *ctl = nullptr;          // [kCtlFields][ns]
     int32_t *flags = nullptr;        // [4]: any active, any running, all cases done
@@ -171,6 +177,10 @@ gks_status launch_permute(const double *src, double *dst, const int32_t *perm, i
 gks_status launch_steady_partial(gks_mesh *m, cudaStream_t s);
 // per-case step control for runs: dt = min(cfl dt, t_final - t) or 0 when done; t += dt
 gks_status launch_clip_dt(gks_mesh *m, cudaStream_t s);
+// shock detector + DWBAP limiter: m->wk.xl from m->wk.x (gks_limiter.cu)
+gks_status launch_limiter(gks_mesh *m, const double *w, const double *x, cudaStream_t s);
+// caller-ordered copy of the limiter flags of the last launch_limiter
+gks_status launch_scatter_flags(gks_mesh *m, int32_t *flags_out, cudaStream_t s);
 
 // optional CUDA-event timing of one kernel class (no-op unless enabled)
 int prof_start(gks_mesh *m, int cls, cudaStream_t s);

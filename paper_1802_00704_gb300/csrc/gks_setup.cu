@@ -192,8 +192,8 @@ namespace {
 struct HostCase {
     int64_t T = 0, F = 0, nbf = 0, nk1 = 0, nnzb = 0, bw = 0;
     int32_t nlo = 0, nup = 0;
-    std::vector<int32_t> perm, nb, cf, fl, fr, ftag, fperm, lev_lo, lev_up;
-    std::vector<double> area, iarea, h, mxx, mxy, myy, inrad, alpha, ex, ey, a0, D, P;
+    std::vector<int32_t> perm, nb, cf, fl, fr, ftag, fperm, lev_lo, lev_up, kord;
+    std::vector<double> area, iarea, h, mxx, mxy, myy, inrad, alpha, ex, ey, ox, oy, a0, D, P;
     std::vector<double> fnx, fny, flen, gl, gr, bc;
 };
 
@@ -293,6 +293,8 @@ gks_status build_case(const CaseIn &in, double w, HostCase &hc)
     // ---- CLS blocks in internal order
     std::vector<int32_t> h_nb(3 * T, -1), h_cf(3 * T, -1);
     std::vector<double> h_alpha(3 * T, 0.0), h_ex(3 * T, 0.0), h_ey(3 * T, 0.0), h_a0(15 * T, 0.0);
+    std::vector<double> h_ox(3 * T, 0.0), h_oy(3 * T, 0.0);
+    std::vector<int32_t> h_kord(T, 2);
     std::vector<double> h_D(15 * T, 0.0), h_Dfull(25 * T, 0.0);
     std::vector<double> h_area(T), h_iarea(T), h_h(T), h_mxx(T), h_mxy(T), h_myy(T), h_inrad(T);
     int64_t nk1 = 0, nnzb = 0, bw = 0;
@@ -305,6 +307,7 @@ gks_status build_case(const CaseIn &in, double w, HostCase &hc)
         h_mxy[i] = c.sxy / (c.h * c.h);
         h_myy[i] = c.syy / (c.h * c.h);
         h_inrad[i] = c.inrad;
+        h_kord[i] = c.k;
         nk1 += c.k == 1;
     }
     for (int64_t i = 0; i < T; ++i) {
@@ -335,6 +338,8 @@ gks_status build_case(const CaseIn &in, double w, HostCase &hc)
             h_alpha[slot * T + i] = w * w * c.h / d.h;
             h_ex[slot * T + i] = c.k == 2 ? dx : 0.0;
             h_ey[slot * T + i] = c.k == 2 ? dy : 0.0;
+            h_ox[slot * T + i] = dx;
+            h_oy[slot * T + i] = dy;
             for (int l = 0; l < 5; ++l) h_a0[(slot * 5 + l) * T + i] = l < ni ? a0[l] : 0.0;
             bw = std::max<int64_t>(bw, std::llabs((long long)(j - i)));
             ++slot;
@@ -490,6 +495,9 @@ gks_status build_case(const CaseIn &in, double w, HostCase &hc)
     hc.alpha = std::move(h_alpha);
     hc.ex = std::move(h_ex);
     hc.ey = std::move(h_ey);
+    hc.ox = std::move(h_ox);
+    hc.oy = std::move(h_oy);
+    hc.kord = std::move(h_kord);
     hc.a0 = std::move(h_a0);
     hc.D = std::move(h_D);
     hc.P = std::move(h_P);
@@ -570,6 +578,8 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
     std::vector<double> h_area(T, 1.0), h_iarea(T, 1.0), h_h(T, 1.0), h_mxx(T, 0.0), h_mxy(T, 0.0), h_myy(T, 0.0);
     std::vector<double> h_inrad(T, std::numeric_limits<double>::infinity());
     std::vector<double> h_alpha(3 * T, 0.0), h_ex(3 * T, 0.0), h_ey(3 * T, 0.0), h_a0(15 * T, 0.0);
+    std::vector<double> h_ox(3 * T, 0.0), h_oy(3 * T, 0.0);
+    std::vector<int32_t> h_kord(T, 2);
     std::vector<double> h_D(15 * T, 0.0), h_P(25 * T, 0.0);
     std::vector<int32_t> h_fl(F), h_fr(F), h_ftag(F), h_fperm(F), h_face_case(F);
     std::vector<double> h_fnx(F), h_fny(F), h_flen(F), h_gl(4 * F), h_gr(4 * F), h_bc(4 * F);
@@ -600,6 +610,7 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
         place(hc.mxx, Tc, 1, h_mxx, T, o); place(hc.mxy, Tc, 1, h_mxy, T, o); place(hc.myy, Tc, 1, h_myy, T, o);
         place(hc.inrad, Tc, 1, h_inrad, T, o);
         place(hc.alpha, Tc, 3, h_alpha, T, o); place(hc.ex, Tc, 3, h_ex, T, o); place(hc.ey, Tc, 3, h_ey, T, o);
+        place(hc.ox, Tc, 3, h_ox, T, o); place(hc.oy, Tc, 3, h_oy, T, o); place(hc.kord, Tc, 1, h_kord, T, o);
         place(hc.a0, Tc, 15, h_a0, T, o); place(hc.D, Tc, 15, h_D, T, o); place(hc.P, Tc, 25, h_P, T, o);
         for (int64_t f = 0; f < Fc; ++f) {
             h_fl[fo + f] = (int32_t)(o + hc.fl[f]);
@@ -654,6 +665,10 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
     UP(fl, h_fl); UP(fr, h_fr); UP(ftag, h_ftag); UP(fperm, h_fperm); UP(fnx, h_fnx); UP(fny, h_fny);
     UP(flen, h_flen); UP(gl, h_gl); UP(gr, h_gr); UP(bc, h_bc);
     UP(blk_case, h_blk_case); UP(case_blk, h_case_blk); UP(face_case, h_face_case);
+
+    if (cfg.limiter) {
+        UP(ox, h_ox); UP(oy, h_oy); UP(kord, h_kord);
+    }
     if (cfg.precision == GKS_MIXED) {
         auto f32 = [](const std::vector<double> &v) { return std::vector<float>(v.begin(), v.end()); };
         UP(D32, f32(h_D)); UP(P32, f32(h_P)); UP(alpha32, f32(h_alpha)); UP(ex32, f32(h_ex)); UP(ey32, f32(h_ey));
@@ -677,8 +692,11 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
         AL(Z, (size_t)mm * 20 * T);
     }
     AL(part, (size_t)nblk * 4 * (mm + 2)); AL(dpart, (size_t)nblk * 4);
+    if (cfg.limiter) {
+        AL(xl, 20 * T); AL(lflag, T);
+    }
     AL(H, ns * (mm + 1) * mm); AL(cs, ns * mm); AL(sn, ns * mm); AL(g, ns * (mm + 1)); AL(y, ns * mm);
-    AL(hcol, ns * (mm + 2)); AL(bnorm, ns); AL(beta, ns); AL(ctl, kCtlFields * ns); AL(flags, 4);
+    AL(hcol, ns * (mm + 2)); AL(hco, ns * (mm + 2)); AL(vn, ns * (mm + 1)); AL(bnorm, ns); AL(beta, ns); AL(ctl, kCtlFields * ns); AL(flags, 4);
     AL(dt, n_cases); AL(tcase, n_cases); AL(tfinal, n_cases); AL(done, n_cases); AL(scal, 8); AL(status, n_cases);
 #undef AL
     GKS_CUDA(cudaMemset(k.x, 0, sizeof(double) * 20 * T));

@@ -26,7 +26,7 @@ FP64, MIXED = 0, 1
 EXPORTED = ["gks_config_default", "gks_mesh_create", "gks_mesh_destroy", "gks_mesh_get_stats", "gks_cfl_dt",
             "gks_cls_reconstruct", "gks_reset_warm_start", "gks_flux", "gks_step", "gks_run", "gks_point_flux",
             "gks_profile_begin", "gks_profile_end", "gks_launch_count", "gks_cfl_dt_noalloc", "gks_batch_create",
-            "gks_batch_run", "gks_last_error"]
+            "gks_batch_run", "gks_limit", "gks_last_error"]
 PROF_FLUX, PROF_SPMV, PROF_ILU, PROF_ORTH, PROF_UPDATE = range(5)
 
 
@@ -40,7 +40,7 @@ class Config(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("mu", C.c_double), ("cls_w", C.c_double),
                 ("gmres_m", C.c_int32), ("gmres_maxit", C.c_int32), ("gmres_rtol", C.c_double),
                 ("precision", C.c_int32), ("precond", C.c_int32), ("ilu_sweeps", C.c_int32),
-                ("tau2_exact", C.c_int32), ("reserved", C.c_int32 * 8)]
+                ("tau2_exact", C.c_int32), ("limiter", C.c_int32), ("reserved", C.c_int32 * 7)]
 
 
 class SolveInfo(C.Structure):
@@ -111,6 +111,8 @@ def load():
     lib.gks_reset_warm_start.restype = st
     lib.gks_flux.argtypes = [P, P, P, D, P, P]
     lib.gks_flux.restype = st
+    lib.gks_limit.argtypes = [P, P, P, P, P, P]
+    lib.gks_limit.restype = st
     lib.gks_step.argtypes = [P, P, C.POINTER(D), C.POINTER(StepInfo), P]
     lib.gks_step.restype = st
     lib.gks_run.argtypes = [P, P, D, I64, D, C.POINTER(RunInfo), P]
@@ -271,6 +273,21 @@ class GksMesh:
         if check:
             _check(st, "gks_flux")
         return out, st
+
+    def limit(self, w, coef, out=None, flags=None, stream=None):
+        """Shock detector and DWBAP limiter on coef (mesh created with limiter=1);
+        returns (limited coefficients, flags: 0 untouched, 1 limited, 2 reset)."""
+        import torch
+        if out is None:
+            out = torch.empty((4, 5, self.T), dtype=torch.float64, device=w.device)
+        if flags is None:
+            flags = torch.empty(self.T, dtype=torch.int32, device=w.device)
+        if not (flags.is_cuda and flags.dtype == torch.int32 and flags.is_contiguous() and flags.numel() == self.T):
+            raise TypeError("flags: expected a contiguous int32 CUDA tensor of n_tri elements")
+        _check(self._lib.gks_limit(self._h, _dev(w, (4, self.T)), _dev(coef, (4, 5, self.T)),
+                                   _dev(out, (4, 5, self.T)), C.c_void_p(flags.data_ptr()), _stream(stream)),
+               "gks_limit")
+        return out, flags
 
     def step(self, w, dt: float = 0.0, stream=None, check=True) -> dict:
         info = StepInfo()

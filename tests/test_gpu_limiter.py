@@ -1,0 +1,149 @@
+"""Parity of the CUDA shock detector and DWBAP limiter (Sec. III.C, Eqs.
+(34)-(38)) with the oracle, and the limited scheme on shock tubes.
+
+Tolerances: from the same input coefficients the flags are equal and the
+limited coefficients agree within 1e-12 of each variable's largest coefficient
+(the two sides differ only in the rounding of atan, tan, pow and hypot); limited
+FP64 steps agree within 1e-10 relative max after one step and 1e-8 after 40.
+The Sod run of the 400 x 8 strip (6,400 triangles, t = 0.2) is checked against
+the exact Riemann solution instead of the oracle (which would need minutes)."""
+import numpy as np
+import pytest
+
+from paper_1802_00704_gb300 import inputs as I
+from tests.exact_riemann import exact_riemann
+from tests.gpu_util import dev, host, needs_gpu, rel_max, torch
+
+pytestmark = [pytest.mark.gpu, needs_gpu]
+
+
+@pytest.fixture(scope="module")
+def O():
+    from oracle import oracle
+    oracle.build()
+    return oracle
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_1802_00704_gb300 import build, gks
+    build.build()
+    return gks
+
+
+LAX = ((0.445, 0.698, 0.0, 3.528), (0.5, 0.0, 0.0, 0.571))
+CASES = {
+    "sod100x4": lambda: I.sod_case(100, 4),
+    "lax90x5": lambda: I.riemann_strip_case(90, 5, left=LAX[0], right=LAX[1], seed=7, name="lax"),
+    "ratio10_70x6": lambda: I.riemann_strip_case(70, 6, left=(1.0, 0.0, 0.0, 1.0), right=(0.1, 0.0, 0.0, 0.1),
+                                                 seed=21, name="ratio10"),
+}
+
+
+def _coef_err(a, b):
+    """Per variable: max |a - b| over its 5 coefficients and all cells, over the
+    variable's largest coefficient (floored at 1e-8 of the largest overall)."""
+    a = np.asarray(a).reshape(4, -1)
+    b = np.asarray(b).reshape(4, -1)
+    floor = 1e-8 * np.max(np.abs(b))
+    return np.max(np.abs(a - b), axis=1) / np.maximum(np.max(np.abs(b), axis=1), floor)
+
+
+def _advance_oracle(O, c, n):
+    om = O.OracleMesh(c.mesh, limiter=1)
+    w = c.w0.copy()
+    for _ in range(n):
+        assert om.step(w).status == 0
+    return om, w
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("steps_before", [0, 25])
+def test_limit_kernel_matches_oracle(O, G, name, steps_before):
+    c = CASES[name]()
+    om, w = _advance_oracle(O, c, steps_before)
+    coef, _, _, _ = om.cls_solve(w)
+    ref, rflag = om.limit(w, coef)
+    assert rflag.sum() > 0
+    gm = G.GksMesh(c.mesh, limiter=1)
+    out, flags = gm.limit(dev(w), dev(coef))
+    gflag = host(flags)
+    assert np.array_equal(gflag, rflag), (np.flatnonzero(gflag != rflag), gflag.sum(), rflag.sum())
+    assert np.all(_coef_err(host(out), ref) <= 1e-12), _coef_err(host(out), ref)
+    # untouched cells keep their coefficients bit for bit
+    keep = rflag == 0
+    assert np.array_equal(host(out)[:, :, keep], coef[:, :, keep])
+
+
+def test_smooth_data_pass_unchanged(G):
+    c = I.advection_case(20)
+    gm = G.GksMesh(c.mesh, limiter=1)
+    w = dev(c.w0)
+    coef, _ = gm.cls_reconstruct(w)
+    out, flags = gm.limit(w, coef)
+    assert int(host(flags).sum()) == 0
+    assert torch.equal(out, coef)
+
+
+def test_limit_refused_without_limiter_data(G):
+    c = I.advection_case(6)
+    gm = G.GksMesh(c.mesh)
+    w = dev(c.w0)
+    coef, _ = gm.cls_reconstruct(w)
+    with pytest.raises(G.GksError):
+        gm.limit(w, coef)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_limited_steps_match_oracle(O, G, name):
+    c = CASES[name]()
+    om = O.OracleMesh(c.mesh, limiter=1)
+    gm = G.GksMesh(c.mesh, limiter=1)
+    wo = c.w0.copy()
+    wg = dev(c.w0)
+    for n in range(40):
+        info = om.step(wo)
+        assert info.status == 0
+        gm.step(wg, info.dt)
+        if n == 0:
+            assert np.all(rel_max(host(wg), wo, axis=1) <= 1e-10), rel_max(host(wg), wo, axis=1)
+    assert np.all(rel_max(host(wg), wo, axis=1) <= 1e-8), rel_max(host(wg), wo, axis=1)
+
+
+def _l1_density(c, w, t):
+    from oracle import oracle
+    cg = oracle.OracleMesh(c.mesh).cell_geometry()
+    left, right = c.meta["left"], c.meta["right"]
+    ex = exact_riemann(cg["cx"], t, (left[0], left[1], left[3]), (right[0], right[1], right[3]))
+    area = cg["area"]
+    return float(np.sum(area * np.abs(w[0] - ex[0])) / area.sum())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_sod_400x8_to_t02_against_exact_solution(O, G, precision):
+    c = I.sod_case(400, 8)
+    gm = G.GksMesh(c.mesh, limiter=1, precision=G.MIXED if precision == "mixed" else G.FP64)
+    w = dev(c.w0)
+    info = gm.run(w, t_final=0.2, max_steps=100000)
+    assert abs(info["t"] - 0.2) <= 1e-14
+    wh = host(w)
+    p = 0.4 * (wh[3] - 0.5 * (wh[1] ** 2 + wh[2] ** 2) / wh[0])
+    assert np.all(wh[0] > 0) and np.all(p > 0)
+    l1 = _l1_density(c, wh, 0.2)
+    print(f"sod 400x8 {precision}: L1(rho - exact) = {l1:.3e}, max |rho v| = {np.max(np.abs(wh[2])):.3e}")
+    assert l1 < 4e-3
+
+
+def test_limited_batch_matches_single_runs(G):
+    cases = [CASES[k]() for k in CASES] + [I.advection_case(10, seed=3)]
+    b = G.GksMesh.batch([c.mesh for c in cases], limiter=1)
+    w = dev(np.ascontiguousarray(np.concatenate([c.w0 for c in cases], axis=1)))
+    r = b.batch_run(w, max_steps=6)
+    assert r["n_failed"] == 0
+    wh, o = host(w), 0
+    for c in cases:
+        m = G.GksMesh(c.mesh, limiter=1)
+        ws = dev(c.w0)
+        m.run(ws, max_steps=6)
+        assert rel_max(wh[:, o:o + c.mesh.n_tri], host(ws)) <= 1e-13, c.name
+        o += c.mesh.n_tri
