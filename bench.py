@@ -38,8 +38,10 @@ FP64_PEAK_TFLOPS = 4 * 152 * 2.07e9 / 1e12
 # (dadd + dmul + 2 dfma, ncu instruction counters on the 399,424-triangle case;
 # profiles/flux_fp64_shock_vortex_400k.md).
 FLUX_FP64_FLOP_PER_GP = 8389.3
-# FP64 flops per Gauss point left in the mixed flux kernel (to be measured).
-FLUX_MIXED_FP64_FLOP_PER_GP = None
+# FP64 and FP32 flops per Gauss point of the mixed flux kernel (same counters,
+# 1,200,168 Gauss points; profiles/flux_mixed_shock_vortex_400k.md).
+FLUX_MIXED_FP64_FLOP_PER_GP = 932.7
+FLUX_MIXED_FP32_FLOP_PER_GP = 8245.1
 
 WORKLOADS = {
     "shock_vortex_1m": dict(kind="shock_vortex", nx=1000, ny=500),
@@ -58,9 +60,10 @@ def make_case(name: str, replica: int = 0):
 
 
 def source_hash() -> str:
+    """Hash of the face-flux kernel's sources (the kernel the traffic record describes)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1802_00704_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in ("gks_flux.cu", "gks_kinetic.cuh"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -75,9 +78,9 @@ def measured_peaks() -> dict:
 
 
 def traffic_record(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources (profiles/traffic.txt: kernel source_hash bytes
-    units_per_launch)."""
+    """(DRAM bytes per launch, Gauss points of that launch) from the committed
+    ncu summary, if it was taken on the current kernel sources
+    (profiles/traffic.txt: kernel source_hash bytes gauss_points)."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
@@ -185,25 +188,40 @@ def oracle_sample(steps: int, warmup: int = 0):
             "seconds": el}
 
 
-def bytes_per_cell(cls: str, sweeps: int, exact: bool, mixed: bool) -> float:
-    """Algorithmic DRAM bytes per cell of one launch group of a kernel class.
-    Operator data per cell: diagonal block 15 values, ILU pivot inverse 25,
-    off-diagonal blocks 3 x (alpha, dx, dy) + 3 int32 neighbours; vectors 20
-    values.  FP64 path: 8-byte everything.  Mixed: 4-byte operator, factors and
-    preconditioner vectors; the Krylov vectors stay FP64."""
-    sm = 4 if mixed else 8          # operator / factor values
-    sz = 4 if mixed else 8          # preconditioner work vectors
-    if cls == "spmv":               # D, offdiag, x (precond output), y (Krylov, FP64)
-        return sm * (15 + 9) + 12 + sz * 20 + 8 * 20
+def class_bytes(cls: str, prof: dict, T: int, F: int, steps: int, sweeps: int, exact: bool, mixed: bool,
+                basis32: bool) -> float:
+    """Algorithmic DRAM bytes moved by one kernel class over the timed region,
+    from the solver's work counters (Arnoldi iterations n, sum of j + 1 over
+    them, preconditioner applications).  Per cell: operator = diagonal block 15
+    values + 3 off-diagonal blocks of 3 values + 3 int32 neighbours; ILU pivot
+    inverse 25 values; a Krylov or work vector 20 values; a neighbour reads the
+    first 2 of the 5 unknowns of each variable (8 values, counted once).  Sizes:
+    sM operator/factor values, sZ preconditioner vectors (8 FP64 path, 4 mixed),
+    sB Krylov basis (8, or 4 with the FP32-stored basis)."""
+    sM = 4 if mixed else 8
+    sZ = 4 if mixed else 8
+    sB = 4 if basis32 else 8
+    n, jsum = prof["arnoldi"], prof["arnoldi_jsum"]
+    op = sM * (15 + 9) + 12
+    if cls == "orth":
+        # per iteration j: dots read V_0..V_j and w, the update reads them again and
+        # writes w: (2 j + 5) vectors; FP64 mode runs the pair twice (CGS2)
+        vecs = 2 * jsum + 3 * n
+        return T * 20 * sB * vecs * (1 if mixed else 2)
+    if cls == "spmv":                   # y = K z: z (own + neighbour values), operator, y (basis)
+        return T * (op + 20 * sZ + 20 * sB) * n
     if cls == "ilu":
-        if exact:                   # one forward and one backward pass over all rows
-            return 2 * (sm * (25 + 9) + 12) + 8 * 20 + 3 * sz * 20 + 8
-        first = sm * 25 + 8 * 20 + sz * 20
-        fwd = sm * (25 + 9) + 12 + 8 * 20 + 2 * sz * 20
-        bwd = sm * (25 + 9) + 12 + 3 * sz * 20
-        return first + sweeps * (fwd + bwd)
-    if cls == "update":             # 3 faces x 4 fluxes, w in/out, 1/area, 3 int32
-        return 8 * (12 + 4 + 4 + 1) + 12
+        pc = prof["precond"]
+        if exact:
+            fwd = 20 * sB + 8 * sZ + sM * 25 + op - sM * 15 + 20 * sZ
+            bwd = 20 * sZ + 8 * sZ + sM * 25 + op - sM * 15 + 20 * sZ
+            return T * (fwd + bwd) * pc
+        first = 20 * sB + sM * 25 + 20 * sZ
+        fwd = 20 * sB + 8 * sZ + sM * (25 + 9) + 12 + 20 * sZ
+        bwd = 20 * sZ + 8 * sZ + sM * (25 + 9) + 12 + 20 * sZ
+        return T * (first + sweeps * (fwd + bwd)) * pc
+    if cls == "update":                 # w in/out, 1/|Omega|, 3 face slots; each face flux once
+        return (T * (8 * 8 + 8 + 12) + F * 4 * 8) * steps
     raise KeyError(cls)
 
 
@@ -213,8 +231,10 @@ def timed_leg(args, case, precision: str, world: int, dev, sample_clocks: bool):
 
     from paper_1802_00704_gb300 import gks
     exact = args.precond == "exact"
+    mixed = precision == "mixed"
     m = gks.GksMesh(case.mesh, precond=gks.PC_ILU_EXACT if exact else gks.PC_ILU_SWEEP, ilu_sweeps=args.sweeps,
-                    precision=gks.MIXED if precision == "mixed" else gks.FP64)
+                    precision=gks.MIXED if mixed else gks.FP64, basis_fp32=int(mixed and args.basis == "fp32"),
+                    limiter=int(args.limiter), warm_extrap=int(args.warm == "extrap"))
     w = torch.from_numpy(case.w0.copy()).to(dev)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -277,47 +297,43 @@ def run_gks(args, world, rank, local):
     e2e_value = world * T * args.steps / e2e_s
     bytes_state = 4 * T * 8
 
-    # roofline of the dominant kernel class
+    # per-class device time (CUDA events on the launching stream) against each class's roof
     prof, info = main["prof"], main["info"]
     names = ["flux", "spmv", "ilu", "orth", "update"]
-    share = {nm: prof["ms"][q] for q, nm in enumerate(names)}
-    dominant = max(share, key=share.get)
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
     hbm_src = "measured" if hbm_peak else "fallback"
     hbm_peak = hbm_peak or HBM_FALLBACK_GBS
-    q = names.index(dominant)
+    basis32 = mixed and args.basis == "fp32"
+    classes = {}
+    for q, nm in enumerate(names):
+        ms_c = prof["ms"][q]
+        ent = {"ms": round(ms_c, 3), "launch_groups": prof["n"][q]}
+        if nm != "flux" and ms_c > 0:
+            by = class_bytes(nm, prof, T, F, args.steps, args.sweeps, exact, mixed, basis32)
+            gbs = by / (ms_c / 1e3) / 1e9
+            ent.update({"bytes": by, "gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 3)})
+        classes[nm] = ent
+    # the dominant kernel is the face-flux kernel (one launch per step): ALU-bound
+    q = names.index("flux")
     per_launch_ms = prof["ms"][q] / max(prof["n"][q], 1)
-    roof = {"kernel": dominant, "launches": prof["n"][q], "avg_ms": per_launch_ms}
-    if dominant == "flux" and not mixed:
-        gp = 2 * F
-        ach = FLUX_FP64_FLOP_PER_GP * gp / (per_launch_ms / 1e3) / 1e12
-        roof.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": ach / FP64_PEAK_TFLOPS, "flop_per_gauss_point": FLUX_FP64_FLOP_PER_GP,
-                     "peak_source": "FP64 pipe rate from unit count and 2070 MHz clock"})
-    elif dominant == "flux":
-        gp = 2 * F
-        ach = FLUX_MIXED_FP64_FLOP_PER_GP * gp / (per_launch_ms / 1e3) / 1e12 if FLUX_MIXED_FP64_FLOP_PER_GP else None
-        roof.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": ach / FP64_PEAK_TFLOPS if ach else None,
-                     "flop_per_gauss_point": FLUX_MIXED_FP64_FLOP_PER_GP,
-                     "peak_source": "FP64 pipe rate from unit count and 2070 MHz clock"})
-    elif dominant == "orth":
-        # CGS2 at Arnoldi index j moves 2 x 160 (2 j + 5) bytes per cell (FP64 basis)
-        its = max(1, int(round(info["gmres_iters"] / 4 / max(info["steps"], 1))))
-        jbar = (its - 1) / 2.0
-        per_cell = 2 * 8 * 20 * ((jbar + 2) + (jbar + 3))
-        ach = per_cell * T / (per_launch_ms / 1e3) / 1e9
-        roof.update({"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                     "peak_source": hbm_src, "bytes_per_cell": per_cell})
-    else:
-        per_cell = bytes_per_cell(dominant, args.sweeps, exact, mixed)
-        ach = per_cell * T / (per_launch_ms / 1e3) / 1e9
-        roof.update({"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                     "peak_source": hbm_src, "bytes_per_cell": per_cell})
-    tr = traffic_record(("mixed_" if mixed else "") + dominant)
-    roof["traffic"] = tr[0] if tr else None
-    roof["class_ms"] = {nm: round(share[nm], 3) for nm in names}
+    gp = 2 * F
+    flop64 = FLUX_FP64_FLOP_PER_GP if not mixed else FLUX_MIXED_FP64_FLOP_PER_GP
+    ach = flop64 * gp / (per_launch_ms / 1e3) / 1e12 if flop64 else None
+    roof = {"kernel": "k_face_flux", "launches": prof["n"][q], "avg_ms": per_launch_ms, "bound": "alu",
+            "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP64_PEAK_TFLOPS if ach else None, "fp64_flop_per_gauss_point": flop64,
+            "peak_source": "FP64 pipe rate from unit count (4 flop/clk/SM) and the 2070 MHz clock"}
+    if mixed:
+        roof["fp32_flop_per_gauss_point"] = FLUX_MIXED_FP32_FLOP_PER_GP
+    tr = traffic_record(("mixed_" if mixed else "") + "flux")
+    roof["traffic"] = tr[0] * gp / tr[1] if tr else None      # scaled by Gauss points
+    roof["hbm_peak"] = {"gbs": hbm_peak, "source": hbm_src}
+    roof["classes"] = classes
+    roof["work"] = {"arnoldi_per_step": prof["arnoldi"] / args.steps,
+                    "mean_j": (prof["arnoldi_jsum"] - prof["arnoldi"]) / max(prof["arnoldi"], 1),
+                    "precond_per_step": prof["precond"] / args.steps,
+                    "fp64_residuals_per_step": prof["residuals"] / args.steps}
     st = main["stats"]
 
     out = {
@@ -327,6 +343,8 @@ def run_gks(args, world, rank, local):
         "config": {"workload": f"shock-vortex {case.mesh.nx}x{case.mesh.ny} split quads, {T} triangles, "
                                f"{F} faces, GMRES(30) rtol 1e-12",
                    "n_tri": T, "n_face": F, "precision": args.precision,
+                   "krylov_basis": "fp32" if basis32 else "fp64", "limiter": bool(args.limiter),
+                   "warm_start": args.warm,
                    "precond": ("ilu0_rcm_exact" if exact else f"ilu0_rcm_sweep{args.sweeps}"),
                    "l2": f"inputs larger than L2: {st['device_bytes'] / 2**30:.1f} GiB resident per replica",
                    "parallelism": "replicas" if world > 1 else "single GPU",
@@ -348,7 +366,8 @@ def run_gks(args, world, rank, local):
         l1 = np.sum(area * np.abs(wm - wf), axis=1) / np.sum(area * np.abs(wf), axis=1)
         out["fp64"] = {"value": world * T * args.steps / (ref["ms"] / 1e3), "ms_per_step": ref["ms"] / args.steps,
                        "gmres_iters_per_step": ref["info"]["gmres_iters"] / max(ref["info"]["steps"], 1),
-                       "class_ms": {nm: round(ref["prof"]["ms"][q], 3) for q, nm in enumerate(names)}}
+                       "class_ms": {nm: round(ref["prof"]["ms"][q], 3) for q, nm in enumerate(names)},
+                       "arnoldi_per_step": ref["prof"]["arnoldi"] / args.steps}
         out["mixed_vs_fp64_rel_l1"] = [float(x) for x in l1]
         out["speedup_vs_fp64"] = value / out["fp64"]["value"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -385,6 +404,11 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison leg")
     ap.add_argument("--sweeps", type=int, default=2)
+    ap.add_argument("--basis", default="fp64", choices=["fp32", "fp64"],
+                    help="storage of the Krylov basis in the mixed path (arithmetic stays FP64)")
+    ap.add_argument("--limiter", action="store_true", help="shock detector + DWBAP limiter on")
+    ap.add_argument("--warm", default="extrap", choices=["prev", "extrap"],
+                    help="CLS initial guess: previous solution, or linear extrapolation of the last two")
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

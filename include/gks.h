@@ -112,7 +112,12 @@ typedef struct gks_config {
                               time integral of Eq. (8) carries                          */
     int32_t limiter;       /* 1: shock detector (Eq. (37)) and DWBAP limiter (Eqs.
                               (34)-(36)) on the reconstruction before the flux        */
-    int32_t reserved[7];   /* must be zero                                             */
+    int32_t basis_fp32;    /* mixed precision only: 1 stores the Krylov basis in FP32
+                              (dot products, updates, norms and Givens stay FP64)     */
+    int32_t warm_extrap;   /* 1: start each solve from 2 x_{n-1} - x_{n-2} (linear
+                              extrapolation of the last two solutions) instead of
+                              x_{n-1}; the same tolerance is met, in fewer iterations */
+    int32_t reserved[5];   /* must be zero                                             */
 } gks_config;
 
 typedef struct gks_mesh gks_mesh;
@@ -309,6 +314,11 @@ GKS_EXPORT gks_status gks_point_flux(int64_t n, const double *wl, const double *
 typedef struct gks_profile {
     int64_t n[5];          /* timed launches (or launch groups) per class              */
     double ms[5];          /* summed device time per class                             */
+    int64_t arnoldi;       /* Arnoldi iterations (all systems of the handle together)  */
+    int64_t arnoldi_jsum;  /* sum over those iterations of j + 1 (vectors orthogonalised
+                              against), for the byte count of the class 3 kernels      */
+    int64_t precond;       /* preconditioner applications                              */
+    int64_t residuals;     /* FP64 residual evaluations (operator applications, mode 1) */
 } gks_profile;
 
 GKS_EXPORT gks_status gks_profile_begin(gks_mesh *mesh, int32_t class_mask);

@@ -56,7 +56,9 @@ gks_status check_config(const gks_config &c)
               c.gmres_m <= kMaxRestart && c.gmres_maxit >= 1 && c.gmres_rtol > 0.0 &&
               (c.tau2_exact == 0 || c.tau2_exact == 1) && c.ilu_sweeps >= 0 && c.ilu_sweeps <= 16;
     ok = ok && (c.limiter == 0 || c.limiter == 1);
-    for (int q = 0; q < 7; ++q) ok = ok && c.reserved[q] == 0;
+    ok = ok && (c.basis_fp32 == 0 || (c.basis_fp32 == 1 && c.precision == GKS_MIXED));
+    ok = ok && (c.warm_extrap == 0 || c.warm_extrap == 1);
+    for (int q = 0; q < 5; ++q) ok = ok && c.reserved[q] == 0;
     if (!ok) {
         set_error("invalid gks_config");
         return GKS_EINVAL;
@@ -284,6 +286,7 @@ gks_status gks_reset_warm_start(gks_mesh *m)
     }
     DeviceGuard g(m->device);
     GKS_CUDA(cudaMemset(m->wk.x, 0, sizeof(double) * 20 * m->d.T));
+    m->wk.nsolve = 0;
     return GKS_OK;
 }
 
@@ -494,6 +497,7 @@ gks_status gks_profile_begin(gks_mesh *m, int32_t class_mask)
     m->prof.mask = class_mask;
     m->prof.used = 0;
     m->prof.cls.clear();
+    m->prof.arnoldi = m->prof.arnoldi_jsum = m->prof.precond = m->prof.residuals = 0;
     return GKS_OK;
 }
 
@@ -513,6 +517,10 @@ gks_status gks_profile_end(gks_mesh *m, gks_profile *out)
         out->ms[p.cls[q]] += ms;
         out->n[p.cls[q]] += 1;
     }
+    out->arnoldi = p.arnoldi;
+    out->arnoldi_jsum = p.arnoldi_jsum;
+    out->precond = p.precond;
+    out->residuals = p.residuals;
     p.mask = 0;
     p.used = 0;
     p.cls.clear();

@@ -97,11 +97,12 @@ __global__ void k_rhs(DeviceMesh d, const double *__restrict__ w, double *__rest
 
 // y = K x (mode 0) or y = b - K x with partial sums of |y|^2 and |b|^2 (mode 1).
 // K_ii = D_i (symmetric, 15 stored values), K_ij = -O_ij.  TX: type of x,
-// TM: type of the operator data and of the arithmetic (mode 1 is FP64 only).
-template <typename TX, typename TM>
+// TM: type of the operator data and of the arithmetic (mode 1 is FP64 only),
+// TY: type of y (the residual norms are those of the FP64 values).
+template <typename TX, typename TM, typename TY>
 __global__ void k_spmv(DeviceMesh d, const TM *__restrict__ Dg, const TM *__restrict__ alg,
                        const TM *__restrict__ exg, const TM *__restrict__ eyg, const TX *__restrict__ x,
-                       double *__restrict__ y, int mode, const double *__restrict__ b, double *__restrict__ part,
+                       TY *__restrict__ y, int mode, const double *__restrict__ b, double *__restrict__ part,
                        int pstride)
 {
     __shared__ double sh[32 * NV];
@@ -140,7 +141,7 @@ __global__ void k_spmv(DeviceMesh d, const TM *__restrict__ Dg, const TM *__rest
         }
         if (mode == 0) {
 #pragma unroll
-            for (int q = 0; q < NX; ++q) y[q * T + i] = double(acc[q]);
+            for (int q = 0; q < NX; ++q) y[q * T + i] = TY(acc[q]);
         } else {
 #pragma unroll
             for (int v = 0; v < NV; ++v)
@@ -148,7 +149,7 @@ __global__ void k_spmv(DeviceMesh d, const TM *__restrict__ Dg, const TM *__rest
                 for (int l = 0; l < ND; ++l) {
                     const double bv = b[(v * ND + l) * T + i];
                     const double rv = bv - double(acc[v * ND + l]);
-                    y[(v * ND + l) * T + i] = rv;
+                    y[(v * ND + l) * T + i] = TY(rv);
                     nr[v] += rv * rv;
                     nb[v] += bv * bv;
                 }
@@ -263,8 +264,10 @@ __global__ void k_ilu_bwd(DeviceMesh d, const TM *__restrict__ Pg, const TM *__r
 // four cells each (64 apart), all 40 loads issued before the sums (read-only
 // kernels need many bytes in flight); the warp sums then the two warps of a
 // variable give part[blk][v][k].  Fixed order: the sums are deterministic.
-__global__ void __launch_bounds__(kDotThreads, 3) k_dots(int64_t T, int64_t nblk, const double *__restrict__ V,
-                                                         const double *__restrict__ w, double *__restrict__ part,
+// TB: type of the stored basis; products and sums are FP64.
+template <typename TB>
+__global__ void __launch_bounds__(kDotThreads, 3) k_dots(int64_t T, int64_t nblk, const TB *__restrict__ V,
+                                                         const TB *__restrict__ w, double *__restrict__ part,
                                                          int pstride)
 {
     constexpr int kPerVar = kDotThreads / NV;          // 64 threads (two warps) per variable
@@ -273,8 +276,8 @@ __global__ void __launch_bounds__(kDotThreads, 3) k_dots(int64_t T, int64_t nblk
     const int k = blockIdx.x;
     const int v = threadIdx.x / kPerVar, t = threadIdx.x % kPerVar;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const double *vk = V + (int64_t)k * NX * T + (int64_t)v * ND * T;
-    const double *wv = w + (int64_t)v * ND * T;
+    const TB *vk = V + (int64_t)k * NX * T + (int64_t)v * ND * T;
+    const TB *wv = w + (int64_t)v * ND * T;
     for (int64_t b = blockIdx.y; b < nblk; b += gridDim.y) {
         const int64_t c0 = b * kBlock + t;
         double s = 0.0;
@@ -282,7 +285,7 @@ __global__ void __launch_bounds__(kDotThreads, 3) k_dots(int64_t T, int64_t nblk
         for (int q = 0; q < kCells; ++q) {
             const int64_t i = c0 + q * kPerVar;
 #pragma unroll
-            for (int l = 0; l < ND; ++l) s += i < T ? vk[l * T + i] * wv[l * T + i] : 0.0;
+            for (int l = 0; l < ND; ++l) s += i < T ? double(vk[l * T + i]) * double(wv[l * T + i]) : 0.0;
         }
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0) sh[warp] = s;
@@ -295,7 +298,8 @@ __global__ void __launch_bounds__(kDotThreads, 3) k_dots(int64_t T, int64_t nblk
 // w -= sum_{k<=j} c[s][k] V_k for running systems s = case * 4 + v (c: the
 // Gram-Schmidt coefficients of the unnormalised basis), w = 0 for the others;
 // optional partial |w|^2 per block.
-__global__ void k_orth_update(DeviceMesh d, const double *__restrict__ V, double *__restrict__ w, int j,
+template <typename TB>
+__global__ void k_orth_update(DeviceMesh d, const TB *__restrict__ V, TB *__restrict__ w, int j,
                               const double *__restrict__ hc, int hstride, const int32_t *__restrict__ ctl, int ns,
                               double *__restrict__ part, int pstride, int want_norm)
 {
@@ -311,22 +315,23 @@ __global__ void k_orth_update(DeviceMesh d, const double *__restrict__ V, double
             const int sy = 4 * c + v;
             if (!ctl[kCtlRunning * ns + sy]) {
 #pragma unroll
-                for (int l = 0; l < ND; ++l) w[(v * ND + l) * T + i] = 0.0;
+                for (int l = 0; l < ND; ++l) w[(v * ND + l) * T + i] = TB(0);
                 continue;
             }
             double wv[ND];
 #pragma unroll
-            for (int l = 0; l < ND; ++l) wv[l] = w[(v * ND + l) * T + i];
+            for (int l = 0; l < ND; ++l) wv[l] = double(w[(v * ND + l) * T + i]);
             for (int k = 0; k <= j; ++k) {
                 const double hk = hc[sy * hstride + k];
-                const double *vk = V + k * vs;
+                const TB *vk = V + k * vs;
 #pragma unroll
-                for (int l = 0; l < ND; ++l) wv[l] -= hk * vk[(v * ND + l) * T + i];
+                for (int l = 0; l < ND; ++l) wv[l] -= hk * double(vk[(v * ND + l) * T + i]);
             }
 #pragma unroll
             for (int l = 0; l < ND; ++l) {
-                w[(v * ND + l) * T + i] = wv[l];
-                nrm[v] += wv[l] * wv[l];
+                const TB st = TB(wv[l]);                // the norm is that of the stored vector
+                w[(v * ND + l) * T + i] = st;
+                nrm[v] += double(st) * double(st);
             }
         }
     }
@@ -435,6 +440,11 @@ __global__ void k_scale_y(int m, double *y, const double *__restrict__ vn, const
 }
 
 // x += sum_{k<jv} y_k Z_k with Z_k = M^{-1} V_k kept from the iterations
+// x += sum_k y[s][k] Z_k.  FP64 path: FP64 sums.  Mixed path (FP32 Z): the
+// correction of one inner cycle is formed in FP32 (it only has to be accurate to
+// the inner tolerance; the next FP64 residual measures what is left) and added
+// to x in FP64, so the FP64 pipe sees one add per value instead of one
+// conversion and one FMA per value and Krylov vector.
 template <typename TZ>
 __global__ void k_combine_z(DeviceMesh d, const TZ *__restrict__ Z, const double *__restrict__ y, int m,
                             const int32_t *__restrict__ ctl, int ns, double *__restrict__ x)
@@ -447,14 +457,30 @@ __global__ void k_combine_z(DeviceMesh d, const TZ *__restrict__ Z, const double
     const int jv = ctl[kCtlJv * ns + sy];
     if (jv <= 0) return;
     const int64_t vs = (int64_t)NX * T;
-    double acc[ND] = {0, 0, 0, 0, 0};
+    TZ acc[ND] = {0, 0, 0, 0, 0};
     for (int k = 0; k < jv; ++k) {
-        const double yk = y[sy * m + k];
+        const TZ yk = TZ(y[sy * m + k]);
 #pragma unroll
-        for (int l = 0; l < ND; ++l) acc[l] += yk * double(Z[k * vs + (v * ND + l) * T + i]);
+        for (int l = 0; l < ND; ++l) acc[l] += yk * Z[k * vs + (v * ND + l) * T + i];
     }
 #pragma unroll
-    for (int l = 0; l < ND; ++l) x[(v * ND + l) * T + i] += acc[l];
+    for (int l = 0; l < ND; ++l) x[(v * ND + l) * T + i] += double(acc[l]);
+}
+
+// Warm start of the next solve (cases not done): extrapolate = 1 sets
+// x = 2 x - x_prev; in both cases x_prev takes the old x.
+__global__ void k_warm(DeviceMesh d, double *__restrict__ x, double *__restrict__ xp, const int32_t *__restrict__ done,
+                       int extrapolate)
+{
+    const int64_t T = d.T;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= T || done[d.blk_case[blockIdx.x]]) return;
+#pragma unroll 4
+    for (int q = 0; q < NX; ++q) {
+        const double a = x[q * T + i];
+        if (extrapolate) x[q * T + i] = 2.0 * a - xp[q * T + i];
+        xp[q * T + i] = a;
+    }
 }
 
 // Start (first = 1) or restart of every system: sums[s][0] = |r|^2,
@@ -531,8 +557,8 @@ inline unsigned nblocks(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock
 
 // dst = M^{-1} src (block ILU(0) on the RCM order).  TZ, TM: storage and
 // arithmetic precision of the application; tA, tB: work buffers of type TZ.
-template <typename TZ, typename TM>
-gks_status precond_t(gks_mesh *m, const TM *Pg, const TM *alg, const TM *exg, const TM *eyg, const double *src,
+template <typename TR, typename TZ, typename TM>
+gks_status precond_t(gks_mesh *m, const TM *Pg, const TM *alg, const TM *exg, const TM *eyg, const TR *src,
                      TZ *dst, TZ *tA, TZ *tB, cudaStream_t s)
 {
     DeviceMesh &d = m->d;
@@ -541,7 +567,7 @@ gks_status precond_t(gks_mesh *m, const TM *Pg, const TM *alg, const TM *exg, co
         const auto &lp = m->lvl_lo_ptr;
         for (size_t l = 0; l + 1 < lp.size(); ++l) {
             const int64_t n = lp[l + 1] - lp[l];
-            k_ilu_fwd<double, TZ, TM><<<nblocks(n), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, d.lvl_lo + lp[l], n, src,
+            k_ilu_fwd<TR, TZ, TM><<<nblocks(n), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, d.lvl_lo + lp[l], n, src,
                                                                      dst, dst, 1);
             note_launch();
         }
@@ -556,10 +582,10 @@ gks_status precond_t(gks_mesh *m, const TM *Pg, const TM *alg, const TM *exg, co
         const int ns = m->cfg.ilu_sweeps;
         TZ *za = (ns % 2 == 0) ? tA : dst;   // buffers chosen so that z ends in tA
         TZ *zb = (ns % 2 == 0) ? dst : tA;
-        k_ilu_fwd<double, TZ, TM><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, src, nullptr, za, 0);
+        k_ilu_fwd<TR, TZ, TM><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, src, nullptr, za, 0);
         note_launch();
         for (int q = 0; q < ns; ++q) {
-            k_ilu_fwd<double, TZ, TM><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, src, za, zb, 1);
+            k_ilu_fwd<TR, TZ, TM><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, src, za, zb, 1);
             note_launch();
             std::swap(za, zb);
         }
@@ -580,16 +606,18 @@ gks_status precond_t(gks_mesh *m, const TM *Pg, const TM *alg, const TM *exg, co
     return GKS_OK;
 }
 
-gks_status precond(gks_mesh *m, const double *src, double *dst, cudaStream_t s)
+template <typename TR>
+gks_status precond(gks_mesh *m, const TR *src, double *dst, cudaStream_t s)
 {
     DeviceMesh &d = m->d;
-    return precond_t<double, double>(m, d.P, d.alpha, d.ex, d.ey, src, dst, m->wk.t2, m->wk.t3, s);
+    return precond_t<TR, double, double>(m, d.P, d.alpha, d.ex, d.ey, src, dst, m->wk.t2, m->wk.t3, s);
 }
 
-gks_status precond32(gks_mesh *m, const double *src, float *dst, cudaStream_t s)
+template <typename TR>
+gks_status precond32(gks_mesh *m, const TR *src, float *dst, cudaStream_t s)
 {
     DeviceMesh &d = m->d;
-    return precond_t<float, float>(m, d.P32, d.alpha32, d.ex32, d.ey32, src, dst, m->wk.t2_32, m->wk.t3_32, s);
+    return precond_t<TR, float, float>(m, d.P32, d.alpha32, d.ex32, d.ey32, src, dst, m->wk.t2_32, m->wk.t3_32, s);
 }
 
 gks_status read_flags(gks_mesh *m, cudaStream_t s)
@@ -602,11 +630,12 @@ gks_status read_flags(gks_mesh *m, cudaStream_t s)
 }
 
 // part[blk][v][k] = partial <V_k, w>, k <= j, per cell block
-gks_status dots(gks_mesh *m, const double *w, int j, double *part, int ps, cudaStream_t s)
+template <typename TB>
+gks_status dots(gks_mesh *m, const TB *V, const TB *w, int j, double *part, int ps, cudaStream_t s)
 {
     const int64_t nblk = m->wk.nblk;
     const dim3 g((unsigned)(j + 1), (unsigned)std::min<int64_t>(nblk, kDotMaxTiles));
-    k_dots<<<g, kDotThreads, 0, s>>>(m->d.T, nblk, m->wk.V, w, part, ps);
+    k_dots<TB><<<g, kDotThreads, 0, s>>>(m->d.T, nblk, V, w, part, ps);
     note_launch();
     GKS_CUDA(cudaGetLastError());
     return GKS_OK;
@@ -620,7 +649,10 @@ inline unsigned sblocks(int n) { return (unsigned)((n + 127) / 128); }
 // m->wk.w; the solutions (and warm starts) are m->wk.x.  GMRES cycles of all
 // systems run in lockstep: every launch covers all cases, and per-system masks
 // stop the systems that have converged.
-gks_status cls_solve(gks_mesh *m, cudaStream_t s, int32_t *iters, double *relres, int32_t *converged)
+// The whole solve with the Krylov basis stored as TB (double, or float in the
+// mixed mode with basis_fp32).
+template <typename TB>
+gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, double *relres, int32_t *converged)
 {
     DeviceMesh &d = m->d;
     Work &k = m->wk;
@@ -638,8 +670,9 @@ gks_status cls_solve(gks_mesh *m, cudaStream_t s, int32_t *iters, double *relres
 
     k_rhs<<<nb, kBlock, 0, s>>>(d, k.w, k.b); note_launch();
     // residual r = b - K x, written straight into the basis slot V_0 (v_0 = V_0 / beta)
-    k_spmv<double, double><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, k.V, 1, k.b, k.part, ps);
+    k_spmv<double, double, TB><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, V, 1, k.b, k.part, ps);
     note_launch();
+    m->prof.residuals += 1;
     k_reduce<<<dim3(2, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.hcol, ps, 0); note_launch();
     k_start<<<sblocks(ns), 128, 0, s>>>(k.hcol, ps, k.bnorm, k.beta, k.vn, mm, k.ctl, ns, k.done, rtol, maxit, 1);
     note_launch();
@@ -650,34 +683,37 @@ gks_status cls_solve(gks_mesh *m, cudaStream_t s, int32_t *iters, double *relres
     while (k.h_flags[0]) {
         k_init_g<<<sblocks(ns * (mm + 1)), 128, 0, s>>>(k.g, mm, k.beta, k.ctl, ns); note_launch();
         for (int j = 0; j < mm; ++j) {
-            double *vj = k.V + j * vs, *vj1 = k.V + (j + 1) * vs;
+            TB *vj = V + j * vs, *vj1 = V + (j + 1) * vs;
             int slot = prof_start(m, kProfIlu, s);
             // Z_j = M^{-1} V_j, kept for the update of x at the end of the cycle
             if ((st = mixed ? precond32(m, vj, k.Z32 + j * vs, s) : precond(m, vj, k.Z + j * vs, s)) != GKS_OK)
                 return st;
             prof_stop(m, slot, s);
+            m->prof.precond += 1;
+            m->prof.arnoldi += 1;
+            m->prof.arnoldi_jsum += j + 1;
             slot = prof_start(m, kProfSpmv, s);
             if (mixed)
-                k_spmv<float, float><<<nb, kBlock, 0, s>>>(d, d.D32, d.alpha32, d.ex32, d.ey32, k.Z32 + j * vs, vj1, 0,
-                                                           nullptr, nullptr, 0);
+                k_spmv<float, float, TB><<<nb, kBlock, 0, s>>>(d, d.D32, d.alpha32, d.ex32, d.ey32, k.Z32 + j * vs,
+                                                               vj1, 0, nullptr, nullptr, 0);
             else
-                k_spmv<double, double><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.Z + j * vs, vj1, 0, nullptr,
-                                                             nullptr, 0);
+                k_spmv<double, double, TB><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.Z + j * vs, vj1, 0,
+                                                                 nullptr, nullptr, 0);
             note_launch();
             prof_stop(m, slot, s);
             slot = prof_start(m, kProfOrth, s);
             // classical Gram-Schmidt: twice in FP64 mode; once in the mixed mode, whose
             // cycles only reduce the residual by kInnerRtol before an FP64 restart
-            if ((st = dots(m, vj1, j, k.part, ps, s)) != GKS_OK) return st;
+            if ((st = dots<TB>(m, V, vj1, j, k.part, ps, s)) != GKS_OK) return st;
             k_reduce<<<dim3(j + 1, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.hcol, ps, 0, k.vn, mm + 1, k.hco, ps);
             note_launch();
-            k_orth_update<<<nb, kBlock, 0, s>>>(d, k.V, vj1, j, k.hco, ps, k.ctl, ns, k.part, ps, mixed ? 1 : 0);
+            k_orth_update<TB><<<nb, kBlock, 0, s>>>(d, V, vj1, j, k.hco, ps, k.ctl, ns, k.part, ps, mixed ? 1 : 0);
             note_launch();
             if (!mixed) {
-                if ((st = dots(m, vj1, j, k.part, ps, s)) != GKS_OK) return st;
+                if ((st = dots<TB>(m, V, vj1, j, k.part, ps, s)) != GKS_OK) return st;
                 k_reduce<<<dim3(j + 1, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.y, mm, 0, k.vn, mm + 1, k.hco, ps);
                 note_launch();
-                k_orth_update<<<nb, kBlock, 0, s>>>(d, k.V, vj1, j, k.hco, ps, k.ctl, ns, k.part, ps, 1); note_launch();
+                k_orth_update<TB><<<nb, kBlock, 0, s>>>(d, V, vj1, j, k.hco, ps, k.ctl, ns, k.part, ps, 1); note_launch();
                 k_hadd<<<sblocks(ns * (j + 1)), 128, 0, s>>>(k.hcol, ps, k.y, mm, j, ns); note_launch();
             }
             k_reduce<<<dim3(1, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.hcol + j + 1, ps, 2); note_launch();
@@ -696,8 +732,9 @@ gks_status cls_solve(gks_mesh *m, cudaStream_t s, int32_t *iters, double *relres
         else
             k_combine_z<double><<<dim3(nb, NV), kBlock, 0, s>>>(d, k.Z, k.y, mm, k.ctl, ns, k.x);
         note_launch();
-        k_spmv<double, double><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, k.V, 1, k.b, k.part, ps);
+        k_spmv<double, double, TB><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, V, 1, k.b, k.part, ps);
         note_launch();
+        m->prof.residuals += 1;
         k_reduce<<<dim3(2, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.hcol, ps, 0); note_launch();
         k_start<<<sblocks(ns), 128, 0, s>>>(k.hcol, ps, k.bnorm, k.beta, k.vn, mm, k.ctl, ns, k.done, rtol, maxit, 0);
         note_launch();
@@ -722,6 +759,21 @@ gks_status cls_solve(gks_mesh *m, cudaStream_t s, int32_t *iters, double *relres
         if (converged) *converged = conv;
     }
     return GKS_OK;
+}
+
+gks_status cls_solve(gks_mesh *m, cudaStream_t s, int32_t *iters, double *relres, int32_t *converged)
+{
+    Work &k = m->wk;
+    if (m->cfg.warm_extrap) {
+        // initial guess 2 x_{n-1} - x_{n-2} once two solutions exist, else keep x_{n-1}
+        const unsigned nb = (unsigned)k.nblk;
+        k_warm<<<nb, kBlock, 0, s>>>(m->d, k.x, k.x_prev, k.done, k.nsolve >= 2 ? 1 : 0); note_launch();
+        GKS_CUDA(cudaGetLastError());
+    }
+    gks_status st = k.V32 ? cls_solve_t<float>(m, k.V32, s, iters, relres, converged)
+                          : cls_solve_t<double>(m, k.V, s, iters, relres, converged);
+    if (st == GKS_OK) ++k.nsolve;
+    return st;
 }
 
 }  // namespace gks

@@ -86,11 +86,14 @@ struct Work {
     double *w = nullptr;             // [4][T] state (internal order)
     double *w_old = nullptr;         // [4][T]
     double *x = nullptr;             // [20][T] CLS coefficients (warm start)
+    double *x_prev = nullptr;        // [20][T] the solution before (extrapolated warm start)
+    int64_t nsolve = 0;              // solves since creation or the last warm-start reset
     double *xl = nullptr;            // [20][T] limited coefficients (limiter on)
     int32_t *lflag = nullptr;        // [T] 0 untouched, 1 limited, 2 reset to the average
     double *b = nullptr, *r = nullptr, *t2 = nullptr, *t3 = nullptr;  // [20][T]
     float *t2_32 = nullptr, *t3_32 = nullptr;  // [20][T] FP32 preconditioner work
     double *V = nullptr;             // [(m+1)][20][T] Krylov basis, unnormalised: v_k = V_k / vn_k
+    float *V32 = nullptr;            // the same stored in FP32 (mixed mode with basis_fp32; V unused)
     double *Z = nullptr;             // [m][20][T] M^{-1} V_k (FP64 path)
     float *Z32 = nullptr;            // [m][20][T] M^{-1} V_k (mixed path)
     double *flux = nullptr;          // [4][F]
@@ -125,6 +128,7 @@ struct gks_profiler {
     std::vector<cudaEvent_t> events;                // pool
     size_t used = 0;
     std::vector<int> cls;                           // class of each start/stop pair
+    int64_t arnoldi = 0, arnoldi_jsum = 0, precond = 0, residuals = 0;  // work counters
 };
 
 struct gks_mesh {

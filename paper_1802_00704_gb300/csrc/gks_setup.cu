@@ -685,7 +685,12 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
 #define AL(ptr, n) \
     if ((st = dalloc(m, &k.ptr, (size_t)(n))) != GKS_OK) return st
     AL(w, 4 * T); AL(w_old, 4 * T); AL(x, 20 * T); AL(b, 20 * T); AL(r, 20 * T); AL(t2, 20 * T); AL(t3, 20 * T);
-    AL(V, (size_t)(mm + 1) * 20 * T); AL(flux, 4 * F);
+    if (cfg.basis_fp32) {
+        AL(V32, (size_t)(mm + 1) * 20 * T);
+    } else {
+        AL(V, (size_t)(mm + 1) * 20 * T);
+    }
+    AL(flux, 4 * F);
     if (cfg.precision == GKS_MIXED) {
         AL(t2_32, 20 * T); AL(t3_32, 20 * T); AL(Z32, (size_t)mm * 20 * T);
     } else {
@@ -695,6 +700,7 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
     if (cfg.limiter) {
         AL(xl, 20 * T); AL(lflag, T);
     }
+    if (cfg.warm_extrap) AL(x_prev, 20 * T);
     AL(H, ns * (mm + 1) * mm); AL(cs, ns * mm); AL(sn, ns * mm); AL(g, ns * (mm + 1)); AL(y, ns * mm);
     AL(hcol, ns * (mm + 2)); AL(hco, ns * (mm + 2)); AL(vn, ns * (mm + 1)); AL(bnorm, ns); AL(beta, ns); AL(ctl, kCtlFields * ns); AL(flags, 4);
     AL(dt, n_cases); AL(tcase, n_cases); AL(tfinal, n_cases); AL(done, n_cases); AL(scal, 8); AL(status, n_cases);

@@ -40,7 +40,8 @@ class Config(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("mu", C.c_double), ("cls_w", C.c_double),
                 ("gmres_m", C.c_int32), ("gmres_maxit", C.c_int32), ("gmres_rtol", C.c_double),
                 ("precision", C.c_int32), ("precond", C.c_int32), ("ilu_sweeps", C.c_int32),
-                ("tau2_exact", C.c_int32), ("limiter", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("tau2_exact", C.c_int32), ("limiter", C.c_int32),
+                ("basis_fp32", C.c_int32), ("warm_extrap", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class SolveInfo(C.Structure):
@@ -57,7 +58,8 @@ class RunInfo(C.Structure):
 
 
 class Profile(C.Structure):
-    _fields_ = [("n", C.c_int64 * 5), ("ms", C.c_double * 5)]
+    _fields_ = [("n", C.c_int64 * 5), ("ms", C.c_double * 5), ("arnoldi", C.c_int64), ("arnoldi_jsum", C.c_int64),
+                ("precond", C.c_int64), ("residuals", C.c_int64)]
 
 
 class MeshStats(C.Structure):
@@ -310,7 +312,8 @@ class GksMesh:
     def profile_end(self) -> dict:
         p = Profile()
         _check(self._lib.gks_profile_end(self._h, C.byref(p)), "gks_profile_end")
-        return {"n": list(p.n), "ms": list(p.ms)}
+        return {"n": list(p.n), "ms": list(p.ms), "arnoldi": p.arnoldi, "arnoldi_jsum": p.arnoldi_jsum,
+                "precond": p.precond, "residuals": p.residuals}
 
     def run(self, w, t_final: float = 0.0, max_steps: int = 1, steady_tol: float = 0.0, stream=None,
             check=True) -> dict:

@@ -49,13 +49,14 @@ def test_mixed_point_flux_close_to_oracle(O, G):
     assert np.all(err <= 1e-7), err
 
 
+@pytest.mark.parametrize("basis_fp32", [0, 1])
 @pytest.mark.parametrize("name", ["advection20", "shock_vortex40x20", "walled13x9"])
-def test_mixed_cls_reaches_fp64_tolerance(O, G, name):
+def test_mixed_cls_reaches_fp64_tolerance(O, G, name, basis_fp32):
     from tests.test_gpu_parity import CASES
     c = CASES[name]()
     om = O.OracleMesh(c.mesh)
     ref, _, _, _ = om.cls_solve(c.w0)
-    m = G.GksMesh(c.mesh, precision=G.MIXED)
+    m = G.GksMesh(c.mesh, precision=G.MIXED, basis_fp32=basis_fp32)
     coef, info = m.cls_reconstruct(dev(c.w0))
     assert info["converged"] == 1 and max(info["relres"]) <= 1e-12
     got = host(coef)
@@ -64,14 +65,15 @@ def test_mixed_cls_reaches_fp64_tolerance(O, G, name):
             assert rel_max(got[v], ref[v]) <= 1e-9
 
 
+@pytest.mark.parametrize("basis_fp32", [0, 1])
 @pytest.mark.parametrize("name,steps", [("advection20", 20), ("shock_vortex40x20", 20)])
-def test_mixed_steps_within_1e8_l1(O, G, name, steps):
+def test_mixed_steps_within_1e8_l1(O, G, name, steps, basis_fp32):
     from tests.test_gpu_parity import CASES
     c = CASES[name]()
     om = O.OracleMesh(c.mesh)
     area = om.cell_geometry()["area"]
     wo = c.w0.copy()
-    m = G.GksMesh(c.mesh, precision=G.MIXED)
+    m = G.GksMesh(c.mesh, precision=G.MIXED, basis_fp32=basis_fp32)
     w = dev(c.w0)
     for _ in range(steps):
         dt = om.cfl_dt(wo)
@@ -94,3 +96,24 @@ def test_mixed_exact_ilu_and_sweeps_agree(G):
             m.step(w)
         out.append(host(w))
     assert rel_max(out[0], out[1]) <= 1e-11
+
+
+def test_fp32_basis_needs_mixed_precision(G):
+    c = I.advection_case(6)
+    with pytest.raises(G.GksError):
+        G.GksMesh(c.mesh, precision=G.FP64, basis_fp32=1)
+
+
+def test_fp32_basis_batch_matches_single_runs(G):
+    cases = [I.advection_case(9, k=2), I.shock_vortex_case(24, 12), I.sod_case(60, 4)]
+    b = G.GksMesh.batch([c.mesh for c in cases], precision=G.MIXED, basis_fp32=1, limiter=1)
+    w = dev(np.ascontiguousarray(np.concatenate([c.w0 for c in cases], axis=1)))
+    r = b.batch_run(w, max_steps=4)
+    assert r["n_failed"] == 0
+    wh, o = host(w), 0
+    for c in cases:
+        m = G.GksMesh(c.mesh, precision=G.MIXED, basis_fp32=1, limiter=1)
+        ws = dev(c.w0)
+        m.run(ws, max_steps=4)
+        assert rel_max(wh[:, o:o + c.mesh.n_tri], host(ws)) <= 1e-13, c.name
+        o += c.mesh.n_tri

@@ -1,0 +1,63 @@
+"""Solver options that change how the CLS system is solved but not what it
+solves: the extrapolated warm start (initial guess 2 x_{n-1} - x_{n-2}) must
+reach the same tolerance, so the states stay within the FP64 parity bounds of
+the oracle, with no more GMRES iterations than the plain warm start."""
+import numpy as np
+import pytest
+
+from paper_1802_00704_gb300 import inputs as I
+from tests.gpu_util import dev, host, needs_gpu, rel_max
+
+pytestmark = [pytest.mark.gpu, needs_gpu]
+
+
+@pytest.fixture(scope="module")
+def O():
+    from oracle import oracle
+    oracle.build()
+    return oracle
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_1802_00704_gb300 import build, gks
+    build.build()
+    return gks
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_extrapolated_warm_start_matches_oracle(O, G, precision):
+    c = I.shock_vortex_case(40, 20)
+    om = O.OracleMesh(c.mesh)
+    prec = G.MIXED if precision == "mixed" else G.FP64
+    plain = G.GksMesh(c.mesh, precision=prec)
+    extrap = G.GksMesh(c.mesh, precision=prec, warm_extrap=1)
+    wo, wp, we = c.w0.copy(), dev(c.w0), dev(c.w0)
+    its_p = its_e = 0
+    for n in range(30):
+        info = om.step(wo)
+        assert info.status == 0
+        its_p += max(plain.step(wp, info.dt)["iters"])
+        r = extrap.step(we, info.dt)
+        its_e += max(r["iters"])
+        assert max(r["relres"]) <= 1e-12
+    assert np.all(rel_max(host(we), wo, axis=1) <= 1e-8)
+    assert rel_max(host(we), host(wp)) <= 1e-10
+    assert its_e <= its_p, (its_e, its_p)
+
+
+def test_warm_start_reset_forgets_both_solutions(G):
+    c = I.advection_case(12)
+    m = G.GksMesh(c.mesh, warm_extrap=1)
+    w = dev(c.w0)
+    for _ in range(3):
+        m.step(w)
+    m.reset_warm_start()
+    # after the reset the handle repeats what a fresh one does, bit for bit
+    fresh = G.GksMesh(c.mesh, warm_extrap=1)
+    wa, wb = dev(c.w0), dev(c.w0)
+    for _ in range(4):
+        ia = m.step(wa, 1e-3)
+        ib = fresh.step(wb, 1e-3)
+        assert ia["iters"] == ib["iters"]
+    assert np.array_equal(host(wa), host(wb))
