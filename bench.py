@@ -237,6 +237,7 @@ def timed_leg(args, case, precision: str, world: int, dev, sample_clocks: bool):
                     limiter=int(args.limiter), warm_extrap=int(args.warm == "extrap"))
     w = torch.from_numpy(case.w0.copy()).to(dev)
     stream = torch.cuda.current_stream()
+    tune = m.autotune(w, trial_steps=2) if args.tune else None
     for _ in range(args.warmup):
         m.run(w, max_steps=1)
     torch.cuda.synchronize()
@@ -264,7 +265,9 @@ def timed_leg(args, case, precision: str, world: int, dev, sample_clocks: bool):
     clocks = sampler.stop() if sampler else None
     ms = allmax(world, ev0.elapsed_time(ev1))
     return {"mesh": m, "w": w, "info": info, "prof": prof, "launches": launches, "clocks": clocks, "ms": ms,
-            "stats": m.stats()}
+            "stats": m.stats(), "tune": tune,
+            "knobs": {"ilu_sweeps": m.cfg.ilu_sweeps, "warm_extrap": m.cfg.warm_extrap,
+                      "inner_rtol": m.cfg.inner_rtol}}
 
 
 def run_gks(args, world, rank, local):
@@ -310,7 +313,7 @@ def run_gks(args, world, rank, local):
         ms_c = prof["ms"][q]
         ent = {"ms": round(ms_c, 3), "launch_groups": prof["n"][q]}
         if nm != "flux" and ms_c > 0:
-            by = class_bytes(nm, prof, T, F, args.steps, args.sweeps, exact, mixed, basis32)
+            by = class_bytes(nm, prof, T, F, args.steps, main["knobs"]["ilu_sweeps"], exact, mixed, basis32)
             gbs = by / (ms_c / 1e3) / 1e9
             ent.update({"bytes": by, "gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 3)})
         classes[nm] = ent
@@ -344,8 +347,8 @@ def run_gks(args, world, rank, local):
                                f"{F} faces, GMRES(30) rtol 1e-12",
                    "n_tri": T, "n_face": F, "precision": args.precision,
                    "krylov_basis": "fp32" if basis32 else "fp64", "limiter": bool(args.limiter),
-                   "warm_start": args.warm,
-                   "precond": ("ilu0_rcm_exact" if exact else f"ilu0_rcm_sweep{args.sweeps}"),
+                   "warm_start": args.warm, "autotuned": bool(args.tune), "knobs": main["knobs"],
+                   "precond": ("ilu0_rcm_exact" if exact else f"ilu0_rcm_sweep{main['knobs']['ilu_sweeps']}"),
                    "l2": f"inputs larger than L2: {st['device_bytes'] / 2**30:.1f} GiB resident per replica",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "gmres_iters_per_step": info["gmres_iters"] / max(info["steps"], 1),
@@ -367,7 +370,7 @@ def run_gks(args, world, rank, local):
         out["fp64"] = {"value": world * T * args.steps / (ref["ms"] / 1e3), "ms_per_step": ref["ms"] / args.steps,
                        "gmres_iters_per_step": ref["info"]["gmres_iters"] / max(ref["info"]["steps"], 1),
                        "class_ms": {nm: round(ref["prof"]["ms"][q], 3) for q, nm in enumerate(names)},
-                       "arnoldi_per_step": ref["prof"]["arnoldi"] / args.steps}
+                       "arnoldi_per_step": ref["prof"]["arnoldi"] / args.steps, "knobs": ref["knobs"]}
         out["mixed_vs_fp64_rel_l1"] = [float(x) for x in l1]
         out["speedup_vs_fp64"] = value / out["fp64"]["value"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -407,6 +410,8 @@ def main():
     ap.add_argument("--basis", default="fp64", choices=["fp32", "fp64"],
                     help="storage of the Krylov basis in the mixed path (arithmetic stays FP64)")
     ap.add_argument("--limiter", action="store_true", help="shock detector + DWBAP limiter on")
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="skip the autotuner (ilu_sweeps, warm start, inner tolerance) before the warm-up")
     ap.add_argument("--warm", default="extrap", choices=["prev", "extrap"],
                     help="CLS initial guess: previous solution, or linear extrapolation of the last two")
     ap.add_argument("--cpu-steps", type=int, default=3)

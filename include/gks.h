@@ -117,7 +117,10 @@ typedef struct gks_config {
     int32_t warm_extrap;   /* 1: start each solve from 2 x_{n-1} - x_{n-2} (linear
                               extrapolation of the last two solutions) instead of
                               x_{n-1}; the same tolerance is met, in fewer iterations */
-    int32_t reserved[5];   /* must be zero                                             */
+    int32_t reserved[3];   /* must be zero                                             */
+    double inner_rtol;     /* mixed precision: an inner FP32 GMRES cycle stops once its
+                              residual estimate has dropped by this factor (0 < r < 1,
+                              default 1e-6); the next FP64 residual then restarts it   */
 } gks_config;
 
 typedef struct gks_mesh gks_mesh;
@@ -305,6 +308,29 @@ GKS_EXPORT gks_status gks_run(gks_mesh *mesh, double *w, double t_final, int64_t
  * synchronisation. */
 GKS_EXPORT gks_status gks_point_flux(int64_t n, const double *wl, const double *wr, double dt, const gks_config *cfg,
                           double *out, void *stream);
+
+/* Autotuner.  Times trial steps of the handle's own workload (all its cases)
+ * for each candidate of the knobs that change the cost of a step but not its
+ * result beyond the solver tolerance: ilu_sweeps in {1, 2, 3} (sweep
+ * preconditioner only), warm_extrap in {0, 1} and, in mixed precision,
+ * inner_rtol in {1e-4, 1e-5, 1e-6}.  Each candidate starts from w (device,
+ * [4][n_tri], caller order, not modified) with a cleared warm start, takes
+ * 3 untimed steps, then trial_steps (>= 1) steps timed with CUDA events; a
+ * candidate whose steps fail is skipped.  The fastest candidate is written to
+ * the handle's configuration and to *out (host), and the warm start is cleared.
+ * Synchronises the stream. */
+typedef struct gks_tune_result {
+    int32_t ilu_sweeps;
+    int32_t warm_extrap;
+    double inner_rtol;
+    double ms_per_step;           /* chosen candidate                               */
+    double ms_per_step_before;    /* the configuration the handle had before        */
+    int32_t n_candidates;         /* candidates timed                               */
+    int32_t n_failed;             /* candidates skipped because a step failed       */
+} gks_tune_result;
+
+GKS_EXPORT gks_status gks_autotune(gks_mesh *mesh, const double *w, int32_t trial_steps, gks_tune_result *out,
+                                   void *stream);
 
 /* Optional CUDA-event timing of kernel classes, for benchmarks.  Bit c of
  * class_mask enables class c: 0 face flux, 1 CLS operator application in

@@ -58,7 +58,8 @@ gks_status check_config(const gks_config &c)
     ok = ok && (c.limiter == 0 || c.limiter == 1);
     ok = ok && (c.basis_fp32 == 0 || (c.basis_fp32 == 1 && c.precision == GKS_MIXED));
     ok = ok && (c.warm_extrap == 0 || c.warm_extrap == 1);
-    for (int q = 0; q < 5; ++q) ok = ok && c.reserved[q] == 0;
+    ok = ok && c.inner_rtol > 0.0 && c.inner_rtol < 1.0;
+    for (int q = 0; q < 3; ++q) ok = ok && c.reserved[q] == 0;
     if (!ok) {
         set_error("invalid gks_config");
         return GKS_EINVAL;
@@ -177,6 +178,7 @@ void gks_config_default(gks_config *c)
     c->precond = GKS_PC_ILU_SWEEP;
     c->ilu_sweeps = 2;
     c->tau2_exact = 0;
+    c->inner_rtol = 1e-6;
 }
 
 const char *gks_last_error(void) { return gks::last_error(); }

@@ -21,10 +21,6 @@ namespace gks {
 namespace {
 
 constexpr int NV = 4, ND = 5, NX = 20;
-// Mixed precision: an inner GMRES cycle (FP32 operator and ILU) stops once its
-// residual estimate has dropped by this factor; the FP64 residual of the next
-// refinement sweep then measures the true error.
-constexpr double kInnerRtol = 1e-6;
 constexpr int kDotThreads = 256;       // threads per block of the dot-product kernel
 constexpr int kDotMaxTiles = 65535;    // grid.y limit of the dot-product kernel
 
@@ -665,7 +661,10 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
     const int maxit = m->cfg.gmres_maxit;
     const int64_t vs = (int64_t)NX * T;
     const bool mixed = m->cfg.precision == GKS_MIXED;
-    const double eta = mixed ? kInnerRtol : 0.0;
+    // mixed precision: an inner GMRES cycle (FP32 operator and ILU) stops once its
+    // residual estimate has dropped by inner_rtol; the FP64 residual of the next
+    // refinement sweep then measures the true error
+    const double eta = mixed ? m->cfg.inner_rtol : 0.0;
     gks_status st;
 
     k_rhs<<<nb, kBlock, 0, s>>>(d, k.w, k.b); note_launch();
@@ -703,7 +702,7 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
             prof_stop(m, slot, s);
             slot = prof_start(m, kProfOrth, s);
             // classical Gram-Schmidt: twice in FP64 mode; once in the mixed mode, whose
-            // cycles only reduce the residual by kInnerRtol before an FP64 restart
+            // cycles only reduce the residual by inner_rtol before an FP64 restart
             if ((st = dots<TB>(m, V, vj1, j, k.part, ps, s)) != GKS_OK) return st;
             k_reduce<<<dim3(j + 1, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.hcol, ps, 0, k.vn, mm + 1, k.hco, ps);
             note_launch();

@@ -26,7 +26,7 @@ FP64, MIXED = 0, 1
 EXPORTED = ["gks_config_default", "gks_mesh_create", "gks_mesh_destroy", "gks_mesh_get_stats", "gks_cfl_dt",
             "gks_cls_reconstruct", "gks_reset_warm_start", "gks_flux", "gks_step", "gks_run", "gks_point_flux",
             "gks_profile_begin", "gks_profile_end", "gks_launch_count", "gks_cfl_dt_noalloc", "gks_batch_create",
-            "gks_batch_run", "gks_limit", "gks_last_error"]
+            "gks_batch_run", "gks_limit", "gks_autotune", "gks_last_error"]
 PROF_FLUX, PROF_SPMV, PROF_ILU, PROF_ORTH, PROF_UPDATE = range(5)
 
 
@@ -41,7 +41,8 @@ class Config(C.Structure):
                 ("gmres_m", C.c_int32), ("gmres_maxit", C.c_int32), ("gmres_rtol", C.c_double),
                 ("precision", C.c_int32), ("precond", C.c_int32), ("ilu_sweeps", C.c_int32),
                 ("tau2_exact", C.c_int32), ("limiter", C.c_int32),
-                ("basis_fp32", C.c_int32), ("warm_extrap", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("basis_fp32", C.c_int32), ("warm_extrap", C.c_int32), ("reserved", C.c_int32 * 3),
+                ("inner_rtol", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -55,6 +56,12 @@ class StepInfo(C.Structure):
 class RunInfo(C.Structure):
     _fields_ = [("steps", C.c_int64), ("t", C.c_double), ("last_dt", C.c_double), ("gmres_iters", C.c_int64),
                 ("steady_res", C.c_double), ("status", C.c_int32)]
+
+
+class TuneResult(C.Structure):
+    _fields_ = [("ilu_sweeps", C.c_int32), ("warm_extrap", C.c_int32), ("inner_rtol", C.c_double),
+                ("ms_per_step", C.c_double), ("ms_per_step_before", C.c_double), ("n_candidates", C.c_int32),
+                ("n_failed", C.c_int32)]
 
 
 class Profile(C.Structure):
@@ -113,6 +120,8 @@ def load():
     lib.gks_reset_warm_start.restype = st
     lib.gks_flux.argtypes = [P, P, P, D, P, P]
     lib.gks_flux.restype = st
+    lib.gks_autotune.argtypes = [P, P, I32, C.POINTER(TuneResult), P]
+    lib.gks_autotune.restype = st
     lib.gks_limit.argtypes = [P, P, P, P, P, P]
     lib.gks_limit.restype = st
     lib.gks_step.argtypes = [P, P, C.POINTER(D), C.POINTER(StepInfo), P]
@@ -275,6 +284,15 @@ class GksMesh:
         if check:
             _check(st, "gks_flux")
         return out, st
+
+    def autotune(self, w, trial_steps: int = 3, stream=None) -> dict:
+        """Pick ilu_sweeps, warm_extrap and (mixed) inner_rtol by timing trial steps
+        from the state w (not modified); the handle keeps the fastest."""
+        r = TuneResult()
+        _check(self._lib.gks_autotune(self._h, _dev(w, (4, self.T)), int(trial_steps), C.byref(r), _stream(stream)),
+               "gks_autotune")
+        self.cfg.ilu_sweeps, self.cfg.warm_extrap, self.cfg.inner_rtol = r.ilu_sweeps, r.warm_extrap, r.inner_rtol
+        return {k: getattr(r, k) for k, _ in TuneResult._fields_}
 
     def limit(self, w, coef, out=None, flags=None, stream=None):
         """Shock detector and DWBAP limiter on coef (mesh created with limiter=1);

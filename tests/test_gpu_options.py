@@ -61,3 +61,39 @@ def test_warm_start_reset_forgets_both_solutions(G):
         ib = fresh.step(wb, 1e-3)
         assert ia["iters"] == ib["iters"]
     assert np.array_equal(host(wa), host(wb))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotune_keeps_the_state_and_the_results(G, precision):
+    c = I.shock_vortex_case(60, 30)
+    prec = G.MIXED if precision == "mixed" else G.FP64
+    w = dev(c.w0)
+    tuned = G.GksMesh(c.mesh, precision=prec)
+    r = tuned.autotune(w, trial_steps=2)
+    assert np.array_equal(host(w), c.w0)                   # the caller's state is untouched
+    assert r["ilu_sweeps"] in (1, 2, 3) and r["warm_extrap"] in (0, 1)
+    assert r["n_candidates"] == (18 if precision == "mixed" else 6) and r["n_failed"] == 0
+    assert 0 < r["ms_per_step"] <= r["ms_per_step_before"]
+    if precision == "fp64":
+        assert r["inner_rtol"] == 1e-6
+    plain = G.GksMesh(c.mesh, precision=prec)
+    wt, wp = dev(c.w0), dev(c.w0)
+    for _ in range(6):
+        dt = plain.cfl_dt(wp)
+        a = tuned.step(wt, dt)
+        plain.step(wp, dt)
+        assert max(a["relres"]) <= 1e-12
+    assert rel_max(host(wt), host(wp)) <= 1e-10
+
+
+def test_autotune_on_a_batch(G):
+    cases = [I.advection_case(14, k=2), I.shock_vortex_case(30, 15), I.sod_case(50, 4)]
+    w0 = np.ascontiguousarray(np.concatenate([c.w0 for c in cases], axis=1))
+    b = G.GksMesh.batch([c.mesh for c in cases], precision=G.MIXED, limiter=1)
+    r = b.autotune(dev(w0), trial_steps=2)
+    assert r["n_failed"] == 0
+    ref = G.GksMesh.batch([c.mesh for c in cases], precision=G.MIXED, limiter=1)
+    wa, wb = dev(w0), dev(w0)
+    assert b.batch_run(wa, max_steps=5)["n_failed"] == 0
+    ref.batch_run(wb, max_steps=5)
+    assert rel_max(host(wa), host(wb)) <= 1e-10
