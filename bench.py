@@ -37,11 +37,11 @@ FP64_PEAK_TFLOPS = 4 * 152 * 2.07e9 / 1e12
 # FP64 flops executed per face Gauss point by the FP64 flux kernel
 # (dadd + dmul + 2 dfma, ncu instruction counters on the 399,424-triangle case;
 # profiles/flux_fp64_shock_vortex_400k.md).
-FLUX_FP64_FLOP_PER_GP = 8389.3
+FLUX_FP64_FLOP_PER_GP = 8392.3
 # FP64 and FP32 flops per Gauss point of the mixed flux kernel (same counters,
 # 1,200,168 Gauss points; profiles/flux_mixed_shock_vortex_400k.md).
-FLUX_MIXED_FP64_FLOP_PER_GP = 932.7
-FLUX_MIXED_FP32_FLOP_PER_GP = 8245.1
+FLUX_MIXED_FP64_FLOP_PER_GP = 698.7
+FLUX_MIXED_FP32_FLOP_PER_GP = 7577.5
 
 WORKLOADS = {
     "shock_vortex_1m": dict(kind="shock_vortex", nx=1000, ny=500),

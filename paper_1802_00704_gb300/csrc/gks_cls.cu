@@ -28,15 +28,17 @@ constexpr int kDotMaxTiles = 65535;    // grid.y limit of the dot-product kernel
 // running (iterating in the current cycle), [8..11] Krylov vectors in the
 // cycle, [12..15] iterations so far.
 
-// y = O x_j for the gradient entries (g1, g2) of neighbour j
+// acc += sa [e1 + dx e3 + dy e4 | e2 + dx e4 + dy e5] (g1, g2): the off-diagonal
+// block O_ij = alpha [...] applied to the gradient entries (g1, g2) of
+// neighbour j, scaled by sa = +-alpha, with sax = sa dx, say = sa dy; all FMAs
 template <typename R>
-__device__ __forceinline__ void oapply(R a, R ex, R ey, R g1, R g2, R *o)
+__device__ __forceinline__ void oacc(R sa, R sax, R say, R g1, R g2, R *acc)
 {
-    o[0] = a * g1;
-    o[1] = a * g2;
-    o[2] = a * ex * g1;
-    o[3] = a * (ey * g1 + ex * g2);
-    o[4] = a * ey * g2;
+    acc[0] = fma(sa, g1, acc[0]);
+    acc[1] = fma(sa, g2, acc[1]);
+    acc[2] = fma(sax, g1, acc[2]);
+    acc[3] = fma(say, g1, fma(sax, g2, acc[3]));
+    acc[4] = fma(say, g2, acc[4]);
 }
 
 // Block reduction of NV values; thread 0 of the block gets the totals.
@@ -126,14 +128,10 @@ __global__ void k_spmv(DeviceMesh d, const TM *__restrict__ Dg, const TM *__rest
         for (int s = 0; s < 3; ++s) {
             const int j = d.nb[s * T + i];
             if (j < 0) continue;
-            const TM a = alg[s * T + i], ex = exg[s * T + i], ey = eyg[s * T + i];
+            const TM sa = -alg[s * T + i], sax = sa * exg[s * T + i], say = sa * eyg[s * T + i];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                TM o[ND];
-                oapply(a, ex, ey, TM(x[(v * ND + 0) * T + j]), TM(x[(v * ND + 1) * T + j]), o);
-#pragma unroll
-                for (int l = 0; l < ND; ++l) acc[v * ND + l] -= o[l];
-            }
+            for (int v = 0; v < NV; ++v)
+                oacc(sa, sax, say, TM(x[(v * ND + 0) * T + j]), TM(x[(v * ND + 1) * T + j]), acc + v * ND);
         }
         if (mode == 0) {
 #pragma unroll
@@ -165,10 +163,13 @@ __global__ void k_spmv(DeviceMesh d, const TM *__restrict__ Dg, const TM *__rest
 // Forward block-ILU relation for the listed rows (or all rows when rows == nullptr):
 //   z_i = P_i (r_i + sum_{k<i} O_ik zin_k)      (use_nb = 0: z_i = P_i r_i)
 // TR: type of r, TZ: type of z, TM: type of the factors and of the arithmetic.
+// rcopy (may be NULL): also store TZ(r_i), so that later sweeps read r in the
+// working precision (same values as converting r again).  Own data (r, P) is
+// loaded before the neighbour gathers so that the two overlap.
 template <typename TR, typename TZ, typename TM>
 __global__ void k_ilu_fwd(DeviceMesh d, const TM *__restrict__ Pg, const TM *__restrict__ alg,
                           const TM *__restrict__ exg, const TM *__restrict__ eyg, const int32_t *__restrict__ rows,
-                          int64_t nrows, const TR *r, const TZ *zin, TZ *zout, int use_nb)
+                          int64_t nrows, const TR *r, const TZ *zin, TZ *zout, int use_nb, TZ *__restrict__ rcopy)
 {
     const int64_t T = d.T;
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -177,24 +178,23 @@ __global__ void k_ilu_fwd(DeviceMesh d, const TM *__restrict__ Pg, const TM *__r
     TM y[NX];
 #pragma unroll
     for (int k = 0; k < NX; ++k) y[k] = TM(r[k * T + i]);
+    TM Pm[25];
+#pragma unroll
+    for (int k = 0; k < 25; ++k) Pm[k] = Pg[k * T + i];
+    if (rcopy)
+#pragma unroll
+        for (int k = 0; k < NX; ++k) rcopy[k * T + i] = TZ(y[k]);
     if (use_nb) {
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
             const int j = d.nb[s * T + i];
             if (j < 0 || j >= i) continue;
-            const TM a = alg[s * T + i], ex = exg[s * T + i], ey = eyg[s * T + i];
+            const TM sa = alg[s * T + i], sax = sa * exg[s * T + i], say = sa * eyg[s * T + i];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                TM o[ND];
-                oapply(a, ex, ey, TM(zin[(v * ND + 0) * T + j]), TM(zin[(v * ND + 1) * T + j]), o);
-#pragma unroll
-                for (int l = 0; l < ND; ++l) y[v * ND + l] += o[l];
-            }
+            for (int v = 0; v < NV; ++v)
+                oacc(sa, sax, say, TM(zin[(v * ND + 0) * T + j]), TM(zin[(v * ND + 1) * T + j]), y + v * ND);
         }
     }
-    TM Pm[25];
-#pragma unroll
-    for (int k = 0; k < 25; ++k) Pm[k] = Pg[k * T + i];
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
@@ -206,7 +206,9 @@ __global__ void k_ilu_fwd(DeviceMesh d, const TM *__restrict__ Pg, const TM *__r
         }
 }
 
-// Backward block-ILU relation: x_i = z_i + P_i sum_{j>i} O_ij xin_j
+// Backward block-ILU relation: x_i = z_i + P_i sum_{j>i} O_ij xin_j (own data
+// loaded before the neighbour gathers; with no upper neighbour the sum is 0
+// and x_i = z_i exactly).
 template <typename TZ, typename TM>
 __global__ void k_ilu_bwd(DeviceMesh d, const TM *__restrict__ Pg, const TM *__restrict__ alg,
                           const TM *__restrict__ exg, const TM *__restrict__ eyg, const int32_t *__restrict__ rows,
@@ -216,38 +218,29 @@ __global__ void k_ilu_bwd(DeviceMesh d, const TM *__restrict__ Pg, const TM *__r
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= nrows) return;
     const int64_t i = rows ? rows[q] : q;
-    TM y[NX];
+    TM zi[NX], y[NX];
 #pragma unroll
-    for (int k = 0; k < NX; ++k) y[k] = TM(0);
-    bool any = false;
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        const int j = d.nb[s * T + i];
-        if (j <= i) continue;
-        any = true;
-        const TM a = alg[s * T + i], ex = exg[s * T + i], ey = eyg[s * T + i];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            TM o[ND];
-            oapply(a, ex, ey, TM(xin[(v * ND + 0) * T + j]), TM(xin[(v * ND + 1) * T + j]), o);
-#pragma unroll
-            for (int l = 0; l < ND; ++l) y[v * ND + l] += o[l];
-        }
-    }
-    if (!any) {
-        if (xout != z)
-#pragma unroll
-            for (int k = 0; k < NX; ++k) xout[k * T + i] = z[k * T + i];
-        return;
+    for (int k = 0; k < NX; ++k) {
+        zi[k] = TM(z[k * T + i]);
+        y[k] = TM(0);
     }
     TM Pm[25];
 #pragma unroll
     for (int k = 0; k < 25; ++k) Pm[k] = Pg[k * T + i];
 #pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        const int j = d.nb[s * T + i];
+        if (j <= i) continue;
+        const TM sa = alg[s * T + i], sax = sa * exg[s * T + i], say = sa * eyg[s * T + i];
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+            oacc(sa, sax, say, TM(xin[(v * ND + 0) * T + j]), TM(xin[(v * ND + 1) * T + j]), y + v * ND);
+    }
+#pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
         for (int a = 0; a < ND; ++a) {
-            TM s = TM(z[(v * ND + a) * T + i]);
+            TM s = zi[v * ND + a];
 #pragma unroll
             for (int c = 0; c < ND; ++c) s += Pm[a * ND + c] * y[v * ND + c];
             xout[(v * ND + a) * T + i] = TZ(s);
@@ -555,7 +548,7 @@ inline unsigned nblocks(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock
 // arithmetic precision of the application; tA, tB: work buffers of type TZ.
 template <typename TR, typename TZ, typename TM>
 gks_status precond_t(gks_mesh *m, const TM *Pg, const TM *alg, const TM *exg, const TM *eyg, const TR *src,
-                     TZ *dst, TZ *tA, TZ *tB, cudaStream_t s)
+                     TZ *dst, TZ *tA, TZ *tB, TZ *rz, cudaStream_t s)
 {
     DeviceMesh &d = m->d;
     const int64_t T = d.T;
@@ -564,7 +557,7 @@ gks_status precond_t(gks_mesh *m, const TM *Pg, const TM *alg, const TM *exg, co
         for (size_t l = 0; l + 1 < lp.size(); ++l) {
             const int64_t n = lp[l + 1] - lp[l];
             k_ilu_fwd<TR, TZ, TM><<<nblocks(n), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, d.lvl_lo + lp[l], n, src,
-                                                                     dst, dst, 1);
+                                                                 dst, dst, 1, nullptr);
             note_launch();
         }
         const auto &up = m->lvl_up_ptr;
@@ -578,10 +571,17 @@ gks_status precond_t(gks_mesh *m, const TM *Pg, const TM *alg, const TM *exg, co
         const int ns = m->cfg.ilu_sweeps;
         TZ *za = (ns % 2 == 0) ? tA : dst;   // buffers chosen so that z ends in tA
         TZ *zb = (ns % 2 == 0) ? dst : tA;
-        k_ilu_fwd<TR, TZ, TM><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, src, nullptr, za, 0);
+        // a wider source is rounded to TZ once, in the first pass, for the sweeps
+        TZ *rc = (sizeof(TR) > sizeof(TZ) && ns > 0) ? rz : nullptr;
+        k_ilu_fwd<TR, TZ, TM><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, src, nullptr, za, 0, rc);
         note_launch();
         for (int q = 0; q < ns; ++q) {
-            k_ilu_fwd<TR, TZ, TM><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, src, za, zb, 1);
+            if (rc)
+                k_ilu_fwd<TZ, TZ, TM><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, rc, za, zb, 1,
+                                                                     nullptr);
+            else
+                k_ilu_fwd<TR, TZ, TM><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, src, za, zb, 1,
+                                                                     nullptr);
             note_launch();
             std::swap(za, zb);
         }
@@ -606,14 +606,15 @@ template <typename TR>
 gks_status precond(gks_mesh *m, const TR *src, double *dst, cudaStream_t s)
 {
     DeviceMesh &d = m->d;
-    return precond_t<TR, double, double>(m, d.P, d.alpha, d.ex, d.ey, src, dst, m->wk.t2, m->wk.t3, s);
+    return precond_t<TR, double, double>(m, d.P, d.alpha, d.ex, d.ey, src, dst, m->wk.t2, m->wk.t3, nullptr, s);
 }
 
 template <typename TR>
 gks_status precond32(gks_mesh *m, const TR *src, float *dst, cudaStream_t s)
 {
     DeviceMesh &d = m->d;
-    return precond_t<TR, float, float>(m, d.P32, d.alpha32, d.ex32, d.ey32, src, dst, m->wk.t2_32, m->wk.t3_32, s);
+    return precond_t<TR, float, float>(m, d.P32, d.alpha32, d.ex32, d.ey32, src, dst, m->wk.t2_32, m->wk.t3_32,
+                                       m->wk.r32, s);
 }
 
 gks_status read_flags(gks_mesh *m, cudaStream_t s)

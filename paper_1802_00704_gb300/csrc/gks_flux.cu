@@ -62,19 +62,20 @@ __device__ __forceinline__ void to_face(const double *g, double nx, double ny, d
 
 // Mixed precision reconstruction: FP64 values, FP32 derivative rows (global frame).
 __device__ __forceinline__ void recon_mixed(const DeviceMesh &d, const double *__restrict__ w,
-                                            const double *__restrict__ x, int c, double dx, double dy, double *val,
-                                            float *der)
+                                            const double *__restrict__ x, const float *__restrict__ x32, int c,
+                                            double dx, double dy, double *val, float *der)
 {
     const int64_t T = d.T;
     const double qx = dx * dx - d.mxx[c], qxy = dx * dy - d.mxy[c], qy = dy * dy - d.myy[c];
-    const float ih = float(1.0 / d.h[c]);
+    const float ih = d.ih32[c];
     const float fx = float(dx), fy = float(dy);
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
         const double u1 = x[(v * 5 + 0) * T + c], u2 = x[(v * 5 + 1) * T + c], u3 = x[(v * 5 + 2) * T + c];
         const double u4 = x[(v * 5 + 3) * T + c], u5 = x[(v * 5 + 4) * T + c];
         val[v] = w[v * T + c] + u1 * dx + u2 * dy + 0.5 * u3 * qx + u4 * qxy + 0.5 * u5 * qy;
-        const float f1 = float(u1), f2 = float(u2), f3 = float(u3), f4 = float(u4), f5 = float(u5);
+        const float f1 = x32[(v * 5 + 0) * T + c], f2 = x32[(v * 5 + 1) * T + c], f3 = x32[(v * 5 + 2) * T + c];
+        const float f4 = x32[(v * 5 + 3) * T + c], f5 = x32[(v * 5 + 4) * T + c];
         der[v] = (f1 + f3 * fx + f4 * fy) * ih;
         der[4 + v] = (f2 + f4 * fx + f5 * fy) * ih;
         der[8 + v] = f3 * ih * ih;
@@ -200,12 +201,21 @@ __device__ __forceinline__ void ghost(int tag, const double *bc, double nx, doub
     }
 }
 
+// y = float(x), n values
+__global__ void k_to_f32(const double *__restrict__ x, float *__restrict__ y, int64_t n)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = float(x[i]);
+}
+
 // MIXED: interface state and leading terms in FP64, slope-carrying terms in FP32.
 template <bool MIXED>
 __global__ void __launch_bounds__(kFluxBlock) k_face_flux(DeviceMesh d, const double *__restrict__ w,
-                                                          const double *__restrict__ x, double dt_const,
-                                                          const double *__restrict__ dt_dev, double gamma, double mu,
-                                                          int tau2, double *__restrict__ flux, int32_t *status)
+                                                          const double *__restrict__ x,
+                                                          const float *__restrict__ x32, double dt_const,
+                                                          const double *__restrict__ dt_dev, double gamma, double K,
+                                                          double mu, int tau2, double *__restrict__ flux,
+                                                          int32_t *status)
 {
     const int64_t F = d.F;
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -223,16 +233,16 @@ __global__ void __launch_bounds__(kFluxBlock) k_face_flux(DeviceMesh d, const do
         if (MIXED) {
             double vl[4], vr[4];
             float dl[20], dr[20];
-            recon_mixed(d, w, x, l, d.gl[(2 * k) * F + f], d.gl[(2 * k + 1) * F + f], vl, dl);
+            recon_mixed(d, w, x, x32, l, d.gl[(2 * k) * F + f], d.gl[(2 * k + 1) * F + f], vl, dl);
             to_face_mixed(vl, dl, nx, ny);
             if (r >= 0) {
-                recon_mixed(d, w, x, r, d.gr[(2 * k) * F + f], d.gr[(2 * k + 1) * F + f], vr, dr);
+                recon_mixed(d, w, x, x32, r, d.gr[(2 * k) * F + f], d.gr[(2 * k + 1) * F + f], vr, dr);
                 to_face_mixed(vr, dr, nx, ny);
             } else {
                 const double bc[4] = {d.bc[f], d.bc[F + f], d.bc[2 * F + f], d.bc[3 * F + f]};
                 ghost_mixed(d.ftag[f], bc, nx, ny, gamma, vl, dl, vr, dr);
             }
-            ok = kin::gp_flux_mixed_split(vl, vr, dl, dr, dt, gamma, mu, tau2, fk);
+            ok = kin::gp_flux_mixed_split(vl, vr, dl, dr, dt, gamma, K, mu, tau2, fk);
         } else {
             double gl[24], wl[24], wr[24];
             recon(d, w, x, l, d.gl[(2 * k) * F + f], d.gl[(2 * k + 1) * F + f], gl);
@@ -427,15 +437,20 @@ gks_status launch_flux(gks_mesh *m, const double *w, const double *x, double dt_
                        double *flux, cudaStream_t s)
 {
     const int64_t npts = 2 * m->d.F;
+    const double K = 2.0 / (m->cfg.gamma - 1.0) - 2.0;
     const int slot = prof_start(m, kProfFlux, s);
     if (m->cfg.precision == GKS_MIXED) {
-        k_face_flux<true><<<blocks(npts, kFluxBlock), kFluxBlock, 0, s>>>(m->d, w, x, dt_const, dt_dev, m->cfg.gamma,
-                                                                          m->cfg.mu, m->cfg.tau2_exact, flux,
-                                                                          m->wk.status);
+        // FP32 copy of the coefficients: the slope-carrying rows of every Gauss
+        // point of a cell read it instead of converting the FP64 values again
+        k_to_f32<<<blocks(20 * m->d.T, kBlock), kBlock, 0, s>>>(x, m->wk.x32, 20 * m->d.T);
+        note_launch();
+        k_face_flux<true><<<blocks(npts, kFluxBlock), kFluxBlock, 0, s>>>(m->d, w, x, m->wk.x32, dt_const, dt_dev,
+                                                                          m->cfg.gamma, K, m->cfg.mu,
+                                                                          m->cfg.tau2_exact, flux, m->wk.status);
     } else {
-        k_face_flux<false><<<blocks(npts, kFluxBlock), kFluxBlock, 0, s>>>(m->d, w, x, dt_const, dt_dev, m->cfg.gamma,
-                                                                           m->cfg.mu, m->cfg.tau2_exact, flux,
-                                                                           m->wk.status);
+        k_face_flux<false><<<blocks(npts, kFluxBlock), kFluxBlock, 0, s>>>(m->d, w, x, nullptr, dt_const, dt_dev,
+                                                                           m->cfg.gamma, K, m->cfg.mu,
+                                                                           m->cfg.tau2_exact, flux, m->wk.status);
     }
     note_launch();
     prof_stop(m, slot, s);

@@ -64,6 +64,7 @@ struct DeviceMesh {
     double *P = nullptr;             // [25][T] inverse of the ILU(0) diagonal block, row-major
     // FP32 copies of the operator and factors (mixed precision)
     float *D32 = nullptr, *P32 = nullptr, *alpha32 = nullptr, *ex32 = nullptr, *ey32 = nullptr;
+    float *ih32 = nullptr;           // [T] 1 / h_i (mixed flux)
     double *ox = nullptr, *oy = nullptr;  // [3][T] neighbour centroid in i's scaled frame (limiter)
     int32_t *kord = nullptr;         // [T] reconstruction order k_i of Eq. (28) (limiter)
     int32_t *cf = nullptr;           // [3][T] (face << 1) | side, -1 unused
@@ -89,9 +90,11 @@ struct Work {
     double *x_prev = nullptr;        // [20][T] the solution before (extrapolated warm start)
     int64_t nsolve = 0;              // solves since creation or the last warm-start reset
     double *xl = nullptr;            // [20][T] limited coefficients (limiter on)
+    float *x32 = nullptr;            // [20][T] FP32 copy of the coefficients the mixed flux reads
     int32_t *lflag = nullptr;        // [T] 0 untouched, 1 limited, 2 reset to the average
     double *b = nullptr, *r = nullptr, *t2 = nullptr, *t3 = nullptr;  // [20][T]
     float *t2_32 = nullptr, *t3_32 = nullptr;  // [20][T] FP32 preconditioner work
+    float *r32 = nullptr;            // [20][T] FP32 copy of the preconditioner's source (sweeps)
     double *V = nullptr;             // [(m+1)][20][T] Krylov basis, unnormalised: v_k = V_k / vn_k
     float *V32 = nullptr;            // the same stored in FP32 (mixed mode with basis_fp32; V unused)
     double *Z = nullptr;             // [m][20][T] M^{-1} V_k (FP64 path)

@@ -505,18 +505,9 @@ __device__ __forceinline__ bool gp_flux(const R *wl, const R *wr, R dt, R gamma,
     return true;
 }
 
-template <typename A, typename B>
-__device__ __forceinline__ void kstate_cast(const KState<A> &a, KState<B> &b)
-{
-    b.rho = B(a.rho);
-    b.U = B(a.U);
-    b.V = B(a.V);
-    b.lam = B(a.lam);
-    b.p = B(a.p);
-}
-
-// Primitive state from the FP64 values with one reciprocal.
-__device__ __forceinline__ bool prim64(const double *w, double gamma, double K, KState<double> &s)
+// Primitive state from the FP64 values with two reciprocals; h = 1/(2 lam)
+// comes out of the same quantities without a further division.
+__device__ __forceinline__ bool prim64(const double *w, double gamma, double K, KState<double> &s, double &h)
 {
     s.rho = w[0];
     const double ir = 1.0 / w[0];
@@ -525,74 +516,96 @@ __device__ __forceinline__ bool prim64(const double *w, double gamma, double K, 
     const double eint = w[3] - 0.5 * s.rho * (s.U * s.U + s.V * s.V);
     s.p = (gamma - 1.0) * eint;
     s.lam = 0.25 * (K + 2.0) * s.rho / eint;
+    h = 2.0 / (K + 2.0) * eint * ir;                 // (K + 2) rho / (4 eint) = lam
     return s.rho > 0.0 && s.p > 0.0;
 }
 
-// Half-space moments <u^k>, k = 0..3, in FP64 (sign = +1: u > 0, -1: u < 0).
-__device__ __forceinline__ void mom_half4(double U, double lam, double sign, double *m)
+// Half-space moments <u^k>, k = 0..3, in FP64 (sign = +1: u > 0, -1: u < 0);
+// h = 1/(2 lam).
+__device__ __forceinline__ void mom_half4(double U, double lam, double h, double sign, double *m)
 {
-    const double h = 0.5 / lam;
-    const double sl = sqrt(lam);
-    m[0] = 0.5 * erfc(-sign * sl * U);
-    m[1] = U * m[0] + sign * 0.5 * exp(-lam * U * U) / (sl * 1.7724538509055160273);
+    const double rs = rsqrt(lam);                    // 1/sqrt(lam); sqrt(lam) = lam rs
+    m[0] = 0.5 * erfc(-sign * (lam * rs) * U);
+    m[1] = U * m[0] + sign * (0.5 / 1.7724538509055160273) * exp(-lam * U * U) * rs;
     m[2] = U * m[1] + h * m[0];
     m[3] = U * m[2] + 2.0 * h * m[1];
 }
 
+// FP64 time integrals of c1 and c7 (Eq. (13)) over [0, dt], the coefficients of
+// the zeroth-order terms: int c1 = dt - T0, int c7 = T0, T0 = tau (1 - e^{-dt/tau});
+// power series where the closed form cancels (x = dt/tau < 1/2).
+__device__ __forceinline__ void lead_integrals(double dt, double tau, double &c0, double &c6)
+{
+    const double x = dt / tau;
+    double t0, c1;
+    if (x >= 0.5) {
+        t0 = -expm1(-x);
+        c1 = x - t0;
+    } else {
+        // t0 = sum_{p>=1} (-1)^{p+1} x^p / p!,  c1 = x - t0 = sum_{p>=2} (-1)^p x^p / p!
+        double pw = x, sg = 1.0;
+        t0 = 0.0;
+        c1 = 0.0;
+#pragma unroll
+        for (int p = 1; p < 20; ++p) {
+            t0 += sg * pw;
+            if (p >= 2) c1 -= sg * pw;
+            pw *= x * (1.0 / double(p + 1));
+            sg = -sg;
+        }
+    }
+    c0 = tau * c1;
+    c6 = tau * t0;
+}
+
 // Mixed precision Gauss-point flux.  vl, vr: FP64 face-frame values
 // (rho, rho U, rho V, E); dl, dr: FP32 face-frame derivative rows [5][4]
-// (d/dn, d/dt, d2/dn2, d2/dndt, d2/dt2).  The interface state W0, the
+// (d/dn, d/dt, d2/dn2, d2/dndt, d2/dt2); K = 2/(gamma - 1) - 2.  The interface state W0, the
 // collision time, the time integrals and the zeroth-order terms
 // C1 rho0 <u psi>_0 + C7 (rho_l <u psi>_{u>0} + rho_r <u psi>_{u<0}) are FP64;
 // every slope-carrying term is FP32.
 __device__ __forceinline__ bool gp_flux_mixed_split(const double *vl, const double *vr, const float *dl, const float *dr,
-                                                    double dt, double gamma, double mu, int tau2_exact, double *f)
+                                                    double dt, double gamma, double K, double mu, int tau2_exact,
+                                                    double *f)
 {
-    const double K = 2.0 / (gamma - 1.0) - 2.0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) f[q] = 0.0;
     KState<double> L, Rs, Z;
-    if (!(prim64(vl, gamma, K, L) & prim64(vr, gamma, K, Rs))) return false;
+    double hl, hr, hz;
+    if (!(prim64(vl, gamma, K, L, hl) & prim64(vr, gamma, K, Rs, hr))) return false;
     double ml[4], mr[4];
-    mom_half4(L.U, L.lam, 1.0, ml);
-    mom_half4(Rs.U, Rs.lam, -1.0, mr);
-    const double hl = 0.5 / L.lam, hr = 0.5 / Rs.lam;
+    mom_half4(L.U, L.lam, hl, 1.0, ml);
+    mom_half4(Rs.U, Rs.lam, hr, -1.0, mr);
     const double v2l = L.V * L.V + hl, v2r = Rs.V * Rs.V + hr;
-    const double zl = 0.5 * K / L.lam, zr = 0.5 * K / Rs.lam;
+    const double zl = K * hl, zr = K * hr;           // <xi.xi> / 2 = K / (4 lam)
     double w0[4];
     w0[0] = L.rho * ml[0] + Rs.rho * mr[0];
     w0[1] = L.rho * ml[1] + Rs.rho * mr[1];
     w0[2] = L.rho * ml[0] * L.V + Rs.rho * mr[0] * Rs.V;
     w0[3] = L.rho * 0.5 * (ml[2] + ml[0] * (v2l + zl)) + Rs.rho * 0.5 * (mr[2] + mr[0] * (v2r + zr));
-    if (!prim64(w0, gamma, K, Z)) return false;
+    if (!prim64(w0, gamma, K, Z, hz)) return false;
     const double jump = fabs(L.p - Rs.p) / fabs(L.p + Rs.p);
     const double tau = mu > 0.0 ? mu / Z.p + dt * jump : 0.01 * dt + dt * jump;
-    double C[9];
-    time_integrals(dt, tau, tau2_exact, C);
+    double C0, C6;
+    lead_integrals(dt, tau, C0, C6);
     // leading terms (FP64)
     {
-        const double h = 0.5 / Z.lam;
-        const double m2 = Z.U * Z.U + h, m3 = Z.U * m2 + 2.0 * h * Z.U;
-        const double v2 = Z.V * Z.V + h, z1 = 0.5 * K / Z.lam;
-        const double s0 = C[0] * Z.rho;
+        const double m2 = Z.U * Z.U + hz, m3 = Z.U * m2 + 2.0 * hz * Z.U;
+        const double v2 = Z.V * Z.V + hz, z1 = K * hz;
+        const double s0 = C0 * Z.rho;
         f[0] = s0 * Z.U;
         f[1] = s0 * m2;
         f[2] = s0 * Z.U * Z.V;
         f[3] = s0 * 0.5 * (m3 + Z.U * (v2 + z1));
-        const double sl = C[6] * L.rho, sr = C[6] * Rs.rho;
+        const double sl = C6 * L.rho, sr = C6 * Rs.rho;
         f[0] += sl * ml[1] + sr * mr[1];
         f[1] += sl * ml[2] + sr * mr[2];
         f[2] += sl * ml[1] * L.V + sr * mr[1] * Rs.V;
         f[3] += sl * 0.5 * (ml[3] + ml[1] * (v2l + zl)) + sr * 0.5 * (mr[3] + mr[1] * (v2r + zr));
     }
-    // slope-carrying terms (FP32)
+    // slope-carrying terms (FP32): states, interface values and time integrals
+    // are formed in FP32 from the rounded values (no per-field conversions)
     Iface<float> J;
-    kstate_cast(L, J.L);
-    kstate_cast(Rs, J.Rs);
-    kstate_cast(Z, J.Z);
-    J.tau = float(tau);
-#pragma unroll
-    for (int q = 0; q < 9; ++q) J.C[q] = float(C[q]);
     float fl[24], fr[24], g[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -606,7 +619,13 @@ __device__ __forceinline__ bool gp_flux_mixed_split(const double *vl, const doub
         fr[4 + q] = dr[q];
         J.w0[4 + q] = 0.5f * (dl[q] + dr[q]);
     }
-    body_flux(fl, fr, J, float(gamma), false, g);
+    const float gf = float(gamma), Kf = float(K);
+    prim(fl, gf, Kf, J.L);
+    prim(fr, gf, Kf, J.Rs);
+    prim(J.w0, gf, Kf, J.Z);
+    J.tau = float(tau);
+    time_integrals(float(dt), J.tau, tau2_exact, J.C);
+    body_flux(fl, fr, J, gf, false, g);
 #pragma unroll
     for (int q = 0; q < 4; ++q) f[q] += double(g[q]);
     return true;
@@ -622,7 +641,7 @@ __device__ __forceinline__ bool gp_flux_mixed(const double *wl, const double *wr
         dl[q] = float(wl[4 + q]);
         dr[q] = float(wr[4 + q]);
     }
-    return gp_flux_mixed_split(wl, wr, dl, dr, dt, gamma, mu, tau2_exact, f);
+    return gp_flux_mixed_split(wl, wr, dl, dr, dt, gamma, 2.0 / (gamma - 1.0) - 2.0, mu, tau2_exact, f);
 }
 
 }  // namespace kin

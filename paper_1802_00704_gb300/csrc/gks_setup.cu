@@ -672,6 +672,9 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
     if (cfg.precision == GKS_MIXED) {
         auto f32 = [](const std::vector<double> &v) { return std::vector<float>(v.begin(), v.end()); };
         UP(D32, f32(h_D)); UP(P32, f32(h_P)); UP(alpha32, f32(h_alpha)); UP(ex32, f32(h_ex)); UP(ey32, f32(h_ey));
+        std::vector<float> h_ih32(T);
+        for (int64_t i = 0; i < T; ++i) h_ih32[i] = float(1.0 / h_h[i]);
+        UP(ih32, h_ih32);
     }
 #undef UP
 
@@ -692,7 +695,7 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
     }
     AL(flux, 4 * F);
     if (cfg.precision == GKS_MIXED) {
-        AL(t2_32, 20 * T); AL(t3_32, 20 * T); AL(Z32, (size_t)mm * 20 * T);
+        AL(t2_32, 20 * T); AL(t3_32, 20 * T); AL(r32, 20 * T); AL(Z32, (size_t)mm * 20 * T);
     } else {
         AL(Z, (size_t)mm * 20 * T);
     }
@@ -701,6 +704,7 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
         AL(xl, 20 * T); AL(lflag, T);
     }
     AL(x_prev, 20 * T);   // extrapolated warm start (also for the autotuner's candidates)
+    if (cfg.precision == GKS_MIXED) AL(x32, 20 * T);
     AL(H, ns * (mm + 1) * mm); AL(cs, ns * mm); AL(sn, ns * mm); AL(g, ns * (mm + 1)); AL(y, ns * mm);
     AL(hcol, ns * (mm + 2)); AL(hco, ns * (mm + 2)); AL(vn, ns * (mm + 1)); AL(bnorm, ns); AL(beta, ns); AL(ctl, kCtlFields * ns); AL(flags, 4);
     AL(dt, n_cases); AL(tcase, n_cases); AL(tfinal, n_cases); AL(done, n_cases); AL(scal, 8); AL(status, n_cases);
