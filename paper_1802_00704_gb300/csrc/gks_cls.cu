@@ -93,10 +93,13 @@ __global__ void k_rhs(DeviceMesh d, const double *__restrict__ w, double *__rest
     for (int q = 0; q < NX; ++q) b[q * T + i] = acc[q];
 }
 
-// y = K x (mode 0) or y = b - K x with partial sums of |y|^2 and |b|^2 (mode 1).
-// K_ii = D_i (symmetric, 15 stored values), K_ij = -O_ij.  TX: type of x,
-// TM: type of the operator data and of the arithmetic (mode 1 is FP64 only),
-// TY: type of y (the residual norms are those of the FP64 values).
+// y = K x (mode 0), or y = b - K x with partial sums of |y|^2 (mode >= 1) and
+// of |b|^2 (mode 1).  K_ii = D_i (symmetric, 15 stored values), K_ij = -O_ij.
+// TX: type of x, TM: type of the operator data and of the arithmetic (modes
+// 1, 2 are FP64 only), TY: type of y (the residual norms are those of the FP64
+// values).  Every load (neighbour indices, blocks, the neighbours' gradient
+// entries, own data) is issued before the arithmetic; a missing neighbour reads
+// the cell's own entries with a zero block.
 template <typename TX, typename TM, typename TY>
 __global__ void k_spmv(DeviceMesh d, const TM *__restrict__ Dg, const TM *__restrict__ alg,
                        const TM *__restrict__ exg, const TM *__restrict__ eyg, const TX *__restrict__ x,
@@ -108,6 +111,24 @@ __global__ void k_spmv(DeviceMesh d, const TM *__restrict__ Dg, const TM *__rest
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double nr[NV] = {0, 0, 0, 0}, nb[NV] = {0, 0, 0, 0};
     if (i < T) {
+        int64_t jn[3];
+        TM sa[3], sax[3], say[3];
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            const int j = d.nb[s * T + i];
+            jn[s] = j >= 0 ? j : i;
+            sa[s] = j >= 0 ? -alg[s * T + i] : TM(0);
+            sax[s] = sa[s] * exg[s * T + i];
+            say[s] = sa[s] * eyg[s * T + i];
+        }
+        TM g[3][2 * NV];
+#pragma unroll
+        for (int s = 0; s < 3; ++s)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                g[s][2 * v] = TM(x[(v * ND + 0) * T + jn[s]]);
+                g[s][2 * v + 1] = TM(x[(v * ND + 1) * T + jn[s]]);
+            }
         TM Dm[15];
 #pragma unroll
         for (int q = 0; q < 15; ++q) Dm[q] = Dg[q * T + i];
@@ -125,14 +146,9 @@ __global__ void k_spmv(DeviceMesh d, const TM *__restrict__ Dg, const TM *__rest
             acc[v * ND + 4] = Dm[4] * xv[0] + Dm[8] * xv[1] + Dm[11] * xv[2] + Dm[13] * xv[3] + Dm[14] * xv[4];
         }
 #pragma unroll
-        for (int s = 0; s < 3; ++s) {
-            const int j = d.nb[s * T + i];
-            if (j < 0) continue;
-            const TM sa = -alg[s * T + i], sax = sa * exg[s * T + i], say = sa * eyg[s * T + i];
+        for (int s = 0; s < 3; ++s)
 #pragma unroll
-            for (int v = 0; v < NV; ++v)
-                oacc(sa, sax, say, TM(x[(v * ND + 0) * T + j]), TM(x[(v * ND + 1) * T + j]), acc + v * ND);
-        }
+            for (int v = 0; v < NV; ++v) oacc(sa[s], sax[s], say[s], g[s][2 * v], g[s][2 * v + 1], acc + v * ND);
         if (mode == 0) {
 #pragma unroll
             for (int q = 0; q < NX; ++q) y[q * T + i] = TY(acc[q]);
@@ -145,17 +161,17 @@ __global__ void k_spmv(DeviceMesh d, const TM *__restrict__ Dg, const TM *__rest
                     const double rv = bv - double(acc[v * ND + l]);
                     y[(v * ND + l) * T + i] = TY(rv);
                     nr[v] += rv * rv;
-                    nb[v] += bv * bv;
+                    if (mode == 1) nb[v] += bv * bv;
                 }
         }
     }
-    if (mode == 1) {
+    if (mode >= 1) {
         block_sum4(nr, sh);
-        block_sum4(nb, sh);
+        if (mode == 1) block_sum4(nb, sh);
         if (threadIdx.x == 0)
             for (int v = 0; v < NV; ++v) {
                 part[(blockIdx.x * NV + v) * pstride + 0] = nr[v];
-                part[(blockIdx.x * NV + v) * pstride + 1] = nb[v];
+                if (mode == 1) part[(blockIdx.x * NV + v) * pstride + 1] = nb[v];
             }
     }
 }
@@ -479,7 +495,8 @@ __global__ void k_start(const double *__restrict__ sums, int sstride, double *bn
 {
     const int sy = blockIdx.x * blockDim.x + threadIdx.x;
     if (sy >= ns) return;
-    const double bn = sqrt(sums[sy * sstride + 1]), be = sqrt(sums[sy * sstride + 0]);
+    // |b| comes with the first residual; restarts reuse it
+    const double bn = first ? sqrt(sums[sy * sstride + 1]) : bnorm[sy], be = sqrt(sums[sy * sstride + 0]);
     if (first) {
         bnorm[sy] = bn;
         ctl[kCtlIters * ns + sy] = 0;
@@ -732,10 +749,10 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
         else
             k_combine_z<double><<<dim3(nb, NV), kBlock, 0, s>>>(d, k.Z, k.y, mm, k.ctl, ns, k.x);
         note_launch();
-        k_spmv<double, double, TB><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, V, 1, k.b, k.part, ps);
+        k_spmv<double, double, TB><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, V, 2, k.b, k.part, ps);
         note_launch();
         m->prof.residuals += 1;
-        k_reduce<<<dim3(2, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.hcol, ps, 0); note_launch();
+        k_reduce<<<dim3(1, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.hcol, ps, 0); note_launch();
         k_start<<<sblocks(ns), 128, 0, s>>>(k.hcol, ps, k.bnorm, k.beta, k.vn, mm, k.ctl, ns, k.done, rtol, maxit, 0);
         note_launch();
         GKS_CUDA(cudaGetLastError());

@@ -1,4 +1,6 @@
 """Input generator: split-quad meshes, periodic pairing, boundary tags, determinism."""
+import os
+
 import numpy as np
 import pytest
 
@@ -6,10 +8,11 @@ from paper_1802_00704_gb300 import inputs as I
 
 
 def test_splitmix64_reference_values():
-    # First outputs of SplitMix64 with seed 0 (published reference sequence of
-    # the generator: 0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F).
-    z = I.splitmix64(0, 3)
-    assert [int(v) for v in z] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    # first outputs of SplitMix64 from state 0 (published reference sequence, tests/golden)
+    gold = os.path.join(os.path.dirname(__file__), "golden", "splitmix64_seed0.txt")
+    ref = [int(l, 16) for l in open(gold) if l.strip() and not l.startswith("#")]
+    z = I.splitmix64(0, len(ref))
+    assert [int(v) for v in z] == ref
 
 
 @pytest.mark.parametrize("n", [3, 4, 20])

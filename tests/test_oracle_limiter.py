@@ -3,6 +3,8 @@ data are not flagged and keep their coefficients; the limited scheme runs the
 Sod problem (Eq. (44)) to t = 0.2 with positive states, and its distance to the
 exact Riemann solution (Rankine-Hugoniot and isentropic relations, solved by
 Newton iteration on the star pressure) shrinks under mesh refinement."""
+import os
+
 import numpy as np
 
 from paper_1802_00704_gb300 import inputs as I
@@ -10,10 +12,14 @@ from tests.exact_riemann import exact_riemann
 
 
 def test_exact_riemann_solver_star_state():
-    # Sod: star pressure 0.30313 and velocity 0.92745 (textbook values of the problem)
-    x = np.array([0.5 + 0.92745 * 0.2 - 1e-4])
+    # Sod star region against the tabulated five-digit values (tests/golden)
+    gold = os.path.join(os.path.dirname(__file__), "golden", "sod_star_state.txt")
+    ref = dict((k, float(v)) for k, v in (l.split() for l in open(gold) if l.strip() and not l.startswith("#")))
+    us = ref["u_star"]
+    x = np.array([0.5 + us * 0.2 - 1e-4, 0.5 + us * 0.2 + 1e-4])
     r, u, p = exact_riemann(x, 0.2, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1))
-    assert abs(p[0] - 0.30313) < 1e-4 and abs(u[0] - 0.92745) < 1e-4
+    assert np.all(np.abs(p - ref["p_star"]) < 1e-5) and np.all(np.abs(u - us) < 1e-5)
+    assert abs(r[0] - ref["rho_star_left"]) < 1e-5 and abs(r[1] - ref["rho_star_right"]) < 1e-5
 
 
 def test_smooth_data_not_limited(oracle_mod):
