@@ -347,22 +347,29 @@ __global__ void k_orth_update(DeviceMesh d, const TB *__restrict__ V, TB *__rest
     }
 }
 
-// Segmented sums over the partial-sum rows of each case (cell blocks or
-// super-blocks, seg[c]..seg[c+1]), fixed order:
+// Segmented sums over the partial-sum rows of each case (cell blocks,
+// seg[c]..seg[c+1]), fixed order:
 // out[s][q] (op) sum_{b in case(s)} part[b][v(s)][q], q < nq; op 0 store, 1 add,
 // 2 store sqrt.  With vn given, also co[s][q] = sum / vn[s][q]^2 (the
-// Gram-Schmidt coefficient of the unnormalised basis vector q).  One warp per
-// (q, s): grid (nq, ns), 32 threads.
-__global__ void k_reduce(const double *__restrict__ part, const int32_t *__restrict__ seg, int pstride,
-                         double *out, int ostride, int op, const double *__restrict__ vn = nullptr,
-                         int vstride = 0, double *co = nullptr, int cstride = 0)
+// Gram-Schmidt coefficient of the unnormalised basis vector q).  One block of
+// kReduceThreads per (q, s): grid (nq, ns).
+constexpr int kReduceThreads = 256;
+__global__ void __launch_bounds__(kReduceThreads) k_reduce(const double *__restrict__ part,
+                                                           const int32_t *__restrict__ seg, int pstride, double *out,
+                                                           int ostride, int op, const double *__restrict__ vn = nullptr,
+                                                           int vstride = 0, double *co = nullptr, int cstride = 0)
 {
+    __shared__ double sh[kReduceThreads / 32];
     const int q = blockIdx.x, sy = blockIdx.y, c = sy >> 2, v = sy & 3;
     const int b0 = seg[c], b1 = seg[c + 1];
     double acc = 0.0;
-    for (int b = b0 + threadIdx.x; b < b1; b += 32) acc += part[(b * NV + v) * pstride + q];
+    for (int b = b0 + threadIdx.x; b < b1; b += kReduceThreads) acc += part[((int64_t)b * NV + v) * pstride + q];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
     if (threadIdx.x == 0) {
+        acc = 0.0;
+        for (int w = 0; w < kReduceThreads / 32; ++w) acc += sh[w];
         if (op == 0) out[sy * ostride + q] = acc;
         else if (op == 1) out[sy * ostride + q] += acc;
         else out[sy * ostride + q] = sqrt(acc);
@@ -690,7 +697,7 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
     k_spmv<double, double, TB><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, V, 1, k.b, k.part, ps);
     note_launch();
     m->prof.residuals += 1;
-    k_reduce<<<dim3(2, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.hcol, ps, 0); note_launch();
+    k_reduce<<<dim3(2, ns), kReduceThreads, 0, s>>>(k.part, d.case_blk, ps, k.hcol, ps, 0); note_launch();
     k_start<<<sblocks(ns), 128, 0, s>>>(k.hcol, ps, k.bnorm, k.beta, k.vn, mm, k.ctl, ns, k.done, rtol, maxit, 1);
     note_launch();
     k_zero_trivial<<<nb, kBlock, 0, s>>>(d, k.x, k.bnorm); note_launch();
@@ -722,18 +729,21 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
             // classical Gram-Schmidt: twice in FP64 mode; once in the mixed mode, whose
             // cycles only reduce the residual by inner_rtol before an FP64 restart
             if ((st = dots<TB>(m, V, vj1, j, k.part, ps, s)) != GKS_OK) return st;
-            k_reduce<<<dim3(j + 1, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.hcol, ps, 0, k.vn, mm + 1, k.hco, ps);
+            k_reduce<<<dim3(j + 1, ns), kReduceThreads, 0, s>>>(k.part, d.case_blk, ps, k.hcol, ps, 0, k.vn, mm + 1,
+                                                                 k.hco, ps);
             note_launch();
             k_orth_update<TB><<<nb, kBlock, 0, s>>>(d, V, vj1, j, k.hco, ps, k.ctl, ns, k.part, ps, mixed ? 1 : 0);
             note_launch();
             if (!mixed) {
                 if ((st = dots<TB>(m, V, vj1, j, k.part, ps, s)) != GKS_OK) return st;
-                k_reduce<<<dim3(j + 1, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.y, mm, 0, k.vn, mm + 1, k.hco, ps);
+                k_reduce<<<dim3(j + 1, ns), kReduceThreads, 0, s>>>(k.part, d.case_blk, ps, k.y, mm, 0, k.vn, mm + 1,
+                                                                     k.hco, ps);
                 note_launch();
                 k_orth_update<TB><<<nb, kBlock, 0, s>>>(d, V, vj1, j, k.hco, ps, k.ctl, ns, k.part, ps, 1); note_launch();
                 k_hadd<<<sblocks(ns * (j + 1)), 128, 0, s>>>(k.hcol, ps, k.y, mm, j, ns); note_launch();
             }
-            k_reduce<<<dim3(1, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.hcol + j + 1, ps, 2); note_launch();
+            k_reduce<<<dim3(1, ns), kReduceThreads, 0, s>>>(k.part, d.case_blk, ps, k.hcol + j + 1, ps, 2);
+            note_launch();
             prof_stop(m, slot, s);
             k_givens<<<sblocks(ns), 128, 0, s>>>(j, mm, k.hcol, ps, k.vn, k.H, k.cs, k.sn, k.g, k.ctl, ns, k.bnorm,
                                                   k.beta, rtol, eta, maxit);
@@ -752,7 +762,7 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
         k_spmv<double, double, TB><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, V, 2, k.b, k.part, ps);
         note_launch();
         m->prof.residuals += 1;
-        k_reduce<<<dim3(1, ns), 32, 0, s>>>(k.part, d.case_blk, ps, k.hcol, ps, 0); note_launch();
+        k_reduce<<<dim3(1, ns), kReduceThreads, 0, s>>>(k.part, d.case_blk, ps, k.hcol, ps, 0); note_launch();
         k_start<<<sblocks(ns), 128, 0, s>>>(k.hcol, ps, k.bnorm, k.beta, k.vn, mm, k.ctl, ns, k.done, rtol, maxit, 0);
         note_launch();
         GKS_CUDA(cudaGetLastError());
