@@ -48,6 +48,7 @@ WORKLOADS = {
     "shock_vortex_small": dict(kind="shock_vortex", nx=200, ny=100),
     "shock_vortex_400k": dict(kind="shock_vortex", nx=632, ny=316),
     "advection_20": dict(kind="advection", n=20),
+    "batch_512": dict(kind="batch", n=512),
 }
 
 
@@ -137,6 +138,17 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "power_w_median": statistics.median(power) if power else None, "samples": len(sm),
                 "reasons": sorted(reasons)}
+
+
+def gpu_id_of(dev) -> str:
+    """nvidia-smi id of a torch device (its UUID when torch exposes it)."""
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    gid = str(dev.index)
+    if getattr(props, "uuid", None) is not None:
+        gid = str(props.uuid)
+        gid = gid if gid.startswith("GPU-") else "GPU-" + gid
+    return gid
 
 
 def dist_setup():
@@ -243,12 +255,7 @@ def timed_leg(args, case, precision: str, world: int, dev, sample_clocks: bool):
     torch.cuda.synchronize()
     sampler = None
     if sample_clocks:
-        props = torch.cuda.get_device_properties(dev)
-        gpu_id = str(dev.index)
-        if getattr(props, "uuid", None) is not None:
-            gpu_id = str(props.uuid)
-            gpu_id = gpu_id if gpu_id.startswith("GPU-") else "GPU-" + gpu_id
-        sampler = ClockSampler(gpu_id)
+        sampler = ClockSampler(gpu_id_of(dev))
         time.sleep(0.3)
     barrier(world)
     torch.cuda.synchronize()
@@ -381,6 +388,136 @@ def run_gks(args, world, rank, local):
         print(json.dumps(out), flush=True)
 
 
+def oracle_batch_sample(cases, steps: int):
+    """The CPU oracle (limiter on) on the six smallest cases of the batch."""
+    from oracle import oracle
+    oracle.build()
+    small = sorted(cases, key=lambda c: c.mesh.n_tri)[:6]
+    t0, tri = time.perf_counter(), 0
+    for c in small:
+        om = oracle.OracleMesh(c.mesh, limiter=1)
+        w = c.w0.copy()
+        for _ in range(steps):
+            if om.step(w).status != 0:
+                raise RuntimeError("oracle step failed")
+        tri += c.mesh.n_tri * steps
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": tri / el, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} oracle steps (limiter on) of each of the 6 smallest cases of the batch "
+                      f"({sum(c.mesh.n_tri for c in small)} triangles), FP64"}
+
+
+def run_batch(args, world, rank, local):
+    """Config 5: 512 independent cases (log-uniform 1e3-2e5 triangles) in one
+    handle, mixed precision, limiter on, every kernel covering all cases."""
+    import numpy as np
+    import torch
+
+    from paper_1802_00704_gb300 import gks
+    from paper_1802_00704_gb300 import inputs as I
+    cases = I.batch_cases(WORKLOADS[args.workload]["n"], workers=min(16, os.cpu_count() or 1))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    T = sum(c.mesh.n_tri for c in cases)
+    F = sum(c.mesh.n_face for c in cases)
+    w0 = np.ascontiguousarray(np.concatenate([c.w0 for c in cases], axis=1))
+    mixed = args.precision == "mixed"
+
+    def leg(prec_mixed: bool, clocks: bool):
+        b = gks.GksMesh.batch([c.mesh for c in cases], precision=gks.MIXED if prec_mixed else gks.FP64,
+                              limiter=1, gmres_m=12, warm_extrap=int(args.warm == "extrap"))
+        w = torch.from_numpy(w0.copy()).to(dev)
+        tune = b.autotune(w, trial_steps=1) if args.tune else None
+        r = b.batch_run(w, max_steps=args.warmup)
+        if r["n_failed"]:
+            raise RuntimeError(f"{r['n_failed']} cases failed in the warm-up")
+        torch.cuda.synchronize()
+        sampler = ClockSampler(gpu_id_of(dev)) if clocks else None
+        if sampler:
+            time.sleep(0.3)
+        barrier(world)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = gks.launch_count()
+        b.profile_begin([gks.PROF_FLUX, gks.PROF_SPMV, gks.PROF_ILU, gks.PROF_ORTH, gks.PROF_UPDATE])
+        ev0.record(torch.cuda.current_stream())
+        r = b.batch_run(w, max_steps=args.steps)
+        ev1.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        prof = b.profile_end()
+        launches = gks.launch_count() - l0
+        barrier(world)
+        ck = sampler.stop() if sampler else None
+        ms = allmax(world, ev0.elapsed_time(ev1))
+        return b, w, r, prof, launches, ck, ms, tune
+
+    b, w, r, prof, launches, clocks, ms, tune = leg(mixed, True)
+    value = world * T * args.steps / (ms / 1e3)
+    # end to end: state copied host -> device and back every step
+    w_host = torch.from_numpy(w0.copy()).pin_memory()
+    w_dev = torch.empty_like(w)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        w_dev.copy_(w_host, non_blocking=True)
+        b.batch_run(w_dev, max_steps=1)
+        w_host.copy_(w_dev, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_value = world * T * args.steps / allmax(world, time.perf_counter() - t0)
+    knobs = {"ilu_sweeps": b.cfg.ilu_sweeps, "warm_extrap": b.cfg.warm_extrap, "inner_rtol": b.cfg.inner_rtol}
+    names = ["flux", "spmv", "ilu", "orth", "update"]
+    classes = {}
+    for q, nm in enumerate(names):
+        ent = {"ms": round(prof["ms"][q], 3), "launch_groups": prof["n"][q]}
+        if nm != "flux" and prof["ms"][q] > 0:
+            by = class_bytes(nm, prof, T, F, args.steps, knobs["ilu_sweeps"], False, mixed, False)
+            gbs = by / (prof["ms"][q] / 1e3) / 1e9
+            ent.update({"bytes": by, "gbs": round(gbs, 1), "frac": round(gbs / HBM_FALLBACK_GBS, 3)})
+        classes[nm] = ent
+    per_launch_ms = prof["ms"][0] / max(prof["n"][0], 1)
+    flop64 = FLUX_MIXED_FP64_FLOP_PER_GP if mixed else FLUX_FP64_FLOP_PER_GP
+    ach = flop64 * 2 * F / (per_launch_ms / 1e3) / 1e12
+    wm = w.cpu().numpy()
+    stat = r["status"]
+    out = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64 (mixed)" if mixed else "f64", "data": "synthetic",
+        "config": {"workload": f"batch of {len(cases)} cases (log-uniform 1e3-2e5 triangles; advection / "
+                               f"Riemann strips), {T} triangles, {F} faces, limiter on, GMRES(12) rtol 1e-12",
+                   "n_tri": T, "n_face": F, "n_cases": len(cases), "precision": args.precision,
+                   "autotuned": bool(args.tune), "knobs": knobs, "failed_cases": int(np.sum(stat != 0)),
+                   "l2": "inputs larger than L2", "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"kernel": "k_face_flux", "launches": prof["n"][0], "avg_ms": per_launch_ms, "bound": "alu",
+                     "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                     "fp64_flop_per_gauss_point": flop64, "traffic": None, "classes": classes,
+                     "work": {"arnoldi_per_step": prof["arnoldi"] / args.steps,
+                              "mean_j": (prof["arnoldi_jsum"] - prof["arnoldi"]) / max(prof["arnoldi"], 1)}},
+        "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": 4 * T * 8, "d2h_bytes_per_step": 4 * T * 8},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    del b
+    if mixed and not args.no_compare:
+        bf, wf, rf, proff, _, _, msf, _ = leg(False, False)
+        wfh = wf.cpu().numpy()
+        area = np.concatenate([0.5 * np.abs(np.cross(c.mesh.nodes[c.mesh.tris[:, 1]] - c.mesh.nodes[c.mesh.tris[:, 0]],
+                                                     c.mesh.nodes[c.mesh.tris[:, 2]] - c.mesh.nodes[c.mesh.tris[:, 0]]))
+                               for c in cases])
+        l1 = np.sum(area * np.abs(wm - wfh), axis=1) / np.sum(area * np.abs(wfh), axis=1)
+        out["fp64"] = {"value": world * T * args.steps / (msf / 1e3), "ms_per_step": msf / args.steps,
+                       "class_ms": {nm: round(proff["ms"][q], 3) for q, nm in enumerate(names)}}
+        out["mixed_vs_fp64_rel_l1"] = [float(x) for x in l1]
+        out["speedup_vs_fp64"] = value / out["fp64"]["value"]
+        del bf
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_batch_sample(cases, args.cpu_steps)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -422,6 +559,8 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif WORKLOADS[args.workload]["kind"] == "batch":
+        run_batch(args, world, rank, local)
     else:
         run_gks(args, world, rank, local)
     if world > 1:

@@ -367,24 +367,34 @@ def cavity_case(n: int = 256, *, seed: int = 1802, gamma: float = 1.4, lid_mach:
     return Case("cavity", mesh, w0, gamma=gamma, mu=mu, meta={"u_lid": u_lid, "re": reynolds})
 
 
-def batch_cases(n_cases: int = 512, *, seed: int = 704, t_min: float = 1e3, t_max: float = 2e5,
-                mesh_seed: int = 1802) -> list[Case]:
-    """Independent cases with log-uniform triangle counts: even index periodic
+def batch_case(c: int, n_cases: int = 512, *, seed: int = 704, t_min: float = 1e3, t_max: float = 2e5,
+               mesh_seed: int = 1802) -> Case:
+    """Case c of the batch: log-uniform triangle count; even index periodic
     advection (wavenumber 1-4, amplitude 0.05-0.2), odd index Riemann strip
     (density and pressure ratios 2-10)."""
     r = uniform01(seed, 4 * n_cases).reshape(n_cases, 4)
-    cases = []
-    for c in range(n_cases):
-        t_target = math.exp(math.log(t_min) + r[c, 0] * (math.log(t_max) - math.log(t_min)))
-        if c % 2 == 0:
-            n = max(3, int(round(math.sqrt(t_target / 2.0))))
-            k = 1 + int(r[c, 1] * 4.0) % 4
-            amp = 0.05 + 0.15 * r[c, 2]
-            cases.append(advection_case(n, seed=mesh_seed + c, k=k, amp=amp))
-        else:
-            nx = max(3, int(round(t_target / 16.0)))
-            rr = 2.0 + 8.0 * r[c, 1]
-            rp = 2.0 + 8.0 * r[c, 2]
-            cases.append(riemann_strip_case(nx, 8, left=(rr, 0.0, 0.0, rp), right=(1.0, 0.0, 0.0, 1.0),
-                                            seed=mesh_seed + c, name="riemann"))
-    return cases
+    t_target = math.exp(math.log(t_min) + r[c, 0] * (math.log(t_max) - math.log(t_min)))
+    if c % 2 == 0:
+        n = max(3, int(round(math.sqrt(t_target / 2.0))))
+        k = 1 + int(r[c, 1] * 4.0) % 4
+        amp = 0.05 + 0.15 * r[c, 2]
+        return advection_case(n, seed=mesh_seed + c, k=k, amp=amp)
+    nx = max(3, int(round(t_target / 16.0)))
+    rr = 2.0 + 8.0 * r[c, 1]
+    rp = 2.0 + 8.0 * r[c, 2]
+    return riemann_strip_case(nx, 8, left=(rr, 0.0, 0.0, rp), right=(1.0, 0.0, 0.0, 1.0), seed=mesh_seed + c,
+                              name="riemann")
+
+
+def batch_cases(n_cases: int = 512, *, seed: int = 704, t_min: float = 1e3, t_max: float = 2e5,
+                mesh_seed: int = 1802, workers: int = 1) -> list[Case]:
+    """All cases of the batch (see batch_case), generated by `workers` spawned
+    processes when workers > 1 (the result does not depend on it)."""
+    kw = dict(n_cases=n_cases, seed=seed, t_min=t_min, t_max=t_max, mesh_seed=mesh_seed)
+    if workers <= 1:
+        return [batch_case(c, **kw) for c in range(n_cases)]
+    import functools
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(functools.partial(batch_case, **kw), range(n_cases), chunksize=4))
