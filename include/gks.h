@@ -111,12 +111,17 @@ typedef struct gks_config {
                               1: with the 2 tau^2 (1 - e^{-t/tau}) term that the exact
                               time integral of Eq. (8) carries                          */
     int32_t limiter;       /* 1: shock detector (Eq. (37)) and DWBAP limiter (Eqs.
-                              (34)-(36)) on the reconstruction before the flux        */
+                              (34)-(36)) on the reconstruction before the flux; 2: the
+                              detector with first order (cell average) in the cells
+                              it flags (robust mode for density ratios near 10; not
+                              in the paper)                                           */
     int32_t basis_fp32;    /* mixed precision only: 1 stores the Krylov basis in FP32
                               (dot products, updates, norms and Givens stay FP64)     */
-    int32_t warm_extrap;   /* 1: start each solve from 2 x_{n-1} - x_{n-2} (linear
-                              extrapolation of the last two solutions) instead of
-                              x_{n-1}; the same tolerance is met, in fewer iterations */
+    int32_t warm_extrap;   /* initial guess of each solve: 0 the last solution x_{n-1};
+                              1 its linear extrapolation 2 x_{n-1} - x_{n-2}; 2 the
+                              quadratic one 3 x_{n-1} - 3 x_{n-2} + x_{n-3} (as many
+                              past solutions as exist); the same tolerance is met,
+                              in fewer iterations when the flow changes smoothly      */
     int32_t reserved[3];   /* must be zero                                             */
     double inner_rtol;     /* mixed precision: an inner FP32 GMRES cycle stops once its
                               residual estimate has dropped by this factor (0 < r < 1,
@@ -277,12 +282,14 @@ GKS_EXPORT gks_status gks_flux(gks_mesh *mesh, const double *w, const double *co
  * returned by gks_cls_reconstruct) in, limited coefficients coef_out (device
  * [4][5][n_tri], may not alias coef) out; flags (device [n_tri], may be NULL)
  * receives 0 for an untouched cell, 1 for a limited one and 2 for a limited
- * cell reset to its average because its limited polynomial still had rho <= 0
- * or p <= 0 at a face Gauss point.  Derivatives are replaced by
+ * cell reset to its average (robust mode, or its limited polynomial still had
+ * rho <= 0 or p <= 0 at a face Gauss point).  A cell is limited when the
+ * detector flags it or its polynomial has rho <= 0 or p <= 0 at a face Gauss
+ * point.  Derivatives are replaced by
  * u_0 tan(sum_j omega_j arctan(u_j / u_0)) over the cell's own and its face
  * neighbours' polynomials at the centroid, omega_j from the distances to the
  * face midpoints and the spread of the neighbour pressures (Eqs. (35)-(36)).
- * Requires a mesh created with gks_config.limiter = 1 (GKS_EINVAL otherwise);
+ * Requires a mesh created with gks_config.limiter = 1 or 2 (GKS_EINVAL otherwise);
  * with it, gks_step, gks_run and gks_batch_run limit every reconstruction
  * before the flux.  Stream-ordered, no synchronisation. */
 GKS_EXPORT gks_status gks_limit(gks_mesh *mesh, const double *w, const double *coef, double *coef_out,
@@ -312,7 +319,7 @@ GKS_EXPORT gks_status gks_point_flux(int64_t n, const double *wl, const double *
 /* Autotuner.  Times trial steps of the handle's own workload (all its cases)
  * for each candidate of the knobs that change the cost of a step but not its
  * result beyond the solver tolerance: ilu_sweeps in {1, 2, 3} (sweep
- * preconditioner only), warm_extrap in {0, 1} and, in mixed precision,
+ * preconditioner only), warm_extrap in {0, 1, 2} and, in mixed precision,
  * inner_rtol in {1e-4, 1e-5, 1e-6}.  Each candidate starts from w (device,
  * [4][n_tri], caller order, not modified) with a cleared warm start, takes
  * 3 untimed steps, then trial_steps (>= 1) steps timed with CUDA events; a

@@ -25,7 +25,8 @@ typedef struct or_params {
     double gmres_rtol;  /* relative residual target                              */
     int    tau2_exact;  /* 1: c4..c6 with the 2 tau^2 (1 - e^{-t/tau}) term       */
     int    slope0_mode; /* 0: interface-equilibrium derivatives = mean of L/R     */
-    int    limiter;     /* 1: shock detector + DWBAP limiter (Sec. III.C)          */
+    int    limiter;     /* 1: shock detector + DWBAP limiter (Sec. III.C); 2: the
+                           detector with first order in limited cells (robust)   */
 } or_params;
 
 /* Boundary tags (same numbering as the input generator). */

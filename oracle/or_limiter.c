@@ -16,9 +16,13 @@
  *    j = 0) to the cell's face midpoints, S(chi) = 1/(sqrt(chi + 1e-8) + 0.05),
  *    chi = std / mean of the neighbours' pressures; second derivatives first,
  *    then first derivatives, all from the unlimited neighbour polynomials;
- *  - safeguard (not in the paper): if the limited polynomial of a flagged
- *    cell still gives rho <= 0 or p <= 0 at one of its face Gauss points, the
- *    cell falls back to its cell average (all coefficients zero).
+ *  - robust mode (limiter = 2, not in the paper): a limited cell keeps its
+ *    cell average only (first order), for contacts with density ratios near
+ *    10, where the DWBAP polynomials let cell averages turn negative;
+ *  - positivity (not in the paper): a cell is also limited when its
+ *    unlimited polynomial gives rho <= 0 or p <= 0 at one of its face Gauss
+ *    points; if the limited polynomial of a limited cell still does, the cell
+ *    falls back to its cell average (all coefficients zero).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -54,6 +58,26 @@ static double detector(const or_mesh *m, const double *w, const double *coef, in
     return s / (J * pow(m->h[i], 0.5 * (m->korder[i] + 1)) * umax);
 }
 
+/* 1 if the polynomial of cell i (coefficients coef) gives rho > 0 and p > 0
+ * at all of its face Gauss points. */
+static int physical_at_gauss_points(const or_mesh *m, const double *w, const double *coef, int64_t i)
+{
+    const double gamma = m->prm.gamma;
+    for (int s = 0; s < 3; ++s) {
+        int f = m->cface[3 * i + s];
+        if (f < 0) continue;
+        for (int g = 0; g < 2; ++g) {
+            double x = m->gx[2 * f + g], y = m->gy[2 * f + g];
+            if (m->face[5 * f + 2] != (int)i) { x -= m->shift[2 * f]; y -= m->shift[2 * f + 1]; }
+            double e[24];
+            or_eval_cell(m, w, coef, (int)i, x, y, e);
+            double p = (gamma - 1.0) * (e[3] - 0.5 * (e[1] * e[1] + e[2] * e[2]) / e[0]);
+            if (!(e[0] > 0.0) || !(p > 0.0)) return 0;
+        }
+    }
+    return 1;
+}
+
 /* Limited coefficients coef_out (same layout as coef) and the detector flags
  * (flag[i] = 1 limited, 2 limited and reset to the average).  Returns the
  * number of flagged cells. */
@@ -67,9 +91,16 @@ int or_limit(const or_mesh *m, const double *w, const double *coef, double *coef
         flag[i] = 0;
         const int J = m->nb_cnt[i];
         if (J == 0) continue;
-        if (detector(m, w, coef, (int)i, 0) < 1.0 && detector(m, w, coef, (int)i, 3) < 1.0) continue;
+        if (detector(m, w, coef, (int)i, 0) < 1.0 && detector(m, w, coef, (int)i, 3) < 1.0 &&
+            physical_at_gauss_points(m, w, coef, i))
+            continue;
         flag[i] = 1;
         ++nflag;
+        if (m->prm.limiter == 2) {
+            flag[i] = 2;
+            for (int q = 0; q < 20; ++q) coef_out[(size_t)q * T + i] = 0.0;
+            continue;
+        }
         /* weights, Eqs. (35)-(36) */
         double fmx[3], fmy[3];
         int nf = 0;
@@ -140,19 +171,7 @@ int or_limit(const or_mesh *m, const double *w, const double *coef, double *coef
             coef_out[((size_t)v * 5 + 1) * T + i] = hi * biased(gy, om, J + 1);
         }
         /* safeguard at the cell's face Gauss points */
-        int bad = 0;
-        for (int s = 0; s < 3 && !bad; ++s) {
-            int f = m->cface[3 * i + s];
-            if (f < 0) continue;
-            for (int g = 0; g < 2; ++g) {
-                double x = m->gx[2 * f + g], y = m->gy[2 * f + g];
-                if (m->face[5 * f + 2] != (int)i) { x -= m->shift[2 * f]; y -= m->shift[2 * f + 1]; }
-                double e[24];
-                or_eval_cell(m, w, coef_out, (int)i, x, y, e);
-                double p = (gamma - 1.0) * (e[3] - 0.5 * (e[1] * e[1] + e[2] * e[2]) / e[0]);
-                if (!(e[0] > 0.0) || !(p > 0.0)) bad = 1;
-            }
-        }
+        const int bad = !physical_at_gauss_points(m, w, coef_out, i);
         if (bad) {
             flag[i] = 2;
             for (int q = 0; q < 20; ++q) coef_out[(size_t)q * T + i] = 0.0;

@@ -55,9 +55,9 @@ gks_status check_config(const gks_config &c)
     bool ok = c.gamma > 1.0 && c.cfl > 0.0 && c.mu >= 0.0 && c.cls_w > 0.0 && c.gmres_m >= 1 &&
               c.gmres_m <= kMaxRestart && c.gmres_maxit >= 1 && c.gmres_rtol > 0.0 &&
               (c.tau2_exact == 0 || c.tau2_exact == 1) && c.ilu_sweeps >= 0 && c.ilu_sweeps <= 16;
-    ok = ok && (c.limiter == 0 || c.limiter == 1);
+    ok = ok && c.limiter >= 0 && c.limiter <= 2;
     ok = ok && (c.basis_fp32 == 0 || (c.basis_fp32 == 1 && c.precision == GKS_MIXED));
-    ok = ok && (c.warm_extrap == 0 || c.warm_extrap == 1);
+    ok = ok && c.warm_extrap >= 0 && c.warm_extrap <= 2;
     ok = ok && c.inner_rtol > 0.0 && c.inner_rtol < 1.0;
     for (int q = 0; q < 3; ++q) ok = ok && c.reserved[q] == 0;
     if (!ok) {

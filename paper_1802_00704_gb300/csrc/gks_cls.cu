@@ -479,18 +479,22 @@ __global__ void k_combine_z(DeviceMesh d, const TZ *__restrict__ Z, const double
     for (int l = 0; l < ND; ++l) x[(v * ND + l) * T + i] += double(acc[l]);
 }
 
-// Warm start of the next solve (cases not done): extrapolate = 1 sets
-// x = 2 x - x_prev; in both cases x_prev takes the old x.
-__global__ void k_warm(DeviceMesh d, double *__restrict__ x, double *__restrict__ xp, const int32_t *__restrict__ done,
-                       int extrapolate)
+// Warm start of the next solve (cases not done) from the last solutions
+// x = s_{n-1}, xp = s_{n-2}, xpp = s_{n-3}: order 0 keeps x, order 1 takes
+// 2 x - xp, order 2 takes 3 x - 3 xp + xpp (polynomial extrapolation in the
+// step index); the history then shifts (xpp = xp, xp = old x).
+__global__ void k_warm(DeviceMesh d, double *__restrict__ x, double *__restrict__ xp, double *__restrict__ xpp,
+                       const int32_t *__restrict__ done, int order)
 {
     const int64_t T = d.T;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= T || done[d.blk_case[blockIdx.x]]) return;
 #pragma unroll 4
     for (int q = 0; q < NX; ++q) {
-        const double a = x[q * T + i];
-        if (extrapolate) x[q * T + i] = 2.0 * a - xp[q * T + i];
+        const double a = x[q * T + i], b = xp[q * T + i];
+        if (order == 2) x[q * T + i] = 3.0 * (a - b) + xpp[q * T + i];
+        else if (order == 1) x[q * T + i] = 2.0 * a - b;
+        xpp[q * T + i] = b;
         xp[q * T + i] = a;
     }
 }
@@ -792,9 +796,10 @@ gks_status cls_solve(gks_mesh *m, cudaStream_t s, int32_t *iters, double *relres
 {
     Work &k = m->wk;
     if (m->cfg.warm_extrap) {
-        // initial guess 2 x_{n-1} - x_{n-2} once two solutions exist, else keep x_{n-1}
+        // extrapolate from as many past solutions as exist (up to the configured order)
+        const int order = (m->cfg.warm_extrap >= 2 && k.nsolve >= 3) ? 2 : (k.nsolve >= 2 ? 1 : 0);
         const unsigned nb = (unsigned)k.nblk;
-        k_warm<<<nb, kBlock, 0, s>>>(m->d, k.x, k.x_prev, k.done, k.nsolve >= 2 ? 1 : 0); note_launch();
+        k_warm<<<nb, kBlock, 0, s>>>(m->d, k.x, k.x_prev, k.x_prev2, k.done, order); note_launch();
         GKS_CUDA(cudaGetLastError());
     }
     gks_status st = k.V32 ? cls_solve_t<float>(m, k.V32, s, iters, relres, converged)

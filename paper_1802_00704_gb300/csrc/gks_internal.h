@@ -88,6 +88,7 @@ struct Work {
     double *w_old = nullptr;         // [4][T]
     double *x = nullptr;             // [20][T] CLS coefficients (warm start)
     double *x_prev = nullptr;        // [20][T] the solution before (extrapolated warm start)
+    double *x_prev2 = nullptr;       // [20][T] the one before that
     int64_t nsolve = 0;              // solves since creation or the last warm-start reset
     double *xl = nullptr;            // [20][T] limited coefficients (limiter on)
     float *x32 = nullptr;            // [20][T] FP32 copy of the coefficients the mixed flux reads

@@ -15,9 +15,13 @@
 //    + 0.05), chi = standard deviation / mean of the neighbours' pressures;
 //    second derivatives (from neighbours with k_j = 2, weights renormalised)
 //    and first derivatives, all from the unlimited polynomials;
-//  - safeguard (not in the paper): a flagged cell whose limited polynomial still
-//    has rho <= 0 or p <= 0 at one of its face Gauss points keeps its cell
-//    average only (all coefficients zero).
+//  - positivity (not in the paper): a cell is also limited when its unlimited
+//    polynomial has rho <= 0 or p <= 0 at one of its face Gauss points; a
+//    limited cell whose polynomial still has one keeps its cell average only
+//    (all coefficients zero);
+//  - robust mode (limiter = 2, not in the paper): a limited cell keeps its
+//    cell average only (first order), for contacts with density ratios near
+//    10, where the DWBAP polynomials let cell averages turn negative.
 //
 // One thread per cell, FP64.  The unlimited coefficients stay in x (the warm
 // start of the next CLS solve); the limited ones are written to a separate
@@ -50,9 +54,34 @@ __device__ __forceinline__ double biased_mean(const double (&u)[4], const double
     return u[0] * tan(acc);
 }
 
+// rho > 0 and p > 0 at all face Gauss points of cell i for the coefficients c.
+__device__ __forceinline__ bool physical_gp(const DeviceMesh &d, const double *__restrict__ w, const double *c,
+                                            int64_t i, double gamma)
+{
+    const int64_t T = d.T, F = d.F;
+    bool ok = true;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        const int32_t cf = d.cf[s * T + i];
+        if (cf < 0) continue;
+        const int64_t f = cf >> 1;
+        const double *g = (cf & 1) ? d.gr : d.gl;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const double dx = g[(2 * k) * F + f], dy = g[(2 * k + 1) * F + f];
+            const double rho = poly_value(d, w, c, i, 0, dx, dy);
+            const double mx = poly_value(d, w, c, i, 1, dx, dy), my = poly_value(d, w, c, i, 2, dx, dy);
+            const double E = poly_value(d, w, c, i, 3, dx, dy);
+            const double p = (gamma - 1.0) * (E - 0.5 * (mx * mx + my * my) / rho);
+            ok = ok && rho > 0.0 && p > 0.0;
+        }
+    }
+    return ok;
+}
+
 __global__ void __launch_bounds__(kBlock) k_limit(const DeviceMesh d, const double *__restrict__ w,
                                                   const double *__restrict__ x, double *xl,
-                                                  int32_t *__restrict__ flag, double gamma)
+                                                  int32_t *__restrict__ flag, double gamma, int robust)
 {
     const int64_t T = d.T, F = d.F;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -86,12 +115,17 @@ __global__ void __launch_bounds__(kBlock) k_limit(const DeviceMesh d, const doub
             m3 = fmax(m3, w[3 * T + j]);
         }
         const double scale = J * pow(hi, 0.5 * (ki + 1));
-        flagged = !(s0 / (scale * m0) < 1.0 && s3 / (scale * m3) < 1.0);
+        flagged = !(s0 / (scale * m0) < 1.0 && s3 / (scale * m3) < 1.0) || !physical_gp(d, w, x, i, gamma);
     }
     if (!flagged) {
 #pragma unroll 4
         for (int q = 0; q < 20; ++q) xl[q * T + i] = x[q * T + i];
         flag[i] = 0;
+        return;
+    }
+    if (robust) {
+        for (int q = 0; q < 20; ++q) xl[q * T + i] = 0.0;
+        flag[i] = 2;
         return;
     }
 
@@ -195,23 +229,7 @@ __global__ void __launch_bounds__(kBlock) k_limit(const DeviceMesh d, const doub
     }
 
     // ---- safeguard at the cell's face Gauss points
-    bool bad = false;
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        const int32_t cf = d.cf[s * T + i];
-        if (cf < 0) continue;
-        const int64_t f = cf >> 1;
-        const double *g = (cf & 1) ? d.gr : d.gl;
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const double dx = g[(2 * k) * F + f], dy = g[(2 * k + 1) * F + f];
-            const double rho = poly_value(d, w, xl, i, 0, dx, dy);
-            const double mx = poly_value(d, w, xl, i, 1, dx, dy), my = poly_value(d, w, xl, i, 2, dx, dy);
-            const double E = poly_value(d, w, xl, i, 3, dx, dy);
-            const double p = (gamma - 1.0) * (E - 0.5 * (mx * mx + my * my) / rho);
-            bad = bad || !(rho > 0.0) || !(p > 0.0);
-        }
-    }
+    const bool bad = !physical_gp(d, w, xl, i, gamma);
     if (bad)
         for (int q = 0; q < 20; ++q) xl[q * T + i] = 0.0;
     flag[i] = bad ? 2 : 1;
@@ -238,7 +256,7 @@ gks_status launch_limiter(gks_mesh *m, const double *w, const double *x, cudaStr
     }
     if (d.T == 0) return GKS_OK;
     const unsigned nb = (unsigned)((d.T + kBlock - 1) / kBlock);
-    k_limit<<<nb, kBlock, 0, s>>>(d, w, x, m->wk.xl, m->wk.lflag, m->cfg.gamma);
+    k_limit<<<nb, kBlock, 0, s>>>(d, w, x, m->wk.xl, m->wk.lflag, m->cfg.gamma, m->cfg.limiter == 2 ? 1 : 0);
     note_launch();
     GKS_CUDA(cudaGetLastError());
     return GKS_OK;

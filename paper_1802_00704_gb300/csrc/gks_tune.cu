@@ -89,7 +89,7 @@ extern "C" gks_status gks_autotune(gks_mesh *m, const double *w, int32_t trial_s
     std::vector<Candidate> cand;
     for (int32_t sw : {1, 2, 3}) {
         if (!sweep && sw != 1) continue;
-        for (int32_t wx : {0, 1})
+        for (int32_t wx : {0, 1, 2})
             for (double eta : {1e-4, 1e-5, 1e-6}) {
                 if (!mixed && eta != 1e-6) continue;
                 cand.push_back({sweep ? sw : before.ilu_sweeps, wx, mixed ? eta : before.inner_rtol});

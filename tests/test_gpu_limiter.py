@@ -1,7 +1,8 @@
 """Parity of the CUDA shock detector and DWBAP limiter (Sec. III.C, Eqs.
 (34)-(38)) with the oracle, and the limited scheme on shock tubes.
 
-Tolerances: from the same input coefficients the flags are equal and the
+Both modes: 1 the paper's DWBAP, 2 the robust mode (first order in the flagged
+cells).  Tolerances: from the same input coefficients the flags are equal and the
 limited coefficients agree within 1e-12 of each variable's largest coefficient
 (the two sides differ only in the rounding of atan, tan, pow and hypot); limited
 FP64 steps agree within 1e-10 relative max after one step and 1e-8 after 40.
@@ -37,6 +38,8 @@ CASES = {
     "lax90x5": lambda: I.riemann_strip_case(90, 5, left=LAX[0], right=LAX[1], seed=7, name="lax"),
     "ratio10_70x6": lambda: I.riemann_strip_case(70, 6, left=(1.0, 0.0, 0.0, 1.0), right=(0.1, 0.0, 0.0, 0.1),
                                                  seed=21, name="ratio10"),
+    "contact10_60x4": lambda: I.riemann_strip_case(60, 4, left=(10.0, 0.0, 0.0, 2.0), right=(1.0, 0.0, 0.0, 1.0),
+                                                   seed=5, name="contact10"),
 }
 
 
@@ -49,23 +52,26 @@ def _coef_err(a, b):
     return np.max(np.abs(a - b), axis=1) / np.maximum(np.max(np.abs(b), axis=1), floor)
 
 
-def _advance_oracle(O, c, n):
-    om = O.OracleMesh(c.mesh, limiter=1)
+def _advance_oracle(O, c, n, mode=1):
+    om = O.OracleMesh(c.mesh, limiter=mode)
     w = c.w0.copy()
     for _ in range(n):
         assert om.step(w).status == 0
     return om, w
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("steps_before", [0, 25])
-def test_limit_kernel_matches_oracle(O, G, name, steps_before):
+def test_limit_kernel_matches_oracle(O, G, name, steps_before, mode):
     c = CASES[name]()
-    om, w = _advance_oracle(O, c, steps_before)
+    # the strong contact is advanced in the robust mode (the plain one does not keep it physical)
+    _, w = _advance_oracle(O, c, steps_before, mode=2 if name == "contact10_60x4" else mode)
+    om = O.OracleMesh(c.mesh, limiter=mode)
     coef, _, _, _ = om.cls_solve(w)
     ref, rflag = om.limit(w, coef)
     assert rflag.sum() > 0
-    gm = G.GksMesh(c.mesh, limiter=1)
+    gm = G.GksMesh(c.mesh, limiter=mode)
     out, flags = gm.limit(dev(w), dev(coef))
     gflag = host(flags)
     assert np.array_equal(gflag, rflag), (np.flatnonzero(gflag != rflag), gflag.sum(), rflag.sum())
@@ -97,8 +103,9 @@ def test_limit_refused_without_limiter_data(G):
 @pytest.mark.parametrize("name", list(CASES))
 def test_limited_steps_match_oracle(O, G, name):
     c = CASES[name]()
-    om = O.OracleMesh(c.mesh, limiter=1)
-    gm = G.GksMesh(c.mesh, limiter=1)
+    mode = 2 if name == "contact10_60x4" else 1
+    om = O.OracleMesh(c.mesh, limiter=mode)
+    gm = G.GksMesh(c.mesh, limiter=mode)
     wo = c.w0.copy()
     wg = dev(c.w0)
     for n in range(40):
@@ -134,15 +141,16 @@ def test_sod_400x8_to_t02_against_exact_solution(O, G, precision):
     assert l1 < 4e-3
 
 
-def test_limited_batch_matches_single_runs(G):
-    cases = [CASES[k]() for k in CASES] + [I.advection_case(10, seed=3)]
-    b = G.GksMesh.batch([c.mesh for c in cases], limiter=1)
+@pytest.mark.parametrize("mode", [1, 2])
+def test_limited_batch_matches_single_runs(G, mode):
+    cases = [CASES[k]() for k in CASES if mode == 2 or k != "contact10_60x4"] + [I.advection_case(10, seed=3)]
+    b = G.GksMesh.batch([c.mesh for c in cases], limiter=mode)
     w = dev(np.ascontiguousarray(np.concatenate([c.w0 for c in cases], axis=1)))
     r = b.batch_run(w, max_steps=6)
     assert r["n_failed"] == 0
     wh, o = host(w), 0
     for c in cases:
-        m = G.GksMesh(c.mesh, limiter=1)
+        m = G.GksMesh(c.mesh, limiter=mode)
         ws = dev(c.w0)
         m.run(ws, max_steps=6)
         assert rel_max(wh[:, o:o + c.mesh.n_tri], host(ws)) <= 1e-13, c.name
