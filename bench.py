@@ -141,6 +141,12 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def tri_area(nodes, tris):
+    p = nodes[tris]
+    return 0.5 * abs((p[:, 1, 0] - p[:, 0, 0]) * (p[:, 2, 1] - p[:, 0, 1]) -
+                     (p[:, 2, 0] - p[:, 0, 0]) * (p[:, 1, 1] - p[:, 0, 1]))
+
+
 def gpu_id_of(dev) -> str:
     """nvidia-smi id of a torch device (its UUID when torch exposes it)."""
     import torch
@@ -371,9 +377,7 @@ def run_gks(args, world, rank, local):
         # the plain FP64 path on the same GPU, same steps, and the distance between the two states
         ref = timed_leg(args, case, "fp64", world, dev, sample_clocks=False)
         wm, wf = main["w"].cpu().numpy(), ref["w"].cpu().numpy()
-        p = case.mesh.nodes[case.mesh.tris]
-        area = 0.5 * np.abs((p[:, 1, 0] - p[:, 0, 0]) * (p[:, 2, 1] - p[:, 0, 1]) -
-                            (p[:, 2, 0] - p[:, 0, 0]) * (p[:, 1, 1] - p[:, 0, 1]))
+        area = tri_area(case.mesh.nodes, case.mesh.tris)
         l1 = np.sum(area * np.abs(wm - wf), axis=1) / np.sum(area * np.abs(wf), axis=1)
         out["fp64"] = {"value": world * T * args.steps / (ref["ms"] / 1e3), "ms_per_step": ref["ms"] / args.steps,
                        "gmres_iters_per_step": ref["info"]["gmres_iters"] / max(ref["info"]["steps"], 1),
@@ -504,9 +508,7 @@ def run_batch(args, world, rank, local):
     if mixed and not args.no_compare:
         bf, wf, rf, proff, _, _, msf, _ = leg(False, False)
         wfh = wf.cpu().numpy()
-        area = np.concatenate([0.5 * np.abs(np.cross(c.mesh.nodes[c.mesh.tris[:, 1]] - c.mesh.nodes[c.mesh.tris[:, 0]],
-                                                     c.mesh.nodes[c.mesh.tris[:, 2]] - c.mesh.nodes[c.mesh.tris[:, 0]]))
-                               for c in cases])
+        area = np.concatenate([tri_area(c.mesh.nodes, c.mesh.tris) for c in cases])
         l1 = np.sum(area * np.abs(wm - wfh), axis=1) / np.sum(area * np.abs(wfh), axis=1)
         out["fp64"] = {"value": world * T * args.steps / (msf / 1e3), "ms_per_step": msf / args.steps,
                        "class_ms": {nm: round(proff["ms"][q], 3) for q, nm in enumerate(names)}}

@@ -122,7 +122,10 @@ typedef struct gks_config {
                               quadratic one 3 x_{n-1} - 3 x_{n-2} + x_{n-3} (as many
                               past solutions as exist); the same tolerance is met,
                               in fewer iterations when the flow changes smoothly      */
-    int32_t reserved[3];   /* must be zero                                             */
+    int32_t second_order;  /* 1: second-order variant, k_i = 1 (linear CLS
+                              reconstruction) for every cell (the paper's second- vs
+                              third-order comparison, Sec. IV)                        */
+    int32_t reserved[2];   /* must be zero                                             */
     double inner_rtol;     /* mixed precision: an inner FP32 GMRES cycle stops once its
                               residual estimate has dropped by this factor (0 < r < 1,
                               default 1e-6); the next FP64 residual then restarts it   */

@@ -55,7 +55,7 @@ int or_build_geometry(or_mesh *m)
         }
         m->mxx[i] = sxx / 3.0; m->mxy[i] = sxy / 3.0; m->myy[i] = syy / 3.0;
         m->cface[3 * i] = m->cface[3 * i + 1] = m->cface[3 * i + 2] = -1;
-        m->korder[i] = 2;
+        m->korder[i] = m->prm.second_order ? 1 : 2;   /* second-order variant: linear everywhere */
     }
     for (int64_t f = 0; f < F; ++f) {
         const int *fc = &m->face[5 * f];

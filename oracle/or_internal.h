@@ -27,6 +27,7 @@ typedef struct or_params {
     int    slope0_mode; /* 0: interface-equilibrium derivatives = mean of L/R     */
     int    limiter;     /* 1: shock detector + DWBAP limiter (Sec. III.C); 2: the
                            detector with first order in limited cells (robust)   */
+    int    second_order; /* 1: k_i = 1 for every cell (linear CLS reconstruction) */
 } or_params;
 
 /* Boundary tags (same numbering as the input generator). */

@@ -59,7 +59,8 @@ gks_status check_config(const gks_config &c)
     ok = ok && (c.basis_fp32 == 0 || (c.basis_fp32 == 1 && c.precision == GKS_MIXED));
     ok = ok && c.warm_extrap >= 0 && c.warm_extrap <= 2;
     ok = ok && c.inner_rtol > 0.0 && c.inner_rtol < 1.0;
-    for (int q = 0; q < 3; ++q) ok = ok && c.reserved[q] == 0;
+    ok = ok && (c.second_order == 0 || c.second_order == 1);
+    for (int q = 0; q < 2; ++q) ok = ok && c.reserved[q] == 0;
     if (!ok) {
         set_error("invalid gks_config");
         return GKS_EINVAL;

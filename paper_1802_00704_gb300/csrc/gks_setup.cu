@@ -199,7 +199,7 @@ struct HostCase {
 
 // Geometry, boundary order reduction (Eq. (28)), RCM order, CLS blocks
 // (Eq. (29)), block ILU(0) factors and levels of one case.
-gks_status build_case(const CaseIn &in, double w, HostCase &hc)
+gks_status build_case(const CaseIn &in, double w, int second_order, HostCase &hc)
 {
     const double *nodes = in.nodes, *face_shift = in.face_shift, *bc_state = in.bc_state;
     const int32_t *tris = in.tris, *faces = in.faces;
@@ -242,7 +242,7 @@ gks_status build_case(const CaseIn &in, double w, HostCase &hc)
             c.sxy += dx * dy / 12.0;
             c.syy += dy * dy / 12.0;
         }
-        c.k = 2;
+        c.k = second_order ? 1 : 2;     // the second-order variant is linear everywhere
         c.nf = 0;
         c.face[0] = c.face[1] = c.face[2] = -1;
     }
@@ -540,7 +540,7 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
         unsigned nt = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), (unsigned)n_cases));
         auto work = [&]() {
             for (int32_t c; (c = next.fetch_add(1)) < n_cases;) {
-                st[c] = build_case(cases[c], cfg.cls_w, hcs[c]);
+                st[c] = build_case(cases[c], cfg.cls_w, cfg.second_order, hcs[c]);
                 if (st[c] != GKS_OK) {
                     msg[c] = last_error();
                     int expect = -1;

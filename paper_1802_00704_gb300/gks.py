@@ -41,7 +41,8 @@ class Config(C.Structure):
                 ("gmres_m", C.c_int32), ("gmres_maxit", C.c_int32), ("gmres_rtol", C.c_double),
                 ("precision", C.c_int32), ("precond", C.c_int32), ("ilu_sweeps", C.c_int32),
                 ("tau2_exact", C.c_int32), ("limiter", C.c_int32),
-                ("basis_fp32", C.c_int32), ("warm_extrap", C.c_int32), ("reserved", C.c_int32 * 3),
+                ("basis_fp32", C.c_int32), ("warm_extrap", C.c_int32), ("second_order", C.c_int32),
+                ("reserved", C.c_int32 * 2),
                 ("inner_rtol", C.c_double)]
 
 

@@ -367,6 +367,22 @@ def cavity_case(n: int = 256, *, seed: int = 1802, gamma: float = 1.4, lid_mach:
     return Case("cavity", mesh, w0, gamma=gamma, mu=mu, meta={"u_lid": u_lid, "re": reynolds})
 
 
+def acoustic_pulse_case(n: int, *, seed: int = 1802, eps: float = 0.01, half_width: float = 0.04,
+                        gamma: float = 1.4) -> Case:
+    """Acoustic pressure pulse of Sec. IV (Eq. (45)): unit square (periodic; the
+    pulse stays far from the sides for t <= 0.2), rho = 1, u = v = 0,
+    p = 1 + eps exp(-alpha eta^2), eta = |x - (0.5, 0.5)|, alpha = ln 2 / half_width^2."""
+    alpha = math.log(2.0) / half_width ** 2
+    mesh = split_quad_mesh(n, n, 1.0, 1.0, seed=seed, periodic_x=True, periodic_y=True)
+
+    def fn(x, y):
+        p = 1.0 + eps * np.exp(-alpha * ((x - 0.5) ** 2 + (y - 0.5) ** 2))
+        return prim_to_cons(np.ones_like(x), np.zeros_like(x), np.zeros_like(x), p, gamma)
+
+    return Case("acoustic_pulse", mesh, cell_average(mesh, fn), gamma=gamma,
+                meta={"eps": eps, "alpha": alpha, "x0": 0.5, "y0": 0.5})
+
+
 def batch_case(c: int, n_cases: int = 512, *, seed: int = 704, t_min: float = 1e3, t_max: float = 2e5,
                mesh_seed: int = 1802) -> Case:
     """Case c of the batch: log-uniform triangle count; even index periodic

@@ -1,0 +1,42 @@
+"""Exact (linear acoustics) pressure of the Gaussian pulse of Sec. IV (Eq. (46)):
+p(eta, t) = p_inf + eps/(2 alpha) int_0^inf exp(-xi^2/(4 alpha)) cos(c xi t) J0(xi eta) xi dxi,
+evaluated by Gauss-Legendre quadrature on [0, xi_max] with xi_max where the
+Gaussian factor is below 1e-30.  Test helper."""
+import math
+
+import numpy as np
+from scipy.special import j0
+
+
+def pulse_pressure(eta, t, *, eps=0.01, alpha=math.log(2.0) / 0.04 ** 2, c=math.sqrt(1.4), p_inf=1.0, nodes=4000):
+    eta = np.asarray(eta, dtype=np.float64)
+    xi_max = math.sqrt(4.0 * alpha * 69.1)          # exp(-xi^2/(4 alpha)) = 1e-30
+    x, w = np.polynomial.legendre.leggauss(nodes)
+    xi = 0.5 * xi_max * (x + 1.0)
+    wq = 0.5 * xi_max * w * np.exp(-xi ** 2 / (4.0 * alpha)) * np.cos(c * xi * t) * xi
+    out = np.empty(eta.size)
+    flat = eta.ravel()
+    for s in range(0, flat.size, 2048):
+        blk = flat[s:s + 2048]
+        out[s:s + blk.size] = j0(np.outer(blk, xi)) @ wq
+    return p_inf + eps / (2.0 * alpha) * out.reshape(eta.shape)
+
+
+# degree-5 seven-point rule on the triangle (Dunavant 1985): barycentric points, weights
+_BARY = np.array([[1 / 3, 1 / 3, 1 / 3],
+                  [0.059715871789770, 0.470142064105115, 0.470142064105115],
+                  [0.470142064105115, 0.059715871789770, 0.470142064105115],
+                  [0.470142064105115, 0.470142064105115, 0.059715871789770],
+                  [0.797426985353087, 0.101286507323456, 0.101286507323456],
+                  [0.101286507323456, 0.797426985353087, 0.101286507323456],
+                  [0.101286507323456, 0.101286507323456, 0.797426985353087]])
+_W = np.array([0.225, 0.132394152788506, 0.132394152788506, 0.132394152788506,
+               0.125939180544827, 0.125939180544827, 0.125939180544827])
+
+
+def pulse_pressure_cell_average(nodes, tris, t, x0=0.5, y0=0.5, **kw):
+    """Cell averages of the exact pressure over each triangle (7-point rule)."""
+    p = nodes[tris]                                   # (T, 3, 2)
+    pts = np.einsum("qk,tkd->tqd", _BARY, p)          # (T, 7, 2)
+    eta = np.hypot(pts[..., 0] - x0, pts[..., 1] - y0)
+    return pulse_pressure(eta, t, **kw) @ _W

@@ -65,3 +65,58 @@ def test_fullsize_sampled_fluxes_and_balance(big):
     out = fl[:, bnd].sum(axis=1)
     tot = (np.abs(c.w0) * area).sum(axis=1)
     assert np.all(np.abs(d_tot + out) <= 1e-12 * tot), (d_tot, out)
+
+
+def test_fullsize_mixed_path_as_benchmarked(big):
+    """The mixed path with the knobs the benchmark's tuner picks (2 sweeps,
+    quadratic warm start, inner tolerance 1e-4): 4 steps stay within 1e-8
+    relative L1 of the FP64 path, and sampled mixed face fluxes agree with the
+    oracle to 1e-7 of the largest flux."""
+    c, om, g, G = big
+    area = om.cell_geometry()["area"]
+    mx = G.GksMesh(c.mesh, precision=G.MIXED, ilu_sweeps=2, warm_extrap=2, inner_rtol=1e-4)
+    g.reset_warm_start()
+    wm, wf = dev(c.w0), dev(c.w0)
+    for _ in range(4):
+        dt = g.cfl_dt(wf)
+        assert mx.step(wm, dt)["status"] == 0
+        assert g.step(wf, dt)["status"] == 0
+    a, b = host(wm), host(wf)
+    l1 = np.sum(area * np.abs(a - b), axis=1) / np.sum(area * np.abs(b), axis=1)
+    assert np.all(l1 <= 1e-8), l1
+    coef, _ = mx.cls_reconstruct(dev(c.w0))
+    dt = g.cfl_dt(dev(c.w0))
+    fl = host(mx.flux(dev(c.w0), coef, dt)[0])
+    ids = np.random.default_rng(11).integers(0, c.mesh.n_face, 2000)
+    ref = om.face_flux_subset(c.w0, host(coef), dt, ids)
+    scale = np.max(np.abs(fl), axis=1, keepdims=True)
+    assert np.all(np.abs(fl[:, ids] - ref) <= 1e-7 * scale)
+
+
+def test_config5_batch_sampled_against_oracle():
+    """The 512-case batch (19.2M triangles, log-uniform 1e3-2e5 per case,
+    advection and Riemann strips with ratios 2-10) in the benchmark's launch
+    configuration (mixed, robust limiter, GMRES(12)): 3 steps of the whole batch,
+    every case physical, and the three smallest cases equal the oracle's own
+    steps to 1e-8 relative L1."""
+    from oracle import oracle
+    from paper_1802_00704_gb300 import build, gks
+    oracle.build()
+    build.build()
+    cases = I.batch_cases(512, workers=16)
+    b = gks.GksMesh.batch([c.mesh for c in cases], precision=gks.MIXED, limiter=2, gmres_m=12)
+    w = dev(np.ascontiguousarray(np.concatenate([c.w0 for c in cases], axis=1)))
+    r = b.batch_run(w, max_steps=3)
+    assert r["n_failed"] == 0 and r["steps"] == 3
+    wh = host(w)
+    offs = np.concatenate([[0], np.cumsum([c.mesh.n_tri for c in cases])])
+    for q in np.argsort([c.mesh.n_tri for c in cases])[:3]:
+        c = cases[q]
+        om = oracle.OracleMesh(c.mesh, limiter=2)
+        wo = c.w0.copy()
+        for _ in range(3):
+            assert om.step(wo).status == 0
+        area = om.cell_geometry()["area"]
+        got = wh[:, offs[q]:offs[q + 1]]
+        l1 = np.sum(area * np.abs(got - wo), axis=1) / np.sum(area * np.abs(wo), axis=1)
+        assert np.all(l1 <= 1e-8), (q, l1)

@@ -125,3 +125,34 @@ def test_sod_without_limiter_reports_nonphysical_state(oracle_mod):
     om = oracle_mod.OracleMesh(c.mesh)
     w = c.w0.copy()
     assert om.step(w).status == 1
+
+
+def test_acoustic_pulse_third_vs_second_order(oracle_mod):
+    """Acoustic pressure pulse (Sec. IV): the error against the exact linear
+    acoustics solution (Hankel integral, checked at t = 0 below) is smaller for
+    the third-order scheme and falls faster under refinement than for the
+    second-order variant (k_i = 1 everywhere)."""
+    import math
+    from tests.acoustic_exact import pulse_pressure, pulse_pressure_cell_average
+    eta = np.linspace(0.0, 0.4, 9)
+    alpha = math.log(2.0) / 0.04 ** 2
+    assert np.max(np.abs(pulse_pressure(eta, 0.0) - (1.0 + 0.01 * np.exp(-alpha * eta ** 2)))) < 1e-13
+    tend = 0.05
+
+    def err(n, second):
+        c = I.acoustic_pulse_case(n)
+        om = oracle_mod.OracleMesh(c.mesh, second_order=second)
+        w, t = c.w0.copy(), 0.0
+        while t < tend - 1e-14:
+            dt = min(om.cfl_dt(w), tend - t)
+            assert om.step(w, dt).status == 0
+            t += dt
+        area = om.cell_geometry()["area"]
+        p = 0.4 * (w[3] - 0.5 * (w[1] ** 2 + w[2] ** 2) / w[0])
+        ex = pulse_pressure_cell_average(c.mesh.nodes, c.mesh.tris, tend)
+        return np.sum(area * np.abs(p - ex)) / area.sum()
+
+    e3 = [err(n, 0) for n in (20, 40)]
+    e2 = [err(n, 1) for n in (20, 40)]
+    r3, r2 = math.log2(e3[0] / e3[1]), math.log2(e2[0] / e2[1])
+    assert e3[1] < e2[1] and r3 > 2.1 and r3 > r2 + 0.4, (e3, e2, r3, r2)
