@@ -3,7 +3,10 @@ pulse of Sec. IV on the GPU: parity of the second-order variant with the oracle
 (1e-10 relative max after one step, 1e-8 after 20), and the third- against the
 second-order scheme on the pulse, measured against the exact linear-acoustics
 solution (cell averages of the Hankel integral) on 40^2, 80^2 and 160^2
-split-quad meshes."""
+split-quad meshes.  The convergence test uses the amplitude 1e-4 instead of the
+paper's 0.01: the Euler solution departs from linear acoustics by O(eps^2),
+which at 0.01 is a floor (about 3.5e-7 in L1) that the third-order scheme
+reaches at 160^2."""
 import math
 
 import numpy as np
@@ -47,8 +50,8 @@ def test_second_order_variant_matches_oracle(O, G, name):
     assert np.all(rel_max(host(wg), wo, axis=1) <= 1e-8)
 
 
-def _pulse_error(G, n, second, precision, tend=0.05):
-    c = I.acoustic_pulse_case(n)
+def _pulse_error(G, n, second, precision, tend=0.05, eps=1e-4):
+    c = I.acoustic_pulse_case(n, eps=eps)
     m = G.GksMesh(c.mesh, second_order=second, precision=G.MIXED if precision == "mixed" else G.FP64)
     w = dev(c.w0)
     info = m.run(w, t_final=tend, max_steps=100000)
@@ -59,7 +62,7 @@ def _pulse_error(G, n, second, precision, tend=0.05):
     q = nodes[tris]
     a = 0.5 * np.abs((q[:, 1, 0] - q[:, 0, 0]) * (q[:, 2, 1] - q[:, 0, 1]) -
                      (q[:, 2, 0] - q[:, 0, 0]) * (q[:, 1, 1] - q[:, 0, 1]))
-    ex = pulse_pressure_cell_average(nodes, tris, tend)
+    ex = pulse_pressure_cell_average(nodes, tris, tend, eps=eps)
     return np.sum(a * np.abs(p - ex)) / a.sum()
 
 
