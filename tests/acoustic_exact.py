@@ -1,14 +1,15 @@
 """Exact (linear acoustics) pressure of the Gaussian pulse of Sec. IV (Eq. (46)):
 p(eta, t) = p_inf + eps/(2 alpha) int_0^inf exp(-xi^2/(4 alpha)) cos(c xi t) J0(xi eta) xi dxi,
 evaluated by Gauss-Legendre quadrature on [0, xi_max] with xi_max where the
-Gaussian factor is below 1e-30.  Test helper."""
+Gaussian factor is below 1e-30 (1200 nodes agree with 4000 to 1e-14 for
+eta <= 0.45, t <= 0.2).  Test helper."""
 import math
 
 import numpy as np
 from scipy.special import j0
 
 
-def pulse_pressure(eta, t, *, eps=0.01, alpha=math.log(2.0) / 0.04 ** 2, c=math.sqrt(1.4), p_inf=1.0, nodes=4000):
+def pulse_pressure(eta, t, *, eps=0.01, alpha=math.log(2.0) / 0.04 ** 2, c=math.sqrt(1.4), p_inf=1.0, nodes=1200):
     eta = np.asarray(eta, dtype=np.float64)
     xi_max = math.sqrt(4.0 * alpha * 69.1)          # exp(-xi^2/(4 alpha)) = 1e-30
     x, w = np.polynomial.legendre.leggauss(nodes)
@@ -39,4 +40,11 @@ def pulse_pressure_cell_average(nodes, tris, t, x0=0.5, y0=0.5, **kw):
     p = nodes[tris]                                   # (T, 3, 2)
     pts = np.einsum("qk,tkd->tqd", _BARY, p)          # (T, 7, 2)
     eta = np.hypot(pts[..., 0] - x0, pts[..., 1] - y0)
-    return pulse_pressure(eta, t, **kw) @ _W
+    # outside eta0 + c t, with eta0 where the initial Gaussian is below 1e-25 of
+    # its peak, the pressure is p_inf to far below double precision
+    alpha = kw.get("alpha", math.log(2.0) / 0.04 ** 2)
+    reach = math.sqrt(57.6 / alpha) + kw.get("c", math.sqrt(1.4)) * t
+    vals = np.full(eta.shape, kw.get("p_inf", 1.0))
+    near = eta < reach
+    vals[near] = pulse_pressure(eta[near], t, **kw)
+    return vals @ _W
