@@ -60,7 +60,8 @@ gks_status check_config(const gks_config &c)
     ok = ok && c.warm_extrap >= 0 && c.warm_extrap <= 2;
     ok = ok && c.inner_rtol > 0.0 && c.inner_rtol < 1.0;
     ok = ok && (c.second_order == 0 || c.second_order == 1);
-    for (int q = 0; q < 2; ++q) ok = ok && c.reserved[q] == 0;
+    ok = ok && (c.no_graphs == 0 || c.no_graphs == 1);
+    for (int q = 0; q < 1; ++q) ok = ok && c.reserved[q] == 0;
     if (!ok) {
         set_error("invalid gks_config");
         return GKS_EINVAL;

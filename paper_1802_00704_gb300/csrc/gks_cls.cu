@@ -645,11 +645,84 @@ gks_status precond32(gks_mesh *m, const TR *src, float *dst, cudaStream_t s)
                                        m->wk.r32, s);
 }
 
-gks_status read_flags(gks_mesh *m, cudaStream_t s)
+// Any active / any running system into the pinned host flags (no synchronisation).
+gks_status enqueue_flags(gks_mesh *m, cudaStream_t s)
 {
     k_any<<<1, kBlock, 0, s>>>(m->wk.ctl, m->wk.ns, m->wk.flags);
     note_launch();
     GKS_CUDA(cudaMemcpyAsync(m->wk.h_flags, m->wk.flags, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, s));
+    return GKS_OK;
+}
+
+// Graphs are used unless disabled or the profiler (events between kernels) is on;
+// a change of a knob baked into the captured kernel arguments drops them.
+bool prepare_graphs(gks_mesh *m)
+{
+    if (m->cfg.no_graphs || m->prof.mask) return false;
+    if (!m->graphs) m->graphs = new SolveGraphs;
+    SolveGraphs &g = *m->graphs;
+    if (g.disabled) return false;
+    const gks_config &c = m->cfg;
+    if (g.sweeps != c.ilu_sweeps || g.precond != c.precond || g.maxit != c.gmres_maxit || g.eta != c.inner_rtol ||
+        g.rtol != c.gmres_rtol || (int)g.iter.size() != m->wk.m) {
+        destroy_graph_execs(&g);
+        g.sweeps = c.ilu_sweeps;
+        g.precond = c.precond;
+        g.maxit = c.gmres_maxit;
+        g.eta = c.inner_rtol;
+        g.rtol = c.gmres_rtol;
+        g.iter.assign(m->wk.m, nullptr);
+        g.iter_launches.assign(m->wk.m, 0);
+    }
+    return true;
+}
+
+// Capture enq(stream) into *exec on the private stream; *nl = kernels captured.
+template <typename F>
+gks_status capture_part(gks_mesh *m, cudaGraphExec_t *exec, int64_t *nl, F &&enq)
+{
+    SolveGraphs &g = *m->graphs;
+    if (!g.cap) GKS_CUDA(cudaStreamCreateWithFlags(&g.cap, cudaStreamNonBlocking));
+    const int64_t l0 = g_launches.load();
+    GKS_CUDA(cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeThreadLocal));
+    const gks_status st = enq(g.cap);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(g.cap, &graph);
+    const int64_t n = g_launches.load() - l0;
+    g_launches.fetch_sub(n, std::memory_order_relaxed);   // captured, not run
+    if (st != GKS_OK || e != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return st != GKS_OK ? st : GKS_ECUDA;
+    }
+    e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        *exec = nullptr;
+        cudaGetLastError();
+        return GKS_ECUDA;
+    }
+    *nl = n;
+    return GKS_OK;
+}
+
+// Run one part of the solve on s and wait for its host flags: a replay of its
+// graph (captured on first use), or the launches themselves.
+template <typename F>
+gks_status run_part(gks_mesh *m, bool use_graph, cudaGraphExec_t *exec, int64_t *nl, cudaStream_t s, F &&enq)
+{
+    use_graph = use_graph && !m->graphs->disabled;
+    if (use_graph && !*exec && capture_part(m, exec, nl, enq) != GKS_OK) {
+        m->graphs->disabled = true;                   // fall back to direct launches for good
+        use_graph = false;
+    }
+    if (use_graph) {
+        GKS_CUDA(cudaGraphLaunch(*exec, s));
+        g_launches.fetch_add(*nl, std::memory_order_relaxed);
+    } else {
+        const gks_status st = enq(s);
+        if (st != GKS_OK) return st;
+    }
     GKS_CUDA(cudaStreamSynchronize(s));
     return GKS_OK;
 }
@@ -696,81 +769,105 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
     const double eta = mixed ? m->cfg.inner_rtol : 0.0;
     gks_status st;
 
-    k_rhs<<<nb, kBlock, 0, s>>>(d, k.w, k.b); note_launch();
-    // residual r = b - K x, written straight into the basis slot V_0 (v_0 = V_0 / beta)
-    k_spmv<double, double, TB><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, V, 1, k.b, k.part, ps);
-    note_launch();
-    m->prof.residuals += 1;
-    k_reduce<<<dim3(2, ns), kReduceThreads, 0, s>>>(k.part, d.case_blk, ps, k.hcol, ps, 0); note_launch();
-    k_start<<<sblocks(ns), 128, 0, s>>>(k.hcol, ps, k.bnorm, k.beta, k.vn, mm, k.ctl, ns, k.done, rtol, maxit, 1);
-    note_launch();
-    k_zero_trivial<<<nb, kBlock, 0, s>>>(d, k.x, k.bnorm); note_launch();
-    GKS_CUDA(cudaGetLastError());
-    if ((st = read_flags(m, s)) != GKS_OK) return st;
+    // the three fixed launch sequences; each ends with the flags for the host
+    auto start_part = [&](cudaStream_t q) -> gks_status {
+        k_rhs<<<nb, kBlock, 0, q>>>(d, k.w, k.b); note_launch();
+        // residual r = b - K x, written straight into the basis slot V_0 (v_0 = V_0 / beta)
+        k_spmv<double, double, TB><<<nb, kBlock, 0, q>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, V, 1, k.b, k.part, ps);
+        note_launch();
+        k_reduce<<<dim3(2, ns), kReduceThreads, 0, q>>>(k.part, d.case_blk, ps, k.hcol, ps, 0); note_launch();
+        k_start<<<sblocks(ns), 128, 0, q>>>(k.hcol, ps, k.bnorm, k.beta, k.vn, mm, k.ctl, ns, k.done, rtol, maxit,
+                                             1);
+        note_launch();
+        k_zero_trivial<<<nb, kBlock, 0, q>>>(d, k.x, k.bnorm); note_launch();
+        k_init_g<<<sblocks(ns * (mm + 1)), 128, 0, q>>>(k.g, mm, k.beta, k.ctl, ns); note_launch();
+        GKS_CUDA(cudaGetLastError());
+        return enqueue_flags(m, q);
+    };
+    auto iter_part = [&](cudaStream_t q, int j) -> gks_status {
+        TB *vj = V + j * vs, *vj1 = V + (j + 1) * vs;
+        gks_status st;
+        int slot = prof_start(m, kProfIlu, q);
+        // Z_j = M^{-1} V_j, kept for the update of x at the end of the cycle
+        if ((st = mixed ? precond32(m, vj, k.Z32 + j * vs, q) : precond(m, vj, k.Z + j * vs, q)) != GKS_OK)
+            return st;
+        prof_stop(m, slot, q);
+        slot = prof_start(m, kProfSpmv, q);
+        if (mixed)
+            k_spmv<float, float, TB><<<nb, kBlock, 0, q>>>(d, d.D32, d.alpha32, d.ex32, d.ey32, k.Z32 + j * vs, vj1,
+                                                           0, nullptr, nullptr, 0);
+        else
+            k_spmv<double, double, TB><<<nb, kBlock, 0, q>>>(d, d.D, d.alpha, d.ex, d.ey, k.Z + j * vs, vj1, 0,
+                                                             nullptr, nullptr, 0);
+        note_launch();
+        prof_stop(m, slot, q);
+        slot = prof_start(m, kProfOrth, q);
+        // classical Gram-Schmidt: twice in FP64 mode; once in the mixed mode, whose
+        // cycles only reduce the residual by inner_rtol before an FP64 restart
+        if ((st = dots<TB>(m, V, vj1, j, k.part, ps, q)) != GKS_OK) return st;
+        k_reduce<<<dim3(j + 1, ns), kReduceThreads, 0, q>>>(k.part, d.case_blk, ps, k.hcol, ps, 0, k.vn, mm + 1,
+                                                             k.hco, ps);
+        note_launch();
+        k_orth_update<TB><<<nb, kBlock, 0, q>>>(d, V, vj1, j, k.hco, ps, k.ctl, ns, k.part, ps, mixed ? 1 : 0);
+        note_launch();
+        if (!mixed) {
+            if ((st = dots<TB>(m, V, vj1, j, k.part, ps, q)) != GKS_OK) return st;
+            k_reduce<<<dim3(j + 1, ns), kReduceThreads, 0, q>>>(k.part, d.case_blk, ps, k.y, mm, 0, k.vn, mm + 1,
+                                                                 k.hco, ps);
+            note_launch();
+            k_orth_update<TB><<<nb, kBlock, 0, q>>>(d, V, vj1, j, k.hco, ps, k.ctl, ns, k.part, ps, 1); note_launch();
+            k_hadd<<<sblocks(ns * (j + 1)), 128, 0, q>>>(k.hcol, ps, k.y, mm, j, ns); note_launch();
+        }
+        k_reduce<<<dim3(1, ns), kReduceThreads, 0, q>>>(k.part, d.case_blk, ps, k.hcol + j + 1, ps, 2);
+        note_launch();
+        prof_stop(m, slot, q);
+        k_givens<<<sblocks(ns), 128, 0, q>>>(j, mm, k.hcol, ps, k.vn, k.H, k.cs, k.sn, k.g, k.ctl, ns, k.bnorm,
+                                              k.beta, rtol, eta, maxit);
+        note_launch();
+        GKS_CUDA(cudaGetLastError());
+        return enqueue_flags(m, q);
+    };
+    auto restart_part = [&](cudaStream_t q) -> gks_status {
+        k_backsolve<<<sblocks(ns), 128, 0, q>>>(mm, k.H, k.g, k.y, k.ctl, ns); note_launch();
+        k_scale_y<<<sblocks(ns), 128, 0, q>>>(mm, k.y, k.vn, k.ctl, ns); note_launch();
+        if (mixed)
+            k_combine_z<float><<<dim3(nb, NV), kBlock, 0, q>>>(d, k.Z32, k.y, mm, k.ctl, ns, k.x);
+        else
+            k_combine_z<double><<<dim3(nb, NV), kBlock, 0, q>>>(d, k.Z, k.y, mm, k.ctl, ns, k.x);
+        note_launch();
+        k_spmv<double, double, TB><<<nb, kBlock, 0, q>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, V, 2, k.b, k.part, ps);
+        note_launch();
+        k_reduce<<<dim3(1, ns), kReduceThreads, 0, q>>>(k.part, d.case_blk, ps, k.hcol, ps, 0); note_launch();
+        k_start<<<sblocks(ns), 128, 0, q>>>(k.hcol, ps, k.bnorm, k.beta, k.vn, mm, k.ctl, ns, k.done, rtol, maxit,
+                                             0);
+        note_launch();
+        k_init_g<<<sblocks(ns * (mm + 1)), 128, 0, q>>>(k.g, mm, k.beta, k.ctl, ns); note_launch();
+        GKS_CUDA(cudaGetLastError());
+        return enqueue_flags(m, q);
+    };
 
+    const bool use_graph = prepare_graphs(m);
+    SolveGraphs *G = use_graph ? m->graphs : nullptr;
+    cudaGraphExec_t none = nullptr;
+    int64_t none_n = 0;
+    if ((st = run_part(m, use_graph, G ? &G->start : &none, G ? &G->start_launches : &none_n, s, start_part)) !=
+        GKS_OK)
+        return st;
+    m->prof.residuals += 1;
     while (k.h_flags[0]) {
-        k_init_g<<<sblocks(ns * (mm + 1)), 128, 0, s>>>(k.g, mm, k.beta, k.ctl, ns); note_launch();
         for (int j = 0; j < mm; ++j) {
-            TB *vj = V + j * vs, *vj1 = V + (j + 1) * vs;
-            int slot = prof_start(m, kProfIlu, s);
-            // Z_j = M^{-1} V_j, kept for the update of x at the end of the cycle
-            if ((st = mixed ? precond32(m, vj, k.Z32 + j * vs, s) : precond(m, vj, k.Z + j * vs, s)) != GKS_OK)
-                return st;
-            prof_stop(m, slot, s);
             m->prof.precond += 1;
             m->prof.arnoldi += 1;
             m->prof.arnoldi_jsum += j + 1;
-            slot = prof_start(m, kProfSpmv, s);
-            if (mixed)
-                k_spmv<float, float, TB><<<nb, kBlock, 0, s>>>(d, d.D32, d.alpha32, d.ex32, d.ey32, k.Z32 + j * vs,
-                                                               vj1, 0, nullptr, nullptr, 0);
-            else
-                k_spmv<double, double, TB><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.Z + j * vs, vj1, 0,
-                                                                 nullptr, nullptr, 0);
-            note_launch();
-            prof_stop(m, slot, s);
-            slot = prof_start(m, kProfOrth, s);
-            // classical Gram-Schmidt: twice in FP64 mode; once in the mixed mode, whose
-            // cycles only reduce the residual by inner_rtol before an FP64 restart
-            if ((st = dots<TB>(m, V, vj1, j, k.part, ps, s)) != GKS_OK) return st;
-            k_reduce<<<dim3(j + 1, ns), kReduceThreads, 0, s>>>(k.part, d.case_blk, ps, k.hcol, ps, 0, k.vn, mm + 1,
-                                                                 k.hco, ps);
-            note_launch();
-            k_orth_update<TB><<<nb, kBlock, 0, s>>>(d, V, vj1, j, k.hco, ps, k.ctl, ns, k.part, ps, mixed ? 1 : 0);
-            note_launch();
-            if (!mixed) {
-                if ((st = dots<TB>(m, V, vj1, j, k.part, ps, s)) != GKS_OK) return st;
-                k_reduce<<<dim3(j + 1, ns), kReduceThreads, 0, s>>>(k.part, d.case_blk, ps, k.y, mm, 0, k.vn, mm + 1,
-                                                                     k.hco, ps);
-                note_launch();
-                k_orth_update<TB><<<nb, kBlock, 0, s>>>(d, V, vj1, j, k.hco, ps, k.ctl, ns, k.part, ps, 1); note_launch();
-                k_hadd<<<sblocks(ns * (j + 1)), 128, 0, s>>>(k.hcol, ps, k.y, mm, j, ns); note_launch();
-            }
-            k_reduce<<<dim3(1, ns), kReduceThreads, 0, s>>>(k.part, d.case_blk, ps, k.hcol + j + 1, ps, 2);
-            note_launch();
-            prof_stop(m, slot, s);
-            k_givens<<<sblocks(ns), 128, 0, s>>>(j, mm, k.hcol, ps, k.vn, k.H, k.cs, k.sn, k.g, k.ctl, ns, k.bnorm,
-                                                  k.beta, rtol, eta, maxit);
-            note_launch();
-            GKS_CUDA(cudaGetLastError());
-            if ((st = read_flags(m, s)) != GKS_OK) return st;
+            st = run_part(m, use_graph, G ? &G->iter[j] : &none, G ? &G->iter_launches[j] : &none_n, s,
+                          [&](cudaStream_t q) { return iter_part(q, j); });
+            if (st != GKS_OK) return st;
             if (!k.h_flags[1]) break;
         }
-        k_backsolve<<<sblocks(ns), 128, 0, s>>>(mm, k.H, k.g, k.y, k.ctl, ns); note_launch();
-        k_scale_y<<<sblocks(ns), 128, 0, s>>>(mm, k.y, k.vn, k.ctl, ns); note_launch();
-        if (mixed)
-            k_combine_z<float><<<dim3(nb, NV), kBlock, 0, s>>>(d, k.Z32, k.y, mm, k.ctl, ns, k.x);
-        else
-            k_combine_z<double><<<dim3(nb, NV), kBlock, 0, s>>>(d, k.Z, k.y, mm, k.ctl, ns, k.x);
-        note_launch();
-        k_spmv<double, double, TB><<<nb, kBlock, 0, s>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, V, 2, k.b, k.part, ps);
-        note_launch();
+        if ((st = run_part(m, use_graph, G ? &G->restart : &none, G ? &G->restart_launches : &none_n, s,
+                           restart_part)) != GKS_OK)
+            return st;
         m->prof.residuals += 1;
-        k_reduce<<<dim3(1, ns), kReduceThreads, 0, s>>>(k.part, d.case_blk, ps, k.hcol, ps, 0); note_launch();
-        k_start<<<sblocks(ns), 128, 0, s>>>(k.hcol, ps, k.bnorm, k.beta, k.vn, mm, k.ctl, ns, k.done, rtol, maxit, 0);
-        note_launch();
-        GKS_CUDA(cudaGetLastError());
-        if ((st = read_flags(m, s)) != GKS_OK) return st;
     }
     k_mark_noconv<<<sblocks(ns), 128, 0, s>>>(k.bnorm, k.beta, k.done, ns, rtol, k.status); note_launch();
     if (iters || relres || converged) {
@@ -806,6 +903,18 @@ gks_status cls_solve(gks_mesh *m, cudaStream_t s, int32_t *iters, double *relres
                           : cls_solve_t<double>(m, k.V, s, iters, relres, converged);
     if (st == GKS_OK) ++k.nsolve;
     return st;
+}
+
+void destroy_graph_execs(SolveGraphs *g)
+{
+    for (cudaGraphExec_t &e : g->iter)
+        if (e) {
+            cudaGraphExecDestroy(e);
+            e = nullptr;
+        }
+    if (g->start) cudaGraphExecDestroy(g->start);
+    if (g->restart) cudaGraphExecDestroy(g->restart);
+    g->start = g->restart = nullptr;
 }
 
 }  // namespace gks

@@ -125,6 +125,22 @@ struct Work {
     double *h_scal = nullptr;        // [8]
 };
 
+// CUDA graphs of the fixed launch sequences of the CLS solve (the start, one
+// per Arnoldi index, the restart), captured on first use on a private stream
+// and replayed on the caller's stream; rebuilt when a knob baked into their
+// kernel arguments changes.
+struct SolveGraphs {
+    cudaStream_t cap = nullptr;
+    std::vector<cudaGraphExec_t> iter;
+    std::vector<int64_t> iter_launches;
+    cudaGraphExec_t start = nullptr, restart = nullptr;
+    int64_t start_launches = 0, restart_launches = 0;
+    int32_t sweeps = -1, precond = -1, maxit = -1;
+    double eta = -1.0, rtol = -1.0;
+    bool disabled = false;                          // a capture failed: launch directly
+};
+void destroy_graph_execs(SolveGraphs *g);
+
 }  // namespace gks
 
 struct gks_profiler {
@@ -147,6 +163,7 @@ struct gks_mesh {
     gks::Work wk;
     int64_t device_bytes = 0;
     std::vector<void *> allocations;
+    gks::SolveGraphs *graphs = nullptr;
 };
 
 namespace gks {

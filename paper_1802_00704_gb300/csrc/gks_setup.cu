@@ -729,6 +729,12 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
 
 void free_mesh(gks_mesh *m)
 {
+    if (m->graphs) {
+        destroy_graph_execs(m->graphs);
+        if (m->graphs->cap) cudaStreamDestroy(m->graphs->cap);
+        delete m->graphs;
+        m->graphs = nullptr;
+    }
     for (void *p : m->allocations) cudaFree(p);
     m->allocations.clear();
     if (m->wk.h_flags) cudaFreeHost(m->wk.h_flags);

@@ -42,7 +42,7 @@ class Config(C.Structure):
                 ("precision", C.c_int32), ("precond", C.c_int32), ("ilu_sweeps", C.c_int32),
                 ("tau2_exact", C.c_int32), ("limiter", C.c_int32),
                 ("basis_fp32", C.c_int32), ("warm_extrap", C.c_int32), ("second_order", C.c_int32),
-                ("reserved", C.c_int32 * 2),
+                ("no_graphs", C.c_int32), ("reserved", C.c_int32 * 1),
                 ("inner_rtol", C.c_double)]
 
 

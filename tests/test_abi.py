@@ -38,7 +38,8 @@ def test_config_defaults(lib):
     c = gks.config()
     assert c.gamma == 1.4 and c.cfl == 0.3 and c.cls_w == 0.3 and c.gmres_m == 30
     assert c.gmres_rtol == 1e-12 and c.precision == gks.FP64 and c.limiter == 0 and c.basis_fp32 == 0
-    assert c.warm_extrap == 0 and c.second_order == 0 and list(c.reserved) == [0] * 2 and c.inner_rtol == 1e-6
+    assert c.warm_extrap == 0 and c.second_order == 0 and c.no_graphs == 0
+    assert list(c.reserved) == [0] and c.inner_rtol == 1e-6
     # the ctypes mirror has the size of the C struct: 4 doubles, 2 ints, 1 double, 10 ints, 1 double
     assert C.sizeof(gks.Config) == 4 * 8 + 2 * 4 + 8 + 10 * 4 + 8
     assert gks.Config.inner_rtol.offset == 88

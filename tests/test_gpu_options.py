@@ -98,3 +98,40 @@ def test_autotune_on_a_batch(G):
     assert b.batch_run(wa, max_steps=5)["n_failed"] == 0
     ref.batch_run(wb, max_steps=5)
     assert rel_max(host(wa), host(wb)) <= 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_replay_equals_direct_launches(G, precision):
+    """The CLS solve replays CUDA graphs of its fixed launch sequences; with
+    no_graphs = 1 it launches the same kernels one by one.  Same kernels, same
+    order: the states agree bit for bit, and the library counts the same number
+    of kernel launches either way."""
+    prec = G.MIXED if precision == "mixed" else G.FP64
+    c = I.shock_vortex_case(40, 20)
+    out, counts = [], []
+    for no_graphs in (0, 1):
+        m = G.GksMesh(c.mesh, precision=prec, warm_extrap=2, no_graphs=no_graphs)
+        w = dev(c.w0)
+        l0 = G.launch_count()
+        its = [m.step(w, 2e-4)["iters"] for _ in range(6)]
+        counts.append(G.launch_count() - l0)
+        out.append((host(w), its))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
+    assert counts[0] == counts[1]
+
+
+def test_graphs_follow_knob_changes(G):
+    """Knobs baked into the captured kernel arguments (sweeps, warm start, inner
+    tolerance) drop the graphs when they change: after the autotuner has run
+    every candidate, the handle steps exactly like a fresh handle built with the
+    knobs it picked and launching its kernels one by one."""
+    c = I.shock_vortex_case(30, 15)
+    m = G.GksMesh(c.mesh, precision=G.MIXED)
+    r = m.autotune(dev(c.w0), trial_steps=1)
+    ref = G.GksMesh(c.mesh, precision=G.MIXED, ilu_sweeps=r["ilu_sweeps"], warm_extrap=r["warm_extrap"],
+                    inner_rtol=r["inner_rtol"], no_graphs=1)
+    wa, wb = dev(c.w0), dev(c.w0)
+    for _ in range(5):
+        assert m.step(wa, 2e-4)["iters"] == ref.step(wb, 2e-4)["iters"]
+    assert np.array_equal(host(wa), host(wb))
