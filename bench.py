@@ -479,13 +479,14 @@ def run_batch(args, world, rank, local):
     e2e_value = world * T * args.steps / allmax(world, time.perf_counter() - t0)
     knobs = {"ilu_sweeps": b.cfg.ilu_sweeps, "warm_extrap": b.cfg.warm_extrap, "inner_rtol": b.cfg.inner_rtol}
     names = ["flux", "spmv", "ilu", "orth", "update"]
+    hbm_peak = measured_peaks().get("hbm_gbs") or HBM_FALLBACK_GBS
     classes = {}
     for q, nm in enumerate(names):
         ent = {"ms": round(prof["ms"][q], 3), "launch_groups": prof["n"][q]}
         if nm != "flux" and prof["ms"][q] > 0:
             by = class_bytes(nm, prof, T, F, args.steps, knobs["ilu_sweeps"], False, mixed, False)
             gbs = by / (prof["ms"][q] / 1e3) / 1e9
-            ent.update({"bytes": by, "gbs": round(gbs, 1), "frac": round(gbs / HBM_FALLBACK_GBS, 3)})
+            ent.update({"bytes": by, "gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 3)})
         classes[nm] = ent
     per_launch_ms = prof["ms"][0] / max(prof["n"][0], 1)
     flop64 = FLUX_MIXED_FP64_FLOP_PER_GP if mixed else FLUX_FP64_FLOP_PER_GP
