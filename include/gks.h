@@ -132,6 +132,9 @@ typedef struct gks_config {
     double inner_rtol;     /* mixed precision: an inner FP32 GMRES cycle stops once its
                               residual estimate has dropped by this factor (0 < r < 1,
                               default 1e-6); the next FP64 residual then restarts it   */
+    double prandtl;        /* Prandtl number (> 0, default 1 = the BGK model's own):
+                              != 1 rescales the heat flux relative to the interface
+                              velocity by 1/Pr in the energy flux (not in the paper)  */
 } gks_config;
 
 typedef struct gks_mesh gks_mesh;

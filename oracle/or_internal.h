@@ -28,6 +28,7 @@ typedef struct or_params {
     int    limiter;     /* 1: shock detector + DWBAP limiter (Sec. III.C); 2: the
                            detector with first order in limited cells (robust)   */
     int    second_order; /* 1: k_i = 1 for every cell (linear CLS reconstruction) */
+    double prandtl;     /* Prandtl number of the heat-flux correction (1: none)  */
 } or_params;
 
 /* Boundary tags (same numbering as the input generator). */

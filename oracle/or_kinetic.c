@@ -352,6 +352,21 @@ static void flux_moment(const poly *Q, const moments *m, double *out)
     out[3] = 0.5 * (p_moment_shift(Q, m, 3, 0, 0) + p_moment_shift(Q, m, 1, 2, 0) + p_moment_shift(Q, m, 1, 0, 1));
 }
 
+/* Heat flux <(1/2) (u - U) |c|^2 Q>, c = (u - U, v - V, xi), of the time-integrated
+ * distribution Q relative to the velocity (U, V): the polynomial
+ * (1/2)[(u-U)^3 + (u-U)(v-V)^2 + (u-U) zeta] expanded in monomials, each moment
+ * taken directly. */
+static double heat_moment(const poly *Q, const moments *m, double U, double V)
+{
+    const struct { int a, b, z; double c; } t[10] = {
+        {3, 0, 0, 0.5}, {2, 0, 0, -1.5 * U}, {1, 0, 0, 0.5 * (3.0 * U * U + V * V)},
+        {0, 0, 0, -0.5 * (U * U * U + U * V * V)}, {1, 2, 0, 0.5}, {1, 1, 0, -V}, {0, 2, 0, -0.5 * U},
+        {0, 1, 0, U * V}, {1, 0, 1, 0.5}, {0, 0, 1, -0.5 * U}};
+    double q = 0.0;
+    for (int k = 0; k < 10; ++k) q += t[k].c * p_moment_shift(Q, m, t[k].a, t[k].b, t[k].z);
+    return q;
+}
+
 /* Time-integrated flux through a unit-length face at one Gauss point, in the
  * face frame, from the left and right states wl[24], wr[24] (rows: value,
  * d/dn, d/dt, d2/dn2, d2/dndt, d2/dt2).  f[4] = int_0^dt F dt.
@@ -401,6 +416,15 @@ int or_gp_flux(const double *wl, const double *wr, double dt, const or_params *p
     flux_moment(&Ql, &L.half, fl);
     flux_moment(&Qr, &R.half, fr);
     for (int k = 0; k < 4; ++k) f[k] = Z.rho * f0[k] + L.rho * fl[k] + R.rho * fr[k];
+    /* Prandtl number (not in the paper; the BGK model has Pr = 1): the heat flux
+     * relative to the interface equilibrium velocity is rescaled by 1/Pr in the
+     * energy flux, F_E += (1/Pr - 1) q (the correction of the BGK-NS scheme,
+     * K. Xu, J. Comput. Phys. 171 (2001) 289-335). */
+    if (prm->prandtl != 1.0) {
+        const double q = Z.rho * heat_moment(&Q0, &Z.full, Z.U, Z.V) + L.rho * heat_moment(&Ql, &L.half, Z.U, Z.V) +
+                         R.rho * heat_moment(&Qr, &R.half, Z.U, Z.V);
+        f[3] += (1.0 / prm->prandtl - 1.0) * q;
+    }
     if (aux) {
         aux[0] = tau;
         for (int k = 0; k < 4; ++k) aux[1 + k] = w0[k];

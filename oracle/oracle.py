@@ -42,7 +42,8 @@ def build(force: bool = False) -> str:
 class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("mu", C.c_double), ("cls_w", C.c_double),
                 ("gmres_m", C.c_int), ("gmres_maxit", C.c_int), ("gmres_rtol", C.c_double),
-                ("tau2_exact", C.c_int), ("slope0_mode", C.c_int), ("limiter", C.c_int), ("second_order", C.c_int)]
+                ("tau2_exact", C.c_int), ("slope0_mode", C.c_int), ("limiter", C.c_int), ("second_order", C.c_int),
+                ("prandtl", C.c_double)]
 
 
 def _load():

@@ -58,7 +58,7 @@ gks_status check_config(const gks_config &c)
     ok = ok && c.limiter >= 0 && c.limiter <= 2;
     ok = ok && (c.basis_fp32 == 0 || (c.basis_fp32 == 1 && c.precision == GKS_MIXED));
     ok = ok && c.warm_extrap >= 0 && c.warm_extrap <= 2;
-    ok = ok && c.inner_rtol > 0.0 && c.inner_rtol < 1.0;
+    ok = ok && c.inner_rtol > 0.0 && c.inner_rtol < 1.0 && c.prandtl > 0.0;
     ok = ok && (c.second_order == 0 || c.second_order == 1);
     ok = ok && (c.no_graphs == 0 || c.no_graphs == 1);
     for (int q = 0; q < 1; ++q) ok = ok && c.reserved[q] == 0;
@@ -181,6 +181,7 @@ void gks_config_default(gks_config *c)
     c->ilu_sweeps = 2;
     c->tau2_exact = 0;
     c->inner_rtol = 1e-6;
+    c->prandtl = 1.0;
 }
 
 const char *gks_last_error(void) { return gks::last_error(); }
@@ -543,6 +544,8 @@ gks_status gks_point_flux(int64_t n, const double *wl, const double *wr, double 
     gks_config c;
     if (cfg) c = *cfg;
     else gks_config_default(&c);
+    gks_status st = check_config(c);
+    if (st != GKS_OK) return st;
     return launch_point_flux(n, wl, wr, dt, c, out, nullptr, (cudaStream_t)stream);
 }
 

@@ -209,13 +209,14 @@ __global__ void k_to_f32(const double *__restrict__ x, float *__restrict__ y, in
 }
 
 // MIXED: interface state and leading terms in FP64, slope-carrying terms in FP32.
-template <bool MIXED>
+// HEAT: Prandtl correction of the energy flux (prandtl != 1).
+template <bool MIXED, bool HEAT>
 __global__ void __launch_bounds__(kFluxBlock) k_face_flux(DeviceMesh d, const double *__restrict__ w,
                                                           const double *__restrict__ x,
                                                           const float *__restrict__ x32, double dt_const,
                                                           const double *__restrict__ dt_dev, double gamma, double K,
-                                                          double mu, int tau2, double *__restrict__ flux,
-                                                          int32_t *status)
+                                                          double mu, int tau2, double prandtl,
+                                                          double *__restrict__ flux, int32_t *status)
 {
     const int64_t F = d.F;
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -242,7 +243,7 @@ __global__ void __launch_bounds__(kFluxBlock) k_face_flux(DeviceMesh d, const do
                 const double bc[4] = {d.bc[f], d.bc[F + f], d.bc[2 * F + f], d.bc[3 * F + f]};
                 ghost_mixed(d.ftag[f], bc, nx, ny, gamma, vl, dl, vr, dr);
             }
-            ok = kin::gp_flux_mixed_split(vl, vr, dl, dr, dt, gamma, K, mu, tau2, fk);
+            ok = kin::gp_flux_mixed_split<HEAT>(vl, vr, dl, dr, dt, gamma, K, mu, tau2, fk, prandtl);
         } else {
             double gl[24], wl[24], wr[24];
             recon(d, w, x, l, d.gl[(2 * k) * F + f], d.gl[(2 * k + 1) * F + f], gl);
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(kFluxBlock) k_face_flux(DeviceMesh d, const do
                 const double bc[4] = {d.bc[f], d.bc[F + f], d.bc[2 * F + f], d.bc[3 * F + f]};
                 ghost(d.ftag[f], bc, nx, ny, gamma, wl, wr);
             }
-            ok = kin::gp_flux<double>(wl, wr, dt, gamma, mu, tau2, fk);
+            ok = kin::gp_flux<double, HEAT>(wl, wr, dt, gamma, mu, tau2, fk, prandtl);
         }
         if (!ok) atomicOr(&status[cs], kStatusNonPhys);
         const double s = 0.5 * d.flen[f];      // Gauss weight 1/2 times the face length
@@ -354,11 +355,11 @@ __global__ void k_clip_dt(double *dt, double *t, const double *__restrict__ tf, 
     t[c] += dt[c];
 }
 
-template <bool MIXED>
+template <bool MIXED, bool HEAT>
 __global__ void __launch_bounds__(kFluxBlock) k_point_flux(int64_t n, const double *__restrict__ wl,
                                                            const double *__restrict__ wr, double dt, double gamma,
-                                                           double mu, int tau2, double *__restrict__ out,
-                                                           int32_t *status)
+                                                           double mu, int tau2, double prandtl,
+                                                           double *__restrict__ out, int32_t *status)
 {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= n) return;
@@ -368,7 +369,8 @@ __global__ void __launch_bounds__(kFluxBlock) k_point_flux(int64_t n, const doub
         a[k] = wl[24 * q + k];
         b[k] = wr[24 * q + k];
     }
-    const bool ok = MIXED ? kin::gp_flux_mixed(a, b, dt, gamma, mu, tau2, f) : kin::gp_flux<double>(a, b, dt, gamma, mu, tau2, f);
+    const bool ok = MIXED ? kin::gp_flux_mixed<HEAT>(a, b, dt, gamma, mu, tau2, f, prandtl)
+                          : kin::gp_flux<double, HEAT>(a, b, dt, gamma, mu, tau2, f, prandtl);
     if (!ok && status) atomicOr(status, kStatusNonPhys);
 #pragma unroll
     for (int k = 0; k < 4; ++k) out[4 * q + k] = f[k];
@@ -439,18 +441,26 @@ gks_status launch_flux(gks_mesh *m, const double *w, const double *x, double dt_
     const int64_t npts = 2 * m->d.F;
     const double K = 2.0 / (m->cfg.gamma - 1.0) - 2.0;
     const int slot = prof_start(m, kProfFlux, s);
-    if (m->cfg.precision == GKS_MIXED) {
+    const gks_config &c = m->cfg;
+    const bool heat = c.prandtl != 1.0;
+    const unsigned g = blocks(npts, kFluxBlock);
+    if (c.precision == GKS_MIXED) {
         // FP32 copy of the coefficients: the slope-carrying rows of every Gauss
         // point of a cell read it instead of converting the FP64 values again
         k_to_f32<<<blocks(20 * m->d.T, kBlock), kBlock, 0, s>>>(x, m->wk.x32, 20 * m->d.T);
         note_launch();
-        k_face_flux<true><<<blocks(npts, kFluxBlock), kFluxBlock, 0, s>>>(m->d, w, x, m->wk.x32, dt_const, dt_dev,
-                                                                          m->cfg.gamma, K, m->cfg.mu,
-                                                                          m->cfg.tau2_exact, flux, m->wk.status);
+        if (heat)
+            k_face_flux<true, true><<<g, kFluxBlock, 0, s>>>(m->d, w, x, m->wk.x32, dt_const, dt_dev, c.gamma, K, c.mu,
+                                                             c.tau2_exact, c.prandtl, flux, m->wk.status);
+        else
+            k_face_flux<true, false><<<g, kFluxBlock, 0, s>>>(m->d, w, x, m->wk.x32, dt_const, dt_dev, c.gamma, K,
+                                                              c.mu, c.tau2_exact, c.prandtl, flux, m->wk.status);
+    } else if (heat) {
+        k_face_flux<false, true><<<g, kFluxBlock, 0, s>>>(m->d, w, x, nullptr, dt_const, dt_dev, c.gamma, K, c.mu,
+                                                          c.tau2_exact, c.prandtl, flux, m->wk.status);
     } else {
-        k_face_flux<false><<<blocks(npts, kFluxBlock), kFluxBlock, 0, s>>>(m->d, w, x, nullptr, dt_const, dt_dev,
-                                                                           m->cfg.gamma, K, m->cfg.mu,
-                                                                           m->cfg.tau2_exact, flux, m->wk.status);
+        k_face_flux<false, false><<<g, kFluxBlock, 0, s>>>(m->d, w, x, nullptr, dt_const, dt_dev, c.gamma, K, c.mu,
+                                                           c.tau2_exact, c.prandtl, flux, m->wk.status);
     }
     note_launch();
     prof_stop(m, slot, s);
@@ -480,12 +490,20 @@ gks_status launch_point_flux(int64_t n, const double *wl, const double *wr, doub
                              double *out, int32_t *status, cudaStream_t s)
 {
     if (n <= 0) return GKS_OK;
-    if (cfg.precision == GKS_MIXED)
-        k_point_flux<true><<<blocks(n, kFluxBlock), kFluxBlock, 0, s>>>(n, wl, wr, dt, cfg.gamma, cfg.mu, cfg.tau2_exact,
-                                                                         out, status);
+    const unsigned g = blocks(n, kFluxBlock);
+    const bool heat = cfg.prandtl != 1.0;
+    if (cfg.precision == GKS_MIXED && heat)
+        k_point_flux<true, true><<<g, kFluxBlock, 0, s>>>(n, wl, wr, dt, cfg.gamma, cfg.mu, cfg.tau2_exact,
+                                                          cfg.prandtl, out, status);
+    else if (cfg.precision == GKS_MIXED)
+        k_point_flux<true, false><<<g, kFluxBlock, 0, s>>>(n, wl, wr, dt, cfg.gamma, cfg.mu, cfg.tau2_exact,
+                                                           cfg.prandtl, out, status);
+    else if (heat)
+        k_point_flux<false, true><<<g, kFluxBlock, 0, s>>>(n, wl, wr, dt, cfg.gamma, cfg.mu, cfg.tau2_exact,
+                                                           cfg.prandtl, out, status);
     else
-        k_point_flux<false><<<blocks(n, kFluxBlock), kFluxBlock, 0, s>>>(n, wl, wr, dt, cfg.gamma, cfg.mu,
-                                                                          cfg.tau2_exact, out, status);
+        k_point_flux<false, false><<<g, kFluxBlock, 0, s>>>(n, wl, wr, dt, cfg.gamma, cfg.mu, cfg.tau2_exact,
+                                                            cfg.prandtl, out, status);
     note_launch();
     GKS_CUDA(cudaGetLastError());
     return GKS_OK;

@@ -410,8 +410,12 @@ __device__ __forceinline__ bool interface_state(const R *wl, const R *wr, R dt, 
 // Flux terms of Eqs. (11) and (15) at y = 0, from the slopes of the three
 // states.  with_const = false leaves out the zeroth-order terms C1 g0 and
 // C7 g_k (see lead_flux).
-template <typename R>
-__device__ __forceinline__ void body_flux(const R *wl, const R *wr, Iface<R> &I, R gamma, bool with_const, R *f)
+//
+// HEAT: also d_alpha = <psi_alpha f> (the time-integrated moments without the
+// factor u), for the heat flux of the Prandtl correction.
+template <typename R, bool HEAT = false>
+__device__ __forceinline__ void body_flux(const R *wl, const R *wr, Iface<R> &I, R gamma, bool with_const, R *f,
+                                          R *d = nullptr)
 {
     const R K = R(2) / (gamma - R(1)) - R(2);
     const R tau = I.tau;
@@ -430,6 +434,11 @@ __device__ __forceinline__ void body_flux(const R *wl, const R *wr, Iface<R> &I,
     upsi_contract(Q, m, out);
 #pragma unroll
     for (int q = 0; q < 4; ++q) f[q] += I.Z.rho * out[q];
+    if (HEAT) {
+        psi_contract<R, 4>(Q, m, out);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d[q] = I.Z.rho * out[q];
+    }
     // non-equilibrium part, Eq. (11), left (u > 0) and right (u < 0)
     const R kA = -tau * C[6], kL = C[7] - tau * C[6], kS = R(0.5) * C[8] - tau * C[7], kAL = -tau * C[7];
     const R k7 = with_const ? C[6] : R(0);
@@ -442,6 +451,11 @@ __device__ __forceinline__ void body_flux(const R *wl, const R *wr, Iface<R> &I,
     upsi_contract(Q, m, out);
 #pragma unroll
     for (int q = 0; q < 4; ++q) f[q] += I.L.rho * out[q];
+    if (HEAT) {
+        psi_contract<R, 4>(Q, m, out);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d[q] += I.L.rho * out[q];
+    }
     mom_full(I.Rs.U, I.Rs.lam, m.u);
     mom_full(I.Rs.V, I.Rs.lam, m.v);
     mom_xi(I.Rs.lam, K, m.z);
@@ -451,6 +465,22 @@ __device__ __forceinline__ void body_flux(const R *wl, const R *wr, Iface<R> &I,
     upsi_contract(Q, m, out);
 #pragma unroll
     for (int q = 0; q < 4; ++q) f[q] += I.Rs.rho * out[q];
+    if (HEAT) {
+        psi_contract<R, 4>(Q, m, out);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d[q] += I.Rs.rho * out[q];
+    }
+}
+
+// Heat flux relative to the velocity (U, V) from the flux moments F = <u psi f>
+// and the moments D = <psi f>: <(1/2)(u - U)|c|^2 f>, c = (u - U, v - V, xi),
+// expanded in the moments u e, u^2, u v, u, e, v, 1.
+template <typename R>
+__device__ __forceinline__ R heat_flux(const R *F, const R *D, R U, R V)
+{
+    const R q2 = U * U + V * V;
+    return F[3] - U * F[1] - V * F[2] + (R(0.5) * q2 + U * U) * F[0] - U * D[3] + U * V * D[2] -
+           R(0.5) * U * q2 * D[0];
 }
 
 // Zeroth-order (leading) terms: C1 rho0 <u psi>_0 + C7 (rho_l <u psi>_{u>0,l} +
@@ -492,8 +522,12 @@ __device__ __forceinline__ void lead_flux(const Iface<R> &I, R gamma, R *f)
 // Time-integrated flux through a unit-length face at one Gauss point, all in
 // precision R.  wl, wr: [6][4] face-frame rows (value, d/dn, d/dt, d2/dn2,
 // d2/dndt, d2/dt2).  Returns false if a state is not physical (f is zero).
-template <typename R>
-__device__ __forceinline__ bool gp_flux(const R *wl, const R *wr, R dt, R gamma, R mu, int tau2_exact, R *f)
+// HEAT: Prandtl correction F_E += (1/Pr - 1) q, q the heat flux relative to the
+// interface equilibrium velocity (not in the paper; the BGK model has Pr = 1;
+// the correction of the BGK-NS scheme, K. Xu, J. Comput. Phys. 171 (2001)).
+template <typename R, bool HEAT = false>
+__device__ __forceinline__ bool gp_flux(const R *wl, const R *wr, R dt, R gamma, R mu, int tau2_exact, R *f,
+                                        R prandtl = R(1))
 {
     Iface<R> I;
     if (!interface_state(wl, wr, dt, gamma, mu, tau2_exact, I)) {
@@ -501,7 +535,9 @@ __device__ __forceinline__ bool gp_flux(const R *wl, const R *wr, R dt, R gamma,
         for (int q = 0; q < 4; ++q) f[q] = R(0);
         return false;
     }
-    body_flux(wl, wr, I, gamma, true, f);
+    R d[4];
+    body_flux<R, HEAT>(wl, wr, I, gamma, true, f, d);
+    if (HEAT) f[3] += (R(1) / prandtl - R(1)) * heat_flux(f, d, I.Z.U, I.Z.V);
     return true;
 }
 
@@ -564,9 +600,10 @@ __device__ __forceinline__ void lead_integrals(double dt, double tau, double &c0
 // collision time, the time integrals and the zeroth-order terms
 // C1 rho0 <u psi>_0 + C7 (rho_l <u psi>_{u>0} + rho_r <u psi>_{u<0}) are FP64;
 // every slope-carrying term is FP32.
+template <bool HEAT = false>
 __device__ __forceinline__ bool gp_flux_mixed_split(const double *vl, const double *vr, const float *dl, const float *dr,
                                                     double dt, double gamma, double K, double mu, int tau2_exact,
-                                                    double *f)
+                                                    double *f, double prandtl = 1.0)
 {
 #pragma unroll
     for (int q = 0; q < 4; ++q) f[q] = 0.0;
@@ -603,6 +640,15 @@ __device__ __forceinline__ bool gp_flux_mixed_split(const double *vl, const doub
         f[2] += sl * ml[1] * L.V + sr * mr[1] * Rs.V;
         f[3] += sl * 0.5 * (ml[3] + ml[1] * (v2l + zl)) + sr * 0.5 * (mr[3] + mr[1] * (v2r + zr));
     }
+    // <psi f> of the same zeroth-order terms, for the heat flux
+    double dlead[4] = {0.0, 0.0, 0.0, 0.0};
+    if (HEAT) {
+        const double sl = C6 * L.rho, sr = C6 * Rs.rho;
+        dlead[0] = C0 * w0[0] + sl * ml[0] + sr * mr[0];
+        dlead[1] = C0 * w0[1] + sl * ml[1] + sr * mr[1];
+        dlead[2] = C0 * w0[2] + sl * ml[0] * L.V + sr * mr[0] * Rs.V;
+        dlead[3] = C0 * w0[3] + sl * 0.5 * (ml[2] + ml[0] * (v2l + zl)) + sr * 0.5 * (mr[2] + mr[0] * (v2r + zr));
+    }
     // slope-carrying terms (FP32): states, interface values and time integrals
     // are formed in FP32 from the rounded values (no per-field conversions)
     Iface<float> J;
@@ -625,15 +671,23 @@ __device__ __forceinline__ bool gp_flux_mixed_split(const double *vl, const doub
     prim(J.w0, gf, Kf, J.Z);
     J.tau = float(tau);
     time_integrals(float(dt), J.tau, tau2_exact, J.C);
-    body_flux(fl, fr, J, gf, false, g);
+    float dg[4];
+    body_flux<float, HEAT>(fl, fr, J, gf, false, g, dg);
 #pragma unroll
     for (int q = 0; q < 4; ++q) f[q] += double(g[q]);
+    if (HEAT) {
+        double D[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) D[q] = dlead[q] + double(dg[q]);
+        f[3] += (1.0 / prandtl - 1.0) * heat_flux(f, D, Z.U, Z.V);
+    }
     return true;
 }
 
 // Mixed precision flux from FP64 rows [6][4] (used by the point-flux entry point).
+template <bool HEAT = false>
 __device__ __forceinline__ bool gp_flux_mixed(const double *wl, const double *wr, double dt, double gamma, double mu,
-                                              int tau2_exact, double *f)
+                                              int tau2_exact, double *f, double prandtl = 1.0)
 {
     float dl[20], dr[20];
 #pragma unroll
@@ -641,7 +695,8 @@ __device__ __forceinline__ bool gp_flux_mixed(const double *wl, const double *wr
         dl[q] = float(wl[4 + q]);
         dr[q] = float(wr[4 + q]);
     }
-    return gp_flux_mixed_split(wl, wr, dl, dr, dt, gamma, 2.0 / (gamma - 1.0) - 2.0, mu, tau2_exact, f);
+    return gp_flux_mixed_split<HEAT>(wl, wr, dl, dr, dt, gamma, 2.0 / (gamma - 1.0) - 2.0, mu, tau2_exact, f,
+                                     prandtl);
 }
 
 }  // namespace kin

@@ -40,9 +40,10 @@ def test_config_defaults(lib):
     assert c.gmres_rtol == 1e-12 and c.precision == gks.FP64 and c.limiter == 0 and c.basis_fp32 == 0
     assert c.warm_extrap == 0 and c.second_order == 0 and c.no_graphs == 0
     assert list(c.reserved) == [0] and c.inner_rtol == 1e-6
-    # the ctypes mirror has the size of the C struct: 4 doubles, 2 ints, 1 double, 10 ints, 1 double
-    assert C.sizeof(gks.Config) == 4 * 8 + 2 * 4 + 8 + 10 * 4 + 8
-    assert gks.Config.inner_rtol.offset == 88
+    assert c.prandtl == 1.0
+    # the ctypes mirror has the size of the C struct: 4 doubles, 2 ints, 1 double, 10 ints, 2 doubles
+    assert C.sizeof(gks.Config) == 4 * 8 + 2 * 4 + 8 + 10 * 4 + 2 * 8
+    assert gks.Config.inner_rtol.offset == 88 and gks.Config.prandtl.offset == 96
 
 
 def test_binding_refuses_cpu_tensors(lib):

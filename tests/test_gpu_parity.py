@@ -72,6 +72,28 @@ def test_point_flux_matches_oracle(O, G, mu, tau2, jump, dt):
     assert np.all(np.max(np.abs(got - ref), axis=0) <= 1e-12 * scale), np.max(np.abs(got - ref), axis=0) / scale
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_prandtl_point_flux_matches_oracle(O, G, precision):
+    """Prandtl-corrected energy flux (Pr = 0.72, viscous collision time) against
+    the oracle, which takes the heat flux as the moment of (1/2)(u - U)|c|^2
+    directly: 1e-12 of each flux scale in FP64, 1e-7 in mixed precision."""
+    rng = np.random.default_rng(23)
+    n = 200
+    wl, wr = _random_states(rng, n, 0.3), _random_states(rng, n, 0.3)
+    if precision == "mixed":
+        for q in (wl, wr):
+            q[:, 1:] *= 0.1
+    dt, mu = 0.004, 2e-3
+    got = host(G.point_flux(dev(wl), dev(wr), dt, mu=mu, prandtl=0.72,
+                            precision=G.MIXED if precision == "mixed" else G.FP64))
+    ref = np.stack([O.point_flux(wl[q], wr[q], dt, mu=mu, prandtl=0.72)[0] for q in range(n)])
+    base = np.stack([O.point_flux(wl[q], wr[q], dt, mu=mu)[0] for q in range(n)])
+    assert np.max(np.abs(ref[:, 3] - base[:, 3])) > 1e-6 * np.max(np.abs(ref[:, 3]))   # the correction acts
+    scale = np.max(np.abs(ref), axis=0)
+    tol = 1e-12 if precision == "fp64" else 1e-7
+    assert np.all(np.max(np.abs(got - ref), axis=0) <= tol * scale), np.max(np.abs(got - ref), axis=0) / scale
+
+
 # --------------------------------------------------------------------------- reconstruction and flux
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -161,11 +183,12 @@ def test_run_matches_steps(G):
     assert np.array_equal(host(w1), host(w2))
 
 
-def test_viscous_noslip_cavity_matches_oracle(O, G):
+@pytest.mark.parametrize("prandtl", [1.0, 0.72])
+def test_viscous_noslip_cavity_matches_oracle(O, G, prandtl):
     c = I.cavity_case(10)
-    om = O.OracleMesh(c.mesh, mu=c.mu)
+    om = O.OracleMesh(c.mesh, mu=c.mu, prandtl=prandtl)
     wo = c.w0.copy()
-    m = G.GksMesh(c.mesh, mu=c.mu)
+    m = G.GksMesh(c.mesh, mu=c.mu, prandtl=prandtl)
     w = dev(c.w0)
     for _ in range(5):
         dt = om.cfl_dt(wo)

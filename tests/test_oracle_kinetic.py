@@ -293,3 +293,45 @@ def test_flux_time_taylor_general_flow(oracle_mod):
         assert st == 0
         errs.append(np.abs(f - ref).max() / np.abs(ref).max())
     assert max(errs) < 1e-12, errs
+
+
+def _conduction_rows(g=0.1, T0=1.0, p=1.0, U=0.0, V=0.0, gamma=GAMMA):
+    """Face-frame rows of a state with uniform pressure and velocity and a
+    temperature T = p / rho growing linearly along the face normal (T0 + g n)."""
+    rho0, drho, d2rho = p / T0, -p * g / T0 ** 2, 2.0 * p * g * g / T0 ** 3
+    w = np.zeros((6, 4))
+    for r, d in ((0, rho0), (1, drho), (3, d2rho)):
+        w[r] = [d, d * U, d * V, 0.5 * d * (U * U + V * V)]
+    w[0, 3] += p / (gamma - 1.0)
+    return w
+
+
+@pytest.mark.parametrize("prandtl", [1.0, 0.72, 2.0 / 3.0])
+def test_heat_flux_is_fourier_conduction(oracle_mod, prandtl):
+    """At rest, uniform pressure, linear temperature: the flux is pressure in the
+    normal momentum and Fourier conduction -c_p (mu / Pr) dT/dn in the energy
+    (c_p = gamma / (gamma - 1), the conductivity of the BGK-NS limit rescaled by
+    the Prandtl correction), whatever tangential velocity the gas has."""
+    g, mu, dt = 0.1, 1e-4, 1e-2
+    cp = GAMMA / (GAMMA - 1.0)
+    for V in (0.0, 0.3):
+        w = _conduction_rows(g=g, V=V)
+        f, _, st = oracle_mod.point_flux(w, w, dt, mu=mu, prandtl=prandtl)
+        assert st == 0
+        assert abs(f[0]) < 1e-15 and abs(f[1] - dt) < 1e-14
+        assert abs(f[3] - (-cp * mu / prandtl * g * dt)) < 1e-10 * cp * mu * g * dt
+        assert abs(f[2]) < 1e-14
+
+
+def test_prandtl_rescales_only_the_heat_flux(oracle_mod):
+    """With normal flow the energy flux also carries U (E + p): the Prandtl
+    correction changes the energy flux by (1/Pr - 1) times the conduction part
+    only, and leaves mass and momentum fluxes untouched."""
+    g, mu, dt, U = 0.1, 1e-4, 1e-3, 0.4
+    cp = GAMMA / (GAMMA - 1.0)
+    w = _conduction_rows(g=g, U=U)
+    f1, _, _ = oracle_mod.point_flux(w, w, dt, mu=mu, prandtl=1.0)
+    f2, _, _ = oracle_mod.point_flux(w, w, dt, mu=mu, prandtl=0.72)
+    assert np.all(np.abs(f2[:3] - f1[:3]) <= 1e-15 * np.abs(f1[:3]).max())
+    heat = -cp * mu * g * dt
+    assert abs((f2[3] - f1[3]) - (1.0 / 0.72 - 1.0) * heat) < 0.02 * abs((1.0 / 0.72 - 1.0) * heat)
