@@ -128,7 +128,9 @@ typedef struct gks_config {
     int32_t no_graphs;     /* 1: launch the CLS solve's kernels one by one instead of
                               replaying CUDA graphs of its fixed launch sequences
                               (same kernels, same order, same results)                */
-    int32_t reserved[1];   /* must be zero                                             */
+    int32_t limit_char;    /* 1: the DWBAP limiter works on characteristic variables
+                              (eigenvectors of the Euler flux Jacobian at the cell
+                              average, Sec. IV.B) instead of conservative ones        */
     double inner_rtol;     /* mixed precision: an inner FP32 GMRES cycle stops once its
                               residual estimate has dropped by this factor (0 < r < 1,
                               default 1e-6); the next FP64 residual then restarts it   */

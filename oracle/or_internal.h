@@ -29,6 +29,7 @@ typedef struct or_params {
                            detector with first order in limited cells (robust)   */
     int    second_order; /* 1: k_i = 1 for every cell (linear CLS reconstruction) */
     double prandtl;     /* Prandtl number of the heat-flux correction (1: none)  */
+    int    limit_char;  /* 1: DWBAP in characteristic variables (Sec. IV.B)       */
 } or_params;
 
 /* Boundary tags (same numbering as the input generator). */
@@ -94,5 +95,6 @@ int  or_gp_flux(const double *wl, const double *wr, double dt, const or_params *
 
 /* limiter (or_limiter.c) */
 int  or_limit(const or_mesh *m, const double *w, const double *coef, double *coef_out, int32_t *flag);
+void or_char_basis(const double *W, double gamma, double nx, double ny, double *R, double *L);
 
 #endif

@@ -16,6 +16,12 @@
  *    j = 0) to the cell's face midpoints, S(chi) = 1/(sqrt(chi + 1e-8) + 0.05),
  *    chi = std / mean of the neighbours' pressures; second derivatives first,
  *    then first derivatives, all from the unlimited neighbour polynomials;
+ *  - characteristic variables (limit_char = 1, Sec. IV.B compares them with
+ *    the conservative ones): each derivative row is limited in the
+ *    eigenvector basis of the Euler flux Jacobian along a direction (x for
+ *    d/dx and d2/dx2, y for d/dy and d2/dy2, the diagonal for d2/dxdy) at the
+ *    cell average; candidates are mapped by the left eigenvectors, limited
+ *    component by component, and mapped back by the right ones;
  *  - robust mode (limiter = 2, not in the paper): a limited cell keeps its
  *    cell average only (first order), for contacts with density ratios near
  *    10, where the DWBAP polynomials let cell averages turn negative;
@@ -56,6 +62,29 @@ static double detector(const or_mesh *m, const double *w, const double *coef, in
         umax = fmax(umax, w[(size_t)var * T + j]);
     }
     return s / (J * pow(m->h[i], 0.5 * (m->korder[i] + 1)) * umax);
+}
+
+/* Right (columns) and left (rows) eigenvectors of the Jacobian of the Euler
+ * flux along the unit direction (nx, ny) at the conservative state W:
+ * eigenvalues q_n - c, q_n, q_n, q_n + c.  R and L are 4x4 row-major. */
+void or_char_basis(const double *W, double gamma, double nx, double ny, double *R, double *L)
+{
+    const double rho = W[0], u = W[1] / rho, v = W[2] / rho;
+    const double ke = 0.5 * (u * u + v * v);
+    const double p = (gamma - 1.0) * (W[3] - rho * ke);
+    const double c = sqrt(gamma * p / rho), H = (W[3] + p) / rho;
+    const double qn = u * nx + v * ny, qt = -u * ny + v * nx;
+    const double Rm[16] = {1.0, 1.0, 0.0, 1.0,
+                           u - c * nx, u, -ny, u + c * nx,
+                           v - c * ny, v, nx, v + c * ny,
+                           H - qn * c, ke, qt, H + qn * c};
+    const double b1 = (gamma - 1.0) / (c * c), b2 = b1 * ke;
+    const double Lm[16] = {0.5 * (b2 + qn / c), -0.5 * (b1 * u + nx / c), -0.5 * (b1 * v + ny / c), 0.5 * b1,
+                           1.0 - b2, b1 * u, b1 * v, -b1,
+                           -qt, -ny, nx, 0.0,
+                           0.5 * (b2 - qn / c), -0.5 * (b1 * u - nx / c), -0.5 * (b1 * v - ny / c), 0.5 * b1};
+    memcpy(R, Rm, sizeof(Rm));
+    memcpy(L, Lm, sizeof(Lm));
 }
 
 /* 1 if the polynomial of cell i (coefficients coef) gives rho > 0 and p > 0
@@ -138,37 +167,56 @@ int or_limit(const or_mesh *m, const double *w, const double *coef, double *coef
         double om[4];
         for (int j = 0; j <= J; ++j) om[j] = beta[j] / bsum;
         const double hi = m->h[i];
-        for (int v = 0; v < 4; ++v) {
-            /* second derivatives (physical) from the cells with k = 2 */
-            if (m->korder[i] == 2) {
-                for (int l = 2; l < 5; ++l) {
-                    double cand[4], omc[4], os = 0.0;
-                    int n = 0;
-                    cand[n] = coef[((size_t)v * 5 + l) * T + i] / (hi * hi); omc[n] = om[0]; os += om[0]; ++n;
-                    for (int k = 0; k < J; ++k) {
-                        int j = m->nb_cell[3 * i + k];
-                        if (m->korder[j] != 2) continue;
-                        cand[n] = coef[((size_t)v * 5 + l) * T + j] / (m->h[j] * m->h[j]);
-                        omc[n] = om[k + 1]; os += om[k + 1]; ++n;
-                    }
-                    for (int q = 0; q < n; ++q) omc[q] /= os;
-                    coef_out[((size_t)v * 5 + l) * T + i] = hi * hi * biased(cand, omc, n);
-                }
-            }
-            /* first derivatives at the centroid: own vs neighbour polynomials at r_i */
-            double gi[24];
-            or_eval_cell(m, w, coef, (int)i, m->cx[i], m->cy[i], gi);
-            double gx[4], gy[4];
-            gx[0] = gi[4 + v]; gy[0] = gi[8 + v];
+        /* candidates per derivative row l (physical units), cand[c][v]: the cell's
+         * own derivative (c = 0) and the neighbours' at r_i */
+        double gi[24], gnb[3][24];
+        or_eval_cell(m, w, coef, (int)i, m->cx[i], m->cy[i], gi);
+        for (int k = 0; k < J; ++k) {
+            int j = m->nb_cell[3 * i + k];
+            or_eval_cell(m, w, coef, j, m->cx[i] - m->nb_dx[3 * i + k], m->cy[i] - m->nb_dy[3 * i + k], gnb[k]);
+        }
+        const double wi[4] = {w[i], w[T + i], w[2 * T + i], w[3 * T + i]};
+        for (int l = 0; l < 5; ++l) {
+            if (l >= 2 && m->korder[i] != 2) continue;
+            double cand[4][4], omc[4], os = 0.0;
+            int n = 0;
+            for (int v = 0; v < 4; ++v)   /* own: d/dx = u1/h at the centroid, second derivatives u/h^2 */
+                cand[0][v] = l < 2 ? gi[4 * (l + 1) + v] : coef[((size_t)v * 5 + l) * T + i] / (hi * hi);
+            omc[n] = om[0]; os += om[0]; ++n;
             for (int k = 0; k < J; ++k) {
                 int j = m->nb_cell[3 * i + k];
-                double gj[24];
-                or_eval_cell(m, w, coef, j, m->cx[i] - m->nb_dx[3 * i + k], m->cy[i] - m->nb_dy[3 * i + k], gj);
-                gx[k + 1] = gj[4 + v]; gy[k + 1] = gj[8 + v];
+                if (l >= 2 && m->korder[j] != 2) continue;
+                for (int v = 0; v < 4; ++v)
+                    cand[n][v] = l < 2 ? gnb[k][4 * (l + 1) + v]
+                                       : coef[((size_t)v * 5 + l) * T + j] / (m->h[j] * m->h[j]);
+                omc[n] = om[k + 1]; os += om[k + 1]; ++n;
             }
-            /* own gradient at the centroid is (u1 + u3*0 + u4*0)/h: the centroid has zero offset */
-            coef_out[((size_t)v * 5 + 0) * T + i] = hi * biased(gx, om, J + 1);
-            coef_out[((size_t)v * 5 + 1) * T + i] = hi * biased(gy, om, J + 1);
+            for (int q = 0; q < n; ++q) omc[q] /= os;
+            double res[4];
+            if (m->prm.limit_char) {
+                static const double dir[5][2] = {{1, 0}, {0, 1}, {1, 0}, {0.70710678118654752, 0.70710678118654752},
+                                                 {0, 1}};
+                double Rm[16], Lm[16], ch[4][4], lim[4];
+                or_char_basis(wi, gamma, dir[l][0], dir[l][1], Rm, Lm);
+                for (int q = 0; q < n; ++q)
+                    for (int a = 0; a < 4; ++a) {
+                        ch[a][q] = 0.0;
+                        for (int b = 0; b < 4; ++b) ch[a][q] += Lm[4 * a + b] * cand[q][b];
+                    }
+                for (int a = 0; a < 4; ++a) lim[a] = biased(ch[a], omc, n);
+                for (int a = 0; a < 4; ++a) {
+                    res[a] = 0.0;
+                    for (int b = 0; b < 4; ++b) res[a] += Rm[4 * a + b] * lim[b];
+                }
+            } else {
+                for (int v = 0; v < 4; ++v) {
+                    double cv[4];
+                    for (int q = 0; q < n; ++q) cv[q] = cand[q][v];
+                    res[v] = biased(cv, omc, n);
+                }
+            }
+            const double sc = l < 2 ? hi : hi * hi;
+            for (int v = 0; v < 4; ++v) coef_out[((size_t)v * 5 + l) * T + i] = sc * res[v];
         }
         /* safeguard at the cell's face Gauss points */
         const int bad = !physical_at_gauss_points(m, w, coef_out, i);

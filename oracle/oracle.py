@@ -43,7 +43,7 @@ class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("mu", C.c_double), ("cls_w", C.c_double),
                 ("gmres_m", C.c_int), ("gmres_maxit", C.c_int), ("gmres_rtol", C.c_double),
                 ("tau2_exact", C.c_int), ("slope0_mode", C.c_int), ("limiter", C.c_int), ("second_order", C.c_int),
-                ("prandtl", C.c_double)]
+                ("prandtl", C.c_double), ("limit_char", C.c_int)]
 
 
 def _load():
@@ -56,6 +56,8 @@ def _load():
         lib.or_mesh_new.restype = P
         lib.or_mesh_new.argtypes = [P, I64, P, I64, P, P, I64, P, C.POINTER(Params), C.POINTER(I)]
         lib.or_mesh_free.argtypes = [P]
+        lib.or_char_basis.argtypes = [P, C.c_double, C.c_double, C.c_double, P, P]
+        lib.or_char_basis.restype = None
         lib.or_mesh_ndof.restype = I64
         lib.or_mesh_ndof.argtypes = [P]
         lib.or_cell_geometry.argtypes = [P, P]
@@ -261,6 +263,16 @@ def point_flux(wl: np.ndarray, wr: np.ndarray, dt: float, **prm):
     aux = np.zeros(16)
     st = lib.or_point_flux(_ptr(wl), _ptr(wr), float(dt), C.byref(p), _ptr(f), _ptr(aux))
     return f, aux, int(st)
+
+
+def char_basis(W, gamma: float = 1.4, nx: float = 1.0, ny: float = 0.0):
+    """(R, L) eigenvectors of the Euler flux Jacobian along (nx, ny) at W (4,)."""
+    lib = _load()
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    R = np.zeros(16)
+    L = np.zeros(16)
+    lib.or_char_basis(_ptr(W), float(gamma), float(nx), float(ny), _ptr(R), _ptr(L))
+    return R.reshape(4, 4), L.reshape(4, 4)
 
 
 def state_slopes(w: np.ndarray, gamma: float = 1.4) -> np.ndarray:

@@ -61,7 +61,7 @@ gks_status check_config(const gks_config &c)
     ok = ok && c.inner_rtol > 0.0 && c.inner_rtol < 1.0 && c.prandtl > 0.0;
     ok = ok && (c.second_order == 0 || c.second_order == 1);
     ok = ok && (c.no_graphs == 0 || c.no_graphs == 1);
-    for (int q = 0; q < 1; ++q) ok = ok && c.reserved[q] == 0;
+    ok = ok && (c.limit_char == 0 || c.limit_char == 1);
     if (!ok) {
         set_error("invalid gks_config");
         return GKS_EINVAL;

@@ -19,6 +19,10 @@
 //    polynomial has rho <= 0 or p <= 0 at one of its face Gauss points; a
 //    limited cell whose polynomial still has one keeps its cell average only
 //    (all coefficients zero);
+//  - characteristic variables (limit_char = 1; Sec. IV.B compares them with the
+//    conservative ones): each derivative row is limited in the eigenvector
+//    basis of the Euler flux Jacobian at the cell average, along x for d/dx and
+//    d2/dx2, y for d/dy and d2/dy2 and the diagonal for d2/dxdy;
 //  - robust mode (limiter = 2, not in the paper): a limited cell keeps its
 //    cell average only (first order), for contacts with density ratios near
 //    10, where the DWBAP polynomials let cell averages turn negative.
@@ -41,6 +45,27 @@ __device__ __forceinline__ double poly_value(const DeviceMesh &d, const double *
     const double qx = dx * dx - d.mxx[c], qxy = dx * dy - d.mxy[c], qy = dy * dy - d.myy[c];
     return w[v * T + c] + x[(v * 5 + 0) * T + c] * dx + x[(v * 5 + 1) * T + c] * dy +
            0.5 * x[(v * 5 + 2) * T + c] * qx + x[(v * 5 + 3) * T + c] * qxy + 0.5 * x[(v * 5 + 4) * T + c] * qy;
+}
+
+// Right (columns) and left (rows) eigenvectors, row-major 4x4, of the Jacobian
+// of the Euler flux along the unit direction (nx, ny) at the conservative
+// state W (eigenvalues q_n - c, q_n, q_n, q_n + c).
+__device__ __forceinline__ void char_basis(const double *W, double gamma, double nx, double ny, double *R, double *L)
+{
+    const double rho = W[0], u = W[1] / rho, v = W[2] / rho;
+    const double ke = 0.5 * (u * u + v * v);
+    const double p = (gamma - 1.0) * (W[3] - rho * ke);
+    const double c = sqrt(gamma * p / rho), H = (W[3] + p) / rho;
+    const double qn = u * nx + v * ny, qt = -u * ny + v * nx;
+    const double b1 = (gamma - 1.0) / (c * c), b2 = b1 * ke, ic = 1.0 / c;
+    R[0] = 1.0;             R[1] = 1.0; R[2] = 0.0; R[3] = 1.0;
+    R[4] = u - c * nx;      R[5] = u;   R[6] = -ny; R[7] = u + c * nx;
+    R[8] = v - c * ny;      R[9] = v;   R[10] = nx; R[11] = v + c * ny;
+    R[12] = H - qn * c;     R[13] = ke; R[14] = qt; R[15] = H + qn * c;
+    L[0] = 0.5 * (b2 + qn * ic);  L[1] = -0.5 * (b1 * u + nx * ic); L[2] = -0.5 * (b1 * v + ny * ic); L[3] = 0.5 * b1;
+    L[4] = 1.0 - b2;              L[5] = b1 * u;                    L[6] = b1 * v;                    L[7] = -b1;
+    L[8] = -qt;                   L[9] = -ny;                       L[10] = nx;                       L[11] = 0.0;
+    L[12] = 0.5 * (b2 - qn * ic); L[13] = -0.5 * (b1 * u - nx * ic); L[14] = -0.5 * (b1 * v - ny * ic); L[15] = 0.5 * b1;
 }
 
 // u_0 tan(sum_j om_j atan(u_j / u_0)) over the first n of 4 candidates.
@@ -81,7 +106,7 @@ __device__ __forceinline__ bool physical_gp(const DeviceMesh &d, const double *_
 
 __global__ void __launch_bounds__(kBlock) k_limit(const DeviceMesh d, const double *__restrict__ w,
                                                   const double *__restrict__ x, double *xl,
-                                                  int32_t *__restrict__ flag, double gamma, int robust)
+                                                  int32_t *__restrict__ flag, double gamma, int robust, int charm)
 {
     const int64_t T = d.T, F = d.F;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -185,47 +210,78 @@ __global__ void __launch_bounds__(kBlock) k_limit(const DeviceMesh d, const doub
         ddy[s] = -oyj[s] * hi / hj[s];
         k2[s] = d.kord[nbj[s]] == 2;
     }
-    for (int v = 0; v < 4; ++v) {
-        // second derivatives (physical), Eq. (34) over the k = 2 candidates
-        if (ki == 2) {
-            for (int l = 2; l < 5; ++l) {
-                double cand[4] = {0.0, 0.0, 0.0, 0.0}, omc[4] = {0.0, 0.0, 0.0, 0.0};
-                cand[0] = x[(v * 5 + l) * T + i] / (hi * hi);
-                omc[0] = om[0];
-                double os = om[0];
-                int n = 1;
-#pragma unroll
-                for (int s = 0; s < 3; ++s) {
-                    if (s >= J || !k2[s]) continue;
-                    const double c = x[(v * 5 + l) * T + nbj[s]] / (hj[s] * hj[s]);
-                    if (n == 1) { cand[1] = c; omc[1] = om[s + 1]; }
-                    else if (n == 2) { cand[2] = c; omc[2] = om[s + 1]; }
-                    else { cand[3] = c; omc[3] = om[s + 1]; }
-                    os += om[s + 1];
-                    ++n;
-                }
-#pragma unroll
-                for (int q = 0; q < 4; ++q) omc[q] /= os;
-                xl[(v * 5 + l) * T + i] = hi * hi * biased_mean(cand, omc, n);
-            }
-        } else {
-            for (int l = 2; l < 5; ++l) xl[(v * 5 + l) * T + i] = x[(v * 5 + l) * T + i];
+    // candidates of every derivative row l, in physical units: cand[c][v] for the
+    // cell's own polynomial (c = 0) and the neighbours' (at r_i; for the second
+    // derivatives only neighbours with k = 2, weights renormalised)
+    const double Wi[4] = {w[i], w[T + i], w[2 * T + i], w[3 * T + i]};
+    for (int l = 0; l < 5; ++l) {
+        if (l >= 2 && ki != 2) {
+            for (int v = 0; v < 4; ++v) xl[(v * 5 + l) * T + i] = x[(v * 5 + l) * T + i];
+            continue;
         }
-        // first derivatives at the centroid: own polynomial and the neighbours' at r_i
-        double gx[4] = {0.0, 0.0, 0.0, 0.0}, gy[4] = {0.0, 0.0, 0.0, 0.0};
-        gx[0] = x[(v * 5 + 0) * T + i] / hi;
-        gy[0] = x[(v * 5 + 1) * T + i] / hi;
+        double cand[4][4] = {}, omc[4] = {0.0, 0.0, 0.0, 0.0};
+        const double sc = l < 2 ? hi : hi * hi;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) cand[0][v] = x[(v * 5 + l) * T + i] / sc;
+        omc[0] = om[0];
+        double os = om[0];
+        int n = 1;
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
-            if (s >= J) continue;
+            if (s >= J || (l >= 2 && !k2[s])) continue;
             const int64_t j = nbj[s];
-            const double u1 = x[(v * 5 + 0) * T + j], u2 = x[(v * 5 + 1) * T + j], u3 = x[(v * 5 + 2) * T + j];
-            const double u4 = x[(v * 5 + 3) * T + j], u5 = x[(v * 5 + 4) * T + j];
-            gx[s + 1] = (u1 + u3 * ddx[s] + u4 * ddy[s]) / hj[s];
-            gy[s + 1] = (u2 + u4 * ddx[s] + u5 * ddy[s]) / hj[s];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                double c;
+                if (l >= 2) {
+                    c = x[(v * 5 + l) * T + j] / (hj[s] * hj[s]);
+                } else {
+                    const double ua = x[(v * 5 + l) * T + j];          // u1 (l = 0) or u2 (l = 1)
+                    const double ub = x[(v * 5 + 2 + l) * T + j];      // u3 or u4
+                    const double uc = x[(v * 5 + 3 + l) * T + j];      // u4 or u5
+                    c = (ua + ub * ddx[s] + uc * ddy[s]) / hj[s];
+                }
+                if (n == 1) cand[1][v] = c;
+                else if (n == 2) cand[2][v] = c;
+                else cand[3][v] = c;
+            }
+            if (n == 1) omc[1] = om[s + 1];
+            else if (n == 2) omc[2] = om[s + 1];
+            else omc[3] = om[s + 1];
+            os += om[s + 1];
+            ++n;
         }
-        xl[(v * 5 + 0) * T + i] = hi * biased_mean(gx, om, J + 1);
-        xl[(v * 5 + 1) * T + i] = hi * biased_mean(gy, om, J + 1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) omc[q] /= os;
+        double res[4];
+        if (charm) {
+            // characteristic variables along x (d/dx, d2/dx2), y (d/dy, d2/dy2), the diagonal (d2/dxdy)
+            const double nx = l == 1 || l == 4 ? 0.0 : (l == 3 ? 0.70710678118654752 : 1.0);
+            const double ny = l == 0 || l == 2 ? 0.0 : (l == 3 ? 0.70710678118654752 : 1.0);
+            double Rm[16], Lm[16];
+            char_basis(Wi, gamma, nx, ny, Rm, Lm);
+            double lim[4];
+#pragma unroll
+            for (int a2 = 0; a2 < 4; ++a2) {
+                double ch[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    ch[q] = Lm[4 * a2] * cand[q][0] + Lm[4 * a2 + 1] * cand[q][1] + Lm[4 * a2 + 2] * cand[q][2] +
+                            Lm[4 * a2 + 3] * cand[q][3];
+                lim[a2] = biased_mean(ch, omc, n);
+            }
+#pragma unroll
+            for (int a2 = 0; a2 < 4; ++a2)
+                res[a2] = Rm[4 * a2] * lim[0] + Rm[4 * a2 + 1] * lim[1] + Rm[4 * a2 + 2] * lim[2] + Rm[4 * a2 + 3] * lim[3];
+        } else {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const double cv[4] = {cand[0][v], cand[1][v], cand[2][v], cand[3][v]};
+                res[v] = biased_mean(cv, omc, n);
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) xl[(v * 5 + l) * T + i] = sc * res[v];
     }
 
     // ---- safeguard at the cell's face Gauss points
@@ -256,7 +312,8 @@ gks_status launch_limiter(gks_mesh *m, const double *w, const double *x, cudaStr
     }
     if (d.T == 0) return GKS_OK;
     const unsigned nb = (unsigned)((d.T + kBlock - 1) / kBlock);
-    k_limit<<<nb, kBlock, 0, s>>>(d, w, x, m->wk.xl, m->wk.lflag, m->cfg.gamma, m->cfg.limiter == 2 ? 1 : 0);
+    k_limit<<<nb, kBlock, 0, s>>>(d, w, x, m->wk.xl, m->wk.lflag, m->cfg.gamma, m->cfg.limiter == 2 ? 1 : 0,
+                                  m->cfg.limit_char);
     note_launch();
     GKS_CUDA(cudaGetLastError());
     return GKS_OK;

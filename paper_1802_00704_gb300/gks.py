@@ -42,7 +42,7 @@ class Config(C.Structure):
                 ("precision", C.c_int32), ("precond", C.c_int32), ("ilu_sweeps", C.c_int32),
                 ("tau2_exact", C.c_int32), ("limiter", C.c_int32),
                 ("basis_fp32", C.c_int32), ("warm_extrap", C.c_int32), ("second_order", C.c_int32),
-                ("no_graphs", C.c_int32), ("reserved", C.c_int32 * 1),
+                ("no_graphs", C.c_int32), ("limit_char", C.c_int32),
                 ("inner_rtol", C.c_double), ("prandtl", C.c_double)]
 
 

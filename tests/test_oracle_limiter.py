@@ -101,3 +101,57 @@ def test_robust_mode_converges_to_exact_riemann(oracle_mod):
         return np.sum(cg["area"] * np.abs(w[0] - ex[0])) / cg["area"].sum()
     e1, e2 = l1(40, 3), l1(80, 6)
     assert e2 < e1 / 1.3, (e1, e2)
+
+
+def test_char_basis_diagonalises_the_euler_jacobian(oracle_mod):
+    """The eigenvectors used for characteristic limiting: L R = I and
+    R diag(q_n - c, q_n, q_n, q_n + c) L equals the Jacobian of the Euler flux
+    along n (central differences of the flux)."""
+    g = 1.4
+    W = np.array([1.3, 1.3 * 0.4, -1.3 * 0.7, 2.5 / 0.4 + 0.5 * 1.3 * (0.4 ** 2 + 0.7 ** 2)])
+
+    def flux(W, nx, ny):
+        rho, u, v = W[0], W[1] / W[0], W[2] / W[0]
+        p = (g - 1) * (W[3] - 0.5 * rho * (u * u + v * v))
+        qn = u * nx + v * ny
+        return np.array([rho * qn, rho * u * qn + p * nx, rho * v * qn + p * ny, (W[3] + p) * qn])
+
+    for nx, ny in [(1.0, 0.0), (0.0, 1.0), (0.6, 0.8)]:
+        R, L = oracle_mod.char_basis(W, g, nx, ny)
+        A = np.zeros((4, 4))
+        for k in range(4):
+            d = np.zeros(4)
+            d[k] = 1e-6 * max(1.0, abs(W[k]))
+            A[:, k] = (flux(W + d, nx, ny) - flux(W - d, nx, ny)) / (2 * d[k])
+        rho, u, v = W[0], W[1] / W[0], W[2] / W[0]
+        c = np.sqrt(g * (g - 1) * (W[3] - 0.5 * rho * (u * u + v * v)) / rho)
+        qn = u * nx + v * ny
+        assert np.max(np.abs(L @ R - np.eye(4))) < 1e-14
+        assert np.max(np.abs(R @ np.diag([qn - c, qn, qn, qn + c]) @ L - A)) < 1e-8
+
+
+def test_characteristic_limiting_on_sod(oracle_mod):
+    """DWBAP in characteristic variables: smooth data untouched, and the Sod
+    run stays physical and converges to the exact solution under refinement."""
+    c = I.advection_case(16)
+    om = oracle_mod.OracleMesh(c.mesh, limiter=1, limit_char=1)
+    coef, _, _, _ = om.cls_solve(c.w0)
+    lim, flag = om.limit(c.w0, coef)
+    assert np.all(flag == 0) and np.array_equal(lim, coef)
+
+    def l1(nx, ny):
+        c = I.sod_case(nx, ny)
+        om = oracle_mod.OracleMesh(c.mesh, limiter=1, limit_char=1)
+        w, t = c.w0.copy(), 0.0
+        while t < 0.2 - 1e-14:
+            dt = min(om.cfl_dt(w), 0.2 - t)
+            assert om.step(w, dt).status == 0
+            t += dt
+        p = 0.4 * (w[3] - 0.5 * (w[1] ** 2 + w[2] ** 2) / w[0])
+        assert np.all(w[0] > 0) and np.all(p > 0)
+        cg = om.cell_geometry()
+        ex = exact_riemann(cg["cx"], 0.2, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1))
+        return np.sum(cg["area"] * np.abs(w[0] - ex[0])) / cg["area"].sum()
+
+    e1, e2 = l1(40, 3), l1(80, 6)
+    assert e2 < e1 / 1.4 and e2 < 0.01, (e1, e2)
