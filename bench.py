@@ -435,7 +435,8 @@ def run_batch(args, world, rank, local):
 
     def leg(prec_mixed: bool, clocks: bool):
         b = gks.GksMesh.batch([c.mesh for c in cases], precision=gks.MIXED if prec_mixed else gks.FP64,
-                              limiter=2, gmres_m=12, warm_extrap=WARM[args.warm])
+                              limiter=2, gmres_m=12, warm_extrap=WARM[args.warm],
+                              basis_fp32=int(prec_mixed and args.basis == "fp32"))
         w = torch.from_numpy(w0.copy()).to(dev)
         tune = b.autotune(w, trial_steps=1) if args.tune else None
         r = b.batch_run(w, max_steps=args.warmup)
@@ -484,7 +485,8 @@ def run_batch(args, world, rank, local):
     for q, nm in enumerate(names):
         ent = {"ms": round(prof["ms"][q], 3), "launch_groups": prof["n"][q]}
         if nm != "flux" and prof["ms"][q] > 0:
-            by = class_bytes(nm, prof, T, F, args.steps, knobs["ilu_sweeps"], False, mixed, False)
+            by = class_bytes(nm, prof, T, F, args.steps, knobs["ilu_sweeps"], False, mixed,
+                             mixed and args.basis == "fp32")
             gbs = by / (prof["ms"][q] / 1e3) / 1e9
             ent.update({"bytes": by, "gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 3)})
         classes[nm] = ent
@@ -500,6 +502,7 @@ def run_batch(args, world, rank, local):
         "config": {"workload": f"batch of {len(cases)} cases (log-uniform 1e3-2e5 triangles; advection / "
                                f"Riemann strips), {T} triangles, {F} faces, robust limiter, GMRES(12) rtol 1e-12",
                    "n_tri": T, "n_face": F, "n_cases": len(cases), "precision": args.precision,
+                   "krylov_basis": "fp32" if mixed and args.basis == "fp32" else "fp64",
                    "autotuned": bool(args.tune), "knobs": knobs, "failed_cases": int(np.sum(stat != 0)),
                    "l2": "inputs larger than L2", "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"kernel": "k_face_flux", "launches": prof["n"][0], "avg_ms": per_launch_ms, "bound": "alu",
@@ -554,8 +557,9 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison leg")
     ap.add_argument("--sweeps", type=int, default=2)
-    ap.add_argument("--basis", default="fp64", choices=["fp32", "fp64"],
-                    help="storage of the Krylov basis in the mixed path (arithmetic stays FP64)")
+    ap.add_argument("--basis", default="fp32", choices=["fp32", "fp64"],
+                    help="Krylov basis of the mixed path's inner cycles: FP32 (FP32 Gram-Schmidt arithmetic, "
+                         "FP64 sums across threads) or FP64")
     ap.add_argument("--limiter", action="store_true", help="shock detector + DWBAP limiter on")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the autotuner (ilu_sweeps, warm start, inner tolerance) before the warm-up")

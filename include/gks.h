@@ -125,9 +125,12 @@ typedef struct gks_config {
     int32_t second_order;  /* 1: second-order variant, k_i = 1 (linear CLS
                               reconstruction) for every cell (the paper's second- vs
                               third-order comparison, Sec. IV)                        */
-    int32_t no_graphs;     /* 1: launch the CLS solve's kernels one by one instead of
-                              replaying CUDA graphs of its fixed launch sequences
-                              (same kernels, same order, same results)                */
+    int32_t no_graphs;     /* how the CLS solve is launched (same kernels, same order,
+                              same results): 0 one CUDA graph per solve whose while
+                              and if nodes take the GMRES cycle and Arnoldi decisions
+                              on the device (no host round trip); 1 the kernels one
+                              by one, the host reading the stop flags after every
+                              Arnoldi step; 2 as 1 but replaying a graph per step     */
     int32_t limit_char;    /* 1: the DWBAP limiter works on characteristic variables
                               (eigenvectors of the Euler flux Jacobian at the cell
                               average, Sec. IV.B) instead of conservative ones        */

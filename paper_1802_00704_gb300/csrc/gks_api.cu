@@ -60,7 +60,7 @@ gks_status check_config(const gks_config &c)
     ok = ok && c.warm_extrap >= 0 && c.warm_extrap <= 2;
     ok = ok && c.inner_rtol > 0.0 && c.inner_rtol < 1.0 && c.prandtl > 0.0;
     ok = ok && (c.second_order == 0 || c.second_order == 1);
-    ok = ok && (c.no_graphs == 0 || c.no_graphs == 1);
+    ok = ok && c.no_graphs >= 0 && c.no_graphs <= 2;
     ok = ok && (c.limit_char == 0 || c.limit_char == 1);
     if (!ok) {
         set_error("invalid gks_config");
@@ -499,6 +499,7 @@ gks_status gks_profile_begin(gks_mesh *m, int32_t class_mask)
         set_error("gks_profile_begin: bad argument");
         return GKS_EINVAL;
     }
+    flush_solve_counters(m);                        // work of earlier calls stays out
     m->prof.mask = class_mask;
     m->prof.used = 0;
     m->prof.cls.clear();
@@ -514,6 +515,7 @@ gks_status gks_profile_end(gks_mesh *m, gks_profile *out)
     }
     DeviceGuard g(m->device);
     std::memset(out, 0, sizeof(*out));
+    flush_solve_counters(m);
     gks_profiler &p = m->prof;
     for (size_t q = 0; q < p.cls.size(); ++q) {
         GKS_CUDA(cudaEventSynchronize(p.events[2 * q + 1]));

@@ -269,7 +269,11 @@ __global__ void k_ilu_bwd(DeviceMesh d, const TM *__restrict__ Pg, const TM *__r
 // four cells each (64 apart), all 40 loads issued before the sums (read-only
 // kernels need many bytes in flight); the warp sums then the two warps of a
 // variable give part[blk][v][k].  Fixed order: the sums are deterministic.
-// TB: type of the stored basis; products and sums are FP64.
+// TB: type of the stored basis.  An FP64 basis is multiplied and summed in
+// FP64; an FP32 basis (the inner cycles of the mixed mode) in FP32 within a
+// thread (20 products), each thread's sum then widened once and summed across
+// threads and blocks in FP64, so that the FP64 pipe sees one conversion per
+// 20 products instead of a DFMA per product.
 template <typename TB>
 __global__ void __launch_bounds__(kDotThreads, 3) k_dots(int64_t T, int64_t nblk, const TB *__restrict__ V,
                                                          const TB *__restrict__ w, double *__restrict__ part,
@@ -285,13 +289,14 @@ __global__ void __launch_bounds__(kDotThreads, 3) k_dots(int64_t T, int64_t nblk
     const TB *wv = w + (int64_t)v * ND * T;
     for (int64_t b = blockIdx.y; b < nblk; b += gridDim.y) {
         const int64_t c0 = b * kBlock + t;
-        double s = 0.0;
+        TB st = TB(0);
 #pragma unroll
         for (int q = 0; q < kCells; ++q) {
             const int64_t i = c0 + q * kPerVar;
 #pragma unroll
-            for (int l = 0; l < ND; ++l) s += i < T ? double(vk[l * T + i]) * double(wv[l * T + i]) : 0.0;
+            for (int l = 0; l < ND; ++l) st = i < T ? fma(vk[l * T + i], wv[l * T + i], st) : st;
         }
+        double s = double(st);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0) sh[warp] = s;
         __syncthreads();
@@ -302,18 +307,24 @@ __global__ void __launch_bounds__(kDotThreads, 3) k_dots(int64_t T, int64_t nblk
 
 // w -= sum_{k<=j} c[s][k] V_k for running systems s = case * 4 + v (c: the
 // Gram-Schmidt coefficients of the unnormalised basis), w = 0 for the others;
-// optional partial |w|^2 per block.
+// optional partial |w|^2 per block.  The arithmetic is in the basis precision
+// TB (FP32 for the inner cycles of the mixed mode); the block's coefficients
+// are rounded to TB once, in shared memory.
 template <typename TB>
 __global__ void k_orth_update(DeviceMesh d, const TB *__restrict__ V, TB *__restrict__ w, int j,
                               const double *__restrict__ hc, int hstride, const int32_t *__restrict__ ctl, int ns,
                               double *__restrict__ part, int pstride, int want_norm)
 {
     __shared__ double sh[32 * NV];
+    __shared__ TB shc[NV][kMaxRestart];
     const int64_t T = d.T;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t vs = (int64_t)NX * T;
     const int c = d.blk_case[blockIdx.x];
-    double nrm[NV] = {0, 0, 0, 0};
+    for (int q = threadIdx.x; q < NV * (j + 1); q += blockDim.x)
+        shc[q / (j + 1)][q % (j + 1)] = TB(hc[(4 * c + q / (j + 1)) * hstride + q % (j + 1)]);
+    __syncthreads();
+    TB nrm[NV] = {0, 0, 0, 0};
     if (i < T) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
@@ -323,27 +334,27 @@ __global__ void k_orth_update(DeviceMesh d, const TB *__restrict__ V, TB *__rest
                 for (int l = 0; l < ND; ++l) w[(v * ND + l) * T + i] = TB(0);
                 continue;
             }
-            double wv[ND];
+            TB wv[ND];
 #pragma unroll
-            for (int l = 0; l < ND; ++l) wv[l] = double(w[(v * ND + l) * T + i]);
+            for (int l = 0; l < ND; ++l) wv[l] = w[(v * ND + l) * T + i];
             for (int k = 0; k <= j; ++k) {
-                const double hk = hc[sy * hstride + k];
+                const TB hk = shc[v][k];
                 const TB *vk = V + k * vs;
 #pragma unroll
-                for (int l = 0; l < ND; ++l) wv[l] -= hk * double(vk[(v * ND + l) * T + i]);
+                for (int l = 0; l < ND; ++l) wv[l] = fma(-hk, vk[(v * ND + l) * T + i], wv[l]);
             }
 #pragma unroll
             for (int l = 0; l < ND; ++l) {
-                const TB st = TB(wv[l]);                // the norm is that of the stored vector
-                w[(v * ND + l) * T + i] = st;
-                nrm[v] += double(st) * double(st);
+                w[(v * ND + l) * T + i] = wv[l];
+                nrm[v] = fma(wv[l], wv[l], nrm[v]);
             }
         }
     }
     if (want_norm) {
-        block_sum4(nrm, sh);
+        double nd[NV] = {double(nrm[0]), double(nrm[1]), double(nrm[2]), double(nrm[3])};
+        block_sum4(nd, sh);
         if (threadIdx.x == 0)
-            for (int v = 0; v < NV; ++v) part[(blockIdx.x * NV + v) * pstride + 0] = nrm[v];
+            for (int v = 0; v < NV; ++v) part[(blockIdx.x * NV + v) * pstride + 0] = nd[v];
     }
 }
 
@@ -538,6 +549,31 @@ __global__ void k_any(const int32_t *__restrict__ ctl, int ns, int32_t *flags)
     if (threadIdx.x < 2) flags[threadIdx.x] = sh[threadIdx.x];
 }
 
+// Condition of the device-controlled solve (one block): any system active
+// (which = 0, the cycle loop) or running (which = 1, the next Arnoldi index).
+// Thread 0 counts the run in ctr[slot] (slot >= 0) and sets the handle (set).
+// guard 1 starts the solve's cycle count; guard 2 counts a cycle and ends the
+// loop once more than limit cycles ran (each cycle takes at least one
+// iteration of every active system, which stops at maxit, so the limit
+// maxit + 1 is a backstop that a correct solve never reaches).
+__global__ void k_cond(const int32_t *__restrict__ ctl, int ns, int which, cudaGraphConditionalHandle h, int set,
+                       int64_t *ctr, int slot, int guard, int64_t limit)
+{
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    int a = 0;
+    for (int sy = threadIdx.x; sy < ns; sy += blockDim.x) a |= ctl[(which ? kCtlRunning : kCtlActive) * ns + sy];
+    if (a) atomicOr(&any, 1);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    unsigned v = any ? 1u : 0u;
+    if (slot >= 0) ctr[slot] += 1;
+    if (guard == 1) ctr[kCtrGuard] = 0;
+    if (guard == 2 && ++ctr[kCtrGuard] > limit) v = 0u;
+    if (set) cudaGraphSetConditional(h, v);
+}
+
 // g = beta e_1 for active systems.
 __global__ void k_init_g(double *g, int m, const double *__restrict__ beta, const int32_t *__restrict__ ctl, int ns)
 {
@@ -654,17 +690,38 @@ gks_status enqueue_flags(gks_mesh *m, cudaStream_t s)
     return GKS_OK;
 }
 
+// Add what the device-controlled solves ran since the last call (counters
+// already copied to h_ctr, stream synchronised) to the launch and work totals.
+void take_counters(gks_mesh *m)
+{
+    SolveGraphs &g = *m->graphs;
+    for (int q = 0; q < kCtrLen; ++q) {
+        const int64_t d = g.h_ctr[q] - g.ctr_seen[q];
+        g.ctr_seen[q] = g.h_ctr[q];
+        if (q < kCtrCycles && d > 0) {
+            if (q < (int)g.whole_iter_launches.size()) g_launches.fetch_add(d * g.whole_iter_launches[q]);
+            m->prof.arnoldi += d;
+            m->prof.precond += d;
+            m->prof.arnoldi_jsum += d * (q + 1);
+        } else if (q == kCtrCycles && d > 0) {
+            g_launches.fetch_add(d * g.whole_cycle_launches);
+            m->prof.residuals += d;
+        }
+    }
+}
+
 // Graphs are used unless disabled or the profiler (events between kernels) is on;
 // a change of a knob baked into the captured kernel arguments drops them.
 bool prepare_graphs(gks_mesh *m)
 {
-    if (m->cfg.no_graphs || m->prof.mask) return false;
+    if (m->cfg.no_graphs == 1 || m->prof.mask) return false;
     if (!m->graphs) m->graphs = new SolveGraphs;
     SolveGraphs &g = *m->graphs;
     if (g.disabled) return false;
     const gks_config &c = m->cfg;
     if (g.sweeps != c.ilu_sweeps || g.precond != c.precond || g.maxit != c.gmres_maxit || g.eta != c.inner_rtol ||
         g.rtol != c.gmres_rtol || (int)g.iter.size() != m->wk.m) {
+        if (g.whole) flush_solve_counters(m);
         destroy_graph_execs(&g);
         g.sweeps = c.ilu_sweeps;
         g.precond = c.precond;
@@ -727,6 +784,133 @@ gks_status run_part(gks_mesh *m, bool use_graph, cudaGraphExec_t *exec, int64_t 
     return GKS_OK;
 }
 
+// Append enq(stream) to graph g after the nodes deps[0..nd) by capture on the
+// private stream; *sink = the last captured node, *nl = kernels captured.
+template <typename F>
+gks_status capture_into(gks_mesh *m, cudaGraph_t g, const cudaGraphNode_t *deps, size_t nd, cudaGraphNode_t *sink,
+                        int64_t *nl, F &&enq)
+{
+    SolveGraphs &G = *m->graphs;
+    if (!G.cap) GKS_CUDA(cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking));
+    const int64_t l0 = g_launches.load();
+    GKS_CUDA(cudaStreamBeginCaptureToGraph(G.cap, g, deps, nullptr, nd, cudaStreamCaptureModeThreadLocal));
+    const gks_status st = enq(G.cap);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaGraphNode_t *tail = nullptr;
+    size_t nt = 0;
+    const cudaError_t e = cudaStreamGetCaptureInfo(G.cap, &cs, nullptr, nullptr, &tail, nullptr, &nt);
+    const cudaGraphNode_t last = (e == cudaSuccess && nt == 1) ? tail[0] : nullptr;
+    cudaGraph_t out = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(G.cap, &out);
+    const int64_t n = g_launches.load() - l0;
+    g_launches.fetch_sub(n, std::memory_order_relaxed);   // captured, not run
+    if (st != GKS_OK || e != cudaSuccess || e2 != cudaSuccess || !last) {
+        cudaGetLastError();
+        return st != GKS_OK ? st : GKS_ECUDA;
+    }
+    *sink = last;
+    *nl = n;
+    return GKS_OK;
+}
+
+// Add a conditional node (if / while, one body) on handle h after dep.
+gks_status add_cond(cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHandle h,
+                    cudaGraphConditionalNodeType type, cudaGraphNode_t *node, cudaGraph_t *body)
+{
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = type;
+    p.conditional.size = 1;
+    GKS_CUDA(cudaGraphAddNode(node, g, &dep, nullptr, 1, &p));
+    *body = p.conditional.phGraph_out[0];
+    return GKS_OK;
+}
+
+// The device-controlled solve as one executable graph:
+//   start; c = any active
+//   while (c) { i_0 = any running
+//               if (i_0) { Arnoldi 0; i_1 = any running
+//                          if (i_1) { Arnoldi 1; ... if (i_{m-1}) { Arnoldi m-1 } } }
+//               restart; c = any active (and within the cycle limit) }
+// The condition kernels replace the host flags of the per-part graphs; the
+// conditions of an index are only evaluated once the one before it has run.
+template <typename SB, typename IB, typename RB>
+gks_status build_whole(gks_mesh *m, cudaStream_t s, SB &&start_body, IB &&iter_body, RB &&restart_body)
+{
+    SolveGraphs &G = *m->graphs;
+    Work &k = m->wk;
+    const int ns = k.ns, mm = k.m;
+    const int64_t limit = (int64_t)m->cfg.gmres_maxit + 1;
+    if (!G.ctr) {
+        GKS_CUDA(cudaMalloc(&G.ctr, sizeof(int64_t) * kCtrLen));
+        GKS_CUDA(cudaMallocHost(&G.h_ctr, sizeof(int64_t) * kCtrLen));
+        GKS_CUDA(cudaMemsetAsync(G.ctr, 0, sizeof(int64_t) * kCtrLen, s));
+        G.ctr_seen.assign(kCtrLen, 0);
+    }
+    int64_t *ctr = G.ctr;
+    const int32_t *ctl = k.ctl;
+    cudaGraph_t top = nullptr;
+    GKS_CUDA(cudaGraphCreate(&top, 0));
+    gks_status st = GKS_OK;
+    std::vector<int64_t> nl_iter(mm, 0);
+    int64_t nl_start = 0, nl_c0 = 0, nl_restart = 0;
+    do {
+        cudaGraphConditionalHandle h_outer, h_next;
+        if (cudaGraphConditionalHandleCreate(&h_outer, top, 0, 0) != cudaSuccess) { st = GKS_ECUDA; break; }
+        cudaGraphNode_t sink, wnode, inode;
+        cudaGraph_t wbody, ibody;
+        st = capture_into(m, top, nullptr, 0, &sink, &nl_start, [&](cudaStream_t q) -> gks_status {
+            gks_status r = start_body(q);
+            if (r != GKS_OK) return r;
+            k_cond<<<1, kBlock, 0, q>>>(ctl, ns, 0, h_outer, 1, ctr, -1, 1, limit); note_launch();
+            return GKS_OK;
+        });
+        if (st != GKS_OK || (st = add_cond(top, sink, h_outer, cudaGraphCondTypeWhile, &wnode, &wbody)) != GKS_OK)
+            break;
+        if (cudaGraphConditionalHandleCreate(&h_next, wbody, 0, 0) != cudaSuccess) { st = GKS_ECUDA; break; }
+        st = capture_into(m, wbody, nullptr, 0, &sink, &nl_c0, [&](cudaStream_t q) -> gks_status {
+            k_cond<<<1, kBlock, 0, q>>>(ctl, ns, 1, h_next, 1, ctr, -1, 0, limit); note_launch();
+            return GKS_OK;
+        });
+        if (st != GKS_OK || (st = add_cond(wbody, sink, h_next, cudaGraphCondTypeIf, &inode, &ibody)) != GKS_OK)
+            break;
+        st = capture_into(m, wbody, &inode, 1, &sink, &nl_restart, [&](cudaStream_t q) -> gks_status {
+            gks_status r = restart_body(q);
+            if (r != GKS_OK) return r;
+            k_cond<<<1, kBlock, 0, q>>>(ctl, ns, 0, h_outer, 1, ctr, kCtrCycles, 2, limit); note_launch();
+            return GKS_OK;
+        });
+        if (st != GKS_OK) break;
+        for (int j = 0; j < mm && st == GKS_OK; ++j) {
+            const bool more = j + 1 < mm;
+            if (more && cudaGraphConditionalHandleCreate(&h_next, ibody, 0, 0) != cudaSuccess) {
+                st = GKS_ECUDA;
+                break;
+            }
+            st = capture_into(m, ibody, nullptr, 0, &sink, &nl_iter[j], [&](cudaStream_t q) -> gks_status {
+                gks_status r = iter_body(q, j);
+                if (r != GKS_OK) return r;
+                k_cond<<<1, kBlock, 0, q>>>(ctl, ns, 1, h_next, more ? 1 : 0, ctr, j, 0, limit); note_launch();
+                return GKS_OK;
+            });
+            if (st == GKS_OK && more) st = add_cond(ibody, sink, h_next, cudaGraphCondTypeIf, &inode, &ibody);
+        }
+        if (st != GKS_OK) break;
+        if (cudaGraphInstantiate(&G.whole, top, 0) != cudaSuccess) {
+            G.whole = nullptr;
+            st = GKS_ECUDA;
+        }
+    } while (false);
+    cudaGraphDestroy(top);
+    cudaGetLastError();
+    if (st != GKS_OK) return st;
+    G.whole_start_launches = nl_start;
+    G.whole_cycle_launches = nl_c0 + nl_restart;
+    G.whole_iter_launches = nl_iter;
+    return GKS_OK;
+}
+
 // part[blk][v][k] = partial <V_k, w>, k <= j, per cell block
 template <typename TB>
 gks_status dots(gks_mesh *m, const TB *V, const TB *w, int j, double *part, int ps, cudaStream_t s)
@@ -769,8 +953,9 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
     const double eta = mixed ? m->cfg.inner_rtol : 0.0;
     gks_status st;
 
-    // the three fixed launch sequences; each ends with the flags for the host
-    auto start_part = [&](cudaStream_t q) -> gks_status {
+    // the three fixed launch sequences (the per-part graphs end each with the
+    // flags for the host, the whole-solve graph with a condition kernel)
+    auto start_body = [&](cudaStream_t q) -> gks_status {
         k_rhs<<<nb, kBlock, 0, q>>>(d, k.w, k.b); note_launch();
         // residual r = b - K x, written straight into the basis slot V_0 (v_0 = V_0 / beta)
         k_spmv<double, double, TB><<<nb, kBlock, 0, q>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, V, 1, k.b, k.part, ps);
@@ -782,9 +967,9 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
         k_zero_trivial<<<nb, kBlock, 0, q>>>(d, k.x, k.bnorm); note_launch();
         k_init_g<<<sblocks(ns * (mm + 1)), 128, 0, q>>>(k.g, mm, k.beta, k.ctl, ns); note_launch();
         GKS_CUDA(cudaGetLastError());
-        return enqueue_flags(m, q);
+        return GKS_OK;
     };
-    auto iter_part = [&](cudaStream_t q, int j) -> gks_status {
+    auto iter_body = [&](cudaStream_t q, int j) -> gks_status {
         TB *vj = V + j * vs, *vj1 = V + (j + 1) * vs;
         gks_status st;
         int slot = prof_start(m, kProfIlu, q);
@@ -825,9 +1010,9 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
                                               k.beta, rtol, eta, maxit);
         note_launch();
         GKS_CUDA(cudaGetLastError());
-        return enqueue_flags(m, q);
+        return GKS_OK;
     };
-    auto restart_part = [&](cudaStream_t q) -> gks_status {
+    auto restart_body = [&](cudaStream_t q) -> gks_status {
         k_backsolve<<<sblocks(ns), 128, 0, q>>>(mm, k.H, k.g, k.y, k.ctl, ns); note_launch();
         k_scale_y<<<sblocks(ns), 128, 0, q>>>(mm, k.y, k.vn, k.ctl, ns); note_launch();
         if (mixed)
@@ -843,18 +1028,40 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
         note_launch();
         k_init_g<<<sblocks(ns * (mm + 1)), 128, 0, q>>>(k.g, mm, k.beta, k.ctl, ns); note_launch();
         GKS_CUDA(cudaGetLastError());
-        return enqueue_flags(m, q);
+        return GKS_OK;
     };
+    auto with_flags = [&](cudaStream_t q, gks_status r) { return r != GKS_OK ? r : enqueue_flags(m, q); };
+    auto start_part = [&](cudaStream_t q) { return with_flags(q, start_body(q)); };
+    auto iter_part = [&](cudaStream_t q, int j) { return with_flags(q, iter_body(q, j)); };
+    auto restart_part = [&](cudaStream_t q) { return with_flags(q, restart_body(q)); };
 
     const bool use_graph = prepare_graphs(m);
     SolveGraphs *G = use_graph ? m->graphs : nullptr;
+    bool whole = false;
+    // the whole-solve graph holds every Arnoldi index up front: with the
+    // level-scheduled exact ILU (two launches per level) that is too many nodes
+    // on large meshes, whose per-step graphs are built only for the indices used
+    const bool few_nodes = m->cfg.precond != GKS_PC_ILU_EXACT || m->lvl_lo_ptr.size() + m->lvl_up_ptr.size() <= 256;
+    if (G && few_nodes && !G->disabled && !G->whole_failed && m->cfg.no_graphs != 2) {
+        if (!G->whole && build_whole(m, s, start_body, iter_body, restart_body) != GKS_OK) {
+            G->whole_failed = true;                     // per-part graphs with host control from now on
+            cudaGetLastError();
+        }
+        whole = G->whole != nullptr;
+    }
     cudaGraphExec_t none = nullptr;
     int64_t none_n = 0;
-    if ((st = run_part(m, use_graph, G ? &G->start : &none, G ? &G->start_launches : &none_n, s, start_part)) !=
-        GKS_OK)
-        return st;
-    m->prof.residuals += 1;
-    while (k.h_flags[0]) {
+    if (whole) {
+        GKS_CUDA(cudaGraphLaunch(G->whole, s));
+        g_launches.fetch_add(G->whole_start_launches, std::memory_order_relaxed);
+        m->prof.residuals += 1;
+    } else {
+        if ((st = run_part(m, use_graph, G ? &G->start : &none, G ? &G->start_launches : &none_n, s,
+                           start_part)) != GKS_OK)
+            return st;
+        m->prof.residuals += 1;
+    }
+    while (!whole && k.h_flags[0]) {
         for (int j = 0; j < mm; ++j) {
             m->prof.precond += 1;
             m->prof.arnoldi += 1;
@@ -876,7 +1083,10 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
         GKS_CUDA(cudaMemcpyAsync(it.data(), k.ctl + kCtlIters * ns, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost, s));
         GKS_CUDA(cudaMemcpyAsync(be.data(), k.beta, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));
         GKS_CUDA(cudaMemcpyAsync(bn.data(), k.bnorm, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));
+        if (whole)
+            GKS_CUDA(cudaMemcpyAsync(G->h_ctr, G->ctr, sizeof(int64_t) * kCtrLen, cudaMemcpyDeviceToHost, s));
         GKS_CUDA(cudaStreamSynchronize(s));
+        if (whole) take_counters(m);
         int32_t conv = 1;
         for (int q = 0; q < ns; ++q) {
             const double rr = bn[q] > 0.0 ? be[q] / bn[q] : 0.0;
@@ -905,6 +1115,16 @@ gks_status cls_solve(gks_mesh *m, cudaStream_t s, int32_t *iters, double *relres
     return st;
 }
 
+void flush_solve_counters(gks_mesh *m)
+{
+    SolveGraphs *g = m->graphs;
+    if (!g || !g->ctr) return;
+    if (cudaDeviceSynchronize() == cudaSuccess &&
+        cudaMemcpy(g->h_ctr, g->ctr, sizeof(int64_t) * kCtrLen, cudaMemcpyDeviceToHost) == cudaSuccess)
+        take_counters(m);
+    cudaGetLastError();
+}
+
 void destroy_graph_execs(SolveGraphs *g)
 {
     for (cudaGraphExec_t &e : g->iter)
@@ -914,7 +1134,8 @@ void destroy_graph_execs(SolveGraphs *g)
         }
     if (g->start) cudaGraphExecDestroy(g->start);
     if (g->restart) cudaGraphExecDestroy(g->restart);
-    g->start = g->restart = nullptr;
+    if (g->whole) cudaGraphExecDestroy(g->whole);
+    g->start = g->restart = g->whole = nullptr;
 }
 
 }  // namespace gks

@@ -211,7 +211,7 @@ __global__ void k_to_f32(const double *__restrict__ x, float *__restrict__ y, in
 // MIXED: interface state and leading terms in FP64, slope-carrying terms in FP32.
 // HEAT: Prandtl correction of the energy flux (prandtl != 1).
 template <bool MIXED, bool HEAT>
-__global__ void __launch_bounds__(kFluxBlock) k_face_flux(DeviceMesh d, const double *__restrict__ w,
+__global__ void __launch_bounds__(kFluxBlock, MIXED ? 4 : 1) k_face_flux(DeviceMesh d, const double *__restrict__ w,
                                                           const double *__restrict__ x,
                                                           const float *__restrict__ x32, double dt_const,
                                                           const double *__restrict__ dt_dev, double gamma, double K,

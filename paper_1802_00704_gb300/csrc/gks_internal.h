@@ -129,6 +129,15 @@ struct Work {
 // per Arnoldi index, the restart), captured on first use on a private stream
 // and replayed on the caller's stream; rebuilt when a knob baked into their
 // kernel arguments changes.
+//
+// The whole solve is also built as one graph with device-side control: a
+// while node over the GMRES cycles whose body holds the Arnoldi indices as
+// nested if nodes, their conditions set by one-block kernels from the
+// per-system masks, so a solve needs no host round trip.  Device counters
+// (ctr) record how often each part ran, for the launch and work counts.
+constexpr int kCtrCycles = kMaxRestart;             // ctr[j]: runs of Arnoldi index j; then cycles
+constexpr int kCtrGuard = kMaxRestart + 1;          // cycles of the current solve (loop guard)
+constexpr int kCtrLen = kMaxRestart + 2;
 struct SolveGraphs {
     cudaStream_t cap = nullptr;
     std::vector<cudaGraphExec_t> iter;
@@ -138,8 +147,19 @@ struct SolveGraphs {
     int32_t sweeps = -1, precond = -1, maxit = -1;
     double eta = -1.0, rtol = -1.0;
     bool disabled = false;                          // a capture failed: launch directly
+    // device-controlled whole solve
+    cudaGraphExec_t whole = nullptr;
+    bool whole_failed = false;                      // building it failed: per-part graphs
+    int64_t whole_start_launches = 0, whole_cycle_launches = 0;
+    std::vector<int64_t> whole_iter_launches;       // per Arnoldi index
+    int64_t *ctr = nullptr;                         // [kCtrLen] device counters
+    int64_t *h_ctr = nullptr;                       // pinned mirror
+    std::vector<int64_t> ctr_seen;                  // counts already added to the host totals
 };
 void destroy_graph_execs(SolveGraphs *g);
+// Add the counts of the device-controlled solves run so far to the launch and
+// work totals (synchronises the device).
+void flush_solve_counters(gks_mesh *m);
 
 }  // namespace gks
 

@@ -732,6 +732,8 @@ void free_mesh(gks_mesh *m)
     if (m->graphs) {
         destroy_graph_execs(m->graphs);
         if (m->graphs->cap) cudaStreamDestroy(m->graphs->cap);
+        if (m->graphs->ctr) cudaFree(m->graphs->ctr);
+        if (m->graphs->h_ctr) cudaFreeHost(m->graphs->h_ctr);
         delete m->graphs;
         m->graphs = nullptr;
     }

@@ -141,6 +141,7 @@ extern "C" gks_status gks_autotune(gks_mesh *m, const double *w, int32_t trial_s
     cudaMemsetAsync(m->wk.status, 0, sizeof(int32_t) * m->n_case, s);
     m->wk.nsolve = 0;
     cudaError_t e = cudaStreamSynchronize(s);
+    flush_solve_counters(m);
     if (st == GKS_OK && e != cudaSuccess) {
         set_error("gks_autotune: %s", cudaGetErrorString(e));
         st = GKS_ECUDA;

@@ -69,12 +69,12 @@ def test_fullsize_sampled_fluxes_and_balance(big):
 
 def test_fullsize_mixed_path_as_benchmarked(big):
     """The mixed path with the knobs the benchmark's tuner picks (2 sweeps,
-    quadratic warm start, inner tolerance 1e-4): 4 steps stay within 1e-8
+    quadratic warm start, inner tolerance 1e-4) and its FP32 Krylov basis: 4 steps stay within 1e-8
     relative L1 of the FP64 path, and sampled mixed face fluxes agree with the
     oracle to 1e-7 of the largest flux."""
     c, om, g, G = big
     area = om.cell_geometry()["area"]
-    mx = G.GksMesh(c.mesh, precision=G.MIXED, ilu_sweeps=2, warm_extrap=2, inner_rtol=1e-4)
+    mx = G.GksMesh(c.mesh, precision=G.MIXED, ilu_sweeps=2, warm_extrap=2, inner_rtol=1e-4, basis_fp32=1)
     g.reset_warm_start()
     wm, wf = dev(c.w0), dev(c.w0)
     for _ in range(4):
@@ -104,7 +104,7 @@ def test_config5_batch_sampled_against_oracle():
     oracle.build()
     build.build()
     cases = I.batch_cases(512, workers=16)
-    b = gks.GksMesh.batch([c.mesh for c in cases], precision=gks.MIXED, limiter=2, gmres_m=12)
+    b = gks.GksMesh.batch([c.mesh for c in cases], precision=gks.MIXED, limiter=2, gmres_m=12, basis_fp32=1)
     w = dev(np.ascontiguousarray(np.concatenate([c.w0 for c in cases], axis=1)))
     r = b.batch_run(w, max_steps=3)
     assert r["n_failed"] == 0 and r["steps"] == 3

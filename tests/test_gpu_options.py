@@ -101,24 +101,54 @@ def test_autotune_on_a_batch(G):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_graph_replay_equals_direct_launches(G, precision):
-    """The CLS solve replays CUDA graphs of its fixed launch sequences; with
-    no_graphs = 1 it launches the same kernels one by one.  Same kernels, same
-    order: the states agree bit for bit, and the library counts the same number
-    of kernel launches either way."""
+@pytest.mark.parametrize("basis_fp32", [0, 1])
+def test_device_control_and_graphs_equal_direct_launches(G, precision, basis_fp32):
+    """The CLS solve runs as one CUDA graph whose while / if nodes take the
+    GMRES decisions on the device (no_graphs = 0), as kernels launched one by
+    one with the host reading the stop flags (1), or as per-step graph replays
+    under host control (2).  Same kernels, same order: the states and iteration
+    counts agree bit for bit; 1 and 2 count the same launches, and the device
+    control launches one condition kernel more per GMRES cycle."""
+    if precision == "fp64" and basis_fp32:
+        pytest.skip("the FP32 basis belongs to the mixed mode")
     prec = G.MIXED if precision == "mixed" else G.FP64
     c = I.shock_vortex_case(40, 20)
-    out, counts = [], []
-    for no_graphs in (0, 1):
-        m = G.GksMesh(c.mesh, precision=prec, warm_extrap=2, no_graphs=no_graphs)
+    out, counts, cycles, work = [], [], [], []
+    for mode in (0, 1, 2):
+        m = G.GksMesh(c.mesh, precision=prec, warm_extrap=2, no_graphs=mode, basis_fp32=basis_fp32)
         w = dev(c.w0)
+        m.profile_begin([])
         l0 = G.launch_count()
         its = [m.step(w, 2e-4)["iters"] for _ in range(6)]
         counts.append(G.launch_count() - l0)
+        p = m.profile_end()
+        cycles.append(p["residuals"] - 6)
+        work.append((p["arnoldi"], p["arnoldi_jsum"], p["precond"], p["residuals"]))
         out.append((host(w), its))
-    assert np.array_equal(out[0][0], out[1][0])
-    assert out[0][1] == out[1][1]
-    assert counts[0] == counts[1]
+    for q in (1, 2):
+        assert np.array_equal(out[0][0], out[q][0])
+        assert out[0][1] == out[q][1]
+        assert work[0] == work[q]
+    assert counts[1] == counts[2]
+    assert cycles[0] > 0 and counts[0] == counts[1] + cycles[0]
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_iteration_cap_stops_solve_the_same_way(G, mode):
+    """gmres_maxit below what the tolerance needs: the solve stops at the cap
+    under device and host control alike, reports it (GKS_ENOCONV with the
+    iterations and relative residuals of the cap), and leaves the same state."""
+    c = I.shock_vortex_case(30, 15)
+    res = []
+    for no_graphs in (mode, 1):
+        m = G.GksMesh(c.mesh, gmres_maxit=3, no_graphs=no_graphs)
+        w = dev(c.w0)
+        r = m.step(w, 2e-4, check=False)
+        assert r["status"] == G.GKS_ENOCONV
+        assert max(r["iters"]) == 3 and max(r["relres"]) > 1e-12
+        res.append((host(w), r["iters"], r["relres"]))
+    assert np.array_equal(res[0][0], res[1][0])
+    assert res[0][1] == res[1][1] and res[0][2] == res[1][2]
 
 
 def test_graphs_follow_knob_changes(G):
