@@ -39,6 +39,8 @@ FP64_PEAK_TFLOPS = 4 * 152 * 2.07e9 / 1e12
 # (dadd + dmul + 2 dfma, ncu instruction counters on the 399,424-triangle case;
 # profiles/flux_fp64_shock_vortex_400k.md).
 FLUX_FP64_FLOP_PER_GP = 8392.3
+# event-timed kernel classes of the library's profiler, in its class order
+PROF_NAMES = ["flux", "spmv", "ilu", "orth", "update", "resid", "corr", "ctl"]
 # FP64 and FP32 flops per Gauss point of the mixed flux kernel (same counters,
 # 1,200,168 Gauss points; profiles/flux_mixed_shock_vortex_400k.md).
 FLUX_MIXED_FP64_FLOP_PER_GP = 698.7
@@ -241,6 +243,11 @@ def class_bytes(cls: str, prof: dict, T: int, F: int, steps: int, sweeps: int, e
         return T * (first + sweeps * (fwd + bwd)) * pc
     if cls == "update":                 # w in/out, 1/|Omega|, 3 face slots; each face flux once
         return (T * (8 * 8 + 8 + 12) + F * 4 * 8) * steps
+    if cls == "resid":                  # FP64 b - K x: x (own + neighbour values), operator, b, r (basis)
+        return T * (8 * (15 + 9) + 12 + 20 * 8 + 8 * 8 + 20 * 8 + 20 * sB) * prof["residuals"]
+    if cls == "corr":                   # x += Z y: the cycle's Z vectors, x read and written (FP64)
+        cycles = max(prof["residuals"] - steps, 0)
+        return T * (20 * sZ * n + 20 * 8 * 2 * cycles)
     raise KeyError(cls)
 
 
@@ -278,7 +285,7 @@ def timed_leg(args, case, precision: str, world: int, dev, sample_clocks: bool):
     ms = allmax(world, ev0.elapsed_time(ev1))
     # a second pass of K steps with CUDA events around each kernel class (the
     # events would perturb the timed pass) for the per-class times and work counts
-    m.profile_begin([gks.PROF_FLUX, gks.PROF_SPMV, gks.PROF_ILU, gks.PROF_ORTH, gks.PROF_UPDATE])
+    m.profile_begin(range(gks.PROF_CLASSES))
     m.run(w, max_steps=args.steps)
     torch.cuda.synchronize()
     prof = m.profile_end()
@@ -320,7 +327,7 @@ def run_gks(args, world, rank, local):
 
     # per-class device time (CUDA events on the launching stream) against each class's roof
     prof, info = main["prof"], main["info"]
-    names = ["flux", "spmv", "ilu", "orth", "update"]
+    names = PROF_NAMES
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
     hbm_src = "measured" if hbm_peak else "fallback"
@@ -330,7 +337,7 @@ def run_gks(args, world, rank, local):
     for q, nm in enumerate(names):
         ms_c = prof["ms"][q]
         ent = {"ms": round(ms_c, 3), "launch_groups": prof["n"][q]}
-        if nm != "flux" and ms_c > 0:
+        if nm not in ("flux", "ctl") and ms_c > 0:
             by = class_bytes(nm, prof, T, F, args.steps, main["knobs"]["ilu_sweeps"], exact, mixed, basis32)
             gbs = by / (ms_c / 1e3) / 1e9
             ent.update({"bytes": by, "gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 3)})
@@ -458,7 +465,7 @@ def run_batch(args, world, rank, local):
         barrier(world)
         ck = sampler.stop() if sampler else None
         ms = allmax(world, ev0.elapsed_time(ev1))
-        b.profile_begin([gks.PROF_FLUX, gks.PROF_SPMV, gks.PROF_ILU, gks.PROF_ORTH, gks.PROF_UPDATE])
+        b.profile_begin(range(gks.PROF_CLASSES))
         b.batch_run(w, max_steps=args.steps)
         torch.cuda.synchronize()
         prof = b.profile_end()
@@ -479,12 +486,12 @@ def run_batch(args, world, rank, local):
     torch.cuda.synchronize()
     e2e_value = world * T * args.steps / allmax(world, time.perf_counter() - t0)
     knobs = {"ilu_sweeps": b.cfg.ilu_sweeps, "warm_extrap": b.cfg.warm_extrap, "inner_rtol": b.cfg.inner_rtol}
-    names = ["flux", "spmv", "ilu", "orth", "update"]
+    names = PROF_NAMES
     hbm_peak = measured_peaks().get("hbm_gbs") or HBM_FALLBACK_GBS
     classes = {}
     for q, nm in enumerate(names):
         ent = {"ms": round(prof["ms"][q], 3), "launch_groups": prof["n"][q]}
-        if nm != "flux" and prof["ms"][q] > 0:
+        if nm not in ("flux", "ctl") and prof["ms"][q] > 0:
             by = class_bytes(nm, prof, T, F, args.steps, knobs["ilu_sweeps"], False, mixed,
                              mixed and args.basis == "fp32")
             gbs = by / (prof["ms"][q] / 1e3) / 1e9

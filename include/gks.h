@@ -356,11 +356,17 @@ GKS_EXPORT gks_status gks_autotune(gks_mesh *mesh, const double *w, int32_t tria
 /* Optional CUDA-event timing of kernel classes, for benchmarks.  Bit c of
  * class_mask enables class c: 0 face flux, 1 CLS operator application in
  * GMRES, 2 ILU(0) preconditioner application, 3 Gram-Schmidt orthogonalisation
- * (dot products, updates, reductions), 4 conservative update.  Events are
- * recorded on the stream of each call between begin and end. */
+ * (dot products, updates, reductions), 4 conservative update, 5 FP64 residual
+ * b - K x of the solve's start and restarts (with its norms), 6 correction of
+ * a GMRES cycle (back-substitution, x += Z y), 7 the step's small kernels
+ * (CFL time step, warm start, right-hand side, masks, Givens rotations, stop
+ * conditions).  Events are recorded on the stream of each call between begin
+ * and end; while any class is timed the solve launches its kernels one by one
+ * (events between kernels), so the timed steps are slower than untimed ones. */
+#define GKS_PROF_CLASSES 8
 typedef struct gks_profile {
-    int64_t n[5];          /* timed launches (or launch groups) per class              */
-    double ms[5];          /* summed device time per class                             */
+    int64_t n[GKS_PROF_CLASSES];  /* timed launches (or launch groups) per class       */
+    double ms[GKS_PROF_CLASSES];  /* summed device time per class                      */
     int64_t arnoldi;       /* Arnoldi iterations (all systems of the handle together)  */
     int64_t arnoldi_jsum;  /* sum over those iterations of j + 1 (vectors orthogonalised
                               against), for the byte count of the class 3 kernels      */

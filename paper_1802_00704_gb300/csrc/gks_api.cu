@@ -291,6 +291,7 @@ gks_status gks_reset_warm_start(gks_mesh *m)
     }
     DeviceGuard g(m->device);
     GKS_CUDA(cudaMemset(m->wk.x, 0, sizeof(double) * 20 * m->d.T));
+    GKS_CUDA(cudaMemset(m->wk.bnorm, 0, sizeof(double) * m->wk.ns));
     m->wk.nsolve = 0;
     return GKS_OK;
 }

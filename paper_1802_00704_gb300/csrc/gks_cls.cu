@@ -14,6 +14,7 @@
 // which saves one read and one write of the new vector per iteration.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "gks_internal.h"
 
@@ -41,6 +42,13 @@ __device__ __forceinline__ void oacc(R sa, R sax, R say, R g1, R g2, R *acc)
     acc[4] = fma(say, g2, acc[4]);
 }
 
+// 2^e exactly (|e| <= 1022)
+__device__ __forceinline__ double pow2(int e)
+{
+    e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
 // Block reduction of NV values; thread 0 of the block gets the totals.
 __device__ __forceinline__ void block_sum4(double *v, double *sh)
 {
@@ -64,115 +72,305 @@ __device__ __forceinline__ void block_sum4(double *v, double *sh)
 }
 
 // r_i = sum_j a0_ij (ubar_j - ubar_i), Eq. (25) with b_ij = (ubar_j - ubar_i, 0, 0)
-__global__ void k_rhs(DeviceMesh d, const double *__restrict__ w, double *__restrict__ b)
-{
-    const int64_t T = d.T;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= T) return;
-    double acc[NX];
-#pragma unroll
-    for (int q = 0; q < NX; ++q) acc[q] = 0.0;
-    double wi[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) wi[v] = w[v * T + i];
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        const int j = d.nb[s * T + i];
-        if (j < 0) continue;
-        double a[ND];
-#pragma unroll
-        for (int l = 0; l < ND; ++l) a[l] = d.a0[(s * ND + l) * T + i];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            const double du = w[v * T + j] - wi[v];
-#pragma unroll
-            for (int l = 0; l < ND; ++l) acc[v * ND + l] += a[l] * du;
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < NX; ++q) b[q * T + i] = acc[q];
-}
-
-// y = K x (mode 0), or y = b - K x with partial sums of |y|^2 (mode >= 1) and
-// of |b|^2 (mode 1).  K_ii = D_i (symmetric, 15 stored values), K_ij = -O_ij.
-// TX: type of x, TM: type of the operator data and of the arithmetic (modes
-// 1, 2 are FP64 only), TY: type of y (the residual norms are those of the FP64
-// values).  Every load (neighbour indices, blocks, the neighbours' gradient
-// entries, own data) is issued before the arithmetic; a missing neighbour reads
-// the cell's own entries with a zero block.
-template <typename TX, typename TM, typename TY>
-__global__ void k_spmv(DeviceMesh d, const TM *__restrict__ Dg, const TM *__restrict__ alg,
-                       const TM *__restrict__ exg, const TM *__restrict__ eyg, const TX *__restrict__ x,
-                       TY *__restrict__ y, int mode, const double *__restrict__ b, double *__restrict__ part,
-                       int pstride)
+// with partial sums of |b|^2 per block and variable in part[blk][v][1]
+__global__ void k_rhs(DeviceMesh d, const double *__restrict__ w, double *__restrict__ b, double *__restrict__ part,
+                      int pstride)
 {
     __shared__ double sh[32 * NV];
     const int64_t T = d.T;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    double nr[NV] = {0, 0, 0, 0}, nb[NV] = {0, 0, 0, 0};
+    double nb[NV] = {0, 0, 0, 0};
     if (i < T) {
-        int64_t jn[3];
-        TM sa[3], sax[3], say[3];
+        double acc[NX];
+#pragma unroll
+        for (int q = 0; q < NX; ++q) acc[q] = 0.0;
+        double wi[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) wi[v] = w[v * T + i];
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
             const int j = d.nb[s * T + i];
-            jn[s] = j >= 0 ? j : i;
-            sa[s] = j >= 0 ? -alg[s * T + i] : TM(0);
-            sax[s] = sa[s] * exg[s * T + i];
-            say[s] = sa[s] * eyg[s * T + i];
-        }
-        TM g[3][2 * NV];
+            if (j < 0) continue;
+            double a[ND];
 #pragma unroll
-        for (int s = 0; s < 3; ++s)
+            for (int l = 0; l < ND; ++l) a[l] = d.a0[(s * ND + l) * T + i];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                g[s][2 * v] = TM(x[(v * ND + 0) * T + jn[s]]);
-                g[s][2 * v + 1] = TM(x[(v * ND + 1) * T + jn[s]]);
+                const double du = w[v * T + j] - wi[v];
+#pragma unroll
+                for (int l = 0; l < ND; ++l) acc[v * ND + l] += a[l] * du;
             }
-        TM Dm[15];
-#pragma unroll
-        for (int q = 0; q < 15; ++q) Dm[q] = Dg[q * T + i];
-        TM acc[NX];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            TM xv[ND];
-#pragma unroll
-            for (int l = 0; l < ND; ++l) xv[l] = TM(x[(v * ND + l) * T + i]);
-            // symmetric 5x5 times vector
-            acc[v * ND + 0] = Dm[0] * xv[0] + Dm[1] * xv[1] + Dm[2] * xv[2] + Dm[3] * xv[3] + Dm[4] * xv[4];
-            acc[v * ND + 1] = Dm[1] * xv[0] + Dm[5] * xv[1] + Dm[6] * xv[2] + Dm[7] * xv[3] + Dm[8] * xv[4];
-            acc[v * ND + 2] = Dm[2] * xv[0] + Dm[6] * xv[1] + Dm[9] * xv[2] + Dm[10] * xv[3] + Dm[11] * xv[4];
-            acc[v * ND + 3] = Dm[3] * xv[0] + Dm[7] * xv[1] + Dm[10] * xv[2] + Dm[12] * xv[3] + Dm[13] * xv[4];
-            acc[v * ND + 4] = Dm[4] * xv[0] + Dm[8] * xv[1] + Dm[11] * xv[2] + Dm[13] * xv[3] + Dm[14] * xv[4];
         }
 #pragma unroll
-        for (int s = 0; s < 3; ++s)
+        for (int v = 0; v < NV; ++v)
 #pragma unroll
-            for (int v = 0; v < NV; ++v) oacc(sa[s], sax[s], say[s], g[s][2 * v], g[s][2 * v + 1], acc + v * ND);
+            for (int l = 0; l < ND; ++l) {
+                const double bv = acc[v * ND + l];
+                b[(v * ND + l) * T + i] = bv;
+                nb[v] += bv * bv;
+            }
+    }
+    block_sum4(nb, sh);
+    if (threadIdx.x == 0)
+        for (int v = 0; v < NV; ++v) part[(blockIdx.x * NV + v) * pstride + 1] = nb[v];
+}
+
+// acc = (K x)_i, the operator row of cell i applied to x (TM arithmetic).
+// Every load (neighbour indices, blocks, the neighbours' gradient entries, own
+// data) is issued before the arithmetic; a missing neighbour reads the cell's
+// own entries with a zero block.
+template <typename TX, typename TM>
+__device__ __forceinline__ void cell_apply(const DeviceMesh &d, const TM *__restrict__ Dg, const TM *__restrict__ alg,
+                                           const TM *__restrict__ exg, const TM *__restrict__ eyg,
+                                           const TX *__restrict__ x, int64_t i, TM *acc)
+{
+    const int64_t T = d.T;
+    int64_t jn[3];
+    TM sa[3], sax[3], say[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        const int j = d.nb[s * T + i];
+        jn[s] = j >= 0 ? j : i;
+        sa[s] = j >= 0 ? -alg[s * T + i] : TM(0);
+        sax[s] = sa[s] * exg[s * T + i];
+        say[s] = sa[s] * eyg[s * T + i];
+    }
+    TM g[3][2 * NV];
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            g[s][2 * v] = TM(x[(v * ND + 0) * T + jn[s]]);
+            g[s][2 * v + 1] = TM(x[(v * ND + 1) * T + jn[s]]);
+        }
+    TM Dm[15];
+#pragma unroll
+    for (int q = 0; q < 15; ++q) Dm[q] = Dg[q * T + i];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        TM xv[ND];
+#pragma unroll
+        for (int l = 0; l < ND; ++l) xv[l] = TM(x[(v * ND + l) * T + i]);
+        // symmetric 5x5 times vector
+        acc[v * ND + 0] = Dm[0] * xv[0] + Dm[1] * xv[1] + Dm[2] * xv[2] + Dm[3] * xv[3] + Dm[4] * xv[4];
+        acc[v * ND + 1] = Dm[1] * xv[0] + Dm[5] * xv[1] + Dm[6] * xv[2] + Dm[7] * xv[3] + Dm[8] * xv[4];
+        acc[v * ND + 2] = Dm[2] * xv[0] + Dm[6] * xv[1] + Dm[9] * xv[2] + Dm[10] * xv[3] + Dm[11] * xv[4];
+        acc[v * ND + 3] = Dm[3] * xv[0] + Dm[7] * xv[1] + Dm[10] * xv[2] + Dm[12] * xv[3] + Dm[13] * xv[4];
+        acc[v * ND + 4] = Dm[4] * xv[0] + Dm[8] * xv[1] + Dm[11] * xv[2] + Dm[13] * xv[3] + Dm[14] * xv[4];
+    }
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) oacc(sa[s], sax[s], say[s], g[s][2 * v], g[s][2 * v + 1], acc + v * ND);
+}
+
+// y = K x (mode 0), or y = 2^-e (b - K x) with partial sums of |y|^2 of the
+// stored y (mode 1), e = sexp[system] (0 when sexp is NULL): an FP32 Krylov
+// basis keeps its first vector near unit size whatever the size of b.
+// K_ii = D_i (symmetric, 15 stored values), K_ij = -O_ij.  TX: type of x, TM:
+// type of the operator data and of the arithmetic (mode 1 is FP64 only), TY:
+// type of y.
+template <typename TX, typename TM, typename TY>
+__global__ void k_spmv(DeviceMesh d, const TM *__restrict__ Dg, const TM *__restrict__ alg,
+                       const TM *__restrict__ exg, const TM *__restrict__ eyg, const TX *__restrict__ x,
+                       TY *__restrict__ y, int mode, const double *__restrict__ b, double *__restrict__ part,
+                       int pstride, const int32_t *__restrict__ sexp = nullptr)
+{
+    __shared__ double sh[32 * NV];
+    const int64_t T = d.T;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double nr[NV] = {0, 0, 0, 0};
+    if (i < T) {
+        TM acc[NX];
+        cell_apply<TX, TM>(d, Dg, alg, exg, eyg, x, i, acc);
         if (mode == 0) {
 #pragma unroll
             for (int q = 0; q < NX; ++q) y[q * T + i] = TY(acc[q]);
         } else {
+            const int c = d.blk_case[blockIdx.x];
 #pragma unroll
-            for (int v = 0; v < NV; ++v)
+            for (int v = 0; v < NV; ++v) {
+                const double sig = sexp ? pow2(-sexp[4 * c + v]) : 1.0;
 #pragma unroll
                 for (int l = 0; l < ND; ++l) {
-                    const double bv = b[(v * ND + l) * T + i];
-                    const double rv = bv - double(acc[v * ND + l]);
-                    y[(v * ND + l) * T + i] = TY(rv);
-                    nr[v] += rv * rv;
-                    if (mode == 1) nb[v] += bv * bv;
+                    const double rv = b[(v * ND + l) * T + i] - double(acc[v * ND + l]);
+                    const TY st = TY(rv * sig);
+                    y[(v * ND + l) * T + i] = st;
+                    nr[v] += double(st) * double(st);
                 }
+            }
         }
     }
     if (mode >= 1) {
         block_sum4(nr, sh);
-        if (mode == 1) block_sum4(nb, sh);
         if (threadIdx.x == 0)
-            for (int v = 0; v < NV; ++v) {
-                part[(blockIdx.x * NV + v) * pstride + 0] = nr[v];
-                if (mode == 1) part[(blockIdx.x * NV + v) * pstride + 1] = nb[v];
-            }
+            for (int v = 0; v < NV; ++v) part[(blockIdx.x * NV + v) * pstride + 0] = nr[v];
+    }
+}
+
+// ---- double-FP32 arithmetic for the refinement residual of the mixed mode.
+// A value is the unevaluated sum h + l of two FP32 numbers (about 48
+// significant bits; Dekker 1971).  The product of two high parts is exact as
+// p + e with e = fma(a, b, -p); sums use Knuth's TwoSum (TAOCP vol. 2, 4.2.2),
+// whose rounding error is exact; the small cross terms a_h b_l + a_l b_h are
+// plain FP32.  The _rn intrinsics keep the compiler from contracting or
+// reordering these steps.  GB300 runs FP32 at 64 times its FP64 rate, so the
+// 13 FP32 operations of a product-sum cost far less than one DFMA.
+
+// 2^-e v = h + l on the integer pipe (no FP64 instruction; e is applied to the
+// exponent field): h holds the upper 24 significant bits (truncated), l the
+// next 29 rounded to 24, so |2^-e v - h - l| <= 2^-47 |2^-e v|.  The residual
+// scales each system by 2^-e ~ 1/|b|, against which smaller parts do not
+// count: below 2^-74 only h is kept, below 2^-126 nothing (with operator
+// entries <= 2^30 either drop is under 2^-68 |2^-e b| per term).  Returns
+// false for 2^-e v >= 2^128 or a value that is not finite; that cell then
+// takes the FP64 operator.
+__device__ __forceinline__ bool df_split(double v, int e, float &h, float &l)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const unsigned hw = (unsigned)(u >> 32), lw = (unsigned)u;
+    const int E = (int)((hw >> 20) & 0x7FFu);           // biased FP64 exponent
+    const int Es = E - e;                                // that of 2^-e v
+    h = l = 0.0f;
+    if (E == 2047 || (E != 0 && Es > 1150)) return false;
+    if (E == 0 || Es < 897) return true;                 // zero, FP64 subnormal, or negligible
+    const unsigned sgn = hw & 0x80000000u;
+    h = __uint_as_float(sgn | ((unsigned)(Es - 896) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
+    if (Es >= 949) {
+        // the remaining 29 bits times 2^(Es - 1075), a normal FP32 power of two here
+        const float r = __fmul_rn(__uint2float_rn(lw & 0x1FFFFFFFu), __uint_as_float((unsigned)(Es - 948) << 23));
+        l = sgn ? -r : r;
+    }
+    return true;
+}
+
+// (sh, sl) += (ah, al) (bh, bl)
+__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, float &sh, float &sl)
+{
+    const float p = __fmul_rn(ah, bh);
+    const float e = __fmaf_rn(ah, bh, -p);
+    const float t = __fadd_rn(sh, p);
+    const float z = __fsub_rn(t, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(p, z));
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(err, __fadd_rn(e, __fmaf_rn(ah, bl, __fmul_rn(al, bh)))));
+}
+
+// (bh, bl) - (sh, sl), rounded to FP32
+__device__ __forceinline__ float df_sub_round(float bh, float bl, float sh, float sl)
+{
+    const float t = __fsub_rn(bh, sh);
+    const float z = __fsub_rn(t, bh);
+    const float err = __fadd_rn(__fsub_rn(bh, __fsub_rn(t, z)), __fsub_rn(-sh, z));
+    return __fadd_rn(t, __fadd_rn(err, __fsub_rn(bl, sl)));
+}
+
+// FP64 fallback of k_resid_df for variable v of cell i: out = 2^-e (b - K x)
+__device__ __noinline__ void resid64_cell(const DeviceMesh &d, const double *__restrict__ x,
+                                          const double *__restrict__ b, int64_t i, int v, int e, float *out)
+{
+    double acc[NX];
+    cell_apply<double, double>(d, d.D, d.alpha, d.ex, d.ey, x, i, acc);
+    for (int l = 0; l < ND; ++l) out[l] = float((b[(v * ND + l) * d.T + i] - acc[v * ND + l]) * pow2(-e));
+}
+
+// V_0 = 2^-e (b - K x) in FP32 and partial |V_0|^2 (as k_spmv mode 1 with an
+// FP32 basis), in double-FP32 arithmetic: the operator as FP32 pairs D2 ([30][T]:
+// the 15 diagonal-block values, then their low parts) and S2 ([18][T]: sa,
+// sa dx, sa dy of each neighbour, then their low parts), 2^-e x and 2^-e b
+// split on the fly, so the sums come out scaled.  One thread per cell and
+// variable (the double-FP32 chains are latency-bound: many small threads hide
+// it better than one thread per cell); block q of the 1-D grid takes variable
+// q % 4 of cell block q / 4, so the four blocks of a cell block run together
+// and share the operator through L2.  A value outside the split range sends
+// the thread to the FP64 operator.  Each thread's five squares are summed in
+// FP32 (the scaled vector is near unit size).
+__global__ void __launch_bounds__(kBlock, 4) k_resid_df(DeviceMesh d, const float *__restrict__ D2,
+                                                       const float *__restrict__ S2, const double *__restrict__ x,
+                                                       float *__restrict__ y, const double *__restrict__ b,
+                                                       double *__restrict__ part, int pstride,
+                                                       const int32_t *__restrict__ sexp)
+{
+    __shared__ double sh[kBlock / 32];
+    const int64_t T = d.T;
+    const int v = blockIdx.x & 3;
+    const int64_t blk = blockIdx.x >> 2;
+    const int64_t i = blk * kBlock + threadIdx.x;
+    double nr = 0.0;
+    if (i < T) {
+        const int e = sexp[4 * d.blk_case[blk] + v];
+        int64_t jn[3];
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            const int j = d.nb[s * T + i];
+            jn[s] = j >= 0 ? j : i;
+        }
+        // every load first (the arithmetic below is a long dependent chain)
+        double xv[ND], gv[3][2], bv[ND];
+        float dp[30], op[18];
+#pragma unroll
+        for (int l = 0; l < ND; ++l) xv[l] = x[(v * ND + l) * T + i];
+#pragma unroll
+        for (int s = 0; s < 3; ++s)
+#pragma unroll
+            for (int l = 0; l < 2; ++l) gv[s][l] = x[(v * ND + l) * T + jn[s]];
+#pragma unroll
+        for (int q = 0; q < 30; ++q) dp[q] = D2[q * T + i];
+#pragma unroll
+        for (int q = 0; q < 18; ++q) op[q] = S2[q * T + i];
+#pragma unroll
+        for (int l = 0; l < ND; ++l) bv[l] = b[(v * ND + l) * T + i];
+        bool ok = true;
+        float xh[ND], xl[ND], gh[3][2], gl[3][2], ah[ND], al[ND], out[ND];
+#pragma unroll
+        for (int l = 0; l < ND; ++l) {
+            ok &= df_split(xv[l], e, xh[l], xl[l]);
+            ah[l] = al[l] = 0.0f;
+        }
+#pragma unroll
+        for (int s = 0; s < 3; ++s)
+#pragma unroll
+            for (int l = 0; l < 2; ++l) ok &= df_split(gv[s][l], e, gh[s][l], gl[s][l]);
+        // symmetric 5x5 block: entry (a, k) in the upper-triangle order
+        constexpr int kIdx[5][5] = {{0, 1, 2, 3, 4}, {1, 5, 6, 7, 8}, {2, 6, 9, 10, 11}, {3, 7, 10, 12, 13},
+                                    {4, 8, 11, 13, 14}};
+#pragma unroll
+        for (int a = 0; a < ND; ++a)
+#pragma unroll
+            for (int k = 0; k < ND; ++k) df_mac(dp[kIdx[a][k]], dp[15 + kIdx[a][k]], xh[k], xl[k], ah[a], al[a]);
+        // off-diagonal block of neighbour s (see oacc): sa, sax = sa dx, say = sa dy
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            const int q = 3 * s;
+            df_mac(op[q], op[9 + q], gh[s][0], gl[s][0], ah[0], al[0]);
+            df_mac(op[q], op[9 + q], gh[s][1], gl[s][1], ah[1], al[1]);
+            df_mac(op[q + 1], op[10 + q], gh[s][0], gl[s][0], ah[2], al[2]);
+            df_mac(op[q + 1], op[10 + q], gh[s][1], gl[s][1], ah[3], al[3]);
+            df_mac(op[q + 2], op[11 + q], gh[s][0], gl[s][0], ah[3], al[3]);
+            df_mac(op[q + 2], op[11 + q], gh[s][1], gl[s][1], ah[4], al[4]);
+        }
+#pragma unroll
+        for (int l = 0; l < ND; ++l) {
+            float bh, bl;
+            ok &= df_split(bv[l], e, bh, bl);
+            out[l] = df_sub_round(bh, bl, ah[l], al[l]);
+        }
+        if (!ok) resid64_cell(d, x, b, i, v, e, out);   // a value outside the split range
+        float sq = 0.0f;
+#pragma unroll
+        for (int l = 0; l < ND; ++l) {
+            y[(v * ND + l) * T + i] = out[l];
+            sq = __fmaf_rn(out[l], out[l], sq);
+        }
+        nr = double(sq);
+    }
+    for (int o = 16; o > 0; o >>= 1) nr += __shfl_down_sync(0xffffffffu, nr, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = nr;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) t += sh[w];
+        part[(blk * NV + v) * pstride + 0] = t;
     }
 }
 
@@ -454,12 +652,25 @@ __global__ void k_backsolve(int m, const double *__restrict__ H, const double *_
 }
 
 // y_k /= vn_k: coefficients of the unnormalised preconditioned vectors
-__global__ void k_scale_y(int m, double *y, const double *__restrict__ vn, const int32_t *__restrict__ ctl, int ns)
+// With sexp given (FP32 basis, rows [current][next] exponents e of the scale
+// 2^-e of the first basis vector): y is also scaled by 2^-e of the current
+// cycle (the combination adds 2^e sum y_k Z_k, so its FP32 sums stay near unit
+// size), and the next residual's exponent comes from the cycle's estimate
+// |g_jv| of its norm (at least 1e-3 rtol |b|).
+__global__ void k_scale_y(int m, double *y, const double *__restrict__ vn, const int32_t *__restrict__ ctl, int ns,
+                          const double *__restrict__ g = nullptr, const double *__restrict__ bnorm = nullptr,
+                          double rtol = 0.0, int32_t *sexp = nullptr)
 {
     const int sy = blockIdx.x * blockDim.x + threadIdx.x;
     if (sy >= ns) return;
     const int jv = ctl[kCtlJv * ns + sy];
-    for (int k = 0; k < jv; ++k) y[sy * m + k] /= vn[sy * (m + 1) + k];
+    const double f = sexp ? pow2(-sexp[sy]) : 1.0;
+    for (int k = 0; k < jv; ++k) y[sy * m + k] = sexp ? y[sy * m + k] / vn[sy * (m + 1) + k] * f
+                                                      : y[sy * m + k] / vn[sy * (m + 1) + k];
+    if (sexp && jv > 0) {
+        const double est = fmax(fabs(g[sy * (m + 1) + jv]), 1e-3 * rtol * bnorm[sy]);
+        if (est > 0.0 && est < 1e300) sexp[ns + sy] = max(-1000, ilogb(est));
+    }
 }
 
 // x += sum_{k<jv} y_k Z_k with Z_k = M^{-1} V_k kept from the iterations
@@ -467,10 +678,13 @@ __global__ void k_scale_y(int m, double *y, const double *__restrict__ vn, const
 // correction of one inner cycle is formed in FP32 (it only has to be accurate to
 // the inner tolerance; the next FP64 residual measures what is left) and added
 // to x in FP64, so the FP64 pipe sees one add per value instead of one
-// conversion and one FMA per value and Krylov vector.
+// conversion and one FMA per value and Krylov vector.  With sexp given (FP32
+// basis): y carries 2^-e of the cycle (see k_scale_y) and the sum is scaled
+// back by 2^e in FP64 (exact).
 template <typename TZ>
 __global__ void k_combine_z(DeviceMesh d, const TZ *__restrict__ Z, const double *__restrict__ y, int m,
-                            const int32_t *__restrict__ ctl, int ns, double *__restrict__ x)
+                            const int32_t *__restrict__ ctl, int ns, double *__restrict__ x,
+                            const int32_t *__restrict__ sexp = nullptr)
 {
     const int64_t T = d.T;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -486,8 +700,9 @@ __global__ void k_combine_z(DeviceMesh d, const TZ *__restrict__ Z, const double
 #pragma unroll
         for (int l = 0; l < ND; ++l) acc[l] += yk * Z[k * vs + (v * ND + l) * T + i];
     }
+    const double f = sexp ? pow2(sexp[sy]) : 1.0;
 #pragma unroll
-    for (int l = 0; l < ND; ++l) x[(v * ND + l) * T + i] += double(acc[l]);
+    for (int l = 0; l < ND; ++l) x[(v * ND + l) * T + i] += sexp ? double(acc[l]) * f : double(acc[l]);
 }
 
 // Warm start of the next solve (cases not done) from the last solutions
@@ -512,20 +727,43 @@ __global__ void k_warm(DeviceMesh d, double *__restrict__ x, double *__restrict_
 
 // Start (first = 1) or restart of every system: sums[s][0] = |r|^2,
 // sums[s][1] = |b|^2.  Systems of finished cases stay inactive.
+// Scale of the first residual of a solve: next exponent sexp[ns + s] = e with 2^-e B in [1, 2),
+// B = max(|b|, |b_prev|) (sums[s][1] = |b|^2, bnorm = |b| of the previous
+// solve, 0 at first): the warm start solved the previous system, so its
+// residual is of the order of B at most; e = 0 when B = 0.
+__global__ void k_sigma(const double *__restrict__ sums, int sstride, const double *__restrict__ bnorm,
+                        int32_t *sexp, int ns)
+{
+    const int sy = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sy >= ns) return;
+    const double bn = fmax(sqrt(sums[sy * sstride + 1]), bnorm[sy]);
+    sexp[ns + sy] = bn > 0.0 && bn < 1e300 ? max(-1000, ilogb(bn)) : 0;
+}
+
+// sums[s][0] = |V_0|^2 of the stored first basis vector V_0 = 2^-e r (e: the
+// next exponent sexp[ns + s], which becomes the current one sexp[s]; e = 0
+// when sexp is NULL), sums[s][1] = |b|^2 (first solve of a step).
 __global__ void k_start(const double *__restrict__ sums, int sstride, double *bnorm, double *beta, double *vn, int m,
-                        int32_t *ctl, int ns, const int32_t *__restrict__ done, double rtol, int maxit, int first)
+                        int32_t *ctl, int ns, const int32_t *__restrict__ done, double rtol, int maxit, int first,
+                        int32_t *sexp = nullptr)
 {
     const int sy = blockIdx.x * blockDim.x + threadIdx.x;
     if (sy >= ns) return;
     // |b| comes with the first residual; restarts reuse it
-    const double bn = first ? sqrt(sums[sy * sstride + 1]) : bnorm[sy], be = sqrt(sums[sy * sstride + 0]);
+    const double vn0 = sqrt(sums[sy * sstride + 0]);
+    double be = vn0;
+    if (sexp) {
+        be = vn0 * pow2(sexp[ns + sy]);
+        sexp[sy] = sexp[ns + sy];
+    }
+    const double bn = first ? sqrt(sums[sy * sstride + 1]) : bnorm[sy];
     if (first) {
         bnorm[sy] = bn;
         ctl[kCtlIters * ns + sy] = 0;
         ctl[kCtlActive * ns + sy] = !done[sy >> 2];
     }
     beta[sy] = be;
-    vn[sy * (m + 1)] = be;                             // V_0 = r, v_0 = r / beta
+    vn[sy * (m + 1)] = vn0;                            // V_0 = 2^-e r, v_0 = r / beta
     const int act = ctl[kCtlActive * ns + sy] && bn > 0.0 && be > rtol * bn && ctl[kCtlIters * ns + sy] < maxit;
     ctl[kCtlActive * ns + sy] = act;
     ctl[kCtlRunning * ns + sy] = act;
@@ -684,9 +922,11 @@ gks_status precond32(gks_mesh *m, const TR *src, float *dst, cudaStream_t s)
 // Any active / any running system into the pinned host flags (no synchronisation).
 gks_status enqueue_flags(gks_mesh *m, cudaStream_t s)
 {
+    const int slot = prof_start(m, kProfCtl, s);
     k_any<<<1, kBlock, 0, s>>>(m->wk.ctl, m->wk.ns, m->wk.flags);
     note_launch();
     GKS_CUDA(cudaMemcpyAsync(m->wk.h_flags, m->wk.flags, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, s));
+    prof_stop(m, slot, s);
     return GKS_OK;
 }
 
@@ -953,19 +1193,48 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
     const double eta = mixed ? m->cfg.inner_rtol : 0.0;
     gks_status st;
 
+    // FP32 basis: first basis vector scaled by a power of two; exponents per
+    // system, [current cycle][next residual]
+    int32_t *sx = std::is_same<TB, float>::value ? k.sexp : nullptr;
+    const int32_t *sxn = sx ? sx + ns : nullptr;
+    // V_0 = 2^-e (b - K x) and partial |V_0|^2: double-FP32 arithmetic into the
+    // FP32 basis when the operator has FP32 pairs, FP64 arithmetic otherwise
+    auto residual = [&](cudaStream_t q) -> gks_status {
+        if (std::is_same<TB, float>::value && d.D2)
+            k_resid_df<<<4 * nb, kBlock, 0, q>>>(d, d.D2, d.S2, k.x, reinterpret_cast<float *>(V), k.b, k.part, ps,
+                                                 sxn);
+        else
+            k_spmv<double, double, TB><<<nb, kBlock, 0, q>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, V, 1, k.b, k.part,
+                                                             ps, sxn);
+        note_launch();
+        GKS_CUDA(cudaGetLastError());
+        return GKS_OK;
+    };
     // the three fixed launch sequences (the per-part graphs end each with the
     // flags for the host, the whole-solve graph with a condition kernel)
     auto start_body = [&](cudaStream_t q) -> gks_status {
-        k_rhs<<<nb, kBlock, 0, q>>>(d, k.w, k.b); note_launch();
+        int slot = prof_start(m, kProfCtl, q);
+        k_rhs<<<nb, kBlock, 0, q>>>(d, k.w, k.b, k.part, ps); note_launch();
+        if (sx) {
+            // the FP32 basis stores its first vector scaled by a power of two 2^-e
+            k_reduce<<<dim3(1, ns), kReduceThreads, 0, q>>>(k.part + 1, d.case_blk, ps, k.hcol + 1, ps, 0);
+            note_launch();
+            k_sigma<<<sblocks(ns), 128, 0, q>>>(k.hcol, ps, k.bnorm, k.sexp, ns); note_launch();
+        }
+        prof_stop(m, slot, q);
+        slot = prof_start(m, kProfResid, q);
         // residual r = b - K x, written straight into the basis slot V_0 (v_0 = V_0 / beta)
-        k_spmv<double, double, TB><<<nb, kBlock, 0, q>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, V, 1, k.b, k.part, ps);
+        if (const gks_status r = residual(q); r != GKS_OK) return r;
+        k_reduce<<<dim3(sx ? 1 : 2, ns), kReduceThreads, 0, q>>>(k.part, d.case_blk, ps, k.hcol, ps, 0);
         note_launch();
-        k_reduce<<<dim3(2, ns), kReduceThreads, 0, q>>>(k.part, d.case_blk, ps, k.hcol, ps, 0); note_launch();
+        prof_stop(m, slot, q);
+        slot = prof_start(m, kProfCtl, q);
         k_start<<<sblocks(ns), 128, 0, q>>>(k.hcol, ps, k.bnorm, k.beta, k.vn, mm, k.ctl, ns, k.done, rtol, maxit,
-                                             1);
+                                             1, sx);
         note_launch();
         k_zero_trivial<<<nb, kBlock, 0, q>>>(d, k.x, k.bnorm); note_launch();
         k_init_g<<<sblocks(ns * (mm + 1)), 128, 0, q>>>(k.g, mm, k.beta, k.ctl, ns); note_launch();
+        prof_stop(m, slot, q);
         GKS_CUDA(cudaGetLastError());
         return GKS_OK;
     };
@@ -1006,27 +1275,34 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
         k_reduce<<<dim3(1, ns), kReduceThreads, 0, q>>>(k.part, d.case_blk, ps, k.hcol + j + 1, ps, 2);
         note_launch();
         prof_stop(m, slot, q);
+        slot = prof_start(m, kProfCtl, q);
         k_givens<<<sblocks(ns), 128, 0, q>>>(j, mm, k.hcol, ps, k.vn, k.H, k.cs, k.sn, k.g, k.ctl, ns, k.bnorm,
                                               k.beta, rtol, eta, maxit);
         note_launch();
+        prof_stop(m, slot, q);
         GKS_CUDA(cudaGetLastError());
         return GKS_OK;
     };
     auto restart_body = [&](cudaStream_t q) -> gks_status {
+        int slot = prof_start(m, kProfCorr, q);
         k_backsolve<<<sblocks(ns), 128, 0, q>>>(mm, k.H, k.g, k.y, k.ctl, ns); note_launch();
-        k_scale_y<<<sblocks(ns), 128, 0, q>>>(mm, k.y, k.vn, k.ctl, ns); note_launch();
+        k_scale_y<<<sblocks(ns), 128, 0, q>>>(mm, k.y, k.vn, k.ctl, ns, k.g, k.bnorm, rtol, sx); note_launch();
         if (mixed)
-            k_combine_z<float><<<dim3(nb, NV), kBlock, 0, q>>>(d, k.Z32, k.y, mm, k.ctl, ns, k.x);
+            k_combine_z<float><<<dim3(nb, NV), kBlock, 0, q>>>(d, k.Z32, k.y, mm, k.ctl, ns, k.x, sx);
         else
             k_combine_z<double><<<dim3(nb, NV), kBlock, 0, q>>>(d, k.Z, k.y, mm, k.ctl, ns, k.x);
         note_launch();
-        k_spmv<double, double, TB><<<nb, kBlock, 0, q>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, V, 2, k.b, k.part, ps);
-        note_launch();
+        prof_stop(m, slot, q);
+        slot = prof_start(m, kProfResid, q);
+        if (const gks_status r = residual(q); r != GKS_OK) return r;
         k_reduce<<<dim3(1, ns), kReduceThreads, 0, q>>>(k.part, d.case_blk, ps, k.hcol, ps, 0); note_launch();
+        prof_stop(m, slot, q);
+        slot = prof_start(m, kProfCtl, q);
         k_start<<<sblocks(ns), 128, 0, q>>>(k.hcol, ps, k.bnorm, k.beta, k.vn, mm, k.ctl, ns, k.done, rtol, maxit,
-                                             0);
+                                             0, sx);
         note_launch();
         k_init_g<<<sblocks(ns * (mm + 1)), 128, 0, q>>>(k.g, mm, k.beta, k.ctl, ns); note_launch();
+        prof_stop(m, slot, q);
         GKS_CUDA(cudaGetLastError());
         return GKS_OK;
     };
@@ -1106,7 +1382,9 @@ gks_status cls_solve(gks_mesh *m, cudaStream_t s, int32_t *iters, double *relres
         // extrapolate from as many past solutions as exist (up to the configured order)
         const int order = (m->cfg.warm_extrap >= 2 && k.nsolve >= 3) ? 2 : (k.nsolve >= 2 ? 1 : 0);
         const unsigned nb = (unsigned)k.nblk;
+        const int slot = prof_start(m, kProfCtl, s);
         k_warm<<<nb, kBlock, 0, s>>>(m->d, k.x, k.x_prev, k.x_prev2, k.done, order); note_launch();
+        prof_stop(m, slot, s);
         GKS_CUDA(cudaGetLastError());
     }
     gks_status st = k.V32 ? cls_solve_t<float>(m, k.V32, s, iters, relres, converged)

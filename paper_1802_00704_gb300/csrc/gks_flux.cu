@@ -480,8 +480,10 @@ gks_status launch_update(gks_mesh *m, double *w, const double *flux, cudaStream_
 gks_status launch_cfl_dt(gks_mesh *m, const double *w, double *dt_dev, cudaStream_t s)
 {
     const unsigned nb = blocks(m->d.T, kBlock);
+    const int slot = prof_start(m, kProfCtl, s);
     k_cfl_partial<<<nb, kBlock, 0, s>>>(m->d, w, m->cfg.gamma, m->cfg.mu, m->wk.dpart); note_launch();
     k_min_final<<<m->d.ncase, kBlock, 0, s>>>(m->wk.dpart, m->d.case_blk, m->cfg.cfl, dt_dev); note_launch();
+    prof_stop(m, slot, s);
     GKS_CUDA(cudaGetLastError());
     return GKS_OK;
 }

@@ -38,7 +38,10 @@ extern std::atomic<int64_t> g_launches;
 inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // Kernel classes timed by the optional CUDA-event profiler.
-enum : int { kProfFlux = 0, kProfSpmv = 1, kProfIlu = 2, kProfOrth = 3, kProfUpdate = 4, kProfClasses = 5 };
+enum : int {
+    kProfFlux = 0, kProfSpmv = 1, kProfIlu = 2, kProfOrth = 3, kProfUpdate = 4, kProfResid = 5, kProfCorr = 6,
+    kProfCtl = 7, kProfClasses = GKS_PROF_CLASSES
+};
 
 // Device status bits (per case words the kernels OR into).
 enum : int { kStatusNonPhys = 1, kStatusNoConv = 2 };
@@ -65,6 +68,11 @@ struct DeviceMesh {
     // FP32 copies of the operator and factors (mixed precision)
     float *D32 = nullptr, *P32 = nullptr, *alpha32 = nullptr, *ex32 = nullptr, *ey32 = nullptr;
     float *ih32 = nullptr;           // [T] 1 / h_i (mixed flux)
+    // the operator as FP32 pairs hi + lo for the double-FP32 refinement residual
+    // (mixed mode with an FP32 basis; NULL when a value is outside the pair range)
+    float *D2 = nullptr;             // [30][T] the 15 diagonal-block values, then their low parts
+    float *S2 = nullptr;             // [18][T] sa, sa dx, sa dy per neighbour slot (sa = -alpha, 0
+                                     //         without neighbour), then their low parts
     double *ox = nullptr, *oy = nullptr;  // [3][T] neighbour centroid in i's scaled frame (limiter)
     int32_t *kord = nullptr;         // [T] reconstruction order k_i of Eq. (28) (limiter)
     int32_t *cf = nullptr;           // [3][T] (face << 1) | side, -1 unused
@@ -113,6 +121,8 @@ struct Work {
     double *vn = nullptr;            // [ns][m+1] norms vn_k of the stored basis vectors
     double *bnorm = nullptr, *beta = nullptr;  // [ns]
     int32_t *ctl = nullptr;          // [kCtlFields][ns]
+    int32_t *sexp = nullptr;         // [2][ns] FP32 basis: first basis vector stored as 2^-e r; e of the
+                                     //         current cycle, then that of the next residual
     int32_t *flags = nullptr;        // [4]: any active, any running, all cases done
     double *dt = nullptr;            // [ncase] step of each case (0: case inactive)
     double *tcase = nullptr;         // [ncase] time reached

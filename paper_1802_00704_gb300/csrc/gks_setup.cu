@@ -675,6 +675,30 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
         std::vector<float> h_ih32(T);
         for (int64_t i = 0; i < T; ++i) h_ih32[i] = float(1.0 / h_h[i]);
         UP(ih32, h_ih32);
+        if (cfg.basis_fp32) {
+            // FP32 pairs of the operator: v = hi + lo to 2^-48 for v = 0 or 2^-74 <= |v| <= 2^30
+            // (the bound on |v| keeps the parts of x the residual drops negligible)
+            bool in_range = true;
+            auto pair = [&](double v, float &hi, float &lo) {
+                const double a = std::fabs(v);
+                if (v != 0.0 && !(a >= 0x1p-74 && a <= 0x1p30)) in_range = false;
+                hi = float(v);
+                lo = float(v - double(hi));
+            };
+            std::vector<float> h_D2(30 * T), h_S2(18 * T);
+            for (int64_t i = 0; i < T; ++i) {
+                for (int q = 0; q < 15; ++q) pair(h_D[q * T + i], h_D2[q * T + i], h_D2[(15 + q) * T + i]);
+                for (int s = 0; s < 3; ++s) {
+                    const double sa = h_nb[s * T + i] >= 0 ? -h_alpha[s * T + i] : 0.0;
+                    const double o[3] = {sa, sa * h_ex[s * T + i], sa * h_ey[s * T + i]};
+                    for (int q = 0; q < 3; ++q)
+                        pair(o[q], h_S2[(3 * s + q) * T + i], h_S2[(9 + 3 * s + q) * T + i]);
+                }
+            }
+            if (in_range) {
+                UP(D2, h_D2); UP(S2, h_S2);
+            }
+        }
     }
 #undef UP
 
@@ -707,10 +731,13 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
     if (cfg.precision == GKS_MIXED) AL(x32, 20 * T);
     AL(H, ns * (mm + 1) * mm); AL(cs, ns * mm); AL(sn, ns * mm); AL(g, ns * (mm + 1)); AL(y, ns * mm);
     AL(hcol, ns * (mm + 2)); AL(hco, ns * (mm + 2)); AL(vn, ns * (mm + 1)); AL(bnorm, ns); AL(beta, ns); AL(ctl, kCtlFields * ns); AL(flags, 4);
+    AL(sexp, 2 * ns);
     AL(dt, n_cases); AL(tcase, n_cases); AL(tfinal, n_cases); AL(done, n_cases); AL(scal, 8); AL(status, n_cases);
 #undef AL
     GKS_CUDA(cudaMemset(k.x, 0, sizeof(double) * 20 * T));
+    GKS_CUDA(cudaMemset(k.bnorm, 0, sizeof(double) * ns));
     GKS_CUDA(cudaMemset(k.ctl, 0, sizeof(int32_t) * kCtlFields * ns));
+    GKS_CUDA(cudaMemset(k.sexp, 0, sizeof(int32_t) * 2 * ns));
     GKS_CUDA(cudaMemset(k.status, 0, sizeof(int32_t) * n_cases));
     GKS_CUDA(cudaMemset(k.done, 0, sizeof(int32_t) * n_cases));
     {

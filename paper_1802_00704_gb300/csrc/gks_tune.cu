@@ -39,6 +39,7 @@ gks_status time_candidate(gks_mesh *m, const double *w, int trial_steps, cudaStr
     const int32_t n = m->n_case;
     gks_status st;
     GKS_CUDA(cudaMemsetAsync(k.x, 0, sizeof(double) * 20 * m->d.T, s));
+    GKS_CUDA(cudaMemsetAsync(k.bnorm, 0, sizeof(double) * k.ns, s));
     k.nsolve = 0;
     GKS_CUDA(cudaMemsetAsync(k.tfinal, 0, sizeof(double) * n, s));
     GKS_CUDA(cudaMemsetAsync(k.tcase, 0, sizeof(double) * n, s));
@@ -137,6 +138,7 @@ extern "C" gks_status gks_autotune(gks_mesh *m, const double *w, int32_t trial_s
     }
     // leave the handle as a fresh one: cleared warm start and case state
     cudaMemsetAsync(m->wk.x, 0, sizeof(double) * 20 * m->d.T, s);
+    cudaMemsetAsync(m->wk.bnorm, 0, sizeof(double) * m->wk.ns, s);
     cudaMemsetAsync(m->wk.done, 0, sizeof(int32_t) * m->n_case, s);
     cudaMemsetAsync(m->wk.status, 0, sizeof(int32_t) * m->n_case, s);
     m->wk.nsolve = 0;

@@ -27,7 +27,8 @@ EXPORTED = ["gks_config_default", "gks_mesh_create", "gks_mesh_destroy", "gks_me
             "gks_cls_reconstruct", "gks_reset_warm_start", "gks_flux", "gks_step", "gks_run", "gks_point_flux",
             "gks_profile_begin", "gks_profile_end", "gks_launch_count", "gks_cfl_dt_noalloc", "gks_batch_create",
             "gks_batch_run", "gks_limit", "gks_autotune", "gks_last_error"]
-PROF_FLUX, PROF_SPMV, PROF_ILU, PROF_ORTH, PROF_UPDATE = range(5)
+PROF_FLUX, PROF_SPMV, PROF_ILU, PROF_ORTH, PROF_UPDATE, PROF_RESID, PROF_CORR, PROF_CTL = range(8)
+PROF_CLASSES = 8
 
 
 class GksError(RuntimeError):
@@ -66,7 +67,8 @@ class TuneResult(C.Structure):
 
 
 class Profile(C.Structure):
-    _fields_ = [("n", C.c_int64 * 5), ("ms", C.c_double * 5), ("arnoldi", C.c_int64), ("arnoldi_jsum", C.c_int64),
+    _fields_ = [("n", C.c_int64 * PROF_CLASSES), ("ms", C.c_double * PROF_CLASSES), ("arnoldi", C.c_int64),
+                ("arnoldi_jsum", C.c_int64),
                 ("precond", C.c_int64), ("residuals", C.c_int64)]
 
 

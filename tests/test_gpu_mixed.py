@@ -117,3 +117,88 @@ def test_fp32_basis_batch_matches_single_runs(G):
         m.run(ws, max_steps=4)
         assert rel_max(wh[:, o:o + c.mesh.n_tri], host(ws)) <= 1e-13, c.name
         o += c.mesh.n_tri
+
+
+def _true_relres(om, w, coef):
+    """||b - K x|| / ||b|| per variable in FP64 from the oracle's CLS matrix."""
+    import scipy.sparse as sp
+    rp, col, val, off = om.cls_matrix()
+    n = len(rp) - 1
+    K = sp.csr_matrix((val, col, rp), shape=(n, n))
+    b = om.cls_rhs(w)
+    nd = np.diff(np.append(off, n))
+    X = np.zeros((4, n))
+    for i in range(len(off)):
+        X[:, off[i]:off[i] + nd[i]] = coef[:, :nd[i], i]
+    out = []
+    for v in range(4):
+        bn = np.linalg.norm(b[v])
+        out.append(np.linalg.norm(b[v] - K @ X[v]) / bn if bn > 0 else 0.0)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("name", ["advection20", "shock_vortex40x20", "walled13x9"])
+def test_refinement_residual_matches_fp64_residual(O, G, name):
+    """The mixed mode's refinement residual (double-FP32 arithmetic with the FP32
+    basis) certifies the FP64 tolerance: the relative residual the solve reports
+    equals the FP64 residual of the returned coefficients, computed from the
+    oracle's matrix, to 1e-14 of |b|, and that residual is below 1e-12."""
+    from tests.test_gpu_parity import CASES
+    c = CASES[name]()
+    om = O.OracleMesh(c.mesh)
+    m = G.GksMesh(c.mesh, precision=G.MIXED, basis_fp32=1)
+    coef, info = m.cls_reconstruct(dev(c.w0))
+    assert info["converged"] == 1
+    true = _true_relres(om, c.w0, host(coef))
+    rep = np.array(info["relres"])
+    assert np.all(true <= 1.01e-12), true
+    assert np.all(np.abs(rep - true) <= 1e-14), (rep, true)
+
+
+@pytest.mark.parametrize("where", ["everywhere", "left_half"])
+def test_tiny_variable_keeps_fp32_basis_accurate(O, G, where):
+    """A variable of size 1e-30 (rho v of a nearly one-dimensional flow) is
+    below the range of the double-FP32 split (such cells take the FP64
+    operator) and its squares below FP32's range: the first basis vector is
+    stored scaled by a power of two near 1/|b|, so the solve still reaches the
+    FP64 tolerance and matches the oracle."""
+    c = I.advection_case(20, seed=9)
+    w = c.w0.copy()
+    rng = np.random.default_rng(3)
+    tiny = 1e-30 * (0.5 + rng.random(w.shape[1]))
+    if where == "everywhere":
+        w[2] = tiny
+    else:
+        cx = O.OracleMesh(c.mesh).cell_geometry()["cx"]
+        w[2] = np.where(cx < 0.5, tiny, 1e-3 * (0.5 + rng.random(w.shape[1])))
+    om = O.OracleMesh(c.mesh)
+    ref, _, _, _ = om.cls_solve(w)
+    m = G.GksMesh(c.mesh, precision=G.MIXED, basis_fp32=1)
+    coef, info = m.cls_reconstruct(dev(w))
+    assert info["converged"] == 1 and max(info["relres"]) <= 1e-12, info
+    got = host(coef)
+    for v in range(4):
+        assert rel_max(got[v], ref[v]) <= 1e-9, (v, rel_max(got[v], ref[v]))
+    assert np.all(_true_relres(om, w, got) <= 1.01e-12)
+
+
+def test_warm_start_far_from_new_system(O, G):
+    """A warm start from a flow whose rho v is 1e50 times larger than the new
+    one: the first residual is 1e48 times |b|, and the FP32 basis stores it
+    scaled by the larger of |b| and the previous |b| (the warm start's own
+    scale), not overflowing; later restarts rescale by the cycle's estimate.
+    The solve meets the FP64 tolerance and matches the oracle's solve from zero."""
+    c = I.advection_case(20, seed=4)
+    rng = np.random.default_rng(8)
+    m = G.GksMesh(c.mesh, precision=G.MIXED, basis_fp32=1)
+    _, info1 = m.cls_reconstruct(dev(c.w0))     # warm start with rho v of order one
+    assert info1["converged"] == 1
+    w2 = c.w0.copy()
+    w2[2] = 1e-50 * (0.5 + rng.random(w2.shape[1]))
+    om = O.OracleMesh(c.mesh)
+    ref, _, _, _ = om.cls_solve(w2)
+    coef, info = m.cls_reconstruct(dev(w2))
+    assert info["converged"] == 1 and max(info["relres"]) <= 1e-12, info
+    got = host(coef)
+    for v in range(4):
+        assert rel_max(got[v], ref[v]) <= 1e-9, (v, rel_max(got[v], ref[v]))

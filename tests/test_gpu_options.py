@@ -165,3 +165,22 @@ def test_graphs_follow_knob_changes(G):
     for _ in range(5):
         assert m.step(wa, 2e-4)["iters"] == ref.step(wb, 2e-4)["iters"]
     assert np.array_equal(host(wa), host(wb))
+
+
+def test_profiler_classes_cover_the_step(G):
+    """Every kernel class of a mixed step is timed: flux, operator, ILU,
+    Gram-Schmidt, update, FP64 residual, correction and the small kernels; the
+    work counters agree with the residuals and Arnoldi iterations run."""
+    c = I.shock_vortex_case(40, 20)
+    m = G.GksMesh(c.mesh, precision=G.MIXED, basis_fp32=1, warm_extrap=2)
+    w = dev(c.w0)
+    m.step(w, 2e-4)
+    m.profile_begin(range(G.PROF_CLASSES))
+    for _ in range(3):
+        m.step(w, 2e-4)
+    p = m.profile_end()
+    assert len(p["n"]) == G.PROF_CLASSES == 8
+    assert all(n > 0 for n in p["n"]) and all(t > 0.0 for t in p["ms"]), p
+    assert p["arnoldi"] > 0 and p["precond"] == p["arnoldi"]
+    # one residual at the start of each solve and one after every cycle
+    assert p["residuals"] >= 2 * 3 and p["n"][G.PROF_RESID] == p["residuals"]
