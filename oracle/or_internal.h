@@ -24,7 +24,8 @@ typedef struct or_params {
     int    gmres_maxit; /* iteration cap per variable                            */
     double gmres_rtol;  /* relative residual target                              */
     int    tau2_exact;  /* 1: c4..c6 with the 2 tau^2 (1 - e^{-t/tau}) term       */
-    int    slope0_mode; /* 0: interface-equilibrium derivatives = mean of L/R     */
+    int    slope0_mode; /* interface-equilibrium derivatives: 0 mean of L/R,      */
+                        /* 1 kinetic weighting (half-space moments of L/R slopes) */
     int    limiter;     /* 1: shock detector + DWBAP limiter (Sec. III.C); 2: the
                            detector with first order in limited cells (robust)   */
     int    second_order; /* 1: k_i = 1 for every cell (linear CLS reconstruction) */
@@ -90,6 +91,7 @@ int  or_dense_lu_solve(int n, double *a, double *b);
 /* kinetic part (or_kinetic.c) */
 void or_gauss_legendre(int n, double *x, double *w);
 void or_time_integrals(double dt, double tau, int tau2_exact, double *c);
+int  or_interface_w0(const double *wl, const double *wr, double gamma, int mode, double *w0);
 int  or_gp_flux(const double *wl, const double *wr, double dt, const or_params *prm,
                 double *f, double *aux);
 

@@ -367,6 +367,54 @@ static double heat_moment(const poly *Q, const moments *m, double U, double V)
     return q;
 }
 
+/* Interface equilibrium W0 of one Gauss point, rows value, d/dn, d/dt, d2/dn2,
+ * d2/dndt, d2/dt2 (face frame), from the left/right states with their slopes.
+ * The value is rho_l <psi>_{u>0,l} + rho_r <psi>_{u<0,r}.  The derivative rows:
+ *   mode 0: the mean of the left and right rows;
+ *   mode 1: the kinetic weighting of the same splitting, the half-space moments
+ *     of the derivatives of the two distributions, rho_k <psi g_k'/g_k>_k with
+ *     g_n/g = a1.psi, g_t/g = a2.psi, g_nn/g = (a1.psi)^2 + a11.psi,
+ *     g_nt/g = (a1.psi)(a2.psi) + a12.psi, g_tt/g = (a2.psi)^2 + a22.psi
+ *     (the derivatives of a Maxwellian in the paper's nomenclature); these are
+ *     the exact derivatives of the value formula when the two states vary as
+ *     their reconstructions do. */
+static void interface_w0(const kstate *L, const kstate *R, const double *wl, const double *wr, int mode,
+                         double *w0)
+{
+    double ml[4], mr[4];
+    poly one;
+    p_mono(&one, 1.0, 0, 0, 0);
+    psi_moment(&one, &L->half, ml);
+    psi_moment(&one, &R->half, mr);
+    for (int k = 0; k < 4; ++k) w0[k] = L->rho * ml[k] + R->rho * mr[k];
+    if (mode == 0) {
+        for (int k = 4; k < 24; ++k) w0[k] = 0.5 * (wl[k] + wr[k]);
+        return;
+    }
+    for (int k = 4; k < 24; ++k) w0[k] = 0.0;
+    const kstate *S[2] = {L, R};
+    for (int side = 0; side < 2; ++side) {
+        const kstate *s = S[side];
+        poly s1, s2, t, u;
+        double out[4];
+        p_slope(&s1, s->a1);
+        p_slope(&s2, s->a2);
+        psi_moment(&s1, &s->half, out);
+        for (int q = 0; q < 4; ++q) w0[4 + q] += s->rho * out[q];
+        psi_moment(&s2, &s->half, out);
+        for (int q = 0; q < 4; ++q) w0[8 + q] += s->rho * out[q];
+        const poly *fa[3] = {&s1, &s1, &s2}, *fb[3] = {&s1, &s2, &s2};
+        const double *sec[3] = {s->a11, s->a12, s->a22};
+        for (int r = 0; r < 3; ++r) {
+            p_mul(&t, fa[r], fb[r]);
+            p_slope(&u, sec[r]);
+            p_axpy(&t, 1.0, &u);
+            psi_moment(&t, &s->half, out);
+            for (int q = 0; q < 4; ++q) w0[12 + 4 * r + q] += s->rho * out[q];
+        }
+    }
+}
+
 /* Time-integrated flux through a unit-length face at one Gauss point, in the
  * face frame, from the left and right states wl[24], wr[24] (rows: value,
  * d/dn, d/dt, d2/dn2, d2/dndt, d2/dt2).  f[4] = int_0^dt F dt.
@@ -385,13 +433,8 @@ int or_gp_flux(const double *wl, const double *wr, double dt, const or_params *p
     state_slopes(&R, wr, 0);
 
     /* interface equilibrium: W0 = rho_l <psi>_{u>0,l} + rho_r <psi>_{u<0,r} */
-    double w0[24], ml[4], mr[4];
-    poly one;
-    p_mono(&one, 1.0, 0, 0, 0);
-    psi_moment(&one, &L.half, ml);
-    psi_moment(&one, &R.half, mr);
-    for (int k = 0; k < 4; ++k) w0[k] = L.rho * ml[k] + R.rho * mr[k];
-    for (int k = 4; k < 24; ++k) w0[k] = 0.5 * (wl[k] + wr[k]);   /* slope0_mode 0 */
+    double w0[24];
+    interface_w0(&L, &R, wl, wr, prm->slope0_mode, w0);
     state_moments(&Z, w0, gamma, 0);
     if (!(Z.rho > 0.0) || !(Z.p > 0.0)) return 1;
     state_slopes(&Z, w0, 1);
@@ -431,6 +474,22 @@ int or_gp_flux(const double *wl, const double *wr, double dt, const or_params *p
         for (int k = 0; k < 9; ++k) aux[5 + k] = C[k];
         aux[14] = L.p; aux[15] = R.p;
     }
+    return g_overflow ? 2 : 0;
+}
+
+/* W0 rows [24] of a Gauss point (exported for tests; see interface_w0).
+ * Returns nonzero if a state is not physical. */
+int or_interface_w0(const double *wl, const double *wr, double gamma, int mode, double *w0)
+{
+    g_K = 2.0 / (gamma - 1.0) - 2.0;
+    g_overflow = 0;
+    kstate L, R;
+    state_moments(&L, wl, gamma, +1);
+    state_moments(&R, wr, gamma, -1);
+    if (!(L.rho > 0.0) || !(R.rho > 0.0) || !(L.p > 0.0) || !(R.p > 0.0)) return 1;
+    state_slopes(&L, wl, 0);
+    state_slopes(&R, wr, 0);
+    interface_w0(&L, &R, wl, wr, mode, w0);
     return g_overflow ? 2 : 0;
 }
 

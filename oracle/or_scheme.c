@@ -47,7 +47,10 @@ or_mesh *or_mesh_new(const double *nodes, int64_t n_nodes, const int32_t *tris, 
                      const double *bc_state, const or_params *prm, int *err)
 {
     *err = 0;
-    if (n_tri <= 0 || n_nodes <= 0 || n_face <= 0 || prm->slope0_mode != 0) { *err = -10; return NULL; }
+    if (n_tri <= 0 || n_nodes <= 0 || n_face <= 0 || (prm->slope0_mode != 0 && prm->slope0_mode != 1)) {
+        *err = -10;
+        return NULL;
+    }
     or_mesh *m = calloc(1, sizeof(or_mesh));
     if (!m) { *err = -1; return NULL; }
     m->prm = *prm;

@@ -84,6 +84,8 @@ def _load():
         lib.or_point_flux.argtypes = [P, P, D, C.POINTER(Params), P, P]
         lib.or_state_slopes.restype = I
         lib.or_state_slopes.argtypes = [P, D, P]
+        lib.or_interface_w0.restype = I
+        lib.or_interface_w0.argtypes = [P, P, D, I, P]
         lib.or_moment_abz.restype = D
         lib.or_moment_abz.argtypes = [D, D, D, D, I, I, I, I]
         lib.or_time_integrals.argtypes = [D, D, I, P]
@@ -282,6 +284,19 @@ def state_slopes(w: np.ndarray, gamma: float = 1.4) -> np.ndarray:
     out = np.zeros((9, 4))
     if lib.or_state_slopes(_ptr(w), float(gamma), _ptr(out)) != 0:
         raise RuntimeError("polynomial degree overflow")
+    return out
+
+
+def interface_w0(wl: np.ndarray, wr: np.ndarray, gamma: float = 1.4, mode: int = 0) -> np.ndarray:
+    """Interface equilibrium W0 (6, 4) of one Gauss point from the face-frame
+    states wl, wr (6, 4); mode = slope0_mode (0 mean, 1 kinetic weighting)."""
+    lib = _load()
+    wl = np.ascontiguousarray(wl, dtype=np.float64)
+    wr = np.ascontiguousarray(wr, dtype=np.float64)
+    out = np.zeros((6, 4))
+    st = lib.or_interface_w0(_ptr(wl), _ptr(wr), float(gamma), int(mode), _ptr(out))
+    if st != 0:
+        raise RuntimeError("non-physical state" if st == 1 else "polynomial degree overflow")
     return out
 
 

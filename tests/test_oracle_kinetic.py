@@ -335,3 +335,67 @@ def test_prandtl_rescales_only_the_heat_flux(oracle_mod):
     assert np.all(np.abs(f2[:3] - f1[:3]) <= 1e-15 * np.abs(f1[:3]).max())
     heat = -cp * mu * g * dt
     assert abs((f2[3] - f1[3]) - (1.0 / 0.72 - 1.0) * heat) < 0.02 * abs((1.0 / 0.72 - 1.0) * heat)
+
+
+# --------------------------------------------------- interface derivatives (slope0_mode)
+
+
+def _two_fields():
+    rho, U, V, p = _field("general")
+    rho2 = 0.6 + sp.Rational(1, 5) * sp.cos(sp.Rational(9, 10) * x_ - sp.Rational(3, 5) * y_)
+    U2 = sp.Rational(-1, 5) + sp.Rational(3, 10) * sp.sin(sp.Rational(6, 5) * x_ + sp.Rational(1, 2) * y_)
+    V2 = sp.Rational(2, 5) + sp.Rational(1, 5) * sp.cos(sp.Rational(3, 10) * x_ + y_)
+    p2 = sp.Rational(7, 10) + sp.Rational(1, 10) * sp.sin(x_ - sp.Rational(2, 5) * y_)
+    pt = {x_: 0.4, y_: -0.2}
+    return _rows(_cons(rho, U, V, p), pt), _rows(_cons(rho2, U2, V2, p2), pt)
+
+
+def _taylor(rows, x, y):
+    """Value row of the state whose reconstruction has the given rows, at (x, y)."""
+    out = np.zeros((6, 4))
+    out[0] = rows[0] + x * rows[1] + y * rows[2] + 0.5 * x * x * rows[3] + x * y * rows[4] + 0.5 * y * y * rows[5]
+    return out
+
+
+def test_kinetic_interface_derivatives_are_derivatives_of_w0(oracle_mod):
+    """slope0_mode = 1: the derivative rows of W0 are the derivatives of the value
+    rho_l <psi>_{u>0,l} + rho_r <psi>_{u<0,r} when the left and right states vary
+    as their reconstructions do: checked against Richardson-extrapolated central
+    differences of that value (computed from shifted states with zero derivative
+    rows, so only the zeroth-order half-space moments enter)."""
+    wl, wr = _two_fields()
+    got = oracle_mod.interface_w0(wl, wr, GAMMA, mode=1)
+
+    def F(x, y):
+        return oracle_mod.interface_w0(_taylor(wl, x, y), _taylor(wr, x, y), GAMMA, mode=0)[0]
+
+    def rich(d, e):
+        return (4.0 * d(e / 2) - d(e)) / 3.0
+
+    e = 2e-3
+    d_n = rich(lambda h: (F(h, 0) - F(-h, 0)) / (2 * h), e)
+    d_t = rich(lambda h: (F(0, h) - F(0, -h)) / (2 * h), e)
+    d_nn = rich(lambda h: (F(h, 0) - 2 * F(0, 0) + F(-h, 0)) / (h * h), e)
+    d_tt = rich(lambda h: (F(0, h) - 2 * F(0, 0) + F(0, -h)) / (h * h), e)
+    d_nt = rich(lambda h: (F(h, h) - F(h, -h) - F(-h, h) + F(-h, -h)) / (4 * h * h), e)
+    fd = np.array([F(0, 0), d_n, d_t, d_nn, d_nt, d_tt])
+    for r in range(6):
+        scale = np.max(np.abs(fd[r]))
+        assert np.max(np.abs(got[r] - fd[r])) <= 1e-8 * scale, (r, got[r], fd[r])
+    # and they differ from the mean of the left and right rows (mode 0)
+    mean = oracle_mod.interface_w0(wl, wr, GAMMA, mode=0)
+    assert np.max(np.abs(got[1:] - mean[1:])) > 1e-3 * np.max(np.abs(mean[1:]))
+
+
+def test_kinetic_interface_derivatives_reduce_to_the_state_for_continuous_data(oracle_mod):
+    """For equal left and right states the two half spaces add up to the full
+    space: both modes give W0 = W with the state's own derivative rows, and the
+    same flux."""
+    wl, _ = _two_fields()
+    for mode in (0, 1):
+        w0 = oracle_mod.interface_w0(wl, wl, GAMMA, mode=mode)
+        assert np.allclose(w0, wl, rtol=1e-13, atol=1e-13 * np.max(np.abs(wl)))
+    f0, _, s0 = oracle_mod.point_flux(wl, wl, 0.01)
+    f1, _, s1 = oracle_mod.point_flux(wl, wl, 0.01, slope0_mode=1)
+    assert s0 == s1 == 0
+    assert np.allclose(f1, f0, rtol=1e-12, atol=1e-14)
