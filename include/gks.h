@@ -140,6 +140,13 @@ typedef struct gks_config {
     double prandtl;        /* Prandtl number (> 0, default 1 = the BGK model's own):
                               != 1 rescales the heat flux relative to the interface
                               velocity by 1/Pr in the energy flux (not in the paper)  */
+    int32_t slope0_mode;   /* derivatives of the interface equilibrium W0 (the paper
+                              defers their construction to its references, Sec. II.B):
+                              0 the mean of the left and right reconstructed
+                              derivatives (default); 1 kinetic weighting, the
+                              half-space moments rho_l <psi g_l'/g_l>_{u>0} +
+                              rho_r <psi g_r'/g_r>_{u<0} of the derivatives of the two
+                              distributions                                            */
 } gks_config;
 
 typedef struct gks_mesh gks_mesh;

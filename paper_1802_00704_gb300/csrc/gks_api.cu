@@ -62,6 +62,7 @@ gks_status check_config(const gks_config &c)
     ok = ok && (c.second_order == 0 || c.second_order == 1);
     ok = ok && c.no_graphs >= 0 && c.no_graphs <= 2;
     ok = ok && (c.limit_char == 0 || c.limit_char == 1);
+    ok = ok && (c.slope0_mode == 0 || c.slope0_mode == 1);
     if (!ok) {
         set_error("invalid gks_config");
         return GKS_EINVAL;
@@ -182,6 +183,7 @@ void gks_config_default(gks_config *c)
     c->tau2_exact = 0;
     c->inner_rtol = 1e-6;
     c->prandtl = 1.0;
+    c->slope0_mode = 0;
 }
 
 const char *gks_last_error(void) { return gks::last_error(); }

@@ -7,6 +7,8 @@
 // order, one write per cell.
 #include <cfloat>
 
+#include <type_traits>
+
 #include "gks_internal.h"
 #include "gks_kinetic.cuh"
 
@@ -210,7 +212,8 @@ __global__ void k_to_f32(const double *__restrict__ x, float *__restrict__ y, in
 
 // MIXED: interface state and leading terms in FP64, slope-carrying terms in FP32.
 // HEAT: Prandtl correction of the energy flux (prandtl != 1).
-template <bool MIXED, bool HEAT>
+// KIN: interface derivatives by kinetic weighting (slope0_mode 1).
+template <bool MIXED, bool HEAT, bool KIN>
 __global__ void __launch_bounds__(kFluxBlock, MIXED ? 4 : 1) k_face_flux(DeviceMesh d, const double *__restrict__ w,
                                                           const double *__restrict__ x,
                                                           const float *__restrict__ x32, double dt_const,
@@ -243,7 +246,7 @@ __global__ void __launch_bounds__(kFluxBlock, MIXED ? 4 : 1) k_face_flux(DeviceM
                 const double bc[4] = {d.bc[f], d.bc[F + f], d.bc[2 * F + f], d.bc[3 * F + f]};
                 ghost_mixed(d.ftag[f], bc, nx, ny, gamma, vl, dl, vr, dr);
             }
-            ok = kin::gp_flux_mixed_split<HEAT>(vl, vr, dl, dr, dt, gamma, K, mu, tau2, fk, prandtl);
+            ok = kin::gp_flux_mixed_split<HEAT, KIN>(vl, vr, dl, dr, dt, gamma, K, mu, tau2, fk, prandtl);
         } else {
             double gl[24], wl[24], wr[24];
             recon(d, w, x, l, d.gl[(2 * k) * F + f], d.gl[(2 * k + 1) * F + f], gl);
@@ -255,7 +258,7 @@ __global__ void __launch_bounds__(kFluxBlock, MIXED ? 4 : 1) k_face_flux(DeviceM
                 const double bc[4] = {d.bc[f], d.bc[F + f], d.bc[2 * F + f], d.bc[3 * F + f]};
                 ghost(d.ftag[f], bc, nx, ny, gamma, wl, wr);
             }
-            ok = kin::gp_flux<double, HEAT>(wl, wr, dt, gamma, mu, tau2, fk, prandtl);
+            ok = kin::gp_flux<double, HEAT, KIN>(wl, wr, dt, gamma, mu, tau2, fk, prandtl);
         }
         if (!ok) atomicOr(&status[cs], kStatusNonPhys);
         const double s = 0.5 * d.flen[f];      // Gauss weight 1/2 times the face length
@@ -355,7 +358,7 @@ __global__ void k_clip_dt(double *dt, double *t, const double *__restrict__ tf, 
     t[c] += dt[c];
 }
 
-template <bool MIXED, bool HEAT>
+template <bool MIXED, bool HEAT, bool KIN>
 __global__ void __launch_bounds__(kFluxBlock) k_point_flux(int64_t n, const double *__restrict__ wl,
                                                            const double *__restrict__ wr, double dt, double gamma,
                                                            double mu, int tau2, double prandtl,
@@ -369,8 +372,8 @@ __global__ void __launch_bounds__(kFluxBlock) k_point_flux(int64_t n, const doub
         a[k] = wl[24 * q + k];
         b[k] = wr[24 * q + k];
     }
-    const bool ok = MIXED ? kin::gp_flux_mixed<HEAT>(a, b, dt, gamma, mu, tau2, f, prandtl)
-                          : kin::gp_flux<double, HEAT>(a, b, dt, gamma, mu, tau2, f, prandtl);
+    const bool ok = MIXED ? kin::gp_flux_mixed<HEAT, KIN>(a, b, dt, gamma, mu, tau2, f, prandtl)
+                          : kin::gp_flux<double, HEAT, KIN>(a, b, dt, gamma, mu, tau2, f, prandtl);
     if (!ok && status) atomicOr(status, kStatusNonPhys);
 #pragma unroll
     for (int k = 0; k < 4; ++k) out[4 * q + k] = f[k];
@@ -433,6 +436,22 @@ __global__ void k_sum4_final(const double *__restrict__ part, int n, double *out
 
 inline unsigned blocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
+// f(std::bool_constant<a>, std::bool_constant<b>, std::bool_constant<c>): one
+// kernel instantiation per combination of three compile-time switches
+template <typename F>
+void dispatch3(bool a, bool b, bool c, F &&f)
+{
+    using Y = std::true_type;
+    using N = std::false_type;
+    if (a) {
+        if (b) c ? f(Y{}, Y{}, Y{}) : f(Y{}, Y{}, N{});
+        else c ? f(Y{}, N{}, Y{}) : f(Y{}, N{}, N{});
+    } else {
+        if (b) c ? f(N{}, Y{}, Y{}) : f(N{}, Y{}, N{});
+        else c ? f(N{}, N{}, Y{}) : f(N{}, N{}, N{});
+    }
+}
+
 }  // namespace
 
 gks_status launch_flux(gks_mesh *m, const double *w, const double *x, double dt_const, const double *dt_dev,
@@ -444,24 +463,18 @@ gks_status launch_flux(gks_mesh *m, const double *w, const double *x, double dt_
     const gks_config &c = m->cfg;
     const bool heat = c.prandtl != 1.0;
     const unsigned g = blocks(npts, kFluxBlock);
-    if (c.precision == GKS_MIXED) {
+    const bool mixed = c.precision == GKS_MIXED;
+    if (mixed) {
         // FP32 copy of the coefficients: the slope-carrying rows of every Gauss
         // point of a cell read it instead of converting the FP64 values again
         k_to_f32<<<blocks(20 * m->d.T, kBlock), kBlock, 0, s>>>(x, m->wk.x32, 20 * m->d.T);
         note_launch();
-        if (heat)
-            k_face_flux<true, true><<<g, kFluxBlock, 0, s>>>(m->d, w, x, m->wk.x32, dt_const, dt_dev, c.gamma, K, c.mu,
-                                                             c.tau2_exact, c.prandtl, flux, m->wk.status);
-        else
-            k_face_flux<true, false><<<g, kFluxBlock, 0, s>>>(m->d, w, x, m->wk.x32, dt_const, dt_dev, c.gamma, K,
-                                                              c.mu, c.tau2_exact, c.prandtl, flux, m->wk.status);
-    } else if (heat) {
-        k_face_flux<false, true><<<g, kFluxBlock, 0, s>>>(m->d, w, x, nullptr, dt_const, dt_dev, c.gamma, K, c.mu,
-                                                          c.tau2_exact, c.prandtl, flux, m->wk.status);
-    } else {
-        k_face_flux<false, false><<<g, kFluxBlock, 0, s>>>(m->d, w, x, nullptr, dt_const, dt_dev, c.gamma, K, c.mu,
-                                                           c.tau2_exact, c.prandtl, flux, m->wk.status);
     }
+    dispatch3(mixed, heat, c.slope0_mode == 1, [&](auto M, auto H, auto Kw) {
+        k_face_flux<decltype(M)::value, decltype(H)::value, decltype(Kw)::value><<<g, kFluxBlock, 0, s>>>(
+            m->d, w, x, mixed ? m->wk.x32 : nullptr, dt_const, dt_dev, c.gamma, K, c.mu, c.tau2_exact, c.prandtl,
+            flux, m->wk.status);
+    });
     note_launch();
     prof_stop(m, slot, s);
     GKS_CUDA(cudaGetLastError());
@@ -494,18 +507,10 @@ gks_status launch_point_flux(int64_t n, const double *wl, const double *wr, doub
     if (n <= 0) return GKS_OK;
     const unsigned g = blocks(n, kFluxBlock);
     const bool heat = cfg.prandtl != 1.0;
-    if (cfg.precision == GKS_MIXED && heat)
-        k_point_flux<true, true><<<g, kFluxBlock, 0, s>>>(n, wl, wr, dt, cfg.gamma, cfg.mu, cfg.tau2_exact,
-                                                          cfg.prandtl, out, status);
-    else if (cfg.precision == GKS_MIXED)
-        k_point_flux<true, false><<<g, kFluxBlock, 0, s>>>(n, wl, wr, dt, cfg.gamma, cfg.mu, cfg.tau2_exact,
-                                                           cfg.prandtl, out, status);
-    else if (heat)
-        k_point_flux<false, true><<<g, kFluxBlock, 0, s>>>(n, wl, wr, dt, cfg.gamma, cfg.mu, cfg.tau2_exact,
-                                                           cfg.prandtl, out, status);
-    else
-        k_point_flux<false, false><<<g, kFluxBlock, 0, s>>>(n, wl, wr, dt, cfg.gamma, cfg.mu, cfg.tau2_exact,
-                                                            cfg.prandtl, out, status);
+    dispatch3(cfg.precision == GKS_MIXED, heat, cfg.slope0_mode == 1, [&](auto M, auto H, auto Kw) {
+        k_point_flux<decltype(M)::value, decltype(H)::value, decltype(Kw)::value><<<g, kFluxBlock, 0, s>>>(
+            n, wl, wr, dt, cfg.gamma, cfg.mu, cfg.tau2_exact, cfg.prandtl, out, status);
+    });
     note_launch();
     GKS_CUDA(cudaGetLastError());
     return GKS_OK;

@@ -407,13 +407,50 @@ __device__ __forceinline__ bool interface_state(const R *wl, const R *wr, R dt, 
     return true;
 }
 
+// Kinetic weighting of the interface derivatives (slope0_mode 1): the
+// derivative rows of W0 become the half-space moments of the derivatives of
+// the left and right distributions, rho_k <psi g_k'/g_k>_k (u > 0 left, u < 0
+// right) with g_n/g = a1.psi, g_t/g = a2.psi, g_nn/g = (a1.psi)^2 + a11.psi,
+// g_nt/g = (a1.psi)(a2.psi) + a12.psi, g_tt/g = (a2.psi)^2 + a22.psi: the
+// derivatives of the value rho_l <psi>_{u>0} + rho_r <psi>_{u<0} when the two
+// states vary as their reconstructions do.  Needs the slopes of I.L and I.Rs.
+template <typename R>
+__device__ __forceinline__ void kinetic_w0(Iface<R> &I, R K)
+{
+#pragma unroll
+    for (int q = 4; q < 24; ++q) I.w0[q] = R(0);
+    Mom<R> m;
+    Poly<R> P;
+    R out[4];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const KState<R> &s = side ? I.Rs : I.L;
+        mom_half(s.U, s.lam, side ? R(-1) : R(1), m.u);
+        mom_full(s.V, s.lam, m.v);
+        mom_xi(s.lam, K, m.z);
+        const R *lin[5] = {s.a1, s.a2, s.a11, s.a12, s.a22};
+        const R *pa[5] = {nullptr, nullptr, s.a1, s.a1, s.a2}, *pb[5] = {nullptr, nullptr, s.a1, s.a2, s.a2};
+#pragma unroll
+        for (int r = 0; r < 5; ++r) {
+            pzero(P);
+            if (r >= 2) add_prod(P, R(1), pa[r], pb[r], 0, 0);
+            add_lin(P, R(1), lin[r], 0, 0);
+            psi_contract<R, 2>(P, m, out);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) I.w0[4 + 4 * r + q] += s.rho * out[q];
+        }
+    }
+}
+
 // Flux terms of Eqs. (11) and (15) at y = 0, from the slopes of the three
 // states.  with_const = false leaves out the zeroth-order terms C1 g0 and
 // C7 g_k (see lead_flux).
 //
 // HEAT: also d_alpha = <psi_alpha f> (the time-integrated moments without the
 // factor u), for the heat flux of the Prandtl correction.
-template <typename R, bool HEAT = false>
+// KIN: interface derivatives by kinetic weighting (kinetic_w0) instead of the
+// mean of the left and right rows held in I.w0.
+template <typename R, bool HEAT = false, bool KIN = false>
 __device__ __forceinline__ void body_flux(const R *wl, const R *wr, Iface<R> &I, R gamma, bool with_const, R *f,
                                           R *d = nullptr)
 {
@@ -425,6 +462,18 @@ __device__ __forceinline__ void body_flux(const R *wl, const R *wr, Iface<R> &I,
     R out[4];
     Poly<R> Q;
     Mom<R> m;
+    if (KIN) {
+        // the left and right slopes first: the interface derivatives are built from them
+        mom_full(I.L.U, I.L.lam, m.u);
+        mom_full(I.L.V, I.L.lam, m.v);
+        mom_xi(I.L.lam, K, m.z);
+        slopes(I.L, wl, K, m, false);
+        mom_full(I.Rs.U, I.Rs.lam, m.u);
+        mom_full(I.Rs.V, I.Rs.lam, m.v);
+        mom_xi(I.Rs.lam, K, m.z);
+        slopes(I.Rs, wr, K, m, false);
+        kinetic_w0(I, K);
+    }
     // equilibrium part, Eq. (15)
     mom_full(I.Z.U, I.Z.lam, m.u);
     mom_full(I.Z.V, I.Z.lam, m.v);
@@ -445,7 +494,7 @@ __device__ __forceinline__ void body_flux(const R *wl, const R *wr, Iface<R> &I,
     mom_full(I.L.U, I.L.lam, m.u);
     mom_full(I.L.V, I.L.lam, m.v);
     mom_xi(I.L.lam, K, m.z);
-    slopes(I.L, wl, K, m, false);
+    if (!KIN) slopes(I.L, wl, K, m, false);
     build_q(Q, I.L, k7, kA, kL, kS, kAL, R(0));
     mom_half(I.L.U, I.L.lam, R(1), m.u);
     upsi_contract(Q, m, out);
@@ -459,7 +508,7 @@ __device__ __forceinline__ void body_flux(const R *wl, const R *wr, Iface<R> &I,
     mom_full(I.Rs.U, I.Rs.lam, m.u);
     mom_full(I.Rs.V, I.Rs.lam, m.v);
     mom_xi(I.Rs.lam, K, m.z);
-    slopes(I.Rs, wr, K, m, false);
+    if (!KIN) slopes(I.Rs, wr, K, m, false);
     build_q(Q, I.Rs, k7, kA, kL, kS, kAL, R(0));
     mom_half(I.Rs.U, I.Rs.lam, R(-1), m.u);
     upsi_contract(Q, m, out);
@@ -525,7 +574,7 @@ __device__ __forceinline__ void lead_flux(const Iface<R> &I, R gamma, R *f)
 // HEAT: Prandtl correction F_E += (1/Pr - 1) q, q the heat flux relative to the
 // interface equilibrium velocity (not in the paper; the BGK model has Pr = 1;
 // the correction of the BGK-NS scheme, K. Xu, J. Comput. Phys. 171 (2001)).
-template <typename R, bool HEAT = false>
+template <typename R, bool HEAT = false, bool KIN = false>
 __device__ __forceinline__ bool gp_flux(const R *wl, const R *wr, R dt, R gamma, R mu, int tau2_exact, R *f,
                                         R prandtl = R(1))
 {
@@ -536,7 +585,7 @@ __device__ __forceinline__ bool gp_flux(const R *wl, const R *wr, R dt, R gamma,
         return false;
     }
     R d[4];
-    body_flux<R, HEAT>(wl, wr, I, gamma, true, f, d);
+    body_flux<R, HEAT, KIN>(wl, wr, I, gamma, true, f, d);
     if (HEAT) f[3] += (R(1) / prandtl - R(1)) * heat_flux(f, d, I.Z.U, I.Z.V);
     return true;
 }
@@ -600,7 +649,7 @@ __device__ __forceinline__ void lead_integrals(double dt, double tau, double &c0
 // collision time, the time integrals and the zeroth-order terms
 // C1 rho0 <u psi>_0 + C7 (rho_l <u psi>_{u>0} + rho_r <u psi>_{u<0}) are FP64;
 // every slope-carrying term is FP32.
-template <bool HEAT = false>
+template <bool HEAT = false, bool KIN = false>
 __device__ __forceinline__ bool gp_flux_mixed_split(const double *vl, const double *vr, const float *dl, const float *dr,
                                                     double dt, double gamma, double K, double mu, int tau2_exact,
                                                     double *f, double prandtl = 1.0)
@@ -672,7 +721,7 @@ __device__ __forceinline__ bool gp_flux_mixed_split(const double *vl, const doub
     J.tau = float(tau);
     time_integrals(float(dt), J.tau, tau2_exact, J.C);
     float dg[4];
-    body_flux<float, HEAT>(fl, fr, J, gf, false, g, dg);
+    body_flux<float, HEAT, KIN>(fl, fr, J, gf, false, g, dg);
 #pragma unroll
     for (int q = 0; q < 4; ++q) f[q] += double(g[q]);
     if (HEAT) {
@@ -685,7 +734,7 @@ __device__ __forceinline__ bool gp_flux_mixed_split(const double *vl, const doub
 }
 
 // Mixed precision flux from FP64 rows [6][4] (used by the point-flux entry point).
-template <bool HEAT = false>
+template <bool HEAT = false, bool KIN = false>
 __device__ __forceinline__ bool gp_flux_mixed(const double *wl, const double *wr, double dt, double gamma, double mu,
                                               int tau2_exact, double *f, double prandtl = 1.0)
 {
@@ -695,8 +744,8 @@ __device__ __forceinline__ bool gp_flux_mixed(const double *wl, const double *wr
         dl[q] = float(wl[4 + q]);
         dr[q] = float(wr[4 + q]);
     }
-    return gp_flux_mixed_split<HEAT>(wl, wr, dl, dr, dt, gamma, 2.0 / (gamma - 1.0) - 2.0, mu, tau2_exact, f,
-                                     prandtl);
+    return gp_flux_mixed_split<HEAT, KIN>(wl, wr, dl, dr, dt, gamma, 2.0 / (gamma - 1.0) - 2.0, mu, tau2_exact, f,
+                                          prandtl);
 }
 
 }  // namespace kin
