@@ -39,6 +39,10 @@ FP64_PEAK_TFLOPS = 4 * 152 * 2.07e9 / 1e12
 # (dadd + dmul + 2 dfma, ncu instruction counters on the 399,424-triangle case;
 # profiles/flux_fp64_shock_vortex_400k.md).
 FLUX_FP64_FLOP_PER_GP = 8392.3
+# how the CLS solve is launched (gks_config.no_graphs): one graph per solve with
+# device-side GMRES control, per-part graphs under host control (ncu cannot
+# profile the kernel nodes of graphs with conditional nodes), or plain launches
+GRAPHS = {"device": 0, "host": 2, "none": 1}
 # event-timed kernel classes of the library's profiler, in its class order
 PROF_NAMES = ["flux", "spmv", "ilu", "orth", "update", "resid", "corr", "ctl"]
 # FP64 and FP32 flops per Gauss point of the mixed flux kernel (same counters,
@@ -260,7 +264,7 @@ def timed_leg(args, case, precision: str, world: int, dev, sample_clocks: bool):
     mixed = precision == "mixed"
     m = gks.GksMesh(case.mesh, precond=gks.PC_ILU_EXACT if exact else gks.PC_ILU_SWEEP, ilu_sweeps=args.sweeps,
                     precision=gks.MIXED if mixed else gks.FP64, basis_fp32=int(mixed and args.basis == "fp32"),
-                    limiter=int(args.limiter), warm_extrap=WARM[args.warm])
+                    limiter=int(args.limiter), warm_extrap=WARM[args.warm], no_graphs=GRAPHS[args.graphs])
     w = torch.from_numpy(case.w0.copy()).to(dev)
     stream = torch.cuda.current_stream()
     tune = m.autotune(w, trial_steps=2) if args.tune else None
@@ -372,6 +376,7 @@ def run_gks(args, world, rank, local):
                                f"{F} faces, GMRES(30) rtol 1e-12",
                    "n_tri": T, "n_face": F, "precision": args.precision,
                    "krylov_basis": "fp32" if basis32 else "fp64", "limiter": bool(args.limiter),
+                   "solve_graphs": args.graphs,
                    "warm_start": args.warm, "autotuned": bool(args.tune), "knobs": main["knobs"],
                    "precond": ("ilu0_rcm_exact" if exact else f"ilu0_rcm_sweep{main['knobs']['ilu_sweeps']}"),
                    "l2": f"inputs larger than L2: {st['device_bytes'] / 2**30:.1f} GiB resident per replica",
@@ -443,7 +448,7 @@ def run_batch(args, world, rank, local):
     def leg(prec_mixed: bool, clocks: bool):
         b = gks.GksMesh.batch([c.mesh for c in cases], precision=gks.MIXED if prec_mixed else gks.FP64,
                               limiter=2, gmres_m=12, warm_extrap=WARM[args.warm],
-                              basis_fp32=int(prec_mixed and args.basis == "fp32"))
+                              basis_fp32=int(prec_mixed and args.basis == "fp32"), no_graphs=GRAPHS[args.graphs])
         w = torch.from_numpy(w0.copy()).to(dev)
         tune = b.autotune(w, trial_steps=1) if args.tune else None
         r = b.batch_run(w, max_steps=args.warmup)
@@ -568,6 +573,8 @@ def main():
                     help="Krylov basis of the mixed path's inner cycles: FP32 (FP32 Gram-Schmidt arithmetic, "
                          "FP64 sums across threads) or FP64")
     ap.add_argument("--limiter", action="store_true", help="shock detector + DWBAP limiter on")
+    ap.add_argument("--graphs", default="device", choices=sorted(GRAPHS),
+                    help="CLS solve launch: device-controlled graph (default), per-part graphs, plain launches")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the autotuner (ilu_sweeps, warm start, inner tolerance) before the warm-up")
     ap.add_argument("--warm", default="extrap", choices=sorted(WARM),

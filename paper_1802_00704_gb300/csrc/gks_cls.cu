@@ -424,9 +424,10 @@ __global__ void k_ilu_fwd(DeviceMesh d, const TM *__restrict__ Pg, const TM *__r
 // loaded before the neighbour gathers; with no upper neighbour the sum is 0
 // and x_i = z_i exactly).
 template <typename TZ, typename TM>
-__global__ void k_ilu_bwd(DeviceMesh d, const TM *__restrict__ Pg, const TM *__restrict__ alg,
-                          const TM *__restrict__ exg, const TM *__restrict__ eyg, const int32_t *__restrict__ rows,
-                          int64_t nrows, const TZ *z, const TZ *xin, TZ *xout)
+__global__ void __launch_bounds__(kBlock, sizeof(TM) == 4 ? 3 : 1)
+    k_ilu_bwd(DeviceMesh d, const TM *__restrict__ Pg, const TM *__restrict__ alg, const TM *__restrict__ exg,
+              const TM *__restrict__ eyg, const int32_t *__restrict__ rows, int64_t nrows, const TZ *z, const TZ *xin,
+              TZ *xout)
 {
     const int64_t T = d.T;
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -469,9 +470,8 @@ __global__ void k_ilu_bwd(DeviceMesh d, const TM *__restrict__ Pg, const TM *__r
 // variable give part[blk][v][k].  Fixed order: the sums are deterministic.
 // TB: type of the stored basis.  An FP64 basis is multiplied and summed in
 // FP64; an FP32 basis (the inner cycles of the mixed mode) in FP32 within a
-// thread (20 products), each thread's sum then widened once and summed across
-// threads and blocks in FP64, so that the FP64 pipe sees one conversion per
-// 20 products instead of a DFMA per product.
+// warp (640 products), each warp's sum then widened once and summed across
+// warps and blocks in FP64, so that the FP64 pipe sees almost nothing.
 template <typename TB>
 __global__ void __launch_bounds__(kDotThreads, 3) k_dots(int64_t T, int64_t nblk, const TB *__restrict__ V,
                                                          const TB *__restrict__ w, double *__restrict__ part,
@@ -494,9 +494,9 @@ __global__ void __launch_bounds__(kDotThreads, 3) k_dots(int64_t T, int64_t nblk
 #pragma unroll
             for (int l = 0; l < ND; ++l) st = i < T ? fma(vk[l * T + i], wv[l * T + i], st) : st;
         }
-        double s = double(st);
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) sh[warp] = s;
+        // warp sum in the basis precision, widened once per warp
+        for (int o = 16; o > 0; o >>= 1) st += __shfl_down_sync(0xffffffffu, st, o);
+        if (lane == 0) sh[warp] = double(st);
         __syncthreads();
         if (threadIdx.x < NV) part[(b * NV + threadIdx.x) * pstride + k] = sh[2 * threadIdx.x] + sh[2 * threadIdx.x + 1];
         __syncthreads();
@@ -549,8 +549,27 @@ __global__ void k_orth_update(DeviceMesh d, const TB *__restrict__ V, TB *__rest
         }
     }
     if (want_norm) {
-        double nd[NV] = {double(nrm[0]), double(nrm[1]), double(nrm[2]), double(nrm[3])};
-        block_sum4(nd, sh);
+        double nd[NV];
+        if (std::is_same<TB, float>::value) {
+            // warp sums in FP32, widened once per warp
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                for (int o = 16; o > 0; o >>= 1) nrm[v] += __shfl_down_sync(0xffffffffu, nrm[v], o);
+                if (lane == 0) sh[warp * NV + v] = double(nrm[v]);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0)
+                for (int v = 0; v < NV; ++v) {
+                    double t = 0.0;
+                    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w * NV + v];
+                    nd[v] = t;
+                }
+        } else {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) nd[v] = double(nrm[v]);
+            block_sum4(nd, sh);
+        }
         if (threadIdx.x == 0)
             for (int v = 0; v < NV; ++v) part[(blockIdx.x * NV + v) * pstride + 0] = nd[v];
     }
@@ -657,16 +676,19 @@ __global__ void k_backsolve(int m, const double *__restrict__ H, const double *_
 // cycle (the combination adds 2^e sum y_k Z_k, so its FP32 sums stay near unit
 // size), and the next residual's exponent comes from the cycle's estimate
 // |g_jv| of its norm (at least 1e-3 rtol |b|).
+// y32 (optional): an FP32 copy of the result for the FP32 combination.
 __global__ void k_scale_y(int m, double *y, const double *__restrict__ vn, const int32_t *__restrict__ ctl, int ns,
                           const double *__restrict__ g = nullptr, const double *__restrict__ bnorm = nullptr,
-                          double rtol = 0.0, int32_t *sexp = nullptr)
+                          double rtol = 0.0, int32_t *sexp = nullptr, float *y32 = nullptr)
 {
     const int sy = blockIdx.x * blockDim.x + threadIdx.x;
     if (sy >= ns) return;
     const int jv = ctl[kCtlJv * ns + sy];
     const double f = sexp ? pow2(-sexp[sy]) : 1.0;
-    for (int k = 0; k < jv; ++k) y[sy * m + k] = sexp ? y[sy * m + k] / vn[sy * (m + 1) + k] * f
-                                                      : y[sy * m + k] / vn[sy * (m + 1) + k];
+    for (int k = 0; k < jv; ++k) {
+        y[sy * m + k] = sexp ? y[sy * m + k] / vn[sy * (m + 1) + k] * f : y[sy * m + k] / vn[sy * (m + 1) + k];
+        if (y32) y32[sy * m + k] = float(y[sy * m + k]);
+    }
     if (sexp && jv > 0) {
         const double est = fmax(fabs(g[sy * (m + 1) + jv]), 1e-3 * rtol * bnorm[sy]);
         if (est > 0.0 && est < 1e300) sexp[ns + sy] = max(-1000, ilogb(est));
@@ -681,10 +703,14 @@ __global__ void k_scale_y(int m, double *y, const double *__restrict__ vn, const
 // conversion and one FMA per value and Krylov vector.  With sexp given (FP32
 // basis): y carries 2^-e of the cycle (see k_scale_y) and the sum is scaled
 // back by 2^e in FP64 (exact).
+// y32 (FP32 Z only, optional): the FP32 copy of y, read instead of converting
+// y per thread; the scale 2^e is applied in FP32 when it is a normal FP32
+// number (|e| <= 100), so the FP64 pipe sees one conversion and one add per
+// value.
 template <typename TZ>
 __global__ void k_combine_z(DeviceMesh d, const TZ *__restrict__ Z, const double *__restrict__ y, int m,
                             const int32_t *__restrict__ ctl, int ns, double *__restrict__ x,
-                            const int32_t *__restrict__ sexp = nullptr)
+                            const int32_t *__restrict__ sexp = nullptr, const float *__restrict__ y32 = nullptr)
 {
     const int64_t T = d.T;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -696,13 +722,25 @@ __global__ void k_combine_z(DeviceMesh d, const TZ *__restrict__ Z, const double
     const int64_t vs = (int64_t)NX * T;
     TZ acc[ND] = {0, 0, 0, 0, 0};
     for (int k = 0; k < jv; ++k) {
-        const TZ yk = TZ(y[sy * m + k]);
+        const TZ yk = y32 ? TZ(y32[sy * m + k]) : TZ(y[sy * m + k]);
 #pragma unroll
         for (int l = 0; l < ND; ++l) acc[l] += yk * Z[k * vs + (v * ND + l) * T + i];
     }
-    const double f = sexp ? pow2(sexp[sy]) : 1.0;
+    if (sexp) {
+        const int e = sexp[sy];
+        if (std::is_same<TZ, float>::value && e >= -100 && e <= 100) {
+            const TZ fs = TZ(__int_as_float((e + 127) << 23));   // 2^e, exact
 #pragma unroll
-    for (int l = 0; l < ND; ++l) x[(v * ND + l) * T + i] += sexp ? double(acc[l]) * f : double(acc[l]);
+            for (int l = 0; l < ND; ++l) x[(v * ND + l) * T + i] += double(acc[l] * fs);
+        } else {
+            const double f = pow2(e);
+#pragma unroll
+            for (int l = 0; l < ND; ++l) x[(v * ND + l) * T + i] += double(acc[l]) * f;
+        }
+    } else {
+#pragma unroll
+        for (int l = 0; l < ND; ++l) x[(v * ND + l) * T + i] += double(acc[l]);
+    }
 }
 
 // Warm start of the next solve (cases not done) from the last solutions
@@ -1286,9 +1324,11 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
     auto restart_body = [&](cudaStream_t q) -> gks_status {
         int slot = prof_start(m, kProfCorr, q);
         k_backsolve<<<sblocks(ns), 128, 0, q>>>(mm, k.H, k.g, k.y, k.ctl, ns); note_launch();
-        k_scale_y<<<sblocks(ns), 128, 0, q>>>(mm, k.y, k.vn, k.ctl, ns, k.g, k.bnorm, rtol, sx); note_launch();
+        k_scale_y<<<sblocks(ns), 128, 0, q>>>(mm, k.y, k.vn, k.ctl, ns, k.g, k.bnorm, rtol, sx,
+                                               mixed ? k.y32 : nullptr);
+        note_launch();
         if (mixed)
-            k_combine_z<float><<<dim3(nb, NV), kBlock, 0, q>>>(d, k.Z32, k.y, mm, k.ctl, ns, k.x, sx);
+            k_combine_z<float><<<dim3(nb, NV), kBlock, 0, q>>>(d, k.Z32, k.y, mm, k.ctl, ns, k.x, sx, k.y32);
         else
             k_combine_z<double><<<dim3(nb, NV), kBlock, 0, q>>>(d, k.Z, k.y, mm, k.ctl, ns, k.x);
         note_launch();

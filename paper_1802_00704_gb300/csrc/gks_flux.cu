@@ -1,10 +1,7 @@
-// Face fluxes, conservative update, CFL time step and permutations.
-//
-// Flux (Eqs. (7), (11), (15)): one thread per face Gauss point; the two points
-// of a face sit in neighbouring lanes and are summed with one shuffle, so each
-// face flux is written once, without atomics.  The update (Eq. (6)) gathers
-// the (at most three) face fluxes of each cell: no atomics, a fixed summation
-// order, one write per cell.
+// Face fluxes (Eqs. (7), (11), (15)): reconstruction at the Gauss points,
+// ghost states, and the kinetic flux; one thread per face Gauss point, the two
+// points of a face in neighbouring lanes summed with one shuffle, so each face
+// flux is written once, without atomics.
 #include <cfloat>
 
 #include <type_traits>
@@ -274,90 +271,6 @@ __global__ void __launch_bounds__(kFluxBlock, MIXED ? 4 : 1) k_face_flux(DeviceM
         for (int q = 0; q < 4; ++q) flux[q * F + f] = out[q];
 }
 
-// w_i -= (1/|Omega_i|) sum_f sigma_if F_f; flags non-physical results.
-__global__ void k_update(DeviceMesh d, double *__restrict__ w, const double *__restrict__ flux, double gamma,
-                         int32_t *status)
-{
-    const int64_t T = d.T, F = d.F;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= T) return;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        const int cf = d.cf[s * T + i];
-        if (cf < 0) continue;
-        const int64_t f = cf >> 1;
-        const double sg = (cf & 1) ? 1.0 : -1.0;
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[v] += sg * flux[v * F + f];
-    }
-    const double ia = d.inv_area[i];
-    double wn[4];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        wn[v] = w[v * T + i] + acc[v] * ia;
-        w[v * T + i] = wn[v];
-    }
-    const double p = (gamma - 1.0) * (wn[3] - 0.5 * (wn[1] * wn[1] + wn[2] * wn[2]) / wn[0]);
-    if (!(wn[0] > 0.0) || !(p > 0.0)) atomicOr(&status[d.blk_case[blockIdx.x]], kStatusNonPhys);
-}
-
-// Per-cell CFL bound, block minimum.
-__global__ void k_cfl_partial(DeviceMesh d, const double *__restrict__ w, double gamma, double mu,
-                              double *__restrict__ part)
-{
-    __shared__ double sh[kBlock];
-    const int64_t T = d.T;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    double dti = DBL_MAX;
-    if (i < T) {
-        const double rho = w[i], u = w[T + i] / rho, v = w[2 * T + i] / rho;
-        const double p = (gamma - 1.0) * (w[3 * T + i] - 0.5 * rho * (u * u + v * v));
-        const double c = sqrt(gamma * p / rho);
-        const double r = d.inrad[i];
-        dti = r / (sqrt(u * u + v * v) + c + 2.0 * mu / (rho * r));
-        if (!(dti > 0.0)) dti = 0.0;          // non-physical cell: forces dt = 0
-    }
-    sh[threadIdx.x] = dti;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + o]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
-}
-
-// out[c] = scale * min of the block minima of case c (one block per case)
-__global__ void k_min_final(const double *__restrict__ part, const int32_t *__restrict__ case_blk, double scale,
-                            double *out)
-{
-    __shared__ double sh[kBlock];
-    const int c = blockIdx.x;
-    double m = DBL_MAX;
-    for (int b = case_blk[c] + threadIdx.x; b < case_blk[c + 1]; b += blockDim.x) m = fmin(m, part[b]);
-    sh[threadIdx.x] = m;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + o]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[c] = scale * sh[0];
-}
-
-// Per-case step control: dt = min(cfl step, t_final - t), 0 once done; t += dt.
-__global__ void k_clip_dt(double *dt, double *t, const double *__restrict__ tf, int32_t *done, int n)
-{
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
-    if (done[c] || (tf[c] > 0.0 && t[c] >= tf[c] * (1.0 - 1e-14))) {
-        done[c] = 1;
-        dt[c] = 0.0;
-        return;
-    }
-    if (tf[c] > 0.0) dt[c] = fmin(dt[c], tf[c] - t[c]);
-    t[c] += dt[c];
-}
-
 template <bool MIXED, bool HEAT, bool KIN>
 __global__ void __launch_bounds__(kFluxBlock) k_point_flux(int64_t n, const double *__restrict__ wl,
                                                            const double *__restrict__ wr, double dt, double gamma,
@@ -377,61 +290,6 @@ __global__ void __launch_bounds__(kFluxBlock) k_point_flux(int64_t n, const doub
     if (!ok && status) atomicOr(status, kStatusNonPhys);
 #pragma unroll
     for (int k = 0; k < 4; ++k) out[4 * q + k] = f[k];
-}
-
-// Internal rows [nvar][n] <-> caller rows [nvar][nc]; padding (perm < 0) untouched.
-__global__ void k_permute(const double *__restrict__ src, double *__restrict__ dst, const int32_t *__restrict__ perm,
-                          int64_t n, int64_t nc, int nvar, int gather)
-{
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t p = perm[i];
-    if (p < 0) return;
-    for (int v = 0; v < nvar; ++v) {
-        if (gather) dst[v * n + i] = src[v * nc + p];
-        else dst[v * nc + p] = src[v * n + i];
-    }
-}
-
-// partial sums over cells of area * (w - w_old)^2 per variable
-__global__ void k_steady_partial(DeviceMesh d, const double *__restrict__ w, const double *__restrict__ w_old,
-                                 double *__restrict__ part)
-{
-    __shared__ double sh[kBlock];
-    const int64_t T = d.T;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    for (int v = 0; v < 4; ++v) {
-        double s = 0.0;
-        if (i < T) {
-            const double dw = w[v * T + i] - w_old[v * T + i];
-            s = d.area[i] * dw * dw;
-        }
-        sh[threadIdx.x] = s;
-        __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) part[blockIdx.x * 4 + v] = sh[0];
-        __syncthreads();
-    }
-}
-
-__global__ void k_sum4_final(const double *__restrict__ part, int n, double *out)
-{
-    __shared__ double sh[kBlock];
-    for (int v = 0; v < 4; ++v) {
-        double s = 0.0;
-        for (int b = threadIdx.x; b < n; b += blockDim.x) s += part[b * 4 + v];
-        sh[threadIdx.x] = s;
-        __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) out[v] = sh[0];
-        __syncthreads();
-    }
 }
 
 inline unsigned blocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -481,26 +339,6 @@ gks_status launch_flux(gks_mesh *m, const double *w, const double *x, double dt_
     return GKS_OK;
 }
 
-gks_status launch_update(gks_mesh *m, double *w, const double *flux, cudaStream_t s)
-{
-    const int slot = prof_start(m, kProfUpdate, s);
-    k_update<<<blocks(m->d.T, kBlock), kBlock, 0, s>>>(m->d, w, flux, m->cfg.gamma, m->wk.status); note_launch();
-    prof_stop(m, slot, s);
-    GKS_CUDA(cudaGetLastError());
-    return GKS_OK;
-}
-
-gks_status launch_cfl_dt(gks_mesh *m, const double *w, double *dt_dev, cudaStream_t s)
-{
-    const unsigned nb = blocks(m->d.T, kBlock);
-    const int slot = prof_start(m, kProfCtl, s);
-    k_cfl_partial<<<nb, kBlock, 0, s>>>(m->d, w, m->cfg.gamma, m->cfg.mu, m->wk.dpart); note_launch();
-    k_min_final<<<m->d.ncase, kBlock, 0, s>>>(m->wk.dpart, m->d.case_blk, m->cfg.cfl, dt_dev); note_launch();
-    prof_stop(m, slot, s);
-    GKS_CUDA(cudaGetLastError());
-    return GKS_OK;
-}
-
 gks_status launch_point_flux(int64_t n, const double *wl, const double *wr, double dt, const gks_config &cfg,
                              double *out, int32_t *status, cudaStream_t s)
 {
@@ -512,32 +350,6 @@ gks_status launch_point_flux(int64_t n, const double *wl, const double *wr, doub
             n, wl, wr, dt, cfg.gamma, cfg.mu, cfg.tau2_exact, cfg.prandtl, out, status);
     });
     note_launch();
-    GKS_CUDA(cudaGetLastError());
-    return GKS_OK;
-}
-
-gks_status launch_permute(const double *src, double *dst, const int32_t *perm, int64_t n, int64_t ncaller, int nvar,
-                          bool gather, cudaStream_t s)
-{
-    k_permute<<<blocks(n, kBlock), kBlock, 0, s>>>(src, dst, perm, n, ncaller, nvar, gather ? 1 : 0); note_launch();
-    GKS_CUDA(cudaGetLastError());
-    return GKS_OK;
-}
-
-gks_status launch_clip_dt(gks_mesh *m, cudaStream_t s)
-{
-    const int n = m->d.ncase;
-    k_clip_dt<<<(n + 127) / 128, 128, 0, s>>>(m->wk.dt, m->wk.tcase, m->wk.tfinal, m->wk.done, n); note_launch();
-    GKS_CUDA(cudaGetLastError());
-    return GKS_OK;
-}
-
-// m->wk.scal[0..3] = sum over cells of area (w - w_old)^2 per variable
-gks_status launch_steady_partial(gks_mesh *m, cudaStream_t s)
-{
-    const unsigned nb = blocks(m->d.T, kBlock);
-    k_steady_partial<<<nb, kBlock, 0, s>>>(m->d, m->wk.w, m->wk.w_old, m->wk.dpart); note_launch();
-    k_sum4_final<<<1, kBlock, 0, s>>>(m->wk.dpart, (int)nb, m->wk.scal); note_launch();
     GKS_CUDA(cudaGetLastError());
     return GKS_OK;
 }

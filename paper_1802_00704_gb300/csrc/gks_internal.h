@@ -116,6 +116,7 @@ struct Work {
     double *cs = nullptr, *sn = nullptr;  // [ns][m]
     double *g = nullptr;             // [ns][m+1]
     double *y = nullptr;             // [ns][m]
+    float *y32 = nullptr;            // [ns][m] FP32 copy of y (mixed mode)
     double *hcol = nullptr;          // [ns][m+2] raw sums <V_k, u> of the current column, then |V_{j+1}|
     double *hco = nullptr;           // [ns][m+2] Gram-Schmidt coefficients <V_k, u> / vn_k^2
     double *vn = nullptr;            // [ns][m+1] norms vn_k of the stored basis vectors

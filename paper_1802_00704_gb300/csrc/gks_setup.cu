@@ -728,7 +728,10 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
         AL(xl, 20 * T); AL(lflag, T);
     }
     AL(x_prev, 20 * T); AL(x_prev2, 20 * T);   // extrapolated warm start (also for the autotuner)
-    if (cfg.precision == GKS_MIXED) AL(x32, 20 * T);
+    if (cfg.precision == GKS_MIXED) {
+        AL(x32, 20 * T);
+        AL(y32, ns * mm);
+    }
     AL(H, ns * (mm + 1) * mm); AL(cs, ns * mm); AL(sn, ns * mm); AL(g, ns * (mm + 1)); AL(y, ns * mm);
     AL(hcol, ns * (mm + 2)); AL(hco, ns * (mm + 2)); AL(vn, ns * (mm + 1)); AL(bnorm, ns); AL(beta, ns); AL(ctl, kCtlFields * ns); AL(flags, 4);
     AL(sexp, 2 * ns);
