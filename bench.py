@@ -214,7 +214,7 @@ def oracle_sample(steps: int, warmup: int = 0):
 
 
 def class_bytes(cls: str, prof: dict, T: int, F: int, steps: int, sweeps: int, exact: bool, mixed: bool,
-                basis32: bool) -> float:
+                basis32: bool, ilu16: bool = False) -> float:
     """Algorithmic DRAM bytes moved by one kernel class over the timed region,
     from the solver's work counters (Arnoldi iterations n, sum of j + 1 over
     them, preconditioner applications).  Per cell: operator = diagonal block 15
@@ -222,10 +222,12 @@ def class_bytes(cls: str, prof: dict, T: int, F: int, steps: int, sweeps: int, e
     inverse 25 values; a Krylov or work vector 20 values; a neighbour reads the
     first 2 of the 5 unknowns of each variable (8 values, counted once).  Sizes:
     sM operator/factor values, sZ preconditioner vectors (8 FP64 path, 4 mixed),
-    sB Krylov basis (8, or 4 with the FP32-stored basis)."""
+    sB Krylov basis (8, or 4 with the FP32-stored basis), sP the ILU factors (sM,
+    or 2 with FP16 copies)."""
     sM = 4 if mixed else 8
     sZ = 4 if mixed else 8
     sB = 4 if basis32 else 8
+    sP = 2 if ilu16 else sM
     n, jsum = prof["arnoldi"], prof["arnoldi_jsum"]
     op = sM * (15 + 9) + 12
     if cls == "orth":
@@ -238,12 +240,12 @@ def class_bytes(cls: str, prof: dict, T: int, F: int, steps: int, sweeps: int, e
     if cls == "ilu":
         pc = prof["precond"]
         if exact:
-            fwd = 20 * sB + 8 * sZ + sM * 25 + op - sM * 15 + 20 * sZ
-            bwd = 20 * sZ + 8 * sZ + sM * 25 + op - sM * 15 + 20 * sZ
+            fwd = 20 * sB + 8 * sZ + sP * (25 + 9) + 12 + 20 * sZ
+            bwd = 20 * sZ + 8 * sZ + sP * (25 + 9) + 12 + 20 * sZ
             return T * (fwd + bwd) * pc
-        first = 20 * sB + sM * 25 + 20 * sZ
-        fwd = 20 * sB + 8 * sZ + sM * (25 + 9) + 12 + 20 * sZ
-        bwd = 20 * sZ + 8 * sZ + sM * (25 + 9) + 12 + 20 * sZ
+        first = 20 * sB + sP * 25 + 20 * sZ
+        fwd = 20 * sB + 8 * sZ + sP * (25 + 9) + 12 + 20 * sZ
+        bwd = 20 * sZ + 8 * sZ + sP * (25 + 9) + 12 + 20 * sZ
         return T * (first + sweeps * (fwd + bwd)) * pc
     if cls == "update":                 # w in/out, 1/|Omega|, 3 face slots; each face flux once
         return (T * (8 * 8 + 8 + 12) + F * 4 * 8) * steps
@@ -264,7 +266,8 @@ def timed_leg(args, case, precision: str, world: int, dev, sample_clocks: bool):
     mixed = precision == "mixed"
     m = gks.GksMesh(case.mesh, precond=gks.PC_ILU_EXACT if exact else gks.PC_ILU_SWEEP, ilu_sweeps=args.sweeps,
                     precision=gks.MIXED if mixed else gks.FP64, basis_fp32=int(mixed and args.basis == "fp32"),
-                    limiter=int(args.limiter), warm_extrap=WARM[args.warm], no_graphs=GRAPHS[args.graphs])
+                    limiter=int(args.limiter), warm_extrap=WARM[args.warm], no_graphs=GRAPHS[args.graphs],
+                    ilu_fp16=int(mixed and args.ilu16 == "on"))
     w = torch.from_numpy(case.w0.copy()).to(dev)
     stream = torch.cuda.current_stream()
     tune = m.autotune(w, trial_steps=2) if args.tune else None
@@ -342,7 +345,8 @@ def run_gks(args, world, rank, local):
         ms_c = prof["ms"][q]
         ent = {"ms": round(ms_c, 3), "launch_groups": prof["n"][q]}
         if nm not in ("flux", "ctl") and ms_c > 0:
-            by = class_bytes(nm, prof, T, F, args.steps, main["knobs"]["ilu_sweeps"], exact, mixed, basis32)
+            by = class_bytes(nm, prof, T, F, args.steps, main["knobs"]["ilu_sweeps"], exact, mixed, basis32,
+                             mixed and args.ilu16 == "on")
             gbs = by / (ms_c / 1e3) / 1e9
             ent.update({"bytes": by, "gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 3)})
         classes[nm] = ent
@@ -376,7 +380,7 @@ def run_gks(args, world, rank, local):
                                f"{F} faces, GMRES(30) rtol 1e-12",
                    "n_tri": T, "n_face": F, "precision": args.precision,
                    "krylov_basis": "fp32" if basis32 else "fp64", "limiter": bool(args.limiter),
-                   "solve_graphs": args.graphs,
+                   "solve_graphs": args.graphs, "ilu_factors": "fp16" if mixed and args.ilu16 == "on" else None,
                    "warm_start": args.warm, "autotuned": bool(args.tune), "knobs": main["knobs"],
                    "precond": ("ilu0_rcm_exact" if exact else f"ilu0_rcm_sweep{main['knobs']['ilu_sweeps']}"),
                    "l2": f"inputs larger than L2: {st['device_bytes'] / 2**30:.1f} GiB resident per replica",
@@ -448,7 +452,8 @@ def run_batch(args, world, rank, local):
     def leg(prec_mixed: bool, clocks: bool):
         b = gks.GksMesh.batch([c.mesh for c in cases], precision=gks.MIXED if prec_mixed else gks.FP64,
                               limiter=2, gmres_m=12, warm_extrap=WARM[args.warm],
-                              basis_fp32=int(prec_mixed and args.basis == "fp32"), no_graphs=GRAPHS[args.graphs])
+                              basis_fp32=int(prec_mixed and args.basis == "fp32"), no_graphs=GRAPHS[args.graphs],
+                              ilu_fp16=int(prec_mixed and args.ilu16 == "on"))
         w = torch.from_numpy(w0.copy()).to(dev)
         tune = b.autotune(w, trial_steps=1) if args.tune else None
         r = b.batch_run(w, max_steps=args.warmup)
@@ -498,7 +503,7 @@ def run_batch(args, world, rank, local):
         ent = {"ms": round(prof["ms"][q], 3), "launch_groups": prof["n"][q]}
         if nm not in ("flux", "ctl") and prof["ms"][q] > 0:
             by = class_bytes(nm, prof, T, F, args.steps, knobs["ilu_sweeps"], False, mixed,
-                             mixed and args.basis == "fp32")
+                             mixed and args.basis == "fp32", mixed and args.ilu16 == "on")
             gbs = by / (prof["ms"][q] / 1e3) / 1e9
             ent.update({"bytes": by, "gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 3)})
         classes[nm] = ent
@@ -573,6 +578,8 @@ def main():
                     help="Krylov basis of the mixed path's inner cycles: FP32 (FP32 Gram-Schmidt arithmetic, "
                          "FP64 sums across threads) or FP64")
     ap.add_argument("--limiter", action="store_true", help="shock detector + DWBAP limiter on")
+    ap.add_argument("--ilu16", default="on", choices=["on", "off"],
+                    help="mixed path: FP16 copies of the ILU(0) factors for the FP32 preconditioner")
     ap.add_argument("--graphs", default="device", choices=sorted(GRAPHS),
                     help="CLS solve launch: device-controlled graph (default), per-part graphs, plain launches")
     ap.add_argument("--no-tune", dest="tune", action="store_false",

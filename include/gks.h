@@ -147,6 +147,11 @@ typedef struct gks_config {
                               half-space moments rho_l <psi g_l'/g_l>_{u>0} +
                               rho_r <psi g_r'/g_r>_{u<0} of the derivatives of the two
                               distributions                                            */
+    int32_t ilu_fp16;      /* 1 (GKS_MIXED only): the FP32 preconditioner reads its ILU(0)
+                              factors (block inverses, off-diagonal coefficients) from
+                              FP16 copies, FP32 arithmetic; a fixed preconditioner, so
+                              the solution meets the same tolerance; kept in FP32 when
+                              a factor is outside FP16's normal range                  */
 } gks_config;
 
 typedef struct gks_mesh gks_mesh;

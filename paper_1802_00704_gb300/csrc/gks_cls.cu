@@ -380,9 +380,11 @@ __global__ void __launch_bounds__(kBlock, 4) k_resid_df(DeviceMesh d, const floa
 // rcopy (may be NULL): also store TZ(r_i), so that later sweeps read r in the
 // working precision (same values as converting r again).  Own data (r, P) is
 // loaded before the neighbour gathers so that the two overlap.
-template <typename TR, typename TZ, typename TM>
-__global__ void k_ilu_fwd(DeviceMesh d, const TM *__restrict__ Pg, const TM *__restrict__ alg,
-                          const TM *__restrict__ exg, const TM *__restrict__ eyg, const int32_t *__restrict__ rows,
+// TP: storage type of the factors (TM, or FP16 for the mixed mode's FP32
+// preconditioner), widened to TM on load.
+template <typename TR, typename TZ, typename TM, typename TP = TM>
+__global__ void k_ilu_fwd(DeviceMesh d, const TP *__restrict__ Pg, const TP *__restrict__ alg,
+                          const TP *__restrict__ exg, const TP *__restrict__ eyg, const int32_t *__restrict__ rows,
                           int64_t nrows, const TR *r, const TZ *zin, TZ *zout, int use_nb, TZ *__restrict__ rcopy)
 {
     const int64_t T = d.T;
@@ -394,7 +396,7 @@ __global__ void k_ilu_fwd(DeviceMesh d, const TM *__restrict__ Pg, const TM *__r
     for (int k = 0; k < NX; ++k) y[k] = TM(r[k * T + i]);
     TM Pm[25];
 #pragma unroll
-    for (int k = 0; k < 25; ++k) Pm[k] = Pg[k * T + i];
+    for (int k = 0; k < 25; ++k) Pm[k] = TM(Pg[k * T + i]);
     if (rcopy)
 #pragma unroll
         for (int k = 0; k < NX; ++k) rcopy[k * T + i] = TZ(y[k]);
@@ -403,7 +405,7 @@ __global__ void k_ilu_fwd(DeviceMesh d, const TM *__restrict__ Pg, const TM *__r
         for (int s = 0; s < 3; ++s) {
             const int j = d.nb[s * T + i];
             if (j < 0 || j >= i) continue;
-            const TM sa = alg[s * T + i], sax = sa * exg[s * T + i], say = sa * eyg[s * T + i];
+            const TM sa = TM(alg[s * T + i]), sax = sa * TM(exg[s * T + i]), say = sa * TM(eyg[s * T + i]);
 #pragma unroll
             for (int v = 0; v < NV; ++v)
                 oacc(sa, sax, say, TM(zin[(v * ND + 0) * T + j]), TM(zin[(v * ND + 1) * T + j]), y + v * ND);
@@ -423,10 +425,10 @@ __global__ void k_ilu_fwd(DeviceMesh d, const TM *__restrict__ Pg, const TM *__r
 // Backward block-ILU relation: x_i = z_i + P_i sum_{j>i} O_ij xin_j (own data
 // loaded before the neighbour gathers; with no upper neighbour the sum is 0
 // and x_i = z_i exactly).
-template <typename TZ, typename TM>
+template <typename TZ, typename TM, typename TP = TM>
 __global__ void __launch_bounds__(kBlock, sizeof(TM) == 4 ? 3 : 1)
-    k_ilu_bwd(DeviceMesh d, const TM *__restrict__ Pg, const TM *__restrict__ alg, const TM *__restrict__ exg,
-              const TM *__restrict__ eyg, const int32_t *__restrict__ rows, int64_t nrows, const TZ *z, const TZ *xin,
+    k_ilu_bwd(DeviceMesh d, const TP *__restrict__ Pg, const TP *__restrict__ alg, const TP *__restrict__ exg,
+              const TP *__restrict__ eyg, const int32_t *__restrict__ rows, int64_t nrows, const TZ *z, const TZ *xin,
               TZ *xout)
 {
     const int64_t T = d.T;
@@ -441,12 +443,12 @@ __global__ void __launch_bounds__(kBlock, sizeof(TM) == 4 ? 3 : 1)
     }
     TM Pm[25];
 #pragma unroll
-    for (int k = 0; k < 25; ++k) Pm[k] = Pg[k * T + i];
+    for (int k = 0; k < 25; ++k) Pm[k] = TM(Pg[k * T + i]);
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
         const int j = d.nb[s * T + i];
         if (j <= i) continue;
-        const TM sa = alg[s * T + i], sax = sa * exg[s * T + i], say = sa * eyg[s * T + i];
+        const TM sa = TM(alg[s * T + i]), sax = sa * TM(exg[s * T + i]), say = sa * TM(eyg[s * T + i]);
 #pragma unroll
         for (int v = 0; v < NV; ++v)
             oacc(sa, sax, say, TM(xin[(v * ND + 0) * T + j]), TM(xin[(v * ND + 1) * T + j]), y + v * ND);
@@ -886,8 +888,8 @@ inline unsigned nblocks(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock
 
 // dst = M^{-1} src (block ILU(0) on the RCM order).  TZ, TM: storage and
 // arithmetic precision of the application; tA, tB: work buffers of type TZ.
-template <typename TR, typename TZ, typename TM>
-gks_status precond_t(gks_mesh *m, const TM *Pg, const TM *alg, const TM *exg, const TM *eyg, const TR *src,
+template <typename TR, typename TZ, typename TM, typename TP = TM>
+gks_status precond_t(gks_mesh *m, const TP *Pg, const TP *alg, const TP *exg, const TP *eyg, const TR *src,
                      TZ *dst, TZ *tA, TZ *tB, TZ *rz, cudaStream_t s)
 {
     DeviceMesh &d = m->d;
@@ -896,14 +898,14 @@ gks_status precond_t(gks_mesh *m, const TM *Pg, const TM *alg, const TM *exg, co
         const auto &lp = m->lvl_lo_ptr;
         for (size_t l = 0; l + 1 < lp.size(); ++l) {
             const int64_t n = lp[l + 1] - lp[l];
-            k_ilu_fwd<TR, TZ, TM><<<nblocks(n), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, d.lvl_lo + lp[l], n, src,
+            k_ilu_fwd<TR, TZ, TM, TP><<<nblocks(n), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, d.lvl_lo + lp[l], n, src,
                                                                  dst, dst, 1, nullptr);
             note_launch();
         }
         const auto &up = m->lvl_up_ptr;
         for (size_t l = 0; l + 1 < up.size(); ++l) {
             const int64_t n = up[l + 1] - up[l];
-            k_ilu_bwd<TZ, TM><<<nblocks(n), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, d.lvl_up + up[l], n, dst, dst, dst);
+            k_ilu_bwd<TZ, TM, TP><<<nblocks(n), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, d.lvl_up + up[l], n, dst, dst, dst);
             note_launch();
         }
     } else {
@@ -913,14 +915,14 @@ gks_status precond_t(gks_mesh *m, const TM *Pg, const TM *alg, const TM *exg, co
         TZ *zb = (ns % 2 == 0) ? dst : tA;
         // a wider source is rounded to TZ once, in the first pass, for the sweeps
         TZ *rc = (sizeof(TR) > sizeof(TZ) && ns > 0) ? rz : nullptr;
-        k_ilu_fwd<TR, TZ, TM><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, src, nullptr, za, 0, rc);
+        k_ilu_fwd<TR, TZ, TM, TP><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, src, nullptr, za, 0, rc);
         note_launch();
         for (int q = 0; q < ns; ++q) {
             if (rc)
-                k_ilu_fwd<TZ, TZ, TM><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, rc, za, zb, 1,
+                k_ilu_fwd<TZ, TZ, TM, TP><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, rc, za, zb, 1,
                                                                      nullptr);
             else
-                k_ilu_fwd<TR, TZ, TM><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, src, za, zb, 1,
+                k_ilu_fwd<TR, TZ, TM, TP><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, src, za, zb, 1,
                                                                      nullptr);
             note_launch();
             std::swap(za, zb);
@@ -931,7 +933,7 @@ gks_status precond_t(gks_mesh *m, const TM *Pg, const TM *alg, const TM *exg, co
             TZ *xa = za;                                    // x^0 = z (in tA)
             TZ *xb = (ns % 2 == 1) ? dst : tB;
             for (int q = 0; q < ns; ++q) {
-                k_ilu_bwd<TZ, TM><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, za, xa, xb);
+                k_ilu_bwd<TZ, TM, TP><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, za, xa, xb);
                 note_launch();
                 xa = xb;
                 xb = (xb == dst) ? tB : dst;
@@ -953,6 +955,9 @@ template <typename TR>
 gks_status precond32(gks_mesh *m, const TR *src, float *dst, cudaStream_t s)
 {
     DeviceMesh &d = m->d;
+    if (d.P16)   // FP16 factors (ilu_fp16), FP32 arithmetic
+        return precond_t<TR, float, float, __half>(m, d.P16, d.alpha16, d.ex16, d.ey16, src, dst, m->wk.t2_32,
+                                                   m->wk.t3_32, m->wk.r32, s);
     return precond_t<TR, float, float>(m, d.P32, d.alpha32, d.ex32, d.ey32, src, dst, m->wk.t2_32, m->wk.t3_32,
                                        m->wk.r32, s);
 }

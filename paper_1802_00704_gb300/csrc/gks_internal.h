@@ -7,6 +7,7 @@
 // single mesh is the one-case instance (no padding).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -67,6 +68,9 @@ struct DeviceMesh {
     double *P = nullptr;             // [25][T] inverse of the ILU(0) diagonal block, row-major
     // FP32 copies of the operator and factors (mixed precision)
     float *D32 = nullptr, *P32 = nullptr, *alpha32 = nullptr, *ex32 = nullptr, *ey32 = nullptr;
+    // FP16 copies of the ILU(0) factors for the FP32 preconditioner (ilu_fp16;
+    // NULL when not asked for or a value is outside FP16's range)
+    __half *P16 = nullptr, *alpha16 = nullptr, *ex16 = nullptr, *ey16 = nullptr;
     float *ih32 = nullptr;           // [T] 1 / h_i (mixed flux)
     // the operator as FP32 pairs hi + lo for the double-FP32 refinement residual
     // (mixed mode with an FP32 basis; NULL when a value is outside the pair range)

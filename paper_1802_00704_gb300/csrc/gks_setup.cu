@@ -672,6 +672,23 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
     if (cfg.precision == GKS_MIXED) {
         auto f32 = [](const std::vector<double> &v) { return std::vector<float>(v.begin(), v.end()); };
         UP(D32, f32(h_D)); UP(P32, f32(h_P)); UP(alpha32, f32(h_alpha)); UP(ex32, f32(h_ex)); UP(ey32, f32(h_ey));
+        if (cfg.ilu_fp16) {
+            // FP16 copies of the ILU(0) factors if every value fits FP16's normal range
+            // (smaller ones round to FP16's subnormals, far below the block's scale)
+            bool fits = true;
+            auto f16 = [&](const std::vector<double> &v) {
+                std::vector<__half> o(v.size());
+                for (size_t q = 0; q < v.size(); ++q) {
+                    if (!(std::fabs(v[q]) <= 6.0e4)) fits = false;
+                    o[q] = __double2half(v[q]);
+                }
+                return o;
+            };
+            std::vector<__half> p16 = f16(h_P), a16 = f16(h_alpha), x16 = f16(h_ex), y16 = f16(h_ey);
+            if (fits) {
+                UP(P16, p16); UP(alpha16, a16); UP(ex16, x16); UP(ey16, y16);
+            }
+        }
         std::vector<float> h_ih32(T);
         for (int64_t i = 0; i < T; ++i) h_ih32[i] = float(1.0 / h_h[i]);
         UP(ih32, h_ih32);

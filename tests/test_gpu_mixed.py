@@ -202,3 +202,42 @@ def test_warm_start_far_from_new_system(O, G):
     got = host(coef)
     for v in range(4):
         assert rel_max(got[v], ref[v]) <= 1e-9, (v, rel_max(got[v], ref[v]))
+
+
+@pytest.mark.parametrize("name", ["advection20", "shock_vortex40x20", "walled13x9"])
+def test_fp16_ilu_factors_reach_fp64_tolerance(O, G, name):
+    """ilu_fp16: the FP32 preconditioner reads FP16 copies of the ILU(0) factors.
+    A fixed preconditioner: the solve still meets the FP64 tolerance, matches the
+    oracle's coefficients to 1e-9, and needs at most one more Arnoldi iteration
+    per variable than with FP32 factors; with FP16 asked for in FP64 mode the
+    configuration is refused."""
+    from tests.test_gpu_parity import CASES
+    c = CASES[name]()
+    om = O.OracleMesh(c.mesh)
+    ref, _, _, _ = om.cls_solve(c.w0)
+    its = []
+    for f16 in (0, 1):
+        m = G.GksMesh(c.mesh, precision=G.MIXED, basis_fp32=1, ilu_fp16=f16)
+        coef, info = m.cls_reconstruct(dev(c.w0))
+        assert info["converged"] == 1 and max(info["relres"]) <= 1e-12
+        got = host(coef)
+        for v in range(4):
+            if np.max(np.abs(ref[v])) > 0:
+                assert rel_max(got[v], ref[v]) <= 1e-9
+        its.append(info["iters"])
+    assert all(b <= a + 1 for a, b in zip(*its)), its
+    with pytest.raises(G.GksError):
+        G.GksMesh(c.mesh, precision=G.FP64, ilu_fp16=1)
+
+
+def test_fp16_ilu_factors_steps_within_1e8_l1(O, G):
+    c = I.shock_vortex_case(40, 20)
+    area = O.OracleMesh(c.mesh).cell_geometry()["area"]
+    om = O.OracleMesh(c.mesh)
+    m = G.GksMesh(c.mesh, precision=G.MIXED, basis_fp32=1, ilu_fp16=1, warm_extrap=2)
+    wo, w = c.w0.copy(), dev(c.w0)
+    for _ in range(20):
+        dt = om.cfl_dt(wo)
+        assert om.step(wo, dt).status == 0
+        assert m.step(w, dt)["status"] == 0
+    assert np.all(rel_l1(host(w), wo, area) <= 1e-8), rel_l1(host(w), wo, area)
