@@ -160,7 +160,13 @@ int or_build_cls(or_mesh *m)
         }
     }
 
-    /* assemble D_i = sum_j A^T A, O_ij = A^T B, per-cell least squares */
+    /* Blocks of the normal equations.  Cell i's equations about its neighbour j
+     * are A_ij u_i - B_ij u_j = b_ij (rows p = 0, 1, 2 of Eq. (29)).
+     * Per-cell least squares (default): each cell minimises its own equations,
+     *   D_i = sum_j A_ij^T A_ij,  K_ij = -A_ij^T B_ij.
+     * Global (cls_global, Eq. (33)): the sum of all cells' equations is
+     * minimised, so u_i also enters its neighbours' equations through B_ji:
+     *   D_i += sum_j B_ji^T B_ji,  K_ij -= B_ji^T A_ji  (symmetric). */
     int cap = 0;
     for (int i = 0; i < T; ++i) {
         int ni = ndof_of(m->korder[i]);
@@ -171,13 +177,14 @@ int or_build_cls(or_mesh *m)
     int *rowptr = calloc((size_t)m->ndof + 1, sizeof(int));
     int *col = malloc(sizeof(int) * (size_t)(cap > 0 ? cap : 1));
     double *val = malloc(sizeof(double) * (size_t)(cap > 0 ? cap : 1));
-    if (!ent || !rowptr || !col || !val) { free(ent); free(rowptr); free(col); free(val); return -1; }
-    int nnz = 0;
+    double *Dall = calloc((size_t)T * 25, sizeof(double));
+    double *Oall = calloc((size_t)T * 75, sizeof(double));   /* [i][slot][5][5], A^T B parts */
+    if (!ent || !rowptr || !col || !val || !Dall || !Oall) {
+        free(ent); free(rowptr); free(col); free(val); free(Dall); free(Oall);
+        return -1;
+    }
     for (int i = 0; i < T; ++i) {
         int ni = ndof_of(m->korder[i]);
-        double D[5][5] = {{0}};
-        double O[3][5][5];
-        memset(O, 0, sizeof(O));
         for (int k = 0; k < 15; ++k) m->a0[15 * i + k] = 0.0;
         for (int k = 0; k < m->nb_cnt[i]; ++k) {
             int j = m->nb_cell[3 * i + k];
@@ -194,21 +201,48 @@ int or_build_cls(or_mesh *m)
                 B[0][l] = vb[l];  B[1][l] = wp1 * gxb[l]; B[2][l] = wp1 * gyb[l];
             }
             for (int l = 0; l < 5; ++l) m->a0[15 * i + 5 * k + l] = (l < ni) ? A[0][l] : 0.0;
+            double *Di = &Dall[25 * i], *Oik = &Oall[75 * i + 25 * k];
             for (int r = 0; r < ni; ++r) {
                 for (int c = 0; c < ni; ++c)
-                    for (int p = 0; p < 3; ++p) D[r][c] += A[p][r] * A[p][c];
+                    for (int p = 0; p < 3; ++p) Di[5 * r + c] += A[p][r] * A[p][c];
                 for (int c = 0; c < nj; ++c)
-                    for (int p = 0; p < 3; ++p) O[k][r][c] += A[p][r] * B[p][c];
+                    for (int p = 0; p < 3; ++p) Oik[5 * r + c] += A[p][r] * B[p][c];
+            }
+            if (m->prm.cls_global) {
+                /* the same equations seen from j: B^T B on D_j, B^T A on the block
+                 * (j, i) of the slot of j that points back to i through this face */
+                int kb = -1;
+                for (int q = 0; q < m->nb_cnt[j]; ++q)
+                    if (m->nb_cell[3 * j + q] == i && m->nb_dx[3 * j + q] == -ox && m->nb_dy[3 * j + q] == -oy) kb = q;
+                if (kb < 0) {
+                    free(ent); free(rowptr); free(col); free(val); free(Dall); free(Oall);
+                    return -2;
+                }
+                double *Dj = &Dall[25 * j], *Oji = &Oall[75 * j + 25 * kb];
+                for (int r = 0; r < nj; ++r) {
+                    for (int c = 0; c < nj; ++c)
+                        for (int p = 0; p < 3; ++p) Dj[5 * r + c] += B[p][r] * B[p][c];
+                    for (int c = 0; c < ni; ++c)
+                        for (int p = 0; p < 3; ++p) Oji[5 * r + c] += B[p][r] * A[p][c];
+                }
             }
         }
+    }
+    int nnz = 0;
+    for (int i = 0; i < T; ++i) {
+        int ni = ndof_of(m->korder[i]);
         for (int r = 0; r < ni; ++r) {
             int row = m->dof_off[i] + r;
             int ne = 0;
-            for (int c = 0; c < ni; ++c) { ent[ne].col = m->dof_off[i] + c; ent[ne].v = D[r][c]; ++ne; }
+            for (int c = 0; c < ni; ++c) { ent[ne].col = m->dof_off[i] + c; ent[ne].v = Dall[25 * i + 5 * r + c]; ++ne; }
             for (int k = 0; k < m->nb_cnt[i]; ++k) {
                 int j = m->nb_cell[3 * i + k];
                 int nj = ndof_of(m->korder[j]);
-                for (int c = 0; c < nj; ++c) { ent[ne].col = m->dof_off[j] + c; ent[ne].v = -O[k][r][c]; ++ne; }
+                for (int c = 0; c < nj; ++c) {
+                    ent[ne].col = m->dof_off[j] + c;
+                    ent[ne].v = -Oall[75 * i + 25 * k + 5 * r + c];
+                    ++ne;
+                }
             }
             qsort(ent, (size_t)ne, sizeof(or_ent), cmp_ent);
             rowptr[row] = nnz;
@@ -218,6 +252,8 @@ int or_build_cls(or_mesh *m)
             }
         }
     }
+    free(Dall);
+    free(Oall);
     rowptr[m->ndof] = nnz;
     free(ent);
     m->K.n = m->ndof; m->K.nnz = nnz; m->K.rowptr = rowptr; m->K.col = col; m->K.val = val;

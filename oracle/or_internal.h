@@ -31,6 +31,9 @@ typedef struct or_params {
     int    second_order; /* 1: k_i = 1 for every cell (linear CLS reconstruction) */
     double prandtl;     /* Prandtl number of the heat-flux correction (1: none)  */
     int    limit_char;  /* 1: DWBAP in characteristic variables (Sec. IV.B)       */
+    int    cls_global;  /* 1: the global normal equations C^T C u = C^T b of the
+                           whole mesh (Eq. (33), symmetric positive definite)
+                           instead of each cell's own least-squares equations    */
 } or_params;
 
 /* Boundary tags (same numbering as the input generator). */

@@ -28,6 +28,7 @@ void or_params_default(or_params *p)
     p->gmres_m = 30; p->gmres_maxit = 5000; p->gmres_rtol = 1e-14;
     p->tau2_exact = 0; p->slope0_mode = 0; p->limiter = 0; p->second_order = 0; p->prandtl = 1.0;
     p->limit_char = 0;
+    p->cls_global = 0;
 }
 
 void or_mesh_free(or_mesh *m)

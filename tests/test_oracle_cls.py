@@ -54,9 +54,14 @@ def _exact_coef(cg, T):
     return coef
 
 
-def test_cls_operator_exact_for_quadratics(oracle_mod):
+@pytest.mark.parametrize("glob", [0, 1])
+def test_cls_operator_exact_for_quadratics(oracle_mod, glob):
+    """The exact coefficients of a global quadratic satisfy every equation of a
+    cell that can hold it (k = 2); per cell that zeroes the rows of k = 2 cells,
+    in the global system (cls_global, Eq. (33)) the rows of k = 2 cells whose
+    neighbours are k = 2 too (their equations enter through B_ji)."""
     m = _walled(8)
-    om = oracle_mod.OracleMesh(m)
+    om = oracle_mod.OracleMesh(m, cls_global=glob)
     cg = om.cell_geometry()
     qbar = I.cell_average(m, lambda x, y: _quad(x, y)[None])[0]
     w = np.stack([qbar, qbar, qbar, qbar + 3.0])
@@ -70,23 +75,31 @@ def test_cls_operator_exact_for_quadratics(oracle_mod):
         x[off[i]:off[i] + n] = ex[:n, i]
     Kx = np.array([val[rp[r]:rp[r + 1]] @ x[col[rp[r]:rp[r + 1]]] for r in range(om.ndof)])
     res = Kx - rhs
-    interior_rows = np.concatenate([np.arange(off[i], off[i] + 5) for i in range(om.T) if k[i] == 2])
+    nbrs = [set() for _ in range(om.T)]
+    for (_, _, l, r, _) in m.faces:
+        if r >= 0:
+            nbrs[l].add(r)
+            nbrs[r].add(l)
+    keep = [i for i in range(om.T) if k[i] == 2 and (not glob or all(k[j] == 2 for j in nbrs[i]))]
+    interior_rows = np.concatenate([np.arange(off[i], off[i] + 5) for i in keep])
     assert len(interior_rows) > 0
     assert np.abs(res[interior_rows]).max() < 1e-13
     boundary_rows = np.setdiff1d(np.arange(om.ndof), interior_rows)
     assert np.abs(res[boundary_rows]).max() > 1e-6        # k = 1 cells cannot hold a quadratic
 
 
-def test_constant_data_gives_zero_coefficients(oracle_mod):
+@pytest.mark.parametrize("glob", [0, 1])
+def test_constant_data_gives_zero_coefficients(oracle_mod, glob):
     c = I.advection_case(6)
-    om = oracle_mod.OracleMesh(c.mesh)
+    om = oracle_mod.OracleMesh(c.mesh, cls_global=glob)
     w = np.ones((4, om.T)) * np.array([[1.2], [0.3], [-0.1], [3.0]])
     coef, it, rr, bad = om.cls_solve(w)
     assert bad == 0 and np.all(coef == 0.0)
 
 
+@pytest.mark.parametrize("glob", [0, 1])
 @pytest.mark.parametrize("kind", ["periodic4", "periodic8", "walled6"])
-def test_gmres_matches_dense_lu(oracle_mod, kind):
+def test_gmres_matches_dense_lu(oracle_mod, kind, glob):
     if kind.startswith("periodic"):
         c = I.advection_case(int(kind[-1]), k=1, amp=0.3)
         m, w = c.mesh, c.w0
@@ -94,7 +107,7 @@ def test_gmres_matches_dense_lu(oracle_mod, kind):
         m = _walled(6)
         w = I.cell_average(m, lambda x, y: np.stack([1 + 0.2 * np.sin(3 * x + y), np.cos(x - 2 * y),
                                                      0.1 * x * y, 2.5 + np.exp(0.3 * x)]))
-    om = oracle_mod.OracleMesh(m)
+    om = oracle_mod.OracleMesh(m, cls_global=glob)
     coef, it, rr, bad = om.cls_solve(w)
     ref = om.cls_dense(w)
     assert bad == 0 and np.all(rr < 1e-13)
@@ -132,3 +145,26 @@ def test_reconstruction_error_is_third_order(oracle_mod):
                 e = max(e, abs(val - (1 + 0.2 * math.sin(math.pi * (x + y)))))
         errs.append(e)
     assert errs[0] / errs[1] > 6 and errs[1] / errs[2] > 6, errs
+
+
+def _dense(om):
+    rp, col, val, off = om.cls_matrix()
+    K = np.zeros((om.ndof, om.ndof))
+    for r in range(om.ndof):
+        K[r, col[rp[r]:rp[r + 1]]] = val[rp[r]:rp[r + 1]]
+    return K
+
+
+@pytest.mark.parametrize("kind", ["walled6", "periodic5"])
+def test_global_cls_is_symmetric_positive_definite(oracle_mod, kind):
+    """cls_global: the normal equations of all equations together are C^T C,
+    symmetric and positive definite (Eq. (33)); the default per-cell equations
+    are not symmetric.  Both have the same sparsity (face neighbours)."""
+    m = _walled(6) if kind == "walled6" else I.advection_case(5, seed=4).mesh
+    Kg = _dense(oracle_mod.OracleMesh(m, cls_global=1))
+    Kp = _dense(oracle_mod.OracleMesh(m))
+    scale = np.abs(Kg).max()
+    assert np.abs(Kg - Kg.T).max() <= 1e-14 * scale
+    assert np.linalg.eigvalsh(0.5 * (Kg + Kg.T)).min() > 1e-10 * scale
+    assert np.abs(Kp - Kp.T).max() > 1e-3 * np.abs(Kp).max()
+    assert np.array_equal(Kg != 0, (Kg != 0) | (Kp != 0)) or np.array_equal(Kg != 0, Kp != 0)
