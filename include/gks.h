@@ -152,6 +152,11 @@ typedef struct gks_config {
                               FP16 copies, FP32 arithmetic; a fixed preconditioner, so
                               the solution meets the same tolerance; kept in FP32 when
                               a factor is outside FP16's normal range                  */
+    int32_t cls_global;    /* 1: the CLS system is the global normal equations of all
+                              cells' equations together, C^T C u = C^T b (Eq. (33),
+                              symmetric positive definite); 0 (default): each cell's
+                              own least-squares equations (non-symmetric), the reading
+                              that suits GMRES with ILU(0) (Sec. III.B)                */
 } gks_config;
 
 typedef struct gks_mesh gks_mesh;

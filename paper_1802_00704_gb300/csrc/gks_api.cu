@@ -64,6 +64,7 @@ gks_status check_config(const gks_config &c)
     ok = ok && (c.limit_char == 0 || c.limit_char == 1);
     ok = ok && (c.slope0_mode == 0 || c.slope0_mode == 1);
     ok = ok && (c.ilu_fp16 == 0 || (c.ilu_fp16 == 1 && c.precision == GKS_MIXED));
+    ok = ok && (c.cls_global == 0 || c.cls_global == 1);
     if (!ok) {
         set_error("invalid gks_config");
         return GKS_EINVAL;
@@ -186,6 +187,7 @@ void gks_config_default(gks_config *c)
     c->prandtl = 1.0;
     c->slope0_mode = 0;
     c->ilu_fp16 = 0;
+    c->cls_global = 0;
 }
 
 const char *gks_last_error(void) { return gks::last_error(); }

@@ -42,6 +42,17 @@ __device__ __forceinline__ void oacc(R sa, R sax, R say, R g1, R g2, R *acc)
     acc[4] = fma(say, g2, acc[4]);
 }
 
+// acc[0..1] += sr [x0 + dx x2 + dy x3 | x1 + dx x3 + dy x4] (srx = sr dx, sry =
+// sr dy): the transpose form that the global normal equations (Eq. (33)) add
+// to an off-diagonal block from the neighbour's own equations, applied to all
+// five unknowns x of the neighbour
+template <typename R>
+__device__ __forceinline__ void racc(R sr, R srx, R sry, const R *x, R *acc)
+{
+    acc[0] = fma(sr, x[0], fma(srx, x[2], fma(sry, x[3], acc[0])));
+    acc[1] = fma(sr, x[1], fma(srx, x[3], fma(sry, x[4], acc[1])));
+}
+
 // 2^e exactly (|e| <= 1022)
 __device__ __forceinline__ double pow2(int e)
 {
@@ -119,10 +130,14 @@ __global__ void k_rhs(DeviceMesh d, const double *__restrict__ w, double *__rest
 // Every load (neighbour indices, blocks, the neighbours' gradient entries, own
 // data) is issued before the arithmetic; a missing neighbour reads the cell's
 // own entries with a zero block.
-template <typename TX, typename TM>
+// G: global normal equations, with the reverse-slot coefficients arg, exrg,
+// eyrg (the transpose form, racc); unused otherwise.
+template <typename TX, typename TM, bool G = false>
 __device__ __forceinline__ void cell_apply(const DeviceMesh &d, const TM *__restrict__ Dg, const TM *__restrict__ alg,
                                            const TM *__restrict__ exg, const TM *__restrict__ eyg,
-                                           const TX *__restrict__ x, int64_t i, TM *acc)
+                                           const TX *__restrict__ x, int64_t i, TM *acc,
+                                           const TM *__restrict__ arg = nullptr, const TM *__restrict__ exrg = nullptr,
+                                           const TM *__restrict__ eyrg = nullptr)
 {
     const int64_t T = d.T;
     int64_t jn[3];
@@ -162,6 +177,20 @@ __device__ __forceinline__ void cell_apply(const DeviceMesh &d, const TM *__rest
     for (int s = 0; s < 3; ++s)
 #pragma unroll
         for (int v = 0; v < NV; ++v) oacc(sa[s], sax[s], say[s], g[s][2 * v], g[s][2 * v + 1], acc + v * ND);
+    if (G) {
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            const TM sr = sa[s] != TM(0) ? -arg[s * T + i] : TM(0);
+            const TM srx = sr * exrg[s * T + i], sry = sr * eyrg[s * T + i];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                TM xj[ND];
+#pragma unroll
+                for (int l = 0; l < ND; ++l) xj[l] = TM(x[(v * ND + l) * T + jn[s]]);
+                racc(sr, srx, sry, xj, acc + v * ND);
+            }
+        }
+    }
 }
 
 // y = K x (mode 0), or y = 2^-e (b - K x) with partial sums of |y|^2 of the
@@ -170,11 +199,12 @@ __device__ __forceinline__ void cell_apply(const DeviceMesh &d, const TM *__rest
 // K_ii = D_i (symmetric, 15 stored values), K_ij = -O_ij.  TX: type of x, TM:
 // type of the operator data and of the arithmetic (mode 1 is FP64 only), TY:
 // type of y.
-template <typename TX, typename TM, typename TY>
+template <typename TX, typename TM, typename TY, bool G = false>
 __global__ void k_spmv(DeviceMesh d, const TM *__restrict__ Dg, const TM *__restrict__ alg,
                        const TM *__restrict__ exg, const TM *__restrict__ eyg, const TX *__restrict__ x,
                        TY *__restrict__ y, int mode, const double *__restrict__ b, double *__restrict__ part,
-                       int pstride, const int32_t *__restrict__ sexp = nullptr)
+                       int pstride, const int32_t *__restrict__ sexp = nullptr, const TM *__restrict__ arg = nullptr,
+                       const TM *__restrict__ exrg = nullptr, const TM *__restrict__ eyrg = nullptr)
 {
     __shared__ double sh[32 * NV];
     const int64_t T = d.T;
@@ -182,7 +212,7 @@ __global__ void k_spmv(DeviceMesh d, const TM *__restrict__ Dg, const TM *__rest
     double nr[NV] = {0, 0, 0, 0};
     if (i < T) {
         TM acc[NX];
-        cell_apply<TX, TM>(d, Dg, alg, exg, eyg, x, i, acc);
+        cell_apply<TX, TM, G>(d, Dg, alg, exg, eyg, x, i, acc, arg, exrg, eyrg);
         if (mode == 0) {
 #pragma unroll
             for (int q = 0; q < NX; ++q) y[q * T + i] = TY(acc[q]);
@@ -266,11 +296,12 @@ __device__ __forceinline__ float df_sub_round(float bh, float bl, float sh, floa
 }
 
 // FP64 fallback of k_resid_df for variable v of cell i: out = 2^-e (b - K x)
+template <bool G>
 __device__ __noinline__ void resid64_cell(const DeviceMesh &d, const double *__restrict__ x,
                                           const double *__restrict__ b, int64_t i, int v, int e, float *out)
 {
     double acc[NX];
-    cell_apply<double, double>(d, d.D, d.alpha, d.ex, d.ey, x, i, acc);
+    cell_apply<double, double, G>(d, d.D, d.alpha, d.ex, d.ey, x, i, acc, d.alr, d.exr, d.eyr);
     for (int l = 0; l < ND; ++l) out[l] = float((b[(v * ND + l) * d.T + i] - acc[v * ND + l]) * pow2(-e));
 }
 
@@ -284,12 +315,16 @@ __device__ __noinline__ void resid64_cell(const DeviceMesh &d, const double *__r
 // q % 4 of cell block q / 4, so the four blocks of a cell block run together
 // and share the operator through L2.  A value outside the split range sends
 // the thread to the FP64 operator.  Each thread's five squares are summed in
-// FP32 (the scaled vector is near unit size).
+// FP32 (the scaled vector is near unit size).  G: global normal equations, the
+// transpose form from the reverse-slot pairs SR2 ([18][T], as S2) on all five
+// unknowns of each neighbour.
+template <bool G>
 __global__ void __launch_bounds__(kBlock, 4) k_resid_df(DeviceMesh d, const float *__restrict__ D2,
                                                        const float *__restrict__ S2, const double *__restrict__ x,
                                                        float *__restrict__ y, const double *__restrict__ b,
                                                        double *__restrict__ part, int pstride,
-                                                       const int32_t *__restrict__ sexp)
+                                                       const int32_t *__restrict__ sexp,
+                                                       const float *__restrict__ SR2 = nullptr)
 {
     __shared__ double sh[kBlock / 32];
     const int64_t T = d.T;
@@ -306,22 +341,26 @@ __global__ void __launch_bounds__(kBlock, 4) k_resid_df(DeviceMesh d, const floa
             jn[s] = j >= 0 ? j : i;
         }
         // every load first (the arithmetic below is a long dependent chain)
-        double xv[ND], gv[3][2], bv[ND];
-        float dp[30], op[18];
+        constexpr int NG = G ? ND : 2;                    // neighbour unknowns used
+        double xv[ND], gv[3][NG], bv[ND];
+        float dp[30], op[18], rp[G ? 18 : 1];
 #pragma unroll
         for (int l = 0; l < ND; ++l) xv[l] = x[(v * ND + l) * T + i];
 #pragma unroll
         for (int s = 0; s < 3; ++s)
 #pragma unroll
-            for (int l = 0; l < 2; ++l) gv[s][l] = x[(v * ND + l) * T + jn[s]];
+            for (int l = 0; l < NG; ++l) gv[s][l] = x[(v * ND + l) * T + jn[s]];
 #pragma unroll
         for (int q = 0; q < 30; ++q) dp[q] = D2[q * T + i];
 #pragma unroll
         for (int q = 0; q < 18; ++q) op[q] = S2[q * T + i];
+        if (G)
+#pragma unroll
+            for (int q = 0; q < 18; ++q) rp[q] = SR2[q * T + i];
 #pragma unroll
         for (int l = 0; l < ND; ++l) bv[l] = b[(v * ND + l) * T + i];
         bool ok = true;
-        float xh[ND], xl[ND], gh[3][2], gl[3][2], ah[ND], al[ND], out[ND];
+        float xh[ND], xl[ND], gh[3][NG], gl[3][NG], ah[ND], al[ND], out[ND];
 #pragma unroll
         for (int l = 0; l < ND; ++l) {
             ok &= df_split(xv[l], e, xh[l], xl[l]);
@@ -330,7 +369,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_resid_df(DeviceMesh d, const floa
 #pragma unroll
         for (int s = 0; s < 3; ++s)
 #pragma unroll
-            for (int l = 0; l < 2; ++l) ok &= df_split(gv[s][l], e, gh[s][l], gl[s][l]);
+            for (int l = 0; l < NG; ++l) ok &= df_split(gv[s][l], e, gh[s][l], gl[s][l]);
         // symmetric 5x5 block: entry (a, k) in the upper-triangle order
         constexpr int kIdx[5][5] = {{0, 1, 2, 3, 4}, {1, 5, 6, 7, 8}, {2, 6, 9, 10, 11}, {3, 7, 10, 12, 13},
                                     {4, 8, 11, 13, 14}};
@@ -348,6 +387,15 @@ __global__ void __launch_bounds__(kBlock, 4) k_resid_df(DeviceMesh d, const floa
             df_mac(op[q + 1], op[10 + q], gh[s][1], gl[s][1], ah[3], al[3]);
             df_mac(op[q + 2], op[11 + q], gh[s][0], gl[s][0], ah[3], al[3]);
             df_mac(op[q + 2], op[11 + q], gh[s][1], gl[s][1], ah[4], al[4]);
+            if (G) {
+                // transpose form (see racc): rows 0 and 1 from all five unknowns
+                df_mac(rp[q], rp[9 + q], gh[s][0], gl[s][0], ah[0], al[0]);
+                df_mac(rp[q + 1], rp[10 + q], gh[s][NG > 2 ? 2 : 0], gl[s][NG > 2 ? 2 : 0], ah[0], al[0]);
+                df_mac(rp[q + 2], rp[11 + q], gh[s][NG > 3 ? 3 : 0], gl[s][NG > 3 ? 3 : 0], ah[0], al[0]);
+                df_mac(rp[q], rp[9 + q], gh[s][1], gl[s][1], ah[1], al[1]);
+                df_mac(rp[q + 1], rp[10 + q], gh[s][NG > 3 ? 3 : 0], gl[s][NG > 3 ? 3 : 0], ah[1], al[1]);
+                df_mac(rp[q + 2], rp[11 + q], gh[s][NG > 4 ? 4 : 0], gl[s][NG > 4 ? 4 : 0], ah[1], al[1]);
+            }
         }
 #pragma unroll
         for (int l = 0; l < ND; ++l) {
@@ -355,7 +403,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_resid_df(DeviceMesh d, const floa
             ok &= df_split(bv[l], e, bh, bl);
             out[l] = df_sub_round(bh, bl, ah[l], al[l]);
         }
-        if (!ok) resid64_cell(d, x, b, i, v, e, out);   // a value outside the split range
+        if (!ok) resid64_cell<G>(d, x, b, i, v, e, out);   // a value outside the split range
         float sq = 0.0f;
 #pragma unroll
         for (int l = 0; l < ND; ++l) {
@@ -382,10 +430,14 @@ __global__ void __launch_bounds__(kBlock, 4) k_resid_df(DeviceMesh d, const floa
 // loaded before the neighbour gathers so that the two overlap.
 // TP: storage type of the factors (TM, or FP16 for the mixed mode's FP32
 // preconditioner), widened to TM on load.
-template <typename TR, typename TZ, typename TM, typename TP = TM>
+// G: global normal equations, the transpose form with the reverse-slot
+// coefficients arg, exrg, eyrg on all five unknowns of the neighbour.
+template <typename TR, typename TZ, typename TM, typename TP = TM, bool G = false>
 __global__ void k_ilu_fwd(DeviceMesh d, const TP *__restrict__ Pg, const TP *__restrict__ alg,
                           const TP *__restrict__ exg, const TP *__restrict__ eyg, const int32_t *__restrict__ rows,
-                          int64_t nrows, const TR *r, const TZ *zin, TZ *zout, int use_nb, TZ *__restrict__ rcopy)
+                          int64_t nrows, const TR *r, const TZ *zin, TZ *zout, int use_nb, TZ *__restrict__ rcopy,
+                          const TP *__restrict__ arg = nullptr, const TP *__restrict__ exrg = nullptr,
+                          const TP *__restrict__ eyrg = nullptr)
 {
     const int64_t T = d.T;
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -409,6 +461,16 @@ __global__ void k_ilu_fwd(DeviceMesh d, const TP *__restrict__ Pg, const TP *__r
 #pragma unroll
             for (int v = 0; v < NV; ++v)
                 oacc(sa, sax, say, TM(zin[(v * ND + 0) * T + j]), TM(zin[(v * ND + 1) * T + j]), y + v * ND);
+            if (G) {
+                const TM sr = TM(arg[s * T + i]), srx = sr * TM(exrg[s * T + i]), sry = sr * TM(eyrg[s * T + i]);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    TM zj[ND];
+#pragma unroll
+                    for (int l = 0; l < ND; ++l) zj[l] = TM(zin[(v * ND + l) * T + j]);
+                    racc(sr, srx, sry, zj, y + v * ND);
+                }
+            }
         }
     }
 #pragma unroll
@@ -425,11 +487,12 @@ __global__ void k_ilu_fwd(DeviceMesh d, const TP *__restrict__ Pg, const TP *__r
 // Backward block-ILU relation: x_i = z_i + P_i sum_{j>i} O_ij xin_j (own data
 // loaded before the neighbour gathers; with no upper neighbour the sum is 0
 // and x_i = z_i exactly).
-template <typename TZ, typename TM, typename TP = TM>
+template <typename TZ, typename TM, typename TP = TM, bool G = false>
 __global__ void __launch_bounds__(kBlock, sizeof(TM) == 4 ? 3 : 1)
     k_ilu_bwd(DeviceMesh d, const TP *__restrict__ Pg, const TP *__restrict__ alg, const TP *__restrict__ exg,
               const TP *__restrict__ eyg, const int32_t *__restrict__ rows, int64_t nrows, const TZ *z, const TZ *xin,
-              TZ *xout)
+              TZ *xout, const TP *__restrict__ arg = nullptr, const TP *__restrict__ exrg = nullptr,
+              const TP *__restrict__ eyrg = nullptr)
 {
     const int64_t T = d.T;
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -452,6 +515,16 @@ __global__ void __launch_bounds__(kBlock, sizeof(TM) == 4 ? 3 : 1)
 #pragma unroll
         for (int v = 0; v < NV; ++v)
             oacc(sa, sax, say, TM(xin[(v * ND + 0) * T + j]), TM(xin[(v * ND + 1) * T + j]), y + v * ND);
+        if (G) {
+            const TM sr = TM(arg[s * T + i]), srx = sr * TM(exrg[s * T + i]), sry = sr * TM(eyrg[s * T + i]);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                TM xj[ND];
+#pragma unroll
+                for (int l = 0; l < ND; ++l) xj[l] = TM(xin[(v * ND + l) * T + j]);
+                racc(sr, srx, sry, xj, y + v * ND);
+            }
+        }
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v)
@@ -886,28 +959,47 @@ __global__ void k_mark_noconv(const double *__restrict__ bnorm, const double *__
 
 inline unsigned nblocks(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
+// The reverse-slot coefficients of the global normal equations for the ILU
+// kernels (all NULL for the per-cell equations).
+template <typename TP>
+struct RevSlots {
+    const TP *a = nullptr, *x = nullptr, *y = nullptr;
+};
+
 // dst = M^{-1} src (block ILU(0) on the RCM order).  TZ, TM: storage and
-// arithmetic precision of the application; tA, tB: work buffers of type TZ.
+// arithmetic precision of the application; TP: storage of the factors; tA, tB:
+// work buffers of type TZ; rev: reverse slots of the global normal equations.
 template <typename TR, typename TZ, typename TM, typename TP = TM>
 gks_status precond_t(gks_mesh *m, const TP *Pg, const TP *alg, const TP *exg, const TP *eyg, const TR *src,
-                     TZ *dst, TZ *tA, TZ *tB, TZ *rz, cudaStream_t s)
+                     TZ *dst, TZ *tA, TZ *tB, TZ *rz, cudaStream_t s, RevSlots<TP> rev = {})
 {
     DeviceMesh &d = m->d;
     const int64_t T = d.T;
+    // forward / backward relation, the global variant when reverse slots are given
+    auto fwd = [&](int64_t n, const int32_t *rows, auto r, const TZ *zin, TZ *zout, int use_nb, TZ *rc) {
+        using TRx = std::remove_cv_t<std::remove_pointer_t<decltype(r)>>;
+        if (rev.a)
+            k_ilu_fwd<TRx, TZ, TM, TP, true><<<nblocks(n), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, rows, n, r, zin, zout,
+                                                                          use_nb, rc, rev.a, rev.x, rev.y);
+        else
+            k_ilu_fwd<TRx, TZ, TM, TP, false><<<nblocks(n), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, rows, n, r, zin,
+                                                                           zout, use_nb, rc);
+        note_launch();
+    };
+    auto bwd = [&](int64_t n, const int32_t *rows, const TZ *z, const TZ *xin, TZ *xout) {
+        if (rev.a)
+            k_ilu_bwd<TZ, TM, TP, true><<<nblocks(n), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, rows, n, z, xin, xout,
+                                                                     rev.a, rev.x, rev.y);
+        else
+            k_ilu_bwd<TZ, TM, TP, false><<<nblocks(n), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, rows, n, z, xin, xout);
+        note_launch();
+    };
     if (m->cfg.precond == GKS_PC_ILU_EXACT) {
         const auto &lp = m->lvl_lo_ptr;
-        for (size_t l = 0; l + 1 < lp.size(); ++l) {
-            const int64_t n = lp[l + 1] - lp[l];
-            k_ilu_fwd<TR, TZ, TM, TP><<<nblocks(n), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, d.lvl_lo + lp[l], n, src,
-                                                                 dst, dst, 1, nullptr);
-            note_launch();
-        }
+        for (size_t l = 0; l + 1 < lp.size(); ++l)
+            fwd(lp[l + 1] - lp[l], d.lvl_lo + lp[l], src, dst, dst, 1, (TZ *)nullptr);
         const auto &up = m->lvl_up_ptr;
-        for (size_t l = 0; l + 1 < up.size(); ++l) {
-            const int64_t n = up[l + 1] - up[l];
-            k_ilu_bwd<TZ, TM, TP><<<nblocks(n), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, d.lvl_up + up[l], n, dst, dst, dst);
-            note_launch();
-        }
+        for (size_t l = 0; l + 1 < up.size(); ++l) bwd(up[l + 1] - up[l], d.lvl_up + up[l], dst, dst, dst);
     } else {
         // sweeps: forward z^0 = P r, z^{q+1} = F(z^q); backward x^0 = z, x^{q+1} = B(x^q)
         const int ns = m->cfg.ilu_sweeps;
@@ -915,16 +1007,12 @@ gks_status precond_t(gks_mesh *m, const TP *Pg, const TP *alg, const TP *exg, co
         TZ *zb = (ns % 2 == 0) ? dst : tA;
         // a wider source is rounded to TZ once, in the first pass, for the sweeps
         TZ *rc = (sizeof(TR) > sizeof(TZ) && ns > 0) ? rz : nullptr;
-        k_ilu_fwd<TR, TZ, TM, TP><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, src, nullptr, za, 0, rc);
-        note_launch();
+        fwd(T, nullptr, src, nullptr, za, 0, rc);
         for (int q = 0; q < ns; ++q) {
             if (rc)
-                k_ilu_fwd<TZ, TZ, TM, TP><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, rc, za, zb, 1,
-                                                                     nullptr);
+                fwd(T, nullptr, (const TZ *)rc, za, zb, 1, (TZ *)nullptr);
             else
-                k_ilu_fwd<TR, TZ, TM, TP><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, src, za, zb, 1,
-                                                                     nullptr);
-            note_launch();
+                fwd(T, nullptr, src, za, zb, 1, (TZ *)nullptr);
             std::swap(za, zb);
         }
         if (ns == 0) {
@@ -933,8 +1021,7 @@ gks_status precond_t(gks_mesh *m, const TP *Pg, const TP *alg, const TP *exg, co
             TZ *xa = za;                                    // x^0 = z (in tA)
             TZ *xb = (ns % 2 == 1) ? dst : tB;
             for (int q = 0; q < ns; ++q) {
-                k_ilu_bwd<TZ, TM, TP><<<nblocks(T), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, nullptr, T, za, xa, xb);
-                note_launch();
+                bwd(T, nullptr, za, xa, xb);
                 xa = xb;
                 xb = (xb == dst) ? tB : dst;
             }
@@ -948,7 +1035,8 @@ template <typename TR>
 gks_status precond(gks_mesh *m, const TR *src, double *dst, cudaStream_t s)
 {
     DeviceMesh &d = m->d;
-    return precond_t<TR, double, double>(m, d.P, d.alpha, d.ex, d.ey, src, dst, m->wk.t2, m->wk.t3, nullptr, s);
+    return precond_t<TR, double, double>(m, d.P, d.alpha, d.ex, d.ey, src, dst, m->wk.t2, m->wk.t3, nullptr, s,
+                                         {d.alr, d.exr, d.eyr});
 }
 
 template <typename TR>
@@ -957,9 +1045,9 @@ gks_status precond32(gks_mesh *m, const TR *src, float *dst, cudaStream_t s)
     DeviceMesh &d = m->d;
     if (d.P16)   // FP16 factors (ilu_fp16), FP32 arithmetic
         return precond_t<TR, float, float, __half>(m, d.P16, d.alpha16, d.ex16, d.ey16, src, dst, m->wk.t2_32,
-                                                   m->wk.t3_32, m->wk.r32, s);
+                                                   m->wk.t3_32, m->wk.r32, s, {d.alr16, d.exr16, d.eyr16});
     return precond_t<TR, float, float>(m, d.P32, d.alpha32, d.ex32, d.ey32, src, dst, m->wk.t2_32, m->wk.t3_32,
-                                       m->wk.r32, s);
+                                       m->wk.r32, s, {d.alr32, d.exr32, d.eyr32});
 }
 
 // Any active / any running system into the pinned host flags (no synchronisation).
@@ -1242,13 +1330,36 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
     const int32_t *sxn = sx ? sx + ns : nullptr;
     // V_0 = 2^-e (b - K x) and partial |V_0|^2: double-FP32 arithmetic into the
     // FP32 basis when the operator has FP32 pairs, FP64 arithmetic otherwise
-    auto residual = [&](cudaStream_t q) -> gks_status {
-        if (std::is_same<TB, float>::value && d.D2)
-            k_resid_df<<<4 * nb, kBlock, 0, q>>>(d, d.D2, d.S2, k.x, reinterpret_cast<float *>(V), k.b, k.part, ps,
-                                                 sxn);
+    // operator applications y = K x (mode 0) or the FP64 residual (mode 1); the
+    // global normal equations' variant when the mesh has reverse slots
+    auto spmv64 = [&](cudaStream_t q, const double *xs, TB *y, int mode, const double *bb, const int32_t *se) {
+        if (d.alr)
+            k_spmv<double, double, TB, true><<<nb, kBlock, 0, q>>>(d, d.D, d.alpha, d.ex, d.ey, xs, y, mode, bb,
+                                                                   k.part, ps, se, d.alr, d.exr, d.eyr);
         else
-            k_spmv<double, double, TB><<<nb, kBlock, 0, q>>>(d, d.D, d.alpha, d.ex, d.ey, k.x, V, 1, k.b, k.part,
-                                                             ps, sxn);
+            k_spmv<double, double, TB, false><<<nb, kBlock, 0, q>>>(d, d.D, d.alpha, d.ex, d.ey, xs, y, mode, bb,
+                                                                    k.part, ps, se);
+    };
+    auto spmv32 = [&](cudaStream_t q, const float *xs, TB *y) {
+        if (d.alr32)
+            k_spmv<float, float, TB, true><<<nb, kBlock, 0, q>>>(d, d.D32, d.alpha32, d.ex32, d.ey32, xs, y, 0,
+                                                                 nullptr, nullptr, 0, nullptr, d.alr32, d.exr32,
+                                                                 d.eyr32);
+        else
+            k_spmv<float, float, TB, false><<<nb, kBlock, 0, q>>>(d, d.D32, d.alpha32, d.ex32, d.ey32, xs, y, 0,
+                                                                  nullptr, nullptr, 0);
+    };
+    auto residual = [&](cudaStream_t q) -> gks_status {
+        if (std::is_same<TB, float>::value && d.D2) {
+            if (d.SR2)
+                k_resid_df<true><<<4 * nb, kBlock, 0, q>>>(d, d.D2, d.S2, k.x, reinterpret_cast<float *>(V), k.b,
+                                                           k.part, ps, sxn, d.SR2);
+            else
+                k_resid_df<false><<<4 * nb, kBlock, 0, q>>>(d, d.D2, d.S2, k.x, reinterpret_cast<float *>(V), k.b,
+                                                            k.part, ps, sxn);
+        } else {
+            spmv64(q, k.x, V, 1, k.b, sxn);
+        }
         note_launch();
         GKS_CUDA(cudaGetLastError());
         return GKS_OK;
@@ -1291,11 +1402,9 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
         prof_stop(m, slot, q);
         slot = prof_start(m, kProfSpmv, q);
         if (mixed)
-            k_spmv<float, float, TB><<<nb, kBlock, 0, q>>>(d, d.D32, d.alpha32, d.ex32, d.ey32, k.Z32 + j * vs, vj1,
-                                                           0, nullptr, nullptr, 0);
+            spmv32(q, k.Z32 + j * vs, vj1);
         else
-            k_spmv<double, double, TB><<<nb, kBlock, 0, q>>>(d, d.D, d.alpha, d.ex, d.ey, k.Z + j * vs, vj1, 0,
-                                                             nullptr, nullptr, 0);
+            spmv64(q, k.Z + j * vs, vj1, 0, nullptr, nullptr);
         note_launch();
         prof_stop(m, slot, q);
         slot = prof_start(m, kProfOrth, q);

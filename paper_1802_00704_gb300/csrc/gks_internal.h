@@ -63,20 +63,26 @@ struct DeviceMesh {
     int32_t *nb = nullptr;           // [3][T] neighbour (internal index) or -1
     double *alpha = nullptr;         // [3][T] w^2 h_i / h_j
     double *ex = nullptr, *ey = nullptr;  // [3][T] centroid offsets of j in i's frame (0 when k_i = 1)
+    // global normal equations (cls_global, Eq. (33)): the reverse slot's coefficients,
+    // alpha_ji and i's centroid in j's frame (0 when k_j = 1); NULL otherwise
+    double *alr = nullptr, *exr = nullptr, *eyr = nullptr;  // [3][T]
     double *a0 = nullptr;            // [3][5][T] weighted row 0 of A_ij (right-hand side)
     double *D = nullptr;             // [15][T] symmetric diagonal block, upper triangle row-major
     double *P = nullptr;             // [25][T] inverse of the ILU(0) diagonal block, row-major
     // FP32 copies of the operator and factors (mixed precision)
     float *D32 = nullptr, *P32 = nullptr, *alpha32 = nullptr, *ex32 = nullptr, *ey32 = nullptr;
+    float *alr32 = nullptr, *exr32 = nullptr, *eyr32 = nullptr;
     // FP16 copies of the ILU(0) factors for the FP32 preconditioner (ilu_fp16;
     // NULL when not asked for or a value is outside FP16's range)
     __half *P16 = nullptr, *alpha16 = nullptr, *ex16 = nullptr, *ey16 = nullptr;
+    __half *alr16 = nullptr, *exr16 = nullptr, *eyr16 = nullptr;
     float *ih32 = nullptr;           // [T] 1 / h_i (mixed flux)
     // the operator as FP32 pairs hi + lo for the double-FP32 refinement residual
     // (mixed mode with an FP32 basis; NULL when a value is outside the pair range)
     float *D2 = nullptr;             // [30][T] the 15 diagonal-block values, then their low parts
     float *S2 = nullptr;             // [18][T] sa, sa dx, sa dy per neighbour slot (sa = -alpha, 0
                                      //         without neighbour), then their low parts
+    float *SR2 = nullptr;            // [18][T] the same for the reverse slots (global normal equations)
     double *ox = nullptr, *oy = nullptr;  // [3][T] neighbour centroid in i's scaled frame (limiter)
     int32_t *kord = nullptr;         // [T] reconstruction order k_i of Eq. (28) (limiter)
     int32_t *cf = nullptr;           // [3][T] (face << 1) | side, -1 unused

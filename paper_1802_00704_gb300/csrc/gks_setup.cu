@@ -113,6 +113,19 @@ void oblock(double alpha, double ex, double ey, double *O)
     O[4 * 5 + 1] = alpha * ey;
 }
 
+// O += the transpose form alr [e1 (1, 0, exr, eyr, 0) + e2 (0, 1, 0, exr, eyr)]:
+// what the global normal equations (Eq. (33)) add to the block (i, j) from j's
+// own equations about i (alr = alpha_ji, (exr, eyr) = i's centroid in j's frame).
+void oblock_rev(double alr, double exr, double eyr, double *O)
+{
+    O[0 * 5 + 0] += alr;
+    O[0 * 5 + 2] += alr * exr;
+    O[0 * 5 + 3] += alr * eyr;
+    O[1 * 5 + 1] += alr;
+    O[1 * 5 + 3] += alr * exr;
+    O[1 * 5 + 4] += alr * eyr;
+}
+
 // Reverse Cuthill-McKee order (new -> old) of the cell graph given by adjacency lists.
 // Start vertex of each component: a pseudo-peripheral vertex found by repeated
 // breadth-first searches (George & Liu); neighbours are queued by increasing degree.
@@ -194,12 +207,13 @@ struct HostCase {
     int32_t nlo = 0, nup = 0;
     std::vector<int32_t> perm, nb, cf, fl, fr, ftag, fperm, lev_lo, lev_up, kord;
     std::vector<double> area, iarea, h, mxx, mxy, myy, inrad, alpha, ex, ey, ox, oy, a0, D, P;
+    std::vector<double> alr, exr, eyr;   // global normal equations only (empty otherwise)
     std::vector<double> fnx, fny, flen, gl, gr, bc;
 };
 
 // Geometry, boundary order reduction (Eq. (28)), RCM order, CLS blocks
 // (Eq. (29)), block ILU(0) factors and levels of one case.
-gks_status build_case(const CaseIn &in, double w, int second_order, HostCase &hc)
+gks_status build_case(const CaseIn &in, double w, int second_order, int cls_global, HostCase &hc)
 {
     const double *nodes = in.nodes, *face_shift = in.face_shift, *bc_state = in.bc_state;
     const int32_t *tris = in.tris, *faces = in.faces;
@@ -293,6 +307,8 @@ gks_status build_case(const CaseIn &in, double w, int second_order, HostCase &hc
     // ---- CLS blocks in internal order
     std::vector<int32_t> h_nb(3 * T, -1), h_cf(3 * T, -1);
     std::vector<double> h_alpha(3 * T, 0.0), h_ex(3 * T, 0.0), h_ey(3 * T, 0.0), h_a0(15 * T, 0.0);
+    // global normal equations: the reverse slot's coefficients (alpha_ji, i's centroid in j's frame)
+    std::vector<double> h_alr(3 * T, 0.0), h_exr(3 * T, 0.0), h_eyr(3 * T, 0.0);
     std::vector<double> h_ox(3 * T, 0.0), h_oy(3 * T, 0.0);
     std::vector<int32_t> h_kord(T, 2);
     std::vector<double> h_D(15 * T, 0.0), h_Dfull(25 * T, 0.0);
@@ -333,6 +349,15 @@ gks_status build_case(const CaseIn &in, double w, int second_order, HostCase &hc
             double r2[5] = {0.0, w, 0.0, w * dx, w * dy};
             for (int a = 0; a < ni; ++a)
                 for (int b = 0; b < ni; ++b) D[5 * a + b] += a0[a] * a0[b] + r1[a] * r1[b] + r2[a] * r2[b];
+            if (cls_global) {
+                // j's equations about i (Eq. (33)): their B rows (w h_j / h_i) e1, e2 act on u_i
+                const double q = w * d.h / c.h;
+                D[0] += q * q;
+                D[6] += q * q;
+                h_alr[slot * T + i] = w * w * d.h / c.h;
+                h_exr[slot * T + i] = d.k == 2 ? (c.cx - ox - d.cx) / d.h : 0.0;
+                h_eyr[slot * T + i] = d.k == 2 ? (c.cy - oy - d.cy) / d.h : 0.0;
+            }
             int32_t j = inv[cj];
             h_nb[slot * T + i] = j;
             h_alpha[slot * T + i] = w * w * c.h / d.h;
@@ -365,10 +390,12 @@ gks_status build_case(const CaseIn &in, double w, int second_order, HostCase &hc
             if (k < 0 || k >= i) continue;
             double Oik[25];
             oblock(h_alpha[s * T + i], h_ex[s * T + i], h_ey[s * T + i], Oik);
+            if (cls_global) oblock_rev(h_alr[s * T + i], h_exr[s * T + i], h_eyr[s * T + i], Oik);
             for (int s2 = 0; s2 < 3; ++s2) {
                 if (h_nb[s2 * T + k] != (int32_t)i) continue;
                 double Oki[25], tmp[25];
                 oblock(h_alpha[s2 * T + k], h_ex[s2 * T + k], h_ey[s2 * T + k], Oki);
+                if (cls_global) oblock_rev(h_alr[s2 * T + k], h_exr[s2 * T + k], h_eyr[s2 * T + k], Oki);
                 const double *Pk = &Pinv[25 * k];
                 for (int a = 0; a < 5; ++a)
                     for (int b = 0; b < 5; ++b) {
@@ -493,6 +520,11 @@ gks_status build_case(const CaseIn &in, double w, int second_order, HostCase &hc
     hc.myy = std::move(h_myy);
     hc.inrad = std::move(h_inrad);
     hc.alpha = std::move(h_alpha);
+    if (cls_global) {
+        hc.alr = std::move(h_alr);
+        hc.exr = std::move(h_exr);
+        hc.eyr = std::move(h_eyr);
+    }
     hc.ex = std::move(h_ex);
     hc.ey = std::move(h_ey);
     hc.ox = std::move(h_ox);
@@ -540,7 +572,7 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
         unsigned nt = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), (unsigned)n_cases));
         auto work = [&]() {
             for (int32_t c; (c = next.fetch_add(1)) < n_cases;) {
-                st[c] = build_case(cases[c], cfg.cls_w, cfg.second_order, hcs[c]);
+                st[c] = build_case(cases[c], cfg.cls_w, cfg.second_order, cfg.cls_global, hcs[c]);
                 if (st[c] != GKS_OK) {
                     msg[c] = last_error();
                     int expect = -1;
@@ -579,6 +611,7 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
     std::vector<double> h_inrad(T, std::numeric_limits<double>::infinity());
     std::vector<double> h_alpha(3 * T, 0.0), h_ex(3 * T, 0.0), h_ey(3 * T, 0.0), h_a0(15 * T, 0.0);
     std::vector<double> h_ox(3 * T, 0.0), h_oy(3 * T, 0.0);
+    std::vector<double> h_alr(cfg.cls_global ? 3 * T : 0, 0.0), h_exr(h_alr.size(), 0.0), h_eyr(h_alr.size(), 0.0);
     std::vector<int32_t> h_kord(T, 2);
     std::vector<double> h_D(15 * T, 0.0), h_P(25 * T, 0.0);
     std::vector<int32_t> h_fl(F), h_fr(F), h_ftag(F), h_fperm(F), h_face_case(F);
@@ -611,6 +644,9 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
         place(hc.inrad, Tc, 1, h_inrad, T, o);
         place(hc.alpha, Tc, 3, h_alpha, T, o); place(hc.ex, Tc, 3, h_ex, T, o); place(hc.ey, Tc, 3, h_ey, T, o);
         place(hc.ox, Tc, 3, h_ox, T, o); place(hc.oy, Tc, 3, h_oy, T, o); place(hc.kord, Tc, 1, h_kord, T, o);
+        if (cfg.cls_global) {
+            place(hc.alr, Tc, 3, h_alr, T, o); place(hc.exr, Tc, 3, h_exr, T, o); place(hc.eyr, Tc, 3, h_eyr, T, o);
+        }
         place(hc.a0, Tc, 15, h_a0, T, o); place(hc.D, Tc, 15, h_D, T, o); place(hc.P, Tc, 25, h_P, T, o);
         for (int64_t f = 0; f < Fc; ++f) {
             h_fl[fo + f] = (int32_t)(o + hc.fl[f]);
@@ -665,6 +701,9 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
     UP(fl, h_fl); UP(fr, h_fr); UP(ftag, h_ftag); UP(fperm, h_fperm); UP(fnx, h_fnx); UP(fny, h_fny);
     UP(flen, h_flen); UP(gl, h_gl); UP(gr, h_gr); UP(bc, h_bc);
     UP(blk_case, h_blk_case); UP(case_blk, h_case_blk); UP(face_case, h_face_case);
+    if (cfg.cls_global) {
+        UP(alr, h_alr); UP(exr, h_exr); UP(eyr, h_eyr);
+    }
 
     if (cfg.limiter) {
         UP(ox, h_ox); UP(oy, h_oy); UP(kord, h_kord);
@@ -672,6 +711,9 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
     if (cfg.precision == GKS_MIXED) {
         auto f32 = [](const std::vector<double> &v) { return std::vector<float>(v.begin(), v.end()); };
         UP(D32, f32(h_D)); UP(P32, f32(h_P)); UP(alpha32, f32(h_alpha)); UP(ex32, f32(h_ex)); UP(ey32, f32(h_ey));
+        if (cfg.cls_global) {
+            UP(alr32, f32(h_alr)); UP(exr32, f32(h_exr)); UP(eyr32, f32(h_eyr));
+        }
         if (cfg.ilu_fp16) {
             // FP16 copies of the ILU(0) factors if every value fits FP16's normal range
             // (smaller ones round to FP16's subnormals, far below the block's scale)
@@ -685,8 +727,12 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
                 return o;
             };
             std::vector<__half> p16 = f16(h_P), a16 = f16(h_alpha), x16 = f16(h_ex), y16 = f16(h_ey);
+            std::vector<__half> ar16 = f16(h_alr), xr16 = f16(h_exr), yr16 = f16(h_eyr);
             if (fits) {
                 UP(P16, p16); UP(alpha16, a16); UP(ex16, x16); UP(ey16, y16);
+                if (cfg.cls_global) {
+                    UP(alr16, ar16); UP(exr16, xr16); UP(eyr16, yr16);
+                }
             }
         }
         std::vector<float> h_ih32(T);
@@ -702,7 +748,7 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
                 hi = float(v);
                 lo = float(v - double(hi));
             };
-            std::vector<float> h_D2(30 * T), h_S2(18 * T);
+            std::vector<float> h_D2(30 * T), h_S2(18 * T), h_SR2(cfg.cls_global ? 18 * T : 0);
             for (int64_t i = 0; i < T; ++i) {
                 for (int q = 0; q < 15; ++q) pair(h_D[q * T + i], h_D2[q * T + i], h_D2[(15 + q) * T + i]);
                 for (int s = 0; s < 3; ++s) {
@@ -710,10 +756,17 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
                     const double o[3] = {sa, sa * h_ex[s * T + i], sa * h_ey[s * T + i]};
                     for (int q = 0; q < 3; ++q)
                         pair(o[q], h_S2[(3 * s + q) * T + i], h_S2[(9 + 3 * s + q) * T + i]);
+                    if (cfg.cls_global) {
+                        const double sr = h_nb[s * T + i] >= 0 ? -h_alr[s * T + i] : 0.0;
+                        const double r[3] = {sr, sr * h_exr[s * T + i], sr * h_eyr[s * T + i]};
+                        for (int q = 0; q < 3; ++q)
+                            pair(r[q], h_SR2[(3 * s + q) * T + i], h_SR2[(9 + 3 * s + q) * T + i]);
+                    }
                 }
             }
             if (in_range) {
                 UP(D2, h_D2); UP(S2, h_S2);
+                if (cfg.cls_global) UP(SR2, h_SR2);
             }
         }
     }

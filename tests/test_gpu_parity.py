@@ -274,3 +274,47 @@ def test_kinetic_interface_slopes_steps_match_oracle(O, G, name):
         assert om.step(wo, dt).status == 0
         assert m.step(w, dt)["status"] == 0
     assert np.all(rel_max(host(w), wo, axis=1) <= 1e-10), rel_max(host(w), wo, axis=1)
+
+
+# --------------------------------------------------------------------------- global CLS normal equations
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("mode", ["fp64_exact", "fp64_sweep", "mixed"])
+def test_global_cls_matches_oracle(O, G, name, mode):
+    """cls_global (Eq. (33), C^T C u = C^T b) against the oracle's assembly of the
+    same global equations: coefficients within 1e-9 relative max in FP64 (exact
+    and sweep ILU) and in mixed precision (FP32 basis, FP16 ILU factors,
+    double-FP32 residual); the solution differs from the per-cell equations'."""
+    c = CASES[name]()
+    om = O.OracleMesh(c.mesh, cls_global=1)
+    ref, _, rr, bad = om.cls_solve(c.w0)
+    assert bad == 0
+    kw = dict(cls_global=1)
+    if mode == "mixed":
+        kw.update(precision=G.MIXED, basis_fp32=1, ilu_fp16=1)
+    else:
+        kw.update(precond=G.PC_ILU_EXACT if mode == "fp64_exact" else G.PC_ILU_SWEEP)
+    m = G.GksMesh(c.mesh, **kw)
+    coef, info = m.cls_reconstruct(dev(c.w0))
+    assert info["converged"] == 1 and max(info["relres"]) <= 1e-12
+    got = host(coef)
+    for v in range(4):
+        if np.max(np.abs(ref[v])) == 0.0:
+            assert np.all(got[v] == 0.0)
+        else:
+            assert rel_max(got[v], ref[v]) <= 1e-9, (v, rel_max(got[v], ref[v]))
+    per_cell, _, _, _ = O.OracleMesh(c.mesh).cls_solve(c.w0)
+    assert np.max(np.abs(per_cell - ref)) > 1e-6 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("name", ["shock_vortex40x20", "walled13x9"])
+def test_global_cls_steps_match_oracle(O, G, name):
+    c = CASES[name]()
+    om = O.OracleMesh(c.mesh, cls_global=1)
+    m = G.GksMesh(c.mesh, cls_global=1)
+    wo, w = c.w0.copy(), dev(c.w0)
+    for _ in range(5):
+        dt = om.cfl_dt(wo)
+        assert om.step(wo, dt).status == 0
+        assert m.step(w, dt)["status"] == 0
+    assert np.all(rel_max(host(w), wo, axis=1) <= 1e-10), rel_max(host(w), wo, axis=1)
