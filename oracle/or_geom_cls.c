@@ -194,19 +194,32 @@ int or_build_cls(or_mesh *m)
             means_over(m, i, j, ox, oy, 0, va, gxa, gya);   /* basis of i over cell j */
             /* basis of j over its own cell: evaluated in j's own (untranslated) frame */
             means_over(m, j, j, 0.0, 0.0, 1, vb, gxb, gyb);
-            double A[3][5], B[3][5];
+            /* rows p = 0 (value), 1 (x, y derivatives) and, with M = 2, 2 (xx, xy, yy),
+             * each weighted by w_{i,p} = (w h_i)^p; the second derivatives of the
+             * quadratic basis are the constants 1/h^2 on its last three entries */
+            double A[6][5], B[6][5];
             double wp1 = w * m->h[i];                           /* w_{i,1} = (w h_i)^1 */
+            double wp2 = wp1 * wp1;                             /* w_{i,2} = (w h_i)^2 */
+            const int M = m->prm.cls_M, np = M == 0 ? 1 : (M == 1 ? 3 : 6);
             for (int l = 0; l < 5; ++l) {
                 A[0][l] = va[l];  A[1][l] = wp1 * gxa[l]; A[2][l] = wp1 * gya[l];
                 B[0][l] = vb[l];  B[1][l] = wp1 * gxb[l]; B[2][l] = wp1 * gyb[l];
+                for (int p = 3; p < 6; ++p) { A[p][l] = 0.0; B[p][l] = 0.0; }
+            }
+            if (M == 2) {
+                const double hi2 = m->h[i] * m->h[i], hj2 = m->h[j] * m->h[j];
+                for (int p = 0; p < 3; ++p) {
+                    if (ni == 5) A[3 + p][2 + p] = wp2 / hi2;
+                    if (nj == 5) B[3 + p][2 + p] = wp2 / hj2;
+                }
             }
             for (int l = 0; l < 5; ++l) m->a0[15 * i + 5 * k + l] = (l < ni) ? A[0][l] : 0.0;
             double *Di = &Dall[25 * i], *Oik = &Oall[75 * i + 25 * k];
             for (int r = 0; r < ni; ++r) {
                 for (int c = 0; c < ni; ++c)
-                    for (int p = 0; p < 3; ++p) Di[5 * r + c] += A[p][r] * A[p][c];
+                    for (int p = 0; p < np; ++p) Di[5 * r + c] += A[p][r] * A[p][c];
                 for (int c = 0; c < nj; ++c)
-                    for (int p = 0; p < 3; ++p) Oik[5 * r + c] += A[p][r] * B[p][c];
+                    for (int p = 0; p < np; ++p) Oik[5 * r + c] += A[p][r] * B[p][c];
             }
             if (m->prm.cls_global) {
                 /* the same equations seen from j: B^T B on D_j, B^T A on the block
@@ -221,9 +234,9 @@ int or_build_cls(or_mesh *m)
                 double *Dj = &Dall[25 * j], *Oji = &Oall[75 * j + 25 * kb];
                 for (int r = 0; r < nj; ++r) {
                     for (int c = 0; c < nj; ++c)
-                        for (int p = 0; p < 3; ++p) Dj[5 * r + c] += B[p][r] * B[p][c];
+                        for (int p = 0; p < np; ++p) Dj[5 * r + c] += B[p][r] * B[p][c];
                     for (int c = 0; c < ni; ++c)
-                        for (int p = 0; p < 3; ++p) Oji[5 * r + c] += B[p][r] * A[p][c];
+                        for (int p = 0; p < np; ++p) Oji[5 * r + c] += B[p][r] * A[p][c];
                 }
             }
         }

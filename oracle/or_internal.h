@@ -34,6 +34,8 @@ typedef struct or_params {
     int    cls_global;  /* 1: the global normal equations C^T C u = C^T b of the
                            whole mesh (Eq. (33), symmetric positive definite)
                            instead of each cell's own least-squares equations    */
+    int    cls_M;       /* highest derivative order p <= M <= k of the CLS
+                           equations of Eq. (29) (default 1; 0 needs k = 1)      */
 } or_params;
 
 /* Boundary tags (same numbering as the input generator). */

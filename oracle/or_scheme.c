@@ -29,6 +29,7 @@ void or_params_default(or_params *p)
     p->tau2_exact = 0; p->slope0_mode = 0; p->limiter = 0; p->second_order = 0; p->prandtl = 1.0;
     p->limit_char = 0;
     p->cls_global = 0;
+    p->cls_M = 1;
 }
 
 void or_mesh_free(or_mesh *m)
@@ -48,7 +49,8 @@ or_mesh *or_mesh_new(const double *nodes, int64_t n_nodes, const int32_t *tris, 
                      const double *bc_state, const or_params *prm, int *err)
 {
     *err = 0;
-    if (n_tri <= 0 || n_nodes <= 0 || n_face <= 0 || (prm->slope0_mode != 0 && prm->slope0_mode != 1)) {
+    if (n_tri <= 0 || n_nodes <= 0 || n_face <= 0 || (prm->slope0_mode != 0 && prm->slope0_mode != 1) ||
+        prm->cls_M < 0 || prm->cls_M > 2 || (prm->cls_M == 0 && !prm->second_order)) {
         *err = -10;
         return NULL;
     }

@@ -43,7 +43,8 @@ class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("mu", C.c_double), ("cls_w", C.c_double),
                 ("gmres_m", C.c_int), ("gmres_maxit", C.c_int), ("gmres_rtol", C.c_double),
                 ("tau2_exact", C.c_int), ("slope0_mode", C.c_int), ("limiter", C.c_int), ("second_order", C.c_int),
-                ("prandtl", C.c_double), ("limit_char", C.c_int), ("cls_global", C.c_int)]
+                ("prandtl", C.c_double), ("limit_char", C.c_int), ("cls_global", C.c_int),
+                ("cls_M", C.c_int)]
 
 
 def _load():

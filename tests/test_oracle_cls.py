@@ -54,14 +54,17 @@ def _exact_coef(cg, T):
     return coef
 
 
+@pytest.mark.parametrize("M", [1, 2])
 @pytest.mark.parametrize("glob", [0, 1])
-def test_cls_operator_exact_for_quadratics(oracle_mod, glob):
+def test_cls_operator_exact_for_quadratics(oracle_mod, glob, M):
     """The exact coefficients of a global quadratic satisfy every equation of a
     cell that can hold it (k = 2); per cell that zeroes the rows of k = 2 cells,
     in the global system (cls_global, Eq. (33)) the rows of k = 2 cells whose
-    neighbours are k = 2 too (their equations enter through B_ji)."""
+    neighbours are k = 2 too (their equations enter through B_ji).  With M = 2
+    (second-derivative equations) a k = 1 neighbour cannot match the second
+    derivatives either, so the same selection applies per cell."""
     m = _walled(8)
-    om = oracle_mod.OracleMesh(m, cls_global=glob)
+    om = oracle_mod.OracleMesh(m, cls_global=glob, cls_M=M)
     cg = om.cell_geometry()
     qbar = I.cell_average(m, lambda x, y: _quad(x, y)[None])[0]
     w = np.stack([qbar, qbar, qbar, qbar + 3.0])
@@ -80,7 +83,7 @@ def test_cls_operator_exact_for_quadratics(oracle_mod, glob):
         if r >= 0:
             nbrs[l].add(r)
             nbrs[r].add(l)
-    keep = [i for i in range(om.T) if k[i] == 2 and (not glob or all(k[j] == 2 for j in nbrs[i]))]
+    keep = [i for i in range(om.T) if k[i] == 2 and (not (glob or M == 2) or all(k[j] == 2 for j in nbrs[i]))]
     interior_rows = np.concatenate([np.arange(off[i], off[i] + 5) for i in keep])
     assert len(interior_rows) > 0
     assert np.abs(res[interior_rows]).max() < 1e-13
@@ -97,9 +100,10 @@ def test_constant_data_gives_zero_coefficients(oracle_mod, glob):
     assert bad == 0 and np.all(coef == 0.0)
 
 
+@pytest.mark.parametrize("M", [1, 2])
 @pytest.mark.parametrize("glob", [0, 1])
 @pytest.mark.parametrize("kind", ["periodic4", "periodic8", "walled6"])
-def test_gmres_matches_dense_lu(oracle_mod, kind, glob):
+def test_gmres_matches_dense_lu(oracle_mod, kind, glob, M):
     if kind.startswith("periodic"):
         c = I.advection_case(int(kind[-1]), k=1, amp=0.3)
         m, w = c.mesh, c.w0
@@ -107,7 +111,7 @@ def test_gmres_matches_dense_lu(oracle_mod, kind, glob):
         m = _walled(6)
         w = I.cell_average(m, lambda x, y: np.stack([1 + 0.2 * np.sin(3 * x + y), np.cos(x - 2 * y),
                                                      0.1 * x * y, 2.5 + np.exp(0.3 * x)]))
-    om = oracle_mod.OracleMesh(m, cls_global=glob)
+    om = oracle_mod.OracleMesh(m, cls_global=glob, cls_M=M)
     coef, it, rr, bad = om.cls_solve(w)
     ref = om.cls_dense(w)
     assert bad == 0 and np.all(rr < 1e-13)
@@ -155,16 +159,45 @@ def _dense(om):
     return K
 
 
+@pytest.mark.parametrize("M", [1, 2])
 @pytest.mark.parametrize("kind", ["walled6", "periodic5"])
-def test_global_cls_is_symmetric_positive_definite(oracle_mod, kind):
+def test_global_cls_is_symmetric_positive_definite(oracle_mod, kind, M):
     """cls_global: the normal equations of all equations together are C^T C,
     symmetric and positive definite (Eq. (33)); the default per-cell equations
     are not symmetric.  Both have the same sparsity (face neighbours)."""
     m = _walled(6) if kind == "walled6" else I.advection_case(5, seed=4).mesh
-    Kg = _dense(oracle_mod.OracleMesh(m, cls_global=1))
-    Kp = _dense(oracle_mod.OracleMesh(m))
+    Kg = _dense(oracle_mod.OracleMesh(m, cls_global=1, cls_M=M))
+    Kp = _dense(oracle_mod.OracleMesh(m, cls_M=M))
     scale = np.abs(Kg).max()
     assert np.abs(Kg - Kg.T).max() <= 1e-14 * scale
     assert np.linalg.eigvalsh(0.5 * (Kg + Kg.T)).min() > 1e-10 * scale
     assert np.abs(Kp - Kp.T).max() > 1e-3 * np.abs(Kp).max()
     assert np.array_equal(Kg != 0, (Kg != 0) | (Kp != 0)) or np.array_equal(Kg != 0, Kp != 0)
+
+
+def test_value_equations_only_for_the_linear_variant(oracle_mod):
+    """cls_M = 0 with k_i = 1 everywhere (second-order variant): only the value
+    equations, so each cell's gradient is its own least-squares fit to the
+    neighbours' averages, uncoupled (no off-diagonal blocks), and exact for a
+    linear field in every cell.  Every cell needs two neighbours (a y-periodic
+    strip; a corner triangle with one neighbour would leave its gradient
+    undetermined).  Without the linear variant the value equations cannot
+    determine the five quadratic coefficients, which is refused."""
+    c = I.riemann_strip_case(12, 4, left=(1.0, 0.0, 0.0, 1.0), right=(1.0, 0.0, 0.0, 1.0))
+    m = c.mesh
+    om = oracle_mod.OracleMesh(m, cls_M=0, second_order=1)
+    K = _dense(om)
+    rp, col, val, off = om.cls_matrix()
+    tol = 1e-13 * np.abs(K).max()        # the zero-mean basis' means vanish up to rounding
+    for i in range(om.T):
+        blk = K[off[i]:off[i] + 2]
+        assert np.abs(blk[:, :off[i]]).max(initial=0.0) <= tol and np.abs(blk[:, off[i] + 2:]).max(initial=0.0) <= tol
+    cg = om.cell_geometry()
+    qbar = I.cell_average(m, lambda x, y: (0.4 + 0.8 * x + 0.0 * y)[None])[0]
+    w = np.stack([qbar, qbar, qbar, qbar + 3.0])
+    coef, it, rr, bad = om.cls_solve(w)
+    assert bad == 0
+    assert np.allclose(coef[0, 0], 0.8 * cg["h"], rtol=1e-10, atol=1e-13)
+    assert np.allclose(coef[0, 1], 0.0, atol=1e-12)
+    with pytest.raises(Exception):
+        oracle_mod.OracleMesh(m, cls_M=0)
