@@ -157,6 +157,11 @@ typedef struct gks_config {
                               symmetric positive definite); 0 (default): each cell's
                               own least-squares equations (non-symmetric), the reading
                               that suits GMRES with ILU(0) (Sec. III.B)                */
+    int32_t cls_M;         /* highest derivative order of the CLS equations of Eq. (29)
+                              (M <= k): 1 (default) value and first derivatives;
+                              2 also the second derivatives (w h_i)^2 of quadratic
+                              cells; 0 the values only, which needs the second-order
+                              variant (k_i = 1) and two face neighbours per cell       */
 } gks_config;
 
 typedef struct gks_mesh gks_mesh;

@@ -130,14 +130,16 @@ __global__ void k_rhs(DeviceMesh d, const double *__restrict__ w, double *__rest
 // Every load (neighbour indices, blocks, the neighbours' gradient entries, own
 // data) is issued before the arithmetic; a missing neighbour reads the cell's
 // own entries with a zero block.
-// G: global normal equations, with the reverse-slot coefficients arg, exrg,
-// eyrg (the transpose form, racc); unused otherwise.
+// G: extended stencil (global normal equations and / or second-derivative
+// equations): the transpose form with the reverse-slot coefficients arg, exrg,
+// eyrg (racc) and the diagonal coupling bdg of the unknowns 3..5; unused
+// otherwise.
 template <typename TX, typename TM, bool G = false>
 __device__ __forceinline__ void cell_apply(const DeviceMesh &d, const TM *__restrict__ Dg, const TM *__restrict__ alg,
                                            const TM *__restrict__ exg, const TM *__restrict__ eyg,
                                            const TX *__restrict__ x, int64_t i, TM *acc,
                                            const TM *__restrict__ arg = nullptr, const TM *__restrict__ exrg = nullptr,
-                                           const TM *__restrict__ eyrg = nullptr)
+                                           const TM *__restrict__ eyrg = nullptr, const TM *__restrict__ bdgg = nullptr)
 {
     const int64_t T = d.T;
     int64_t jn[3];
@@ -180,14 +182,18 @@ __device__ __forceinline__ void cell_apply(const DeviceMesh &d, const TM *__rest
     if (G) {
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
-            const TM sr = sa[s] != TM(0) ? -arg[s * T + i] : TM(0);
+            const bool has = jn[s] != i;
+            const TM sr = has ? -arg[s * T + i] : TM(0);
             const TM srx = sr * exrg[s * T + i], sry = sr * eyrg[s * T + i];
+            const TM sb = has ? -bdgg[s * T + i] : TM(0);
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 TM xj[ND];
 #pragma unroll
                 for (int l = 0; l < ND; ++l) xj[l] = TM(x[(v * ND + l) * T + jn[s]]);
                 racc(sr, srx, sry, xj, acc + v * ND);
+#pragma unroll
+                for (int l = 2; l < ND; ++l) acc[v * ND + l] = fma(sb, xj[l], acc[v * ND + l]);
             }
         }
     }
@@ -204,7 +210,8 @@ __global__ void k_spmv(DeviceMesh d, const TM *__restrict__ Dg, const TM *__rest
                        const TM *__restrict__ exg, const TM *__restrict__ eyg, const TX *__restrict__ x,
                        TY *__restrict__ y, int mode, const double *__restrict__ b, double *__restrict__ part,
                        int pstride, const int32_t *__restrict__ sexp = nullptr, const TM *__restrict__ arg = nullptr,
-                       const TM *__restrict__ exrg = nullptr, const TM *__restrict__ eyrg = nullptr)
+                       const TM *__restrict__ exrg = nullptr, const TM *__restrict__ eyrg = nullptr,
+                       const TM *__restrict__ bdgg = nullptr)
 {
     __shared__ double sh[32 * NV];
     const int64_t T = d.T;
@@ -212,7 +219,7 @@ __global__ void k_spmv(DeviceMesh d, const TM *__restrict__ Dg, const TM *__rest
     double nr[NV] = {0, 0, 0, 0};
     if (i < T) {
         TM acc[NX];
-        cell_apply<TX, TM, G>(d, Dg, alg, exg, eyg, x, i, acc, arg, exrg, eyrg);
+        cell_apply<TX, TM, G>(d, Dg, alg, exg, eyg, x, i, acc, arg, exrg, eyrg, bdgg);
         if (mode == 0) {
 #pragma unroll
             for (int q = 0; q < NX; ++q) y[q * T + i] = TY(acc[q]);
@@ -301,7 +308,7 @@ __device__ __noinline__ void resid64_cell(const DeviceMesh &d, const double *__r
                                           const double *__restrict__ b, int64_t i, int v, int e, float *out)
 {
     double acc[NX];
-    cell_apply<double, double, G>(d, d.D, d.alpha, d.ex, d.ey, x, i, acc, d.alr, d.exr, d.eyr);
+    cell_apply<double, double, G>(d, d.D, d.alpha, d.ex, d.ey, x, i, acc, d.alr, d.exr, d.eyr, d.bdg);
     for (int l = 0; l < ND; ++l) out[l] = float((b[(v * ND + l) * d.T + i] - acc[v * ND + l]) * pow2(-e));
 }
 
@@ -324,7 +331,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_resid_df(DeviceMesh d, const floa
                                                        float *__restrict__ y, const double *__restrict__ b,
                                                        double *__restrict__ part, int pstride,
                                                        const int32_t *__restrict__ sexp,
-                                                       const float *__restrict__ SR2 = nullptr)
+                                                       const float *__restrict__ SR2 = nullptr,
+                                                       const float *__restrict__ SB2 = nullptr)
 {
     __shared__ double sh[kBlock / 32];
     const int64_t T = d.T;
@@ -343,7 +351,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_resid_df(DeviceMesh d, const floa
         // every load first (the arithmetic below is a long dependent chain)
         constexpr int NG = G ? ND : 2;                    // neighbour unknowns used
         double xv[ND], gv[3][NG], bv[ND];
-        float dp[30], op[18], rp[G ? 18 : 1];
+        float dp[30], op[18], rp[G ? 18 : 1], bp[G ? 6 : 1];
 #pragma unroll
         for (int l = 0; l < ND; ++l) xv[l] = x[(v * ND + l) * T + i];
 #pragma unroll
@@ -354,9 +362,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_resid_df(DeviceMesh d, const floa
         for (int q = 0; q < 30; ++q) dp[q] = D2[q * T + i];
 #pragma unroll
         for (int q = 0; q < 18; ++q) op[q] = S2[q * T + i];
-        if (G)
+        if (G) {
 #pragma unroll
             for (int q = 0; q < 18; ++q) rp[q] = SR2[q * T + i];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) bp[q] = SB2[q * T + i];
+        }
 #pragma unroll
         for (int l = 0; l < ND; ++l) bv[l] = b[(v * ND + l) * T + i];
         bool ok = true;
@@ -395,6 +406,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_resid_df(DeviceMesh d, const floa
                 df_mac(rp[q], rp[9 + q], gh[s][1], gl[s][1], ah[1], al[1]);
                 df_mac(rp[q + 1], rp[10 + q], gh[s][NG > 3 ? 3 : 0], gl[s][NG > 3 ? 3 : 0], ah[1], al[1]);
                 df_mac(rp[q + 2], rp[11 + q], gh[s][NG > 4 ? 4 : 0], gl[s][NG > 4 ? 4 : 0], ah[1], al[1]);
+                // diagonal coupling of the unknowns 3..5 (second-derivative equations)
+#pragma unroll
+                for (int l = 2; l < ND; ++l)
+                    df_mac(bp[s], bp[3 + s], gh[s][NG > l ? l : 0], gl[s][NG > l ? l : 0], ah[l], al[l]);
             }
         }
 #pragma unroll
@@ -437,7 +452,7 @@ __global__ void k_ilu_fwd(DeviceMesh d, const TP *__restrict__ Pg, const TP *__r
                           const TP *__restrict__ exg, const TP *__restrict__ eyg, const int32_t *__restrict__ rows,
                           int64_t nrows, const TR *r, const TZ *zin, TZ *zout, int use_nb, TZ *__restrict__ rcopy,
                           const TP *__restrict__ arg = nullptr, const TP *__restrict__ exrg = nullptr,
-                          const TP *__restrict__ eyrg = nullptr)
+                          const TP *__restrict__ eyrg = nullptr, const TP *__restrict__ bdgg = nullptr)
 {
     const int64_t T = d.T;
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -463,12 +478,15 @@ __global__ void k_ilu_fwd(DeviceMesh d, const TP *__restrict__ Pg, const TP *__r
                 oacc(sa, sax, say, TM(zin[(v * ND + 0) * T + j]), TM(zin[(v * ND + 1) * T + j]), y + v * ND);
             if (G) {
                 const TM sr = TM(arg[s * T + i]), srx = sr * TM(exrg[s * T + i]), sry = sr * TM(eyrg[s * T + i]);
+                const TM sb = TM(bdgg[s * T + i]);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     TM zj[ND];
 #pragma unroll
                     for (int l = 0; l < ND; ++l) zj[l] = TM(zin[(v * ND + l) * T + j]);
                     racc(sr, srx, sry, zj, y + v * ND);
+#pragma unroll
+                    for (int l = 2; l < ND; ++l) y[v * ND + l] = fma(sb, zj[l], y[v * ND + l]);
                 }
             }
         }
@@ -492,7 +510,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(TM) == 4 ? 3 : 1)
     k_ilu_bwd(DeviceMesh d, const TP *__restrict__ Pg, const TP *__restrict__ alg, const TP *__restrict__ exg,
               const TP *__restrict__ eyg, const int32_t *__restrict__ rows, int64_t nrows, const TZ *z, const TZ *xin,
               TZ *xout, const TP *__restrict__ arg = nullptr, const TP *__restrict__ exrg = nullptr,
-              const TP *__restrict__ eyrg = nullptr)
+              const TP *__restrict__ eyrg = nullptr, const TP *__restrict__ bdgg = nullptr)
 {
     const int64_t T = d.T;
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -517,12 +535,15 @@ __global__ void __launch_bounds__(kBlock, sizeof(TM) == 4 ? 3 : 1)
             oacc(sa, sax, say, TM(xin[(v * ND + 0) * T + j]), TM(xin[(v * ND + 1) * T + j]), y + v * ND);
         if (G) {
             const TM sr = TM(arg[s * T + i]), srx = sr * TM(exrg[s * T + i]), sry = sr * TM(eyrg[s * T + i]);
+            const TM sb = TM(bdgg[s * T + i]);
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 TM xj[ND];
 #pragma unroll
                 for (int l = 0; l < ND; ++l) xj[l] = TM(xin[(v * ND + l) * T + j]);
                 racc(sr, srx, sry, xj, y + v * ND);
+#pragma unroll
+                for (int l = 2; l < ND; ++l) y[v * ND + l] = fma(sb, xj[l], y[v * ND + l]);
             }
         }
     }
@@ -963,7 +984,7 @@ inline unsigned nblocks(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock
 // kernels (all NULL for the per-cell equations).
 template <typename TP>
 struct RevSlots {
-    const TP *a = nullptr, *x = nullptr, *y = nullptr;
+    const TP *a = nullptr, *x = nullptr, *y = nullptr, *b = nullptr;
 };
 
 // dst = M^{-1} src (block ILU(0) on the RCM order).  TZ, TM: storage and
@@ -980,7 +1001,7 @@ gks_status precond_t(gks_mesh *m, const TP *Pg, const TP *alg, const TP *exg, co
         using TRx = std::remove_cv_t<std::remove_pointer_t<decltype(r)>>;
         if (rev.a)
             k_ilu_fwd<TRx, TZ, TM, TP, true><<<nblocks(n), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, rows, n, r, zin, zout,
-                                                                          use_nb, rc, rev.a, rev.x, rev.y);
+                                                                          use_nb, rc, rev.a, rev.x, rev.y, rev.b);
         else
             k_ilu_fwd<TRx, TZ, TM, TP, false><<<nblocks(n), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, rows, n, r, zin,
                                                                            zout, use_nb, rc);
@@ -989,7 +1010,7 @@ gks_status precond_t(gks_mesh *m, const TP *Pg, const TP *alg, const TP *exg, co
     auto bwd = [&](int64_t n, const int32_t *rows, const TZ *z, const TZ *xin, TZ *xout) {
         if (rev.a)
             k_ilu_bwd<TZ, TM, TP, true><<<nblocks(n), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, rows, n, z, xin, xout,
-                                                                     rev.a, rev.x, rev.y);
+                                                                     rev.a, rev.x, rev.y, rev.b);
         else
             k_ilu_bwd<TZ, TM, TP, false><<<nblocks(n), kBlock, 0, s>>>(d, Pg, alg, exg, eyg, rows, n, z, xin, xout);
         note_launch();
@@ -1036,7 +1057,7 @@ gks_status precond(gks_mesh *m, const TR *src, double *dst, cudaStream_t s)
 {
     DeviceMesh &d = m->d;
     return precond_t<TR, double, double>(m, d.P, d.alpha, d.ex, d.ey, src, dst, m->wk.t2, m->wk.t3, nullptr, s,
-                                         {d.alr, d.exr, d.eyr});
+                                         {d.alr, d.exr, d.eyr, d.bdg});
 }
 
 template <typename TR>
@@ -1045,9 +1066,9 @@ gks_status precond32(gks_mesh *m, const TR *src, float *dst, cudaStream_t s)
     DeviceMesh &d = m->d;
     if (d.P16)   // FP16 factors (ilu_fp16), FP32 arithmetic
         return precond_t<TR, float, float, __half>(m, d.P16, d.alpha16, d.ex16, d.ey16, src, dst, m->wk.t2_32,
-                                                   m->wk.t3_32, m->wk.r32, s, {d.alr16, d.exr16, d.eyr16});
+                                                   m->wk.t3_32, m->wk.r32, s, {d.alr16, d.exr16, d.eyr16, d.bdg16});
     return precond_t<TR, float, float>(m, d.P32, d.alpha32, d.ex32, d.ey32, src, dst, m->wk.t2_32, m->wk.t3_32,
-                                       m->wk.r32, s, {d.alr32, d.exr32, d.eyr32});
+                                       m->wk.r32, s, {d.alr32, d.exr32, d.eyr32, d.bdg32});
 }
 
 // Any active / any running system into the pinned host flags (no synchronisation).
@@ -1335,7 +1356,7 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
     auto spmv64 = [&](cudaStream_t q, const double *xs, TB *y, int mode, const double *bb, const int32_t *se) {
         if (d.alr)
             k_spmv<double, double, TB, true><<<nb, kBlock, 0, q>>>(d, d.D, d.alpha, d.ex, d.ey, xs, y, mode, bb,
-                                                                   k.part, ps, se, d.alr, d.exr, d.eyr);
+                                                                   k.part, ps, se, d.alr, d.exr, d.eyr, d.bdg);
         else
             k_spmv<double, double, TB, false><<<nb, kBlock, 0, q>>>(d, d.D, d.alpha, d.ex, d.ey, xs, y, mode, bb,
                                                                     k.part, ps, se);
@@ -1344,7 +1365,7 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
         if (d.alr32)
             k_spmv<float, float, TB, true><<<nb, kBlock, 0, q>>>(d, d.D32, d.alpha32, d.ex32, d.ey32, xs, y, 0,
                                                                  nullptr, nullptr, 0, nullptr, d.alr32, d.exr32,
-                                                                 d.eyr32);
+                                                                 d.eyr32, d.bdg32);
         else
             k_spmv<float, float, TB, false><<<nb, kBlock, 0, q>>>(d, d.D32, d.alpha32, d.ex32, d.ey32, xs, y, 0,
                                                                   nullptr, nullptr, 0);
@@ -1353,7 +1374,7 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
         if (std::is_same<TB, float>::value && d.D2) {
             if (d.SR2)
                 k_resid_df<true><<<4 * nb, kBlock, 0, q>>>(d, d.D2, d.S2, k.x, reinterpret_cast<float *>(V), k.b,
-                                                           k.part, ps, sxn, d.SR2);
+                                                           k.part, ps, sxn, d.SR2, d.SB2);
             else
                 k_resid_df<false><<<4 * nb, kBlock, 0, q>>>(d, d.D2, d.S2, k.x, reinterpret_cast<float *>(V), k.b,
                                                             k.part, ps, sxn);

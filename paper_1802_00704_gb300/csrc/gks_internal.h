@@ -66,16 +66,19 @@ struct DeviceMesh {
     // global normal equations (cls_global, Eq. (33)): the reverse slot's coefficients,
     // alpha_ji and i's centroid in j's frame (0 when k_j = 1); NULL otherwise
     double *alr = nullptr, *exr = nullptr, *eyr = nullptr;  // [3][T]
+    // second-derivative equations (cls_M = 2): beta of the diagonal coupling of the
+    // unknowns 3..5 with the neighbour's (plus the reverse one in the global system)
+    double *bdg = nullptr;           // [3][T]; with alr.. allocated for either option (zeros if unused)
     double *a0 = nullptr;            // [3][5][T] weighted row 0 of A_ij (right-hand side)
     double *D = nullptr;             // [15][T] symmetric diagonal block, upper triangle row-major
     double *P = nullptr;             // [25][T] inverse of the ILU(0) diagonal block, row-major
     // FP32 copies of the operator and factors (mixed precision)
     float *D32 = nullptr, *P32 = nullptr, *alpha32 = nullptr, *ex32 = nullptr, *ey32 = nullptr;
-    float *alr32 = nullptr, *exr32 = nullptr, *eyr32 = nullptr;
+    float *alr32 = nullptr, *exr32 = nullptr, *eyr32 = nullptr, *bdg32 = nullptr;
     // FP16 copies of the ILU(0) factors for the FP32 preconditioner (ilu_fp16;
     // NULL when not asked for or a value is outside FP16's range)
     __half *P16 = nullptr, *alpha16 = nullptr, *ex16 = nullptr, *ey16 = nullptr;
-    __half *alr16 = nullptr, *exr16 = nullptr, *eyr16 = nullptr;
+    __half *alr16 = nullptr, *exr16 = nullptr, *eyr16 = nullptr, *bdg16 = nullptr;
     float *ih32 = nullptr;           // [T] 1 / h_i (mixed flux)
     // the operator as FP32 pairs hi + lo for the double-FP32 refinement residual
     // (mixed mode with an FP32 basis; NULL when a value is outside the pair range)
@@ -83,6 +86,7 @@ struct DeviceMesh {
     float *S2 = nullptr;             // [18][T] sa, sa dx, sa dy per neighbour slot (sa = -alpha, 0
                                      //         without neighbour), then their low parts
     float *SR2 = nullptr;            // [18][T] the same for the reverse slots (global normal equations)
+    float *SB2 = nullptr;            // [6][T] -beta per slot, then the low parts (second-derivative equations)
     double *ox = nullptr, *oy = nullptr;  // [3][T] neighbour centroid in i's scaled frame (limiter)
     int32_t *kord = nullptr;         // [T] reconstruction order k_i of Eq. (28) (limiter)
     int32_t *cf = nullptr;           // [3][T] (face << 1) | side, -1 unused

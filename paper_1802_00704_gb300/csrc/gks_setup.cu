@@ -207,13 +207,13 @@ struct HostCase {
     int32_t nlo = 0, nup = 0;
     std::vector<int32_t> perm, nb, cf, fl, fr, ftag, fperm, lev_lo, lev_up, kord;
     std::vector<double> area, iarea, h, mxx, mxy, myy, inrad, alpha, ex, ey, ox, oy, a0, D, P;
-    std::vector<double> alr, exr, eyr;   // global normal equations only (empty otherwise)
+    std::vector<double> alr, exr, eyr, bdg;   // extended stencil only (empty otherwise)
     std::vector<double> fnx, fny, flen, gl, gr, bc;
 };
 
 // Geometry, boundary order reduction (Eq. (28)), RCM order, CLS blocks
 // (Eq. (29)), block ILU(0) factors and levels of one case.
-gks_status build_case(const CaseIn &in, double w, int second_order, int cls_global, HostCase &hc)
+gks_status build_case(const CaseIn &in, double w, int second_order, int cls_global, int cls_M, HostCase &hc)
 {
     const double *nodes = in.nodes, *face_shift = in.face_shift, *bc_state = in.bc_state;
     const int32_t *tris = in.tris, *faces = in.faces;
@@ -307,8 +307,9 @@ gks_status build_case(const CaseIn &in, double w, int second_order, int cls_glob
     // ---- CLS blocks in internal order
     std::vector<int32_t> h_nb(3 * T, -1), h_cf(3 * T, -1);
     std::vector<double> h_alpha(3 * T, 0.0), h_ex(3 * T, 0.0), h_ey(3 * T, 0.0), h_a0(15 * T, 0.0);
-    // global normal equations: the reverse slot's coefficients (alpha_ji, i's centroid in j's frame)
-    std::vector<double> h_alr(3 * T, 0.0), h_exr(3 * T, 0.0), h_eyr(3 * T, 0.0);
+    // extended stencil: global normal equations (the reverse slot's coefficients alpha_ji and i's
+    // centroid in j's frame) and second-derivative equations (the diagonal coupling beta on unknowns 3..5)
+    std::vector<double> h_alr(3 * T, 0.0), h_exr(3 * T, 0.0), h_eyr(3 * T, 0.0), h_bdg(3 * T, 0.0);
     std::vector<double> h_ox(3 * T, 0.0), h_oy(3 * T, 0.0);
     std::vector<int32_t> h_kord(T, 2);
     std::vector<double> h_D(15 * T, 0.0), h_Dfull(25 * T, 0.0);
@@ -345,11 +346,19 @@ gks_status build_case(const CaseIn &in, double w, int second_order, int cls_glob
             double s2 = 1.0 / (c.h * c.h);
             double a0[5] = {dx, dy, 0.5 * (dx * dx + d.sxx * s2 - h_mxx[i]), dx * dy + d.sxy * s2 - h_mxy[i],
                             0.5 * (dy * dy + d.syy * s2 - h_myy[i])};
-            double r1[5] = {w, 0.0, w * dx, w * dy, 0.0};
-            double r2[5] = {0.0, w, 0.0, w * dx, w * dy};
+            // derivative rows of Eq. (29) up to order M: p = 1 (w (1, 0, dx, dy, 0), w (0, 1, 0, dx, dy));
+            // p = 2 (w^2 e3, e4, e5 for a quadratic cell; the B rows (w h_i / h_j)^2 e3.. of a quadratic j)
+            const double f1 = cls_M >= 1 ? 1.0 : 0.0;
+            double r1[5] = {f1 * w, 0.0, f1 * w * dx, f1 * w * dy, 0.0};
+            double r2[5] = {0.0, f1 * w, 0.0, f1 * w * dx, f1 * w * dy};
             for (int a = 0; a < ni; ++a)
                 for (int b = 0; b < ni; ++b) D[5 * a + b] += a0[a] * a0[b] + r1[a] * r1[b] + r2[a] * r2[b];
-            if (cls_global) {
+            const double w4 = w * w * w * w;
+            if (cls_M == 2 && c.k == 2) {
+                for (int a = 2; a < 5; ++a) D[5 * a + a] += w4;
+                if (d.k == 2) h_bdg[slot * T + i] = w4 * (c.h / d.h) * (c.h / d.h);
+            }
+            if (cls_global && cls_M >= 1) {
                 // j's equations about i (Eq. (33)): their B rows (w h_j / h_i) e1, e2 act on u_i
                 const double q = w * d.h / c.h;
                 D[0] += q * q;
@@ -357,10 +366,16 @@ gks_status build_case(const CaseIn &in, double w, int second_order, int cls_glob
                 h_alr[slot * T + i] = w * w * d.h / c.h;
                 h_exr[slot * T + i] = d.k == 2 ? (c.cx - ox - d.cx) / d.h : 0.0;
                 h_eyr[slot * T + i] = d.k == 2 ? (c.cy - oy - d.cy) / d.h : 0.0;
+                if (cls_M == 2 && c.k == 2) {
+                    // and their second-derivative B rows (w h_j / h_i)^2 e3.. on a quadratic i
+                    const double q2 = q * q;
+                    for (int a = 2; a < 5; ++a) D[5 * a + a] += q2 * q2;
+                    if (d.k == 2) h_bdg[slot * T + i] += w4 * (d.h / c.h) * (d.h / c.h);
+                }
             }
             int32_t j = inv[cj];
             h_nb[slot * T + i] = j;
-            h_alpha[slot * T + i] = w * w * c.h / d.h;
+            h_alpha[slot * T + i] = cls_M >= 1 ? w * w * c.h / d.h : 0.0;
             h_ex[slot * T + i] = c.k == 2 ? dx : 0.0;
             h_ey[slot * T + i] = c.k == 2 ? dy : 0.0;
             h_ox[slot * T + i] = dx;
@@ -391,11 +406,13 @@ gks_status build_case(const CaseIn &in, double w, int second_order, int cls_glob
             double Oik[25];
             oblock(h_alpha[s * T + i], h_ex[s * T + i], h_ey[s * T + i], Oik);
             if (cls_global) oblock_rev(h_alr[s * T + i], h_exr[s * T + i], h_eyr[s * T + i], Oik);
+            for (int a = 2; a < 5; ++a) Oik[5 * a + a] += h_bdg[s * T + i];
             for (int s2 = 0; s2 < 3; ++s2) {
                 if (h_nb[s2 * T + k] != (int32_t)i) continue;
                 double Oki[25], tmp[25];
                 oblock(h_alpha[s2 * T + k], h_ex[s2 * T + k], h_ey[s2 * T + k], Oki);
                 if (cls_global) oblock_rev(h_alr[s2 * T + k], h_exr[s2 * T + k], h_eyr[s2 * T + k], Oki);
+                for (int a = 2; a < 5; ++a) Oki[5 * a + a] += h_bdg[s2 * T + k];
                 const double *Pk = &Pinv[25 * k];
                 for (int a = 0; a < 5; ++a)
                     for (int b = 0; b < 5; ++b) {
@@ -520,10 +537,11 @@ gks_status build_case(const CaseIn &in, double w, int second_order, int cls_glob
     hc.myy = std::move(h_myy);
     hc.inrad = std::move(h_inrad);
     hc.alpha = std::move(h_alpha);
-    if (cls_global) {
+    if (cls_global || cls_M == 2) {
         hc.alr = std::move(h_alr);
         hc.exr = std::move(h_exr);
         hc.eyr = std::move(h_eyr);
+        hc.bdg = std::move(h_bdg);
     }
     hc.ex = std::move(h_ex);
     hc.ey = std::move(h_ey);
@@ -572,7 +590,7 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
         unsigned nt = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), (unsigned)n_cases));
         auto work = [&]() {
             for (int32_t c; (c = next.fetch_add(1)) < n_cases;) {
-                st[c] = build_case(cases[c], cfg.cls_w, cfg.second_order, cfg.cls_global, hcs[c]);
+                st[c] = build_case(cases[c], cfg.cls_w, cfg.second_order, cfg.cls_global, cfg.cls_M, hcs[c]);
                 if (st[c] != GKS_OK) {
                     msg[c] = last_error();
                     int expect = -1;
@@ -611,7 +629,10 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
     std::vector<double> h_inrad(T, std::numeric_limits<double>::infinity());
     std::vector<double> h_alpha(3 * T, 0.0), h_ex(3 * T, 0.0), h_ey(3 * T, 0.0), h_a0(15 * T, 0.0);
     std::vector<double> h_ox(3 * T, 0.0), h_oy(3 * T, 0.0);
-    std::vector<double> h_alr(cfg.cls_global ? 3 * T : 0, 0.0), h_exr(h_alr.size(), 0.0), h_eyr(h_alr.size(), 0.0);
+    // extended stencil (global normal equations or second-derivative equations)
+    const bool ext = cfg.cls_global || cfg.cls_M == 2;
+    std::vector<double> h_alr(ext ? 3 * T : 0, 0.0), h_exr(h_alr.size(), 0.0), h_eyr(h_alr.size(), 0.0);
+    std::vector<double> h_bdg(h_alr.size(), 0.0);
     std::vector<int32_t> h_kord(T, 2);
     std::vector<double> h_D(15 * T, 0.0), h_P(25 * T, 0.0);
     std::vector<int32_t> h_fl(F), h_fr(F), h_ftag(F), h_fperm(F), h_face_case(F);
@@ -644,8 +665,9 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
         place(hc.inrad, Tc, 1, h_inrad, T, o);
         place(hc.alpha, Tc, 3, h_alpha, T, o); place(hc.ex, Tc, 3, h_ex, T, o); place(hc.ey, Tc, 3, h_ey, T, o);
         place(hc.ox, Tc, 3, h_ox, T, o); place(hc.oy, Tc, 3, h_oy, T, o); place(hc.kord, Tc, 1, h_kord, T, o);
-        if (cfg.cls_global) {
+        if (ext) {
             place(hc.alr, Tc, 3, h_alr, T, o); place(hc.exr, Tc, 3, h_exr, T, o); place(hc.eyr, Tc, 3, h_eyr, T, o);
+            place(hc.bdg, Tc, 3, h_bdg, T, o);
         }
         place(hc.a0, Tc, 15, h_a0, T, o); place(hc.D, Tc, 15, h_D, T, o); place(hc.P, Tc, 25, h_P, T, o);
         for (int64_t f = 0; f < Fc; ++f) {
@@ -701,8 +723,8 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
     UP(fl, h_fl); UP(fr, h_fr); UP(ftag, h_ftag); UP(fperm, h_fperm); UP(fnx, h_fnx); UP(fny, h_fny);
     UP(flen, h_flen); UP(gl, h_gl); UP(gr, h_gr); UP(bc, h_bc);
     UP(blk_case, h_blk_case); UP(case_blk, h_case_blk); UP(face_case, h_face_case);
-    if (cfg.cls_global) {
-        UP(alr, h_alr); UP(exr, h_exr); UP(eyr, h_eyr);
+    if (ext) {
+        UP(alr, h_alr); UP(exr, h_exr); UP(eyr, h_eyr); UP(bdg, h_bdg);
     }
 
     if (cfg.limiter) {
@@ -711,8 +733,8 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
     if (cfg.precision == GKS_MIXED) {
         auto f32 = [](const std::vector<double> &v) { return std::vector<float>(v.begin(), v.end()); };
         UP(D32, f32(h_D)); UP(P32, f32(h_P)); UP(alpha32, f32(h_alpha)); UP(ex32, f32(h_ex)); UP(ey32, f32(h_ey));
-        if (cfg.cls_global) {
-            UP(alr32, f32(h_alr)); UP(exr32, f32(h_exr)); UP(eyr32, f32(h_eyr));
+        if (ext) {
+            UP(alr32, f32(h_alr)); UP(exr32, f32(h_exr)); UP(eyr32, f32(h_eyr)); UP(bdg32, f32(h_bdg));
         }
         if (cfg.ilu_fp16) {
             // FP16 copies of the ILU(0) factors if every value fits FP16's normal range
@@ -727,11 +749,11 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
                 return o;
             };
             std::vector<__half> p16 = f16(h_P), a16 = f16(h_alpha), x16 = f16(h_ex), y16 = f16(h_ey);
-            std::vector<__half> ar16 = f16(h_alr), xr16 = f16(h_exr), yr16 = f16(h_eyr);
+            std::vector<__half> ar16 = f16(h_alr), xr16 = f16(h_exr), yr16 = f16(h_eyr), b16 = f16(h_bdg);
             if (fits) {
                 UP(P16, p16); UP(alpha16, a16); UP(ex16, x16); UP(ey16, y16);
-                if (cfg.cls_global) {
-                    UP(alr16, ar16); UP(exr16, xr16); UP(eyr16, yr16);
+                if (ext) {
+                    UP(alr16, ar16); UP(exr16, xr16); UP(eyr16, yr16); UP(bdg16, b16);
                 }
             }
         }
@@ -748,7 +770,7 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
                 hi = float(v);
                 lo = float(v - double(hi));
             };
-            std::vector<float> h_D2(30 * T), h_S2(18 * T), h_SR2(cfg.cls_global ? 18 * T : 0);
+            std::vector<float> h_D2(30 * T), h_S2(18 * T), h_SR2(ext ? 18 * T : 0), h_SB2(ext ? 6 * T : 0);
             for (int64_t i = 0; i < T; ++i) {
                 for (int q = 0; q < 15; ++q) pair(h_D[q * T + i], h_D2[q * T + i], h_D2[(15 + q) * T + i]);
                 for (int s = 0; s < 3; ++s) {
@@ -756,17 +778,20 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
                     const double o[3] = {sa, sa * h_ex[s * T + i], sa * h_ey[s * T + i]};
                     for (int q = 0; q < 3; ++q)
                         pair(o[q], h_S2[(3 * s + q) * T + i], h_S2[(9 + 3 * s + q) * T + i]);
-                    if (cfg.cls_global) {
+                    if (ext) {
                         const double sr = h_nb[s * T + i] >= 0 ? -h_alr[s * T + i] : 0.0;
                         const double r[3] = {sr, sr * h_exr[s * T + i], sr * h_eyr[s * T + i]};
                         for (int q = 0; q < 3; ++q)
                             pair(r[q], h_SR2[(3 * s + q) * T + i], h_SR2[(9 + 3 * s + q) * T + i]);
+                        pair(h_nb[s * T + i] >= 0 ? -h_bdg[s * T + i] : 0.0, h_SB2[s * T + i], h_SB2[(3 + s) * T + i]);
                     }
                 }
             }
             if (in_range) {
                 UP(D2, h_D2); UP(S2, h_S2);
-                if (cfg.cls_global) UP(SR2, h_SR2);
+                if (ext) {
+                    UP(SR2, h_SR2); UP(SB2, h_SB2);
+                }
             }
         }
     }

@@ -45,7 +45,7 @@ class Config(C.Structure):
                 ("basis_fp32", C.c_int32), ("warm_extrap", C.c_int32), ("second_order", C.c_int32),
                 ("no_graphs", C.c_int32), ("limit_char", C.c_int32),
                 ("inner_rtol", C.c_double), ("prandtl", C.c_double), ("slope0_mode", C.c_int32),
-                ("ilu_fp16", C.c_int32), ("cls_global", C.c_int32)]
+                ("ilu_fp16", C.c_int32), ("cls_global", C.c_int32), ("cls_M", C.c_int32)]
 
 
 class SolveInfo(C.Structure):

@@ -39,13 +39,14 @@ def test_config_defaults(lib):
     assert c.gamma == 1.4 and c.cfl == 0.3 and c.cls_w == 0.3 and c.gmres_m == 30
     assert c.gmres_rtol == 1e-12 and c.precision == gks.FP64 and c.limiter == 0 and c.basis_fp32 == 0
     assert c.warm_extrap == 0 and c.second_order == 0 and c.no_graphs == 0
+    assert c.cls_M == 1 and c.cls_global == 0 and c.slope0_mode == 0 and c.ilu_fp16 == 0
     assert c.limit_char == 0 and c.inner_rtol == 1e-6
     assert c.prandtl == 1.0
     # the ctypes mirror has the size of the C struct: 4 doubles, 2 ints, 1 double, 10 ints, 2 doubles
-    assert C.sizeof(gks.Config) == 4 * 8 + 2 * 4 + 8 + 10 * 4 + 2 * 8 + 2 * 4 + 8   # cls_global + padding
+    assert C.sizeof(gks.Config) == 4 * 8 + 2 * 4 + 8 + 10 * 4 + 2 * 8 + 4 * 4
     assert gks.Config.inner_rtol.offset == 88 and gks.Config.prandtl.offset == 96
     assert gks.Config.slope0_mode.offset == 104 and gks.Config.ilu_fp16.offset == 108
-    assert gks.Config.cls_global.offset == 112
+    assert gks.Config.cls_global.offset == 112 and gks.Config.cls_M.offset == 116
 
 
 def test_binding_refuses_cpu_tensors(lib):

@@ -318,3 +318,54 @@ def test_global_cls_steps_match_oracle(O, G, name):
         assert om.step(wo, dt).status == 0
         assert m.step(w, dt)["status"] == 0
     assert np.all(rel_max(host(w), wo, axis=1) <= 1e-10), rel_max(host(w), wo, axis=1)
+
+
+# --------------------------------------------------------------------------- derivative order of the CLS equations
+
+@pytest.mark.parametrize("name", ["advection20", "shock_vortex40x20", "walled13x9"])
+@pytest.mark.parametrize("glob", [0, 1])
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_second_derivative_equations_match_oracle(O, G, name, glob, mode):
+    """cls_M = 2 (second-derivative equations of Eq. (29) for quadratic cells),
+    per cell and global, against the oracle's assembly: coefficients within 1e-9
+    relative max in FP64 and in mixed precision."""
+    c = CASES[name]()
+    om = O.OracleMesh(c.mesh, cls_M=2, cls_global=glob)
+    ref, _, rr, bad = om.cls_solve(c.w0)
+    assert bad == 0
+    kw = dict(cls_M=2, cls_global=glob)
+    if mode == "mixed":
+        kw.update(precision=G.MIXED, basis_fp32=1, ilu_fp16=1)
+    m = G.GksMesh(c.mesh, **kw)
+    coef, info = m.cls_reconstruct(dev(c.w0))
+    assert info["converged"] == 1 and max(info["relres"]) <= 1e-12
+    got = host(coef)
+    for v in range(4):
+        if np.max(np.abs(ref[v])) == 0.0:
+            assert np.all(got[v] == 0.0)
+        else:
+            assert rel_max(got[v], ref[v]) <= 1e-9, (v, rel_max(got[v], ref[v]))
+
+
+def test_value_equations_second_order_variant_matches_oracle(O, G):
+    """cls_M = 0 with the second-order variant (values only, k_i = 1) on a
+    y-periodic strip: coefficients and five steps match the oracle; M = 0 with
+    quadratic cells is refused."""
+    c = CASES["weak_riemann60x4"]()
+    om = O.OracleMesh(c.mesh, cls_M=0, second_order=1)
+    ref, _, _, bad = om.cls_solve(c.w0)
+    assert bad == 0
+    m = G.GksMesh(c.mesh, cls_M=0, second_order=1)
+    coef, info = m.cls_reconstruct(dev(c.w0))
+    got = host(coef)
+    for v in range(4):
+        if np.max(np.abs(ref[v])) > 0:
+            assert rel_max(got[v], ref[v]) <= 1e-9
+    wo, w = c.w0.copy(), dev(c.w0)
+    for _ in range(5):
+        dt = om.cfl_dt(wo)
+        assert om.step(wo, dt).status == 0
+        assert m.step(w, dt)["status"] == 0
+    assert np.all(rel_max(host(w), wo, axis=1) <= 1e-10)
+    with pytest.raises(G.GksError):
+        G.GksMesh(c.mesh, cls_M=0)
