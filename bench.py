@@ -214,7 +214,7 @@ def oracle_sample(steps: int, warmup: int = 0):
 
 
 def class_bytes(cls: str, prof: dict, T: int, F: int, steps: int, sweeps: int, exact: bool, mixed: bool,
-                basis32: bool, ilu16: bool = False) -> float:
+                basis32: bool, ilu16: bool = False, sweeps_bwd: int = -1) -> float:
     """Algorithmic DRAM bytes moved by one kernel class over the timed region,
     from the solver's work counters (Arnoldi iterations n, sum of j + 1 over
     them, preconditioner applications).  Per cell: operator = diagonal block 15
@@ -246,7 +246,8 @@ def class_bytes(cls: str, prof: dict, T: int, F: int, steps: int, sweeps: int, e
         first = 20 * sB + sP * 25 + 20 * sZ
         fwd = 20 * sB + 8 * sZ + sP * (25 + 9) + 12 + 20 * sZ
         bwd = 20 * sZ + 8 * sZ + sP * (25 + 9) + 12 + 20 * sZ
-        return T * (first + sweeps * (fwd + bwd)) * pc
+        nbwd = sweeps if sweeps_bwd < 0 else sweeps_bwd
+        return T * (first + sweeps * fwd + nbwd * bwd) * pc
     if cls == "update":                 # w in/out, 1/|Omega|, 3 face slots; each face flux once
         return (T * (8 * 8 + 8 + 12) + F * 4 * 8) * steps
     if cls == "resid":                  # FP64 b - K x: x (own + neighbour values), operator, b, r (basis)
@@ -298,7 +299,8 @@ def timed_leg(args, case, precision: str, world: int, dev, sample_clocks: bool):
     prof = m.profile_end()
     return {"mesh": m, "w": w, "info": info, "prof": prof, "launches": launches, "clocks": clocks, "ms": ms,
             "stats": m.stats(), "tune": tune,
-            "knobs": {"ilu_sweeps": m.cfg.ilu_sweeps, "warm_extrap": m.cfg.warm_extrap,
+            "knobs": {"ilu_sweeps": m.cfg.ilu_sweeps, "ilu_sweeps_bwd": m.cfg.ilu_sweeps_bwd,
+                      "warm_extrap": m.cfg.warm_extrap,
                       "inner_rtol": m.cfg.inner_rtol}}
 
 
@@ -346,7 +348,7 @@ def run_gks(args, world, rank, local):
         ent = {"ms": round(ms_c, 3), "launch_groups": prof["n"][q]}
         if nm not in ("flux", "ctl") and ms_c > 0:
             by = class_bytes(nm, prof, T, F, args.steps, main["knobs"]["ilu_sweeps"], exact, mixed, basis32,
-                             mixed and args.ilu16 == "on")
+                             mixed and args.ilu16 == "on", main["knobs"]["ilu_sweeps_bwd"])
             gbs = by / (ms_c / 1e3) / 1e9
             ent.update({"bytes": by, "gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 3)})
         classes[nm] = ent
@@ -495,7 +497,8 @@ def run_batch(args, world, rank, local):
         w_host.copy_(w_dev, non_blocking=True)
     torch.cuda.synchronize()
     e2e_value = world * T * args.steps / allmax(world, time.perf_counter() - t0)
-    knobs = {"ilu_sweeps": b.cfg.ilu_sweeps, "warm_extrap": b.cfg.warm_extrap, "inner_rtol": b.cfg.inner_rtol}
+    knobs = {"ilu_sweeps": b.cfg.ilu_sweeps, "ilu_sweeps_bwd": b.cfg.ilu_sweeps_bwd,
+             "warm_extrap": b.cfg.warm_extrap, "inner_rtol": b.cfg.inner_rtol}
     names = PROF_NAMES
     hbm_peak = measured_peaks().get("hbm_gbs") or HBM_FALLBACK_GBS
     classes = {}
@@ -503,7 +506,7 @@ def run_batch(args, world, rank, local):
         ent = {"ms": round(prof["ms"][q], 3), "launch_groups": prof["n"][q]}
         if nm not in ("flux", "ctl") and prof["ms"][q] > 0:
             by = class_bytes(nm, prof, T, F, args.steps, knobs["ilu_sweeps"], False, mixed,
-                             mixed and args.basis == "fp32", mixed and args.ilu16 == "on")
+                             mixed and args.basis == "fp32", mixed and args.ilu16 == "on", knobs["ilu_sweeps_bwd"])
             gbs = by / (prof["ms"][q] / 1e3) / 1e9
             ent.update({"bytes": by, "gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 3)})
         classes[nm] = ent

@@ -162,6 +162,9 @@ typedef struct gks_config {
                               2 also the second derivatives (w h_i)^2 of quadratic
                               cells; 0 the values only, which needs the second-order
                               variant (k_i = 1) and two face neighbours per cell       */
+    int32_t ilu_sweeps_bwd; /* GKS_PC_ILU_SWEEP: sweeps of the backward (upper) relation;
+                              -1 (default) the same as ilu_sweeps, 0..8 otherwise; a
+                              fixed preconditioner either way                          */
 } gks_config;
 
 typedef struct gks_mesh gks_mesh;
@@ -370,6 +373,7 @@ typedef struct gks_tune_result {
     double ms_per_step_before;    /* the configuration the handle had before        */
     int32_t n_candidates;         /* candidates timed                               */
     int32_t n_failed;             /* candidates skipped because a step failed       */
+    int32_t ilu_sweeps_bwd;       /* chosen backward sweeps (-1: as ilu_sweeps)     */
 } gks_tune_result;
 
 GKS_EXPORT gks_status gks_autotune(gks_mesh *mesh, const double *w, int32_t trial_steps, gks_tune_result *out,

@@ -66,6 +66,7 @@ gks_status check_config(const gks_config &c)
     ok = ok && (c.ilu_fp16 == 0 || (c.ilu_fp16 == 1 && c.precision == GKS_MIXED));
     ok = ok && (c.cls_global == 0 || c.cls_global == 1);
     ok = ok && c.cls_M >= 0 && c.cls_M <= 2 && (c.cls_M > 0 || c.second_order == 1);
+    ok = ok && c.ilu_sweeps_bwd >= -1 && c.ilu_sweeps_bwd <= 8;
     if (!ok) {
         set_error("invalid gks_config");
         return GKS_EINVAL;
@@ -190,6 +191,7 @@ void gks_config_default(gks_config *c)
     c->ilu_fp16 = 0;
     c->cls_global = 0;
     c->cls_M = 1;
+    c->ilu_sweeps_bwd = -1;
 }
 
 const char *gks_last_error(void) { return gks::last_error(); }

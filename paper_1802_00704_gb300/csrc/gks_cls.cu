@@ -1024,6 +1024,7 @@ gks_status precond_t(gks_mesh *m, const TP *Pg, const TP *alg, const TP *exg, co
     } else {
         // sweeps: forward z^0 = P r, z^{q+1} = F(z^q); backward x^0 = z, x^{q+1} = B(x^q)
         const int ns = m->cfg.ilu_sweeps;
+        const int nsb = m->cfg.ilu_sweeps_bwd < 0 ? ns : m->cfg.ilu_sweeps_bwd;
         TZ *za = (ns % 2 == 0) ? tA : dst;   // buffers chosen so that z ends in tA
         TZ *zb = (ns % 2 == 0) ? dst : tA;
         // a wider source is rounded to TZ once, in the first pass, for the sweeps
@@ -1036,12 +1037,12 @@ gks_status precond_t(gks_mesh *m, const TP *Pg, const TP *alg, const TP *exg, co
                 fwd(T, nullptr, src, za, zb, 1, (TZ *)nullptr);
             std::swap(za, zb);
         }
-        if (ns == 0) {
+        if (nsb == 0) {
             GKS_CUDA(cudaMemcpyAsync(dst, za, sizeof(TZ) * NX * T, cudaMemcpyDeviceToDevice, s));
         } else {
-            TZ *xa = za;                                    // x^0 = z (in tA)
-            TZ *xb = (ns % 2 == 1) ? dst : tB;
-            for (int q = 0; q < ns; ++q) {
+            TZ *xa = za;                                    // x^0 = z (in za)
+            TZ *xb = (nsb % 2 == 1) ? dst : (za == tB ? tA : tB);
+            for (int q = 0; q < nsb; ++q) {
                 bwd(T, nullptr, za, xa, xb);
                 xa = xb;
                 xb = (xb == dst) ? tB : dst;
@@ -1111,11 +1112,13 @@ bool prepare_graphs(gks_mesh *m)
     SolveGraphs &g = *m->graphs;
     if (g.disabled) return false;
     const gks_config &c = m->cfg;
-    if (g.sweeps != c.ilu_sweeps || g.precond != c.precond || g.maxit != c.gmres_maxit || g.eta != c.inner_rtol ||
+    if (g.sweeps != c.ilu_sweeps || g.sweeps_bwd != c.ilu_sweeps_bwd || g.precond != c.precond ||
+        g.maxit != c.gmres_maxit || g.eta != c.inner_rtol ||
         g.rtol != c.gmres_rtol || (int)g.iter.size() != m->wk.m) {
         if (g.whole) flush_solve_counters(m);
         destroy_graph_execs(&g);
         g.sweeps = c.ilu_sweeps;
+        g.sweeps_bwd = c.ilu_sweeps_bwd;
         g.precond = c.precond;
         g.maxit = c.gmres_maxit;
         g.eta = c.inner_rtol;

@@ -6,8 +6,9 @@
 // preconditioner quality for passes over the factors, the extrapolated warm
 // start pays off when the solution changes smoothly in time, and in mixed
 // precision the inner tolerance trades FP32 Arnoldi iterations for FP64
-// refinement residuals.  The tuner times a few steps of the handle's own cases
-// for every combination and keeps the fastest.
+// refinement residuals; the backward relation may take fewer sweeps than the
+// forward one.  The tuner times a few steps of the handle's own cases for every
+// combination and keeps the fastest.
 #include <cfloat>
 #include <vector>
 
@@ -66,6 +67,7 @@ gks_status time_candidate(gks_mesh *m, const double *w, int trial_steps, cudaStr
 struct Candidate {
     int32_t sweeps, warm;
     double eta;
+    int32_t bwd;
 };
 
 }  // namespace
@@ -88,14 +90,17 @@ extern "C" gks_status gks_autotune(gks_mesh *m, const double *w, int32_t trial_s
     const bool mixed = m->cfg.precision == GKS_MIXED;
     const bool sweep = m->cfg.precond == GKS_PC_ILU_SWEEP;
     std::vector<Candidate> cand;
-    for (int32_t sw : {1, 2, 3}) {
-        if (!sweep && sw != 1) continue;
-        for (int32_t wx : {0, 1, 2})
-            for (double eta : {1e-4, 1e-5, 1e-6}) {
-                if (!mixed && eta != 1e-6) continue;
-                cand.push_back({sweep ? sw : before.ilu_sweeps, wx, mixed ? eta : before.inner_rtol});
-            }
-    }
+    for (int32_t sw : {1, 2, 3})
+        for (int32_t bwd : {-1, 1}) {
+            if (!sweep && (sw != 1 || bwd != -1)) continue;
+            if (bwd == 1 && sw == 1) continue;             // the same as -1
+            for (int32_t wx : {0, 1, 2})
+                for (double eta : {1e-4, 1e-5, 1e-6}) {
+                    if (!mixed && eta != 1e-6) continue;
+                    cand.push_back({sweep ? sw : before.ilu_sweeps, wx, mixed ? eta : before.inner_rtol,
+                                    sweep ? bwd : before.ilu_sweeps_bwd});
+                }
+        }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     gks_status st = GKS_OK;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -103,7 +108,7 @@ extern "C" gks_status gks_autotune(gks_mesh *m, const double *w, int32_t trial_s
         st = GKS_ECUDA;
     }
     double best = DBL_MAX, base = DBL_MAX;
-    Candidate pick{before.ilu_sweeps, before.warm_extrap, before.inner_rtol};
+    Candidate pick{before.ilu_sweeps, before.warm_extrap, before.inner_rtol, before.ilu_sweeps_bwd};
     int32_t nfail = 0;
     // the configuration the handle had, then every candidate
     if (st == GKS_OK) st = time_candidate(m, w, trial_steps, s, e0, e1, &base);
@@ -112,6 +117,7 @@ extern "C" gks_status gks_autotune(gks_mesh *m, const double *w, int32_t trial_s
         m->cfg.ilu_sweeps = cand[q].sweeps;
         m->cfg.warm_extrap = cand[q].warm;
         m->cfg.inner_rtol = cand[q].eta;
+        m->cfg.ilu_sweeps_bwd = cand[q].bwd;
         double ms = DBL_MAX;
         st = time_candidate(m, w, trial_steps, s, e0, e1, &ms);
         if (st != GKS_OK) break;
@@ -128,7 +134,9 @@ extern "C" gks_status gks_autotune(gks_mesh *m, const double *w, int32_t trial_s
         m->cfg.ilu_sweeps = pick.sweeps;
         m->cfg.warm_extrap = pick.warm;
         m->cfg.inner_rtol = pick.eta;
+        m->cfg.ilu_sweeps_bwd = pick.bwd;
         out->ilu_sweeps = pick.sweeps;
+        out->ilu_sweeps_bwd = pick.bwd;
         out->warm_extrap = pick.warm;
         out->inner_rtol = pick.eta;
         out->ms_per_step = best;

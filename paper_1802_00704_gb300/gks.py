@@ -45,7 +45,8 @@ class Config(C.Structure):
                 ("basis_fp32", C.c_int32), ("warm_extrap", C.c_int32), ("second_order", C.c_int32),
                 ("no_graphs", C.c_int32), ("limit_char", C.c_int32),
                 ("inner_rtol", C.c_double), ("prandtl", C.c_double), ("slope0_mode", C.c_int32),
-                ("ilu_fp16", C.c_int32), ("cls_global", C.c_int32), ("cls_M", C.c_int32)]
+                ("ilu_fp16", C.c_int32), ("cls_global", C.c_int32), ("cls_M", C.c_int32),
+                ("ilu_sweeps_bwd", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -64,7 +65,7 @@ class RunInfo(C.Structure):
 class TuneResult(C.Structure):
     _fields_ = [("ilu_sweeps", C.c_int32), ("warm_extrap", C.c_int32), ("inner_rtol", C.c_double),
                 ("ms_per_step", C.c_double), ("ms_per_step_before", C.c_double), ("n_candidates", C.c_int32),
-                ("n_failed", C.c_int32)]
+                ("n_failed", C.c_int32), ("ilu_sweeps_bwd", C.c_int32)]
 
 
 class Profile(C.Structure):
@@ -290,12 +291,13 @@ class GksMesh:
         return out, st
 
     def autotune(self, w, trial_steps: int = 3, stream=None) -> dict:
-        """Pick ilu_sweeps, warm_extrap and (mixed) inner_rtol by timing trial steps
-        from the state w (not modified); the handle keeps the fastest."""
+        """Pick ilu_sweeps, ilu_sweeps_bwd, warm_extrap and (mixed) inner_rtol by timing
+        trial steps from the state w (not modified); the handle keeps the fastest."""
         r = TuneResult()
         _check(self._lib.gks_autotune(self._h, _dev(w, (4, self.T)), int(trial_steps), C.byref(r), _stream(stream)),
                "gks_autotune")
         self.cfg.ilu_sweeps, self.cfg.warm_extrap, self.cfg.inner_rtol = r.ilu_sweeps, r.warm_extrap, r.inner_rtol
+        self.cfg.ilu_sweeps_bwd = r.ilu_sweeps_bwd
         return {k: getattr(r, k) for k, _ in TuneResult._fields_}
 
     def limit(self, w, coef, out=None, flags=None, stream=None):

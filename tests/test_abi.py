@@ -43,10 +43,11 @@ def test_config_defaults(lib):
     assert c.limit_char == 0 and c.inner_rtol == 1e-6
     assert c.prandtl == 1.0
     # the ctypes mirror has the size of the C struct: 4 doubles, 2 ints, 1 double, 10 ints, 2 doubles
-    assert C.sizeof(gks.Config) == 4 * 8 + 2 * 4 + 8 + 10 * 4 + 2 * 8 + 4 * 4
+    assert C.sizeof(gks.Config) == 4 * 8 + 2 * 4 + 8 + 10 * 4 + 2 * 8 + 5 * 4 + 4   # + padding
     assert gks.Config.inner_rtol.offset == 88 and gks.Config.prandtl.offset == 96
     assert gks.Config.slope0_mode.offset == 104 and gks.Config.ilu_fp16.offset == 108
     assert gks.Config.cls_global.offset == 112 and gks.Config.cls_M.offset == 116
+    assert gks.Config.ilu_sweeps_bwd.offset == 120
 
 
 def test_binding_refuses_cpu_tensors(lib):

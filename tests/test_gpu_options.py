@@ -72,8 +72,9 @@ def test_autotune_keeps_the_state_and_the_results(G, precision):
     tuned = G.GksMesh(c.mesh, precision=prec)
     r = tuned.autotune(w, trial_steps=2)
     assert np.array_equal(host(w), c.w0)                   # the caller's state is untouched
-    assert r["ilu_sweeps"] in (1, 2, 3) and r["warm_extrap"] in (0, 1, 2)
-    assert r["n_candidates"] == (27 if precision == "mixed" else 9) and r["n_failed"] == 0
+    assert r["ilu_sweeps"] in (1, 2, 3) and r["warm_extrap"] in (0, 1, 2) and r["ilu_sweeps_bwd"] in (-1, 1)
+    # sweeps (1, 2, 3) with the same number backward, and (2, 3) with one backward sweep
+    assert r["n_candidates"] == (45 if precision == "mixed" else 15) and r["n_failed"] == 0
     assert 0 < r["ms_per_step"] <= r["ms_per_step_before"]
     if precision == "fp64":
         assert r["inner_rtol"] == 1e-6
@@ -159,7 +160,8 @@ def test_graphs_follow_knob_changes(G):
     c = I.shock_vortex_case(30, 15)
     m = G.GksMesh(c.mesh, precision=G.MIXED)
     r = m.autotune(dev(c.w0), trial_steps=1)
-    ref = G.GksMesh(c.mesh, precision=G.MIXED, ilu_sweeps=r["ilu_sweeps"], warm_extrap=r["warm_extrap"],
+    ref = G.GksMesh(c.mesh, precision=G.MIXED, ilu_sweeps=r["ilu_sweeps"], ilu_sweeps_bwd=r["ilu_sweeps_bwd"],
+                    warm_extrap=r["warm_extrap"],
                     inner_rtol=r["inner_rtol"], no_graphs=1)
     wa, wb = dev(c.w0), dev(c.w0)
     for _ in range(5):
@@ -184,3 +186,19 @@ def test_profiler_classes_cover_the_step(G):
     assert p["arnoldi"] > 0 and p["precond"] == p["arnoldi"]
     # one residual at the start of each solve and one after every cycle
     assert p["residuals"] >= 2 * 3 and p["n"][G.PROF_RESID] == p["residuals"]
+
+
+@pytest.mark.parametrize("bwd", [0, 1, 3])
+def test_backward_sweeps_knob_reaches_tolerance(O, G, bwd):
+    """ilu_sweeps_bwd: a fixed preconditioner with a different number of backward
+    sweeps; the solve still meets the FP64 tolerance and the oracle's
+    coefficients (1e-9) in FP64 and mixed precision."""
+    c = I.shock_vortex_case(40, 20)
+    ref, _, _, _ = O.OracleMesh(c.mesh).cls_solve(c.w0)
+    for prec in (G.FP64, G.MIXED):
+        m = G.GksMesh(c.mesh, precision=prec, ilu_sweeps=2, ilu_sweeps_bwd=bwd)
+        coef, info = m.cls_reconstruct(dev(c.w0))
+        assert info["converged"] == 1 and max(info["relres"]) <= 1e-12
+        got = host(coef)
+        for v in range(4):
+            assert rel_max(got[v], ref[v]) <= 1e-9
