@@ -42,6 +42,7 @@ FLUX_FP64_FLOP_PER_GP = 8392.3
 # how the CLS solve is launched (gks_config.no_graphs): one graph per solve with
 # device-side GMRES control, per-part graphs under host control (ncu cannot
 # profile the kernel nodes of graphs with conditional nodes), or plain launches
+FLUX_SPLIT = {"on": 1, "off": 0}
 GRAPHS = {"device": 0, "host": 2, "none": 1}
 # event-timed kernel classes of the library's profiler, in its class order
 PROF_NAMES = ["flux", "spmv", "ilu", "orth", "update", "resid", "corr", "ctl"]
@@ -214,7 +215,7 @@ def oracle_sample(steps: int, warmup: int = 0):
 
 
 def class_bytes(cls: str, prof: dict, T: int, F: int, steps: int, sweeps: int, exact: bool, mixed: bool,
-                basis32: bool, ilu16: bool = False, sweeps_bwd: int = -1) -> float:
+                basis32: bool, ilu16: bool = False, sweeps_bwd: int = -1, fuse_first: bool = True) -> float:
     """Algorithmic DRAM bytes moved by one kernel class over the timed region,
     from the solver's work counters (Arnoldi iterations n, sum of j + 1 over
     them, preconditioner applications).  Per cell: operator = diagonal block 15
@@ -223,7 +224,9 @@ def class_bytes(cls: str, prof: dict, T: int, F: int, steps: int, sweeps: int, e
     first 2 of the 5 unknowns of each variable (8 values, counted once).  Sizes:
     sM operator/factor values, sZ preconditioner vectors (8 FP64 path, 4 mixed),
     sB Krylov basis (8, or 4 with the FP32-stored basis), sP the ILU factors (sM,
-    or 2 with FP16 copies)."""
+    or 2 with FP16 copies).  With the block-diagonal pass folded into the first
+    forward sweep the neighbours' z^0 comes from their own factors and right-hand
+    sides, already counted as those cells' reads."""
     sM = 4 if mixed else 8
     sZ = 4 if mixed else 8
     sB = 4 if basis32 else 8
@@ -247,6 +250,8 @@ def class_bytes(cls: str, prof: dict, T: int, F: int, steps: int, sweeps: int, e
         fwd = 20 * sB + 8 * sZ + sP * (25 + 9) + 12 + 20 * sZ
         bwd = 20 * sZ + 8 * sZ + sP * (25 + 9) + 12 + 20 * sZ
         nbwd = sweeps if sweeps_bwd < 0 else sweeps_bwd
+        if fuse_first and sweeps > 0:
+            return T * ((fwd - 8 * sZ) + (sweeps - 1) * fwd + nbwd * bwd) * pc
         return T * (first + sweeps * fwd + nbwd * bwd) * pc
     if cls == "update":                 # w in/out, 1/|Omega|, 3 face slots; each face flux once
         return (T * (8 * 8 + 8 + 12) + F * 4 * 8) * steps
@@ -268,7 +273,8 @@ def timed_leg(args, case, precision: str, world: int, dev, sample_clocks: bool):
     m = gks.GksMesh(case.mesh, precond=gks.PC_ILU_EXACT if exact else gks.PC_ILU_SWEEP, ilu_sweeps=args.sweeps,
                     precision=gks.MIXED if mixed else gks.FP64, basis_fp32=int(mixed and args.basis == "fp32"),
                     limiter=int(args.limiter), warm_extrap=WARM[args.warm], no_graphs=GRAPHS[args.graphs],
-                    ilu_fp16=int(mixed and args.ilu16 == "on"))
+                    ilu_fp16=int(mixed and args.ilu16 == "on"), ilu_fuse_first=int(args.ilu_fuse == "on"),
+                    flux_split=FLUX_SPLIT[args.flux_split])
     w = torch.from_numpy(case.w0.copy()).to(dev)
     stream = torch.cuda.current_stream()
     tune = m.autotune(w, trial_steps=2) if args.tune else None
@@ -300,7 +306,7 @@ def timed_leg(args, case, precision: str, world: int, dev, sample_clocks: bool):
     return {"mesh": m, "w": w, "info": info, "prof": prof, "launches": launches, "clocks": clocks, "ms": ms,
             "stats": m.stats(), "tune": tune,
             "knobs": {"ilu_sweeps": m.cfg.ilu_sweeps, "ilu_sweeps_bwd": m.cfg.ilu_sweeps_bwd,
-                      "warm_extrap": m.cfg.warm_extrap,
+                      "ilu_fuse_first": m.cfg.ilu_fuse_first, "warm_extrap": m.cfg.warm_extrap,
                       "inner_rtol": m.cfg.inner_rtol}}
 
 
@@ -348,7 +354,8 @@ def run_gks(args, world, rank, local):
         ent = {"ms": round(ms_c, 3), "launch_groups": prof["n"][q]}
         if nm not in ("flux", "ctl") and ms_c > 0:
             by = class_bytes(nm, prof, T, F, args.steps, main["knobs"]["ilu_sweeps"], exact, mixed, basis32,
-                             mixed and args.ilu16 == "on", main["knobs"]["ilu_sweeps_bwd"])
+                             mixed and args.ilu16 == "on", main["knobs"]["ilu_sweeps_bwd"],
+                             bool(main["knobs"]["ilu_fuse_first"]))
             gbs = by / (ms_c / 1e3) / 1e9
             ent.update({"bytes": by, "gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 3)})
         classes[nm] = ent
@@ -358,13 +365,15 @@ def run_gks(args, world, rank, local):
     gp = 2 * F
     flop64 = FLUX_FP64_FLOP_PER_GP if not mixed else FLUX_MIXED_FP64_FLOP_PER_GP
     ach = flop64 * gp / (per_launch_ms / 1e3) / 1e12 if flop64 else None
-    roof = {"kernel": "k_face_flux", "launches": prof["n"][q], "avg_ms": per_launch_ms, "bound": "alu",
+    split = mixed and args.flux_split != "off"
+    roof = {"kernel": "k_face_flux_ws" if split else "k_face_flux", "launches": prof["n"][q],
+            "avg_ms": per_launch_ms, "bound": "alu",
             "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": ach / FP64_PEAK_TFLOPS if ach else None, "fp64_flop_per_gauss_point": flop64,
             "peak_source": "FP64 pipe rate from unit count (4 flop/clk/SM) and the 2070 MHz clock"}
     if mixed:
         roof["fp32_flop_per_gauss_point"] = FLUX_MIXED_FP32_FLOP_PER_GP
-    tr = traffic_record(("mixed_" if mixed else "") + "flux")
+    tr = traffic_record("mixed_flux_ws" if split else ("mixed_" if mixed else "") + "flux")
     roof["traffic"] = tr[0] * gp / tr[1] if tr else None      # scaled by Gauss points
     roof["hbm_peak"] = {"gbs": hbm_peak, "source": hbm_src}
     roof["classes"] = classes
@@ -455,7 +464,9 @@ def run_batch(args, world, rank, local):
         b = gks.GksMesh.batch([c.mesh for c in cases], precision=gks.MIXED if prec_mixed else gks.FP64,
                               limiter=2, gmres_m=12, warm_extrap=WARM[args.warm],
                               basis_fp32=int(prec_mixed and args.basis == "fp32"), no_graphs=GRAPHS[args.graphs],
-                              ilu_fp16=int(prec_mixed and args.ilu16 == "on"))
+                              ilu_fp16=int(prec_mixed and args.ilu16 == "on"),
+                              ilu_fuse_first=int(args.ilu_fuse == "on"),
+                              flux_split=FLUX_SPLIT[args.flux_split])
         w = torch.from_numpy(w0.copy()).to(dev)
         tune = b.autotune(w, trial_steps=1) if args.tune else None
         r = b.batch_run(w, max_steps=args.warmup)
@@ -498,7 +509,8 @@ def run_batch(args, world, rank, local):
     torch.cuda.synchronize()
     e2e_value = world * T * args.steps / allmax(world, time.perf_counter() - t0)
     knobs = {"ilu_sweeps": b.cfg.ilu_sweeps, "ilu_sweeps_bwd": b.cfg.ilu_sweeps_bwd,
-             "warm_extrap": b.cfg.warm_extrap, "inner_rtol": b.cfg.inner_rtol}
+             "ilu_fuse_first": b.cfg.ilu_fuse_first, "warm_extrap": b.cfg.warm_extrap,
+             "inner_rtol": b.cfg.inner_rtol}
     names = PROF_NAMES
     hbm_peak = measured_peaks().get("hbm_gbs") or HBM_FALLBACK_GBS
     classes = {}
@@ -506,7 +518,8 @@ def run_batch(args, world, rank, local):
         ent = {"ms": round(prof["ms"][q], 3), "launch_groups": prof["n"][q]}
         if nm not in ("flux", "ctl") and prof["ms"][q] > 0:
             by = class_bytes(nm, prof, T, F, args.steps, knobs["ilu_sweeps"], False, mixed,
-                             mixed and args.basis == "fp32", mixed and args.ilu16 == "on", knobs["ilu_sweeps_bwd"])
+                             mixed and args.basis == "fp32", mixed and args.ilu16 == "on", knobs["ilu_sweeps_bwd"],
+                             bool(knobs["ilu_fuse_first"]))
             gbs = by / (prof["ms"][q] / 1e3) / 1e9
             ent.update({"bytes": by, "gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 3)})
         classes[nm] = ent
@@ -525,7 +538,8 @@ def run_batch(args, world, rank, local):
                    "krylov_basis": "fp32" if mixed and args.basis == "fp32" else "fp64",
                    "autotuned": bool(args.tune), "knobs": knobs, "failed_cases": int(np.sum(stat != 0)),
                    "l2": "inputs larger than L2", "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"kernel": "k_face_flux", "launches": prof["n"][0], "avg_ms": per_launch_ms, "bound": "alu",
+        "roofline": {"kernel": "k_face_flux_ws" if mixed and args.flux_split != "off" else "k_face_flux",
+                     "launches": prof["n"][0], "avg_ms": per_launch_ms, "bound": "alu",
                      "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
                      "fp64_flop_per_gauss_point": flop64, "traffic": None, "classes": classes,
                      "work": {"arnoldi_per_step": prof["arnoldi"] / args.steps,
@@ -583,6 +597,10 @@ def main():
     ap.add_argument("--limiter", action="store_true", help="shock detector + DWBAP limiter on")
     ap.add_argument("--ilu16", default="on", choices=["on", "off"],
                     help="mixed path: FP16 copies of the ILU(0) factors for the FP32 preconditioner")
+    ap.add_argument("--flux-split", default="on", choices=sorted(FLUX_SPLIT),
+                    help="mixed path: FP64 and FP32 parts of the flux in different warps")
+    ap.add_argument("--ilu-fuse", default="on", choices=["on", "off"],
+                    help="fold the block-diagonal ILU pass into the first forward sweep")
     ap.add_argument("--graphs", default="device", choices=sorted(GRAPHS),
                     help="CLS solve launch: device-controlled graph (default), per-part graphs, plain launches")
     ap.add_argument("--no-tune", dest="tune", action="store_false",

@@ -165,6 +165,19 @@ typedef struct gks_config {
     int32_t ilu_sweeps_bwd; /* GKS_PC_ILU_SWEEP: sweeps of the backward (upper) relation;
                               -1 (default) the same as ilu_sweeps, 0..8 otherwise; a
                               fixed preconditioner either way                          */
+    int32_t ilu_fuse_first; /* GKS_PC_ILU_SWEEP with ilu_sweeps > 0: 1 (default) the
+                              block-diagonal pass z^0 = P r is folded into the first
+                              forward sweep (each cell forms its lower neighbours'
+                              z^0 itself); 0 a separate pass.  Same arithmetic, same
+                              results                                                  */
+    int32_t flux_split;    /* mixed precision without the Prandtl correction: 1 (default)
+                              half of the warps of the persistent face flux kernel
+                              form the FP64 part (values, interface state, collision
+                              time, zeroth-order terms), the other half the FP32
+                              slope-carrying part, which keeps GB300's FP64 pipe
+                              busy; 0 every thread does both.  Same arithmetic;
+                              results agree to rounding (multiply-adds may contract
+                              differently in the two kernels)                          */
 } gks_config;
 
 typedef struct gks_mesh gks_mesh;

@@ -67,6 +67,8 @@ gks_status check_config(const gks_config &c)
     ok = ok && (c.cls_global == 0 || c.cls_global == 1);
     ok = ok && c.cls_M >= 0 && c.cls_M <= 2 && (c.cls_M > 0 || c.second_order == 1);
     ok = ok && c.ilu_sweeps_bwd >= -1 && c.ilu_sweeps_bwd <= 8;
+    ok = ok && (c.ilu_fuse_first == 0 || c.ilu_fuse_first == 1);
+    ok = ok && (c.flux_split == 0 || c.flux_split == 1);
     if (!ok) {
         set_error("invalid gks_config");
         return GKS_EINVAL;
@@ -192,6 +194,8 @@ void gks_config_default(gks_config *c)
     c->cls_global = 0;
     c->cls_M = 1;
     c->ilu_sweeps_bwd = -1;
+    c->ilu_fuse_first = 1;
+    c->flux_split = 1;
 }
 
 const char *gks_last_error(void) { return gks::last_error(); }

@@ -439,6 +439,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_resid_df(DeviceMesh d, const floa
 
 // Forward block-ILU relation for the listed rows (or all rows when rows == nullptr):
 //   z_i = P_i (r_i + sum_{k<i} O_ik zin_k)      (use_nb = 0: z_i = P_i r_i)
+// use_nb = 2: the first sweep with the block-diagonal pass folded in, zin_k =
+// P_k r_k formed here from the lower neighbours' factors and right-hand sides
+// (rounded to TZ as the separate pass stores them), which saves the write and
+// the re-read of that pass; the neighbours' data mostly comes from L2.
 // TR: type of r, TZ: type of z, TM: type of the factors and of the arithmetic.
 // rcopy (may be NULL): also store TZ(r_i), so that later sweeps read r in the
 // working precision (same values as converting r again).  Own data (r, P) is
@@ -469,24 +473,46 @@ __global__ void k_ilu_fwd(DeviceMesh d, const TP *__restrict__ Pg, const TP *__r
         for (int k = 0; k < NX; ++k) rcopy[k * T + i] = TZ(y[k]);
     if (use_nb) {
 #pragma unroll
+        // unknowns of a neighbour that its off-diagonal block reaches
+        constexpr int NA = G ? ND : 2;
         for (int s = 0; s < 3; ++s) {
             const int j = d.nb[s * T + i];
             if (j < 0 || j >= i) continue;
             const TM sa = TM(alg[s * T + i]), sax = sa * TM(exg[s * T + i]), say = sa * TM(eyg[s * T + i]);
+            TM zn[NV][NA];
+            if (use_nb == 2) {
+                TM rj[NX];
 #pragma unroll
-            for (int v = 0; v < NV; ++v)
-                oacc(sa, sax, say, TM(zin[(v * ND + 0) * T + j]), TM(zin[(v * ND + 1) * T + j]), y + v * ND);
-            if (G) {
+                for (int k = 0; k < NX; ++k) rj[k] = TM(r[k * T + j]);
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    TM pa[ND];
+#pragma unroll
+                    for (int c = 0; c < ND; ++c) pa[c] = TM(Pg[(a * ND + c) * T + j]);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        TM t = TM(0);
+#pragma unroll
+                        for (int c = 0; c < ND; ++c) t += pa[c] * rj[v * ND + c];
+                        zn[v][a] = TM(TZ(t));
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < NV; ++v)
+#pragma unroll
+                    for (int a = 0; a < NA; ++a) zn[v][a] = TM(zin[(v * ND + a) * T + j]);
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) oacc(sa, sax, say, zn[v][0], zn[v][1], y + v * ND);
+            if constexpr (G) {
                 const TM sr = TM(arg[s * T + i]), srx = sr * TM(exrg[s * T + i]), sry = sr * TM(eyrg[s * T + i]);
                 const TM sb = TM(bdgg[s * T + i]);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    TM zj[ND];
+                    racc(sr, srx, sry, zn[v], y + v * ND);
 #pragma unroll
-                    for (int l = 0; l < ND; ++l) zj[l] = TM(zin[(v * ND + l) * T + j]);
-                    racc(sr, srx, sry, zj, y + v * ND);
-#pragma unroll
-                    for (int l = 2; l < ND; ++l) y[v * ND + l] = fma(sb, zj[l], y[v * ND + l]);
+                    for (int l = 2; l < ND; ++l) y[v * ND + l] = fma(sb, zn[v][l], y[v * ND + l]);
                 }
             }
         }
@@ -1025,12 +1051,15 @@ gks_status precond_t(gks_mesh *m, const TP *Pg, const TP *alg, const TP *exg, co
         // sweeps: forward z^0 = P r, z^{q+1} = F(z^q); backward x^0 = z, x^{q+1} = B(x^q)
         const int ns = m->cfg.ilu_sweeps;
         const int nsb = m->cfg.ilu_sweeps_bwd < 0 ? ns : m->cfg.ilu_sweeps_bwd;
-        TZ *za = (ns % 2 == 0) ? tA : dst;   // buffers chosen so that z ends in tA
-        TZ *zb = (ns % 2 == 0) ? dst : tA;
+        // z^0 folded into the first sweep (ilu_fuse_first) or a pass of its own
+        const bool fuse = ns > 0 && m->cfg.ilu_fuse_first;
+        const int nf = fuse ? ns : ns + 1;   // forward launches
+        TZ *za = (nf % 2 == 1) ? tA : dst;   // buffers chosen so that z ends in tA
+        TZ *zb = (nf % 2 == 1) ? dst : tA;
         // a wider source is rounded to TZ once, in the first pass, for the sweeps
         TZ *rc = (sizeof(TR) > sizeof(TZ) && ns > 0) ? rz : nullptr;
-        fwd(T, nullptr, src, nullptr, za, 0, rc);
-        for (int q = 0; q < ns; ++q) {
+        fwd(T, nullptr, src, nullptr, za, fuse ? 2 : 0, rc);
+        for (int q = fuse ? 1 : 0; q < ns; ++q) {
             if (rc)
                 fwd(T, nullptr, (const TZ *)rc, za, zb, 1, (TZ *)nullptr);
             else
@@ -1112,13 +1141,15 @@ bool prepare_graphs(gks_mesh *m)
     SolveGraphs &g = *m->graphs;
     if (g.disabled) return false;
     const gks_config &c = m->cfg;
-    if (g.sweeps != c.ilu_sweeps || g.sweeps_bwd != c.ilu_sweeps_bwd || g.precond != c.precond ||
+    if (g.sweeps != c.ilu_sweeps || g.sweeps_bwd != c.ilu_sweeps_bwd || g.fuse != c.ilu_fuse_first ||
+        g.precond != c.precond ||
         g.maxit != c.gmres_maxit || g.eta != c.inner_rtol ||
         g.rtol != c.gmres_rtol || (int)g.iter.size() != m->wk.m) {
         if (g.whole) flush_solve_counters(m);
         destroy_graph_execs(&g);
         g.sweeps = c.ilu_sweeps;
         g.sweeps_bwd = c.ilu_sweeps_bwd;
+        g.fuse = c.ilu_fuse_first;
         g.precond = c.precond;
         g.maxit = c.gmres_maxit;
         g.eta = c.inner_rtol;

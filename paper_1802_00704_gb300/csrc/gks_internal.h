@@ -169,7 +169,7 @@ struct SolveGraphs {
     std::vector<int64_t> iter_launches;
     cudaGraphExec_t start = nullptr, restart = nullptr;
     int64_t start_launches = 0, restart_launches = 0;
-    int32_t sweeps = -1, sweeps_bwd = -2, precond = -1, maxit = -1;
+    int32_t sweeps = -1, sweeps_bwd = -2, fuse = -1, precond = -1, maxit = -1;
     double eta = -1.0, rtol = -1.0;
     bool disabled = false;                          // a capture failed: launch directly
     // device-controlled whole solve
@@ -209,6 +209,8 @@ struct gks_mesh {
     int64_t device_bytes = 0;
     std::vector<void *> allocations;
     gks::SolveGraphs *graphs = nullptr;
+    int64_t flux_ws_grid = 0;                      // blocks of the persistent flux kernel
+    int32_t flux_ws_key = -1;                      // ... for this variant
 };
 
 namespace gks {

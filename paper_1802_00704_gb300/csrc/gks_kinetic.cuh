@@ -643,19 +643,25 @@ __device__ __forceinline__ void lead_integrals(double dt, double tau, double &c0
     c6 = tau * t0;
 }
 
-// Mixed precision Gauss-point flux.  vl, vr: FP64 face-frame values
-// (rho, rho U, rho V, E); dl, dr: FP32 face-frame derivative rows [5][4]
-// (d/dn, d/dt, d2/dn2, d2/dndt, d2/dt2); K = 2/(gamma - 1) - 2.  The interface state W0, the
-// collision time, the time integrals and the zeroth-order terms
-// C1 rho0 <u psi>_0 + C7 (rho_l <u psi>_{u>0} + rho_r <u psi>_{u<0}) are FP64;
-// every slope-carrying term is FP32.
-template <bool HEAT = false, bool KIN = false>
-__device__ __forceinline__ bool gp_flux_mixed_split(const double *vl, const double *vr, const float *dl, const float *dr,
-                                                    double dt, double gamma, double K, double mu, int tau2_exact,
-                                                    double *f, double prandtl = 1.0)
+// Mixed precision Gauss-point flux in two parts.  vl, vr: FP64 face-frame
+// values (rho, rho U, rho V, E); dl, dr: FP32 face-frame derivative rows [5][4]
+// (d/dn, d/dt, d2/dn2, d2/dndt, d2/dt2); K = 2/(gamma - 1) - 2.  The interface
+// state W0, the collision time, the time integrals and the zeroth-order terms
+// C1 rho0 <u psi>_0 + C7 (rho_l <u psi>_{u>0} + rho_r <u psi>_{u<0}) are FP64
+// (gp_lead_mixed); every slope-carrying term is FP32 (gp_body_mixed), formed
+// from the FP32 roundings of the FP64 values, W0 and tau.
+struct MixedLead {
+    double f[4];      // zeroth-order terms of the flux
+    double w0[4];     // interface state
+    double tau;       // collision time
+    double dlead[4];  // HEAT: <psi f> of the zeroth-order terms
+    double zu, zv;    // HEAT: interface velocity
+};
+
+template <bool HEAT = false>
+__device__ __forceinline__ bool gp_lead_mixed(const double *vl, const double *vr, double dt, double gamma, double K,
+                                              double mu, MixedLead &o)
 {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) f[q] = 0.0;
     KState<double> L, Rs, Z;
     double hl, hr, hz;
     if (!(prim64(vl, gamma, K, L, hl) & prim64(vr, gamma, K, Rs, hr))) return false;
@@ -664,17 +670,17 @@ __device__ __forceinline__ bool gp_flux_mixed_split(const double *vl, const doub
     mom_half4(Rs.U, Rs.lam, hr, -1.0, mr);
     const double v2l = L.V * L.V + hl, v2r = Rs.V * Rs.V + hr;
     const double zl = K * hl, zr = K * hr;           // <xi.xi> / 2 = K / (4 lam)
-    double w0[4];
+    double *w0 = o.w0;
     w0[0] = L.rho * ml[0] + Rs.rho * mr[0];
     w0[1] = L.rho * ml[1] + Rs.rho * mr[1];
     w0[2] = L.rho * ml[0] * L.V + Rs.rho * mr[0] * Rs.V;
     w0[3] = L.rho * 0.5 * (ml[2] + ml[0] * (v2l + zl)) + Rs.rho * 0.5 * (mr[2] + mr[0] * (v2r + zr));
     if (!prim64(w0, gamma, K, Z, hz)) return false;
     const double jump = fabs(L.p - Rs.p) / fabs(L.p + Rs.p);
-    const double tau = mu > 0.0 ? mu / Z.p + dt * jump : 0.01 * dt + dt * jump;
+    o.tau = mu > 0.0 ? mu / Z.p + dt * jump : 0.01 * dt + dt * jump;
     double C0, C6;
-    lead_integrals(dt, tau, C0, C6);
-    // leading terms (FP64)
+    lead_integrals(dt, o.tau, C0, C6);
+    double *f = o.f;
     {
         const double m2 = Z.U * Z.U + hz, m3 = Z.U * m2 + 2.0 * hz * Z.U;
         const double v2 = Z.V * Z.V + hz, z1 = K * hz;
@@ -689,24 +695,33 @@ __device__ __forceinline__ bool gp_flux_mixed_split(const double *vl, const doub
         f[2] += sl * ml[1] * L.V + sr * mr[1] * Rs.V;
         f[3] += sl * 0.5 * (ml[3] + ml[1] * (v2l + zl)) + sr * 0.5 * (mr[3] + mr[1] * (v2r + zr));
     }
-    // <psi f> of the same zeroth-order terms, for the heat flux
-    double dlead[4] = {0.0, 0.0, 0.0, 0.0};
-    if (HEAT) {
+    if constexpr (HEAT) {
         const double sl = C6 * L.rho, sr = C6 * Rs.rho;
-        dlead[0] = C0 * w0[0] + sl * ml[0] + sr * mr[0];
-        dlead[1] = C0 * w0[1] + sl * ml[1] + sr * mr[1];
-        dlead[2] = C0 * w0[2] + sl * ml[0] * L.V + sr * mr[0] * Rs.V;
-        dlead[3] = C0 * w0[3] + sl * 0.5 * (ml[2] + ml[0] * (v2l + zl)) + sr * 0.5 * (mr[2] + mr[0] * (v2r + zr));
+        o.dlead[0] = C0 * w0[0] + sl * ml[0] + sr * mr[0];
+        o.dlead[1] = C0 * w0[1] + sl * ml[1] + sr * mr[1];
+        o.dlead[2] = C0 * w0[2] + sl * ml[0] * L.V + sr * mr[0] * Rs.V;
+        o.dlead[3] = C0 * w0[3] + sl * 0.5 * (ml[2] + ml[0] * (v2l + zl)) + sr * 0.5 * (mr[2] + mr[0] * (v2r + zr));
+        o.zu = Z.U;
+        o.zv = Z.V;
     }
-    // slope-carrying terms (FP32): states, interface values and time integrals
-    // are formed in FP32 from the rounded values (no per-field conversions)
+    return true;
+}
+
+// The slope-carrying terms in FP32: vl4, vr4, w0f, tauf are the FP32 roundings
+// of the FP64 values, interface state and collision time; g the flux part, dg
+// (HEAT) its <psi f> part.
+template <bool HEAT = false, bool KIN = false>
+__device__ __forceinline__ void gp_body_mixed(const float *vl4, const float *vr4, const float *dl, const float *dr,
+                                              const float *w0f, float tauf, float dtf, float gf, float Kf,
+                                              int tau2_exact, float *g, float *dg)
+{
     Iface<float> J;
-    float fl[24], fr[24], g[4];
+    float fl[24], fr[24];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        J.w0[q] = float(w0[q]);
-        fl[q] = float(vl[q]);
-        fr[q] = float(vr[q]);
+        J.w0[q] = w0f[q];
+        fl[q] = vl4[q];
+        fr[q] = vr4[q];
     }
 #pragma unroll
     for (int q = 0; q < 20; ++q) {
@@ -714,21 +729,40 @@ __device__ __forceinline__ bool gp_flux_mixed_split(const double *vl, const doub
         fr[4 + q] = dr[q];
         J.w0[4 + q] = 0.5f * (dl[q] + dr[q]);
     }
-    const float gf = float(gamma), Kf = float(K);
     prim(fl, gf, Kf, J.L);
     prim(fr, gf, Kf, J.Rs);
     prim(J.w0, gf, Kf, J.Z);
-    J.tau = float(tau);
-    time_integrals(float(dt), J.tau, tau2_exact, J.C);
-    float dg[4];
+    J.tau = tauf;
+    time_integrals(dtf, J.tau, tau2_exact, J.C);
     body_flux<float, HEAT, KIN>(fl, fr, J, gf, false, g, dg);
+}
+
+// Both parts at one Gauss point.  Returns false (f zero) if a state is not physical.
+template <bool HEAT = false, bool KIN = false>
+__device__ __forceinline__ bool gp_flux_mixed_split(const double *vl, const double *vr, const float *dl, const float *dr,
+                                                    double dt, double gamma, double K, double mu, int tau2_exact,
+                                                    double *f, double prandtl = 1.0)
+{
 #pragma unroll
-    for (int q = 0; q < 4; ++q) f[q] += double(g[q]);
+    for (int q = 0; q < 4; ++q) f[q] = 0.0;
+    MixedLead o;
+    if (!gp_lead_mixed<HEAT>(vl, vr, dt, gamma, K, mu, o)) return false;
+    float vl4[4], vr4[4], w0f[4], g[4], dg[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        vl4[q] = float(vl[q]);
+        vr4[q] = float(vr[q]);
+        w0f[q] = float(o.w0[q]);
+    }
+    gp_body_mixed<HEAT, KIN>(vl4, vr4, dl, dr, w0f, float(o.tau), float(dt), float(gamma), float(K), tau2_exact, g,
+                             dg);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) f[q] = o.f[q] + double(g[q]);
     if (HEAT) {
         double D[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) D[q] = dlead[q] + double(dg[q]);
-        f[3] += (1.0 / prandtl - 1.0) * heat_flux(f, D, Z.U, Z.V);
+        for (int q = 0; q < 4; ++q) D[q] = o.dlead[q] + double(dg[q]);
+        f[3] += (1.0 / prandtl - 1.0) * heat_flux(f, D, o.zu, o.zv);
     }
     return true;
 }

@@ -46,7 +46,8 @@ class Config(C.Structure):
                 ("no_graphs", C.c_int32), ("limit_char", C.c_int32),
                 ("inner_rtol", C.c_double), ("prandtl", C.c_double), ("slope0_mode", C.c_int32),
                 ("ilu_fp16", C.c_int32), ("cls_global", C.c_int32), ("cls_M", C.c_int32),
-                ("ilu_sweeps_bwd", C.c_int32)]
+                ("ilu_sweeps_bwd", C.c_int32), ("ilu_fuse_first", C.c_int32),
+                ("flux_split", C.c_int32)]
 
 
 class SolveInfo(C.Structure):

@@ -40,14 +40,16 @@ def test_config_defaults(lib):
     assert c.gmres_rtol == 1e-12 and c.precision == gks.FP64 and c.limiter == 0 and c.basis_fp32 == 0
     assert c.warm_extrap == 0 and c.second_order == 0 and c.no_graphs == 0
     assert c.cls_M == 1 and c.cls_global == 0 and c.slope0_mode == 0 and c.ilu_fp16 == 0
-    assert c.limit_char == 0 and c.inner_rtol == 1e-6
+    assert c.limit_char == 0 and c.inner_rtol == 1e-6 and c.ilu_sweeps_bwd == -1 and c.ilu_fuse_first == 1
+    assert c.flux_split == 1
     assert c.prandtl == 1.0
     # the ctypes mirror has the size of the C struct: 4 doubles, 2 ints, 1 double, 10 ints, 2 doubles
-    assert C.sizeof(gks.Config) == 4 * 8 + 2 * 4 + 8 + 10 * 4 + 2 * 8 + 5 * 4 + 4   # + padding
+    assert C.sizeof(gks.Config) == 4 * 8 + 2 * 4 + 8 + 10 * 4 + 2 * 8 + 7 * 4 + 4   # + padding
     assert gks.Config.inner_rtol.offset == 88 and gks.Config.prandtl.offset == 96
     assert gks.Config.slope0_mode.offset == 104 and gks.Config.ilu_fp16.offset == 108
     assert gks.Config.cls_global.offset == 112 and gks.Config.cls_M.offset == 116
-    assert gks.Config.ilu_sweeps_bwd.offset == 120
+    assert gks.Config.ilu_sweeps_bwd.offset == 120 and gks.Config.ilu_fuse_first.offset == 124
+    assert gks.Config.flux_split.offset == 128
 
 
 def test_binding_refuses_cpu_tensors(lib):

@@ -202,3 +202,69 @@ def test_backward_sweeps_knob_reaches_tolerance(O, G, bwd):
         got = host(coef)
         for v in range(4):
             assert rel_max(got[v], ref[v]) <= 1e-9
+
+
+@pytest.mark.parametrize("cls_global", [0, 1])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fused_first_ilu_pass_is_the_separate_pass(G, precision, cls_global):
+    """ilu_fuse_first folds z^0 = P r into the first forward sweep, each cell
+    forming its lower neighbours' z^0 with the separate pass's arithmetic and
+    rounding: steps and CLS coefficients are bit-identical, with one and three
+    sweeps, FP16 factors in the mixed mode and the global normal equations."""
+    c = I.shock_vortex_case(40, 20)
+    mixed = precision == "mixed"
+    kw = dict(precision=G.MIXED if mixed else G.FP64, basis_fp32=int(mixed), ilu_fp16=int(mixed),
+              cls_global=cls_global)
+    for sweeps in (1, 3):
+        a = G.GksMesh(c.mesh, ilu_sweeps=sweeps, ilu_fuse_first=1, **kw)
+        b = G.GksMesh(c.mesh, ilu_sweeps=sweeps, ilu_fuse_first=0, **kw)
+        ca, ia = a.cls_reconstruct(dev(c.w0))
+        cb, ib = b.cls_reconstruct(dev(c.w0))
+        assert ia["iters"] == ib["iters"] and np.array_equal(host(ca), host(cb))
+        wa, wb = dev(c.w0), dev(c.w0)
+        for _ in range(3):
+            ra, rb = a.step(wa), b.step(wb)
+            assert ra["iters"] == rb["iters"]
+        assert np.array_equal(host(wa), host(wb))
+
+
+@pytest.mark.parametrize("slope0_mode", [0, 1])
+def test_split_flux_kernel_is_the_single_role_kernel(G, slope0_mode):
+    """flux_split gives the FP64 part of the mixed flux (values, interface state,
+    collision time, zeroth-order terms) and its FP32 slope-carrying part to
+    different warps of a persistent block.  The arithmetic is the same as one
+    thread doing both; the compiler may contract multiply-adds differently in
+    the two kernels, so the states agree to rounding (1e-13 of each variable's
+    magnitude after three steps, far below any mistake in the tile hand-over)
+    on Dirichlet, outflow, slip and no-slip boundaries, with enough faces that
+    each block takes several tiles (both buffers reused)."""
+    kw = dict(precision=G.MIXED, basis_fp32=1, ilu_fp16=1, slope0_mode=slope0_mode)
+    for c in (I.shock_vortex_case(200, 100), I.cavity_case(24)):
+        a = G.GksMesh(c.mesh, flux_split=1, **kw)
+        b = G.GksMesh(c.mesh, flux_split=0, **kw)
+        wa, wb = dev(c.w0), dev(c.w0)
+        for _ in range(3):
+            ra, rb = a.step(wa), b.step(wb)
+            assert abs(ra["dt"] - rb["dt"]) <= 1e-13 * rb["dt"]
+        d = rel_max(host(wa), host(wb), axis=1)
+        print(c.name, "split vs single-role kernel, max relative difference per variable:", d)
+        assert np.all(d <= 1e-13), d
+
+
+def test_split_flux_kernel_on_a_batch_with_finished_cases(G):
+    """Per-case time steps and cases that have reached their end time (dt = 0,
+    no flux) in the split kernel: the single-role kernel's states to rounding."""
+    cases = [I.shock_vortex_case(30, 15), I.cavity_case(12), I.advection_case(10)]
+    w0 = np.concatenate([c.w0 for c in cases], axis=1)
+    out = []
+    for split in (1, 0):
+        b = G.GksMesh.batch([c.mesh for c in cases], precision=G.MIXED, basis_fp32=1, flux_split=split)
+        w = dev(w0)
+        r = b.batch_run(w, t_final=np.array([1e-3, 1e9, 2e-3]), max_steps=6)
+        out.append((host(w), r))
+    assert out[0][1]["n_finished"] >= 1 and out[0][1]["n_failed"] == 0
+    assert out[0][1]["steps"] == out[1][1]["steps"]
+    assert np.all(np.abs(out[0][1]["t"] - out[1][1]["t"]) <= 1e-13 * out[1][1]["t"])
+    d = rel_max(out[0][0], out[1][0], axis=1)
+    print("batch: split vs single-role kernel, max relative difference per variable:", d)
+    assert np.all(d <= 1e-13), d
