@@ -437,6 +437,134 @@ __global__ void __launch_bounds__(kBlock, 4) k_resid_df(DeviceMesh d, const floa
     }
 }
 
+// 2^e f as an FP64 value, formed on the integer pipe (exact; an FP32 subnormal
+// f, below 2^-126 of the scale, counts as zero)
+__device__ __forceinline__ double f2d_pow2(float f, int e)
+{
+    const unsigned u = __float_as_uint(f);
+    const int ef = (int)((u >> 23) & 0xFFu);
+    if (ef == 0) return 0.0;
+    const long long E = (long long)ef - 127 + 1023 + e;
+    if (E <= 0 || E >= 2047) return double(f) * pow2(e);
+    const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)E << 52) |
+                                    ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
+// The right-hand side of k_rhs in double-FP32 arithmetic (the FP32-basis
+// solve).  GB300's FP64 pipe made the FP64 kernel (92 FP64 operations per
+// cell) its bottleneck; here a cell and variable take the power of two 2^e of
+// their largest difference w_j - w_i (formed in FP64), split the scaled
+// differences on the integer pipe, multiply them exactly by the weights as FP32
+// pairs a0p ([30][T]: the 15 high parts, then the low parts) and sum with
+// compensation (df_mac); the normalised pair (high + low, 48 bits) is widened
+// on the integer pipe and added in FP64: 32 FP64 operations per cell, b to
+// about 2^-48 relative at any magnitude.  A difference that does not split
+// (not finite) sends the cell to FP64.  part[blk][v][1] gets the block's |b|^2:
+// the scaled high parts squared in FP32, rescaled to the warp's largest 2^e,
+// summed in FP32 within the warp and in FP64 across warps.
+__global__ void k_rhs_df(DeviceMesh d, const float *__restrict__ a0p, const double *__restrict__ w,
+                         double *__restrict__ b, double *__restrict__ part, int pstride)
+{
+    __shared__ double sh[(kBlock / 32) * NV];
+    const int64_t T = d.T;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    float ss[NV] = {0.0f, 0.0f, 0.0f, 0.0f};      // scaled |b|^2 of this cell
+    int ev[NV] = {-1022, -1022, -1022, -1022};    // the scales 2^e
+    if (i < T) {
+        double wi[NV], du[3][NV];
+        int js[3];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) wi[v] = w[v * T + i];
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            js[s] = d.nb[s * T + i];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) du[s][v] = js[s] >= 0 ? w[v * T + js[s]] - wi[v] : 0.0;
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            int em = 1;
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+                const int E = (int)(((unsigned)__double2hiint(du[s][v]) >> 20) & 0x7FFu);
+                em = E > em ? E : em;
+            }
+            ev[v] = (em == 2047 ? 1023 : em) - 1023;
+        }
+        float sh_[NX], sl_[NX];
+#pragma unroll
+        for (int q = 0; q < NX; ++q) sh_[q] = sl_[q] = 0.0f;
+        bool ok = true;
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            if (js[s] < 0) continue;
+            float ah[ND], al[ND];
+#pragma unroll
+            for (int l = 0; l < ND; ++l) {
+                ah[l] = a0p[(s * ND + l) * T + i];
+                al[l] = a0p[(15 + s * ND + l) * T + i];
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                float dh, dl;
+                ok &= df_split(du[s][v], ev[v], dh, dl);
+#pragma unroll
+                for (int l = 0; l < ND; ++l) df_mac(ah[l], al[l], dh, dl, sh_[v * ND + l], sl_[v * ND + l]);
+            }
+        }
+        if (ok) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int l = 0; l < ND; ++l) {
+                    const int q = v * ND + l;
+                    // normalise (TwoSum): h + lo = sh + sl exactly
+                    const float h = __fadd_rn(sh_[q], sl_[q]);
+                    const float z = __fsub_rn(h, sh_[q]);
+                    const float lo = __fadd_rn(__fsub_rn(sh_[q], __fsub_rn(h, z)), __fsub_rn(sl_[q], z));
+                    b[q * T + i] = f2d_pow2(h, ev[v]) + f2d_pow2(lo, ev[v]);
+                    ss[v] = __fmaf_rn(h, h, ss[v]);
+                }
+        } else {
+            // FP64 as in k_rhs; the norm from the values scaled by 2^-e
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                double acc[ND] = {0.0, 0.0, 0.0, 0.0, 0.0};
+                for (int s = 0; s < 3; ++s) {
+                    if (js[s] < 0) continue;
+                    for (int l = 0; l < ND; ++l) acc[l] += d.a0[(s * ND + l) * T + i] * du[s][v];
+                }
+                for (int l = 0; l < ND; ++l) {
+                    b[(v * ND + l) * T + i] = acc[l];
+                    const float h = float(acc[l] * pow2(-ev[v]));
+                    ss[v] = __fmaf_rn(h, h, ss[v]);
+                }
+            }
+        }
+    }
+    // |b|^2 = sum 2^(2e) ss: rescaled to the warp's largest e in FP32 (smaller
+    // terms that underflow are below 2^-126 of the largest), summed in FP32
+    // within the warp, widened once per warp and summed in FP64 across warps
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        int em = ev[v];
+        for (int o = 16; o > 0; o >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
+        const int k = 2 * (ev[v] - em);           // <= 0
+        float c = k >= -126 ? ss[v] * __uint_as_float((unsigned)(127 + k) << 23) : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+        if (lane == 0) sh[warp * NV + v] = double(c) * pow2(em) * pow2(em);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int v = 0; v < NV; ++v) {
+            double t = 0.0;
+            for (int k = 0; k < kBlock / 32; ++k) t += sh[k * NV + v];
+            part[(blockIdx.x * NV + v) * pstride + 1] = t;
+        }
+}
+
 // Forward block-ILU relation for the listed rows (or all rows when rows == nullptr):
 //   z_i = P_i (r_i + sum_{k<i} O_ik zin_k)      (use_nb = 0: z_i = P_i r_i)
 // use_nb = 2: the first sweep with the block-diagonal pass folded in, zin_k =
@@ -472,9 +600,9 @@ __global__ void k_ilu_fwd(DeviceMesh d, const TP *__restrict__ Pg, const TP *__r
 #pragma unroll
         for (int k = 0; k < NX; ++k) rcopy[k * T + i] = TZ(y[k]);
     if (use_nb) {
-#pragma unroll
         // unknowns of a neighbour that its off-diagonal block reaches
         constexpr int NA = G ? ND : 2;
+#pragma unroll
         for (int s = 0; s < 3; ++s) {
             const int j = d.nb[s * T + i];
             if (j < 0 || j >= i) continue;
@@ -1404,6 +1532,8 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
             k_spmv<float, float, TB, false><<<nb, kBlock, 0, q>>>(d, d.D32, d.alpha32, d.ex32, d.ey32, xs, y, 0,
                                                                   nullptr, nullptr, 0);
     };
+    // the FP32-basis solve forms b in double-FP32 arithmetic when the weights fit
+    const bool rhs_df = std::is_same<TB, float>::value && d.a0p;
     auto residual = [&](cudaStream_t q) -> gks_status {
         if (std::is_same<TB, float>::value && d.D2) {
             if (d.SR2)
@@ -1423,7 +1553,11 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
     // flags for the host, the whole-solve graph with a condition kernel)
     auto start_body = [&](cudaStream_t q) -> gks_status {
         int slot = prof_start(m, kProfCtl, q);
-        k_rhs<<<nb, kBlock, 0, q>>>(d, k.w, k.b, k.part, ps); note_launch();
+        if (rhs_df)
+            k_rhs_df<<<nb, kBlock, 0, q>>>(d, d.a0p, k.w, k.b, k.part, ps);
+        else
+            k_rhs<<<nb, kBlock, 0, q>>>(d, k.w, k.b, k.part, ps);
+        note_launch();
         if (sx) {
             // the FP32 basis stores its first vector scaled by a power of two 2^-e
             k_reduce<<<dim3(1, ns), kReduceThreads, 0, q>>>(k.part + 1, d.case_blk, ps, k.hcol + 1, ps, 0);

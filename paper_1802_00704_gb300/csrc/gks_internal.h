@@ -70,6 +70,7 @@ struct DeviceMesh {
     // unknowns 3..5 with the neighbour's (plus the reverse one in the global system)
     double *bdg = nullptr;           // [3][T]; with alr.. allocated for either option (zeros if unused)
     double *a0 = nullptr;            // [3][5][T] weighted row 0 of A_ij (right-hand side)
+    float *a0p = nullptr;            // [30][T] FP32 pairs of a0 (the 15 high parts, then the low parts)
     double *D = nullptr;             // [15][T] symmetric diagonal block, upper triangle row-major
     double *P = nullptr;             // [25][T] inverse of the ILU(0) diagonal block, row-major
     // FP32 copies of the operator and factors (mixed precision)

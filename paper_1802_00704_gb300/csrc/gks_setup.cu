@@ -792,6 +792,18 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
                 if (ext) {
                     UP(SR2, h_SR2); UP(SB2, h_SB2);
                 }
+                // pairs of the right-hand-side weights for the double-FP32 right-hand side
+                // (0 or 2^-50 <= |a0| <= 2^50: the low parts stay normal FP32 and the
+                // scaled squares of the norm stay below 2^128)
+                bool a0_range = true;
+                std::vector<float> h_a0p(30 * T);
+                for (int64_t q = 0; q < 15 * T; ++q) {
+                    const double v = h_a0[q], a = std::fabs(v);
+                    if (v != 0.0 && !(a >= 0x1p-50 && a <= 0x1p50)) a0_range = false;
+                    h_a0p[q] = float(v);
+                    h_a0p[15 * T + q] = float(v - double(h_a0p[q]));
+                }
+                if (a0_range) UP(a0p, h_a0p);
             }
         }
     }
