@@ -996,20 +996,32 @@ __global__ void k_combine_z(DeviceMesh d, const TZ *__restrict__ Z, const double
 // Warm start of the next solve (cases not done) from the last solutions
 // x = s_{n-1}, xp = s_{n-2}, xpp = s_{n-3}: order 0 keeps x, order 1 takes
 // 2 x - xp, order 2 takes 3 x - 3 xp + xpp (polynomial extrapolation in the
-// step index); the history then shifts (xpp = xp, xp = old x).
+// step index).  The history shifts by a swap of the two buffers on the host
+// after this launch: the old x goes into xpp's buffer (the next xp), and xp's
+// buffer (the next xpp) already holds s_{n-2}, so one vector is written
+// instead of two.  Cells of finished cases keep their history: their two
+// buffers exchange contents, which the swap undoes.
 __global__ void k_warm(DeviceMesh d, double *__restrict__ x, double *__restrict__ xp, double *__restrict__ xpp,
                        const int32_t *__restrict__ done, int order)
 {
     const int64_t T = d.T;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= T || done[d.blk_case[blockIdx.x]]) return;
+    if (i >= T) return;
+    if (done[d.blk_case[blockIdx.x]]) {
+#pragma unroll 4
+        for (int q = 0; q < NX; ++q) {
+            const double b = xp[q * T + i], c = xpp[q * T + i];
+            xp[q * T + i] = c;
+            xpp[q * T + i] = b;
+        }
+        return;
+    }
 #pragma unroll 4
     for (int q = 0; q < NX; ++q) {
-        const double a = x[q * T + i], b = xp[q * T + i];
-        if (order == 2) x[q * T + i] = 3.0 * (a - b) + xpp[q * T + i];
-        else if (order == 1) x[q * T + i] = 2.0 * a - b;
-        xpp[q * T + i] = b;
-        xp[q * T + i] = a;
+        const double a = x[q * T + i];
+        if (order == 2) x[q * T + i] = 3.0 * (a - xp[q * T + i]) + xpp[q * T + i];
+        else if (order == 1) x[q * T + i] = 2.0 * a - xp[q * T + i];
+        xpp[q * T + i] = a;
     }
 }
 
@@ -1729,6 +1741,7 @@ gks_status cls_solve(gks_mesh *m, cudaStream_t s, int32_t *iters, double *relres
         k_warm<<<nb, kBlock, 0, s>>>(m->d, k.x, k.x_prev, k.x_prev2, k.done, order); note_launch();
         prof_stop(m, slot, s);
         GKS_CUDA(cudaGetLastError());
+        std::swap(k.x_prev, k.x_prev2);            // the history shift (see k_warm)
     }
     gks_status st = k.V32 ? cls_solve_t<float>(m, k.V32, s, iters, relres, converged)
                           : cls_solve_t<double>(m, k.V, s, iters, relres, converged);

@@ -107,3 +107,29 @@ def test_single_mesh_entry_points_refuse_batches(G):
         b.step(w)
     with pytest.raises(G.GksError):
         b.cfl_dt_noalloc(w, torch.zeros(1, dtype=torch.float64, device="cuda"))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_finished_case_keeps_its_warm_start_history(G, precision):
+    """Extrapolated warm start in a batch whose cases finish at different times
+    (the history buffers rotate for every case; a finished case exchanges its
+    two buffers' contents so that it keeps its history): a second run of the
+    batch reaches, per case, the states of a single run that stopped and
+    resumed at the same times (1e-10: both solves meet 1e-12, from guesses that
+    may differ in rounding)."""
+    cases = _cases()[:3]
+    prec = G.MIXED if precision == "mixed" else G.FP64
+    kw = dict(precision=prec, warm_extrap=2, basis_fp32=int(precision == "mixed"))
+    b = G.GksMesh.batch([c.mesh for c in cases], **kw)
+    w = dev(_concat(cases))
+    t1 = np.array([0.004, 0.0015, 0.003])
+    t2 = np.array([0.006, 0.005, 0.0045])
+    r1 = b.batch_run(w, t_final=t1, max_steps=10000)
+    r2 = b.batch_run(w, t_final=t2, max_steps=10000)
+    assert r1["n_finished"] == 3 and r2["n_finished"] == 3 and r2["n_failed"] == 0
+    for c, g, ta, tb in zip(cases, _split(host(w), cases), t1, t2):
+        m = G.GksMesh(c.mesh, **kw)
+        ws = dev(c.w0)
+        m.run(ws, t_final=ta, max_steps=10000)
+        m.run(ws, t_final=tb, max_steps=10000)
+        assert rel_max(g, host(ws)) <= 1e-10, c.name
