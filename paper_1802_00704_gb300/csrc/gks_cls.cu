@@ -463,8 +463,9 @@ __device__ __forceinline__ double f2d_pow2(float f, int e)
 // (not finite) sends the cell to FP64.  part[blk][v][1] gets the block's |b|^2:
 // the scaled high parts squared in FP32, rescaled to the warp's largest 2^e,
 // summed in FP32 within the warp and in FP64 across warps.
-__global__ void k_rhs_df(DeviceMesh d, const float *__restrict__ a0p, const double *__restrict__ w,
-                         double *__restrict__ b, double *__restrict__ part, int pstride)
+__global__ void __launch_bounds__(kBlock, 3) k_rhs_df(DeviceMesh d, const float *__restrict__ a0p,
+                                                      const double *__restrict__ w, double *__restrict__ b,
+                                                      double *__restrict__ part, int pstride)
 {
     __shared__ double sh[(kBlock / 32) * NV];
     const int64_t T = d.T;
@@ -867,12 +868,15 @@ __global__ void k_hadd(double *hc, int hstride, const double *__restrict__ h2, i
     }
 }
 
-__global__ void k_givens(int j, int m, const double *__restrict__ hc, int hstride, double *vn, double *H,
-                         double *cs, double *sn, double *g, int32_t *ctl, int ns, const double *__restrict__ bnorm,
-                         const double *__restrict__ beta, double rtol, double eta, int maxit)
+// Arnoldi index j of system sy (running systems only): the new Hessenberg
+// column from the raw sums hc, the earlier rotations applied, a new rotation,
+// the rotated residual g and the stopping test.
+__device__ __forceinline__ void givens_step(int sy, int j, int m, const double *__restrict__ hc, int hstride,
+                                            double *vn, double *H, double *cs, double *sn, double *g, int32_t *ctl,
+                                            int ns, const double *__restrict__ bnorm,
+                                            const double *__restrict__ beta, double rtol, double eta, int maxit)
 {
-    const int sy = blockIdx.x * blockDim.x + threadIdx.x;
-    if (sy >= ns || !ctl[kCtlRunning * ns + sy]) return;
+    if (!ctl[kCtlRunning * ns + sy]) return;
     // Hessenberg column of the normalised basis: h_kj = <V_k, u_j> / (vn_k vn_j),
     // h_{j+1,j} = |V_{j+1}| / vn_j; the new vector's norm becomes vn_{j+1}
     double h[kMaxRestart + 1];
@@ -904,6 +908,33 @@ __global__ void k_givens(int j, int m, const double *__restrict__ hc, int hstrid
     if (gn <= rtol * bnorm[sy] || gn <= eta * beta[sy] || !(hnext > 0.0) || ctl[kCtlIters * ns + sy] >= maxit ||
         j + 1 == m)
         ctl[kCtlRunning * ns + sy] = 0;
+}
+
+// The last reduction of an Arnoldi index (|V_{j+1}| of system blockIdx.y into
+// hc[.][j + 1], as k_reduce with op 2) followed by that system's Givens step
+// in thread 0, which saves a launch per index.
+__global__ void __launch_bounds__(kReduceThreads) k_norm_givens(const double *__restrict__ part,
+                                                                const int32_t *__restrict__ seg, int pstride, int j,
+                                                                int m, double *hc, int hstride, double *vn, double *H,
+                                                                double *cs, double *sn, double *g, int32_t *ctl,
+                                                                int ns, const double *__restrict__ bnorm,
+                                                                const double *__restrict__ beta, double rtol,
+                                                                double eta, int maxit)
+{
+    __shared__ double sh[kReduceThreads / 32];
+    const int sy = blockIdx.y, c = sy >> 2, v = sy & 3;
+    const int b0 = seg[c], b1 = seg[c + 1];
+    double acc = 0.0;
+    for (int b = b0 + threadIdx.x; b < b1; b += kReduceThreads) acc += part[((int64_t)b * NV + v) * pstride];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        acc = 0.0;
+        for (int w = 0; w < kReduceThreads / 32; ++w) acc += sh[w];
+        hc[sy * hstride + j + 1] = sqrt(acc);
+        givens_step(sy, j, m, hc, hstride, vn, H, cs, sn, g, ctl, ns, bnorm, beta, rtol, eta, maxit);
+    }
 }
 
 // y = H^{-1} g on the first jv columns (upper triangular after the rotations).
@@ -1625,12 +1656,10 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
             k_orth_update<TB><<<nb, kBlock, 0, q>>>(d, V, vj1, j, k.hco, ps, k.ctl, ns, k.part, ps, 1); note_launch();
             k_hadd<<<sblocks(ns * (j + 1)), 128, 0, q>>>(k.hcol, ps, k.y, mm, j, ns); note_launch();
         }
-        k_reduce<<<dim3(1, ns), kReduceThreads, 0, q>>>(k.part, d.case_blk, ps, k.hcol + j + 1, ps, 2);
-        note_launch();
-        prof_stop(m, slot, q);
-        slot = prof_start(m, kProfCtl, q);
-        k_givens<<<sblocks(ns), 128, 0, q>>>(j, mm, k.hcol, ps, k.vn, k.H, k.cs, k.sn, k.g, k.ctl, ns, k.bnorm,
-                                              k.beta, rtol, eta, maxit);
+        // |V_{j+1}| and the Givens step of every system
+        k_norm_givens<<<dim3(1, ns), kReduceThreads, 0, q>>>(k.part, d.case_blk, ps, j, mm, k.hcol, ps, k.vn, k.H,
+                                                              k.cs, k.sn, k.g, k.ctl, ns, k.bnorm, k.beta, rtol, eta,
+                                                              maxit);
         note_launch();
         prof_stop(m, slot, q);
         GKS_CUDA(cudaGetLastError());
