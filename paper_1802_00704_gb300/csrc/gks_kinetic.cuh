@@ -590,17 +590,18 @@ __device__ __forceinline__ bool gp_flux(const R *wl, const R *wr, R dt, R gamma,
     return true;
 }
 
-// Primitive state from the FP64 values with two reciprocals; h = 1/(2 lam)
-// comes out of the same quantities without a further division.
+// Primitive state from the FP64 values with two reciprocals (correctly rounded
+// reciprocal instructions times the numerators: within 1.5 ulp, no IEEE
+// division); h = 1/(2 lam) comes out of the same quantities.
 __device__ __forceinline__ bool prim64(const double *w, double gamma, double K, KState<double> &s, double &h)
 {
     s.rho = w[0];
-    const double ir = 1.0 / w[0];
+    const double ir = __drcp_rn(w[0]);
     s.U = w[1] * ir;
     s.V = w[2] * ir;
     const double eint = w[3] - 0.5 * s.rho * (s.U * s.U + s.V * s.V);
     s.p = (gamma - 1.0) * eint;
-    s.lam = 0.25 * (K + 2.0) * s.rho / eint;
+    s.lam = 0.25 * (K + 2.0) * s.rho * __drcp_rn(eint);
     h = 2.0 / (K + 2.0) * eint * ir;                 // (K + 2) rho / (4 eint) = lam
     return s.rho > 0.0 && s.p > 0.0;
 }
@@ -621,7 +622,7 @@ __device__ __forceinline__ void mom_half4(double U, double lam, double h, double
 // power series where the closed form cancels (x = dt/tau < 1/2).
 __device__ __forceinline__ void lead_integrals(double dt, double tau, double &c0, double &c6)
 {
-    const double x = dt / tau;
+    const double x = dt * __drcp_rn(tau);
     double t0, c1;
     if (x >= 0.5) {
         t0 = -expm1(-x);
@@ -676,8 +677,8 @@ __device__ __forceinline__ bool gp_lead_mixed(const double *vl, const double *vr
     w0[2] = L.rho * ml[0] * L.V + Rs.rho * mr[0] * Rs.V;
     w0[3] = L.rho * 0.5 * (ml[2] + ml[0] * (v2l + zl)) + Rs.rho * 0.5 * (mr[2] + mr[0] * (v2r + zr));
     if (!prim64(w0, gamma, K, Z, hz)) return false;
-    const double jump = fabs(L.p - Rs.p) / fabs(L.p + Rs.p);
-    o.tau = mu > 0.0 ? mu / Z.p + dt * jump : 0.01 * dt + dt * jump;
+    const double jump = fabs(L.p - Rs.p) * __drcp_rn(fabs(L.p + Rs.p));
+    o.tau = mu > 0.0 ? mu * __drcp_rn(Z.p) + dt * jump : 0.01 * dt + dt * jump;
     double C0, C6;
     lead_integrals(dt, o.tau, C0, C6);
     double *f = o.f;
