@@ -72,7 +72,7 @@ __device__ __forceinline__ double cfl_cell64(const double *__restrict__ w, int64
 // divisions and square roots the cost of this pass, so every cell first forms
 // its step in FP32 from truncated inputs (relative error below 5e-5 when the
 // pressure is not a cancellation, p >= 0.01 E); only the cells within 1e-3 of
-// the block's smallest FP32 step, and the cells the screen cannot judge
+// the block's smallest FP32 step, and the cells the screen cannot bound
 // (cancellation, non-physical, outside the FP32 range), evaluate the FP64
 // formula.  The FP64 minimiser is always among them, so the block minimum is
 // the FP64 minimum bit for bit.
@@ -85,7 +85,7 @@ __global__ void k_cfl_partial(DeviceMesh d, const double *__restrict__ w, double
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float s = FLT_MAX;
-    bool judge = false;                              // the screen cannot judge: always FP64
+    bool need64 = false;                             // the screen cannot bound the step: FP64
     double r = 0.0;
     if (i < T) {
         r = d.inrad[i];
@@ -98,9 +98,9 @@ __global__ void k_cfl_partial(DeviceMesh d, const double *__restrict__ w, double
             if (p >= 0.01f * E && p > 0.0f)
                 s = rf / (sqrtf(u * u + v * v) + sqrtf(gf * p / rho) + 2.0f * float(mu) / (rho * rf));
             else
-                judge = true;
+                need64 = true;
         } else {
-            judge = true;
+            need64 = true;
         }
     }
     // block minimum of the screen
@@ -111,7 +111,7 @@ __global__ void k_cfl_partial(DeviceMesh d, const double *__restrict__ w, double
     m = shf[0];
     for (int k = 1; k < kBlock / 32; ++k) m = fminf(m, shf[k]);
     double dti = DBL_MAX;
-    if (i < T && (judge || s <= m * 1.001f)) dti = cfl_cell64(w, T, i, r, gamma, mu);
+    if (i < T && (need64 || s <= m * 1.001f)) dti = cfl_cell64(w, T, i, r, gamma, mu);
     for (int o = 16; o > 0; o >>= 1) dti = fmin(dti, __shfl_xor_sync(0xffffffffu, dti, o));
     if (lane == 0) shd[warp] = dti;
     __syncthreads();
