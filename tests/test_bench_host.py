@@ -1,0 +1,105 @@
+"""Host logic of the measurement harness (bench.py), no GPU: the algorithmic
+byte model of the solver's kernel classes (the per-cell figures the roofline
+fractions divide by), the profiler class order shared with the library, the
+option maps, and the committed traffic record's format."""
+import os
+import re
+
+import pytest
+
+import bench
+from paper_1802_00704_gb300 import gks
+
+
+def _prof(n=6, jsum=12, precond=6, residuals=3):
+    return {"arnoldi": n, "arnoldi_jsum": jsum, "precond": precond, "residuals": residuals}
+
+
+def test_profiler_classes_match_the_library():
+    assert len(bench.PROF_NAMES) == gks.PROF_CLASSES
+    order = [gks.PROF_FLUX, gks.PROF_SPMV, gks.PROF_ILU, gks.PROF_ORTH, gks.PROF_UPDATE, gks.PROF_RESID,
+             gks.PROF_CORR, gks.PROF_CTL]
+    assert [bench.PROF_NAMES[q] for q in order] == ["flux", "spmv", "ilu", "orth", "update", "resid", "corr", "ctl"]
+
+
+def test_ilu_bytes_per_application():
+    """Per cell and application (FP32 basis and vectors, FP16 factors, 2 + 2
+    sweeps): separate block-diagonal pass 210 B, each forward or backward sweep
+    272 B; with the pass folded into the first forward sweep that sweep moves
+    240 B and the pass is gone (1,056 against 1,298 B: 19 % fewer)."""
+    T, pc = 1000, 5
+    p = _prof(precond=pc)
+    args = dict(T=T, F=0, steps=1, sweeps=2, exact=False, mixed=True, basis32=True, ilu16=True, sweeps_bwd=-1)
+    assert bench.class_bytes("ilu", p, fuse_first=False, **args) == T * 1298 * pc
+    assert bench.class_bytes("ilu", p, fuse_first=True, **args) == T * 1056 * pc
+    # one backward sweep instead of two
+    args1 = dict(args, sweeps_bwd=1)
+    assert bench.class_bytes("ilu", p, fuse_first=True, **args1) == T * (1056 - 272) * pc
+    # no forward sweep: nothing to fold, the block-diagonal pass stays
+    args0 = dict(args, sweeps=0, sweeps_bwd=0)
+    assert bench.class_bytes("ilu", p, fuse_first=True, **args0) == T * 210 * pc
+
+
+def test_fp64_and_exact_ilu_bytes():
+    T, pc = 10, 1
+    p = _prof(precond=pc)
+    # FP64 path: 8-byte values everywhere; level-scheduled exact ILU reads each factor once per relation
+    exact = bench.class_bytes("ilu", p, T=T, F=0, steps=1, sweeps=2, exact=True, mixed=False, basis32=False)
+    fwd = 20 * 8 + 8 * 8 + 8 * 34 + 12 + 20 * 8
+    bwd = 20 * 8 + 8 * 8 + 8 * 34 + 12 + 20 * 8
+    assert exact == T * (fwd + bwd) * pc
+
+
+def test_gram_schmidt_operator_and_residual_bytes():
+    T = 100
+    p = _prof(n=6, jsum=12, residuals=3)
+    # mixed, FP32 basis: (2 jsum + 3 n) vectors of 20 values, once
+    assert bench.class_bytes("orth", p, T=T, F=0, steps=1, sweeps=2, exact=False, mixed=True,
+                             basis32=True) == T * 20 * 4 * (2 * 12 + 3 * 6)
+    # FP64: 8-byte basis and the classical Gram-Schmidt pass twice
+    assert bench.class_bytes("orth", p, T=T, F=0, steps=1, sweeps=2, exact=False, mixed=False,
+                             basis32=False) == T * 20 * 8 * (2 * 12 + 3 * 6) * 2
+    # operator: blocks (24 values) + neighbour indices + source + result per iteration
+    assert bench.class_bytes("spmv", p, T=T, F=0, steps=1, sweeps=2, exact=False, mixed=True,
+                             basis32=True) == T * (4 * 24 + 12 + 20 * 4 + 20 * 4) * 6
+    # refinement residual: FP64 (or FP32-pair) operator, x own + neighbours, b, and the basis slot
+    assert bench.class_bytes("resid", p, T=T, F=0, steps=1, sweeps=2, exact=False, mixed=True,
+                             basis32=True) == T * (8 * 24 + 12 + 160 + 64 + 160 + 80) * 3
+
+
+def test_update_and_correction_bytes():
+    T, F, steps = 50, 80, 4
+    p = _prof(n=6, residuals=3 * steps)
+    assert bench.class_bytes("update", p, T=T, F=F, steps=steps, sweeps=2, exact=False, mixed=True,
+                             basis32=True) == (T * 84 + F * 32) * steps
+    # Z vectors once per Arnoldi iteration, x read and written once per cycle (residuals beyond one per step)
+    assert bench.class_bytes("corr", p, T=T, F=F, steps=steps, sweeps=2, exact=False, mixed=True,
+                             basis32=True) == T * (20 * 4 * 6 + 320 * (3 * steps - steps))
+    with pytest.raises(KeyError):
+        bench.class_bytes("flux", p, T=T, F=F, steps=steps, sweeps=2, exact=False, mixed=True, basis32=True)
+
+
+def test_option_maps_match_the_config():
+    assert bench.WARM == {"prev": 0, "extrap": 1, "extrap2": 2}
+    assert bench.FLUX_SPLIT == {"on": 1, "off": 0}
+    assert bench.GRAPHS == {"device": 0, "host": 2, "none": 1}
+    assert bench.METRIC == "triangle-steps/s"
+
+
+def test_traffic_record_format():
+    """profiles/traffic.txt: kernel, a 16-hex-digit hash of the flux sources,
+    DRAM bytes per launch and the Gauss points of that launch; the record is
+    used only while the hash matches the sources (else the roofline's traffic
+    is null), and bench.py's hash is deterministic."""
+    p = os.path.join(bench.ROOT, "profiles", "traffic.txt")
+    kernels = set()
+    for line in open(p):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, h, by, gp = line.split()[:4]
+        assert re.fullmatch(r"[0-9a-f]{16}", h)
+        assert float(by) > 0 and float(gp) > 0
+        kernels.add(k)
+    assert {"mixed_flux_ws", "mixed_flux", "flux"} <= kernels
+    assert bench.source_hash() == bench.source_hash() and re.fullmatch(r"[0-9a-f]{16}", bench.source_hash())
+    assert bench.traffic_record("no_such_kernel") is None
