@@ -57,3 +57,21 @@ def test_binding_refuses_cpu_tensors(lib):
     from paper_1802_00704_gb300 import gks
     with pytest.raises(TypeError):
         gks._dev(torch.zeros(4, 3, dtype=torch.float64))
+
+
+@pytest.mark.parametrize("field,value", [
+    ("ilu_sweeps_bwd", -2), ("ilu_sweeps_bwd", 9), ("ilu_fuse_first", 2), ("flux_split", 2), ("flux_split", -1),
+    ("ilu_fp16", 1),            # FP16 factors need the mixed precision
+    ("cls_M", 0),               # values-only equations need the second-order variant
+    ("slope0_mode", 2), ("no_graphs", 3), ("warm_extrap", 3), ("inner_rtol", 0.0),
+])
+def test_invalid_config_is_refused_before_any_device_call(lib, field, value):
+    """gks_mesh_create checks the configuration first: an invalid field gives
+    GKS_EINVAL with a message, and no CUDA call is made (this runs without a
+    GPU)."""
+    from paper_1802_00704_gb300 import gks
+    from paper_1802_00704_gb300 import inputs as I
+    case = I.advection_case(3)
+    with pytest.raises(gks.GksError) as e:
+        gks.GksMesh(case.mesh, **{field: value})
+    assert e.value.status == gks.GKS_EINVAL and "invalid gks_config" in str(e.value)
