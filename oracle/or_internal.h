@@ -100,6 +100,9 @@ int  or_interface_w0(const double *wl, const double *wr, double gamma, int mode,
 int  or_gp_flux(const double *wl, const double *wr, double dt, const or_params *prm,
                 double *f, double *aux);
 
+/* boundary ghost states (or_scheme.c) */
+void or_ghost_rows(int tag, const double *bc, double nx, double ny, double gamma, const double *wl, double *wr);
+
 /* limiter (or_limiter.c) */
 int  or_limit(const or_mesh *m, const double *w, const double *coef, double *coef_out, int32_t *flag);
 void or_char_basis(const double *W, double gamma, double nx, double ny, double *R, double *L);

@@ -240,36 +240,122 @@ static void to_face_frame(const double *g, double nx, double ny, double *f)
     }
 }
 
-/* Ghost right state of a boundary face, in the face frame. */
-static void ghost_state(const or_mesh *m, int64_t f, const double *wl, double *wr)
+/* Second-order jets of a field at the Gauss point in the face frame:
+ * j[0] value, j[1] d/dn, j[2] d/dt, j[3] d2/dn2, j[4] d2/dndt, j[5] d2/dt2
+ * (the row order of the face-frame states).  Products and quotients follow
+ * the Leibniz and quotient rules term by term. */
+static const int jet_nord[6] = {0, 1, 0, 2, 1, 0};   /* order in n of each entry */
+
+static void jet_of(const double *rows, int v, double *j)
 {
-    const int tag = m->face[5 * f + 4];
-    const double nx = m->fnx[f], ny = m->fny[f];
-    const double *bc = &m->bc[4 * f];
-    const double gamma = m->prm.gamma;
+    for (int r = 0; r < 6; ++r) j[r] = rows[4 * r + v];
+}
+
+static void jet_mul(const double *a, const double *b, double *c)
+{
+    double o[6];
+    o[0] = a[0] * b[0];
+    o[1] = a[1] * b[0] + a[0] * b[1];
+    o[2] = a[2] * b[0] + a[0] * b[2];
+    o[3] = a[3] * b[0] + 2.0 * a[1] * b[1] + a[0] * b[3];
+    o[4] = a[4] * b[0] + a[1] * b[2] + a[2] * b[1] + a[0] * b[4];
+    o[5] = a[5] * b[0] + 2.0 * a[2] * b[2] + a[0] * b[5];
+    memcpy(c, o, sizeof(o));
+}
+
+/* c = a / b */
+static void jet_div(const double *a, const double *b, double *c)
+{
+    /* 1/b: derivatives of 1/x are -1/x^2 and 2/x^3 */
+    double ib[6], b0 = b[0];
+    ib[0] = 1.0 / b0;
+    ib[1] = -b[1] / (b0 * b0);
+    ib[2] = -b[2] / (b0 * b0);
+    ib[3] = -b[3] / (b0 * b0) + 2.0 * b[1] * b[1] / (b0 * b0 * b0);
+    ib[4] = -b[4] / (b0 * b0) + 2.0 * b[1] * b[2] / (b0 * b0 * b0);
+    ib[5] = -b[5] / (b0 * b0) + 2.0 * b[2] * b[2] / (b0 * b0 * b0);
+    jet_mul(a, ib, c);
+}
+
+/* Mirror image across the face (x_n -> -x_n).  odd = 0: q_g(x_n, x_t) =
+ * q(-x_n, x_t); odd = 1: q_g(x_n, x_t) = 2 c - q(-x_n, x_t), the reflection
+ * about the wall value c.  An entry of order k in n picks up (-1)^k, and the
+ * odd reflection negates every entry except for the value's 2 c. */
+static void jet_reflect(const double *q, int odd, double c, double *g)
+{
+    for (int r = 0; r < 6; ++r) {
+        double s = (jet_nord[r] & 1) ? -1.0 : 1.0;
+        if (odd) s = -s;
+        g[r] = s * q[r];
+    }
+    if (odd) g[0] += 2.0 * c;
+}
+
+/* Ghost right state of a boundary face from the left state wl (face frame
+ * rows), the face normal (nx, ny) and the face's boundary data bc.
+ *  Dirichlet: the prescribed state with zero derivatives.
+ *  outflow:   a copy of the left state.
+ *  slip wall: the mirror image of the conservative fields, normal momentum
+ *             odd, everything else even.
+ *  no-slip isothermal wall (bc = wall velocity x, y and wall temperature
+ *             T_w = p/rho): the mirror image of the primitive fields with the
+ *             pressure even, the velocity odd about the wall velocity and the
+ *             temperature odd about T_w, so that a linear shear or a linear
+ *             temperature profile at uniform pressure continues across the
+ *             wall unchanged; the conservative rows of the ghost follow from
+ *             rho = p / T, rho u, rho v and E = p / (gamma - 1) + rho |u|^2 / 2. */
+void or_ghost_rows(int tag, const double *bc, double nx, double ny, double gamma, const double *wl, double *wr)
+{
     if (tag == OR_OUTFLOW) { memcpy(wr, wl, sizeof(double) * 24); return; }
     if (tag == OR_DIRICHLET) {
         memset(wr, 0, sizeof(double) * 24);
         wr[0] = bc[0]; wr[1] = nx * bc[1] + ny * bc[2]; wr[2] = -ny * bc[1] + nx * bc[2]; wr[3] = bc[3];
         return;
     }
-    /* walls: mirror image across the face, q_R(x_n, x_t) = s_q q_L(-x_n, x_t);
-     * a derivative of order k in x_n picks up (-1)^k. */
-    static const int nord[6] = {0, 1, 0, 2, 1, 0};
-    double s[4] = {1.0, -1.0, 1.0, 1.0};
-    if (tag == OR_NOSLIP) s[2] = -1.0;
-    for (int r = 0; r < 6; ++r)
-        for (int v = 0; v < 4; ++v) wr[4 * r + v] = s[v] * ((nord[r] & 1) ? -1.0 : 1.0) * wl[4 * r + v];
-    if (tag == OR_NOSLIP) {
-        /* values: velocity reflected about the wall velocity, temperature about T_wall */
-        double rho = wl[0], un = wl[1] / rho, ut = wl[2] / rho;
-        double p = (gamma - 1.0) * (wl[3] - 0.5 * rho * (un * un + ut * ut));
-        double uwn = nx * bc[0] + ny * bc[1], uwt = -ny * bc[0] + nx * bc[1];
-        double Tg = 2.0 * bc[2] - p / rho;
-        double ugn = 2.0 * uwn - un, ugt = 2.0 * uwt - ut;
-        wr[0] = rho; wr[1] = rho * ugn; wr[2] = rho * ugt;
-        wr[3] = rho * Tg / (gamma - 1.0) + 0.5 * rho * (ugn * ugn + ugt * ugt);
+    if (tag == OR_SLIP) {
+        double q[6], g[6];
+        for (int v = 0; v < 4; ++v) {
+            jet_of(wl, v, q);
+            jet_reflect(q, v == 1, 0.0, g);
+            for (int r = 0; r < 6; ++r) wr[4 * r + v] = g[r];
+        }
+        return;
     }
+    /* OR_NOSLIP: primitive jets of the interior state */
+    double rho[6], mn[6], mt[6], E[6], un[6], ut[6], ke[6], tmp[6], p[6], T[6];
+    jet_of(wl, 0, rho); jet_of(wl, 1, mn); jet_of(wl, 2, mt); jet_of(wl, 3, E);
+    jet_div(mn, rho, un);
+    jet_div(mt, rho, ut);
+    jet_mul(mn, un, ke);                       /* rho u_n^2 */
+    jet_mul(mt, ut, tmp);                      /* rho u_t^2 */
+    for (int r = 0; r < 6; ++r) p[r] = (gamma - 1.0) * (E[r] - 0.5 * (ke[r] + tmp[r]));
+    jet_div(p, rho, T);
+    /* reflected primitive jets */
+    double uwn = nx * bc[0] + ny * bc[1], uwt = -ny * bc[0] + nx * bc[1];
+    double pg[6], ung[6], utg[6], Tg[6], rhog[6], o[6];
+    jet_reflect(p, 0, 0.0, pg);
+    jet_reflect(un, 1, uwn, ung);
+    jet_reflect(ut, 1, uwt, utg);
+    jet_reflect(T, 1, bc[2], Tg);
+    jet_div(pg, Tg, rhog);
+    /* conservative rows of the ghost */
+    for (int r = 0; r < 6; ++r) wr[4 * r + 0] = rhog[r];
+    jet_mul(rhog, ung, o);
+    for (int r = 0; r < 6; ++r) wr[4 * r + 1] = o[r];
+    jet_mul(rhog, utg, o);
+    for (int r = 0; r < 6; ++r) wr[4 * r + 2] = o[r];
+    double kn[6], kt[6];
+    jet_mul(ung, ung, kn);
+    jet_mul(utg, utg, kt);
+    for (int r = 0; r < 6; ++r) tmp[r] = kn[r] + kt[r];
+    jet_mul(rhog, tmp, o);
+    for (int r = 0; r < 6; ++r) wr[4 * r + 3] = pg[r] / (gamma - 1.0) + 0.5 * o[r];
+}
+
+/* Ghost right state of boundary face f, in the face frame. */
+static void ghost_state(const or_mesh *m, int64_t f, const double *wl, double *wr)
+{
+    or_ghost_rows(m->face[5 * f + 4], &m->bc[4 * f], m->fnx[f], m->fny[f], m->prm.gamma, wl, wr);
 }
 
 /* Time-integrated flux of face f (global frame, 4 values).  Returns the

@@ -92,6 +92,8 @@ def _load():
         lib.or_time_integrals.argtypes = [D, D, I, P]
         lib.or_gauss_legendre.argtypes = [I, P, P]
         lib.or_params_default.argtypes = [C.POINTER(Params)]
+        lib.or_ghost_rows.restype = None
+        lib.or_ghost_rows.argtypes = [I, P, D, D, D, P, P]
         lib.or_limit.restype = I
         lib.or_limit.argtypes = [P, P, P, P, P]
         _lib = lib
@@ -266,6 +268,17 @@ def point_flux(wl: np.ndarray, wr: np.ndarray, dt: float, **prm):
     aux = np.zeros(16)
     st = lib.or_point_flux(_ptr(wl), _ptr(wr), float(dt), C.byref(p), _ptr(f), _ptr(aux))
     return f, aux, int(st)
+
+
+def ghost_rows(tag: int, bc, nx: float, ny: float, wl: np.ndarray, gamma: float = 1.4) -> np.ndarray:
+    """Ghost right state (6, 4) of a boundary face with tag `tag` and boundary
+    data bc (4,) from the left state wl (6, 4), both in the face frame."""
+    lib = _load()
+    bc = np.ascontiguousarray(bc, dtype=np.float64)
+    wl = np.ascontiguousarray(wl, dtype=np.float64)
+    wr = np.zeros((6, 4))
+    lib.or_ghost_rows(int(tag), _ptr(bc), float(nx), float(ny), float(gamma), _ptr(wl), _ptr(wr))
+    return wr
 
 
 def char_basis(W, gamma: float = 1.4, nx: float = 1.0, ny: float = 0.0):

@@ -66,13 +66,16 @@ def _advect(oracle_mod, n, tf):
 
 
 def test_advection_third_order(oracle_mod):
-    """L1 and L2 density errors at t = 0.1 on 20^2 and 40^2 jittered meshes;
-    the paper states that the designed (third) order is reached (Sec. IV.A)."""
-    e20 = _advect(oracle_mod, 20, 0.1)
-    e40 = _advect(oracle_mod, 40, 0.1)
-    o1 = math.log(e20[0] / e40[0], 2)
-    o2 = math.log(e20[1] / e40[1], 2)
-    assert o1 > 2.7 and o2 > 2.7, (e20, e40, o1, o2)
+    """L1 and L2 density errors at t = 0.1 on 20^2, 40^2 and 80^2 jittered
+    meshes; the paper states that the designed (third) order is reached
+    (Sec. IV.A).  Both refinements must show it: one ratio alone cannot tell an
+    order-3 scheme from a lucky pre-asymptotic ratio (measured: 2.83 and 2.95
+    in L1)."""
+    e = [_advect(oracle_mod, n, 0.1) for n in (20, 40, 80)]
+    for a, b in zip(e, e[1:]):
+        o1 = math.log(a[0] / b[0], 2)
+        o2 = math.log(a[1] / b[1], 2)
+        assert o1 > 2.7 and o2 > 2.7, (e, o1, o2)
 
 
 def _rotated_mesh(mesh, th, shift=(0.0, 0.0)):
