@@ -126,6 +126,105 @@ __device__ __forceinline__ void to_face_der(float *der, float fnx, float fny)
     }
 }
 
+// Isothermal no-slip wall as the mirror image of the primitive fields:
+// pressure even in the normal coordinate n, velocity odd about the wall
+// velocity, temperature T = p / rho odd about the wall temperature.  Fields with
+// that symmetry (a linear shear, a linear temperature profile at uniform
+// pressure) continue across the wall unchanged, so the kinetic flux through the
+// wall carries their viscous stress and Fourier conduction.
+//
+// A field near the Gauss point is a second-order jet j[6] in the face frame
+// (value, d/dn, d/dt, d2/dn2, d2/dndt, d2/dt2: the entries of one variable in
+// the face-frame rows).  q = a / b is formed by the recursive quotient rule
+// b q = a differentiated term by term.
+template <typename R>
+__device__ __forceinline__ void jet_quot(const R *a, const R *b, R *q)
+{
+    const R ib = R(1) / b[0];
+    q[0] = a[0] * ib;
+    q[1] = (a[1] - q[0] * b[1]) * ib;
+    q[2] = (a[2] - q[0] * b[2]) * ib;
+    q[3] = (a[3] - R(2) * q[1] * b[1] - q[0] * b[3]) * ib;
+    q[4] = (a[4] - q[1] * b[2] - q[2] * b[1] - q[0] * b[4]) * ib;
+    q[5] = (a[5] - R(2) * q[2] * b[2] - q[0] * b[5]) * ib;
+}
+
+template <typename R>
+__device__ __forceinline__ void jet_prod(const R *a, const R *b, R *c)
+{
+    c[0] = a[0] * b[0];
+    c[1] = a[1] * b[0] + a[0] * b[1];
+    c[2] = a[2] * b[0] + a[0] * b[2];
+    c[3] = a[3] * b[0] + R(2) * a[1] * b[1] + a[0] * b[3];
+    c[4] = a[4] * b[0] + a[1] * b[2] + a[2] * b[1] + a[0] * b[4];
+    c[5] = a[5] * b[0] + R(2) * a[2] * b[2] + a[0] * b[5];
+}
+
+// Ghost state of the no-slip wall.  v0: the interior values (rho, rho u_n,
+// rho u_t, E), der: its five face-frame derivative rows (entry (r, v) of row
+// r = d/dn .. d2/dt2 at der[4 r + v]); uwn, uwt the wall velocity along n and
+// t, tw the wall temperature.  Out: the ghost values vg (skipped if NULL) and
+// derivative rows dg, same layouts.
+template <typename R>
+__device__ __forceinline__ void noslip_jets(const R *v0, const R *der, R uwn, R uwt, R tw, R gamma, R *vg, R *dg)
+{
+    // interior jets: entry 0 from v0, entries 1..5 from the derivative rows der[4 (r - 1) + v]
+    R rho[6], mn[6], mt[6], en[6];
+    rho[0] = v0[0];
+    mn[0] = v0[1];
+    mt[0] = v0[2];
+    en[0] = v0[3];
+#pragma unroll
+    for (int r = 1; r < 6; ++r) {
+        rho[r] = der[4 * (r - 1) + 0];
+        mn[r] = der[4 * (r - 1) + 1];
+        mt[r] = der[4 * (r - 1) + 2];
+        en[r] = der[4 * (r - 1) + 3];
+    }
+    R un[6], ut[6], kin[6], a[6], b[6], p[6], T[6];
+    jet_quot(mn, rho, un);
+    jet_quot(mt, rho, ut);
+    jet_prod(mn, un, a);
+    jet_prod(mt, ut, b);
+#pragma unroll
+    for (int r = 0; r < 6; ++r) p[r] = (gamma - R(1)) * (en[r] - R(0.5) * (a[r] + b[r]));
+    jet_quot(p, rho, T);
+    // mirror image: an entry of order k in n gets (-1)^k (pressure), the
+    // reflection about a wall value c negates that: 2 c - q, (-1)^{k+1} d^k q
+    const R ev[6] = {R(1), R(-1), R(1), R(1), R(-1), R(1)};
+    R pg[6], ung[6], utg[6], Tg[6];
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+        pg[r] = ev[r] * p[r];
+        ung[r] = -ev[r] * un[r];
+        utg[r] = -ev[r] * ut[r];
+        Tg[r] = -ev[r] * T[r];
+    }
+    ung[0] += R(2) * uwn;
+    utg[0] += R(2) * uwt;
+    Tg[0] += R(2) * tw;
+    R rg[6], mng[6], mtg[6];
+    jet_quot(pg, Tg, rg);
+    jet_prod(rg, ung, mng);
+    jet_prod(rg, utg, mtg);
+    jet_prod(mng, ung, a);
+    jet_prod(mtg, utg, b);
+    const R ig = R(1) / (gamma - R(1));
+    if (vg) {
+        vg[0] = rg[0];
+        vg[1] = mng[0];
+        vg[2] = mtg[0];
+        vg[3] = pg[0] * ig + R(0.5) * (a[0] + b[0]);
+    }
+#pragma unroll
+    for (int r = 1; r < 6; ++r) {
+        dg[4 * (r - 1) + 0] = rg[r];
+        dg[4 * (r - 1) + 1] = mng[r];
+        dg[4 * (r - 1) + 2] = mtg[r];
+        dg[4 * (r - 1) + 3] = pg[r] * ig + R(0.5) * (a[r] + b[r]);
+    }
+}
+
 // Ghost state of a boundary face, FP64 values (face frame) ...
 __device__ __forceinline__ void ghost_val(int tag, const double *bc, double nx, double ny, double gamma,
                                           const double *vl, double *vr)
@@ -143,15 +242,17 @@ __device__ __forceinline__ void ghost_val(int tag, const double *bc, double nx, 
         return;
     }
     if (tag == GKS_BC_NOSLIP) {
+        // same pressure, velocity 2 u_w - u, temperature 2 T_w - T
         const double rho = vl[0], un = vl[1] / rho, ut = vl[2] / rho;
         const double p = (gamma - 1.0) * (vl[3] - 0.5 * rho * (un * un + ut * ut));
         const double uwn = nx * bc[0] + ny * bc[1], uwt = -ny * bc[0] + nx * bc[1];
         const double tg = 2.0 * bc[2] - p / rho;
         const double gn = 2.0 * uwn - un, gt = 2.0 * uwt - ut;
-        vr[0] = rho;
-        vr[1] = rho * gn;
-        vr[2] = rho * gt;
-        vr[3] = rho * tg / (gamma - 1.0) + 0.5 * rho * (gn * gn + gt * gt);
+        const double rg = p / tg;
+        vr[0] = rg;
+        vr[1] = rg * gn;
+        vr[2] = rg * gt;
+        vr[3] = p / (gamma - 1.0) + 0.5 * rg * (gn * gn + gt * gt);
     } else {
         vr[0] = vl[0];
         vr[1] = -vl[1];
@@ -160,22 +261,29 @@ __device__ __forceinline__ void ghost_val(int tag, const double *bc, double nx, 
     }
 }
 
-// ... and FP32 derivative rows: zero (Dirichlet), copied (outflow), or the
-// mirror image with (-1)^p for a derivative of order p in n (walls)
-__device__ __forceinline__ void ghost_der(int tag, const float *dl, float *dr)
+// ... and FP32 derivative rows: zero (Dirichlet), copied (outflow), the mirror
+// image with (-1)^p for a derivative of order p in n (slip wall), or the
+// derivatives of the reflected primitive fields (no-slip wall; vl the FP32
+// roundings of the interior values, face frame)
+__device__ __forceinline__ void ghost_der(int tag, const double *bc, float fnx, float fny, float gamma,
+                                          const float *vl, const float *dl, float *dr)
 {
     if (tag == GKS_BC_DIRICHLET || tag == GKS_BC_OUTFLOW) {
 #pragma unroll
         for (int q = 0; q < 20; ++q) dr[q] = tag == GKS_BC_OUTFLOW ? dl[q] : 0.0f;
         return;
     }
-    const bool noslip = tag == GKS_BC_NOSLIP;
+    if (tag == GKS_BC_NOSLIP) {
+        const float bx = float(bc[0]), by = float(bc[1]);
+        noslip_jets<float>(vl, dl, fnx * bx + fny * by, -fny * bx + fnx * by, float(bc[2]), gamma, nullptr, dr);
+        return;
+    }
     const int npar[5] = {1, 0, 0, 1, 0};   // parity of the n-order of rows d/dn .. d2/dt2
 #pragma unroll
     for (int r = 0; r < 5; ++r)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            float sg = (v == 1 || (noslip && v == 2)) ? -1.0f : 1.0f;
+            float sg = v == 1 ? -1.0f : 1.0f;
             if (npar[r]) sg = -sg;
             dr[4 * r + v] = sg * dl[4 * r + v];
         }
@@ -199,28 +307,20 @@ __device__ __forceinline__ void ghost(int tag, const double *bc, double nx, doub
         for (int q = 0; q < 24; ++q) wr[q] = wl[q];
         return;
     }
-    // mirror image: q_R(n, t) = s_q q_L(-n, t); a derivative of order p in n gets (-1)^p
-    const bool noslip = tag == GKS_BC_NOSLIP;
+    if (tag == GKS_BC_NOSLIP) {
+        noslip_jets<double>(wl, wl + 4, nx * bc[0] + ny * bc[1], -ny * bc[0] + nx * bc[1], bc[2], gamma, wr, wr + 4);
+        return;
+    }
+    // slip wall, mirror image: q_R(n, t) = s_q q_L(-n, t); a derivative of order p in n gets (-1)^p
     const int npar[6] = {0, 1, 0, 0, 1, 0};   // parity of the n-order of each row
 #pragma unroll
     for (int r = 0; r < 6; ++r)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            double s = (v == 1 || (noslip && v == 2)) ? -1.0 : 1.0;
+            double s = v == 1 ? -1.0 : 1.0;
             if (npar[r]) s = -s;
             wr[4 * r + v] = s * wl[4 * r + v];
         }
-    if (noslip) {
-        const double rho = wl[0], un = wl[1] / rho, ut = wl[2] / rho;
-        const double p = (gamma - 1.0) * (wl[3] - 0.5 * rho * (un * un + ut * ut));
-        const double uwn = nx * bc[0] + ny * bc[1], uwt = -ny * bc[0] + nx * bc[1];
-        const double tg = 2.0 * bc[2] - p / rho;
-        const double gn = 2.0 * uwn - un, gt = 2.0 * uwt - ut;
-        wr[0] = rho;
-        wr[1] = rho * gn;
-        wr[2] = rho * gt;
-        wr[3] = rho * tg / (gamma - 1.0) + 0.5 * rho * (gn * gn + gt * gt);
-    }
 }
 
 // y = float(x), n values
@@ -272,7 +372,8 @@ __global__ void __launch_bounds__(kFluxBlock, MIXED ? 4 : 1) k_face_flux(DeviceM
             } else {
                 const double bc[4] = {d.bc[f], d.bc[F + f], d.bc[2 * F + f], d.bc[3 * F + f]};
                 ghost_val(d.ftag[f], bc, nx, ny, gamma, vl, vr);
-                ghost_der(d.ftag[f], dl, dr);
+                const float vlf[4] = {float(vl[0]), float(vl[1]), float(vl[2]), float(vl[3])};
+                ghost_der(d.ftag[f], bc, fnx, fny, float(gamma), vlf, dl, dr);
             }
             ok = kin::gp_flux_mixed_split<HEAT, KIN>(vl, vr, dl, dr, dt, gamma, K, mu, tau2, fk, prandtl);
         } else {
@@ -438,7 +539,9 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_face_flux_ws(DeviceMesh d, co
                                       dr);
                             to_face_der(dr, fnx, fny);
                         } else {
-                            ghost_der(d.ftag[f], dl, dr);
+                            const double bc[4] = {d.bc[f], d.bc[F + f], d.bc[2 * F + f], d.bc[3 * F + f]};
+                            const float vlf[4] = {B.vl[0][p], B.vl[1][p], B.vl[2][p], B.vl[3][p]};
+                            ghost_der(d.ftag[f], bc, fnx, fny, float(gamma), vlf, dl, dr);
                         }
                         float vl4[4], vr4[4], w0f[4], gq[4], dg[4];
 #pragma unroll
