@@ -32,13 +32,10 @@ if ROOT not in sys.path:
 METRIC = "triangle-steps/s"
 WARM = {"prev": 0, "extrap": 1, "extrap2": 2}     # gks_config.warm_extrap
 HBM_FALLBACK_GBS = 6800.0
-# FP64 (non-tensor) peak: 4 flop/clk/SM (2 DFMA) x 152 SMs x 2.07 GHz; the nominal
-# 1.25 TFLOP/s of the part corresponds to 3.97 flop/clk/SM at that clock.
-FP64_PEAK_TFLOPS = 4 * 152 * 2.07e9 / 1e12
-# FP64 flops executed per face Gauss point by the FP64 flux kernel
-# (dadd + dmul + 2 dfma, ncu instruction counters on the 399,424-triangle case;
-# profiles/flux_fp64_shock_vortex_400k.md).
-FLUX_FP64_FLOP_PER_GP = 8392.3
+# non-tensor pipe rates per SM and clock: FP64 2 DFMA (4 flop), FP32 128 FFMA (256 flop)
+FP64_FLOP_PER_CLK_SM = 4
+FP32_FLOP_PER_CLK_SM = 256
+NOMINAL_SM_MHZ = 2070.0
 # how the CLS solve is launched (gks_config.no_graphs): one graph per solve with
 # device-side GMRES control, per-part graphs under host control (ncu cannot
 # profile the kernel nodes of graphs with conditional nodes), or plain launches
@@ -46,10 +43,6 @@ FLUX_SPLIT = {"on": 1, "off": 0}
 GRAPHS = {"device": 0, "host": 2, "none": 1}
 # event-timed kernel classes of the library's profiler, in its class order
 PROF_NAMES = ["flux", "spmv", "ilu", "orth", "update", "resid", "corr", "ctl"]
-# FP64 and FP32 flops per Gauss point of the mixed flux kernel (same counters,
-# 1,200,168 Gauss points; profiles/flux_mixed_shock_vortex_400k.md).
-FLUX_MIXED_FP64_FLOP_PER_GP = 698.7
-FLUX_MIXED_FP32_FLOP_PER_GP = 7577.5
 
 WORKLOADS = {
     "shock_vortex_1m": dict(kind="shock_vortex", nx=1000, ny=500),
@@ -86,19 +79,94 @@ def measured_peaks() -> dict:
     return {}
 
 
-def traffic_record(kernel: str):
-    """(DRAM bytes per launch, Gauss points of that launch) from the committed
-    ncu summary, if it was taken on the current kernel sources
-    (profiles/traffic.txt: kernel source_hash bytes gauss_points)."""
+def counter_record(kernel: str):
+    """ncu counters of a face-flux kernel from the committed record
+    (profiles/traffic.txt: kernel source_hash dram_bytes_per_launch
+    gauss_points_per_launch fp64_flop_per_gp fp32_flop_per_gp), if they were
+    taken on the current kernel sources; '-' marks a counter not taken."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
     cur = source_hash()
     for line in open(p):
         parts = line.split()
-        if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[1] == cur:
-            return float(parts[2]), float(parts[3])
+        if len(parts) >= 6 and not line.startswith("#") and parts[0] == kernel and parts[1] == cur:
+            num = [None if x == "-" else float(x) for x in parts[2:6]]
+            return {"dram_bytes": num[0], "gauss_points": num[1], "fp64_flop_per_gp": num[2],
+                    "fp32_flop_per_gp": num[3]}
     return None
+
+
+def probe_peaks(dev, reps: int = 5) -> dict:
+    """Measured roofs on this GPU: FP64 and FP32 multiply-add chains (the
+    library's FMA probe), a streaming read and a copy of 2 GiB (larger than L2);
+    best of reps launches, CUDA events on the launching stream.  Beside them the
+    rates derived from the pipes' per-SM throughput, the device's SM count and
+    the nominal maximum SM clock."""
+    import torch
+
+    from paper_1802_00704_gb300 import gks
+    props = torch.cuda.get_device_properties(dev)
+    nsm = props.multi_processor_count
+    stream = torch.cuda.current_stream(dev)
+    sink = torch.zeros(16 * nsm, dtype=torch.float64, device=dev)
+
+    def best(launch):
+        out = None
+        for _ in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            work = launch()
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            rate = work / (ms / 1e3)
+            out = rate if out is None else max(out, rate)
+        return out
+
+    fp64 = best(lambda: gks.probe_fma(True, sink, blocks_per_sm=4, iters=512)) / 1e12
+    fp32 = best(lambda: gks.probe_fma(False, sink, blocks_per_sm=8, iters=8192)) / 1e12
+    n = (2 << 30) // 4
+    a = torch.ones(n, dtype=torch.float32, device=dev)
+    b = torch.empty_like(a)
+    rd = best(lambda: gks.probe_read(a, sink)) / 1e9
+    cp = best(lambda: gks.probe_copy(a, b)) / 1e9
+    del a, b
+    clk = NOMINAL_SM_MHZ * 1e6
+    return {"fp64_tflops": fp64, "fp32_tflops": fp32, "read_gbs": rd, "copy_gbs": cp, "sm_count": nsm,
+            "fp64_tflops_derived": FP64_FLOP_PER_CLK_SM * nsm * clk / 1e12,
+            "fp32_tflops_derived": FP32_FLOP_PER_CLK_SM * nsm * clk / 1e12,
+            "how": "gks_probe_fma (8 independent FMA chains per thread, 4 resp. 8 blocks of 256 threads per SM), "
+                   "gks_probe_read / gks_probe_copy (16-byte streaming loads, 2 GiB); best of 5, CUDA events; "
+                   f"derived: 4 (FP64) and 256 (FP32) flop/clk/SM x {nsm} SMs x {NOMINAL_SM_MHZ:.0f} MHz"}
+
+
+def flux_roofline(key: str, name: str, launches: int, per_launch_ms: float, gp: int, peaks: dict) -> dict:
+    """Roofline object of the face-flux kernel, which the arithmetic pipes bound:
+    flop per Gauss point from the ncu record of the current sources (FMA = 2),
+    times the Gauss points of one launch, over the event-timed launch duration,
+    against the measured rate of the busier pipe (FP64 or FP32)."""
+    rec = counter_record(key)
+    roof = {"kernel": name, "launches": launches, "avg_ms": per_launch_ms, "bound": "alu", "unit": "TFLOP/s"}
+    cand = []
+    for pipe in ("fp64", "fp32"):
+        fl = rec[f"{pipe}_flop_per_gp"] if rec else None
+        roof[f"{pipe}_flop_per_gauss_point"] = fl
+        if fl:
+            ach = fl * gp / (per_launch_ms / 1e3) / 1e12
+            cand.append((ach / peaks[f"{pipe}_tflops"], pipe, ach))
+    if cand:
+        frac, pipe, ach = max(cand)
+        roof.update({"pipe": pipe, "achieved": ach, "peak": peaks[f"{pipe}_tflops"], "frac": frac,
+                     "peak_source": f"measured: {pipe.upper()} multiply-add chain probe on this GPU in this run",
+                     "peak_derived": peaks[f"{pipe}_tflops_derived"],
+                     "frac_of_derived": ach / peaks[f"{pipe}_tflops_derived"],
+                     "other_pipes": {p: round(f, 3) for f, p, _ in cand if p != pipe}})
+    else:
+        roof.update({"achieved": None, "peak": None, "frac": None,
+                     "note": "no ncu flop counters for the current flux sources (profiles/traffic.txt)"})
+    roof["traffic"] = rec["dram_bytes"] * gp / rec["gauss_points"] if rec and rec["dram_bytes"] else None
+    return roof
 
 
 class ClockSampler:
@@ -343,8 +411,8 @@ def run_gks(args, world, rank, local):
     # per-class device time (CUDA events on the launching stream) against each class's roof
     prof, info = main["prof"], main["info"]
     names = PROF_NAMES
-    peaks = measured_peaks()
-    hbm_peak = peaks.get("hbm_gbs")
+    peaks = probe_peaks(dev)
+    hbm_peak = measured_peaks().get("hbm_gbs")
     hbm_src = "measured" if hbm_peak else "fallback"
     hbm_peak = hbm_peak or HBM_FALLBACK_GBS
     basis32 = mixed and args.basis == "fp32"
@@ -362,20 +430,12 @@ def run_gks(args, world, rank, local):
     # the dominant kernel is the face-flux kernel (one launch per step): ALU-bound
     q = names.index("flux")
     per_launch_ms = prof["ms"][q] / max(prof["n"][q], 1)
-    gp = 2 * F
-    flop64 = FLUX_FP64_FLOP_PER_GP if not mixed else FLUX_MIXED_FP64_FLOP_PER_GP
-    ach = flop64 * gp / (per_launch_ms / 1e3) / 1e12 if flop64 else None
     split = mixed and args.flux_split != "off"
-    roof = {"kernel": "k_face_flux_ws" if split else "k_face_flux", "launches": prof["n"][q],
-            "avg_ms": per_launch_ms, "bound": "alu",
-            "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach / FP64_PEAK_TFLOPS if ach else None, "fp64_flop_per_gauss_point": flop64,
-            "peak_source": "FP64 pipe rate from unit count (4 flop/clk/SM) and the 2070 MHz clock"}
-    if mixed:
-        roof["fp32_flop_per_gauss_point"] = FLUX_MIXED_FP32_FLOP_PER_GP
-    tr = traffic_record("mixed_flux_ws" if split else ("mixed_" if mixed else "") + "flux")
-    roof["traffic"] = tr[0] * gp / tr[1] if tr else None      # scaled by Gauss points
-    roof["hbm_peak"] = {"gbs": hbm_peak, "source": hbm_src}
+    roof = flux_roofline("mixed_flux_ws" if split else ("mixed_" if mixed else "") + "flux",
+                         "k_face_flux_ws" if split else "k_face_flux", prof["n"][q], per_launch_ms, 2 * F, peaks)
+    roof["hbm_peak"] = {"gbs": hbm_peak, "source": hbm_src, "probe_read_gbs": round(peaks["read_gbs"], 1),
+                        "probe_copy_gbs": round(peaks["copy_gbs"], 1)}
+    roof["peaks"] = peaks
     roof["classes"] = classes
     roof["work"] = {"arnoldi_per_step": prof["arnoldi"] / args.steps,
                     "mean_j": (prof["arnoldi_jsum"] - prof["arnoldi"]) / max(prof["arnoldi"], 1),
@@ -524,8 +584,13 @@ def run_batch(args, world, rank, local):
             ent.update({"bytes": by, "gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 3)})
         classes[nm] = ent
     per_launch_ms = prof["ms"][0] / max(prof["n"][0], 1)
-    flop64 = FLUX_MIXED_FP64_FLOP_PER_GP if mixed else FLUX_FP64_FLOP_PER_GP
-    ach = flop64 * 2 * F / (per_launch_ms / 1e3) / 1e12
+    split = mixed and args.flux_split != "off"
+    roof = flux_roofline("mixed_flux_ws" if split else ("mixed_" if mixed else "") + "flux",
+                         "k_face_flux_ws" if split else "k_face_flux", prof["n"][0], per_launch_ms, 2 * F,
+                         probe_peaks(dev))
+    roof["classes"] = classes
+    roof["work"] = {"arnoldi_per_step": prof["arnoldi"] / args.steps,
+                    "mean_j": (prof["arnoldi_jsum"] - prof["arnoldi"]) / max(prof["arnoldi"], 1)}
     wm = w.cpu().numpy()
     stat = r["status"]
     out = {
@@ -538,12 +603,7 @@ def run_batch(args, world, rank, local):
                    "krylov_basis": "fp32" if mixed and args.basis == "fp32" else "fp64",
                    "autotuned": bool(args.tune), "knobs": knobs, "failed_cases": int(np.sum(stat != 0)),
                    "l2": "inputs larger than L2", "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"kernel": "k_face_flux_ws" if mixed and args.flux_split != "off" else "k_face_flux",
-                     "launches": prof["n"][0], "avg_ms": per_launch_ms, "bound": "alu",
-                     "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                     "fp64_flop_per_gauss_point": flop64, "traffic": None, "classes": classes,
-                     "work": {"arnoldi_per_step": prof["arnoldi"] / args.steps,
-                              "mean_j": (prof["arnoldi_jsum"] - prof["arnoldi"]) / max(prof["arnoldi"], 1)}},
+        "roofline": roof,
         "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": 4 * T * 8, "d2h_bytes_per_step": 4 * T * 8},
         "gpu_launches": launches,
         "clocks": clocks,

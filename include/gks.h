@@ -419,6 +419,25 @@ GKS_EXPORT gks_status gks_profile_end(gks_mesh *mesh, gks_profile *out);
 /* Number of kernel launches issued by the library in this process. */
 GKS_EXPORT int64_t gks_launch_count(void);
 
+/* Measurement probes (not part of the scheme).  A benchmark times them with
+ * CUDA events on `stream` to measure the roofs of the kernels above on the GPU
+ * it runs on.
+ *   gks_probe_fma:  blocks_per_sm x (SM count) blocks of 256 threads, each
+ *                   thread 8 independent chains of 64 iters multiply-adds in
+ *                   FP64 (fp64 = 1) or FP32; *flops (host, may be NULL)
+ *                   receives the flops of the launch (a multiply-add counts 2).
+ *                   sink: device scratch of at least blocks_per_sm x (SM count)
+ *                   doubles, never written in practice (it keeps the chains live).
+ *   gks_probe_read: reads every 16-byte word of buf (device, 16-byte aligned,
+ *                   bytes a positive multiple of 16) with streaming loads;
+ *                   sink: device scratch of 4 x (SM count) doubles.
+ *   gks_probe_copy: copies bytes from src to dst (device, same rules).
+ * GKS_EINVAL for NULL pointers or misaligned buffers; asynchronous otherwise. */
+GKS_EXPORT gks_status gks_probe_fma(int32_t fp64, int32_t blocks_per_sm, int32_t iters, double *sink, void *stream,
+                                    double *flops);
+GKS_EXPORT gks_status gks_probe_read(const void *buf, int64_t bytes, double *sink, void *stream);
+GKS_EXPORT gks_status gks_probe_copy(const void *src, void *dst, int64_t bytes, void *stream);
+
 /* Thread-local message of the last error, or "" if none. */
 GKS_EXPORT const char *gks_last_error(void);
 

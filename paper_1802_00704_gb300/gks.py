@@ -26,7 +26,8 @@ FP64, MIXED = 0, 1
 EXPORTED = ["gks_config_default", "gks_mesh_create", "gks_mesh_destroy", "gks_mesh_get_stats", "gks_cfl_dt",
             "gks_cls_reconstruct", "gks_reset_warm_start", "gks_flux", "gks_step", "gks_run", "gks_point_flux",
             "gks_profile_begin", "gks_profile_end", "gks_launch_count", "gks_cfl_dt_noalloc", "gks_batch_create",
-            "gks_batch_run", "gks_limit", "gks_autotune", "gks_last_error"]
+            "gks_batch_run", "gks_limit", "gks_autotune", "gks_last_error", "gks_probe_fma", "gks_probe_read",
+            "gks_probe_copy"]
 PROF_FLUX, PROF_SPMV, PROF_ILU, PROF_ORTH, PROF_UPDATE, PROF_RESID, PROF_CORR, PROF_CTL = range(8)
 PROF_CLASSES = 8
 
@@ -142,6 +143,12 @@ def load():
     lib.gks_profile_end.restype = st
     lib.gks_launch_count.argtypes = []
     lib.gks_launch_count.restype = I64
+    lib.gks_probe_fma.argtypes = [I32, I32, I32, P, P, C.POINTER(D)]
+    lib.gks_probe_fma.restype = st
+    lib.gks_probe_read.argtypes = [P, I64, P, P]
+    lib.gks_probe_read.restype = st
+    lib.gks_probe_copy.argtypes = [P, P, I64, P]
+    lib.gks_probe_copy.restype = st
     lib.gks_last_error.argtypes = []
     lib.gks_last_error.restype = C.c_char_p
     _lib = lib
@@ -365,3 +372,30 @@ def point_flux(wl, wr, dt: float, out=None, stream=None, **cfg):
     _check(load().gks_point_flux(n, _dev(wl, (n, 6, 4)), _dev(wr, (n, 6, 4)), float(dt), C.byref(c),
                                  _dev(out, (n, 4)), _stream(stream)), "gks_point_flux")
     return out
+
+
+def probe_fma(fp64: bool, sink, blocks_per_sm: int = 8, iters: int = 4096, stream=None) -> float:
+    """Launch the FMA-chain probe on the stream; returns the launch's flops.
+    sink: float64 CUDA tensor of at least blocks_per_sm x (SM count) entries."""
+    fl = C.c_double(0.0)
+    _check(load().gks_probe_fma(int(bool(fp64)), int(blocks_per_sm), int(iters), _dev(sink), _stream(stream),
+                                C.byref(fl)), "gks_probe_fma")
+    return fl.value
+
+
+def probe_read(buf, sink, stream=None) -> int:
+    """Launch the streaming-read probe over a CUDA tensor; returns the bytes read."""
+    nbytes = buf.numel() * buf.element_size()
+    _check(load().gks_probe_read(C.c_void_p(buf.data_ptr()), nbytes, _dev(sink), _stream(stream)),
+           "gks_probe_read")
+    return nbytes
+
+
+def probe_copy(src, dst, stream=None) -> int:
+    """Launch the copy probe src -> dst (CUDA tensors of the same size); returns bytes read + written."""
+    nbytes = src.numel() * src.element_size()
+    if dst.numel() * dst.element_size() != nbytes:
+        raise ValueError("probe_copy: sizes differ")
+    _check(load().gks_probe_copy(C.c_void_p(src.data_ptr()), C.c_void_p(dst.data_ptr()), nbytes, _stream(stream)),
+           "gks_probe_copy")
+    return 2 * nbytes

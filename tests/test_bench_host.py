@@ -86,20 +86,52 @@ def test_option_maps_match_the_config():
     assert bench.METRIC == "triangle-steps/s"
 
 
-def test_traffic_record_format():
+def test_counter_record_format():
     """profiles/traffic.txt: kernel, a 16-hex-digit hash of the flux sources,
-    DRAM bytes per launch and the Gauss points of that launch; the record is
-    used only while the hash matches the sources (else the roofline's traffic
-    is null), and bench.py's hash is deterministic."""
+    DRAM bytes per launch, the Gauss points of that launch and the FP64 / FP32
+    flops per Gauss point ('-' if not taken); a line is used only while the
+    hash matches the sources (else the roofline's achieved rate and traffic are
+    null), and bench.py's hash is deterministic."""
     p = os.path.join(bench.ROOT, "profiles", "traffic.txt")
     kernels = set()
     for line in open(p):
         if line.startswith("#") or not line.strip():
             continue
-        k, h, by, gp = line.split()[:4]
+        k, h, by, gp, f64, f32 = line.split()[:6]
         assert re.fullmatch(r"[0-9a-f]{16}", h)
         assert float(by) > 0 and float(gp) > 0
+        assert all(x == "-" or float(x) > 0 for x in (f64, f32))
         kernels.add(k)
     assert {"mixed_flux_ws", "mixed_flux", "flux"} <= kernels
     assert bench.source_hash() == bench.source_hash() and re.fullmatch(r"[0-9a-f]{16}", bench.source_hash())
-    assert bench.traffic_record("no_such_kernel") is None
+    assert bench.counter_record("no_such_kernel") is None
+
+
+def _peaks():
+    return {"fp64_tflops": 1.2, "fp32_tflops": 74.0, "fp64_tflops_derived": 1.26, "fp32_tflops_derived": 80.5}
+
+
+def test_flux_roofline_uses_the_counters_of_the_timed_kernel(monkeypatch):
+    """The flux roofline takes its flops per Gauss point from the record of the
+    kernel it names (never a constant of another kernel), divides by the event
+    time of one launch, and reports the busier pipe against its measured rate."""
+    seen = []
+
+    def rec(key):
+        seen.append(key)
+        return {"dram_bytes": 2.0e8, "gauss_points": 1.0e6, "fp64_flop_per_gp": 600.0, "fp32_flop_per_gp": 8000.0}
+
+    monkeypatch.setattr(bench, "counter_record", rec)
+    gp, ms = 3_000_000, 2.0
+    r = bench.flux_roofline("mixed_flux_ws", "k_face_flux_ws", 10, ms, gp, _peaks())
+    assert seen == ["mixed_flux_ws"] and r["kernel"] == "k_face_flux_ws"
+    a64 = 600.0 * gp / (ms / 1e3) / 1e12
+    a32 = 8000.0 * gp / (ms / 1e3) / 1e12
+    assert r["pipe"] == ("fp64" if a64 / 1.2 > a32 / 74.0 else "fp32")
+    assert abs(r["achieved"] - (a64 if r["pipe"] == "fp64" else a32)) < 1e-12
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    assert abs(r["traffic"] - 2.0e8 * 3) < 1e-3
+    # stale counters (hash mismatch): no achieved rate, no traffic
+    monkeypatch.setattr(bench, "counter_record", lambda key: None)
+    r = bench.flux_roofline("mixed_flux_ws", "k_face_flux_ws", 10, ms, gp, _peaks())
+    assert r["achieved"] is None and r["frac"] is None and r["traffic"] is None
