@@ -103,8 +103,9 @@ typedef struct gks_config {
                               operator and ILU(0) applications in FP32 inside FP64
                               iterative refinement (FP64 residual, Arnoldi and
                               Givens); the flux's interface state, collision time,
-                              time integrals and zeroth-order terms in FP64 and its
-                              slope-carrying terms in FP32; FP64 update            */
+                              time integrals and zeroth-order terms in double-FP32
+                              or FP64 (flux_lead) and its slope-carrying terms in
+                              FP32; FP64 update                                     */
     int32_t precond;       /* GKS_PC_*                                                 */
     int32_t ilu_sweeps;    /* sweeps per triangular solve for GKS_PC_ILU_SWEEP         */
     int32_t tau2_exact;    /* 0: c4, c5, c6 exactly as printed in Eq. (13);
@@ -178,6 +179,13 @@ typedef struct gks_config {
                               busy; 0 every thread does both.  Same arithmetic;
                               results agree to rounding (multiply-adds may contract
                               differently in the two kernels)                          */
+    int32_t flux_lead;     /* mixed precision: 1 (default) the flux's parts that need
+                              more than FP32 (Gauss-point values, interface state,
+                              collision time, zeroth-order terms) in double-FP32
+                              arithmetic (pairs of FP32 numbers, about 48 bits) on
+                              the FP32 pipe, one thread per Gauss point doing both
+                              parts (flux_split is then ignored); 0 those parts in
+                              FP64 (flux_split chooses the kernel)                     */
 } gks_config;
 
 typedef struct gks_mesh gks_mesh;
@@ -372,7 +380,9 @@ GKS_EXPORT gks_status gks_point_flux(int64_t n, const double *wl, const double *
  * for each candidate of the knobs that change the cost of a step but not its
  * result beyond the solver tolerance: ilu_sweeps in {1, 2, 3} (sweep
  * preconditioner only), warm_extrap in {0, 1, 2} and, in mixed precision,
- * inner_rtol in {1e-4, 1e-5, 1e-6}.  Each candidate starts from w (device,
+ * inner_rtol in {1e-4, 1e-5, 1e-6}; then, with the best of those, the GMRES
+ * restart length in {gmres_m, 16, 8} (at most the gmres_m the handle was
+ * created with, which sized its Krylov buffers).  Each candidate starts from w (device,
  * [4][n_tri], caller order, not modified) with a cleared warm start, takes
  * 3 untimed steps, then trial_steps (>= 1) steps timed with CUDA events; a
  * candidate whose steps fail is skipped.  The fastest candidate is written to
@@ -387,6 +397,7 @@ typedef struct gks_tune_result {
     int32_t n_candidates;         /* candidates timed                               */
     int32_t n_failed;             /* candidates skipped because a step failed       */
     int32_t ilu_sweeps_bwd;       /* chosen backward sweeps (-1: as ilu_sweeps)     */
+    int32_t gmres_m;              /* chosen restart length (also in the config)     */
 } gks_tune_result;
 
 GKS_EXPORT gks_status gks_autotune(gks_mesh *mesh, const double *w, int32_t trial_steps, gks_tune_result *out,
@@ -437,6 +448,22 @@ GKS_EXPORT gks_status gks_probe_fma(int32_t fp64, int32_t blocks_per_sm, int32_t
                                     double *flops);
 GKS_EXPORT gks_status gks_probe_read(const void *buf, int64_t bytes, double *sink, void *stream);
 GKS_EXPORT gks_status gks_probe_copy(const void *src, void *dst, int64_t bytes, void *stream);
+
+/* Test probe of the double-FP32 arithmetic of the mixed flux (pairs of FP32
+ * numbers, about 48 significant bits; not part of the scheme): for each i,
+ * x[i] (and y[i]) are split into FP32 pairs, op is applied in pair arithmetic
+ * and out[2 i] receives the result widened to FP64 (out[2 i + 1] = 0); for
+ * GKS_DF_SPLIT out[2 i], out[2 i + 1] receive the pair itself.  x, y, out:
+ * device arrays of n, n and 2 n doubles (y only for the two-argument ops).
+ * Domains: GKS_DF_EXP x <= 88 (below -87 the result is flushed to 0),
+ * GKS_DF_ERFCX 0 <= x <= 10, GKS_DF_SQRT x > 0.  GKS_EINVAL for a bad op or a
+ * NULL array; asynchronous. */
+enum {
+    GKS_DF_SPLIT = 0, GKS_DF_EXP = 1, GKS_DF_EXPM1 = 2, GKS_DF_ERFCX = 3, GKS_DF_SQRT = 4, GKS_DF_DIV = 5,
+    GKS_DF_MUL = 6, GKS_DF_ADD = 7, GKS_DF_RECIP = 8
+};
+GKS_EXPORT gks_status gks_probe_df(int32_t op, int64_t n, const double *x, const double *y, double *out,
+                                   void *stream);
 
 /* Thread-local message of the last error, or "" if none. */
 GKS_EXPORT const char *gks_last_error(void);

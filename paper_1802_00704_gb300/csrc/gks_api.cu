@@ -69,6 +69,7 @@ gks_status check_config(const gks_config &c)
     ok = ok && c.ilu_sweeps_bwd >= -1 && c.ilu_sweeps_bwd <= 8;
     ok = ok && (c.ilu_fuse_first == 0 || c.ilu_fuse_first == 1);
     ok = ok && (c.flux_split == 0 || c.flux_split == 1);
+    ok = ok && (c.flux_lead == 0 || c.flux_lead == 1);
     if (!ok) {
         set_error("invalid gks_config");
         return GKS_EINVAL;
@@ -196,6 +197,7 @@ void gks_config_default(gks_config *c)
     c->ilu_sweeps_bwd = -1;
     c->ilu_fuse_first = 1;
     c->flux_split = 1;
+    c->flux_lead = 1;
 }
 
 const char *gks_last_error(void) { return gks::last_error(); }

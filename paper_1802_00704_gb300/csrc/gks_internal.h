@@ -81,6 +81,11 @@ struct DeviceMesh {
     __half *P16 = nullptr, *alpha16 = nullptr, *ex16 = nullptr, *ey16 = nullptr;
     __half *alr16 = nullptr, *exr16 = nullptr, *eyr16 = nullptr, *bdg16 = nullptr;
     float *ih32 = nullptr;           // [T] 1 / h_i (mixed flux)
+    // FP32 pairs (hi, lo) of the geometry for the double-FP32 flux (mixed precision)
+    float *m2 = nullptr;             // [6][T] mxx, mxy, myy, then their low parts
+    float *gl2 = nullptr, *gr2 = nullptr;  // [8][F] the 4 rows of gl / gr, then their low parts
+    float *fn2 = nullptr;            // [4][F] nx, ny, then their low parts
+    float *flen2 = nullptr;          // [2][F] half the face length (Gauss weight 1/2), its low part
     // the operator as FP32 pairs hi + lo for the double-FP32 refinement residual
     // (mixed mode with an FP32 basis; NULL when a value is outside the pair range)
     float *D2 = nullptr;             // [30][T] the 15 diagonal-block values, then their low parts
@@ -104,7 +109,8 @@ struct DeviceMesh {
 };
 
 struct Work {
-    int m = 0;                       // restart length
+    int m = 0;                       // restart length in use (the autotuner may lower it)
+    int m_alloc = 0;                 // restart length the Krylov buffers were sized for
     int nblk = 0;                    // cell blocks (kBlock cells each)
     int ns = 4;                      // GMRES systems: 4 per case
     double *w = nullptr;             // [4][T] state (internal order)
@@ -115,6 +121,9 @@ struct Work {
     int64_t nsolve = 0;              // solves since creation or the last warm-start reset
     double *xl = nullptr;            // [20][T] limited coefficients (limiter on)
     float *x32 = nullptr;            // [20][T] FP32 copy of the coefficients the mixed flux reads
+                                     //         (the first half of x2)
+    float *x2 = nullptr;             // [40][T] FP32 pairs of the coefficients: x32, then the low parts
+    float *w2 = nullptr;             // [8][T] FP32 pairs of the state: hi, then lo
     int32_t *lflag = nullptr;        // [T] 0 untouched, 1 limited, 2 reset to the average
     double *b = nullptr, *r = nullptr, *t2 = nullptr, *t3 = nullptr;  // [20][T]
     float *t2_32 = nullptr, *t3_32 = nullptr;  // [20][T] FP32 preconditioner work

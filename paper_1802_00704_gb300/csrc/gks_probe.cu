@@ -2,6 +2,7 @@
 // FP32 fused multiply-add pipes and of streaming HBM reads and copies on the
 // GPU the library runs on.  The benchmark times them with CUDA events and uses
 // the results as the measured roofs of the kernels the FMA pipes or HBM bound.
+#include "gks_df.cuh"
 #include "gks_internal.h"
 
 namespace gks {
@@ -53,6 +54,36 @@ __global__ void __launch_bounds__(kProbeThreads) k_copy(const float4 *__restrict
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) __stcs(d + i, __ldcs(s + i));
+}
+
+// One double-FP32 function per element: the argument is split into an FP32
+// pair by integer operations, the result widened to FP64.
+__global__ void k_df_eval(int op, int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                          double *__restrict__ out)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const dfm::df a = dfm::split_double(x[i]);
+    dfm::df r = {0.0f, 0.0f};
+    switch (op) {
+    case GKS_DF_SPLIT: r = a; break;
+    case GKS_DF_EXP: r = dfm::exp(a); break;
+    case GKS_DF_EXPM1: r = dfm::expm1(a); break;
+    case GKS_DF_ERFCX: r = dfm::erfcx(a); break;
+    case GKS_DF_SQRT: r = dfm::sqrt(a); break;
+    case GKS_DF_DIV: r = dfm::div(a, dfm::split_double(y[i])); break;
+    case GKS_DF_MUL: r = dfm::mul(a, dfm::split_double(y[i])); break;
+    case GKS_DF_ADD: r = dfm::add(a, dfm::split_double(y[i])); break;
+    case GKS_DF_RECIP: r = dfm::recip(a); break;
+    default: break;
+    }
+    if (op == GKS_DF_SPLIT) {
+        out[2 * i] = (double)r.hi;             // the pair itself
+        out[2 * i + 1] = (double)r.lo;
+    } else {
+        out[2 * i] = dfm::to_double(r);
+        out[2 * i + 1] = 0.0;
+    }
 }
 
 gks_status grid_of(int per_sm, unsigned *g)
@@ -116,6 +147,21 @@ extern "C" gks_status gks_probe_copy(const void *src, void *dst, int64_t bytes, 
     if (st != GKS_OK) return st;
     k_copy<<<g, kProbeThreads, 0, (cudaStream_t)stream>>>(static_cast<const float4 *>(src), static_cast<float4 *>(dst),
                                                         bytes / 16);
+    note_launch();
+    GKS_CUDA(cudaGetLastError());
+    return GKS_OK;
+}
+
+extern "C" gks_status gks_probe_df(int32_t op, int64_t n, const double *x, const double *y, double *out, void *stream)
+{
+    if (op < GKS_DF_SPLIT || op > GKS_DF_RECIP || n < 0 || (n > 0 && (!x || !out)) ||
+        ((op == GKS_DF_DIV || op == GKS_DF_MUL || op == GKS_DF_ADD) && n > 0 && !y)) {
+        set_error("gks_probe_df: bad operation or NULL array");
+        return GKS_EINVAL;
+    }
+    if (n == 0) return GKS_OK;
+    k_df_eval<<<(unsigned)((n + kProbeThreads - 1) / kProbeThreads), kProbeThreads, 0, (cudaStream_t)stream>>>(op, n, x,
+                                                                                                             y, out);
     note_launch();
     GKS_CUDA(cudaGetLastError());
     return GKS_OK;

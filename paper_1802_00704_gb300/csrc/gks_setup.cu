@@ -760,6 +760,31 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
         std::vector<float> h_ih32(T);
         for (int64_t i = 0; i < T; ++i) h_ih32[i] = float(1.0 / h_h[i]);
         UP(ih32, h_ih32);
+        // FP32 pairs of the geometry the double-FP32 flux reads
+        auto pairs = [](std::vector<const std::vector<double> *> rows, double scale) {
+            const size_t n = rows[0]->size(), nr = rows.size();
+            std::vector<float> o(2 * nr * n);
+            for (size_t r = 0; r < nr; ++r)
+                for (size_t q = 0; q < n; ++q) {
+                    const double v = scale * (*rows[r])[q];
+                    o[r * n + q] = float(v);
+                    o[(nr + r) * n + q] = float(v - double(o[r * n + q]));
+                }
+            return o;
+        };
+        auto rows4 = [](const std::vector<double> &g, int64_t n) {
+            std::vector<std::vector<double>> r(4);
+            for (int q = 0; q < 4; ++q) r[q].assign(g.begin() + q * n, g.begin() + (q + 1) * n);
+            return r;
+        };
+        {
+            const std::vector<std::vector<double>> glr = rows4(h_gl, F), grr = rows4(h_gr, F);
+            UP(m2, pairs({&h_mxx, &h_mxy, &h_myy}, 1.0));
+            UP(gl2, pairs({&glr[0], &glr[1], &glr[2], &glr[3]}, 1.0));
+            UP(gr2, pairs({&grr[0], &grr[1], &grr[2], &grr[3]}, 1.0));
+            UP(fn2, pairs({&h_fnx, &h_fny}, 1.0));
+            UP(flen2, pairs({&h_flen}, 0.5));
+        }
         if (cfg.basis_fp32) {
             // FP32 pairs of the operator: v = hi + lo to 2^-48 for v = 0 or 2^-74 <= |v| <= 2^30
             // (the bound on |v| keeps the parts of x the residual drops negligible)
@@ -812,6 +837,7 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
     // ---- work buffers
     Work &k = m->wk;
     k.m = cfg.gmres_m;
+    k.m_alloc = cfg.gmres_m;
     k.nblk = (int)nblk;
     k.ns = 4 * n_cases;
     const int mm = k.m;
@@ -836,7 +862,9 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
     }
     AL(x_prev, 20 * T); AL(x_prev2, 20 * T);   // extrapolated warm start (also for the autotuner)
     if (cfg.precision == GKS_MIXED) {
-        AL(x32, 20 * T);
+        AL(x2, 40 * T);
+        k.x32 = k.x2;
+        AL(w2, 8 * T);
         AL(y32, ns * mm);
     }
     AL(H, ns * (mm + 1) * mm); AL(cs, ns * mm); AL(sn, ns * mm); AL(g, ns * (mm + 1)); AL(y, ns * mm);

@@ -27,7 +27,8 @@ EXPORTED = ["gks_config_default", "gks_mesh_create", "gks_mesh_destroy", "gks_me
             "gks_cls_reconstruct", "gks_reset_warm_start", "gks_flux", "gks_step", "gks_run", "gks_point_flux",
             "gks_profile_begin", "gks_profile_end", "gks_launch_count", "gks_cfl_dt_noalloc", "gks_batch_create",
             "gks_batch_run", "gks_limit", "gks_autotune", "gks_last_error", "gks_probe_fma", "gks_probe_read",
-            "gks_probe_copy"]
+            "gks_probe_copy", "gks_probe_df"]
+DF_OPS = {"split": 0, "exp": 1, "expm1": 2, "erfcx": 3, "sqrt": 4, "div": 5, "mul": 6, "add": 7, "recip": 8}
 PROF_FLUX, PROF_SPMV, PROF_ILU, PROF_ORTH, PROF_UPDATE, PROF_RESID, PROF_CORR, PROF_CTL = range(8)
 PROF_CLASSES = 8
 
@@ -48,7 +49,7 @@ class Config(C.Structure):
                 ("inner_rtol", C.c_double), ("prandtl", C.c_double), ("slope0_mode", C.c_int32),
                 ("ilu_fp16", C.c_int32), ("cls_global", C.c_int32), ("cls_M", C.c_int32),
                 ("ilu_sweeps_bwd", C.c_int32), ("ilu_fuse_first", C.c_int32),
-                ("flux_split", C.c_int32)]
+                ("flux_split", C.c_int32), ("flux_lead", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -67,7 +68,7 @@ class RunInfo(C.Structure):
 class TuneResult(C.Structure):
     _fields_ = [("ilu_sweeps", C.c_int32), ("warm_extrap", C.c_int32), ("inner_rtol", C.c_double),
                 ("ms_per_step", C.c_double), ("ms_per_step_before", C.c_double), ("n_candidates", C.c_int32),
-                ("n_failed", C.c_int32), ("ilu_sweeps_bwd", C.c_int32)]
+                ("n_failed", C.c_int32), ("ilu_sweeps_bwd", C.c_int32), ("gmres_m", C.c_int32)]
 
 
 class Profile(C.Structure):
@@ -149,6 +150,8 @@ def load():
     lib.gks_probe_read.restype = st
     lib.gks_probe_copy.argtypes = [P, P, I64, P]
     lib.gks_probe_copy.restype = st
+    lib.gks_probe_df.argtypes = [I32, I64, P, P, P, P]
+    lib.gks_probe_df.restype = st
     lib.gks_last_error.argtypes = []
     lib.gks_last_error.restype = C.c_char_p
     _lib = lib
@@ -299,13 +302,15 @@ class GksMesh:
         return out, st
 
     def autotune(self, w, trial_steps: int = 3, stream=None) -> dict:
-        """Pick ilu_sweeps, ilu_sweeps_bwd, warm_extrap and (mixed) inner_rtol by timing
-        trial steps from the state w (not modified); the handle keeps the fastest."""
+        """Pick ilu_sweeps, ilu_sweeps_bwd, warm_extrap, (mixed) inner_rtol and then the
+        GMRES restart length by timing trial steps from the state w (not modified);
+        the handle keeps the fastest."""
         r = TuneResult()
         _check(self._lib.gks_autotune(self._h, _dev(w, (4, self.T)), int(trial_steps), C.byref(r), _stream(stream)),
                "gks_autotune")
         self.cfg.ilu_sweeps, self.cfg.warm_extrap, self.cfg.inner_rtol = r.ilu_sweeps, r.warm_extrap, r.inner_rtol
         self.cfg.ilu_sweeps_bwd = r.ilu_sweeps_bwd
+        self.cfg.gmres_m = r.gmres_m
         return {k: getattr(r, k) for k, _ in TuneResult._fields_}
 
     def limit(self, w, coef, out=None, flags=None, stream=None):
@@ -399,3 +404,13 @@ def probe_copy(src, dst, stream=None) -> int:
     _check(load().gks_probe_copy(C.c_void_p(src.data_ptr()), C.c_void_p(dst.data_ptr()), nbytes, _stream(stream)),
            "gks_probe_copy")
     return 2 * nbytes
+
+
+def probe_df(op: str, x, y=None, stream=None):
+    """Apply a double-FP32 operation of the mixed flux elementwise to the float64
+    CUDA tensor x (and y); returns a (n, 2) float64 tensor (see gks_probe_df)."""
+    import torch
+    out = torch.empty((x.numel(), 2), dtype=torch.float64, device=x.device)
+    _check(load().gks_probe_df(DF_OPS[op], x.numel(), _dev(x), _dev(y) if y is not None else None, _dev(out),
+                               _stream(stream)), "gks_probe_df")
+    return out
