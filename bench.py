@@ -50,6 +50,8 @@ WORKLOADS = {
     "shock_vortex_400k": dict(kind="shock_vortex", nx=632, ny=316),
     "advection_20": dict(kind="advection", n=20),
     "batch_512": dict(kind="batch", n=512),
+    "cavity_256": dict(kind="cavity", n=256),
+    "cavity_64": dict(kind="cavity", n=64),
 }
 
 
@@ -58,6 +60,8 @@ def make_case(name: str, replica: int = 0):
     w = WORKLOADS[name]
     if w["kind"] == "shock_vortex":
         return I.shock_vortex_case(w["nx"], w["ny"], seed=1802 + replica)
+    if w["kind"] == "cavity":
+        return I.cavity_case(w["n"], seed=1802 + replica)
     return I.advection_case(w["n"], seed=1802 + replica)
 
 
@@ -139,6 +143,15 @@ def probe_peaks(dev, reps: int = 5) -> dict:
             "how": "gks_probe_fma (8 independent FMA chains per thread, 4 resp. 8 blocks of 256 threads per SM), "
                    "gks_probe_read / gks_probe_copy (16-byte streaming loads, 2 GiB); best of 5, CUDA events; "
                    f"derived: 4 (FP64) and 256 (FP32) flop/clk/SM x {nsm} SMs x {NOMINAL_SM_MHZ:.0f} MHz"}
+
+
+def flux_kernel(args, mixed: bool):
+    """(record key, kernel name) of the face-flux kernel a configuration launches."""
+    if mixed and args.flux_lead == "pairs":
+        return "mixed_flux_df", "k_face_flux_df"
+    if mixed and args.flux_split != "off":
+        return "mixed_flux_ws", "k_face_flux_ws"
+    return ("mixed_flux", "k_face_flux") if mixed else ("flux", "k_face_flux")
 
 
 def flux_roofline(key: str, name: str, launches: int, per_launch_ms: float, gp: int, peaks: dict) -> dict:
@@ -259,9 +272,25 @@ def allmax(world, x: float) -> float:
     return float(t.item())
 
 
-def oracle_sample(steps: int, warmup: int = 0):
+def cpu_info() -> dict:
+    """Model, clock and thread count of the host CPU (Linux /proc, lscpu)."""
+    out = {"threads": os.cpu_count()}
+    try:
+        txt = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in txt.splitlines():
+            k, _, v = line.partition(":")
+            k, v = k.strip(), v.strip()
+            if k in ("Model name", "Architecture", "CPU max MHz", "Socket(s)", "Core(s) per socket"):
+                out[k.lower().replace(" ", "_").replace("(s)", "s")] = v
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return out
+
+
+def oracle_sample(steps: int, warmup: int = 0, threads: int | None = None):
     """The CPU oracle on a bounded sample of the workload: the same shock-vortex
-    problem on a 200 x 100 split-quad mesh (40,000 triangles)."""
+    problem on a 200 x 100 split-quad mesh (40,000 triangles).  Returns the
+    baseline record, the final state and the oracle's time steps."""
     from oracle import oracle
     oracle.build()
     c = make_case("shock_vortex_small")
@@ -269,17 +298,58 @@ def oracle_sample(steps: int, warmup: int = 0):
     w = c.w0.copy()
     for _ in range(warmup):
         om.step(w)
+    dts = []
     t0 = time.perf_counter()
     for _ in range(steps):
         info = om.step(w)
         if info.status != 0:
             raise RuntimeError(f"oracle step status {info.status}")
+        dts.append(info.dt)
     el = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": c.mesh.n_tri * steps / el, "unit": METRIC, "cores": cores, "kind": "oracle",
-            "sample": f"{steps} oracle steps of the 200x100 (40,000-triangle) shock-vortex mesh, "
-                      f"FP64, OpenMP over faces, sequential GMRES+ILU(0)",
-            "seconds": el}
+    cores = threads or int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    rec = {"value": c.mesh.n_tri * steps / el, "unit": METRIC, "cores": cores, "kind": "oracle",
+           "sample": f"{steps} oracle steps of the 200x100 (40,000-triangle) shock-vortex mesh, "
+                     f"FP64, OpenMP over faces, sequential GMRES+ILU(0)",
+           "seconds": el}
+    return rec, w, dts, c
+
+
+def oracle_single_thread(steps: int) -> dict:
+    """The oracle with one OpenMP thread on the same sample (a child process,
+    since the thread count is fixed when OpenMP starts)."""
+    code = ("import bench, json; r, _, _, _ = bench.oracle_sample(%d, threads=1); r.pop('seconds'); "
+            "print(json.dumps(r))" % steps)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT, env=env, timeout=900)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else "failed"}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def errors_vs_oracle(case, w_oracle, dts, dev, mixed_kw: dict) -> dict:
+    """The GPU path (mixed and FP64) advanced by the oracle's time steps from
+    the same initial state: relative L1 (sum |Omega| |q - q_o| / sum |Omega| |q_o|)
+    and relative max (max |q - q_o| / max |q_o|) per conserved variable."""
+    import numpy as np
+    import torch
+
+    from paper_1802_00704_gb300 import gks
+    area = tri_area(case.mesh.nodes, case.mesh.tris)
+    out = {}
+    for name, kw in (("mixed", mixed_kw), ("fp64", {})):
+        m = gks.GksMesh(case.mesh, **kw)
+        w = torch.from_numpy(case.w0.copy()).to(dev)
+        for dt in dts:
+            if m.step(w, dt)["status"] != 0:
+                raise RuntimeError("GPU step failed on the oracle sample")
+        g = w.cpu().numpy()
+        l1 = np.sum(area * np.abs(g - w_oracle), axis=1) / np.sum(area * np.abs(w_oracle), axis=1)
+        mx = np.max(np.abs(g - w_oracle), axis=1) / np.max(np.abs(w_oracle), axis=1)
+        out[name] = {"rel_l1": [float(x) for x in l1], "rel_max": [float(x) for x in mx]}
+        del m
+    out["sample"] = (f"{len(dts)} steps of the 200x100 (40,000-triangle) shock-vortex mesh with the oracle's "
+                     "time steps; variables rho, rho u, rho v, E")
+    return out
 
 
 def class_bytes(cls: str, prof: dict, T: int, F: int, steps: int, sweeps: int, exact: bool, mixed: bool,
@@ -342,7 +412,8 @@ def timed_leg(args, case, precision: str, world: int, dev, sample_clocks: bool):
                     precision=gks.MIXED if mixed else gks.FP64, basis_fp32=int(mixed and args.basis == "fp32"),
                     limiter=int(args.limiter), warm_extrap=WARM[args.warm], no_graphs=GRAPHS[args.graphs],
                     ilu_fp16=int(mixed and args.ilu16 == "on"), ilu_fuse_first=int(args.ilu_fuse == "on"),
-                    flux_split=FLUX_SPLIT[args.flux_split])
+                    flux_split=FLUX_SPLIT[args.flux_split], gmres_m=args.gmres_m,
+                    flux_lead=int(args.flux_lead == "pairs"))
     w = torch.from_numpy(case.w0.copy()).to(dev)
     stream = torch.cuda.current_stream()
     tune = m.autotune(w, trial_steps=2) if args.tune else None
@@ -375,7 +446,7 @@ def timed_leg(args, case, precision: str, world: int, dev, sample_clocks: bool):
             "stats": m.stats(), "tune": tune,
             "knobs": {"ilu_sweeps": m.cfg.ilu_sweeps, "ilu_sweeps_bwd": m.cfg.ilu_sweeps_bwd,
                       "ilu_fuse_first": m.cfg.ilu_fuse_first, "warm_extrap": m.cfg.warm_extrap,
-                      "inner_rtol": m.cfg.inner_rtol}}
+                      "inner_rtol": m.cfg.inner_rtol, "gmres_m": m.cfg.gmres_m}}
 
 
 def run_gks(args, world, rank, local):
@@ -430,9 +501,8 @@ def run_gks(args, world, rank, local):
     # the dominant kernel is the face-flux kernel (one launch per step): ALU-bound
     q = names.index("flux")
     per_launch_ms = prof["ms"][q] / max(prof["n"][q], 1)
-    split = mixed and args.flux_split != "off"
-    roof = flux_roofline("mixed_flux_ws" if split else ("mixed_" if mixed else "") + "flux",
-                         "k_face_flux_ws" if split else "k_face_flux", prof["n"][q], per_launch_ms, 2 * F, peaks)
+    key, kname = flux_kernel(args, mixed)
+    roof = flux_roofline(key, kname, prof["n"][q], per_launch_ms, 2 * F, peaks)
     roof["hbm_peak"] = {"gbs": hbm_peak, "source": hbm_src, "probe_read_gbs": round(peaks["read_gbs"], 1),
                         "probe_copy_gbs": round(peaks["copy_gbs"], 1)}
     roof["peaks"] = peaks
@@ -448,7 +518,7 @@ def run_gks(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": main["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64 (mixed)" if mixed else "f64", "data": "synthetic",
         "config": {"workload": f"shock-vortex {case.mesh.nx}x{case.mesh.ny} split quads, {T} triangles, "
-                               f"{F} faces, GMRES(30) rtol 1e-12",
+                               f"{F} faces, GMRES({main['knobs']['gmres_m']}) rtol 1e-12",
                    "n_tri": T, "n_face": F, "precision": args.precision,
                    "krylov_basis": "fp32" if basis32 else "fp64", "limiter": bool(args.limiter),
                    "solve_graphs": args.graphs, "ilu_factors": "fp16" if mixed and args.ilu16 == "on" else None,
@@ -477,11 +547,28 @@ def run_gks(args, world, rank, local):
         out["mixed_vs_fp64_rel_l1"] = [float(x) for x in l1]
         out["speedup_vs_fp64"] = value / out["fp64"]["value"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = oracle_sample(args.cpu_steps)
+        cb, w_o, dts, small = oracle_sample(args.cpu_steps)
         cb.pop("seconds", None)
+        cb["cpu"] = cpu_info()
+        st1 = oracle_single_thread(1)
+        cb["single_thread"] = {k: st1[k] for k in ("value", "cores", "error") if k in st1}
+        cb["single_thread"]["sample"] = "1 oracle step of the same mesh, OMP_NUM_THREADS=1"
         out["cpu_baseline"] = cb
+        if mixed:
+            mkw = gks_mixed_kw(args)
+            mkw.update(main["knobs"])
+            out["error_vs_oracle"] = errors_vs_oracle(small, w_o, dts, dev, mkw)
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def gks_mixed_kw(args) -> dict:
+    """Configuration of the benchmarked mixed path (as timed_leg builds it)."""
+    from paper_1802_00704_gb300 import gks
+    return dict(precision=gks.MIXED, basis_fp32=int(args.basis == "fp32"), ilu_sweeps=args.sweeps,
+                ilu_fp16=int(args.ilu16 == "on"), ilu_fuse_first=int(args.ilu_fuse == "on"),
+                flux_split=FLUX_SPLIT[args.flux_split], warm_extrap=WARM[args.warm],
+                flux_lead=int(args.flux_lead == "pairs"))
 
 
 def oracle_batch_sample(cases, steps: int):
@@ -570,7 +657,7 @@ def run_batch(args, world, rank, local):
     e2e_value = world * T * args.steps / allmax(world, time.perf_counter() - t0)
     knobs = {"ilu_sweeps": b.cfg.ilu_sweeps, "ilu_sweeps_bwd": b.cfg.ilu_sweeps_bwd,
              "ilu_fuse_first": b.cfg.ilu_fuse_first, "warm_extrap": b.cfg.warm_extrap,
-             "inner_rtol": b.cfg.inner_rtol}
+             "inner_rtol": b.cfg.inner_rtol, "gmres_m": b.cfg.gmres_m}
     names = PROF_NAMES
     hbm_peak = measured_peaks().get("hbm_gbs") or HBM_FALLBACK_GBS
     classes = {}
@@ -584,10 +671,8 @@ def run_batch(args, world, rank, local):
             ent.update({"bytes": by, "gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 3)})
         classes[nm] = ent
     per_launch_ms = prof["ms"][0] / max(prof["n"][0], 1)
-    split = mixed and args.flux_split != "off"
-    roof = flux_roofline("mixed_flux_ws" if split else ("mixed_" if mixed else "") + "flux",
-                         "k_face_flux_ws" if split else "k_face_flux", prof["n"][0], per_launch_ms, 2 * F,
-                         probe_peaks(dev))
+    key, kname = flux_kernel(args, mixed)
+    roof = flux_roofline(key, kname, prof["n"][0], per_launch_ms, 2 * F, probe_peaks(dev))
     roof["classes"] = classes
     roof["work"] = {"arnoldi_per_step": prof["arnoldi"] / args.steps,
                     "mean_j": (prof["arnoldi_jsum"] - prof["arnoldi"]) / max(prof["arnoldi"], 1)}
@@ -625,11 +710,97 @@ def run_batch(args, world, rank, local):
         print(json.dumps(out), flush=True)
 
 
+def run_cavity(args, world, rank, local):
+    """Config 3: the viscous lid-driven cavity (isothermal no-slip walls, lid
+    Mach 0.15, Re 1000, Pr 0.72) on 256 x 256 split quads (131,072 triangles),
+    mixed and FP64, for a bounded number of steps (reaching the steady residual
+    1e-8 takes millions of explicit steps): triangle-steps/s of each, the
+    steady-residual history of the run control's rule (max over variables of
+    sqrt(sum |Omega| (w^{n+1} - w^n)^2) / dt, relative to the first step), and
+    the distance between the two paths' states."""
+    import numpy as np
+    import torch
+
+    from paper_1802_00704_gb300 import gks
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    case = make_case(args.workload, replica=rank)
+    T, F = case.mesh.n_tri, case.mesh.n_face
+    pr = case.meta["prandtl"]
+    area = torch.from_numpy(tri_area(case.mesh.nodes, case.mesh.tris)).to(dev)
+
+    def leg(mixed: bool, clocks: bool):
+        kw = gks_mixed_kw(args) if mixed else {}
+        m = gks.GksMesh(case.mesh, mu=case.mu, prandtl=pr, **kw)
+        w = torch.from_numpy(case.w0.copy()).to(dev)
+        tune = m.autotune(w, trial_steps=2) if args.tune else None
+        w.copy_(torch.from_numpy(case.w0))
+        m.reset_warm_start()
+        # residual history from the initial state (every step, host-side rule)
+        hist, r0 = [], None
+        for q in range(args.history):
+            w_old = w.clone()
+            info = m.run(w, max_steps=1)
+            r = max(float(torch.sqrt(torch.sum(area * (w[v] - w_old[v]) ** 2))) / info["last_dt"]
+                    for v in range(4))
+            r0 = r if r0 is None else r0
+            hist.append(r / r0)
+        for _ in range(args.warmup):
+            m.run(w, max_steps=1)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(gpu_id_of(dev)) if clocks else None
+        if sampler:
+            time.sleep(0.3)
+        barrier(world)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = gks.launch_count()
+        ev0.record(torch.cuda.current_stream())
+        info = m.run(w, max_steps=args.steps)
+        ev1.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        launches = gks.launch_count() - l0
+        barrier(world)
+        ck = sampler.stop() if sampler else None
+        ms = allmax(world, ev0.elapsed_time(ev1))
+        return {"m": m, "w": w, "ms": ms, "info": info, "hist": hist, "launches": launches, "clocks": ck,
+                "knobs": {"ilu_sweeps": m.cfg.ilu_sweeps, "warm_extrap": m.cfg.warm_extrap,
+                          "inner_rtol": m.cfg.inner_rtol, "gmres_m": m.cfg.gmres_m}}
+
+    mixed = args.precision == "mixed"
+    a = leg(mixed, True)
+    value = world * T * args.steps / (a["ms"] / 1e3)
+    out = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": a["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+f64 (mixed)" if mixed else "f64", "data": "synthetic",
+           "config": {"workload": f"lid-driven cavity {case.mesh.nx}x{case.mesh.ny} split quads, {T} triangles, "
+                                  f"Re {case.meta['re']:.0f}, lid Mach 0.15, Pr {pr}, isothermal no-slip walls",
+                      "n_tri": T, "n_face": F, "precision": args.precision, "knobs": a["knobs"],
+                      "l2": "inputs smaller than L2 (the Krylov basis is not)",
+                      "parallelism": "replicas" if world > 1 else "single GPU"},
+           "steady_residual": {"rule": "max_v sqrt(sum |Omega| dw_v^2) / dt relative to the first step",
+                               "history_every_step": [round(x, 6) for x in a["hist"]],
+                               "after_timed_steps_steps": int(a["info"]["steps"]) + args.history + args.warmup},
+           "gpu_launches": a["launches"], "clocks": a["clocks"]}
+    if mixed and not args.no_compare:
+        b = leg(False, False)
+        wm, wf = a["w"].cpu().numpy(), b["w"].cpu().numpy()
+        ar = tri_area(case.mesh.nodes, case.mesh.tris)
+        l1 = np.sum(ar * np.abs(wm - wf), axis=1) / np.sum(ar * np.abs(wf), axis=1)
+        out["fp64"] = {"value": world * T * args.steps / (b["ms"] / 1e3), "ms_per_step": b["ms"] / args.steps}
+        out["mixed_vs_fp64_rel_l1"] = [float(x) for x in l1]
+        out["speedup_vs_fp64"] = value / out["fp64"]["value"]
+        out["steady_residual"]["history_every_step_fp64"] = [round(x, 6) for x in b["hist"]]
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    cb = oracle_sample(args.steps, warmup=args.warmup)
+    cb, _, _, _ = oracle_sample(args.steps, warmup=args.warmup)
     secs = cb.pop("seconds")
+    cb["cpu"] = cpu_info()
     out = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": METRIC, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -659,6 +830,9 @@ def main():
                     help="mixed path: FP16 copies of the ILU(0) factors for the FP32 preconditioner")
     ap.add_argument("--flux-split", default="on", choices=sorted(FLUX_SPLIT),
                     help="mixed path: FP64 and FP32 parts of the flux in different warps")
+    ap.add_argument("--gmres-m", type=int, default=30, help="GMRES restart length (the tuner may pick a shorter one)")
+    ap.add_argument("--flux-lead", default="pairs", choices=["pairs", "fp64"],
+                    help="mixed path: the flux's FP64-accuracy part in double-FP32 pairs (default) or in FP64")
     ap.add_argument("--ilu-fuse", default="on", choices=["on", "off"],
                     help="fold the block-diagonal ILU pass into the first forward sweep")
     ap.add_argument("--graphs", default="device", choices=sorted(GRAPHS),
@@ -669,6 +843,8 @@ def main():
                     help="CLS initial guess: previous solution, or its linear / quadratic extrapolation")
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--history", type=int, default=50,
+                    help="cavity workloads: steps of steady-residual history before the warm-up")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gks":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -677,6 +853,8 @@ def main():
         run_reference(args, world, rank)
     elif WORKLOADS[args.workload]["kind"] == "batch":
         run_batch(args, world, rank, local)
+    elif WORKLOADS[args.workload]["kind"] == "cavity":
+        run_cavity(args, world, rank, local)
     else:
         run_gks(args, world, rank, local)
     if world > 1:

@@ -135,3 +135,14 @@ def test_flux_roofline_uses_the_counters_of_the_timed_kernel(monkeypatch):
     monkeypatch.setattr(bench, "counter_record", lambda key: None)
     r = bench.flux_roofline("mixed_flux_ws", "k_face_flux_ws", 10, ms, gp, _peaks())
     assert r["achieved"] is None and r["frac"] is None and r["traffic"] is None
+
+
+def test_flux_kernel_follows_the_configuration():
+    """The roofline names the kernel the configuration launches and reads that
+    kernel's counters: pairs -> k_face_flux_df, FP64 lead split ->
+    k_face_flux_ws, FP64 lead single-role and the FP64 path -> k_face_flux."""
+    from types import SimpleNamespace as NS
+    assert bench.flux_kernel(NS(flux_lead="pairs", flux_split="on"), True) == ("mixed_flux_df", "k_face_flux_df")
+    assert bench.flux_kernel(NS(flux_lead="fp64", flux_split="on"), True) == ("mixed_flux_ws", "k_face_flux_ws")
+    assert bench.flux_kernel(NS(flux_lead="fp64", flux_split="off"), True) == ("mixed_flux", "k_face_flux")
+    assert bench.flux_kernel(NS(flux_lead="pairs", flux_split="on"), False) == ("flux", "k_face_flux")
