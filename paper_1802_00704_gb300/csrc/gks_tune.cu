@@ -8,7 +8,9 @@
 // precision the inner tolerance trades FP32 Arnoldi iterations for FP64
 // refinement residuals; the backward relation may take fewer sweeps than the
 // forward one.  The tuner times a few steps of the handle's own cases for every
-// combination and keeps the fastest.
+// combination and keeps the fastest; then it times shorter GMRES restarts with
+// those knobs (a shorter restart orthogonalises against fewer vectors per
+// iteration but may need more iterations).
 #include <cfloat>
 #include <vector>
 
@@ -68,7 +70,18 @@ struct Candidate {
     int32_t sweeps, warm;
     double eta;
     int32_t bwd;
+    int32_t m;                       // GMRES restart length
 };
+
+void apply(gks_mesh *m, const Candidate &c)
+{
+    m->cfg.ilu_sweeps = c.sweeps;
+    m->cfg.warm_extrap = c.warm;
+    m->cfg.inner_rtol = c.eta;
+    m->cfg.ilu_sweeps_bwd = c.bwd;
+    m->cfg.gmres_m = c.m;
+    m->wk.m = c.m;
+}
 
 }  // namespace
 }  // namespace gks
@@ -98,7 +111,7 @@ extern "C" gks_status gks_autotune(gks_mesh *m, const double *w, int32_t trial_s
                 for (double eta : {1e-4, 1e-5, 1e-6}) {
                     if (!mixed && eta != 1e-6) continue;
                     cand.push_back({sweep ? sw : before.ilu_sweeps, wx, mixed ? eta : before.inner_rtol,
-                                    sweep ? bwd : before.ilu_sweeps_bwd});
+                                    sweep ? bwd : before.ilu_sweeps_bwd, m->wk.m});
                 }
         }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -108,40 +121,48 @@ extern "C" gks_status gks_autotune(gks_mesh *m, const double *w, int32_t trial_s
         st = GKS_ECUDA;
     }
     double best = DBL_MAX, base = DBL_MAX;
-    Candidate pick{before.ilu_sweeps, before.warm_extrap, before.inner_rtol, before.ilu_sweeps_bwd};
-    int32_t nfail = 0;
-    // the configuration the handle had, then every candidate
-    if (st == GKS_OK) st = time_candidate(m, w, trial_steps, s, e0, e1, &base);
-    if (st == GKS_OK) best = base;
-    for (size_t q = 0; st == GKS_OK && q < cand.size(); ++q) {
-        m->cfg.ilu_sweeps = cand[q].sweeps;
-        m->cfg.warm_extrap = cand[q].warm;
-        m->cfg.inner_rtol = cand[q].eta;
-        m->cfg.ilu_sweeps_bwd = cand[q].bwd;
+    const int32_t m0 = m->wk.m;
+    Candidate pick{before.ilu_sweeps, before.warm_extrap, before.inner_rtol, before.ilu_sweeps_bwd, m0};
+    int32_t nfail = 0, ntimed = 0;
+    auto try_one = [&](const Candidate &c) {
+        apply(m, c);
         double ms = DBL_MAX;
         st = time_candidate(m, w, trial_steps, s, e0, e1, &ms);
-        if (st != GKS_OK) break;
+        ++ntimed;
+        if (st != GKS_OK) return;
         if (ms == DBL_MAX) ++nfail;
         if (ms < best) {
             best = ms;
-            pick = cand[q];
+            pick = c;
         }
+    };
+    // the configuration the handle had, then every candidate
+    if (st == GKS_OK) st = time_candidate(m, w, trial_steps, s, e0, e1, &base);
+    if (st == GKS_OK) best = base;
+    for (size_t q = 0; st == GKS_OK && q < cand.size(); ++q) try_one(cand[q]);
+    // second stage: the restart length with the best solver knobs (the Krylov
+    // buffers hold m_alloc vectors, so only shorter restarts are possible)
+    const Candidate knobs = pick;
+    for (int32_t mr : {16, 8}) {
+        if (st != GKS_OK || mr >= m->wk.m_alloc || mr == m0) continue;
+        Candidate c = knobs;
+        c.m = mr;
+        try_one(c);
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     m->cfg = before;
+    m->wk.m = m0;
     if (st == GKS_OK) {
-        m->cfg.ilu_sweeps = pick.sweeps;
-        m->cfg.warm_extrap = pick.warm;
-        m->cfg.inner_rtol = pick.eta;
-        m->cfg.ilu_sweeps_bwd = pick.bwd;
+        apply(m, pick);
+        out->gmres_m = pick.m;
         out->ilu_sweeps = pick.sweeps;
         out->ilu_sweeps_bwd = pick.bwd;
         out->warm_extrap = pick.warm;
         out->inner_rtol = pick.eta;
         out->ms_per_step = best;
         out->ms_per_step_before = base;
-        out->n_candidates = (int32_t)cand.size();
+        out->n_candidates = ntimed;
         out->n_failed = nfail;
     }
     // leave the handle as a fresh one: cleared warm start and case state
