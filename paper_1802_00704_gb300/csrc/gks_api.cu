@@ -382,6 +382,97 @@ gks_status gks_step(gks_mesh *m, double *w, double *dt_inout, gks_step_info *inf
     return res;
 }
 
+namespace gks {
+namespace {
+
+constexpr int64_t kCheckEvery = 16;      // loops between the host's looks at the done flags
+
+// Reset the per-case clocks and counters of a run: end times tf (host, n values;
+// 0 = no end time), time 0, nothing done, no status, no steps, no iterations.
+gks_status run_begin(gks_mesh *m, const double *tf, cudaStream_t s)
+{
+    Work &k = m->wk;
+    const int32_t n = m->n_case;
+    GKS_CUDA(cudaMemcpyAsync(k.tfinal, tf, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    GKS_CUDA(cudaMemsetAsync(k.tcase, 0, sizeof(double) * n, s));
+    GKS_CUDA(cudaMemsetAsync(k.done, 0, sizeof(int32_t) * n, s));
+    GKS_CUDA(cudaMemsetAsync(k.status, 0, sizeof(int32_t) * n, s));
+    GKS_CUDA(cudaMemsetAsync(k.nstep, 0, sizeof(int64_t) * n, s));
+    GKS_CUDA(cudaMemsetAsync(k.last_dt, 0, sizeof(double) * n, s));
+    GKS_CUDA(cudaMemsetAsync(k.iters_acc, 0, sizeof(int64_t) * k.ns, s));
+    // tf is host memory that the caller may free on return
+    GKS_CUDA(cudaStreamSynchronize(s));
+    return GKS_OK;
+}
+
+// The step loop on the device state without a host round trip per step: every
+// loop takes one step of each case that is not done (CFL step clipped to the
+// case's end time, CLS solve, limiter, flux, update), then a case whose status
+// bits are set stops and the others advance their clocks.  The host looks at
+// the done flags every kCheckEvery loops and stops once every case is done.
+gks_status run_steps_async(gks_mesh *m, int64_t max_steps, cudaStream_t s)
+{
+    Work &k = m->wk;
+    const int32_t n = m->n_case;
+    std::vector<int32_t> done(n);
+    gks_status st;
+    int64_t q = 0;
+    while (q < max_steps) {
+        const int64_t chunk = std::min<int64_t>(kCheckEvery, max_steps - q);
+        for (int64_t r = 0; r < chunk; ++r) {
+            if ((st = launch_cfl_dt(m, k.w, k.dt, s)) != GKS_OK) return st;
+            if ((st = launch_clip_only(m, s)) != GKS_OK) return st;
+            if ((st = cls_solve(m, s, nullptr, nullptr, nullptr)) != GKS_OK) return st;
+            if ((st = launch_acc_iters(m, s)) != GKS_OK) return st;
+            if (m->cfg.limiter && (st = launch_limiter(m, k.w, k.x, s)) != GKS_OK) return st;
+            if ((st = launch_flux(m, k.w, m->cfg.limiter ? k.xl : k.x, 0.0, k.dt, k.flux, s)) != GKS_OK) return st;
+            if ((st = launch_update(m, k.w, k.flux, s)) != GKS_OK) return st;
+            if ((st = launch_after_step(m, s)) != GKS_OK) return st;
+        }
+        q += chunk;
+        if (q >= max_steps) break;
+        GKS_CUDA(cudaMemcpyAsync(done.data(), k.done, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+        GKS_CUDA(cudaStreamSynchronize(s));
+        bool all = true;
+        for (int32_t c = 0; c < n; ++c) all = all && done[c];
+        if (all) break;
+    }
+    return GKS_OK;
+}
+
+// per-case results of a run (host arrays of n values, may be NULL) and the
+// iterations summed over systems
+gks_status run_end(gks_mesh *m, cudaStream_t s, int64_t *nstep, double *t, double *last_dt, int32_t *status,
+                   int64_t *iters)
+{
+    Work &k = m->wk;
+    const int32_t n = m->n_case;
+    std::vector<int64_t> ns(n), it(k.ns);
+    std::vector<double> tt(n), ld(n);
+    std::vector<int32_t> stv(n);
+    GKS_CUDA(cudaMemcpyAsync(ns.data(), k.nstep, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s));
+    GKS_CUDA(cudaMemcpyAsync(tt.data(), k.tcase, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    GKS_CUDA(cudaMemcpyAsync(ld.data(), k.last_dt, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    GKS_CUDA(cudaMemcpyAsync(stv.data(), k.status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    GKS_CUDA(cudaMemcpyAsync(it.data(), k.iters_acc, sizeof(int64_t) * k.ns, cudaMemcpyDeviceToHost, s));
+    GKS_CUDA(cudaStreamSynchronize(s));
+    for (int32_t c = 0; c < n; ++c) {
+        if (nstep) nstep[c] = ns[c];
+        if (t) t[c] = tt[c];
+        if (last_dt) last_dt[c] = ld[c];
+        if (status) status[c] = stv[c];
+    }
+    if (iters) {
+        int64_t sum = 0;
+        for (int64_t v : it) sum += v;
+        *iters = sum;
+    }
+    return GKS_OK;
+}
+
+}  // namespace
+}  // namespace gks
+
 gks_status gks_run(gks_mesh *m, double *w, double t_final, int64_t max_steps, double steady_tol, gks_run_info *info,
                    void *stream)
 {
@@ -394,6 +485,31 @@ gks_status gks_run(gks_mesh *m, double *w, double t_final, int64_t max_steps, do
     cudaStream_t s = (cudaStream_t)stream;
     gks_status st, res = GKS_OK;
     Work &k = m->wk;
+    if (steady_tol <= 0.0) {
+        // no steady residual to watch: the whole loop on the device, one host
+        // round trip every few steps
+        const double tf = t_final > 0.0 ? t_final : 0.0;
+        if ((st = run_begin(m, &tf, s)) != GKS_OK) return st;
+        if ((st = launch_permute(w, k.w, m->d.perm, m->d.T, m->n_tri, 4, true, s)) != GKS_OK) return st;
+        if ((st = run_steps_async(m, max_steps, s)) != GKS_OK) return st;
+        if ((st = launch_permute(k.w, w, m->d.perm, m->d.T, m->n_tri, 4, false, s)) != GKS_OK) return st;
+        int64_t nst = 0, its = 0;
+        double tr = 0.0, ld = 0.0;
+        int32_t stat = 0;
+        if ((st = run_end(m, s, &nst, &tr, &ld, &stat, &its)) != GKS_OK) return st;
+        res = (stat & kStatusNonPhys) ? GKS_ENONPHYS : (stat & kStatusNoConv) ? GKS_ENOCONV : GKS_OK;
+        if (res == GKS_ENOCONV) set_error("GMRES did not reach gmres_rtol within gmres_maxit");
+        if (res == GKS_ENONPHYS) set_error("non-physical state (rho <= 0 or p <= 0)");
+        if (info) {
+            info->steps = nst;
+            info->t = tr;
+            info->last_dt = ld;
+            info->gmres_iters = its;
+            info->steady_res = 0.0;
+            info->status = res;
+        }
+        return res;
+    }
     GKS_CUDA(cudaMemsetAsync(k.status, 0, sizeof(int32_t) * m->n_case, s));
     if ((st = launch_permute(w, k.w, m->d.perm, m->d.T, m->n_tri, 4, true, s)) != GKS_OK) return st;
     double t = 0.0, last_dt = 0.0, res0 = -1.0, sres = 0.0;
@@ -456,43 +572,17 @@ gks_status gks_batch_run(gks_mesh *m, double *w, const double *t_final, int64_t 
     std::vector<double> tf(n, 0.0);
     if (t_final)
         for (int32_t c = 0; c < n; ++c) tf[c] = t_final[c];
-    GKS_CUDA(cudaMemcpyAsync(k.tfinal, tf.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
-    GKS_CUDA(cudaMemsetAsync(k.tcase, 0, sizeof(double) * n, s));
-    GKS_CUDA(cudaMemsetAsync(k.done, 0, sizeof(int32_t) * n, s));
-    GKS_CUDA(cudaMemsetAsync(k.status, 0, sizeof(int32_t) * n, s));
+    if ((st = run_begin(m, tf.data(), s)) != GKS_OK) return st;
     if ((st = launch_permute(w, k.w, m->d.perm, m->d.T, m->n_tri, 4, true, s)) != GKS_OK) return st;
-    std::vector<int32_t> done(n), stat(n), it(k.ns);
-    int64_t steps = 0, iters = 0;
-    while (steps < max_steps) {
-        if ((st = launch_cfl_dt(m, k.w, k.dt, s)) != GKS_OK) return st;
-        if ((st = launch_clip_dt(m, s)) != GKS_OK) return st;
-        GKS_CUDA(cudaMemcpyAsync(done.data(), k.done, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
-        GKS_CUDA(cudaStreamSynchronize(s));
-        bool all = true;
-        for (int32_t c = 0; c < n; ++c) all = all && done[c];
-        if (all) break;
-        if ((st = cls_solve(m, s, it.data(), nullptr, nullptr)) != GKS_OK) return st;
-        if (m->cfg.limiter && (st = launch_limiter(m, k.w, k.x, s)) != GKS_OK) return st;
-        if ((st = launch_flux(m, k.w, m->cfg.limiter ? k.xl : k.x, 0.0, k.dt, k.flux, s)) != GKS_OK) return st;
-        if ((st = launch_update(m, k.w, k.flux, s)) != GKS_OK) return st;
-        // a case that failed stops advancing; the others go on
-        GKS_CUDA(cudaMemcpyAsync(stat.data(), k.status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
-        GKS_CUDA(cudaStreamSynchronize(s));
-        bool newfail = false;
-        for (int32_t c = 0; c < n; ++c)
-            if (stat[c] && !done[c]) {
-                done[c] = 1;
-                newfail = true;
-            }
-        if (newfail) GKS_CUDA(cudaMemcpyAsync(k.done, done.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
-        for (int32_t q = 0; q < k.ns; ++q) iters += it[q];
-        ++steps;
-    }
+    // a case that fails stops advancing; the others go on
+    if ((st = run_steps_async(m, max_steps, s)) != GKS_OK) return st;
     if ((st = launch_permute(k.w, w, m->d.perm, m->d.T, m->n_tri, 4, false, s)) != GKS_OK) return st;
+    std::vector<int64_t> nst(n);
     std::vector<double> tr(n);
-    GKS_CUDA(cudaMemcpyAsync(tr.data(), k.tcase, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
-    GKS_CUDA(cudaMemcpyAsync(stat.data(), k.status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
-    GKS_CUDA(cudaStreamSynchronize(s));
+    std::vector<int32_t> stat(n);
+    int64_t iters = 0;
+    if ((st = run_end(m, s, nst.data(), tr.data(), nullptr, stat.data(), &iters)) != GKS_OK) return st;
+    int64_t steps = 0;
     int32_t nfail = 0, ndone = 0;
     for (int32_t c = 0; c < n; ++c) {
         const int32_t cs = (stat[c] & kStatusNonPhys) ? GKS_ENONPHYS : (stat[c] & kStatusNoConv) ? GKS_ENOCONV : GKS_OK;
@@ -500,6 +590,8 @@ gks_status gks_batch_run(gks_mesh *m, double *w, const double *t_final, int64_t 
         if (case_status) case_status[c] = cs;
         nfail += cs != GKS_OK;
         ndone += cs == GKS_OK && tf[c] > 0.0 && tr[c] >= tf[c] * (1.0 - 1e-14);
+        // a failing case's step counts in the loop too
+        steps = std::max<int64_t>(steps, nst[c] + (cs != GKS_OK ? 1 : 0));
     }
     if (info) {
         info->steps = steps;

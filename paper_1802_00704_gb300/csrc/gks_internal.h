@@ -155,6 +155,11 @@ struct Work {
     int32_t *done = nullptr;         // [ncase] case finished or stopped
     double *scal = nullptr;          // [8] misc device scalars
     int32_t *status = nullptr;       // [ncase] status bits
+    // the asynchronous step loop (gks_run, gks_batch_run): per-case steps taken,
+    // last step, and per-system GMRES iterations summed on the device
+    int64_t *nstep = nullptr;        // [ncase]
+    double *last_dt = nullptr;       // [ncase]
+    int64_t *iters_acc = nullptr;    // [ns]
     // pinned host mirrors
     int32_t *h_flags = nullptr;      // [4]
     double *h_scal = nullptr;        // [8]
@@ -259,6 +264,12 @@ gks_status launch_permute(const double *src, double *dst, const int32_t *perm, i
 gks_status launch_steady_partial(gks_mesh *m, cudaStream_t s);
 // per-case step control for runs: dt = min(cfl dt, t_final - t) or 0 when done; t += dt
 gks_status launch_clip_dt(gks_mesh *m, cudaStream_t s);
+// the asynchronous step loop: dt of each case clipped to its end time (0 once
+// the case is done, time not advanced yet); after the step, a case whose status
+// is set stops, the others advance their time and step count
+gks_status launch_clip_only(gks_mesh *m, cudaStream_t s);
+gks_status launch_after_step(gks_mesh *m, cudaStream_t s);
+gks_status launch_acc_iters(gks_mesh *m, cudaStream_t s);
 // shock detector + DWBAP limiter: m->wk.xl from m->wk.x (gks_limiter.cu)
 gks_status launch_limiter(gks_mesh *m, const double *w, const double *x, cudaStream_t s);
 // caller-ordered copy of the limiter flags of the last launch_limiter

@@ -871,6 +871,7 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
     AL(hcol, ns * (mm + 2)); AL(hco, ns * (mm + 2)); AL(vn, ns * (mm + 1)); AL(bnorm, ns); AL(beta, ns); AL(ctl, kCtlFields * ns); AL(flags, 4);
     AL(sexp, 2 * ns);
     AL(dt, n_cases); AL(tcase, n_cases); AL(tfinal, n_cases); AL(done, n_cases); AL(scal, 8); AL(status, n_cases);
+    AL(nstep, n_cases); AL(last_dt, n_cases); AL(iters_acc, ns);
 #undef AL
     GKS_CUDA(cudaMemset(k.x, 0, sizeof(double) * 20 * T));
     GKS_CUDA(cudaMemset(k.bnorm, 0, sizeof(double) * ns));

@@ -153,6 +153,44 @@ __global__ void k_clip_dt(double *dt, double *t, const double *__restrict__ tf, 
     t[c] += dt[c];
 }
 
+// dt of each case clipped to its end time; 0 for a case that is done or has
+// reached its end (which marks it done); the time is advanced after the step
+__global__ void k_clip_only(double *dt, const double *__restrict__ t, const double *__restrict__ tf, int32_t *done,
+                            int n)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    if (done[c] || (tf[c] > 0.0 && t[c] >= tf[c] * (1.0 - 1e-14))) {
+        done[c] = 1;
+        dt[c] = 0.0;
+        return;
+    }
+    if (tf[c] > 0.0) dt[c] = fmin(dt[c], tf[c] - t[c]);
+}
+
+// after a step: a case with status bits set stops (done); every other case
+// that took a step advances its time, step count and last step
+__global__ void k_after_step(const double *__restrict__ dt, double *t, int32_t *done,
+                             const int32_t *__restrict__ status, int64_t *nstep, double *last_dt, int n)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n || done[c] || !(dt[c] > 0.0)) return;
+    if (status[c]) {
+        done[c] = 1;
+        return;
+    }
+    t[c] += dt[c];
+    nstep[c] += 1;
+    last_dt[c] = dt[c];
+}
+
+// acc[s] += iterations of system s in the last solve
+__global__ void k_acc_iters(const int32_t *__restrict__ it, int64_t *acc, int ns)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < ns) acc[q] += it[q];
+}
+
 // Internal rows [nvar][n] <-> caller rows [nvar][nc]; padding (perm < 0) untouched.
 __global__ void k_permute(const double *__restrict__ src, double *__restrict__ dst, const int32_t *__restrict__ perm,
                           int64_t n, int64_t nc, int nvar, int gather)
@@ -244,6 +282,32 @@ gks_status launch_clip_dt(gks_mesh *m, cudaStream_t s)
 {
     const int n = m->d.ncase;
     k_clip_dt<<<(n + 127) / 128, 128, 0, s>>>(m->wk.dt, m->wk.tcase, m->wk.tfinal, m->wk.done, n); note_launch();
+    GKS_CUDA(cudaGetLastError());
+    return GKS_OK;
+}
+
+gks_status launch_clip_only(gks_mesh *m, cudaStream_t s)
+{
+    const int n = m->d.ncase;
+    k_clip_only<<<(n + 127) / 128, 128, 0, s>>>(m->wk.dt, m->wk.tcase, m->wk.tfinal, m->wk.done, n); note_launch();
+    GKS_CUDA(cudaGetLastError());
+    return GKS_OK;
+}
+
+gks_status launch_after_step(gks_mesh *m, cudaStream_t s)
+{
+    const int n = m->d.ncase;
+    Work &k = m->wk;
+    k_after_step<<<(n + 127) / 128, 128, 0, s>>>(k.dt, k.tcase, k.done, k.status, k.nstep, k.last_dt, n);
+    note_launch();
+    GKS_CUDA(cudaGetLastError());
+    return GKS_OK;
+}
+
+gks_status launch_acc_iters(gks_mesh *m, cudaStream_t s)
+{
+    const int ns = m->wk.ns;
+    k_acc_iters<<<(ns + 127) / 128, 128, 0, s>>>(m->wk.ctl + kCtlIters * ns, m->wk.iters_acc, ns); note_launch();
     GKS_CUDA(cudaGetLastError());
     return GKS_OK;
 }
