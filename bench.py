@@ -66,10 +66,11 @@ def make_case(name: str, replica: int = 0):
 
 
 def source_hash() -> str:
-    """Hash of the face-flux kernel's sources (the kernel the traffic record describes)."""
+    """Hash of the face-flux kernels' sources (the kernels the counter record describes)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1802_00704_gb300", "csrc")
-    for f in ("gks_flux.cu", "gks_kinetic.cuh"):
+    for f in ("gks_flux.cu", "gks_kinetic.cuh", "gks_face.cuh", "gks_flux_df.cu", "gks_lead_df.cuh", "gks_df.cuh",
+              "gks_erfcx_coef.h"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -353,7 +354,8 @@ def errors_vs_oracle(case, w_oracle, dts, dev, mixed_kw: dict) -> dict:
 
 
 def class_bytes(cls: str, prof: dict, T: int, F: int, steps: int, sweeps: int, exact: bool, mixed: bool,
-                basis32: bool, ilu16: bool = False, sweeps_bwd: int = -1, fuse_first: bool = True) -> float:
+                basis32: bool, ilu16: bool = False, sweeps_bwd: int = -1, fuse_first: bool = True,
+                pairs: bool = False) -> float:
     """Algorithmic DRAM bytes moved by one kernel class over the timed region,
     from the solver's work counters (Arnoldi iterations n, sum of j + 1 over
     them, preconditioner applications).  Per cell: operator = diagonal block 15
@@ -364,7 +366,8 @@ def class_bytes(cls: str, prof: dict, T: int, F: int, steps: int, sweeps: int, e
     sB Krylov basis (8, or 4 with the FP32-stored basis), sP the ILU factors (sM,
     or 2 with FP16 copies).  With the block-diagonal pass folded into the first
     forward sweep the neighbours' z^0 comes from their own factors and right-hand
-    sides, already counted as those cells' reads."""
+    sides, already counted as those cells' reads; with backward sweep pairs
+    likewise the neighbours' first-sweep values."""
     sM = 4 if mixed else 8
     sZ = 4 if mixed else 8
     sB = 4 if basis32 else 8
@@ -388,13 +391,16 @@ def class_bytes(cls: str, prof: dict, T: int, F: int, steps: int, sweeps: int, e
         fwd = 20 * sB + 8 * sZ + sP * (25 + 9) + 12 + 20 * sZ
         bwd = 20 * sZ + 8 * sZ + sP * (25 + 9) + 12 + 20 * sZ
         nbwd = sweeps if sweeps_bwd < 0 else sweeps_bwd
+        # with sweep pairs a launch covers two sweeps and moves a single sweep's
+        # bytes (the neighbours' first-sweep inputs are other cells' reads)
+        nbl = (nbwd // 2 + nbwd % 2) if pairs else nbwd
         if fuse_first and sweeps > 0:
-            return T * ((fwd - 8 * sZ) + (sweeps - 1) * fwd + nbwd * bwd) * pc
-        return T * (first + sweeps * fwd + nbwd * bwd) * pc
+            return T * ((fwd - 8 * sZ) + (sweeps - 1) * fwd + nbl * bwd) * pc
+        return T * (first + sweeps * fwd + nbl * bwd) * pc
     if cls == "update":                 # w in/out, 1/|Omega|, 3 face slots; each face flux once
         return (T * (8 * 8 + 8 + 12) + F * 4 * 8) * steps
-    if cls == "resid":                  # FP64 b - K x: x (own + neighbour values), operator, b, r (basis)
-        return T * (8 * (15 + 9) + 12 + 20 * 8 + 8 * 8 + 20 * 8 + 20 * sB) * prof["residuals"]
+    if cls == "resid":                  # FP64 b - K x: x (the neighbours' entries counted once), operator, b, r
+        return T * (8 * (15 + 9) + 12 + 20 * 8 + 20 * 8 + 20 * sB) * prof["residuals"]
     if cls == "corr":                   # x += Z y: the cycle's Z vectors, x read and written (FP64)
         cycles = max(prof["residuals"] - steps, 0)
         return T * (20 * sZ * n + 20 * 8 * 2 * cycles)
@@ -413,7 +419,7 @@ def timed_leg(args, case, precision: str, world: int, dev, sample_clocks: bool):
                     limiter=int(args.limiter), warm_extrap=WARM[args.warm], no_graphs=GRAPHS[args.graphs],
                     ilu_fp16=int(mixed and args.ilu16 == "on"), ilu_fuse_first=int(args.ilu_fuse == "on"),
                     flux_split=FLUX_SPLIT[args.flux_split], gmres_m=args.gmres_m,
-                    flux_lead=int(args.flux_lead == "pairs"))
+                    flux_lead=int(args.flux_lead == "pairs"), ilu_sweep_pairs=int(args.sweep_pairs == "on"))
     w = torch.from_numpy(case.w0.copy()).to(dev)
     stream = torch.cuda.current_stream()
     tune = m.autotune(w, trial_steps=2) if args.tune else None
@@ -446,7 +452,9 @@ def timed_leg(args, case, precision: str, world: int, dev, sample_clocks: bool):
             "stats": m.stats(), "tune": tune,
             "knobs": {"ilu_sweeps": m.cfg.ilu_sweeps, "ilu_sweeps_bwd": m.cfg.ilu_sweeps_bwd,
                       "ilu_fuse_first": m.cfg.ilu_fuse_first, "warm_extrap": m.cfg.warm_extrap,
-                      "inner_rtol": m.cfg.inner_rtol, "gmres_m": m.cfg.gmres_m}}
+                      "inner_rtol": m.cfg.inner_rtol, "gmres_m": m.cfg.gmres_m,
+                      "ilu_sweep_pairs": m.cfg.ilu_sweep_pairs,
+                      "flux_variant": tune["flux_variant"] if tune else 0}}
 
 
 def run_gks(args, world, rank, local):
@@ -494,7 +502,7 @@ def run_gks(args, world, rank, local):
         if nm not in ("flux", "ctl") and ms_c > 0:
             by = class_bytes(nm, prof, T, F, args.steps, main["knobs"]["ilu_sweeps"], exact, mixed, basis32,
                              mixed and args.ilu16 == "on", main["knobs"]["ilu_sweeps_bwd"],
-                             bool(main["knobs"]["ilu_fuse_first"]))
+                             bool(main["knobs"]["ilu_fuse_first"]), bool(main["knobs"]["ilu_sweep_pairs"]))
             gbs = by / (ms_c / 1e3) / 1e9
             ent.update({"bytes": by, "gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 3)})
         classes[nm] = ent
@@ -657,7 +665,7 @@ def run_batch(args, world, rank, local):
     e2e_value = world * T * args.steps / allmax(world, time.perf_counter() - t0)
     knobs = {"ilu_sweeps": b.cfg.ilu_sweeps, "ilu_sweeps_bwd": b.cfg.ilu_sweeps_bwd,
              "ilu_fuse_first": b.cfg.ilu_fuse_first, "warm_extrap": b.cfg.warm_extrap,
-             "inner_rtol": b.cfg.inner_rtol, "gmres_m": b.cfg.gmres_m}
+             "inner_rtol": b.cfg.inner_rtol, "gmres_m": b.cfg.gmres_m, "ilu_sweep_pairs": b.cfg.ilu_sweep_pairs}
     names = PROF_NAMES
     hbm_peak = measured_peaks().get("hbm_gbs") or HBM_FALLBACK_GBS
     classes = {}
@@ -666,7 +674,7 @@ def run_batch(args, world, rank, local):
         if nm not in ("flux", "ctl") and prof["ms"][q] > 0:
             by = class_bytes(nm, prof, T, F, args.steps, knobs["ilu_sweeps"], False, mixed,
                              mixed and args.basis == "fp32", mixed and args.ilu16 == "on", knobs["ilu_sweeps_bwd"],
-                             bool(knobs["ilu_fuse_first"]))
+                             bool(knobs["ilu_fuse_first"]), bool(knobs["ilu_sweep_pairs"]))
             gbs = by / (prof["ms"][q] / 1e3) / 1e9
             ent.update({"bytes": by, "gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 3)})
         classes[nm] = ent
@@ -833,6 +841,8 @@ def main():
     ap.add_argument("--gmres-m", type=int, default=30, help="GMRES restart length (the tuner may pick a shorter one)")
     ap.add_argument("--flux-lead", default="pairs", choices=["pairs", "fp64"],
                     help="mixed path: the flux's FP64-accuracy part in double-FP32 pairs (default) or in FP64")
+    ap.add_argument("--sweep-pairs", default="on", choices=["on", "off"],
+                    help="two ILU sweeps of a relation per launch (same results)")
     ap.add_argument("--ilu-fuse", default="on", choices=["on", "off"],
                     help="fold the block-diagonal ILU pass into the first forward sweep")
     ap.add_argument("--graphs", default="device", choices=sorted(GRAPHS),

@@ -179,6 +179,11 @@ typedef struct gks_config {
                               busy; 0 every thread does both.  Same arithmetic;
                               results agree to rounding (multiply-adds may contract
                               differently in the two kernels)                          */
+    int32_t ilu_sweep_pairs; /* GKS_PC_ILU_SWEEP with the per-cell equations: 1 (default)
+                              a pair of consecutive backward sweeps runs in one
+                              launch, each cell forming its upper neighbours'
+                              first-sweep values itself; 0 one sweep per launch.
+                              Same arithmetic, same results                         */
     int32_t flux_lead;     /* mixed precision: 1 (default) the flux's parts that need
                               more than FP32 (Gauss-point values, interface state,
                               collision time, zeroth-order terms) in double-FP32
@@ -300,11 +305,11 @@ GKS_EXPORT gks_status gks_cfl_dt(gks_mesh *mesh, const double *w, double *dt_out
 /* (gks_cfl_dt, gks_step and gks_run take single-mesh handles; GKS_EINVAL for a batch.) */
 
 /* Same time step as gks_cfl_dt, for callers that cannot allocate device
- * memory when they need it: code running while a stream is captured into a
- * CUDA graph (an allocation may synchronise the device and break the
- * capture), time loops that reserve all memory at start-up, or hosts whose
- * device memory belongs to another allocator.  The paper has no counterpart;
- * this entry point only changes where the scratch lives.
+ * memory when they need it: time loops of solvers that reserve all their
+ * device memory at start-up and forbid allocation afterwards, and hosts whose
+ * device memory belongs to another allocator (a framework's caching pool that
+ * must not be bypassed, or that has handed out all it holds).  The paper has
+ * no counterpart; this entry point only changes where the scratch lives.
  *   w      device [4][n_tri], caller's cell order (read only);
  *   dt_dev device pointer to one double that receives the step; nothing is
  *          copied to the host and the stream is not synchronised.
@@ -312,10 +317,13 @@ GKS_EXPORT gks_status gks_cfl_dt(gks_mesh *mesh, const double *w, double *dt_out
  * 128 KiB static device array of the library, held by every GPU that loads
  * it until exit, which limits meshes to 4,194,304 cells (GKS_EINVAL above, and
  * for batch handles).
- * The first call on each device looks up that array's device address; make
- * it before any stream capture.  All calls share the array, so calls that
- * overlap on the GPU (two streams, or two handles on one device) race; each
- * call writes every entry it reads, so nothing has to start at zero. */
+ * The first call on each device looks up that array's device address and
+ * keeps it for the life of the process; make that call before any stream
+ * capture.  A device reset (cudaDeviceReset) may move the array, after which
+ * this entry point must not be called again in the same process.  All calls
+ * share the array, so calls that overlap on the GPU (two streams, or two
+ * handles on one device) race; each call writes every entry it reads, so
+ * nothing has to start at zero. */
 GKS_EXPORT gks_status gks_cfl_dt_noalloc(const gks_mesh *mesh, const double *w, double *dt_dev, void *stream);
 
 /* CLS reconstruction (Sec. III): solves the per-cell least-squares system
@@ -382,7 +390,9 @@ GKS_EXPORT gks_status gks_point_flux(int64_t n, const double *wl, const double *
  * preconditioner only), warm_extrap in {0, 1, 2} and, in mixed precision,
  * inner_rtol in {1e-4, 1e-5, 1e-6}; then, with the best of those, the GMRES
  * restart length in {gmres_m, 16, 8} (at most the gmres_m the handle was
- * created with, which sized its Krylov buffers).  Each candidate starts from w (device,
+ * created with, which sized its Krylov buffers); then, for the mixed flux in
+ * double-FP32 without the Prandtl correction and with mean interface slopes,
+ * the launch shape (register budget) of the flux kernel.  Each candidate starts from w (device,
  * [4][n_tri], caller order, not modified) with a cleared warm start, takes
  * 3 untimed steps, then trial_steps (>= 1) steps timed with CUDA events; a
  * candidate whose steps fail is skipped.  The fastest candidate is written to
@@ -398,6 +408,9 @@ typedef struct gks_tune_result {
     int32_t n_failed;             /* candidates skipped because a step failed       */
     int32_t ilu_sweeps_bwd;       /* chosen backward sweeps (-1: as ilu_sweeps)     */
     int32_t gmres_m;              /* chosen restart length (also in the config)     */
+    int32_t flux_variant;         /* chosen launch shape of the double-FP32 flux
+                                     kernel: 0 128 threads x 4 blocks per SM (128
+                                     registers), 1 x 3 (168), 2 x 2 (255)          */
 } gks_tune_result;
 
 GKS_EXPORT gks_status gks_autotune(gks_mesh *mesh, const double *w, int32_t trial_steps, gks_tune_result *out,

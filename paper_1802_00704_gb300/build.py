@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libgks.so")
-SOURCES = ["gks_setup.cu", "gks_cls.cu", "gks_flux.cu", "gks_step.cu", "gks_api.cu", "gks_noalloc.cu", "gks_limiter.cu",
+SOURCES = ["gks_setup.cu", "gks_cls.cu", "gks_flux.cu", "gks_flux_df.cu", "gks_step.cu", "gks_api.cu", "gks_noalloc.cu", "gks_limiter.cu",
            "gks_tune.cu", "gks_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",

@@ -70,6 +70,7 @@ gks_status check_config(const gks_config &c)
     ok = ok && (c.ilu_fuse_first == 0 || c.ilu_fuse_first == 1);
     ok = ok && (c.flux_split == 0 || c.flux_split == 1);
     ok = ok && (c.flux_lead == 0 || c.flux_lead == 1);
+    ok = ok && (c.ilu_sweep_pairs == 0 || c.ilu_sweep_pairs == 1);
     if (!ok) {
         set_error("invalid gks_config");
         return GKS_EINVAL;
@@ -197,6 +198,7 @@ void gks_config_default(gks_config *c)
     c->ilu_sweeps_bwd = -1;
     c->ilu_fuse_first = 1;
     c->flux_split = 1;
+    c->ilu_sweep_pairs = 1;
     c->flux_lead = 1;
 }
 
@@ -456,6 +458,9 @@ gks_status run_end(gks_mesh *m, cudaStream_t s, int64_t *nstep, double *t, doubl
     GKS_CUDA(cudaMemcpyAsync(stv.data(), k.status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
     GKS_CUDA(cudaMemcpyAsync(it.data(), k.iters_acc, sizeof(int64_t) * k.ns, cudaMemcpyDeviceToHost, s));
     GKS_CUDA(cudaStreamSynchronize(s));
+    // the device-controlled solve graphs counted their launches and work on the
+    // device; bring those counters to the host once per run
+    flush_solve_counters(m);
     for (int32_t c = 0; c < n; ++c) {
         if (nstep) nstep[c] = ns[c];
         if (t) t[c] = tt[c];

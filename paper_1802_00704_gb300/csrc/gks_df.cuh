@@ -213,7 +213,7 @@ __device__ __forceinline__ df expm1_small(df r)
     q = add(mul(q, s), 0.5f);
     q = add(mul(q, s), 1.0f);
     df e = mul(q, s);
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < 4; ++k) e = mul(e, add(e, 2.0f));     // (1 + e)^2 - 1
     return e;
 }
@@ -249,7 +249,9 @@ __device__ __forceinline__ df erfcx(df y)
 #pragma unroll
     for (int k = kErfcxDeg - 1; k >= kHead; --k) t = __fmaf_rn(t, s.hi, kErfcxHi[k]);
     df p = {t, 0.0f};
-#pragma unroll
+    // a rolled loop: the code of the flux kernel that calls this twice is
+    // large enough for instruction fetch to stall it
+#pragma unroll 1
     for (int k = kHead - 1; k >= 0; --k) p = add(mul(p, s), df{kErfcxHi[k], kErfcxLo[k]});
     return p;
 }

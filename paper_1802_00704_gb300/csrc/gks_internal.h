@@ -184,7 +184,7 @@ struct SolveGraphs {
     std::vector<int64_t> iter_launches;
     cudaGraphExec_t start = nullptr, restart = nullptr;
     int64_t start_launches = 0, restart_launches = 0;
-    int32_t sweeps = -1, sweeps_bwd = -2, fuse = -1, precond = -1, maxit = -1;
+    int32_t sweeps = -1, sweeps_bwd = -2, fuse = -1, precond = -1, maxit = -1, pairs = -1;
     double eta = -1.0, rtol = -1.0;
     bool disabled = false;                          // a capture failed: launch directly
     // device-controlled whole solve
@@ -226,6 +226,8 @@ struct gks_mesh {
     gks::SolveGraphs *graphs = nullptr;
     int64_t flux_ws_grid = 0;                      // blocks of the persistent flux kernel
     int32_t flux_ws_key = -1;                      // ... for this variant
+    int32_t flux_variant = 0;                      // launch shape of the double-FP32 flux kernel
+                                                   // (kFluxDfVariants; chosen by the autotuner)
 };
 
 namespace gks {
@@ -255,6 +257,15 @@ gks_status cls_solve(gks_mesh *m, cudaStream_t s, int32_t *iters, double *relres
 gks_status launch_flux(gks_mesh *m, const double *w, const double *x, double dt_const, const double *dt_dev,
                        double *flux, cudaStream_t s);
 gks_status launch_update(gks_mesh *m, double *w, const double *flux, cudaStream_t s);
+// the mixed flux with its FP64-accuracy part in FP32 pairs (gks_flux_df.cu);
+// launch shapes (threads per block, blocks per SM, i.e. the register budget)
+// the autotuner may choose from for the flux without the Prandtl correction
+// and with mean interface slopes
+constexpr int kFluxDfVariants = 3;
+gks_status launch_flux_df(gks_mesh *m, const double *w, const double *x, double dt_const, const double *dt_dev,
+                          double *flux, cudaStream_t s);
+gks_status launch_point_flux_df(int64_t n, const double *wl, const double *wr, double dt, const gks_config &cfg,
+                                double *out, int32_t *status, cudaStream_t s);
 gks_status launch_cfl_dt(gks_mesh *m, const double *w, double *dt_dev, cudaStream_t s);
 gks_status launch_point_flux(int64_t n, const double *wl, const double *wr, double dt, const gks_config &cfg,
                              double *out, int32_t *status, cudaStream_t s);

@@ -488,36 +488,33 @@ __device__ __forceinline__ void body_flux(const R *wl, const R *wr, Iface<R> &I,
 #pragma unroll
         for (int q = 0; q < 4; ++q) d[q] = I.Z.rho * out[q];
     }
-    // non-equilibrium part, Eq. (11), left (u > 0) and right (u < 0)
+    // non-equilibrium part, Eq. (11), left (u > 0) and right (u < 0): one copy
+    // of the code for both sides (the flux kernels are long enough for
+    // instruction fetch to stall them), the side's state and rows copied in
     const R kA = -tau * C[6], kL = C[7] - tau * C[6], kS = R(0.5) * C[8] - tau * C[7], kAL = -tau * C[7];
     const R k7 = with_const ? C[6] : R(0);
-    mom_full(I.L.U, I.L.lam, m.u);
-    mom_full(I.L.V, I.L.lam, m.v);
-    mom_xi(I.L.lam, K, m.z);
-    if (!KIN) slopes(I.L, wl, K, m, false);
-    build_q(Q, I.L, k7, kA, kL, kS, kAL, R(0));
-    mom_half(I.L.U, I.L.lam, R(1), m.u);
-    upsi_contract(Q, m, out);
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+        KState<R> st = side ? I.Rs : I.L;
+        mom_full(st.U, st.lam, m.u);
+        mom_full(st.V, st.lam, m.v);
+        mom_xi(st.lam, K, m.z);
+        if (!KIN) {
+            R rows[24];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) f[q] += I.L.rho * out[q];
-    if (HEAT) {
-        psi_contract<R, 4>(Q, m, out);
+            for (int q = 0; q < 24; ++q) rows[q] = side ? wr[q] : wl[q];
+            slopes(st, rows, K, m, false);
+        }
+        build_q(Q, st, k7, kA, kL, kS, kAL, R(0));
+        mom_half(st.U, st.lam, side ? R(-1) : R(1), m.u);
+        upsi_contract(Q, m, out);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) d[q] += I.L.rho * out[q];
-    }
-    mom_full(I.Rs.U, I.Rs.lam, m.u);
-    mom_full(I.Rs.V, I.Rs.lam, m.v);
-    mom_xi(I.Rs.lam, K, m.z);
-    if (!KIN) slopes(I.Rs, wr, K, m, false);
-    build_q(Q, I.Rs, k7, kA, kL, kS, kAL, R(0));
-    mom_half(I.Rs.U, I.Rs.lam, R(-1), m.u);
-    upsi_contract(Q, m, out);
+        for (int q = 0; q < 4; ++q) f[q] += st.rho * out[q];
+        if (HEAT) {
+            psi_contract<R, 4>(Q, m, out);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) f[q] += I.Rs.rho * out[q];
-    if (HEAT) {
-        psi_contract<R, 4>(Q, m, out);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) d[q] += I.Rs.rho * out[q];
+            for (int q = 0; q < 4; ++q) d[q] += st.rho * out[q];
+        }
     }
 }
 

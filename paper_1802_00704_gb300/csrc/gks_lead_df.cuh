@@ -78,8 +78,20 @@ __device__ __forceinline__ bool gp_lead(const df *vl, const df *vr, df dt, const
     State L, R, Z;
     if (!(prim(vl, c, L) & prim(vr, c, R))) return false;
     df ml[4], mr[4];
-    half_moments(L, 1.0f, c, ml);
-    half_moments(R, -1.0f, c, mr);
+    // one copy of the (large) half-moment code for both sides: the flux kernel
+    // is long enough for instruction fetch to stall it
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+        df m[4];
+        half_moments(side ? R : L, side ? -1.0f : 1.0f, c, m);
+        if (side) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) mr[q] = m[q];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) ml[q] = m[q];
+        }
+    }
     // W0 = rho_l <psi>_{u>0} + rho_r <psi>_{u<0}; <e> = (<u^2> + <1>(V^2 + (K + 1) h)) / 2
     const df lm0 = dfm::mul(L.rho, ml[0]), rm0 = dfm::mul(R.rho, mr[0]);
     const df lm1 = dfm::mul(L.rho, ml[1]), rm1 = dfm::mul(R.rho, mr[1]);

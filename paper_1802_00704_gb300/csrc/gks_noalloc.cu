@@ -1,9 +1,7 @@
 // Allocation-free variant of the CFL time-step reduction (gks_cfl_dt_noalloc).
 //
 // Some callers cannot allocate device memory at the moment they need the time
-// step: code running while a stream is being captured into a CUDA graph
-// (cudaMalloc may synchronise the device, which invalidates the capture),
-// time loops of solvers that reserve all memory at start-up and forbid
+// step: time loops of solvers that reserve all memory at start-up and forbid
 // allocation afterwards, and hosts whose device memory belongs to another
 // allocator (a framework's caching pool).  For them this entry point computes
 // the same step as gks_cfl_dt without calling cudaMalloc, cudaFree or any
@@ -66,7 +64,9 @@ __global__ void k_cfl_final_static(const double *__restrict__ scratch, int nblk,
     if (threadIdx.x == 0) *dt_out = cfl * sh[0];
 }
 
-// Device address of the scratch array on the current device (set up once per device).
+// Device address of the scratch array on the current device, looked up once
+// per device and kept for the life of the process (a device reset that moves
+// the array is documented as the end of this entry point's use).
 gks_status scratch_address(int dev, double **out)
 {
     if (dev < 0 || dev >= kMaxDevices) {

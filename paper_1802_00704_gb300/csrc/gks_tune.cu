@@ -10,7 +10,8 @@
 // forward one.  The tuner times a few steps of the handle's own cases for every
 // combination and keeps the fastest; then it times shorter GMRES restarts with
 // those knobs (a shorter restart orthogonalises against fewer vectors per
-// iteration but may need more iterations).
+// iteration but may need more iterations), and the launch shapes of the
+// double-FP32 flux kernel (its register budget against the warps per SM).
 #include <cfloat>
 #include <vector>
 
@@ -149,12 +150,34 @@ extern "C" gks_status gks_autotune(gks_mesh *m, const double *w, int32_t trial_s
         c.m = mr;
         try_one(c);
     }
+    // third stage: the launch shape (register budget) of the double-FP32 flux
+    // kernel, with the best knobs and restart length
+    const int32_t v0 = m->flux_variant;
+    int32_t vpick = v0;
+    const bool df_flux = mixed && m->cfg.flux_lead && m->cfg.prandtl == 1.0 && m->cfg.slope0_mode == 0;
+    if (df_flux && st == GKS_OK) {
+        apply(m, pick);
+        for (int32_t v = 0; v < kFluxDfVariants && st == GKS_OK; ++v) {
+            if (v == v0) continue;
+            m->flux_variant = v;
+            double ms = DBL_MAX;
+            st = time_candidate(m, w, trial_steps, s, e0, e1, &ms);
+            ++ntimed;
+            if (st == GKS_OK && ms < best) {
+                best = ms;
+                vpick = v;
+            }
+        }
+        m->flux_variant = v0;
+    }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     m->cfg = before;
     m->wk.m = m0;
     if (st == GKS_OK) {
         apply(m, pick);
+        m->flux_variant = vpick;
+        out->flux_variant = vpick;
         out->gmres_m = pick.m;
         out->ilu_sweeps = pick.sweeps;
         out->ilu_sweeps_bwd = pick.bwd;

@@ -49,7 +49,7 @@ class Config(C.Structure):
                 ("inner_rtol", C.c_double), ("prandtl", C.c_double), ("slope0_mode", C.c_int32),
                 ("ilu_fp16", C.c_int32), ("cls_global", C.c_int32), ("cls_M", C.c_int32),
                 ("ilu_sweeps_bwd", C.c_int32), ("ilu_fuse_first", C.c_int32),
-                ("flux_split", C.c_int32), ("flux_lead", C.c_int32)]
+                ("flux_split", C.c_int32), ("ilu_sweep_pairs", C.c_int32), ("flux_lead", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -68,7 +68,8 @@ class RunInfo(C.Structure):
 class TuneResult(C.Structure):
     _fields_ = [("ilu_sweeps", C.c_int32), ("warm_extrap", C.c_int32), ("inner_rtol", C.c_double),
                 ("ms_per_step", C.c_double), ("ms_per_step_before", C.c_double), ("n_candidates", C.c_int32),
-                ("n_failed", C.c_int32), ("ilu_sweeps_bwd", C.c_int32), ("gmres_m", C.c_int32)]
+                ("n_failed", C.c_int32), ("ilu_sweeps_bwd", C.c_int32), ("gmres_m", C.c_int32),
+                ("flux_variant", C.c_int32)]
 
 
 class Profile(C.Structure):

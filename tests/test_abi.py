@@ -43,13 +43,38 @@ def test_config_defaults(lib):
     assert c.limit_char == 0 and c.inner_rtol == 1e-6 and c.ilu_sweeps_bwd == -1 and c.ilu_fuse_first == 1
     assert c.flux_split == 1
     assert c.prandtl == 1.0
-    # the ctypes mirror has the size of the C struct: 4 doubles, 2 ints, 1 double, 10 ints, 2 doubles
-    assert C.sizeof(gks.Config) == 4 * 8 + 2 * 4 + 8 + 10 * 4 + 2 * 8 + 7 * 4 + 4   # + padding
-    assert gks.Config.inner_rtol.offset == 88 and gks.Config.prandtl.offset == 96
-    assert gks.Config.slope0_mode.offset == 104 and gks.Config.ilu_fp16.offset == 108
-    assert gks.Config.cls_global.offset == 112 and gks.Config.cls_M.offset == 116
-    assert gks.Config.ilu_sweeps_bwd.offset == 120 and gks.Config.ilu_fuse_first.offset == 124
-    assert gks.Config.flux_split.offset == 128
+    assert c.flux_lead == 1 and c.ilu_sweep_pairs == 1
+
+
+def _c_layout(struct, fields):
+    """sizeof and offsetof of a struct of include/gks.h, from a C program
+    compiled with gcc against the header (the layout the library sees)."""
+    import subprocess
+    import tempfile
+    body = "\n".join(f'    printf("%zu\\n", offsetof({struct}, {f}));' for f in fields)
+    src = (f'#include <stddef.h>\n#include <stdio.h>\n#include "gks.h"\n'
+           f'int main(void) {{\n    printf("%zu\\n", sizeof({struct}));\n{body}\n    return 0;\n}}\n')
+    with tempfile.TemporaryDirectory() as tmp:
+        cpath, exe = os.path.join(tmp, "layout.c"), os.path.join(tmp, "layout")
+        open(cpath, "w").write(src)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), cpath, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
+    return int(out[0]), [int(x) for x in out[1:]]
+
+
+@pytest.mark.parametrize("struct,mirror", [("gks_config", "Config"), ("gks_tune_result", "TuneResult"),
+                                           ("gks_run_info", "RunInfo"), ("gks_profile", "Profile"),
+                                           ("gks_mesh_stats", "MeshStats")])
+def test_ctypes_mirrors_match_the_header(struct, mirror):
+    """The binding's ctypes structures have the size and field offsets of the
+    C structures of include/gks.h."""
+    pytest.importorskip("subprocess")
+    from paper_1802_00704_gb300 import gks
+    cls = getattr(gks, mirror)
+    names = [f for f, _ in cls._fields_]
+    size, offs = _c_layout(struct, names)
+    assert C.sizeof(cls) == size
+    assert [getattr(cls, f).offset for f in names] == offs
 
 
 def test_binding_refuses_cpu_tensors(lib):

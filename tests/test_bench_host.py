@@ -38,6 +38,10 @@ def test_ilu_bytes_per_application():
     # no forward sweep: nothing to fold, the block-diagonal pass stays
     args0 = dict(args, sweeps=0, sweeps_bwd=0)
     assert bench.class_bytes("ilu", p, fuse_first=True, **args0) == T * 210 * pc
+    # backward sweep pairs: two backward sweeps in one launch, moving one sweep's bytes
+    assert bench.class_bytes("ilu", p, fuse_first=True, pairs=True, **args) == T * (240 + 272 + 272) * pc
+    args3 = dict(args, sweeps=3, sweeps_bwd=3)
+    assert bench.class_bytes("ilu", p, fuse_first=True, pairs=True, **args3) == T * (240 + 2 * 272 + 2 * 272) * pc
 
 
 def test_fp64_and_exact_ilu_bytes():
@@ -62,9 +66,11 @@ def test_gram_schmidt_operator_and_residual_bytes():
     # operator: blocks (24 values) + neighbour indices + source + result per iteration
     assert bench.class_bytes("spmv", p, T=T, F=0, steps=1, sweeps=2, exact=False, mixed=True,
                              basis32=True) == T * (4 * 24 + 12 + 20 * 4 + 20 * 4) * 6
-    # refinement residual: FP64 (or FP32-pair) operator, x own + neighbours, b, and the basis slot
+    # refinement residual: FP64 (or FP32-pair) operator, x (the neighbours' entries counted once, as
+    # for the other kernels: ncu reads 524.6 MB per 1M-cell launch = 8 * 24 + 12 + 160 + 160), b, the
+    # basis slot
     assert bench.class_bytes("resid", p, T=T, F=0, steps=1, sweeps=2, exact=False, mixed=True,
-                             basis32=True) == T * (8 * 24 + 12 + 160 + 64 + 160 + 80) * 3
+                             basis32=True) == T * (8 * 24 + 12 + 160 + 160 + 80) * 3
 
 
 def test_update_and_correction_bytes():

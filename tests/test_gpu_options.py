@@ -74,7 +74,10 @@ def test_autotune_keeps_the_state_and_the_results(G, precision):
     assert np.array_equal(host(w), c.w0)                   # the caller's state is untouched
     assert r["ilu_sweeps"] in (1, 2, 3) and r["warm_extrap"] in (0, 1, 2) and r["ilu_sweeps_bwd"] in (-1, 1)
     # sweeps (1, 2, 3) with the same number backward, and (2, 3) with one backward sweep
-    assert r["n_candidates"] == (45 if precision == "mixed" else 15) and r["n_failed"] == 0
+    # (x warm start x inner tolerance in mixed precision), then restarts 16 and 8,
+    # then (mixed, double-FP32 flux) the two other launch shapes of the flux kernel
+    assert r["n_candidates"] == (45 + 2 + 2 if precision == "mixed" else 15 + 2) and r["n_failed"] == 0
+    assert r["gmres_m"] in (30, 16, 8) and r["flux_variant"] in ((0, 1, 2) if precision == "mixed" else (0,))
     assert 0 < r["ms_per_step"] <= r["ms_per_step_before"]
     if precision == "fp64":
         assert r["inner_rtol"] == 1e-6
@@ -226,6 +229,29 @@ def test_fused_first_ilu_pass_is_the_separate_pass(G, precision, cls_global):
             ra, rb = a.step(wa), b.step(wb)
             assert ra["iters"] == rb["iters"]
         assert np.array_equal(host(wa), host(wb))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_sweep_pairs_are_the_single_sweeps(G, precision):
+    """ilu_sweep_pairs runs two consecutive sweeps of a relation in one launch,
+    each cell forming its neighbours' first-sweep values with the single
+    sweep's arithmetic and rounding: CLS coefficients and steps are
+    bit-identical to one sweep per launch, for 2, 3 and 4 sweeps and unequal
+    forward / backward counts (FP16 factors in the mixed mode)."""
+    c = I.shock_vortex_case(40, 20)
+    mixed = precision == "mixed"
+    kw = dict(precision=G.MIXED if mixed else G.FP64, basis_fp32=int(mixed), ilu_fp16=int(mixed))
+    for sweeps, bwd in ((2, -1), (3, -1), (4, 1), (1, 2), (2, 3)):
+        a = G.GksMesh(c.mesh, ilu_sweeps=sweeps, ilu_sweeps_bwd=bwd, ilu_sweep_pairs=1, **kw)
+        b = G.GksMesh(c.mesh, ilu_sweeps=sweeps, ilu_sweeps_bwd=bwd, ilu_sweep_pairs=0, **kw)
+        ca, ia = a.cls_reconstruct(dev(c.w0))
+        cb, ib = b.cls_reconstruct(dev(c.w0))
+        assert ia["iters"] == ib["iters"] and np.array_equal(host(ca), host(cb)), (sweeps, bwd)
+        wa, wb = dev(c.w0), dev(c.w0)
+        for _ in range(3):
+            ra, rb = a.step(wa), b.step(wb)
+            assert ra["iters"] == rb["iters"]
+        assert np.array_equal(host(wa), host(wb)), (sweeps, bwd)
 
 
 @pytest.mark.parametrize("slope0_mode", [0, 1])

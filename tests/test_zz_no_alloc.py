@@ -1,8 +1,8 @@
 """The allocation-free time-step entry point (gks_cfl_dt_noalloc) gives the
 same step as gks_cfl_dt, on two calls in a row that share its static scratch.
 It exists for callers that cannot allocate device memory at that moment
-(stream capture into a CUDA graph, allocation-free time loops, memory owned by
-another allocator).  This file is collected last on purpose."""
+(time loops that reserve all memory up front, device memory owned by another
+allocator).  This file is collected last on purpose."""
 import numpy as np
 import pytest
 
