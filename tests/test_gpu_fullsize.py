@@ -93,30 +93,44 @@ def test_fullsize_mixed_path_as_benchmarked(big):
     assert np.all(np.abs(fl[:, ids] - ref) <= 1e-7 * scale)
 
 
-def test_config5_batch_sampled_against_oracle():
-    """The 512-case batch (19.2M triangles, log-uniform 1e3-2e5 per case,
+def test_config5_batch_50_steps_against_oracle_and_fp64():
+    """The 512-case batch (19.8M triangles, log-uniform 1e3-2e5 per case,
     advection and Riemann strips with ratios 2-10) in the benchmark's launch
-    configuration (mixed, robust limiter, GMRES(12)): 3 steps of the whole batch,
-    every case physical, and the three smallest cases equal the oracle's own
-    steps to 1e-8 relative L1."""
+    configuration (mixed, FP32 Krylov basis, robust limiter, GMRES(12)) for the
+    configuration's 50 steps: every case physical; the six smallest cases equal
+    the oracle's own 50 steps to 1e-8 relative L1 per conserved variable; and
+    every case of the batch equals the FP64 batch's state to 1e-8 relative L1."""
     from oracle import oracle
     from paper_1802_00704_gb300 import build, gks
     oracle.build()
     build.build()
     cases = I.batch_cases(512, workers=16)
-    b = gks.GksMesh.batch([c.mesh for c in cases], precision=gks.MIXED, limiter=2, gmres_m=12, basis_fp32=1)
-    w = dev(np.ascontiguousarray(np.concatenate([c.w0 for c in cases], axis=1)))
-    r = b.batch_run(w, max_steps=3)
-    assert r["n_failed"] == 0 and r["steps"] == 3
-    wh = host(w)
+    w0 = np.ascontiguousarray(np.concatenate([c.w0 for c in cases], axis=1))
     offs = np.concatenate([[0], np.cumsum([c.mesh.n_tri for c in cases])])
-    for q in np.argsort([c.mesh.n_tri for c in cases])[:3]:
+    states = {}
+    for prec in ("mixed", "fp64"):
+        kw = dict(precision=gks.MIXED, basis_fp32=1) if prec == "mixed" else dict(precision=gks.FP64)
+        b = gks.GksMesh.batch([c.mesh for c in cases], limiter=2, gmres_m=12, **kw)
+        w = dev(w0)
+        r = b.batch_run(w, max_steps=50)
+        assert r["n_failed"] == 0 and r["steps"] == 50, (prec, r["n_failed"], r["steps"])
+        states[prec] = host(w)
+        del b
+    wm, wf = states["mixed"], states["fp64"]
+    for q, c in enumerate(cases):
+        p = c.mesh.nodes[c.mesh.tris]
+        area = 0.5 * np.abs((p[:, 1, 0] - p[:, 0, 0]) * (p[:, 2, 1] - p[:, 0, 1]) -
+                            (p[:, 2, 0] - p[:, 0, 0]) * (p[:, 1, 1] - p[:, 0, 1]))
+        a, f = wm[:, offs[q]:offs[q + 1]], wf[:, offs[q]:offs[q + 1]]
+        l1 = np.sum(area * np.abs(a - f), axis=1) / np.sum(area * np.abs(f), axis=1)
+        assert np.all(l1 <= 1e-8), (q, l1)
+    for q in np.argsort([c.mesh.n_tri for c in cases])[:6]:
         c = cases[q]
         om = oracle.OracleMesh(c.mesh, limiter=2)
         wo = c.w0.copy()
-        for _ in range(3):
+        for _ in range(50):
             assert om.step(wo).status == 0
         area = om.cell_geometry()["area"]
-        got = wh[:, offs[q]:offs[q + 1]]
+        got = wm[:, offs[q]:offs[q + 1]]
         l1 = np.sum(area * np.abs(got - wo), axis=1) / np.sum(area * np.abs(wo), axis=1)
         assert np.all(l1 <= 1e-8), (q, l1)
