@@ -355,7 +355,7 @@ def errors_vs_oracle(case, w_oracle, dts, dev, mixed_kw: dict) -> dict:
 
 def class_bytes(cls: str, prof: dict, T: int, F: int, steps: int, sweeps: int, exact: bool, mixed: bool,
                 basis32: bool, ilu16: bool = False, sweeps_bwd: int = -1, fuse_first: bool = True,
-                pairs: bool = False) -> float:
+                pairs: bool = False, fused_dots: bool = False) -> float:
     """Algorithmic DRAM bytes moved by one kernel class over the timed region,
     from the solver's work counters (Arnoldi iterations n, sum of j + 1 over
     them, preconditioner applications).  Per cell: operator = diagonal block 15
@@ -376,11 +376,13 @@ def class_bytes(cls: str, prof: dict, T: int, F: int, steps: int, sweeps: int, e
     op = sM * (15 + 9) + 12
     if cls == "orth":
         # per iteration j: dots read V_0..V_j and w, the update reads them again and
-        # writes w: (2 j + 5) vectors; FP64 mode runs the pair twice (CGS2)
-        vecs = 2 * jsum + 3 * n
+        # writes w: (2 j + 5) vectors; FP64 mode runs the pair twice (CGS2); with the
+        # products formed in the operator kernel only the update's (j + 3) remain
+        vecs = (jsum + 2 * n) if fused_dots else (2 * jsum + 3 * n)
         return T * 20 * sB * vecs * (1 if mixed else 2)
     if cls == "spmv":                   # y = K z: z (own + neighbour values), operator, y (basis)
-        return T * (op + 20 * sZ + 20 * sB) * n
+        # (+ V_0..V_j when the operator kernel also forms the Gram-Schmidt products)
+        return T * ((op + 20 * sZ + 20 * sB) * n + (20 * sB * jsum if fused_dots else 0))
     if cls == "ilu":
         pc = prof["precond"]
         if exact:
@@ -419,7 +421,8 @@ def timed_leg(args, case, precision: str, world: int, dev, sample_clocks: bool):
                     limiter=int(args.limiter), warm_extrap=WARM[args.warm], no_graphs=GRAPHS[args.graphs],
                     ilu_fp16=int(mixed and args.ilu16 == "on"), ilu_fuse_first=int(args.ilu_fuse == "on"),
                     flux_split=FLUX_SPLIT[args.flux_split], gmres_m=args.gmres_m,
-                    flux_lead=int(args.flux_lead == "pairs"), ilu_sweep_pairs=int(args.sweep_pairs == "on"))
+                    flux_lead=int(args.flux_lead == "pairs"), ilu_sweep_pairs=int(args.sweep_pairs == "on"),
+                    spmv_dots=int(args.spmv_dots == "on"))
     w = torch.from_numpy(case.w0.copy()).to(dev)
     stream = torch.cuda.current_stream()
     tune = m.autotune(w, trial_steps=2) if args.tune else None
@@ -453,7 +456,7 @@ def timed_leg(args, case, precision: str, world: int, dev, sample_clocks: bool):
             "knobs": {"ilu_sweeps": m.cfg.ilu_sweeps, "ilu_sweeps_bwd": m.cfg.ilu_sweeps_bwd,
                       "ilu_fuse_first": m.cfg.ilu_fuse_first, "warm_extrap": m.cfg.warm_extrap,
                       "inner_rtol": m.cfg.inner_rtol, "gmres_m": m.cfg.gmres_m,
-                      "ilu_sweep_pairs": m.cfg.ilu_sweep_pairs,
+                      "ilu_sweep_pairs": m.cfg.ilu_sweep_pairs, "spmv_dots": m.cfg.spmv_dots,
                       "flux_variant": tune["flux_variant"] if tune else 0}}
 
 
@@ -502,7 +505,8 @@ def run_gks(args, world, rank, local):
         if nm not in ("flux", "ctl") and ms_c > 0:
             by = class_bytes(nm, prof, T, F, args.steps, main["knobs"]["ilu_sweeps"], exact, mixed, basis32,
                              mixed and args.ilu16 == "on", main["knobs"]["ilu_sweeps_bwd"],
-                             bool(main["knobs"]["ilu_fuse_first"]), bool(main["knobs"]["ilu_sweep_pairs"]))
+                             bool(main["knobs"]["ilu_fuse_first"]), bool(main["knobs"]["ilu_sweep_pairs"]),
+                             bool(main["knobs"]["spmv_dots"]) and basis32)
             gbs = by / (ms_c / 1e3) / 1e9
             ent.update({"bytes": by, "gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 3)})
         classes[nm] = ent
@@ -564,7 +568,8 @@ def run_gks(args, world, rank, local):
         out["cpu_baseline"] = cb
         if mixed:
             mkw = gks_mixed_kw(args)
-            mkw.update(main["knobs"])
+            # the flux launch shape is a property of the tuned handle, not of its configuration
+            mkw.update({k: v for k, v in main["knobs"].items() if k != "flux_variant"})
             out["error_vs_oracle"] = errors_vs_oracle(small, w_o, dts, dev, mkw)
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -665,7 +670,8 @@ def run_batch(args, world, rank, local):
     e2e_value = world * T * args.steps / allmax(world, time.perf_counter() - t0)
     knobs = {"ilu_sweeps": b.cfg.ilu_sweeps, "ilu_sweeps_bwd": b.cfg.ilu_sweeps_bwd,
              "ilu_fuse_first": b.cfg.ilu_fuse_first, "warm_extrap": b.cfg.warm_extrap,
-             "inner_rtol": b.cfg.inner_rtol, "gmres_m": b.cfg.gmres_m, "ilu_sweep_pairs": b.cfg.ilu_sweep_pairs}
+             "inner_rtol": b.cfg.inner_rtol, "gmres_m": b.cfg.gmres_m, "ilu_sweep_pairs": b.cfg.ilu_sweep_pairs,
+             "spmv_dots": b.cfg.spmv_dots}
     names = PROF_NAMES
     hbm_peak = measured_peaks().get("hbm_gbs") or HBM_FALLBACK_GBS
     classes = {}
@@ -674,7 +680,8 @@ def run_batch(args, world, rank, local):
         if nm not in ("flux", "ctl") and prof["ms"][q] > 0:
             by = class_bytes(nm, prof, T, F, args.steps, knobs["ilu_sweeps"], False, mixed,
                              mixed and args.basis == "fp32", mixed and args.ilu16 == "on", knobs["ilu_sweeps_bwd"],
-                             bool(knobs["ilu_fuse_first"]), bool(knobs["ilu_sweep_pairs"]))
+                             bool(knobs["ilu_fuse_first"]), bool(knobs["ilu_sweep_pairs"]),
+                             bool(knobs["spmv_dots"]) and mixed and args.basis == "fp32")
             gbs = by / (prof["ms"][q] / 1e3) / 1e9
             ent.update({"bytes": by, "gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 3)})
         classes[nm] = ent
@@ -841,6 +848,8 @@ def main():
     ap.add_argument("--gmres-m", type=int, default=30, help="GMRES restart length (the tuner may pick a shorter one)")
     ap.add_argument("--flux-lead", default="pairs", choices=["pairs", "fp64"],
                     help="mixed path: the flux's FP64-accuracy part in double-FP32 pairs (default) or in FP64")
+    ap.add_argument("--spmv-dots", default="on", choices=["on", "off"],
+                    help="FP32 basis: the operator kernel also forms the Gram-Schmidt products")
     ap.add_argument("--sweep-pairs", default="on", choices=["on", "off"],
                     help="two ILU sweeps of a relation per launch (same results)")
     ap.add_argument("--ilu-fuse", default="on", choices=["on", "off"],

@@ -184,6 +184,11 @@ typedef struct gks_config {
                               launch, each cell forming its upper neighbours'
                               first-sweep values itself; 0 one sweep per launch.
                               Same arithmetic, same results                         */
+    int32_t spmv_dots;     /* mixed precision with basis_fp32 and the per-cell equations:
+                              1 (default) the operator kernel of an Arnoldi step also
+                              forms the Gram-Schmidt products with the basis (the new
+                              vector is not read back); 0 a separate dot-product
+                              kernel.  Results agree to rounding                      */
     int32_t flux_lead;     /* mixed precision: 1 (default) the flux's parts that need
                               more than FP32 (Gauss-point values, interface state,
                               collision time, zeroth-order terms) in double-FP32

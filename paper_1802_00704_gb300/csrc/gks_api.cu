@@ -71,6 +71,7 @@ gks_status check_config(const gks_config &c)
     ok = ok && (c.flux_split == 0 || c.flux_split == 1);
     ok = ok && (c.flux_lead == 0 || c.flux_lead == 1);
     ok = ok && (c.ilu_sweep_pairs == 0 || c.ilu_sweep_pairs == 1);
+    ok = ok && (c.spmv_dots == 0 || c.spmv_dots == 1);
     if (!ok) {
         set_error("invalid gks_config");
         return GKS_EINVAL;
@@ -199,6 +200,7 @@ void gks_config_default(gks_config *c)
     c->ilu_fuse_first = 1;
     c->flux_split = 1;
     c->ilu_sweep_pairs = 1;
+    c->spmv_dots = 1;
     c->flux_lead = 1;
 }
 

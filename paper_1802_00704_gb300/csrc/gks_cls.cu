@@ -245,6 +245,57 @@ __global__ void k_spmv(DeviceMesh d, const TM *__restrict__ Dg, const TM *__rest
     }
 }
 
+// y = K z with the first Gram-Schmidt pass fused in (the FP32-basis inner
+// cycles): each thread keeps its cell's y_i in registers and forms the
+// products with V_0..V_j at the same cell, so the new basis vector is not read
+// back from HBM by a separate dot-product kernel.  part[blk][v][k] =
+// sum over the block's cells of <V_k, y>_v: FP32 products and warp sums (as
+// k_dots), each warp's sums widened to FP64 and added across the block's warps
+// in order.  Deterministic; a different summation order than k_dots, so the
+// iterates agree with the unfused path to rounding.
+__global__ void __launch_bounds__(kBlock, 3)
+    k_spmv_dots(DeviceMesh d, const float *__restrict__ Dg, const float *__restrict__ alg,
+                const float *__restrict__ exg, const float *__restrict__ eyg, const float *__restrict__ x,
+                float *__restrict__ y, const float *__restrict__ V, int j, double *__restrict__ part, int pstride)
+{
+    __shared__ float sh[kBlock / 32][NV];
+    const int64_t T = d.T;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float acc[NX];
+#pragma unroll
+    for (int q = 0; q < NX; ++q) acc[q] = 0.0f;
+    if (i < T) {
+        cell_apply<float, float, false>(d, Dg, alg, exg, eyg, x, i, acc);
+#pragma unroll
+        for (int q = 0; q < NX; ++q) y[q * T + i] = acc[q];
+    }
+    const int64_t vs = (int64_t)NX * T;
+    for (int k = 0; k <= j; ++k) {
+        float sv[NV] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (i < T) {
+            const float *vk = V + k * vs;
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int l = 0; l < ND; ++l) sv[v] = fmaf(vk[(v * ND + l) * T + i], acc[v * ND + l], sv[v]);
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+            for (int o = 16; o > 0; o >>= 1) sv[v] += __shfl_down_sync(0xffffffffu, sv[v], o);
+        if (lane == 0)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) sh[warp][v] = sv[v];
+        __syncthreads();
+        if (threadIdx.x < NV) {
+            double t = 0.0;
+            for (int w = 0; w < kBlock / 32; ++w) t += double(sh[w][threadIdx.x]);
+            part[(blockIdx.x * NV + threadIdx.x) * pstride + k] = t;
+        }
+        __syncthreads();
+    }
+}
+
 // ---- double-FP32 arithmetic for the refinement residual of the mixed mode.
 // A value is the unevaluated sum h + l of two FP32 numbers (about 48
 // significant bits; Dekker 1971).  The product of two high parts is exact as
@@ -1403,7 +1454,7 @@ bool prepare_graphs(gks_mesh *m)
     if (g.disabled) return false;
     const gks_config &c = m->cfg;
     if (g.sweeps != c.ilu_sweeps || g.sweeps_bwd != c.ilu_sweeps_bwd || g.fuse != c.ilu_fuse_first ||
-        g.pairs != c.ilu_sweep_pairs ||
+        g.pairs != c.ilu_sweep_pairs || g.spmv_dots != c.spmv_dots ||
         g.precond != c.precond ||
         g.maxit != c.gmres_maxit || g.eta != c.inner_rtol ||
         g.rtol != c.gmres_rtol || (int)g.iter.size() != m->wk.m) {
@@ -1413,6 +1464,7 @@ bool prepare_graphs(gks_mesh *m)
         g.sweeps_bwd = c.ilu_sweeps_bwd;
         g.fuse = c.ilu_fuse_first;
         g.pairs = c.ilu_sweep_pairs;
+        g.spmv_dots = c.spmv_dots;
         g.precond = c.precond;
         g.maxit = c.gmres_maxit;
         g.eta = c.inner_rtol;
@@ -1725,16 +1777,24 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
             return st;
         prof_stop(m, slot, q);
         slot = prof_start(m, kProfSpmv, q);
-        if (mixed)
+        // the FP32 basis with the per-cell equations: the operator kernel also
+        // forms the first Gram-Schmidt products (k_spmv_dots)
+        const bool fused_dots = std::is_same<TB, float>::value && !d.alr32 && m->cfg.spmv_dots;
+        if (fused_dots) {
+            k_spmv_dots<<<nb, kBlock, 0, q>>>(d, d.D32, d.alpha32, d.ex32, d.ey32, k.Z32 + j * vs,
+                                               reinterpret_cast<float *>(vj1), reinterpret_cast<const float *>(V),
+                                               j, k.part, ps);
+        } else if (mixed) {
             spmv32(q, k.Z32 + j * vs, vj1);
-        else
+        } else {
             spmv64(q, k.Z + j * vs, vj1, 0, nullptr, nullptr);
+        }
         note_launch();
         prof_stop(m, slot, q);
         slot = prof_start(m, kProfOrth, q);
         // classical Gram-Schmidt: twice in FP64 mode; once in the mixed mode, whose
         // cycles only reduce the residual by inner_rtol before an FP64 restart
-        if ((st = dots<TB>(m, V, vj1, j, k.part, ps, q)) != GKS_OK) return st;
+        if (!fused_dots && (st = dots<TB>(m, V, vj1, j, k.part, ps, q)) != GKS_OK) return st;
         k_reduce<<<dim3(j + 1, ns), kReduceThreads, 0, q>>>(k.part, d.case_blk, ps, k.hcol, ps, 0, k.vn, mm + 1,
                                                              k.hco, ps);
         note_launch();

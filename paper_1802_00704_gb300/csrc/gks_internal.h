@@ -184,7 +184,7 @@ struct SolveGraphs {
     std::vector<int64_t> iter_launches;
     cudaGraphExec_t start = nullptr, restart = nullptr;
     int64_t start_launches = 0, restart_launches = 0;
-    int32_t sweeps = -1, sweeps_bwd = -2, fuse = -1, precond = -1, maxit = -1, pairs = -1;
+    int32_t sweeps = -1, sweeps_bwd = -2, fuse = -1, precond = -1, maxit = -1, pairs = -1, spmv_dots = -1;
     double eta = -1.0, rtol = -1.0;
     bool disabled = false;                          // a capture failed: launch directly
     // device-controlled whole solve

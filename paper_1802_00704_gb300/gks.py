@@ -49,7 +49,8 @@ class Config(C.Structure):
                 ("inner_rtol", C.c_double), ("prandtl", C.c_double), ("slope0_mode", C.c_int32),
                 ("ilu_fp16", C.c_int32), ("cls_global", C.c_int32), ("cls_M", C.c_int32),
                 ("ilu_sweeps_bwd", C.c_int32), ("ilu_fuse_first", C.c_int32),
-                ("flux_split", C.c_int32), ("ilu_sweep_pairs", C.c_int32), ("flux_lead", C.c_int32)]
+                ("flux_split", C.c_int32), ("ilu_sweep_pairs", C.c_int32), ("spmv_dots", C.c_int32),
+                ("flux_lead", C.c_int32)]
 
 
 class SolveInfo(C.Structure):

@@ -63,6 +63,12 @@ def test_gram_schmidt_operator_and_residual_bytes():
     # FP64: 8-byte basis and the classical Gram-Schmidt pass twice
     assert bench.class_bytes("orth", p, T=T, F=0, steps=1, sweeps=2, exact=False, mixed=False,
                              basis32=False) == T * 20 * 8 * (2 * 12 + 3 * 6) * 2
+    # the first Gram-Schmidt products in the operator kernel: the orth class keeps the update
+    # ((j + 3) vectors), the operator class adds the basis vectors V_0..V_j
+    assert bench.class_bytes("orth", p, T=T, F=0, steps=1, sweeps=2, exact=False, mixed=True, basis32=True,
+                             fused_dots=True) == T * 20 * 4 * (12 + 2 * 6)
+    assert bench.class_bytes("spmv", p, T=T, F=0, steps=1, sweeps=2, exact=False, mixed=True, basis32=True,
+                             fused_dots=True) == T * ((4 * 24 + 12 + 20 * 4 + 20 * 4) * 6 + 20 * 4 * 12)
     # operator: blocks (24 values) + neighbour indices + source + result per iteration
     assert bench.class_bytes("spmv", p, T=T, F=0, steps=1, sweeps=2, exact=False, mixed=True,
                              basis32=True) == T * (4 * 24 + 12 + 20 * 4 + 20 * 4) * 6
