@@ -126,12 +126,17 @@ typedef struct gks_config {
     int32_t second_order;  /* 1: second-order variant, k_i = 1 (linear CLS
                               reconstruction) for every cell (the paper's second- vs
                               third-order comparison, Sec. IV)                        */
-    int32_t no_graphs;     /* how the CLS solve is launched (same kernels, same order,
-                              same results): 0 one CUDA graph per solve whose while
-                              and if nodes take the GMRES cycle and Arnoldi decisions
-                              on the device (no host round trip); 1 the kernels one
-                              by one, the host reading the stop flags after every
-                              Arnoldi step; 2 as 1 but replaying a graph per step     */
+    int32_t no_graphs;     /* how the CLS solve and the step loop are launched (same
+                              kernels, same order, same results): 0 one CUDA graph per
+                              solve whose while and if nodes take the GMRES cycle and
+                              Arnoldi decisions on the device (no host round trip),
+                              and gks_run / gks_batch_run (without a steady tolerance)
+                              as one graph launch whose while node over the steps,
+                              with the solve nested in its body, ends on the device
+                              once every case is done or max_steps loops ran; 1 the
+                              kernels one by one, the host reading the stop flags
+                              after every Arnoldi step and the done flags every 16
+                              steps; 2 as 1 but replaying a graph per solve part     */
     int32_t limit_char;    /* 1: the DWBAP limiter works on characteristic variables
                               (eigenvectors of the Euler flux Jacobian at the cell
                               average, Sec. IV.B) instead of conservative ones        */
@@ -293,7 +298,10 @@ GKS_EXPORT gks_status gks_batch_create(const gks_case_desc *cases, int32_t n_cas
  * goes non-physical or whose GMRES hits gmres_maxit stops; the others go on.
  * w: device [4][sum n_tri].  t_reached, case_status (GKS_OK, GKS_ENONPHYS,
  * GKS_ENOCONV): host [n_cases], may be NULL.  Returns GKS_OK unless an argument
- * or CUDA error occurs.  Synchronises the stream once per step. */
+ * or CUDA error occurs.  No host round trip per step: with graphs on
+ * (no_graphs = 0) the steps are one graph launch that the device ends, else the
+ * host looks at the done flags every 16 steps; the stream is synchronised at the
+ * start and at the end of the call. */
 GKS_EXPORT gks_status gks_batch_run(gks_mesh *batch, double *w, const double *t_final, int64_t max_steps,
                                     double *t_reached, int32_t *case_status, gks_batch_info *info, void *stream);
 
@@ -376,7 +384,9 @@ GKS_EXPORT gks_status gks_step(gks_mesh *mesh, double *w, double *dt_inout, gks_
 /* Steps w (device [4][n_tri]) in place until t_final (the last step is cut to
  * land on it; t_final <= 0: no time limit), max_steps steps, or, if
  * steady_tol > 0, until the steady residual (gks_run_info) drops below it.
- * info (host, may be NULL). */
+ * info (host, may be NULL).  Without a steady tolerance the steps run as in
+ * gks_batch_run (one graph launch with graphs on); with one, the host reads the
+ * residual after every step. */
 GKS_EXPORT gks_status gks_run(gks_mesh *mesh, double *w, double t_final, int64_t max_steps, double steady_tol,
                    gks_run_info *info, void *stream);
 

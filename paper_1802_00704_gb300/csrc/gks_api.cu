@@ -312,7 +312,7 @@ gks_status gks_reset_warm_start(gks_mesh *m)
     DeviceGuard g(m->device);
     GKS_CUDA(cudaMemset(m->wk.x, 0, sizeof(double) * 20 * m->d.T));
     GKS_CUDA(cudaMemset(m->wk.bnorm, 0, sizeof(double) * m->wk.ns));
-    m->wk.nsolve = 0;
+    GKS_CUDA(cudaMemset(m->wk.nsolve, 0, sizeof(int64_t)));
     return GKS_OK;
 }
 
@@ -412,14 +412,19 @@ gks_status run_begin(gks_mesh *m, const double *tf, cudaStream_t s)
 // The step loop on the device state without a host round trip per step: every
 // loop takes one step of each case that is not done (CFL step clipped to the
 // case's end time, CLS solve, limiter, flux, update), then a case whose status
-// bits are set stops and the others advance their clocks.  The host looks at
-// the done flags every kCheckEvery loops and stops once every case is done.
+// bits are set stops and the others advance their clocks.  With graphs on, the
+// loop is one launch of a graph whose while node the device ends once every
+// case is done or max_steps loops ran; otherwise the host enqueues the steps
+// and looks at the done flags every kCheckEvery loops.
 gks_status run_steps_async(gks_mesh *m, int64_t max_steps, cudaStream_t s)
 {
     Work &k = m->wk;
     const int32_t n = m->n_case;
-    std::vector<int32_t> done(n);
     gks_status st;
+    bool graph = false;
+    if (max_steps > 0 && (st = run_graph_launch(m, max_steps, s, &graph)) != GKS_OK) return st;
+    if (graph) return GKS_OK;
+    std::vector<int32_t> done(n);
     int64_t q = 0;
     while (q < max_steps) {
         const int64_t chunk = std::min<int64_t>(kCheckEvery, max_steps - q);

@@ -14,6 +14,7 @@
 // which saves one read and one write of the new vector per iteration.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <type_traits>
 
 #include "gks_internal.h"
@@ -1155,20 +1156,27 @@ __global__ void k_combine_z(DeviceMesh d, const TZ *__restrict__ Z, const double
     }
 }
 
-// Warm start of the next solve (cases not done) from the last solutions
+// Warm start of solve n (cases not done) from the last solutions
 // x = s_{n-1}, xp = s_{n-2}, xpp = s_{n-3}: order 0 keeps x, order 1 takes
 // 2 x - xp, order 2 takes 3 x - 3 xp + xpp (polynomial extrapolation in the
-// step index).  The history shifts by a swap of the two buffers on the host
-// after this launch: the old x goes into xpp's buffer (the next xp), and xp's
-// buffer (the next xpp) already holds s_{n-2}, so one vector is written
+// step index).  The history shifts by an exchange of the two buffers' roles,
+// which follow the parity of the device's solve count n (k_mark_noconv raises
+// it after the solve): the old x goes into xpp's buffer (the next xp), and
+// xp's buffer (the next xpp) already holds s_{n-2}, so one vector is written
 // instead of two.  Cells of finished cases keep their history: their two
-// buffers exchange contents, which the swap undoes.
-__global__ void k_warm(DeviceMesh d, double *__restrict__ x, double *__restrict__ xp, double *__restrict__ xpp,
-                       const int32_t *__restrict__ done, int order)
+// buffers exchange contents, which the exchange of roles undoes.
+__global__ void k_warm(DeviceMesh d, double *__restrict__ x, double *__restrict__ h0, double *__restrict__ h1,
+                       const int32_t *__restrict__ done, const int64_t *__restrict__ nsolve, int max_order)
 {
     const int64_t T = d.T;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= T) return;
+    // n solves so far: the two history buffers swap roles after every solve, and
+    // the extrapolation uses as many past solutions as exist
+    const int64_t n = *nsolve;
+    double *__restrict__ xp = (n & 1) ? h1 : h0;
+    double *__restrict__ xpp = (n & 1) ? h0 : h1;
+    const int order = (max_order >= 2 && n >= 3) ? 2 : (n >= 2 ? 1 : 0);
     if (done[d.blk_case[blockIdx.x]]) {
 #pragma unroll 4
         for (int q = 0; q < NX; ++q) {
@@ -1274,6 +1282,30 @@ __global__ void k_cond(const int32_t *__restrict__ ctl, int ns, int which, cudaG
     if (set) cudaGraphSetConditional(h, v);
 }
 
+// Condition of the device-controlled step loop (one block): any case not done,
+// and the loops of this launch (run_ctl[0]) below its limit (run_ctl[1]).
+// entry = 1 before the loop (no loops yet); otherwise at the end of a loop,
+// which it counts in run_ctl[0] and in ctr[kCtrRun].
+__global__ void k_run_cond(const int32_t *__restrict__ done, int n, int64_t *run_ctl, int64_t *ctr,
+                           cudaGraphConditionalHandle h, int entry)
+{
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    int a = 0;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) a |= done[c] == 0;
+    if (a) atomicOr(&any, 1);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    int64_t loops = 0;
+    if (!entry) {
+        loops = run_ctl[0] + 1;
+        ctr[kCtrRun] += 1;
+    }
+    run_ctl[0] = loops;
+    cudaGraphSetConditional(h, (any && loops < run_ctl[1]) ? 1u : 0u);
+}
+
 // g = beta e_1 for active systems.
 __global__ void k_init_g(double *g, int m, const double *__restrict__ beta, const int32_t *__restrict__ ctl, int ns)
 {
@@ -1297,11 +1329,14 @@ __global__ void k_zero_trivial(DeviceMesh d, double *__restrict__ x, const doubl
     }
 }
 
-// status[c] |= noconv for cases with a system that stopped above the tolerance
+// status[c] |= noconv for cases with a system that stopped above the tolerance;
+// the solve count of the warm start (k_warm) goes up by one
 __global__ void k_mark_noconv(const double *__restrict__ bnorm, const double *__restrict__ beta,
-                              const int32_t *__restrict__ done, int ns, double rtol, int32_t *status)
+                              const int32_t *__restrict__ done, int ns, double rtol, int32_t *status,
+                              int64_t *nsolve)
 {
     const int sy = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sy == 0) ++*nsolve;
     if (sy >= ns || done[sy >> 2]) return;
     if (bnorm[sy] > 0.0 && beta[sy] > rtol * bnorm[sy]) atomicOr(&status[sy >> 2], kStatusNoConv);
 }
@@ -1440,6 +1475,11 @@ void take_counters(gks_mesh *m)
         } else if (q == kCtrCycles && d > 0) {
             g_launches.fetch_add(d * g.whole_cycle_launches);
             m->prof.residuals += d;
+        } else if (q == kCtrRun && d > 0) {
+            // loops of the step-loop graph: their kernels outside the solve's
+            // cycles, and the first residual of each loop's solve
+            g_launches.fetch_add(d * g.run_loop_launches);
+            m->prof.residuals += d;
         }
     }
 }
@@ -1458,7 +1498,7 @@ bool prepare_graphs(gks_mesh *m)
         g.precond != c.precond ||
         g.maxit != c.gmres_maxit || g.eta != c.inner_rtol ||
         g.rtol != c.gmres_rtol || (int)g.iter.size() != m->wk.m) {
-        if (g.whole) flush_solve_counters(m);
+        if (g.whole || g.run) flush_solve_counters(m);
         destroy_graph_execs(&g);
         g.sweeps = c.ilu_sweeps;
         g.sweeps_bwd = c.ilu_sweeps_bwd;
@@ -1568,7 +1608,30 @@ gks_status add_cond(cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHand
     return GKS_OK;
 }
 
-// The device-controlled solve as one executable graph:
+// The device counters of the device-controlled graphs (allocated once per handle).
+gks_status ensure_counters(gks_mesh *m, cudaStream_t s)
+{
+    SolveGraphs &G = *m->graphs;
+    if (G.ctr) return GKS_OK;
+    GKS_CUDA(cudaMalloc(&G.ctr, sizeof(int64_t) * kCtrLen));
+    GKS_CUDA(cudaMallocHost(&G.h_ctr, sizeof(int64_t) * kCtrLen));
+    GKS_CUDA(cudaMemsetAsync(G.ctr, 0, sizeof(int64_t) * kCtrLen, s));
+    G.ctr_seen.assign(kCtrLen, 0);
+    return GKS_OK;
+}
+
+// A device-controlled solve built as part of a larger graph: into g after dep
+// (NULL: with no dependency); sink receives its last node, launches the kernels
+// that run once per solve (the start part and what follows the cycle loop).
+struct SolveEmbed {
+    cudaGraph_t g = nullptr;
+    cudaGraphNode_t dep = nullptr;
+    cudaGraphNode_t sink = nullptr;
+    int64_t launches = 0;
+};
+
+// The device-controlled solve as one executable graph (or, with emb, as nodes
+// of the caller's graph):
 //   start; c = any active
 //   while (c) { i_0 = any running
 //               if (i_0) { Arnoldi 0; i_1 = any running
@@ -1577,22 +1640,19 @@ gks_status add_cond(cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHand
 // The condition kernels replace the host flags of the per-part graphs; the
 // conditions of an index are only evaluated once the one before it has run.
 template <typename SB, typename IB, typename RB>
-gks_status build_whole(gks_mesh *m, cudaStream_t s, SB &&start_body, IB &&iter_body, RB &&restart_body)
+gks_status build_whole(gks_mesh *m, cudaStream_t s, SB &&start_body, IB &&iter_body, RB &&restart_body,
+                       SolveEmbed *emb = nullptr)
 {
     SolveGraphs &G = *m->graphs;
     Work &k = m->wk;
     const int ns = k.ns, mm = k.m;
     const int64_t limit = (int64_t)m->cfg.gmres_maxit + 1;
-    if (!G.ctr) {
-        GKS_CUDA(cudaMalloc(&G.ctr, sizeof(int64_t) * kCtrLen));
-        GKS_CUDA(cudaMallocHost(&G.h_ctr, sizeof(int64_t) * kCtrLen));
-        GKS_CUDA(cudaMemsetAsync(G.ctr, 0, sizeof(int64_t) * kCtrLen, s));
-        G.ctr_seen.assign(kCtrLen, 0);
-    }
+    if (const gks_status r = ensure_counters(m, s); r != GKS_OK) return r;
     int64_t *ctr = G.ctr;
     const int32_t *ctl = k.ctl;
-    cudaGraph_t top = nullptr;
-    GKS_CUDA(cudaGraphCreate(&top, 0));
+    cudaGraph_t top = emb ? emb->g : nullptr;
+    if (!emb) GKS_CUDA(cudaGraphCreate(&top, 0));
+    const size_t ndep = emb && emb->dep ? 1 : 0;
     gks_status st = GKS_OK;
     std::vector<int64_t> nl_iter(mm, 0);
     int64_t nl_start = 0, nl_c0 = 0, nl_restart = 0;
@@ -1601,7 +1661,7 @@ gks_status build_whole(gks_mesh *m, cudaStream_t s, SB &&start_body, IB &&iter_b
         if (cudaGraphConditionalHandleCreate(&h_outer, top, 0, 0) != cudaSuccess) { st = GKS_ECUDA; break; }
         cudaGraphNode_t sink, wnode, inode;
         cudaGraph_t wbody, ibody;
-        st = capture_into(m, top, nullptr, 0, &sink, &nl_start, [&](cudaStream_t q) -> gks_status {
+        st = capture_into(m, top, ndep ? &emb->dep : nullptr, ndep, &sink, &nl_start, [&](cudaStream_t q) -> gks_status {
             gks_status r = start_body(q);
             if (r != GKS_OK) return r;
             k_cond<<<1, kBlock, 0, q>>>(ctl, ns, 0, h_outer, 1, ctr, -1, 1, limit); note_launch();
@@ -1638,12 +1698,14 @@ gks_status build_whole(gks_mesh *m, cudaStream_t s, SB &&start_body, IB &&iter_b
             if (st == GKS_OK && more) st = add_cond(ibody, sink, h_next, cudaGraphCondTypeIf, &inode, &ibody);
         }
         if (st != GKS_OK) break;
-        if (cudaGraphInstantiate(&G.whole, top, 0) != cudaSuccess) {
+        if (emb) {
+            emb->sink = wnode;
+        } else if (cudaGraphInstantiate(&G.whole, top, 0) != cudaSuccess) {
             G.whole = nullptr;
             st = GKS_ECUDA;
         }
     } while (false);
-    cudaGraphDestroy(top);
+    if (!emb) cudaGraphDestroy(top);
     cudaGetLastError();
     if (st != GKS_OK) return st;
     G.whole_start_launches = nl_start;
@@ -1673,9 +1735,11 @@ inline unsigned sblocks(int n) { return (unsigned)((n + 127) / 128); }
 // systems run in lockstep: every launch covers all cases, and per-system masks
 // stop the systems that have converged.
 // The whole solve with the Krylov basis stored as TB (double, or float in the
-// mixed mode with basis_fp32).
+// mixed mode with basis_fp32).  With emb the device-controlled solve and its
+// closing kernel are built into the caller's graph instead of run.
 template <typename TB>
-gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, double *relres, int32_t *converged)
+gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, double *relres, int32_t *converged,
+                       SolveEmbed *emb = nullptr)
 {
     DeviceMesh &d = m->d;
     Work &k = m->wk;
@@ -1854,6 +1918,19 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
     // level-scheduled exact ILU (two launches per level) that is too many nodes
     // on large meshes, whose per-step graphs are built only for the indices used
     const bool few_nodes = m->cfg.precond != GKS_PC_ILU_EXACT || m->lvl_lo_ptr.size() + m->lvl_up_ptr.size() <= 256;
+    if (emb) {
+        if (!G || !few_nodes || G->disabled || m->cfg.no_graphs != 0) return GKS_EINVAL;
+        if ((st = build_whole(m, s, start_body, iter_body, restart_body, emb)) != GKS_OK) return st;
+        int64_t nl = 0;
+        st = capture_into(m, emb->g, &emb->sink, 1, &emb->sink, &nl, [&](cudaStream_t q) -> gks_status {
+            k_mark_noconv<<<sblocks(ns), 128, 0, q>>>(k.bnorm, k.beta, k.done, ns, rtol, k.status, k.nsolve);
+            note_launch();
+            GKS_CUDA(cudaGetLastError());
+            return GKS_OK;
+        });
+        emb->launches = G->whole_start_launches + nl;
+        return st;
+    }
     if (G && few_nodes && !G->disabled && !G->whole_failed && m->cfg.no_graphs != 2) {
         if (!G->whole && build_whole(m, s, start_body, iter_body, restart_body) != GKS_OK) {
             G->whole_failed = true;                     // per-part graphs with host control from now on
@@ -1888,7 +1965,7 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
             return st;
         m->prof.residuals += 1;
     }
-    k_mark_noconv<<<sblocks(ns), 128, 0, s>>>(k.bnorm, k.beta, k.done, ns, rtol, k.status); note_launch();
+    k_mark_noconv<<<sblocks(ns), 128, 0, s>>>(k.bnorm, k.beta, k.done, ns, rtol, k.status, k.nsolve); note_launch();
     if (iters || relres || converged) {
         std::vector<int32_t> it(ns);
         std::vector<double> be(ns), bn(ns);
@@ -1911,23 +1988,121 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
     return GKS_OK;
 }
 
+namespace {
+
+// the extrapolated warm start of the next solve (if configured)
+gks_status launch_warm(gks_mesh *m, cudaStream_t s)
+{
+    Work &k = m->wk;
+    if (!m->cfg.warm_extrap) return GKS_OK;
+    const int slot = prof_start(m, kProfCtl, s);
+    k_warm<<<(unsigned)k.nblk, kBlock, 0, s>>>(m->d, k.x, k.x_prev, k.x_prev2, k.done, k.nsolve, m->cfg.warm_extrap);
+    note_launch();
+    prof_stop(m, slot, s);
+    GKS_CUDA(cudaGetLastError());
+    return GKS_OK;
+}
+
+// The step loop as a graph (see run_graph_launch):
+//   c = any case not done and a loop limit above 0
+//   while (c) { CFL step, clipped to the end times; warm start;
+//               the device-controlled solve; solve count and convergence marks;
+//               iteration sums; limiter; flux; update; per-case clocks;
+//               c = any case not done and the loops of this launch below the limit }
+gks_status build_run(gks_mesh *m, cudaStream_t s)
+{
+    SolveGraphs &G = *m->graphs;
+    Work &k = m->wk;
+    const int n = m->n_case;
+    if (const gks_status r = ensure_counters(m, s); r != GKS_OK) return r;
+    if (!G.h_run) GKS_CUDA(cudaMallocHost(&G.h_run, sizeof(int64_t)));
+    int64_t *ctr = G.ctr;
+    cudaGraph_t top = nullptr;
+    GKS_CUDA(cudaGraphCreate(&top, 0));
+    gks_status st = GKS_OK;
+    int64_t nl_entry = 0, nl_a = 0, nl_b = 0;
+    SolveEmbed e;
+    do {
+        cudaGraphConditionalHandle h;
+        if (cudaGraphConditionalHandleCreate(&h, top, 0, 0) != cudaSuccess) { st = GKS_ECUDA; break; }
+        cudaGraphNode_t sink, wnode;
+        cudaGraph_t body;
+        st = capture_into(m, top, nullptr, 0, &sink, &nl_entry, [&](cudaStream_t q) -> gks_status {
+            k_run_cond<<<1, kBlock, 0, q>>>(k.done, n, k.run_ctl, ctr, h, 1); note_launch();
+            return GKS_OK;
+        });
+        if (st != GKS_OK || (st = add_cond(top, sink, h, cudaGraphCondTypeWhile, &wnode, &body)) != GKS_OK) break;
+        st = capture_into(m, body, nullptr, 0, &sink, &nl_a, [&](cudaStream_t q) -> gks_status {
+            gks_status r;
+            if ((r = launch_cfl_dt(m, k.w, k.dt, q)) != GKS_OK) return r;
+            if ((r = launch_clip_only(m, q)) != GKS_OK) return r;
+            return launch_warm(m, q);
+        });
+        if (st != GKS_OK) break;
+        e.g = body;
+        e.dep = sink;
+        st = k.V32 ? cls_solve_t<float>(m, k.V32, s, nullptr, nullptr, nullptr, &e)
+                   : cls_solve_t<double>(m, k.V, s, nullptr, nullptr, nullptr, &e);
+        if (st != GKS_OK) break;
+        st = capture_into(m, body, &e.sink, 1, &sink, &nl_b, [&](cudaStream_t q) -> gks_status {
+            gks_status r;
+            if ((r = launch_acc_iters(m, q)) != GKS_OK) return r;
+            if (m->cfg.limiter && (r = launch_limiter(m, k.w, k.x, q)) != GKS_OK) return r;
+            if ((r = launch_flux(m, k.w, m->cfg.limiter ? k.xl : k.x, 0.0, k.dt, k.flux, q)) != GKS_OK) return r;
+            if ((r = launch_update(m, k.w, k.flux, q)) != GKS_OK) return r;
+            if ((r = launch_after_step(m, q)) != GKS_OK) return r;
+            k_run_cond<<<1, kBlock, 0, q>>>(k.done, n, k.run_ctl, ctr, h, 0); note_launch();
+            GKS_CUDA(cudaGetLastError());
+            return GKS_OK;
+        });
+        if (st != GKS_OK) break;
+        if (cudaGraphInstantiate(&G.run, top, 0) != cudaSuccess) {
+            G.run = nullptr;
+            st = GKS_ECUDA;
+        }
+    } while (false);
+    cudaGraphDestroy(top);
+    cudaGetLastError();
+    if (st != GKS_OK) return st;
+    G.run_loop_launches = nl_a + e.launches + nl_b;
+    G.run_cfg = m->cfg;
+    G.run_flux_variant = m->flux_variant;
+    return GKS_OK;
+}
+
+}  // namespace
+
 gks_status cls_solve(gks_mesh *m, cudaStream_t s, int32_t *iters, double *relres, int32_t *converged)
 {
     Work &k = m->wk;
-    if (m->cfg.warm_extrap) {
-        // extrapolate from as many past solutions as exist (up to the configured order)
-        const int order = (m->cfg.warm_extrap >= 2 && k.nsolve >= 3) ? 2 : (k.nsolve >= 2 ? 1 : 0);
-        const unsigned nb = (unsigned)k.nblk;
-        const int slot = prof_start(m, kProfCtl, s);
-        k_warm<<<nb, kBlock, 0, s>>>(m->d, k.x, k.x_prev, k.x_prev2, k.done, order); note_launch();
-        prof_stop(m, slot, s);
-        GKS_CUDA(cudaGetLastError());
-        std::swap(k.x_prev, k.x_prev2);            // the history shift (see k_warm)
+    if (const gks_status st = launch_warm(m, s); st != GKS_OK) return st;
+    return k.V32 ? cls_solve_t<float>(m, k.V32, s, iters, relres, converged)
+                 : cls_solve_t<double>(m, k.V, s, iters, relres, converged);
+}
+
+gks_status run_graph_launch(gks_mesh *m, int64_t max_steps, cudaStream_t s, bool *used)
+{
+    *used = false;
+    if (m->cfg.no_graphs != 0 || !prepare_graphs(m)) return GKS_OK;
+    SolveGraphs &G = *m->graphs;
+    if (G.run_failed || G.disabled) return GKS_OK;
+    if (G.run && (std::memcmp(&G.run_cfg, &m->cfg, sizeof(gks_config)) != 0 ||
+                  G.run_flux_variant != m->flux_variant)) {
+        flush_solve_counters(m);                   // counted with the old graph's launch numbers
+        cudaGraphExecDestroy(G.run);
+        G.run = nullptr;
     }
-    gks_status st = k.V32 ? cls_solve_t<float>(m, k.V32, s, iters, relres, converged)
-                          : cls_solve_t<double>(m, k.V, s, iters, relres, converged);
-    if (st == GKS_OK) ++k.nsolve;
-    return st;
+    if (!G.run && build_run(m, s) != GKS_OK) {
+        G.run_failed = true;                       // the host loop from now on
+        cudaGetLastError();
+        return GKS_OK;
+    }
+    *G.h_run = max_steps;
+    GKS_CUDA(cudaMemcpyAsync(m->wk.run_ctl + 1, G.h_run, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    GKS_CUDA(cudaGraphLaunch(G.run, s));
+    g_launches.fetch_add(1, std::memory_order_relaxed);   // the entry condition
+    *used = true;
+    return GKS_OK;
 }
 
 void flush_solve_counters(gks_mesh *m)
@@ -1950,7 +2125,8 @@ void destroy_graph_execs(SolveGraphs *g)
     if (g->start) cudaGraphExecDestroy(g->start);
     if (g->restart) cudaGraphExecDestroy(g->restart);
     if (g->whole) cudaGraphExecDestroy(g->whole);
-    g->start = g->restart = g->whole = nullptr;
+    if (g->run) cudaGraphExecDestroy(g->run);
+    g->start = g->restart = g->whole = g->run = nullptr;
 }
 
 }  // namespace gks

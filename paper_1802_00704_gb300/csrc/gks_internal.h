@@ -118,7 +118,11 @@ struct Work {
     double *x = nullptr;             // [20][T] CLS coefficients (warm start)
     double *x_prev = nullptr;        // [20][T] the solution before (extrapolated warm start)
     double *x_prev2 = nullptr;       // [20][T] the one before that
-    int64_t nsolve = 0;              // solves since creation or the last warm-start reset
+    int64_t *nsolve = nullptr;       // [1] solves since creation or the last warm-start reset,
+                                     //     counted on the device: its parity says which history
+                                     //     buffer holds the latest solution, its value the order
+                                     //     of the extrapolation (no host state, so a step can repeat
+                                     //     inside a graph)
     double *xl = nullptr;            // [20][T] limited coefficients (limiter on)
     float *x32 = nullptr;            // [20][T] FP32 copy of the coefficients the mixed flux reads
                                      //         (the first half of x2)
@@ -160,6 +164,9 @@ struct Work {
     int64_t *nstep = nullptr;        // [ncase]
     double *last_dt = nullptr;       // [ncase]
     int64_t *iters_acc = nullptr;    // [ns]
+    // the device-controlled step loop (one graph launch per run): loops of the
+    // current launch, the launch's loop limit, loops over all launches
+    int64_t *run_ctl = nullptr;      // [4]
     // pinned host mirrors
     int32_t *h_flags = nullptr;      // [4]
     double *h_scal = nullptr;        // [8]
@@ -177,7 +184,8 @@ struct Work {
 // (ctr) record how often each part ran, for the launch and work counts.
 constexpr int kCtrCycles = kMaxRestart;             // ctr[j]: runs of Arnoldi index j; then cycles
 constexpr int kCtrGuard = kMaxRestart + 1;          // cycles of the current solve (loop guard)
-constexpr int kCtrLen = kMaxRestart + 2;
+constexpr int kCtrRun = kMaxRestart + 2;            // loops of the device-controlled step loop
+constexpr int kCtrLen = kMaxRestart + 3;
 struct SolveGraphs {
     cudaStream_t cap = nullptr;
     std::vector<cudaGraphExec_t> iter;
@@ -195,6 +203,14 @@ struct SolveGraphs {
     int64_t *ctr = nullptr;                         // [kCtrLen] device counters
     int64_t *h_ctr = nullptr;                       // pinned mirror
     std::vector<int64_t> ctr_seen;                  // counts already added to the host totals
+    // the step loop of gks_run / gks_batch_run as one graph with device control
+    // (a while node over the steps, the whole solve nested in its body)
+    cudaGraphExec_t run = nullptr;
+    bool run_failed = false;                        // building it failed: the host loop from now on
+    gks_config run_cfg{};                           // configuration and flux launch shape it was built for
+    int32_t run_flux_variant = -1;
+    int64_t run_loop_launches = 0;                  // kernels per loop outside the solve's cycles
+    int64_t *h_run = nullptr;                       // pinned: the loop limit of the next launch
 };
 void destroy_graph_execs(SolveGraphs *g);
 // Add the counts of the device-controlled solves run so far to the launch and
@@ -252,6 +268,12 @@ void free_mesh(gks_mesh *m);
 // Per system (case * 4 + variable, may be NULL): iterations, relative residuals;
 // *converged = 1 if every active system met the tolerance.
 gks_status cls_solve(gks_mesh *m, cudaStream_t s, int32_t *iters, double *relres, int32_t *converged);
+// The step loop of a run (CFL step clipped to the end times, CLS solve, limiter,
+// flux, update, per-case clocks) for at most max_steps loops as one launch of a
+// graph with device-side control; *used = false when graphs are off, the
+// profiler is on or the graph could not be built (the caller's host loop then
+// runs the steps).
+gks_status run_graph_launch(gks_mesh *m, int64_t max_steps, cudaStream_t s, bool *used);
 
 // flux and update (gks_flux.cu)
 gks_status launch_flux(gks_mesh *m, const double *w, const double *x, double dt_const, const double *dt_dev,

@@ -871,8 +871,10 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
     AL(hcol, ns * (mm + 2)); AL(hco, ns * (mm + 2)); AL(vn, ns * (mm + 1)); AL(bnorm, ns); AL(beta, ns); AL(ctl, kCtlFields * ns); AL(flags, 4);
     AL(sexp, 2 * ns);
     AL(dt, n_cases); AL(tcase, n_cases); AL(tfinal, n_cases); AL(done, n_cases); AL(scal, 8); AL(status, n_cases);
-    AL(nstep, n_cases); AL(last_dt, n_cases); AL(iters_acc, ns);
+    AL(nstep, n_cases); AL(last_dt, n_cases); AL(iters_acc, ns); AL(nsolve, 1); AL(run_ctl, 4);
 #undef AL
+    GKS_CUDA(cudaMemset(k.nsolve, 0, sizeof(int64_t)));
+    GKS_CUDA(cudaMemset(k.run_ctl, 0, sizeof(int64_t) * 4));
     GKS_CUDA(cudaMemset(k.x, 0, sizeof(double) * 20 * T));
     GKS_CUDA(cudaMemset(k.bnorm, 0, sizeof(double) * ns));
     GKS_CUDA(cudaMemset(k.ctl, 0, sizeof(int32_t) * kCtlFields * ns));
@@ -900,6 +902,7 @@ void free_mesh(gks_mesh *m)
         if (m->graphs->cap) cudaStreamDestroy(m->graphs->cap);
         if (m->graphs->ctr) cudaFree(m->graphs->ctr);
         if (m->graphs->h_ctr) cudaFreeHost(m->graphs->h_ctr);
+        if (m->graphs->h_run) cudaFreeHost(m->graphs->h_run);
         delete m->graphs;
         m->graphs = nullptr;
     }

@@ -44,7 +44,7 @@ gks_status time_candidate(gks_mesh *m, const double *w, int trial_steps, cudaStr
     gks_status st;
     GKS_CUDA(cudaMemsetAsync(k.x, 0, sizeof(double) * 20 * m->d.T, s));
     GKS_CUDA(cudaMemsetAsync(k.bnorm, 0, sizeof(double) * k.ns, s));
-    k.nsolve = 0;
+    GKS_CUDA(cudaMemsetAsync(k.nsolve, 0, sizeof(int64_t), s));
     GKS_CUDA(cudaMemsetAsync(k.tfinal, 0, sizeof(double) * n, s));
     GKS_CUDA(cudaMemsetAsync(k.tcase, 0, sizeof(double) * n, s));
     GKS_CUDA(cudaMemsetAsync(k.done, 0, sizeof(int32_t) * n, s));
@@ -193,7 +193,7 @@ extern "C" gks_status gks_autotune(gks_mesh *m, const double *w, int32_t trial_s
     cudaMemsetAsync(m->wk.bnorm, 0, sizeof(double) * m->wk.ns, s);
     cudaMemsetAsync(m->wk.done, 0, sizeof(int32_t) * m->n_case, s);
     cudaMemsetAsync(m->wk.status, 0, sizeof(int32_t) * m->n_case, s);
-    m->wk.nsolve = 0;
+    cudaMemsetAsync(m->wk.nsolve, 0, sizeof(int64_t), s);
     cudaError_t e = cudaStreamSynchronize(s);
     flush_solve_counters(m);
     if (st == GKS_OK && e != cudaSuccess) {

@@ -141,6 +141,62 @@ def test_device_control_and_graphs_equal_direct_launches(G, precision, basis_fp3
     assert cycles[0] > 0 and counts[0] == counts[1] + cycles[0]
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_run_graph_equals_the_host_step_loop(G, precision):
+    """gks_run with graphs on is one launch of a graph whose while node the
+    device ends once every case is done or max_steps loops ran (no_graphs = 0);
+    with 2 the host enqueues the same steps, the solve as per-part graph
+    replays, and looks at the done flags every 16 loops; with 1 every kernel is
+    launched one by one.  Same kernels in the same order, the warm-start
+    history rotated by the device's solve count in all three: states, run
+    results and solver work agree exactly, for a run that stops at max_steps
+    and one that stops at its end time; 1 and 2 count the same launches, and
+    the graph adds one condition kernel per GMRES cycle and per loop, and one
+    per launch."""
+    prec = G.MIXED if precision == "mixed" else G.FP64
+    c = I.shock_vortex_case(40, 20)
+    res = []
+    for mode in (0, 2, 1):
+        m = G.GksMesh(c.mesh, precision=prec, warm_extrap=2, no_graphs=mode)
+        w = dev(c.w0)
+        m.profile_begin([])
+        l0 = G.launch_count()
+        a = m.run(w, max_steps=7)
+        tf = 3.5 * m.cfl_dt(w)
+        b = m.run(w, t_final=tf, max_steps=10000)
+        n = G.launch_count() - l0
+        p = m.profile_end()
+        assert a["steps"] == 7 and b["steps"] >= 3 and abs(b["t"] - tf) <= 1e-15 * tf
+        res.append((host(w), a, b, n, (p["arnoldi"], p["arnoldi_jsum"], p["precond"], p["residuals"])))
+    for q in (1, 2):
+        assert np.array_equal(res[0][0], res[q][0])
+        assert res[0][1] == res[q][1] and res[0][2] == res[q][2] and res[0][4] == res[q][4]
+    assert res[1][3] == res[2][3]
+    loops = res[0][1]["steps"] + res[0][2]["steps"]
+    cycles = res[0][4][3] - loops
+    assert cycles > 0 and res[0][3] == res[1][3] + cycles + loops + 2
+
+
+def test_batch_run_graph_equals_the_host_step_loop(G):
+    """The batched run as one graph launch and as the host loop: cases with
+    their own end times finish at different loops (the graph keeps stepping the
+    others under the per-case masks), and every case's state, time and step
+    count agree exactly."""
+    cases = [I.advection_case(12, k=2), I.shock_vortex_case(30, 15), I.advection_case(7, seed=5)]
+    tf = np.array([0.004, 0.0015, 0.003])
+    res = []
+    for mode in (0, 2):
+        b = G.GksMesh.batch([c.mesh for c in cases], precision=G.MIXED, no_graphs=mode)
+        w = dev(np.ascontiguousarray(np.concatenate([c.w0 for c in cases], axis=1)))
+        r = b.batch_run(w, t_final=tf, max_steps=10000)
+        assert r["n_failed"] == 0 and r["n_finished"] == 3
+        res.append((host(w), r))
+    assert np.array_equal(res[0][0], res[1][0])
+    for k in ("t", "status"):
+        assert np.array_equal(res[0][1][k], res[1][1][k])
+    assert res[0][1]["steps"] == res[1][1]["steps"] and res[0][1]["gmres_iters"] == res[1][1]["gmres_iters"]
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_iteration_cap_stops_solve_the_same_way(G, mode):
     """gmres_maxit below what the tolerance needs: the solve stops at the cap
