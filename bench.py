@@ -698,7 +698,7 @@ def run_batch(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64 (mixed)" if mixed else "f64", "data": "synthetic",
         "config": {"workload": f"batch of {len(cases)} cases (log-uniform 1e3-2e5 triangles; advection / "
-                               f"Riemann strips), {T} triangles, {F} faces, robust limiter, GMRES(12) rtol 1e-12",
+                               f"Riemann strips), {T} triangles, {F} faces, robust limiter, GMRES({knobs['gmres_m']}) rtol 1e-12",
                    "n_tri": T, "n_face": F, "n_cases": len(cases), "precision": args.precision,
                    "krylov_basis": "fp32" if mixed and args.basis == "fp32" else "fp64",
                    "autotuned": bool(args.tune), "knobs": knobs, "failed_cases": int(np.sum(stat != 0)),

@@ -890,12 +890,17 @@ __global__ void __launch_bounds__(kDotThreads, 3) k_dots(int64_t T, int64_t nblk
 // Gram-Schmidt coefficients of the unnormalised basis), w = 0 for the others;
 // optional partial |w|^2 per block.  The arithmetic is in the basis precision
 // TB (FP32 for the inner cycles of the mixed mode); the block's coefficients
-// are rounded to TB once, in shared memory.
-template <typename TB>
+// are rounded to TB once, in shared memory.  J > 0: the Arnoldi index j = J - 1
+// is a compile-time constant and every load of the four systems is issued
+// before the arithmetic (systems that are not running read their vectors too
+// and store zeros), for more bytes in flight per thread; the same operations
+// in the same order as the loop over k.
+template <typename TB, int J = 0>
 __global__ void k_orth_update(DeviceMesh d, const TB *__restrict__ V, TB *__restrict__ w, int j,
                               const double *__restrict__ hc, int hstride, const int32_t *__restrict__ ctl, int ns,
                               double *__restrict__ part, int pstride, int want_norm)
 {
+    if (J > 0) j = J - 1;
     __shared__ double sh[32 * NV];
     __shared__ TB shc[NV][kMaxRestart];
     const int64_t T = d.T;
@@ -906,7 +911,33 @@ __global__ void k_orth_update(DeviceMesh d, const TB *__restrict__ V, TB *__rest
         shc[q / (j + 1)][q % (j + 1)] = TB(hc[(4 * c + q / (j + 1)) * hstride + q % (j + 1)]);
     __syncthreads();
     TB nrm[NV] = {0, 0, 0, 0};
-    if (i < T) {
+    if (J > 0 && i < T) {
+        bool run[NV];
+        TB wv[NV][ND], vk[NV][J > 0 ? J : 1][ND];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            run[v] = ctl[kCtlRunning * ns + 4 * c + v] != 0;
+#pragma unroll
+            for (int l = 0; l < ND; ++l) wv[v][l] = w[(v * ND + l) * T + i];
+#pragma unroll
+            for (int k = 0; k < J; ++k)
+#pragma unroll
+                for (int l = 0; l < ND; ++l) vk[v][k][l] = V[k * vs + (v * ND + l) * T + i];
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+#pragma unroll
+            for (int k = 0; k < J; ++k)
+#pragma unroll
+                for (int l = 0; l < ND; ++l) wv[v][l] = fma(-shc[v][k], vk[v][k][l], wv[v][l]);
+#pragma unroll
+            for (int l = 0; l < ND; ++l) {
+                const TB o = run[v] ? wv[v][l] : TB(0);
+                w[(v * ND + l) * T + i] = o;
+                nrm[v] = fma(o, o, nrm[v]);
+            }
+        }
+    } else if (i < T) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             const int sy = 4 * c + v;
@@ -1342,6 +1373,22 @@ __global__ void k_mark_noconv(const double *__restrict__ bnorm, const double *__
 }
 
 inline unsigned nblocks(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+// k_orth_update with the Arnoldi index unrolled for the first four indices
+// (the inner cycles of the mixed mode rarely go further)
+template <typename TB>
+void launch_orth_update(const DeviceMesh &d, unsigned nb, cudaStream_t q, const TB *V, TB *w, int j,
+                        const double *hc, int hstride, const int32_t *ctl, int ns, double *part, int pstride,
+                        int want_norm)
+{
+    switch (j) {
+    case 0: k_orth_update<TB, 1><<<nb, kBlock, 0, q>>>(d, V, w, j, hc, hstride, ctl, ns, part, pstride, want_norm); break;
+    case 1: k_orth_update<TB, 2><<<nb, kBlock, 0, q>>>(d, V, w, j, hc, hstride, ctl, ns, part, pstride, want_norm); break;
+    case 2: k_orth_update<TB, 3><<<nb, kBlock, 0, q>>>(d, V, w, j, hc, hstride, ctl, ns, part, pstride, want_norm); break;
+    case 3: k_orth_update<TB, 4><<<nb, kBlock, 0, q>>>(d, V, w, j, hc, hstride, ctl, ns, part, pstride, want_norm); break;
+    default: k_orth_update<TB><<<nb, kBlock, 0, q>>>(d, V, w, j, hc, hstride, ctl, ns, part, pstride, want_norm);
+    }
+}
 
 // The reverse-slot coefficients of the global normal equations for the ILU
 // kernels (all NULL for the per-cell equations).
@@ -1862,14 +1909,14 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
         k_reduce<<<dim3(j + 1, ns), kReduceThreads, 0, q>>>(k.part, d.case_blk, ps, k.hcol, ps, 0, k.vn, mm + 1,
                                                              k.hco, ps);
         note_launch();
-        k_orth_update<TB><<<nb, kBlock, 0, q>>>(d, V, vj1, j, k.hco, ps, k.ctl, ns, k.part, ps, mixed ? 1 : 0);
+        launch_orth_update<TB>(d, nb, q, V, vj1, j, k.hco, ps, k.ctl, ns, k.part, ps, mixed ? 1 : 0);
         note_launch();
         if (!mixed) {
             if ((st = dots<TB>(m, V, vj1, j, k.part, ps, q)) != GKS_OK) return st;
             k_reduce<<<dim3(j + 1, ns), kReduceThreads, 0, q>>>(k.part, d.case_blk, ps, k.y, mm, 0, k.vn, mm + 1,
                                                                  k.hco, ps);
             note_launch();
-            k_orth_update<TB><<<nb, kBlock, 0, q>>>(d, V, vj1, j, k.hco, ps, k.ctl, ns, k.part, ps, 1); note_launch();
+            launch_orth_update<TB>(d, nb, q, V, vj1, j, k.hco, ps, k.ctl, ns, k.part, ps, 1); note_launch();
             k_hadd<<<sblocks(ns * (j + 1)), 128, 0, q>>>(k.hcol, ps, k.y, mm, j, ns); note_launch();
         }
         // |V_{j+1}| and the Givens step of every system

@@ -148,11 +148,13 @@ def test_run_graph_equals_the_host_step_loop(G, precision):
     with 2 the host enqueues the same steps, the solve as per-part graph
     replays, and looks at the done flags every 16 loops; with 1 every kernel is
     launched one by one.  Same kernels in the same order, the warm-start
-    history rotated by the device's solve count in all three: states, run
-    results and solver work agree exactly, for a run that stops at max_steps
-    and one that stops at its end time; 1 and 2 count the same launches, and
-    the graph adds one condition kernel per GMRES cycle and per loop, and one
-    per launch."""
+    history rotated by the device's solve count in all three: states and run
+    results agree exactly, for a run that stops at max_steps and one that
+    stops at its end time.  On the max_steps run the solver work agrees too;
+    1 and 2 count the same launches, and the graph adds one condition kernel
+    per GMRES cycle and per loop, and one per launch.  (After an end time the
+    host loop may enqueue up to 15 loops in which every case is masked, which
+    change nothing; the graph stops at once.)"""
     prec = G.MIXED if precision == "mixed" else G.FP64
     c = I.shock_vortex_case(40, 20)
     res = []
@@ -162,19 +164,18 @@ def test_run_graph_equals_the_host_step_loop(G, precision):
         m.profile_begin([])
         l0 = G.launch_count()
         a = m.run(w, max_steps=7)
-        tf = 3.5 * m.cfl_dt(w)
-        b = m.run(w, t_final=tf, max_steps=10000)
         n = G.launch_count() - l0
         p = m.profile_end()
+        tf = 3.5 * m.cfl_dt(w)
+        b = m.run(w, t_final=tf, max_steps=10000)
         assert a["steps"] == 7 and b["steps"] >= 3 and abs(b["t"] - tf) <= 1e-15 * tf
         res.append((host(w), a, b, n, (p["arnoldi"], p["arnoldi_jsum"], p["precond"], p["residuals"])))
     for q in (1, 2):
         assert np.array_equal(res[0][0], res[q][0])
         assert res[0][1] == res[q][1] and res[0][2] == res[q][2] and res[0][4] == res[q][4]
     assert res[1][3] == res[2][3]
-    loops = res[0][1]["steps"] + res[0][2]["steps"]
-    cycles = res[0][4][3] - loops
-    assert cycles > 0 and res[0][3] == res[1][3] + cycles + loops + 2
+    cycles = res[0][4][3] - 7
+    assert cycles > 0 and res[0][3] == res[1][3] + cycles + 7 + 1
 
 
 def test_batch_run_graph_equals_the_host_step_loop(G):
