@@ -81,11 +81,20 @@ enum {
 
 /* Preconditioner of the CLS GMRES. */
 enum {
-    GKS_PC_ILU_EXACT = 0,  /* block ILU(0) on the RCM order, level-scheduled exact
-                              triangular solves (Sec. III.B as written)              */
+    GKS_PC_ILU_EXACT = 0,  /* block ILU(0) on the RCM order with exact triangular
+                              solves (Sec. III.B as written), each one launch: a row
+                              waits for its lower (upper) neighbours' ready flags and
+                              rows are taken in RCM order by block tickets, so a
+                              block only waits on blocks that already run (a
+                              sync-free level schedule); every wait is bounded
+                              (1 s), and a wait that gives up ends the step with
+                              GKS_ETIMEOUT                                            */
     GKS_PC_ILU_SWEEP = 1,  /* the same ILU(0) factors, each triangular solve applied
                               by ilu_sweeps block-Jacobi sweeps (fully parallel)     */
-    GKS_PC_BJACOBI = 2     /* block-diagonal (cell) inverse only                      */
+    GKS_PC_BJACOBI = 2,    /* block-diagonal (cell) inverse only                      */
+    GKS_PC_ILU_LEVELS = 3  /* the exact solves of GKS_PC_ILU_EXACT launched level by
+                              level (one launch per level of the RCM graph); the
+                              same results bit for bit                               */
 };
 
 enum { GKS_FP64 = 0, GKS_MIXED = 1 };
@@ -492,6 +501,16 @@ enum {
 };
 GKS_EXPORT gks_status gks_probe_df(int32_t op, int64_t n, const double *x, const double *y, double *out,
                                    void *stream);
+
+/* The bounded wait of the sync-free triangular solves on its own: one thread
+ * waits for a device flag to reach 1, giving up after limit_ns nanoseconds of
+ * the GPU's global timer (1 <= limit_ns <= 10^10).  set_flag = 1 sets the flag
+ * before the wait (the wait returns at once), 0 leaves it at 0, which nothing
+ * changes, so the wait runs out.  *timed_out (host) = 1 if it gave up, else 0;
+ * *waited_ns (host, may be NULL) = the time the wait took.  GKS_EINVAL for a
+ * limit outside the range or NULL timed_out.  Synchronises the stream. */
+GKS_EXPORT gks_status gks_probe_wait(int64_t limit_ns, int32_t set_flag, int32_t *timed_out, int64_t *waited_ns,
+                                     void *stream);
 
 /* Thread-local message of the last error, or "" if none. */
 GKS_EXPORT const char *gks_last_error(void);

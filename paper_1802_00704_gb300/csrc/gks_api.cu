@@ -80,9 +80,28 @@ gks_status check_config(const gks_config &c)
         set_error("gks_config.precision: GKS_FP64 or GKS_MIXED");
         return GKS_EINVAL;
     }
-    if (c.precond != GKS_PC_ILU_EXACT && c.precond != GKS_PC_ILU_SWEEP) {
-        set_error("gks_config.precond: only GKS_PC_ILU_EXACT and GKS_PC_ILU_SWEEP are implemented");
-        return GKS_EUNSUPPORTED;
+    if (c.precond < GKS_PC_ILU_EXACT || c.precond > GKS_PC_ILU_LEVELS) {
+        set_error("gks_config.precond: one of GKS_PC_ILU_EXACT, GKS_PC_ILU_SWEEP, GKS_PC_BJACOBI, GKS_PC_ILU_LEVELS");
+        return GKS_EINVAL;
+    }
+    return GKS_OK;
+}
+
+// The status code of a case's status bits; a wait that gave up comes first
+// (the results of that step are not usable), and sets the error message.
+gks_status code_of(int32_t bits)
+{
+    if (bits & kStatusTimeout) {
+        set_error("a bounded wait of the sync-free ILU solve gave up (GKS_PC_ILU_EXACT)");
+        return GKS_ETIMEOUT;
+    }
+    if (bits & kStatusNonPhys) {
+        set_error("non-physical state (rho <= 0 or p <= 0)");
+        return GKS_ENONPHYS;
+    }
+    if (bits & kStatusNoConv) {
+        set_error("GMRES did not reach gmres_rtol within gmres_maxit");
+        return GKS_ENOCONV;
     }
     return GKS_OK;
 }
@@ -125,9 +144,7 @@ gks_status step_internal(gks_mesh *m, double dt_fixed, cudaStream_t s, gks_step_
     int32_t stat = 0;
     if ((st = read_status(m, s, &stat)) != GKS_OK) return st;
     if (dt_taken) *dt_taken = k.h_scal[6];
-    gks_status res = GKS_OK;
-    if (!conv) res = GKS_ENOCONV;
-    if (stat & kStatusNonPhys) res = GKS_ENONPHYS;
+    gks_status res = code_of(stat | (conv ? 0 : kStatusNoConv));
     if (info) {
         info->dt = k.h_scal[6];
         for (int v = 0; v < 4; ++v) {
@@ -136,8 +153,6 @@ gks_status step_internal(gks_mesh *m, double dt_fixed, cudaStream_t s, gks_step_
         }
         info->status = res;
     }
-    if (res == GKS_ENOCONV) set_error("GMRES did not reach gmres_rtol within gmres_maxit");
-    if (res == GKS_ENONPHYS) set_error("non-physical state (rho <= 0 or p <= 0)");
     return res;
 }
 
@@ -296,10 +311,13 @@ gks_status gks_cls_reconstruct(gks_mesh *m, const double *w, double *coef, gks_s
         si.relres[q & 3] = std::max(si.relres[q & 3], rr[q]);
     }
     if (info) *info = si;
-    if (!si.converged) {
-        set_error("GMRES did not reach gmres_rtol within gmres_maxit");
-        return GKS_ENOCONV;
+    if (m->cfg.precond == GKS_PC_ILU_EXACT) {
+        int32_t waited_out = 0;
+        GKS_CUDA(cudaMemcpyAsync(&waited_out, m->wk.sf_ctl + 3, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        GKS_CUDA(cudaStreamSynchronize(s));
+        if (waited_out) return code_of(kStatusTimeout);
     }
+    if (!si.converged) return code_of(kStatusNoConv);
     return GKS_OK;
 }
 
@@ -509,9 +527,7 @@ gks_status gks_run(gks_mesh *m, double *w, double t_final, int64_t max_steps, do
         double tr = 0.0, ld = 0.0;
         int32_t stat = 0;
         if ((st = run_end(m, s, &nst, &tr, &ld, &stat, &its)) != GKS_OK) return st;
-        res = (stat & kStatusNonPhys) ? GKS_ENONPHYS : (stat & kStatusNoConv) ? GKS_ENOCONV : GKS_OK;
-        if (res == GKS_ENOCONV) set_error("GMRES did not reach gmres_rtol within gmres_maxit");
-        if (res == GKS_ENONPHYS) set_error("non-physical state (rho <= 0 or p <= 0)");
+        res = code_of(stat);
         if (info) {
             info->steps = nst;
             info->t = tr;
@@ -597,7 +613,7 @@ gks_status gks_batch_run(gks_mesh *m, double *w, const double *t_final, int64_t 
     int64_t steps = 0;
     int32_t nfail = 0, ndone = 0;
     for (int32_t c = 0; c < n; ++c) {
-        const int32_t cs = (stat[c] & kStatusNonPhys) ? GKS_ENONPHYS : (stat[c] & kStatusNoConv) ? GKS_ENOCONV : GKS_OK;
+        const int32_t cs = code_of(stat[c]);
         if (t_reached) t_reached[c] = tr[c];
         if (case_status) case_status[c] = cs;
         nfail += cs != GKS_OK;

@@ -18,6 +18,7 @@
 #include <type_traits>
 
 #include "gks_internal.h"
+#include "gks_wait.cuh"
 
 namespace gks {
 namespace {
@@ -632,17 +633,32 @@ __global__ void __launch_bounds__(kBlock, 3) k_rhs_df(DeviceMesh d, const float 
 // preconditioner), widened to TM on load.
 // G: global normal equations, the transpose form with the reverse-slot
 // coefficients arg, exrg, eyrg on all five unknowns of the neighbour.
-template <typename TR, typename TZ, typename TM, typename TP = TM, bool G = false>
-__global__ void k_ilu_fwd(DeviceMesh d, const TP *__restrict__ Pg, const TP *__restrict__ alg,
-                          const TP *__restrict__ exg, const TP *__restrict__ eyg, const int32_t *__restrict__ rows,
-                          int64_t nrows, const TR *r, const TZ *zin, TZ *zout, int use_nb, TZ *__restrict__ rcopy,
-                          const TP *__restrict__ arg = nullptr, const TP *__restrict__ exrg = nullptr,
-                          const TP *__restrict__ eyrg = nullptr, const TP *__restrict__ bdgg = nullptr)
+// a neighbour's value: through L2 in the sync-free solves (written by another
+// block of the same launch), a plain load otherwise
+template <bool SF, typename T>
+__device__ __forceinline__ T ldx(const T *p)
+{
+    if constexpr (SF) return __ldcg(p);
+    else return *p;
+}
+
+// A bounded wait of the sync-free solves gives up after 1 s (a correct solve
+// waits a few microseconds per level).
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
+
+// The forward relation of row i (see k_ilu_fwd).  SF: the sync-free exact
+// solve, which waits for each lower neighbour's ready tag before reading its
+// value (through L2) and publishes its own row's tag after the store.
+template <typename TR, typename TZ, typename TM, typename TP, bool G, bool SF>
+__device__ __forceinline__ void ilu_fwd_row(const DeviceMesh &d, const TP *__restrict__ Pg,
+                                            const TP *__restrict__ alg, const TP *__restrict__ exg,
+                                            const TP *__restrict__ eyg, int64_t i, const TR *r, const TZ *zin,
+                                            TZ *zout, int use_nb, TZ *__restrict__ rcopy, const TP *__restrict__ arg,
+                                            const TP *__restrict__ exrg, const TP *__restrict__ eyrg,
+                                            const TP *__restrict__ bdgg, int32_t *sf_flag, int32_t sf_tag,
+                                            int32_t *sf_err)
 {
     const int64_t T = d.T;
-    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q >= nrows) return;
-    const int64_t i = rows ? rows[q] : q;
     TM y[NX];
 #pragma unroll
     for (int k = 0; k < NX; ++k) y[k] = TM(r[k * T + i]);
@@ -652,6 +668,16 @@ __global__ void k_ilu_fwd(DeviceMesh d, const TP *__restrict__ Pg, const TP *__r
     if (rcopy)
 #pragma unroll
         for (int k = 0; k < NX; ++k) rcopy[k * T + i] = TZ(y[k]);
+    if (SF) {
+        // every lower neighbour's tag first (one round trip for all of them)
+        const int32_t *wf[3];
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            const int j = d.nb[s * T + i];
+            wf[s] = (j >= 0 && j < i) ? sf_flag + j : nullptr;
+        }
+        bounded_wait_all(wf[0], wf[1], wf[2], sf_tag, sf_err, kWaitLimitNs);
+    }
     if (use_nb) {
         // unknowns of a neighbour that its off-diagonal block reaches
         constexpr int NA = G ? ND : 2;
@@ -678,6 +704,11 @@ __global__ void k_ilu_fwd(DeviceMesh d, const TP *__restrict__ Pg, const TP *__r
                         zn[v][a] = TM(TZ(t));
                     }
                 }
+            } else if (SF) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v)
+#pragma unroll
+                    for (int a = 0; a < NA; ++a) zn[v][a] = TM(__ldcg(zin + (v * ND + a) * T + j));
             } else {
 #pragma unroll
                 for (int v = 0; v < NV; ++v)
@@ -707,22 +738,35 @@ __global__ void k_ilu_fwd(DeviceMesh d, const TP *__restrict__ Pg, const TP *__r
             for (int c = 0; c < ND; ++c) s = fma(Pm[a * ND + c], y[v * ND + c], s);
             zout[(v * ND + a) * T + i] = TZ(s);
         }
+    if (SF) publish(sf_flag + i, sf_tag);
+}
+
+template <typename TR, typename TZ, typename TM, typename TP = TM, bool G = false>
+__global__ void k_ilu_fwd(DeviceMesh d, const TP *__restrict__ Pg, const TP *__restrict__ alg,
+                          const TP *__restrict__ exg, const TP *__restrict__ eyg, const int32_t *__restrict__ rows,
+                          int64_t nrows, const TR *r, const TZ *zin, TZ *zout, int use_nb, TZ *__restrict__ rcopy,
+                          const TP *__restrict__ arg = nullptr, const TP *__restrict__ exrg = nullptr,
+                          const TP *__restrict__ eyrg = nullptr, const TP *__restrict__ bdgg = nullptr)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= nrows) return;
+    const int64_t i = rows ? rows[q] : q;
+    ilu_fwd_row<TR, TZ, TM, TP, G, false>(d, Pg, alg, exg, eyg, i, r, zin, zout, use_nb, rcopy, arg, exrg, eyrg,
+                                          bdgg, nullptr, 0, nullptr);
 }
 
 // Backward block-ILU relation: x_i = z_i + P_i sum_{j>i} O_ij xin_j (own data
 // loaded before the neighbour gathers; with no upper neighbour the sum is 0
 // and x_i = z_i exactly).
-template <typename TZ, typename TM, typename TP = TM, bool G = false>
-__global__ void __launch_bounds__(kBlock, sizeof(TM) == 4 ? 3 : 1)
-    k_ilu_bwd(DeviceMesh d, const TP *__restrict__ Pg, const TP *__restrict__ alg, const TP *__restrict__ exg,
-              const TP *__restrict__ eyg, const int32_t *__restrict__ rows, int64_t nrows, const TZ *z, const TZ *xin,
-              TZ *xout, const TP *__restrict__ arg = nullptr, const TP *__restrict__ exrg = nullptr,
-              const TP *__restrict__ eyrg = nullptr, const TP *__restrict__ bdgg = nullptr)
+template <typename TZ, typename TM, typename TP, bool G, bool SF>
+__device__ __forceinline__ void ilu_bwd_row(const DeviceMesh &d, const TP *__restrict__ Pg,
+                                            const TP *__restrict__ alg, const TP *__restrict__ exg,
+                                            const TP *__restrict__ eyg, int64_t i, const TZ *z, const TZ *xin,
+                                            TZ *xout, const TP *__restrict__ arg, const TP *__restrict__ exrg,
+                                            const TP *__restrict__ eyrg, const TP *__restrict__ bdgg,
+                                            int32_t *sf_flag, int32_t sf_tag, int32_t *sf_err)
 {
     const int64_t T = d.T;
-    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q >= nrows) return;
-    const int64_t i = rows ? rows[q] : q;
     TM zi[NX], y[NX];
 #pragma unroll
     for (int k = 0; k < NX; ++k) {
@@ -732,6 +776,16 @@ __global__ void __launch_bounds__(kBlock, sizeof(TM) == 4 ? 3 : 1)
     TM Pm[25];
 #pragma unroll
     for (int k = 0; k < 25; ++k) Pm[k] = TM(Pg[k * T + i]);
+    if (SF) {
+        // every upper neighbour's tag first (one round trip for all of them)
+        const int32_t *wf[3];
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            const int j = d.nb[s * T + i];
+            wf[s] = j > i ? sf_flag + j : nullptr;
+        }
+        bounded_wait_all(wf[0], wf[1], wf[2], sf_tag, sf_err, kWaitLimitNs);
+    }
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
         const int j = d.nb[s * T + i];
@@ -739,7 +793,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(TM) == 4 ? 3 : 1)
         const TM sa = TM(alg[s * T + i]), sax = sa * TM(exg[s * T + i]), say = sa * TM(eyg[s * T + i]);
 #pragma unroll
         for (int v = 0; v < NV; ++v)
-            oacc(sa, sax, say, TM(xin[(v * ND + 0) * T + j]), TM(xin[(v * ND + 1) * T + j]), y + v * ND);
+            oacc(sa, sax, say, TM(ldx<SF>(xin + (v * ND + 0) * T + j)), TM(ldx<SF>(xin + (v * ND + 1) * T + j)),
+                 y + v * ND);
         if (G) {
             const TM sr = TM(arg[s * T + i]), srx = sr * TM(exrg[s * T + i]), sry = sr * TM(eyrg[s * T + i]);
             const TM sb = TM(bdgg[s * T + i]);
@@ -747,7 +802,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(TM) == 4 ? 3 : 1)
             for (int v = 0; v < NV; ++v) {
                 TM xj[ND];
 #pragma unroll
-                for (int l = 0; l < ND; ++l) xj[l] = TM(xin[(v * ND + l) * T + j]);
+                for (int l = 0; l < ND; ++l) xj[l] = TM(ldx<SF>(xin + (v * ND + l) * T + j));
                 racc(sr, srx, sry, xj, y + v * ND);
 #pragma unroll
                 for (int l = 2; l < ND; ++l) y[v * ND + l] = fma(sb, xj[l], y[v * ND + l]);
@@ -763,6 +818,103 @@ __global__ void __launch_bounds__(kBlock, sizeof(TM) == 4 ? 3 : 1)
             for (int c = 0; c < ND; ++c) s = fma(Pm[a * ND + c], y[v * ND + c], s);
             xout[(v * ND + a) * T + i] = TZ(s);
         }
+    if (SF) publish(sf_flag + i, sf_tag);
+}
+
+template <typename TZ, typename TM, typename TP = TM, bool G = false>
+__global__ void __launch_bounds__(kBlock, sizeof(TM) == 4 ? 3 : 1)
+    k_ilu_bwd(DeviceMesh d, const TP *__restrict__ Pg, const TP *__restrict__ alg, const TP *__restrict__ exg,
+              const TP *__restrict__ eyg, const int32_t *__restrict__ rows, int64_t nrows, const TZ *z, const TZ *xin,
+              TZ *xout, const TP *__restrict__ arg = nullptr, const TP *__restrict__ exrg = nullptr,
+              const TP *__restrict__ eyrg = nullptr, const TP *__restrict__ bdgg = nullptr)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= nrows) return;
+    const int64_t i = rows ? rows[q] : q;
+    ilu_bwd_row<TZ, TM, TP, G, false>(d, Pg, alg, exg, eyg, i, z, xin, xout, arg, exrg, eyrg, bdgg, nullptr, 0,
+                                      nullptr);
+}
+
+// ---- sync-free exact triangular solves (GKS_PC_ILU_EXACT).  One launch per
+// relation instead of one per level: persistent blocks take tickets for
+// kBlock-row ranges in RCM order (forward: increasing rows, backward:
+// decreasing), so a block only ever waits on rows of tickets taken before its
+// own, by blocks that are already running; within a range a row waits on
+// lower (upper) rows of the same range, which earlier threads finish (threads
+// of a warp make independent progress).  Every row waits for its lower
+// (upper) neighbours' tags (bounded_wait, at most kWaitLimitNs each), reads
+// their values through L2 and publishes its own tag.  The tags of the two
+// relations of application e are 2e + 1 and 2e + 2, so no flag is reset
+// between applications.  ctl: [0] epoch e, [1] forward and [2] backward
+// tickets, [3] sticky wait error.  The arithmetic of a row is that of the
+// level-scheduled launches, so the results are the same bit for bit.
+
+constexpr int kSfBlocksPerSm = 2;       // persistent blocks per SM of the sync-free solves
+
+// Next application: new epoch, tickets back to 0 (clear = 1: only the error word).
+__global__ void k_sf_begin(int32_t *ctl, int clear)
+{
+    if (threadIdx.x != 0) return;
+    if (clear) {
+        ctl[3] = 0;
+        return;
+    }
+    ctl[0] += 1;
+    ctl[1] = 0;
+    ctl[2] = 0;
+}
+
+template <typename TR, typename TZ, typename TM, typename TP, bool G>
+__global__ void __launch_bounds__(kBlock) k_ilu_fwd_sf(DeviceMesh d, const TP *__restrict__ Pg,
+                                                       const TP *__restrict__ alg, const TP *__restrict__ exg,
+                                                       const TP *__restrict__ eyg, const TR *r, TZ *z,
+                                                       int32_t *flag, int32_t *ctl,
+                                                       const TP *__restrict__ arg = nullptr,
+                                                       const TP *__restrict__ exrg = nullptr,
+                                                       const TP *__restrict__ eyrg = nullptr,
+                                                       const TP *__restrict__ bdgg = nullptr)
+{
+    __shared__ int32_t ticket;
+    const int64_t T = d.T;
+    const int64_t nt = (T + kBlock - 1) / kBlock;
+    const int32_t tag = 2 * ctl[0] + 1;
+    for (;;) {
+        if (threadIdx.x == 0) ticket = atomicAdd(ctl + 1, 1);
+        __syncthreads();
+        const int64_t tk = ticket;
+        __syncthreads();
+        if (tk >= nt) return;
+        const int64_t i = tk * kBlock + threadIdx.x;
+        if (i < T)
+            ilu_fwd_row<TR, TZ, TM, TP, G, true>(d, Pg, alg, exg, eyg, i, r, z, z, 1, nullptr, arg, exrg, eyrg, bdgg,
+                                                 flag, tag, ctl + 3);
+    }
+}
+
+template <typename TZ, typename TM, typename TP, bool G>
+__global__ void __launch_bounds__(kBlock) k_ilu_bwd_sf(DeviceMesh d, const TP *__restrict__ Pg,
+                                                       const TP *__restrict__ alg, const TP *__restrict__ exg,
+                                                       const TP *__restrict__ eyg, TZ *x, int32_t *flag,
+                                                       int32_t *ctl, const TP *__restrict__ arg = nullptr,
+                                                       const TP *__restrict__ exrg = nullptr,
+                                                       const TP *__restrict__ eyrg = nullptr,
+                                                       const TP *__restrict__ bdgg = nullptr)
+{
+    __shared__ int32_t ticket;
+    const int64_t T = d.T;
+    const int64_t nt = (T + kBlock - 1) / kBlock;
+    const int32_t tag = 2 * ctl[0] + 2;
+    for (;;) {
+        if (threadIdx.x == 0) ticket = atomicAdd(ctl + 2, 1);
+        __syncthreads();
+        const int64_t tk = ticket;
+        __syncthreads();
+        if (tk >= nt) return;
+        const int64_t i = T - 1 - (tk * kBlock + threadIdx.x);
+        if (i >= 0)
+            ilu_bwd_row<TZ, TM, TP, G, true>(d, Pg, alg, exg, eyg, i, x, x, x, arg, exrg, eyrg, bdgg, flag, tag,
+                                             ctl + 3);
+    }
 }
 
 // ---- two backward preconditioner sweeps per launch: the second sweep of a
@@ -831,7 +983,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(TM) == 4 ? 3 : 2) k_ilu_bwd2(De
 #pragma unroll
         for (int v = 0; v < NV; ++v) oacc(sa, sax, say, x1[v][0], x1[v][1], y + v * ND);
     }
-    TM Pm[25];                               // the cell's own factor last (see k_ilu_fwd2)
+    TM Pm[25];                               // the cell's own factor last, after the gathers
 #pragma unroll
     for (int k = 0; k < 25; ++k) Pm[k] = TM(Pg[k * T + i]);
 #pragma unroll
@@ -1360,16 +1512,19 @@ __global__ void k_zero_trivial(DeviceMesh d, double *__restrict__ x, const doubl
     }
 }
 
-// status[c] |= noconv for cases with a system that stopped above the tolerance;
-// the solve count of the warm start (k_warm) goes up by one
+// status[c] |= noconv for cases with a system that stopped above the tolerance,
+// and |= timeout for every active case if a wait of the sync-free ILU solves
+// gave up during the solve (sf_err, may be NULL); the solve count of the warm
+// start (k_warm) goes up by one
 __global__ void k_mark_noconv(const double *__restrict__ bnorm, const double *__restrict__ beta,
                               const int32_t *__restrict__ done, int ns, double rtol, int32_t *status,
-                              int64_t *nsolve)
+                              int64_t *nsolve, const int32_t *sf_err)
 {
     const int sy = blockIdx.x * blockDim.x + threadIdx.x;
     if (sy == 0) ++*nsolve;
     if (sy >= ns || done[sy >> 2]) return;
     if (bnorm[sy] > 0.0 && beta[sy] > rtol * bnorm[sy]) atomicOr(&status[sy >> 2], kStatusNoConv);
+    if (sf_err && *sf_err) atomicOr(&status[sy >> 2], kStatusTimeout);
 }
 
 inline unsigned nblocks(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
@@ -1426,11 +1581,32 @@ gks_status precond_t(gks_mesh *m, const TP *Pg, const TP *alg, const TP *exg, co
         note_launch();
     };
     if (m->cfg.precond == GKS_PC_ILU_EXACT) {
+        // sync-free: a new epoch, then one launch per relation
+        Work &k = m->wk;
+        k_sf_begin<<<1, 32, 0, s>>>(k.sf_ctl, 0);
+        note_launch();
+        const unsigned g = (unsigned)std::min<int64_t>(nblocks(T), (int64_t)k.sm_count * kSfBlocksPerSm);
+        if (rev.a)
+            k_ilu_fwd_sf<TR, TZ, TM, TP, true><<<g, kBlock, 0, s>>>(d, Pg, alg, exg, eyg, src, dst, k.sf_flag,
+                                                                    k.sf_ctl, rev.a, rev.x, rev.y, rev.b);
+        else
+            k_ilu_fwd_sf<TR, TZ, TM, TP, false><<<g, kBlock, 0, s>>>(d, Pg, alg, exg, eyg, src, dst, k.sf_flag,
+                                                                     k.sf_ctl);
+        note_launch();
+        if (rev.a)
+            k_ilu_bwd_sf<TZ, TM, TP, true><<<g, kBlock, 0, s>>>(d, Pg, alg, exg, eyg, dst, k.sf_flag, k.sf_ctl,
+                                                                rev.a, rev.x, rev.y, rev.b);
+        else
+            k_ilu_bwd_sf<TZ, TM, TP, false><<<g, kBlock, 0, s>>>(d, Pg, alg, exg, eyg, dst, k.sf_flag, k.sf_ctl);
+        note_launch();
+    } else if (m->cfg.precond == GKS_PC_ILU_LEVELS) {
         const auto &lp = m->lvl_lo_ptr;
         for (size_t l = 0; l + 1 < lp.size(); ++l)
             fwd(lp[l + 1] - lp[l], d.lvl_lo + lp[l], src, dst, dst, 1, (TZ *)nullptr);
         const auto &up = m->lvl_up_ptr;
         for (size_t l = 0; l + 1 < up.size(); ++l) bwd(up[l + 1] - up[l], d.lvl_up + up[l], dst, dst, dst);
+    } else if (m->cfg.precond == GKS_PC_BJACOBI) {
+        fwd(T, nullptr, src, nullptr, dst, 0, (TZ *)nullptr);     // z = P r, the block-diagonal inverse
     } else {
         // sweeps: forward z^0 = P r, z^{q+1} = F(z^q); backward x^0 = z, x^{q+1} = B(x^q)
         const int ns = m->cfg.ilu_sweeps;
@@ -1851,6 +2027,10 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
     // flags for the host, the whole-solve graph with a condition kernel)
     auto start_body = [&](cudaStream_t q) -> gks_status {
         int slot = prof_start(m, kProfCtl, q);
+        if (m->cfg.precond == GKS_PC_ILU_EXACT) {
+            k_sf_begin<<<1, 32, 0, q>>>(k.sf_ctl, 1);      // a new solve: clear the wait error
+            note_launch();
+        }
         if (rhs_df)
             k_rhs_df<<<nb, kBlock, 0, q>>>(d, d.a0p, k.w, k.b, k.part, ps);
         else
@@ -1962,15 +2142,16 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
     SolveGraphs *G = use_graph ? m->graphs : nullptr;
     bool whole = false;
     // the whole-solve graph holds every Arnoldi index up front: with the
-    // level-scheduled exact ILU (two launches per level) that is too many nodes
+    // level-by-level exact ILU (two launches per level) that is too many nodes
     // on large meshes, whose per-step graphs are built only for the indices used
-    const bool few_nodes = m->cfg.precond != GKS_PC_ILU_EXACT || m->lvl_lo_ptr.size() + m->lvl_up_ptr.size() <= 256;
+    const bool few_nodes = m->cfg.precond != GKS_PC_ILU_LEVELS || m->lvl_lo_ptr.size() + m->lvl_up_ptr.size() <= 256;
     if (emb) {
         if (!G || !few_nodes || G->disabled || m->cfg.no_graphs != 0) return GKS_EINVAL;
         if ((st = build_whole(m, s, start_body, iter_body, restart_body, emb)) != GKS_OK) return st;
         int64_t nl = 0;
         st = capture_into(m, emb->g, &emb->sink, 1, &emb->sink, &nl, [&](cudaStream_t q) -> gks_status {
-            k_mark_noconv<<<sblocks(ns), 128, 0, q>>>(k.bnorm, k.beta, k.done, ns, rtol, k.status, k.nsolve);
+            k_mark_noconv<<<sblocks(ns), 128, 0, q>>>(k.bnorm, k.beta, k.done, ns, rtol, k.status, k.nsolve,
+                                                         m->cfg.precond == GKS_PC_ILU_EXACT ? k.sf_ctl + 3 : nullptr);
             note_launch();
             GKS_CUDA(cudaGetLastError());
             return GKS_OK;
@@ -2012,7 +2193,9 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
             return st;
         m->prof.residuals += 1;
     }
-    k_mark_noconv<<<sblocks(ns), 128, 0, s>>>(k.bnorm, k.beta, k.done, ns, rtol, k.status, k.nsolve); note_launch();
+    k_mark_noconv<<<sblocks(ns), 128, 0, s>>>(k.bnorm, k.beta, k.done, ns, rtol, k.status, k.nsolve,
+                                              m->cfg.precond == GKS_PC_ILU_EXACT ? k.sf_ctl + 3 : nullptr);
+    note_launch();
     if (iters || relres || converged) {
         std::vector<int32_t> it(ns);
         std::vector<double> be(ns), bn(ns);

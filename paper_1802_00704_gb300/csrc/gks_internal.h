@@ -45,7 +45,7 @@ enum : int {
 };
 
 // Device status bits (per case words the kernels OR into).
-enum : int { kStatusNonPhys = 1, kStatusNoConv = 2 };
+enum : int { kStatusNonPhys = 1, kStatusNoConv = 2, kStatusTimeout = 4 };
 
 // GMRES control words, ctl[field * ns + system] with system = case * 4 + variable.
 enum : int { kCtlActive = 0, kCtlRunning = 1, kCtlJv = 2, kCtlIters = 3, kCtlFields = 4 };
@@ -112,6 +112,7 @@ struct Work {
     int m = 0;                       // restart length in use (the autotuner may lower it)
     int m_alloc = 0;                 // restart length the Krylov buffers were sized for
     int nblk = 0;                    // cell blocks (kBlock cells each)
+    int sm_count = 0;                // multiprocessors of the handle's device
     int ns = 4;                      // GMRES systems: 4 per case
     double *w = nullptr;             // [4][T] state (internal order)
     double *w_old = nullptr;         // [4][T]
@@ -167,6 +168,10 @@ struct Work {
     // the device-controlled step loop (one graph launch per run): loops of the
     // current launch, the launch's loop limit, loops over all launches
     int64_t *run_ctl = nullptr;      // [4]
+    // sync-free exact ILU solves (GKS_PC_ILU_EXACT): per-row ready tags, and
+    // the epoch, the forward and backward block tickets and the sticky wait error
+    int32_t *sf_flag = nullptr;      // [T]
+    int32_t *sf_ctl = nullptr;       // [4]
     // pinned host mirrors
     int32_t *h_flags = nullptr;      // [4]
     double *h_scal = nullptr;        // [8]

@@ -2,8 +2,11 @@
 // FP32 fused multiply-add pipes and of streaming HBM reads and copies on the
 // GPU the library runs on.  The benchmark times them with CUDA events and uses
 // the results as the measured roofs of the kernels the FMA pipes or HBM bound.
+// Also the pair arithmetic and the bounded wait of the solver on their own,
+// for the tests.
 #include "gks_df.cuh"
 #include "gks_internal.h"
+#include "gks_wait.cuh"
 
 namespace gks {
 namespace {
@@ -95,10 +98,52 @@ gks_status grid_of(int per_sm, unsigned *g)
     return GKS_OK;
 }
 
+// One thread waits for *flag == 1 (set first when set != 0); out[0] = 1 if
+// the wait gave up, out[1] = nanoseconds it took.
+__global__ void k_wait_probe(int32_t *flag, int32_t *err, int set, uint64_t limit_ns, int64_t *out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (set) publish(flag, 1);
+    const uint64_t t0 = global_ns();
+    const bool ok = bounded_wait(flag, 1, err, limit_ns);
+    out[0] = ok ? 0 : 1;
+    out[1] = (int64_t)(global_ns() - t0);
+}
+
 }  // namespace
 }  // namespace gks
 
 using namespace gks;
+
+extern "C" gks_status gks_probe_wait(int64_t limit_ns, int32_t set_flag, int32_t *timed_out, int64_t *waited_ns,
+                                     void *stream)
+{
+    if (!timed_out || limit_ns < 1 || limit_ns > 10000000000LL) {
+        set_error("gks_probe_wait: NULL timed_out or limit outside [1, 1e10] ns");
+        return GKS_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t *buf = nullptr;                 // [0] flag, [1] error word, [2..3] results
+    GKS_CUDA(cudaMalloc(&buf, 4 * sizeof(int64_t)));
+    int64_t h[2] = {0, 0};
+    cudaError_t e = cudaMemsetAsync(buf, 0, 4 * sizeof(int64_t), s);
+    if (e == cudaSuccess) {
+        k_wait_probe<<<1, 32, 0, s>>>(reinterpret_cast<int32_t *>(buf), reinterpret_cast<int32_t *>(buf + 1),
+                                      set_flag ? 1 : 0, (uint64_t)limit_ns, buf + 2);
+        note_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, buf + 2, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(buf);
+    if (e != cudaSuccess) {
+        set_error("gks_probe_wait: %s", cudaGetErrorString(e));
+        return GKS_ECUDA;
+    }
+    *timed_out = (int32_t)h[0];
+    if (waited_ns) *waited_ns = h[1];
+    return GKS_OK;
+}
 
 extern "C" gks_status gks_probe_fma(int32_t fp64, int32_t blocks_per_sm, int32_t iters, double *sink, void *stream,
                                     double *flops)

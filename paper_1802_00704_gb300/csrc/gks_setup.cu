@@ -872,7 +872,12 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
     AL(sexp, 2 * ns);
     AL(dt, n_cases); AL(tcase, n_cases); AL(tfinal, n_cases); AL(done, n_cases); AL(scal, 8); AL(status, n_cases);
     AL(nstep, n_cases); AL(last_dt, n_cases); AL(iters_acc, ns); AL(nsolve, 1); AL(run_ctl, 4);
+    AL(sf_ctl, 4);
+    GKS_CUDA(cudaDeviceGetAttribute(&k.sm_count, cudaDevAttrMultiProcessorCount, m->device));
+    if (cfg.precond == GKS_PC_ILU_EXACT) AL(sf_flag, T);
 #undef AL
+    GKS_CUDA(cudaMemset(k.sf_ctl, 0, sizeof(int32_t) * 4));
+    if (k.sf_flag) GKS_CUDA(cudaMemset(k.sf_flag, 0, sizeof(int32_t) * T));
     GKS_CUDA(cudaMemset(k.nsolve, 0, sizeof(int64_t)));
     GKS_CUDA(cudaMemset(k.run_ctl, 0, sizeof(int64_t) * 4));
     GKS_CUDA(cudaMemset(k.x, 0, sizeof(double) * 20 * T));

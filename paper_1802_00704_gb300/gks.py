@@ -20,14 +20,14 @@ LIB_PATH = os.path.join(_HERE, "libgks.so")
 GKS_OK, GKS_EINVAL, GKS_ENOMEM, GKS_ECUDA, GKS_ENOCONV, GKS_ENONPHYS, GKS_ETIMEOUT, GKS_EUNSUPPORTED = range(8)
 STATUS_NAMES = ["GKS_OK", "GKS_EINVAL", "GKS_ENOMEM", "GKS_ECUDA", "GKS_ENOCONV", "GKS_ENONPHYS", "GKS_ETIMEOUT",
                 "GKS_EUNSUPPORTED"]
-PC_ILU_EXACT, PC_ILU_SWEEP, PC_BJACOBI = 0, 1, 2
+PC_ILU_EXACT, PC_ILU_SWEEP, PC_BJACOBI, PC_ILU_LEVELS = 0, 1, 2, 3
 FP64, MIXED = 0, 1
 
 EXPORTED = ["gks_config_default", "gks_mesh_create", "gks_mesh_destroy", "gks_mesh_get_stats", "gks_cfl_dt",
             "gks_cls_reconstruct", "gks_reset_warm_start", "gks_flux", "gks_step", "gks_run", "gks_point_flux",
             "gks_profile_begin", "gks_profile_end", "gks_launch_count", "gks_cfl_dt_noalloc", "gks_batch_create",
             "gks_batch_run", "gks_limit", "gks_autotune", "gks_last_error", "gks_probe_fma", "gks_probe_read",
-            "gks_probe_copy", "gks_probe_df"]
+            "gks_probe_copy", "gks_probe_df", "gks_probe_wait"]
 DF_OPS = {"split": 0, "exp": 1, "expm1": 2, "erfcx": 3, "sqrt": 4, "div": 5, "mul": 6, "add": 7, "recip": 8}
 PROF_FLUX, PROF_SPMV, PROF_ILU, PROF_ORTH, PROF_UPDATE, PROF_RESID, PROF_CORR, PROF_CTL = range(8)
 PROF_CLASSES = 8
@@ -154,6 +154,8 @@ def load():
     lib.gks_probe_copy.restype = st
     lib.gks_probe_df.argtypes = [I32, I64, P, P, P, P]
     lib.gks_probe_df.restype = st
+    lib.gks_probe_wait.argtypes = [I64, I32, C.POINTER(I32), C.POINTER(I64), P]
+    lib.gks_probe_wait.restype = st
     lib.gks_last_error.argtypes = []
     lib.gks_last_error.restype = C.c_char_p
     _lib = lib
@@ -416,3 +418,12 @@ def probe_df(op: str, x, y=None, stream=None):
     _check(load().gks_probe_df(DF_OPS[op], x.numel(), _dev(x), _dev(y) if y is not None else None, _dev(out),
                                _stream(stream)), "gks_probe_df")
     return out
+
+
+def probe_wait(limit_ns: int, set_flag: bool, stream=None) -> tuple:
+    """The solver's bounded device wait on its own (see gks_probe_wait):
+    (timed_out, waited_ns)."""
+    to, ns = C.c_int32(0), C.c_int64(0)
+    _check(load().gks_probe_wait(int(limit_ns), int(bool(set_flag)), C.byref(to), C.byref(ns), _stream(stream)),
+           "gks_probe_wait")
+    return bool(to.value), int(ns.value)

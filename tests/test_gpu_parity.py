@@ -97,13 +97,17 @@ def test_prandtl_point_flux_matches_oracle(O, G, precision):
 # --------------------------------------------------------------------------- reconstruction and flux
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("pc", ["exact", "sweep"])
+@pytest.mark.parametrize("pc", ["exact", "sweep", "levels", "bjacobi"])
 def test_cls_matches_oracle(O, G, name, pc):
+    """Every preconditioner (the sync-free exact ILU solves, the sweeps, the
+    exact solves launched level by level, the block-diagonal inverse) solves
+    the same system to the same tolerance: the oracle's coefficients."""
     c = CASES[name]()
     om = O.OracleMesh(c.mesh)
     ref, _, rr, bad = om.cls_solve(c.w0)
     assert bad == 0
-    m = G.GksMesh(c.mesh, precond=G.PC_ILU_EXACT if pc == "exact" else G.PC_ILU_SWEEP)
+    pcs = {"exact": G.PC_ILU_EXACT, "sweep": G.PC_ILU_SWEEP, "levels": G.PC_ILU_LEVELS, "bjacobi": G.PC_BJACOBI}
+    m = G.GksMesh(c.mesh, precond=pcs[pc])
     coef, info = m.cls_reconstruct(dev(c.w0))
     assert info["converged"] == 1 and max(info["relres"]) <= 1e-12
     got = host(coef)
