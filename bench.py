@@ -457,7 +457,7 @@ def timed_leg(args, case, precision: str, world: int, dev, sample_clocks: bool):
                       "ilu_fuse_first": m.cfg.ilu_fuse_first, "warm_extrap": m.cfg.warm_extrap,
                       "inner_rtol": m.cfg.inner_rtol, "gmres_m": m.cfg.gmres_m,
                       "ilu_sweep_pairs": m.cfg.ilu_sweep_pairs, "spmv_dots": m.cfg.spmv_dots,
-                      "flux_variant": tune["flux_variant"] if tune else 0}}
+                      "flux_shape": m.cfg.flux_shape}}
 
 
 def run_gks(args, world, rank, local):
@@ -568,8 +568,7 @@ def run_gks(args, world, rank, local):
         out["cpu_baseline"] = cb
         if mixed:
             mkw = gks_mixed_kw(args)
-            # the flux launch shape is a property of the tuned handle, not of its configuration
-            mkw.update({k: v for k, v in main["knobs"].items() if k != "flux_variant"})
+            mkw.update(main["knobs"])
             out["error_vs_oracle"] = errors_vs_oracle(small, w_o, dts, dev, mkw)
     if rank == 0:
         print(json.dumps(out), flush=True)

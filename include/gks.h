@@ -210,6 +210,13 @@ typedef struct gks_config {
                               the FP32 pipe, one thread per Gauss point doing both
                               parts (flux_split is then ignored); 0 those parts in
                               FP64 (flux_split chooses the kernel)                     */
+    int32_t flux_shape;    /* launch shape of the double-FP32 flux kernel: 0 (default)
+                              128 threads x 4 blocks per SM (128 registers), 1 x 3
+                              (168 registers), 2 x 2 (255 registers).  The same
+                              source, compiled once per shape, so results of two
+                              shapes may differ in the last bits; the autotuner's
+                              last stage picks one                                     */
+    int32_t reserved;      /* must be 0                                                */
 } gks_config;
 
 typedef struct gks_mesh gks_mesh;

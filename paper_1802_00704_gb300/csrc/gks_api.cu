@@ -70,6 +70,7 @@ gks_status check_config(const gks_config &c)
     ok = ok && (c.ilu_fuse_first == 0 || c.ilu_fuse_first == 1);
     ok = ok && (c.flux_split == 0 || c.flux_split == 1);
     ok = ok && (c.flux_lead == 0 || c.flux_lead == 1);
+    ok = ok && c.flux_shape >= 0 && c.flux_shape < kFluxDfVariants && c.reserved == 0;
     ok = ok && (c.ilu_sweep_pairs == 0 || c.ilu_sweep_pairs == 1);
     ok = ok && (c.spmv_dots == 0 || c.spmv_dots == 1);
     if (!ok) {
@@ -217,6 +218,8 @@ void gks_config_default(gks_config *c)
     c->ilu_sweep_pairs = 1;
     c->spmv_dots = 1;
     c->flux_lead = 1;
+    c->flux_shape = 0;
+    c->reserved = 0;
 }
 
 const char *gks_last_error(void) { return gks::last_error(); }

@@ -291,7 +291,7 @@ gks_status launch_flux_df(gks_mesh *m, const double *w, const double *x, double 
             go(N{}, Y{});
         } else {
             const float gf = float(c.gamma), kf = float(K);
-            switch (m->flux_variant) {
+            switch (c.flux_shape) {
             case 1:
                 k_face_flux_df<false, false, 128, 3><<<g, 128, 0, s>>>(m->d, m->wk.w2, m->wk.x2, dt_const, dt_dev, lc,
                                                                       gf, kf, c.tau2_exact, pr_fac, flux,

@@ -212,8 +212,7 @@ struct SolveGraphs {
     // (a while node over the steps, the whole solve nested in its body)
     cudaGraphExec_t run = nullptr;
     bool run_failed = false;                        // building it failed: the host loop from now on
-    gks_config run_cfg{};                           // configuration and flux launch shape it was built for
-    int32_t run_flux_variant = -1;
+    gks_config run_cfg{};                           // configuration it was built for
     int64_t run_loop_launches = 0;                  // kernels per loop outside the solve's cycles
     int64_t *h_run = nullptr;                       // pinned: the loop limit of the next launch
 };
@@ -247,8 +246,6 @@ struct gks_mesh {
     gks::SolveGraphs *graphs = nullptr;
     int64_t flux_ws_grid = 0;                      // blocks of the persistent flux kernel
     int32_t flux_ws_key = -1;                      // ... for this variant
-    int32_t flux_variant = 0;                      // launch shape of the double-FP32 flux kernel
-                                                   // (kFluxDfVariants; chosen by the autotuner)
 };
 
 namespace gks {

@@ -152,14 +152,14 @@ extern "C" gks_status gks_autotune(gks_mesh *m, const double *w, int32_t trial_s
     }
     // third stage: the launch shape (register budget) of the double-FP32 flux
     // kernel, with the best knobs and restart length
-    const int32_t v0 = m->flux_variant;
+    const int32_t v0 = m->cfg.flux_shape;
     int32_t vpick = v0;
     const bool df_flux = mixed && m->cfg.flux_lead && m->cfg.prandtl == 1.0 && m->cfg.slope0_mode == 0;
     if (df_flux && st == GKS_OK) {
         apply(m, pick);
         for (int32_t v = 0; v < kFluxDfVariants && st == GKS_OK; ++v) {
             if (v == v0) continue;
-            m->flux_variant = v;
+            m->cfg.flux_shape = v;
             double ms = DBL_MAX;
             st = time_candidate(m, w, trial_steps, s, e0, e1, &ms);
             ++ntimed;
@@ -168,7 +168,7 @@ extern "C" gks_status gks_autotune(gks_mesh *m, const double *w, int32_t trial_s
                 vpick = v;
             }
         }
-        m->flux_variant = v0;
+        m->cfg.flux_shape = v0;
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -176,7 +176,7 @@ extern "C" gks_status gks_autotune(gks_mesh *m, const double *w, int32_t trial_s
     m->wk.m = m0;
     if (st == GKS_OK) {
         apply(m, pick);
-        m->flux_variant = vpick;
+        m->cfg.flux_shape = vpick;
         out->flux_variant = vpick;
         out->gmres_m = pick.m;
         out->ilu_sweeps = pick.sweeps;

@@ -50,7 +50,7 @@ class Config(C.Structure):
                 ("ilu_fp16", C.c_int32), ("cls_global", C.c_int32), ("cls_M", C.c_int32),
                 ("ilu_sweeps_bwd", C.c_int32), ("ilu_fuse_first", C.c_int32),
                 ("flux_split", C.c_int32), ("ilu_sweep_pairs", C.c_int32), ("spmv_dots", C.c_int32),
-                ("flux_lead", C.c_int32)]
+                ("flux_lead", C.c_int32), ("flux_shape", C.c_int32), ("reserved", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -306,15 +306,16 @@ class GksMesh:
         return out, st
 
     def autotune(self, w, trial_steps: int = 3, stream=None) -> dict:
-        """Pick ilu_sweeps, ilu_sweeps_bwd, warm_extrap, (mixed) inner_rtol and then the
-        GMRES restart length by timing trial steps from the state w (not modified);
-        the handle keeps the fastest."""
+        """Pick ilu_sweeps, ilu_sweeps_bwd, warm_extrap, (mixed) inner_rtol, then the
+        GMRES restart length, then (double-FP32 flux) its launch shape, by timing
+        trial steps from the state w (not modified); the handle keeps the fastest."""
         r = TuneResult()
         _check(self._lib.gks_autotune(self._h, _dev(w, (4, self.T)), int(trial_steps), C.byref(r), _stream(stream)),
                "gks_autotune")
         self.cfg.ilu_sweeps, self.cfg.warm_extrap, self.cfg.inner_rtol = r.ilu_sweeps, r.warm_extrap, r.inner_rtol
         self.cfg.ilu_sweeps_bwd = r.ilu_sweeps_bwd
         self.cfg.gmres_m = r.gmres_m
+        self.cfg.flux_shape = r.flux_variant
         return {k: getattr(r, k) for k, _ in TuneResult._fields_}
 
     def limit(self, w, coef, out=None, flags=None, stream=None):

@@ -101,7 +101,7 @@ def test_autotune_on_a_batch(G):
     # iterates within the GMRES tolerance, which the limiter's flags can amplify)
     ref = G.GksMesh.batch([c.mesh for c in cases], precision=G.MIXED, limiter=1, ilu_sweeps=r["ilu_sweeps"],
                           ilu_sweeps_bwd=r["ilu_sweeps_bwd"], warm_extrap=r["warm_extrap"],
-                          inner_rtol=r["inner_rtol"], gmres_m=r["gmres_m"])
+                          inner_rtol=r["inner_rtol"], gmres_m=r["gmres_m"], flux_shape=r["flux_variant"])
     wa, wb = dev(w0), dev(w0)
     assert b.batch_run(wa, max_steps=5)["n_failed"] == 0
     ref.batch_run(wb, max_steps=5)
@@ -218,15 +218,16 @@ def test_iteration_cap_stops_solve_the_same_way(G, mode):
 
 def test_graphs_follow_knob_changes(G):
     """Knobs baked into the captured kernel arguments (sweeps, warm start, inner
-    tolerance) drop the graphs when they change: after the autotuner has run
-    every candidate, the handle steps exactly like a fresh handle built with the
-    knobs it picked and launching its kernels one by one."""
+    tolerance, restart length, flux launch shape) drop the graphs when they
+    change: after the autotuner has run every candidate, the handle steps
+    exactly like a fresh handle built with the knobs it picked and launching its
+    kernels one by one."""
     c = I.shock_vortex_case(30, 15)
     m = G.GksMesh(c.mesh, precision=G.MIXED)
     r = m.autotune(dev(c.w0), trial_steps=1)
     ref = G.GksMesh(c.mesh, precision=G.MIXED, ilu_sweeps=r["ilu_sweeps"], ilu_sweeps_bwd=r["ilu_sweeps_bwd"],
-                    warm_extrap=r["warm_extrap"],
-                    inner_rtol=r["inner_rtol"], no_graphs=1)
+                    warm_extrap=r["warm_extrap"], inner_rtol=r["inner_rtol"], gmres_m=r["gmres_m"],
+                    flux_shape=r["flux_variant"], no_graphs=1)
     wa, wb = dev(c.w0), dev(c.w0)
     for _ in range(5):
         assert m.step(wa, 2e-4)["iters"] == ref.step(wb, 2e-4)["iters"]
