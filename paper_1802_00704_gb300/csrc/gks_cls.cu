@@ -401,18 +401,34 @@ __global__ void __launch_bounds__(kBlock, 4) k_resid_df(DeviceMesh d, const floa
             const int j = d.nb[s * T + i];
             jn[s] = j >= 0 ? j : i;
         }
-        // every load first (the arithmetic below is a long dependent chain)
+        // the cell's own block first, then the neighbours: the two phases keep
+        // fewer values live (no spills at the register cap), and the sums run
+        // in the same order
         constexpr int NG = G ? ND : 2;                    // neighbour unknowns used
         double xv[ND], gv[3][NG], bv[ND];
         float dp[30], op[18], rp[G ? 18 : 1], bp[G ? 6 : 1];
 #pragma unroll
         for (int l = 0; l < ND; ++l) xv[l] = x[(v * ND + l) * T + i];
 #pragma unroll
+        for (int q = 0; q < 30; ++q) dp[q] = D2[q * T + i];
+        bool ok = true;
+        float xh[ND], xl[ND], gh[3][NG], gl[3][NG], ah[ND], al[ND], out[ND];
+#pragma unroll
+        for (int l = 0; l < ND; ++l) {
+            ok &= df_split(xv[l], e, xh[l], xl[l]);
+            ah[l] = al[l] = 0.0f;
+        }
+        // symmetric 5x5 block: entry (a, k) in the upper-triangle order
+        constexpr int kIdx[5][5] = {{0, 1, 2, 3, 4}, {1, 5, 6, 7, 8}, {2, 6, 9, 10, 11}, {3, 7, 10, 12, 13},
+                                    {4, 8, 11, 13, 14}};
+#pragma unroll
+        for (int a = 0; a < ND; ++a)
+#pragma unroll
+            for (int k = 0; k < ND; ++k) df_mac(dp[kIdx[a][k]], dp[15 + kIdx[a][k]], xh[k], xl[k], ah[a], al[a]);
+#pragma unroll
         for (int s = 0; s < 3; ++s)
 #pragma unroll
             for (int l = 0; l < NG; ++l) gv[s][l] = x[(v * ND + l) * T + jn[s]];
-#pragma unroll
-        for (int q = 0; q < 30; ++q) dp[q] = D2[q * T + i];
 #pragma unroll
         for (int q = 0; q < 18; ++q) op[q] = S2[q * T + i];
         if (G) {
@@ -423,24 +439,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_resid_df(DeviceMesh d, const floa
         }
 #pragma unroll
         for (int l = 0; l < ND; ++l) bv[l] = b[(v * ND + l) * T + i];
-        bool ok = true;
-        float xh[ND], xl[ND], gh[3][NG], gl[3][NG], ah[ND], al[ND], out[ND];
-#pragma unroll
-        for (int l = 0; l < ND; ++l) {
-            ok &= df_split(xv[l], e, xh[l], xl[l]);
-            ah[l] = al[l] = 0.0f;
-        }
 #pragma unroll
         for (int s = 0; s < 3; ++s)
 #pragma unroll
             for (int l = 0; l < NG; ++l) ok &= df_split(gv[s][l], e, gh[s][l], gl[s][l]);
-        // symmetric 5x5 block: entry (a, k) in the upper-triangle order
-        constexpr int kIdx[5][5] = {{0, 1, 2, 3, 4}, {1, 5, 6, 7, 8}, {2, 6, 9, 10, 11}, {3, 7, 10, 12, 13},
-                                    {4, 8, 11, 13, 14}};
-#pragma unroll
-        for (int a = 0; a < ND; ++a)
-#pragma unroll
-            for (int k = 0; k < ND; ++k) df_mac(dp[kIdx[a][k]], dp[15 + kIdx[a][k]], xh[k], xl[k], ah[a], al[a]);
         // off-diagonal block of neighbour s (see oacc): sa, sax = sa dx, say = sa dy
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
@@ -546,40 +548,47 @@ __global__ void __launch_bounds__(kBlock, 3) k_rhs_df(DeviceMesh d, const float 
             }
             ev[v] = (em == 2047 ? 1023 : em) - 1023;
         }
-        float sh_[NX], sl_[NX];
-#pragma unroll
-        for (int q = 0; q < NX; ++q) sh_[q] = sl_[q] = 0.0f;
+        // with 2^e the largest difference of its variable, a difference fails to
+        // split only when it is not finite: that sends the cell to FP64
         bool ok = true;
 #pragma unroll
-        for (int s = 0; s < 3; ++s) {
-            if (js[s] < 0) continue;
-            float ah[ND], al[ND];
+        for (int s = 0; s < 3; ++s)
 #pragma unroll
-            for (int l = 0; l < ND; ++l) {
-                ah[l] = a0p[(s * ND + l) * T + i];
-                al[l] = a0p[(15 + s * ND + l) * T + i];
-            }
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                float dh, dl;
-                ok &= df_split(du[s][v], ev[v], dh, dl);
-#pragma unroll
-                for (int l = 0; l < ND; ++l) df_mac(ah[l], al[l], dh, dl, sh_[v * ND + l], sl_[v * ND + l]);
-            }
-        }
+            for (int v = 0; v < NV; ++v) ok &= isfinite(du[s][v]);
         if (ok) {
+            float ah[3][ND], al[3][ND];
 #pragma unroll
-            for (int v = 0; v < NV; ++v)
+            for (int s = 0; s < 3; ++s)
 #pragma unroll
                 for (int l = 0; l < ND; ++l) {
-                    const int q = v * ND + l;
+                    ah[s][l] = js[s] >= 0 ? a0p[(s * ND + l) * T + i] : 0.0f;
+                    al[s][l] = js[s] >= 0 ? a0p[(15 + s * ND + l) * T + i] : 0.0f;
+                }
+            // one variable at a time (ten accumulators live, not forty); each sum
+            // runs over the neighbours in order, as the FP64 kernel's does
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                float sh_[ND], sl_[ND];
+#pragma unroll
+                for (int l = 0; l < ND; ++l) sh_[l] = sl_[l] = 0.0f;
+#pragma unroll
+                for (int s = 0; s < 3; ++s) {
+                    if (js[s] < 0) continue;
+                    float dh, dl;
+                    df_split(du[s][v], ev[v], dh, dl);
+#pragma unroll
+                    for (int l = 0; l < ND; ++l) df_mac(ah[s][l], al[s][l], dh, dl, sh_[l], sl_[l]);
+                }
+#pragma unroll
+                for (int l = 0; l < ND; ++l) {
                     // normalise (TwoSum): h + lo = sh + sl exactly
-                    const float h = __fadd_rn(sh_[q], sl_[q]);
-                    const float z = __fsub_rn(h, sh_[q]);
-                    const float lo = __fadd_rn(__fsub_rn(sh_[q], __fsub_rn(h, z)), __fsub_rn(sl_[q], z));
-                    b[q * T + i] = f2d_pow2(h, ev[v]) + f2d_pow2(lo, ev[v]);
+                    const float h = __fadd_rn(sh_[l], sl_[l]);
+                    const float z = __fsub_rn(h, sh_[l]);
+                    const float lo = __fadd_rn(__fsub_rn(sh_[l], __fsub_rn(h, z)), __fsub_rn(sl_[l], z));
+                    b[(v * ND + l) * T + i] = f2d_pow2(h, ev[v]) + f2d_pow2(lo, ev[v]);
                     ss[v] = __fmaf_rn(h, h, ss[v]);
                 }
+            }
         } else {
             // FP64 as in k_rhs; the norm from the values scaled by 2^-e
 #pragma unroll

@@ -43,7 +43,8 @@ def test_config_defaults(lib):
     assert c.limit_char == 0 and c.inner_rtol == 1e-6 and c.ilu_sweeps_bwd == -1 and c.ilu_fuse_first == 1
     assert c.flux_split == 1
     assert c.prandtl == 1.0
-    assert c.flux_lead == 1 and c.ilu_sweep_pairs == 1
+    assert c.flux_lead == 1 and c.ilu_sweep_pairs == 1 and c.spmv_dots == 1
+    assert c.flux_shape == 0 and c.reserved == 0 and c.precond == gks.PC_ILU_SWEEP
 
 
 def _c_layout(struct, fields):
@@ -89,6 +90,7 @@ def test_binding_refuses_cpu_tensors(lib):
     ("ilu_fp16", 1),            # FP16 factors need the mixed precision
     ("cls_M", 0),               # values-only equations need the second-order variant
     ("slope0_mode", 2), ("no_graphs", 3), ("warm_extrap", 3), ("inner_rtol", 0.0),
+    ("flux_shape", 3), ("flux_shape", -1), ("reserved", 1),
 ])
 def test_invalid_config_is_refused_before_any_device_call(lib, field, value):
     """gks_mesh_create checks the configuration first: an invalid field gives
@@ -100,3 +102,15 @@ def test_invalid_config_is_refused_before_any_device_call(lib, field, value):
     with pytest.raises(gks.GksError) as e:
         gks.GksMesh(case.mesh, **{field: value})
     assert e.value.status == gks.GKS_EINVAL and "invalid gks_config" in str(e.value)
+
+
+@pytest.mark.parametrize("precond", [-1, 4])
+def test_unknown_preconditioner_is_refused(lib, precond):
+    """The four preconditioners (sync-free exact ILU, sweeps, block Jacobi, level
+    launches) are 0..3; anything else is GKS_EINVAL before any device call."""
+    from paper_1802_00704_gb300 import gks
+    from paper_1802_00704_gb300 import inputs as I
+    case = I.advection_case(3)
+    with pytest.raises(gks.GksError) as e:
+        gks.GksMesh(case.mesh, precond=precond)
+    assert e.value.status == gks.GKS_EINVAL and "precond" in str(e.value)
