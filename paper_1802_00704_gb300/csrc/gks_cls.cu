@@ -951,12 +951,9 @@ __global__ void __launch_bounds__(kBlock, sizeof(TM) == 4 ? 3 : 2) k_ilu_bwd2(De
     const int64_t T = d.T;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= T) return;
-    TM zi[NX], y[NX];
+    TM y[NX];
 #pragma unroll
-    for (int k = 0; k < NX; ++k) {
-        zi[k] = TM(z[k * T + i]);
-        y[k] = TM(0);
-    }
+    for (int k = 0; k < NX; ++k) y[k] = TM(0);
 #pragma unroll 1
     for (int s = 0; s < 3; ++s) {
         const int j = d.nb[s * T + i];
@@ -992,9 +989,13 @@ __global__ void __launch_bounds__(kBlock, sizeof(TM) == 4 ? 3 : 2) k_ilu_bwd2(De
 #pragma unroll
         for (int v = 0; v < NV; ++v) oacc(sa, sax, say, x1[v][0], x1[v][1], y + v * ND);
     }
-    TM Pm[25];                               // the cell's own factor last, after the gathers
+    // the cell's own factor and z last, after the gathers (fewer values live
+    // while the neighbours' first sweep is formed)
+    TM Pm[25], zi[NX];
 #pragma unroll
     for (int k = 0; k < 25; ++k) Pm[k] = TM(Pg[k * T + i]);
+#pragma unroll
+    for (int k = 0; k < NX; ++k) zi[k] = TM(z[k * T + i]);
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
