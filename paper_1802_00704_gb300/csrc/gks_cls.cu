@@ -254,13 +254,17 @@ __global__ void k_spmv(DeviceMesh d, const TM *__restrict__ Dg, const TM *__rest
 // sum over the block's cells of <V_k, y>_v: FP32 products and warp sums (as
 // k_dots), each warp's sums widened to FP64 and added across the block's warps
 // in order.  Deterministic; a different summation order than k_dots, so the
-// iterates agree with the unfused path to rounding.
+// iterates agree with the unfused path to rounding.  J > 0: the Arnoldi index
+// j = J - 1 is a compile-time constant, the products with all J basis vectors
+// are formed before one block-wide pass sums them (one barrier instead of two
+// per vector); the same operations in the same order as the loop over k.
+template <int J = 0>
 __global__ void __launch_bounds__(kBlock, 3)
     k_spmv_dots(DeviceMesh d, const float *__restrict__ Dg, const float *__restrict__ alg,
                 const float *__restrict__ exg, const float *__restrict__ eyg, const float *__restrict__ x,
                 float *__restrict__ y, const float *__restrict__ V, int j, double *__restrict__ part, int pstride)
 {
-    __shared__ float sh[kBlock / 32][NV];
+    __shared__ float sh[kBlock / 32][J > 0 ? J : 1][NV];
     const int64_t T = d.T;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -273,6 +277,41 @@ __global__ void __launch_bounds__(kBlock, 3)
         for (int q = 0; q < NX; ++q) y[q * T + i] = acc[q];
     }
     const int64_t vs = (int64_t)NX * T;
+    if constexpr (J > 0) {
+        float sv[J][NV];
+#pragma unroll
+        for (int k = 0; k < J; ++k)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) sv[k][v] = 0.0f;
+        if (i < T) {
+#pragma unroll
+            for (int k = 0; k < J; ++k) {
+                const float *vk = V + k * vs;
+#pragma unroll
+                for (int v = 0; v < NV; ++v)
+#pragma unroll
+                    for (int l = 0; l < ND; ++l) sv[k][v] = fmaf(vk[(v * ND + l) * T + i], acc[v * ND + l], sv[k][v]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < J; ++k)
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+                for (int o = 16; o > 0; o >>= 1) sv[k][v] += __shfl_down_sync(0xffffffffu, sv[k][v], o);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < J; ++k)
+#pragma unroll
+                for (int v = 0; v < NV; ++v) sh[warp][k][v] = sv[k][v];
+        __syncthreads();
+        if (threadIdx.x < J * NV) {
+            const int k = threadIdx.x / NV, v = threadIdx.x % NV;
+            double t = 0.0;
+            for (int w = 0; w < kBlock / 32; ++w) t += double(sh[w][k][v]);
+            part[(blockIdx.x * NV + v) * pstride + k] = t;
+        }
+        return;
+    }
     for (int k = 0; k <= j; ++k) {
         float sv[NV] = {0.0f, 0.0f, 0.0f, 0.0f};
         if (i < T) {
@@ -287,11 +326,11 @@ __global__ void __launch_bounds__(kBlock, 3)
             for (int o = 16; o > 0; o >>= 1) sv[v] += __shfl_down_sync(0xffffffffu, sv[v], o);
         if (lane == 0)
 #pragma unroll
-            for (int v = 0; v < NV; ++v) sh[warp][v] = sv[v];
+            for (int v = 0; v < NV; ++v) sh[warp][0][v] = sv[v];
         __syncthreads();
         if (threadIdx.x < NV) {
             double t = 0.0;
-            for (int w = 0; w < kBlock / 32; ++w) t += double(sh[w][threadIdx.x]);
+            for (int w = 0; w < kBlock / 32; ++w) t += double(sh[w][0][threadIdx.x]);
             part[(blockIdx.x * NV + threadIdx.x) * pstride + k] = t;
         }
         __syncthreads();
@@ -2105,9 +2144,16 @@ gks_status cls_solve_t(gks_mesh *m, TB *V, cudaStream_t s, int32_t *iters, doubl
         // forms the first Gram-Schmidt products (k_spmv_dots)
         const bool fused_dots = std::is_same<TB, float>::value && !d.alr32 && m->cfg.spmv_dots;
         if (fused_dots) {
-            k_spmv_dots<<<nb, kBlock, 0, q>>>(d, d.D32, d.alpha32, d.ex32, d.ey32, k.Z32 + j * vs,
-                                               reinterpret_cast<float *>(vj1), reinterpret_cast<const float *>(V),
-                                               j, k.part, ps);
+            float *yv = reinterpret_cast<float *>(vj1);
+            const float *Vf = reinterpret_cast<const float *>(V);
+            const float *zj = k.Z32 + j * vs;
+            switch (j) {     // the first four Arnoldi indices unrolled (the inner cycles rarely go further)
+            case 0: k_spmv_dots<1><<<nb, kBlock, 0, q>>>(d, d.D32, d.alpha32, d.ex32, d.ey32, zj, yv, Vf, j, k.part, ps); break;
+            case 1: k_spmv_dots<2><<<nb, kBlock, 0, q>>>(d, d.D32, d.alpha32, d.ex32, d.ey32, zj, yv, Vf, j, k.part, ps); break;
+            case 2: k_spmv_dots<3><<<nb, kBlock, 0, q>>>(d, d.D32, d.alpha32, d.ex32, d.ey32, zj, yv, Vf, j, k.part, ps); break;
+            case 3: k_spmv_dots<4><<<nb, kBlock, 0, q>>>(d, d.D32, d.alpha32, d.ex32, d.ey32, zj, yv, Vf, j, k.part, ps); break;
+            default: k_spmv_dots<<<nb, kBlock, 0, q>>>(d, d.D32, d.alpha32, d.ex32, d.ey32, zj, yv, Vf, j, k.part, ps);
+            }
         } else if (mixed) {
             spmv32(q, k.Z32 + j * vs, vj1);
         } else {
