@@ -417,8 +417,9 @@ GKS_EXPORT gks_status gks_point_flux(int64_t n, const double *wl, const double *
 
 /* Autotuner.  Times trial steps of the handle's own workload (all its cases)
  * for each candidate of the knobs that change the cost of a step but not its
- * result beyond the solver tolerance: ilu_sweeps in {1, 2, 3} (sweep
- * preconditioner only), warm_extrap in {0, 1, 2} and, in mixed precision,
+ * result beyond the solver tolerance: (ilu_sweeps, ilu_sweeps_bwd) in
+ * {(1, -1), (2, -1), (3, -1), (2, 1), (3, 1), (1, 2)} (sweep preconditioner
+ * only), warm_extrap in {0, 1, 2} and, in mixed precision,
  * inner_rtol in {1e-4, 1e-5, 1e-6}; then, with the best of those, the GMRES
  * restart length in {gmres_m, 16, 8} (at most the gmres_m the handle was
  * created with, which sized its Krylov buffers); then, for the mixed flux in

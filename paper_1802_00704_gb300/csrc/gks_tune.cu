@@ -104,17 +104,20 @@ extern "C" gks_status gks_autotune(gks_mesh *m, const double *w, int32_t trial_s
     const bool mixed = m->cfg.precision == GKS_MIXED;
     const bool sweep = m->cfg.precond == GKS_PC_ILU_SWEEP;
     std::vector<Candidate> cand;
-    for (int32_t sw : {1, 2, 3})
-        for (int32_t bwd : {-1, 1}) {
-            if (!sweep && (sw != 1 || bwd != -1)) continue;
-            if (bwd == 1 && sw == 1) continue;             // the same as -1
-            for (int32_t wx : {0, 1, 2})
-                for (double eta : {1e-4, 1e-5, 1e-6}) {
-                    if (!mixed && eta != 1e-6) continue;
-                    cand.push_back({sweep ? sw : before.ilu_sweeps, wx, mixed ? eta : before.inner_rtol,
-                                    sweep ? bwd : before.ilu_sweeps_bwd, m->wk.m});
-                }
-        }
+    // (forward, backward) sweeps: the same number each way (bwd -1), one
+    // backward sweep after two or three forward ones, and one forward sweep
+    // before a backward pair (one launch, k_ilu_bwd2)
+    const int32_t pairs[6][2] = {{1, -1}, {2, -1}, {3, -1}, {2, 1}, {3, 1}, {1, 2}};
+    for (const auto &pr : pairs) {
+        const int32_t sw = pr[0], bwd = pr[1];
+        if (!sweep && (sw != 1 || bwd != -1)) continue;
+        for (int32_t wx : {0, 1, 2})
+            for (double eta : {1e-4, 1e-5, 1e-6}) {
+                if (!mixed && eta != 1e-6) continue;
+                cand.push_back({sweep ? sw : before.ilu_sweeps, wx, mixed ? eta : before.inner_rtol,
+                                sweep ? bwd : before.ilu_sweeps_bwd, m->wk.m});
+            }
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     gks_status st = GKS_OK;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {

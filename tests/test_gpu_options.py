@@ -72,11 +72,12 @@ def test_autotune_keeps_the_state_and_the_results(G, precision):
     tuned = G.GksMesh(c.mesh, precision=prec)
     r = tuned.autotune(w, trial_steps=2)
     assert np.array_equal(host(w), c.w0)                   # the caller's state is untouched
-    assert r["ilu_sweeps"] in (1, 2, 3) and r["warm_extrap"] in (0, 1, 2) and r["ilu_sweeps_bwd"] in (-1, 1)
-    # sweeps (1, 2, 3) with the same number backward, and (2, 3) with one backward sweep
+    assert r["ilu_sweeps"] in (1, 2, 3) and r["warm_extrap"] in (0, 1, 2) and r["ilu_sweeps_bwd"] in (-1, 1, 2)
+    # sweeps (1, 2, 3) with the same number backward, (2, 3) with one backward sweep and
+    # 1 with a backward pair
     # (x warm start x inner tolerance in mixed precision), then restarts 16 and 8,
     # then (mixed, double-FP32 flux) the two other launch shapes of the flux kernel
-    assert r["n_candidates"] == (45 + 2 + 2 if precision == "mixed" else 15 + 2) and r["n_failed"] == 0
+    assert r["n_candidates"] == (54 + 2 + 2 if precision == "mixed" else 18 + 2) and r["n_failed"] == 0
     assert r["gmres_m"] in (30, 16, 8) and r["flux_variant"] in ((0, 1, 2) if precision == "mixed" else (0,))
     assert 0 < r["ms_per_step"] <= r["ms_per_step_before"]
     if precision == "fp64":
