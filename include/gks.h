@@ -209,7 +209,11 @@ typedef struct gks_config {
                               arithmetic (pairs of FP32 numbers, about 48 bits) on
                               the FP32 pipe, one thread per Gauss point doing both
                               parts (flux_split is then ignored); 0 those parts in
-                              FP64 (flux_split chooses the kernel)                     */
+                              FP64 (flux_split chooses the kernel); 2 the whole flux
+                              in FP64 (the FP64 path's kernel, reading the FP64
+                              coefficients of the refinement), for viscous flows
+                              whose FP32 slope-carrying terms (the viscous stress)
+                              would limit the agreement with the FP64 path         */
     int32_t flux_shape;    /* launch shape of the double-FP32 flux kernel: 0 (default)
                               128 threads x 4 blocks per SM (128 registers), 1 x 3
                               (168 registers), 2 x 2 (255 registers).  The same

@@ -69,7 +69,7 @@ gks_status check_config(const gks_config &c)
     ok = ok && c.ilu_sweeps_bwd >= -1 && c.ilu_sweeps_bwd <= 8;
     ok = ok && (c.ilu_fuse_first == 0 || c.ilu_fuse_first == 1);
     ok = ok && (c.flux_split == 0 || c.flux_split == 1);
-    ok = ok && (c.flux_lead == 0 || c.flux_lead == 1);
+    ok = ok && c.flux_lead >= 0 && c.flux_lead <= 2;
     ok = ok && c.flux_shape >= 0 && c.flux_shape < kFluxDfVariants && c.reserved == 0;
     ok = ok && (c.ilu_sweep_pairs == 0 || c.ilu_sweep_pairs == 1);
     ok = ok && (c.spmv_dots == 0 || c.spmv_dots == 1);

@@ -338,8 +338,9 @@ gks_status launch_flux(gks_mesh *m, const double *w, const double *x, double dt_
     const gks_config &c = m->cfg;
     const bool heat = c.prandtl != 1.0;
     const unsigned g = blocks(npts, kFluxBlock);
-    const bool mixed = c.precision == GKS_MIXED;
-    if (mixed && c.flux_lead) {
+    // flux_lead = 2: the mixed solver with the FP64 path's flux kernel
+    const bool mixed = c.precision == GKS_MIXED && c.flux_lead != 2;
+    if (mixed && c.flux_lead == 1) {
         const gks_status st = launch_flux_df(m, w, x, dt_const, dt_dev, flux, s);
         if (st != GKS_OK) return st;
     } else {
@@ -375,11 +376,12 @@ gks_status launch_point_flux(int64_t n, const double *wl, const double *wr, doub
     if (n <= 0) return GKS_OK;
     const unsigned g = blocks(n, kFluxBlock);
     const bool heat = cfg.prandtl != 1.0;
-    if (cfg.precision == GKS_MIXED && cfg.flux_lead) {
+    const bool mixed = cfg.precision == GKS_MIXED && cfg.flux_lead != 2;
+    if (mixed && cfg.flux_lead == 1) {
         const gks_status st = launch_point_flux_df(n, wl, wr, dt, cfg, out, status, s);
         if (st != GKS_OK) return st;
     } else {
-        dispatch3(cfg.precision == GKS_MIXED, heat, cfg.slope0_mode == 1, [&](auto M, auto H, auto Kw) {
+        dispatch3(mixed, heat, cfg.slope0_mode == 1, [&](auto M, auto H, auto Kw) {
             k_point_flux<decltype(M)::value, decltype(H)::value, decltype(Kw)::value><<<g, kFluxBlock, 0, s>>>(
                 n, wl, wr, dt, cfg.gamma, cfg.mu, cfg.tau2_exact, cfg.prandtl, out, status);
         });

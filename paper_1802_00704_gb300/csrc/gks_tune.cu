@@ -157,7 +157,7 @@ extern "C" gks_status gks_autotune(gks_mesh *m, const double *w, int32_t trial_s
     // kernel, with the best knobs and restart length
     const int32_t v0 = m->cfg.flux_shape;
     int32_t vpick = v0;
-    const bool df_flux = mixed && m->cfg.flux_lead && m->cfg.prandtl == 1.0 && m->cfg.slope0_mode == 0;
+    const bool df_flux = mixed && m->cfg.flux_lead == 1 && m->cfg.prandtl == 1.0 && m->cfg.slope0_mode == 0;
     if (df_flux && st == GKS_OK) {
         apply(m, pick);
         for (int32_t v = 0; v < kFluxDfVariants && st == GKS_OK; ++v) {

@@ -154,3 +154,44 @@ def test_fullsize_fp64_step_against_oracle(O, G):
     got = host(w)
     err = np.max(np.abs(got - wo), axis=1) / np.max(np.abs(wo), axis=1)
     assert np.all(err <= 1e-10), err
+
+
+def test_fp64_flux_option_is_the_fp64_point_flux(G):
+    """flux_lead = 2: the mixed solver with the FP64 path's flux kernel; the
+    point flux equals the FP64 path's bit for bit (viscous, Prandtl 0.72)."""
+    rng = np.random.default_rng(5)
+    n = 2000
+    w = np.zeros((2, n, 6, 4))
+    for s in range(2):
+        rho = rng.uniform(0.5, 2.0, n)
+        U, V, p = rng.uniform(-1, 1, n), rng.uniform(-1, 1, n), rng.uniform(0.5, 2.0, n)
+        w[s, :, 0] = np.stack([rho, rho * U, rho * V, p / 0.4 + 0.5 * rho * (U * U + V * V)], axis=1)
+        w[s, :, 1:] = rng.normal(0.0, 0.05, (n, 5, 4))
+    kw = dict(mu=2e-3, prandtl=0.72)
+    a = host(G.point_flux(dev(w[0]), dev(w[1]), 0.004, precision=G.MIXED, flux_lead=2, **kw))
+    b = host(G.point_flux(dev(w[0]), dev(w[1]), 0.004, precision=G.FP64, **kw))
+    assert np.array_equal(a, b)
+
+
+def test_viscous_cavity_mixed_solver_with_fp64_flux(G):
+    """The lid-driven cavity (Re 1000, Pr 0.72, isothermal no-slip walls) for 60
+    steps: with the FP64 flux (flux_lead = 2) the mixed path differs from the FP64
+    path only by the CLS solve's tolerance, within 1e-10 relative L1 on every
+    conserved variable; the default double-FP32 lead with FP32 slope terms moves
+    the momenta further (their viscous stress is carried in FP32)."""
+    c = I.cavity_case(24)
+    p = c.mesh.nodes[c.mesh.tris]
+    area = 0.5 * np.abs((p[:, 1, 0] - p[:, 0, 0]) * (p[:, 2, 1] - p[:, 0, 1]) -
+                        (p[:, 2, 0] - p[:, 0, 0]) * (p[:, 1, 1] - p[:, 0, 1]))
+    out = {}
+    for name, kw in (("fp64", {}), ("fp64_flux", dict(precision=G.MIXED, flux_lead=2)),
+                     ("pairs", dict(precision=G.MIXED, flux_lead=1))):
+        m = G.GksMesh(c.mesh, mu=c.mu, prandtl=0.72, **kw)
+        w = dev(c.w0)
+        assert m.run(w, max_steps=60)["status"] == 0
+        out[name] = host(w)
+    ref = out["fp64"]
+    l1 = {k: np.sum(area * np.abs(out[k] - ref), axis=1) / np.sum(area * np.abs(ref), axis=1)
+          for k in ("fp64_flux", "pairs")}
+    assert np.all(l1["fp64_flux"] <= 1e-10), l1
+    assert l1["pairs"][1:3].max() > l1["fp64_flux"][1:3].max(), l1
