@@ -65,12 +65,22 @@ def make_case(name: str, replica: int = 0):
     return I.advection_case(w["n"], seed=1802 + replica)
 
 
-def source_hash() -> str:
-    """Hash of the face-flux kernels' sources (the kernels the counter record describes)."""
+# the source files of each face-flux kernel a counter record describes (the
+# file that defines it and the headers with its device code)
+FLUX_SOURCES = {
+    "mixed_flux_df": ("gks_flux_df.cu", "gks_kinetic.cuh", "gks_face.cuh", "gks_lead_df.cuh", "gks_df.cuh",
+                      "gks_erfcx_coef.h"),
+    "mixed_flux_ws": ("gks_flux.cu", "gks_kinetic.cuh", "gks_face.cuh"),
+    "mixed_flux": ("gks_flux.cu", "gks_kinetic.cuh", "gks_face.cuh"),
+    "flux": ("gks_flux.cu", "gks_kinetic.cuh", "gks_face.cuh"),
+}
+
+
+def source_hash(kernel: str = "mixed_flux_df") -> str:
+    """Hash of the sources of a face-flux kernel (those its counter record was taken on)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1802_00704_gb300", "csrc")
-    for f in ("gks_flux.cu", "gks_kinetic.cuh", "gks_face.cuh", "gks_flux_df.cu", "gks_lead_df.cuh", "gks_df.cuh",
-              "gks_erfcx_coef.h"):
+    for f in FLUX_SOURCES[kernel]:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -92,7 +102,9 @@ def counter_record(kernel: str):
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
-    cur = source_hash()
+    if kernel not in FLUX_SOURCES:
+        return None
+    cur = source_hash(kernel)
     for line in open(p):
         parts = line.split()
         if len(parts) >= 6 and not line.startswith("#") and parts[0] == kernel and parts[1] == cur:
