@@ -397,8 +397,11 @@ GKS_EXPORT gks_status gks_limit(gks_mesh *mesh, const double *w, const double *c
                                 int32_t *flags, void *stream);
 
 /* One explicit step (Eq. (6)) in place on w (device [4][n_tri]).
- * *dt_inout (host): > 0 fixes the step; <= 0 takes the CFL step and returns it.
- * info (host, may be NULL).  The call synchronises the stream. */
+ * *dt_inout (host): > 0 fixes the step; <= 0 takes the CFL step and returns it
+ * (with graphs on, as one launch of the step-loop graph of gks_run, read back
+ * with one synchronisation).  The step always advances the case, also after a
+ * gks_run that ended it at its end time.  info (host, may be NULL).  The call
+ * synchronises the stream. */
 GKS_EXPORT gks_status gks_step(gks_mesh *mesh, double *w, double *dt_inout, gks_step_info *info, void *stream);
 
 /* Steps w (device [4][n_tri]) in place until t_final (the last step is cut to

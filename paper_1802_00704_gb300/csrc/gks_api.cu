@@ -187,6 +187,52 @@ gks_status create(const CaseIn *cases, int32_t n, const gks_config *cfg, gks_mes
     return GKS_OK;
 }
 
+// One CFL step of a single-case handle (state already in m->wk.w) as one
+// launch of the step-loop graph (loop limit 1, no end time), its results
+// enqueued for the host: *used = false when the graph cannot be used (graphs
+// off, the profiler on), and nothing was launched.
+gks_status step_graph_launch(gks_mesh *m, cudaStream_t s, bool *used)
+{
+    Work &k = m->wk;
+    *used = false;
+    GKS_CUDA(cudaMemsetAsync(k.tfinal, 0, sizeof(double), s));
+    GKS_CUDA(cudaMemsetAsync(k.tcase, 0, sizeof(double), s));
+    gks_status st = run_graph_launch(m, 1, s, used);
+    if (st != GKS_OK || !*used) return st;
+    // the solve's iterations and residuals, the step taken and the status bits
+    const int ns = k.ns;
+    GKS_CUDA(cudaMemcpyAsync(k.h_step, k.beta, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));
+    GKS_CUDA(cudaMemcpyAsync(k.h_step + 4, k.bnorm, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));
+    GKS_CUDA(cudaMemcpyAsync(k.h_step + 8, k.last_dt, sizeof(double), cudaMemcpyDeviceToHost, s));
+    GKS_CUDA(cudaMemcpyAsync(k.h_stepi, k.ctl + kCtlIters * ns, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost, s));
+    GKS_CUDA(cudaMemcpyAsync(k.h_stepi + 4, k.status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    return GKS_OK;
+}
+
+// The results of step_graph_launch once the stream has been synchronised.
+gks_status step_graph_results(gks_mesh *m, gks_step_info *info, double *dt_taken)
+{
+    const Work &k = m->wk;
+    const double rtol = m->cfg.gmres_rtol;
+    int32_t conv = 1;
+    double rr[4];
+    for (int v = 0; v < 4; ++v) {
+        rr[v] = k.h_step[4 + v] > 0.0 ? k.h_step[v] / k.h_step[4 + v] : 0.0;
+        if (rr[v] > rtol) conv = 0;
+    }
+    const gks_status res = code_of(k.h_stepi[4] | (conv ? 0 : kStatusNoConv));
+    if (dt_taken) *dt_taken = k.h_step[8];
+    if (info) {
+        info->dt = k.h_step[8];
+        for (int v = 0; v < 4; ++v) {
+            info->iters[v] = k.h_stepi[v];
+            info->relres[v] = rr[v];
+        }
+        info->status = res;
+    }
+    return res;
+}
+
 }  // namespace
 
 extern "C" {
@@ -396,13 +442,26 @@ gks_status gks_step(gks_mesh *m, double *w, double *dt_inout, gks_step_info *inf
     DeviceGuard g(m->device);
     cudaStream_t s = (cudaStream_t)stream;
     gks_status st;
+    // a new step of the case: no status bits, not done (a run may have ended it)
     GKS_CUDA(cudaMemsetAsync(m->wk.status, 0, sizeof(int32_t) * m->n_case, s));
+    GKS_CUDA(cudaMemsetAsync(m->wk.done, 0, sizeof(int32_t) * m->n_case, s));
     if ((st = launch_permute(w, m->wk.w, m->d.perm, m->d.T, m->n_tri, 4, true, s)) != GKS_OK) return st;
     double dt = 0.0;
-    gks_status res = step_internal(m, dt_inout ? *dt_inout : 0.0, s, info, &dt);
-    if (res != GKS_OK && res != GKS_ENOCONV && res != GKS_ENONPHYS) return res;
-    if ((st = launch_permute(m->wk.w, w, m->d.perm, m->d.T, m->n_tri, 4, false, s)) != GKS_OK) return st;
-    GKS_CUDA(cudaStreamSynchronize(s));
+    gks_status res;
+    // the CFL step as one launch of the step-loop graph, read back with one
+    // synchronisation; a fixed step (or graphs off) takes the host path
+    bool graph = false;
+    if ((!dt_inout || *dt_inout <= 0.0) && (st = step_graph_launch(m, s, &graph)) != GKS_OK) return st;
+    if (graph) {
+        if ((st = launch_permute(m->wk.w, w, m->d.perm, m->d.T, m->n_tri, 4, false, s)) != GKS_OK) return st;
+        GKS_CUDA(cudaStreamSynchronize(s));
+        res = step_graph_results(m, info, &dt);
+    } else {
+        res = step_internal(m, dt_inout ? *dt_inout : 0.0, s, info, &dt);
+        if (res != GKS_OK && res != GKS_ENOCONV && res != GKS_ENONPHYS && res != GKS_ETIMEOUT) return res;
+        if ((st = launch_permute(m->wk.w, w, m->d.perm, m->d.T, m->n_tri, 4, false, s)) != GKS_OK) return st;
+        GKS_CUDA(cudaStreamSynchronize(s));
+    }
     if (dt_inout) *dt_inout = dt;
     return res;
 }

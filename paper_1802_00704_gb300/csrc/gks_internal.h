@@ -175,6 +175,10 @@ struct Work {
     // pinned host mirrors
     int32_t *h_flags = nullptr;      // [4]
     double *h_scal = nullptr;        // [8]
+    // gks_step's results when it runs as one launch of the step-loop graph:
+    // beta, |b| per variable and the step; iterations per variable and status
+    double *h_step = nullptr;        // [9]
+    int32_t *h_stepi = nullptr;      // [5]
 };
 
 // CUDA graphs of the fixed launch sequences of the CLS solve (the start, one

@@ -897,6 +897,8 @@ gks_status build_batch(gks_mesh *m, const CaseIn *cases, int32_t n_cases)
     }
     GKS_CUDA(cudaMallocHost(&k.h_flags, sizeof(int32_t) * 4));
     GKS_CUDA(cudaMallocHost(&k.h_scal, sizeof(double) * 8));
+    GKS_CUDA(cudaMallocHost(&k.h_step, sizeof(double) * 9));
+    GKS_CUDA(cudaMallocHost(&k.h_stepi, sizeof(int32_t) * 5));
     return GKS_OK;
 }
 
@@ -915,8 +917,12 @@ void free_mesh(gks_mesh *m)
     m->allocations.clear();
     if (m->wk.h_flags) cudaFreeHost(m->wk.h_flags);
     if (m->wk.h_scal) cudaFreeHost(m->wk.h_scal);
+    if (m->wk.h_step) cudaFreeHost(m->wk.h_step);
+    if (m->wk.h_stepi) cudaFreeHost(m->wk.h_stepi);
     m->wk.h_flags = nullptr;
     m->wk.h_scal = nullptr;
+    m->wk.h_step = nullptr;
+    m->wk.h_stepi = nullptr;
 }
 
 }  // namespace gks

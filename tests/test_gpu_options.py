@@ -179,6 +179,30 @@ def test_run_graph_equals_the_host_step_loop(G, precision):
     assert cycles > 0 and res[0][3] == res[1][3] + cycles + 7 + 1
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cfl_step_as_a_graph_launch_equals_the_host_step(G, precision):
+    """gks_step with the CFL step runs as one launch of the step-loop graph (one
+    synchronisation); with no_graphs = 1 it takes the host path.  Same kernels:
+    the states and every field of the step info agree exactly, also for a step
+    taken after a run that ended the case at its end time (the step clears the
+    done flag, so the solve runs)."""
+    prec = G.MIXED if precision == "mixed" else G.FP64
+    c = I.shock_vortex_case(40, 20)
+    res = []
+    for mode in (0, 1):
+        m = G.GksMesh(c.mesh, precision=prec, warm_extrap=2, no_graphs=mode)
+        w = dev(c.w0)
+        infos = [m.step(w) for _ in range(4)]
+        tf = 2.5 * infos[-1]["dt"]
+        m.run(w, t_final=tf, max_steps=100)
+        infos.append(m.step(w))
+        res.append((host(w), infos))
+    assert np.array_equal(res[0][0], res[1][0])
+    for a, b in zip(res[0][1], res[1][1]):
+        assert a == b
+    assert min(res[0][1][-1]["iters"]) > 0 and res[0][1][-1]["dt"] > 0.0
+
+
 def test_batch_run_graph_equals_the_host_step_loop(G):
     """The batched run as one graph launch and as the host loop: cases with
     their own end times finish at different loops (the graph keeps stepping the
