@@ -569,6 +569,15 @@ __global__ void __launch_bounds__(kBlock, 3) k_rhs_df(DeviceMesh d, const float 
     if (i < T) {
         double wi[NV], du[3][NV];
         int js[3];
+        // the cell's weights first: their loads overlap the neighbour gathers
+        float ah[3][ND], al[3][ND];
+#pragma unroll
+        for (int s = 0; s < 3; ++s)
+#pragma unroll
+            for (int l = 0; l < ND; ++l) {
+                ah[s][l] = a0p[(s * ND + l) * T + i];
+                al[s][l] = a0p[(15 + s * ND + l) * T + i];
+            }
 #pragma unroll
         for (int v = 0; v < NV; ++v) wi[v] = w[v * T + i];
 #pragma unroll
@@ -595,14 +604,6 @@ __global__ void __launch_bounds__(kBlock, 3) k_rhs_df(DeviceMesh d, const float 
 #pragma unroll
             for (int v = 0; v < NV; ++v) ok &= isfinite(du[s][v]);
         if (ok) {
-            float ah[3][ND], al[3][ND];
-#pragma unroll
-            for (int s = 0; s < 3; ++s)
-#pragma unroll
-                for (int l = 0; l < ND; ++l) {
-                    ah[s][l] = js[s] >= 0 ? a0p[(s * ND + l) * T + i] : 0.0f;
-                    al[s][l] = js[s] >= 0 ? a0p[(15 + s * ND + l) * T + i] : 0.0f;
-                }
             // one variable at a time (ten accumulators live, not forty); each sum
             // runs over the neighbours in order, as the FP64 kernel's does
 #pragma unroll
