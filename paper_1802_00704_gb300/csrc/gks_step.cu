@@ -34,8 +34,10 @@ __global__ void k_update(DeviceMesh d, double *__restrict__ w, const double *__r
         wn[v] = w[v * T + i] + acc[v] * ia;
         w[v * T + i] = wn[v];
     }
-    const double p = (gamma - 1.0) * (wn[3] - 0.5 * (wn[1] * wn[1] + wn[2] * wn[2]) / wn[0]);
-    if (!(wn[0] > 0.0) || !(p > 0.0)) atomicOr(&status[d.blk_case[blockIdx.x]], kStatusNonPhys);
+    // rho > 0 and p > 0, the latter as 2 rho E - |rho U|^2 > 0 (the same sign for
+    // rho > 0): no FP64 division, which GB300 runs on its slow FP64 pipe
+    const double q = 2.0 * wn[3] * wn[0] - (wn[1] * wn[1] + wn[2] * wn[2]);
+    if (!(wn[0] > 0.0) || !(q > 0.0)) atomicOr(&status[d.blk_case[blockIdx.x]], kStatusNonPhys);
 }
 
 // v truncated to FP32 on the integer pipe (no FP64 instruction): false if v is
