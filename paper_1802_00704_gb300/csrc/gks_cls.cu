@@ -310,30 +310,30 @@ __global__ void __launch_bounds__(kBlock, 3)
             for (int w = 0; w < kBlock / 32; ++w) t += double(sh[w][k][v]);
             part[(blockIdx.x * NV + v) * pstride + k] = t;
         }
-        return;
-    }
-    for (int k = 0; k <= j; ++k) {
-        float sv[NV] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (i < T) {
-            const float *vk = V + k * vs;
+    } else {
+        for (int k = 0; k <= j; ++k) {
+            float sv[NV] = {0.0f, 0.0f, 0.0f, 0.0f};
+            if (i < T) {
+                const float *vk = V + k * vs;
+#pragma unroll
+                for (int v = 0; v < NV; ++v)
+#pragma unroll
+                    for (int l = 0; l < ND; ++l) sv[v] = fmaf(vk[(v * ND + l) * T + i], acc[v * ND + l], sv[v]);
+            }
 #pragma unroll
             for (int v = 0; v < NV; ++v)
+                for (int o = 16; o > 0; o >>= 1) sv[v] += __shfl_down_sync(0xffffffffu, sv[v], o);
+            if (lane == 0)
 #pragma unroll
-                for (int l = 0; l < ND; ++l) sv[v] = fmaf(vk[(v * ND + l) * T + i], acc[v * ND + l], sv[v]);
+                for (int v = 0; v < NV; ++v) sh[warp][0][v] = sv[v];
+            __syncthreads();
+            if (threadIdx.x < NV) {
+                double t = 0.0;
+                for (int w = 0; w < kBlock / 32; ++w) t += double(sh[w][0][threadIdx.x]);
+                part[(blockIdx.x * NV + threadIdx.x) * pstride + k] = t;
+            }
+            __syncthreads();
         }
-#pragma unroll
-        for (int v = 0; v < NV; ++v)
-            for (int o = 16; o > 0; o >>= 1) sv[v] += __shfl_down_sync(0xffffffffu, sv[v], o);
-        if (lane == 0)
-#pragma unroll
-            for (int v = 0; v < NV; ++v) sh[warp][0][v] = sv[v];
-        __syncthreads();
-        if (threadIdx.x < NV) {
-            double t = 0.0;
-            for (int w = 0; w < kBlock / 32; ++w) t += double(sh[w][0][threadIdx.x]);
-            part[(blockIdx.x * NV + threadIdx.x) * pstride + k] = t;
-        }
-        __syncthreads();
     }
 }
 
@@ -1373,9 +1373,8 @@ __global__ void k_scale_y(int m, double *y, const double *__restrict__ vn, const
 // basis): y carries 2^-e of the cycle (see k_scale_y) and the sum is scaled
 // back by 2^e in FP64 (exact).
 // y32 (FP32 Z only, optional): the FP32 copy of y, read instead of converting
-// y per thread; the scale 2^e is applied in FP32 when it is a normal FP32
-// number (|e| <= 100), so the FP64 pipe sees one conversion and one add per
-// value.
+// y per thread; the scaled value 2^e acc is formed exactly on the integer pipe
+// (f2d_pow2), so the FP64 pipe sees one add per value.
 template <typename TZ>
 __global__ void k_combine_z(DeviceMesh d, const TZ *__restrict__ Z, const double *__restrict__ y, int m,
                             const int32_t *__restrict__ ctl, int ns, double *__restrict__ x,
@@ -1397,10 +1396,11 @@ __global__ void k_combine_z(DeviceMesh d, const TZ *__restrict__ Z, const double
     }
     if (sexp) {
         const int e = sexp[sy];
-        if (std::is_same<TZ, float>::value && e >= -100 && e <= 100) {
-            const TZ fs = TZ(__int_as_float((e + 127) << 23));   // 2^e, exact
+        if (std::is_same<TZ, float>::value) {
+            // 2^e acc as an FP64 value formed on the integer pipe (exact; no
+            // conversion instruction on the FP64 pipe), one FP64 add per value
 #pragma unroll
-            for (int l = 0; l < ND; ++l) x[(v * ND + l) * T + i] += double(acc[l] * fs);
+            for (int l = 0; l < ND; ++l) x[(v * ND + l) * T + i] += f2d_pow2(float(acc[l]), e);
         } else {
             const double f = pow2(e);
 #pragma unroll
