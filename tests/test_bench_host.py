@@ -158,3 +158,18 @@ def test_flux_kernel_follows_the_configuration():
     assert bench.flux_kernel(NS(flux_lead="fp64", flux_split="on"), True) == ("mixed_flux_ws", "k_face_flux_ws")
     assert bench.flux_kernel(NS(flux_lead="fp64", flux_split="off"), True) == ("mixed_flux", "k_face_flux")
     assert bench.flux_kernel(NS(flux_lead="pairs", flux_split="on"), False) == ("flux", "k_face_flux")
+
+
+def test_counter_records_name_known_kernels_and_the_default_one_is_current():
+    """Every record of profiles/traffic.txt names a flux kernel whose sources
+    bench.py knows, each kernel's hash covers only its own files, and the
+    default mixed kernel's record was taken on its current sources (else the
+    benchmark's roofline would have no achieved rate)."""
+    p = os.path.join(bench.ROOT, "profiles", "traffic.txt")
+    for line in open(p):
+        if line.startswith("#") or not line.strip():
+            continue
+        assert line.split()[0] in bench.FLUX_SOURCES
+    assert bench.source_hash("mixed_flux_df") != bench.source_hash("flux")
+    rec = bench.counter_record("mixed_flux_df")
+    assert rec is not None and rec["fp32_flop_per_gp"] > 0 and rec["dram_bytes"] > 0
