@@ -732,8 +732,12 @@ __device__ __forceinline__ void ilu_fwd_row(const DeviceMesh &d, const TP *__res
         constexpr int NA = G ? ND : 2;
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
-            const int j = d.nb[s * T + i];
-            if (j < 0 || j >= i) continue;
+            // every slot's loads are issued (a slot that is not a lower
+            // neighbour reads the cell's own data, which is discarded), only the
+            // accumulation is conditional: the gathers of the slots overlap
+            const int jn = d.nb[s * T + i];
+            const bool lower = jn >= 0 && jn < i;
+            const int64_t j = lower ? jn : i;
             const TM sa = TM(alg[s * T + i]), sax = sa * TM(exg[s * T + i]), say = sa * TM(eyg[s * T + i]);
             TM zn[NV][NA];
             if (use_nb == 2) {
@@ -764,6 +768,7 @@ __device__ __forceinline__ void ilu_fwd_row(const DeviceMesh &d, const TP *__res
 #pragma unroll
                     for (int a = 0; a < NA; ++a) zn[v][a] = TM(zin[(v * ND + a) * T + j]);
             }
+            if (!lower) continue;
 #pragma unroll
             for (int v = 0; v < NV; ++v) oacc(sa, sax, say, zn[v][0], zn[v][1], y + v * ND);
             if constexpr (G) {
