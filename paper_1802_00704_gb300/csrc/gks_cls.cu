@@ -1008,14 +1008,24 @@ __global__ void __launch_bounds__(kBlock, sizeof(TM) == 4 ? 3 : 2) k_ilu_bwd2(De
         TM yj[NX];
 #pragma unroll
         for (int q = 0; q < NX; ++q) yj[q] = TM(0);
-#pragma unroll 1
-        for (int s2 = 0; s2 < 3; ++s2) {
-            const int k = d.nb[s2 * T + j];
-            if (k <= j) continue;
-            const TM sb = TM(alg[s2 * T + j]), sbx = sb * TM(exg[s2 * T + j]), sby = sb * TM(eyg[s2 * T + j]);
+        // the three slots' loads issued together (a slot that is not an upper
+        // neighbour of j reads j's own values, discarded); only the sums are
+        // conditional, in slot order
 #pragma unroll
-            for (int v = 0; v < NV; ++v)
-                oacc(sb, sbx, sby, TM(xin[(v * ND + 0) * T + k]), TM(xin[(v * ND + 1) * T + k]), yj + v * ND);
+        for (int s2 = 0; s2 < 3; ++s2) {
+            const int kn = d.nb[s2 * T + j];
+            const bool upper = kn > j;
+            const int64_t k = upper ? kn : j;
+            const TM sb = TM(alg[s2 * T + j]), sbx = sb * TM(exg[s2 * T + j]), sby = sb * TM(eyg[s2 * T + j]);
+            TM xk[NV][2];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                xk[v][0] = TM(xin[(v * ND + 0) * T + k]);
+                xk[v][1] = TM(xin[(v * ND + 1) * T + k]);
+            }
+            if (!upper) continue;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) oacc(sb, sbx, sby, xk[v][0], xk[v][1], yj + v * ND);
         }
         TM x1[NV][2];
 #pragma unroll
