@@ -173,3 +173,21 @@ def test_counter_records_name_known_kernels_and_the_default_one_is_current():
     assert bench.source_hash("mixed_flux_df") != bench.source_hash("flux")
     rec = bench.counter_record("mixed_flux_df")
     assert rec is not None and rec["fp32_flop_per_gp"] > 0 and rec["dram_bytes"] > 0
+
+
+def test_reference_arm_prints_its_line():
+    """bench.py --impl reference times the oracle on the host cores (the only
+    reference this tier has) and prints the contract's line: impl, the metric of
+    the GPU arm, a cpu_baseline describing the run and an e2e with no copies."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=bench.ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["value"] > 0
+    assert line["higher_is_better"] is True and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["cpu_baseline"]["value"] == line["value"] and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
